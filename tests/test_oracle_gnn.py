@@ -1,0 +1,232 @@
+"""Pins of the oracle's GNN (Sec. 4.2 "Architecture", App. A.3), the loss
+Eq. (loss_Ab) with its gradient, and Adam (App. A.4)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2305_16432_gb300 import inputs as I
+
+
+def _unpack(cfg, w):
+    """Flat weights -> list of MLPs, each a list of (W, b)."""
+    w = np.asarray(w, np.float64)
+    lin = cfg.linears()
+    mats, k = [], 0
+    for fi, fo in lin:
+        W = w[k:k + fi * fo].reshape(fo, fi)
+        k += fi * fo
+        b = w[k:k + fo]
+        k += fo
+        mats.append((W, b))
+    sizes = [cfg.l + 1] * 2 + [cfg.l_mp + 1, cfg.l_mp + 1] * cfg.n_mp + [cfg.l + 1]
+    out, k = [], 0
+    for s in sizes:
+        out.append(mats[k:k + s])
+        k += s
+    assert k == len(mats)
+    return out
+
+
+def _mlp(layers, X):
+    """Batched MLP over the last axis: ReLU between Linears, none at the end."""
+    for q, (W, b) in enumerate(layers):
+        X = X @ W.T + b
+        if q < len(layers) - 1:
+            X = np.maximum(X, 0)
+    return X
+
+
+def _dense_gnn(cfg, D, b, w):
+    """Independent dense-tensor formulation: node features V [n, h], edge
+    features E [n, n, h] on the nonzeros of D; message passing as a masked
+    einsum.  Returns the lower-triangular L as a dense matrix."""
+    n = D.shape[0]
+    mask = D != 0
+    mlps = _unpack(cfg, w)
+    s = np.max(np.diag(D))
+    binf = np.max(np.abs(b)) or 1.0
+    V = _mlp(mlps[0], (b / binf)[:, None])
+    E = _mlp(mlps[1], (D / s)[:, :, None]) * mask[:, :, None]
+    for t in range(cfg.n_mp):
+        agg = np.einsum("ijh,jh->ih", E, V)                 # sum_j e_ij (.) v_j
+        V = _mlp(mlps[2 + 2 * t], np.concatenate([V, agg], 1))
+        X = np.concatenate([E, np.broadcast_to(V[:, None, :], E.shape),
+                            np.broadcast_to(V[None, :, :], E.shape)], 2)
+        E = _mlp(mlps[3 + 2 * t], X) * mask[:, :, None]
+    S = _mlp(mlps[-1], E)[:, :, 0] * mask
+    sym = 0.5 * (S + S.T)
+    L = np.tril(sym, -1)
+    sp = np.maximum(np.diag(S), 0) + np.log1p(np.exp(-np.abs(np.diag(S))))
+    L[np.diag_indices(n)] = sp
+    return math.sqrt(s) * L * np.tril(mask)
+
+
+@pytest.mark.parametrize("cfg", [I.GnnConfig(n_mp=2, l=2, l_mp=2, h=4),
+                                 I.GnnConfig(n_mp=3, l=1, l_mp=2, h=5),
+                                 I.GnnConfig(n_mp=0, l=2, l_mp=2, h=3)])
+def test_gnn_matches_dense_formulation(cfg):
+    A = O.assemble(I.fem2d(6, sigma=1.0, seed=2))
+    b = I.rhs(A.n, 3)
+    w = I.gnn_weights(cfg, 7, scale=2.0)
+    L = O.gnn_forward(cfg, A, b, w)
+    Ld = _dense_gnn(cfg, A.dense(), b, w)
+    assert np.allclose(L.dense(), Ld, rtol=1e-12, atol=1e-12 * np.abs(Ld).max())
+    assert O.gnn_nparams(cfg) == cfg.nparams == len(w)
+
+
+def test_gnn_zero_weights():
+    cfg = I.GnnConfig(n_mp=2, l=2, l_mp=2, h=8)
+    A = O.assemble(I.fd2d(5, 4, sigma=1.0, seed=1))
+    L = O.gnn_forward(cfg, A, I.rhs(A.n, 1), np.zeros(cfg.nparams))
+    D = L.dense()
+    s = A.dense().diagonal().max()
+    assert np.allclose(np.diag(D), math.sqrt(s) * math.log(2.0), rtol=1e-15)
+    assert np.all(np.tril(D, -1) == 0)
+
+
+def test_gnn_no_message_passing_is_elementwise():
+    # n_mp = 0: L_ij depends on A_ij only (A symmetric), L_ii on A_ii only
+    cfg = I.GnnConfig(n_mp=0, l=2, l_mp=2, h=6)
+    w = I.gnn_weights(cfg, 3)
+    A = O.assemble(I.fd2d(6, 6, sigma=1.0, seed=4))
+    L1 = O.gnn_forward(cfg, A, I.rhs(A.n, 1), w)
+    L2 = O.gnn_forward(cfg, A, I.rhs(A.n, 2), w)      # b does not reach L
+    assert np.array_equal(L1.val, L2.val)
+    _, a2l = O.tril(A)
+    vals = {}
+    for k in range(A.nnz):
+        if a2l[k] >= 0:
+            vals.setdefault(round(A.val[k], 15), set()).add(round(L1.val[a2l[k]], 12))
+    assert all(len(v) == 1 for v in vals.values())
+
+
+def test_gnn_permutation_equivariance():
+    cfg = I.GnnConfig(n_mp=2, l=2, l_mp=2, h=6)
+    w = I.gnn_weights(cfg, 5, scale=1.5)
+    A = O.assemble(I.fem2d(7, sigma=1.0, seed=9))
+    b = I.rhs(A.n, 9)
+    D = A.dense()
+    perm = np.random.default_rng(0).permutation(A.n)
+    Dp = D[np.ix_(perm, perm)]
+    rp, ci, v = [0], [], []
+    for i in range(A.n):
+        nz = np.nonzero(Dp[i])[0]
+        ci += list(nz)
+        v += list(Dp[i, nz])
+        rp.append(len(ci))
+    Ap = O.CSR(rp, ci, v)
+    _, s = O.gnn_forward(cfg, A, b, w, return_s=True)
+    _, sp = O.gnn_forward(cfg, Ap, b[perm], w, return_s=True)
+    S = np.zeros_like(D)
+    Sp = np.zeros_like(D)
+    for M, AA, ss in ((S, A, s), (Sp, Ap, sp)):
+        for i in range(AA.n):
+            for k in range(AA.row_ptr[i], AA.row_ptr[i + 1]):
+                M[i, AA.col_idx[k]] = ss[k]
+    assert np.allclose(Sp, S[np.ix_(perm, perm)], rtol=1e-12, atol=1e-12)
+
+
+def test_gnn_preconditioner_is_spd():
+    cfg = I.GnnConfig(n_mp=2, l=2, l_mp=2, h=8)
+    A = O.assemble(I.fem2d(8, sigma=1.0, seed=5))
+    L = O.gnn_forward(cfg, A, I.rhs(A.n, 0), I.gnn_weights(cfg, 1))
+    P = L.dense() @ L.dense().T
+    assert np.allclose(P, P.T) and np.linalg.eigvalsh(P).min() > 0
+
+
+# ----------------------------------------------------------------- loss
+def _tiny_system():
+    A = O.assemble(I.fem2d(5, sigma=1.0, seed=3))          # n = 9
+    return A
+
+
+def test_loss_zero_for_exact_factor_and_solution():
+    n = 12
+    T = 2 * np.eye(n) - np.eye(n, k=1) - np.eye(n, k=-1)
+    rp, ci, v = [0], [], []
+    for i in range(n):
+        nz = np.nonzero(T[i])[0]
+        ci += list(nz)
+        v += list(T[i, nz])
+        rp.append(len(ci))
+    A = O.CSR(rp, ci, v)
+    L, _ = O.ic0(A)                                          # exact on a tridiagonal
+    B = I.rhs(n, 4, count=3)
+    X = np.linalg.solve(T, B.T).T
+    loss, dL = O.llt_loss(L, X, B)
+    assert loss < 1e-25 and np.abs(dL).max() < 1e-12
+
+
+def test_loss_gradient_wrt_L_by_finite_differences():
+    A = _tiny_system()
+    L, _ = O.ic0(A)
+    g = np.random.default_rng(0)
+    L = O.CSR(L.row_ptr, L.col_idx, L.val + 0.1 * g.standard_normal(L.nnz))
+    X = g.standard_normal((3, A.n))
+    B = g.standard_normal((3, A.n))
+    loss, dL = O.llt_loss(L, X, B)
+    # loss definition by dense matrices
+    Ld = L.dense()
+    dense = np.mean([np.sum((Ld @ Ld.T @ X[p] - B[p]) ** 2) for p in range(3)])
+    assert math.isclose(loss, dense, rel_tol=1e-13)
+    eps = 1e-6
+    for k in range(L.nnz):
+        vp, vm = L.val.copy(), L.val.copy()
+        vp[k] += eps
+        vm[k] -= eps
+        fp = O.llt_loss(O.CSR(L.row_ptr, L.col_idx, vp), X, B, False)[0]
+        fm = O.llt_loss(O.CSR(L.row_ptr, L.col_idx, vm), X, B, False)[0]
+        fd = (fp - fm) / (2 * eps)
+        assert abs(fd - dL[k]) <= 1e-6 * max(1.0, abs(dL[k]))
+
+
+@pytest.mark.parametrize("cfg", [I.GnnConfig(n_mp=2, l=2, l_mp=2, h=3),
+                                 I.GnnConfig(n_mp=1, l=1, l_mp=1, h=4)])
+def test_loss_and_grad_central_differences(cfg):
+    # central differences, eps = 1e-6, FP64, on every weight
+    A = _tiny_system()
+    g = np.random.default_rng(1)
+    B = g.standard_normal((2, A.n))
+    X = np.linalg.solve(A.dense(), B.T).T
+    w = I.gnn_weights(cfg, 2, scale=1.5).astype(np.float64)
+    loss, grad = O.loss_and_grad(cfg, A, X, B, w)
+    # relative error per weight; components far below the largest one are
+    # measured against 1e-3 of it, because there the rounding noise of the
+    # difference quotient (~ 1e-16 * loss / eps) dominates
+    eps = 1e-6
+    floor = 1e-3 * np.abs(grad).max()
+    err = 0.0
+    for k in range(len(w)):
+        wp, wm = w.copy(), w.copy()
+        wp[k] += eps
+        wm[k] -= eps
+        fd = (O.loss_and_grad(cfg, A, X, B, wp, False)[0] -
+              O.loss_and_grad(cfg, A, X, B, wm, False)[0]) / (2 * eps)
+        err = max(err, abs(fd - grad[k]) / max(floor, abs(grad[k])))
+    assert err < 1e-6, err
+    # loss equals the mean over pairs of ||L L^T x - b||^2 of the forward L
+    lp = []
+    for p in range(2):
+        L = O.gnn_forward(cfg, A, B[p], w).dense()
+        lp.append(np.sum((L @ L.T @ X[p] - B[p]) ** 2))
+    assert math.isclose(loss, np.mean(lp), rel_tol=1e-12)
+
+
+def test_adam_single_step_by_hand():
+    # w = [1, -2], g = [0.5, -0.1], first step: m_hat = g, v_hat = g^2,
+    # update = lr * g / (|g| + eps)
+    w = np.array([1.0, -2.0])
+    g = np.array([0.5, -0.1])
+    m, v = np.zeros(2), np.zeros(2)
+    O.adam(w, g, m, v, 1)
+    expect = np.array([1.0 - 1e-3 * 0.5 / (0.5 + 1e-8), -2.0 + 1e-3 * 0.1 / (0.1 + 1e-8)])
+    assert np.allclose(w, expect, rtol=0, atol=1e-15)
+    assert np.allclose(m, [0.05, -0.01]) and np.allclose(v, [0.00025, 0.00001])
+    # second step with the same gradient: m = 0.19 g, v = 0.001999 g^2
+    O.adam(w, g, m, v, 2)
+    mh = 0.19 * g / (1 - 0.81)
+    vh = 0.001999 * g * g / (1 - 0.998001)
+    expect2 = expect - 1e-3 * mh / (np.sqrt(vh) + 1e-8)
+    assert np.allclose(w, expect2, rtol=0, atol=1e-15)
