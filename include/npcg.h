@@ -1,0 +1,270 @@
+/*
+ * npcg.h -- C ABI of the GB300 learned-preconditioner PCG library
+ * (Li, Chen, Du, Matusik, "Learning Preconditioners for Conjugate Gradient
+ * PDE Solvers", ICML 2023).
+ *
+ * The library solves A x = b for sparse SPD A from a discretised linear
+ * second-order PDE (Sec. 3, "Discretization") with PCG (Algorithm 1) and the
+ * preconditioner P = L L^T, where L lives on the lower-triangular pattern of
+ * A and is written by a graph network over the sparsity graph of A
+ * (Sec. 4.1-4.2, App. A.3).  IC(0), Jacobi and plain CG are the comparison
+ * preconditioners (Sec. 5.1, "Baseline Methods").
+ *
+ * Conventions for every call:
+ *   - All array arguments are DEVICE pointers on the handle's device unless
+ *     a parameter says "host".  The caller allocates and owns every array
+ *     it passes; the library never frees caller memory.  Objects the library
+ *     creates (handles, patterns) are freed by their own destroy call.
+ *   - Work is enqueued on the handle's stream.  A call returns after
+ *     enqueueing unless it returns host data (documented per call), in which
+ *     case it synchronises that stream.
+ *   - Indices are int32, row-major CSR with strictly ascending columns; the
+ *     pattern of A must be structurally symmetric with every diagonal entry
+ *     present (a matrix of an undirected mesh graph with self-loops).
+ *   - The return code is the only error channel.  On error, npcg_last_error()
+ *     gives a one-line description.  Calls never abort the process.
+ *   - Device-side waits (the sync-free triangular solves and IC(0)) have an
+ *     iteration limit; reaching it returns NPCG_ETIMEOUT and leaves the
+ *     context usable.
+ */
+#ifndef NPCG_H
+#define NPCG_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define NPCG_API __attribute__((visibility("default")))
+#else
+#define NPCG_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    NPCG_OK = 0,
+    NPCG_EINVAL = 1,       /* malformed argument or matrix pattern           */
+    NPCG_ENOMEM = 2,       /* device allocation failed                       */
+    NPCG_ECUDA = 3,        /* CUDA runtime error                             */
+    NPCG_ENOTSPD = 4,      /* IC(0) failed for every shift; L_ii <= 0        */
+    NPCG_EBREAKDOWN = 5,   /* PCG: p^T A p <= 0, r^T z <= 0, or non-finite   */
+    NPCG_EMAXITER = 6,     /* PCG: max_iter updates without reaching rtol    */
+    NPCG_ETIMEOUT = 7      /* a device spin-wait reached its iteration limit */
+} npcg_status;
+
+typedef struct npcg_handle_s* npcg_handle;     /* stream, workspace, error text */
+typedef struct npcg_pattern_s* npcg_pattern;   /* analysed sparsity pattern     */
+
+/* --------------------------------------------------------------------------
+ * Handle.
+ * ------------------------------------------------------------------------ */
+/* Creates a handle bound to the current CUDA device and to `stream`
+ * (a cudaStream_t; NULL = legacy default stream).  *out is owned by the
+ * caller and released with npcg_destroy. */
+NPCG_API npcg_status npcg_create(npcg_handle* out, void* stream);
+NPCG_API npcg_status npcg_destroy(npcg_handle h);
+/* Last error message of the handle (static storage owned by the handle). */
+NPCG_API const char* npcg_last_error(npcg_handle h);
+NPCG_API const char* npcg_status_string(npcg_status s);
+
+/* --------------------------------------------------------------------------
+ * Assembly of A (Sec. 3 "Discretization": Galerkin stiffness matrix of
+ * -div(k grad u) = f with homogeneous Dirichlet boundary).  The paper's own
+ * meshes are not available; the problems are synthetic stand-ins:
+ *   NPCG_FD : 5-point (dim 2) / 7-point (dim 3) finite differences on the
+ *             nx x ny (x nz) interior grid of the unit square / cube, natural
+ *             order (x fastest); face coefficient = harmonic mean of the
+ *             nodal k; h factors dropped.
+ *   NPCG_FEM: P1 elements on the Delaunay triangulation of an m x m lattice
+ *             (m = nx) on [0,1]^2 with integer jitter (units of 1/1024 of the
+ *             spacing); boundary points are eliminated, (m-2)^2 unknowns,
+ *             index (a-1) + (m-2)(c-1).  The cell diagonal is chosen by the
+ *             exact in-circle predicate (ties: (a,c)-(a+1,c+1)); an edge
+ *             whose every cotangent numerator is exactly zero is dropped.
+ * log k is a Gaussian random field by random Fourier features:
+ *   g(p) = sigma sqrt(2/M) sum_m cos(omega_m . p + phase_m),  k = exp(g),
+ * k at the nodes (FD) or k_T = exp(mean of the three nodal g) (FEM).
+ * ------------------------------------------------------------------------ */
+enum { NPCG_FD = 0, NPCG_FEM = 1 };
+
+typedef struct {
+    int32_t kind;             /* NPCG_FD or NPCG_FEM                            */
+    int32_t dim;              /* 2 or 3 (FEM: 2)                                */
+    int32_t nx, ny, nz;       /* FD: interior grid; FEM: nx = m lattice points  */
+    int32_t n_features;       /* M, number of random Fourier features           */
+    double sigma;             /* GRF standard deviation (0: k == 1)             */
+    const double* omega;      /* device [M * dim] frequencies                   */
+    const double* phase;      /* device [M] phases                              */
+    const int32_t* jitter;    /* device [m * m * 2] (FEM only; NULL for FD)     */
+} npcg_problem;
+
+/* Size of the assembled system: *n_out, *nnz_out (host).  Synchronises. */
+NPCG_API npcg_status npcg_assemble_count(npcg_handle h, const npcg_problem* p,
+                                int64_t* n_out, int64_t* nnz_out);
+/* Assembles A into caller arrays row_ptr [n+1], col_idx [nnz], val [nnz]
+ * (sizes from npcg_assemble_count). */
+NPCG_API npcg_status npcg_assemble_system(npcg_handle h, const npcg_problem* p,
+                                 int32_t* row_ptr, int32_t* col_idx, double* val);
+
+/* --------------------------------------------------------------------------
+ * Pattern analysis (the sparsity graph of A, Sec. 4.2, and the triangular
+ * structure of "Solve P z = r", Algorithm 1): validation, L = tril(A) pattern,
+ * mirror edges e_ij <-> e_ji, forward/backward level sets of L y = r and
+ * L^T z = y (computed on the device), and the level-ordered layouts used by
+ * the solvers.  A pattern may hold nsys independent systems concatenated
+ * block-diagonally (row offsets sys_ptr, host [nsys+1], sys_ptr[0] = 0,
+ * sys_ptr[nsys] = n; NULL when nsys == 1).  The row_ptr / col_idx arrays are
+ * copied; the caller may free them afterwards.  Synchronises.
+ * ------------------------------------------------------------------------ */
+NPCG_API npcg_status npcg_analyse(npcg_handle h, int64_t n, int64_t nnz, const int32_t* row_ptr,
+                         const int32_t* col_idx, int32_t nsys, const int64_t* sys_ptr,
+                         npcg_pattern* out);
+NPCG_API npcg_status npcg_pattern_free(npcg_pattern p);
+
+typedef struct {
+    int64_t n, nnz, nnz_L;
+    int32_t nsys;
+    int32_t nlev_fwd, nlev_bwd;   /* number of levels of L y = r / L^T z = y */
+} npcg_pattern_info;
+NPCG_API npcg_status npcg_pattern_get_info(npcg_pattern p, npcg_pattern_info* out);  /* host out */
+
+/* Copies of the analysis results (device arrays, caller-allocated):
+ * L_row_ptr [n+1], L_col_idx [nnz_L] (tril(A), diagonal last in each row),
+ * lev_fwd / lev_bwd [n] (level of each row), perm_fwd / perm_bwd [n] (rows in
+ * processing order: by level, ascending row within a level).  Any pointer
+ * may be NULL. */
+NPCG_API npcg_status npcg_pattern_export(npcg_handle h, npcg_pattern p, int32_t* L_row_ptr,
+                                int32_t* L_col_idx, int32_t* lev_fwd, int32_t* lev_bwd,
+                                int32_t* perm_fwd, int32_t* perm_bwd);
+
+/* --------------------------------------------------------------------------
+ * Graph-network factor (Sec. 4.2 "Architecture", App. A.3).
+ *   MLP of depth d: Linear(in,h) ReLU [Linear(h,h) ReLU] x (d-1) Linear(h,out)
+ *   node input b_i / ||b||_inf, edge input A_ij / s with s = max_i A_ii
+ *   (per system), encoders of depth l to width h;
+ *   n_mp times:  v_i <- MLP_v([v_i || sum_j e_ij (.) v_j])   (j over row i)
+ *                e_ij <- MLP_e([e_ij || v_i || v_j])          (new v)
+ *   decoder of depth l: s_ij = MLP_dec(e_ij);
+ *   L_ij = sqrt(s) (s_ij + s_ji) / 2 for i > j;  L_ii = sqrt(s) softplus(s_ii)
+ * Flat FP32 weights: node encoder, edge encoder, n_mp x (node MLP with input
+ * 2h, edge MLP with input 3h, both of depth l_mp), decoder (output 1); each
+ * Linear stored as W[out][in] row-major followed by bias[out].
+ * ------------------------------------------------------------------------ */
+enum { NPCG_FP32 = 0, NPCG_BF16 = 1 };
+enum { NPCG_DIAG_SOFTPLUS = 0 };
+
+typedef struct {
+    int32_t n_mp;        /* message-passing layers                       */
+    int32_t l;           /* depth of encoders and decoder                */
+    int32_t l_mp;        /* depth of the node / edge update MLPs         */
+    int32_t h;           /* hidden = latent width: 16, 32 or 64          */
+    int32_t diag_mode;   /* NPCG_DIAG_SOFTPLUS                           */
+    int32_t precision;   /* NPCG_FP32 (parity) or NPCG_BF16 (tensor cores)*/
+} npcg_gnn_config;
+
+/* Number of FP32 parameters of the flat weight vector (host out). */
+NPCG_API npcg_status npcg_gnn_nparams(const npcg_gnn_config* cfg, int64_t* out);
+/* L values on the tril(A) pattern (order of npcg_pattern_export's L arrays),
+ * FP64 [nnz_L].  A_val [nnz], b [n], weights [nparams]. */
+NPCG_API npcg_status npcg_gnn_factor(npcg_handle h, npcg_pattern p, const double* A_val,
+                            const double* b, const npcg_gnn_config* cfg,
+                            const float* weights, double* L_val);
+
+/* --------------------------------------------------------------------------
+ * IC(0) (Sec. 5.1 baseline "IC"), textbook row-oriented form on tril(A):
+ *   L_ij = (A_ij - sum_{k<j} L_ik L_jk) / L_jj,  L_ii = sqrt(A_ii - sum L_ik^2).
+ * On a non-positive pivot a system is refactored from A + alpha diag(A),
+ * alpha = 1e-3 * 2^t, t = 0..30.  alpha_out (host [nsys], may be NULL)
+ * receives the shift used per system (0: none).  Synchronises.
+ * ------------------------------------------------------------------------ */
+NPCG_API npcg_status npcg_ic0_factor(npcg_handle h, npcg_pattern p, const double* A_val,
+                            double* L_val, double* alpha_out);
+
+/* --------------------------------------------------------------------------
+ * Preconditioned conjugate gradient, Algorithm 1, in FP64.
+ * Stops when ||r_k||_2 <= rtol ||b||_2 (per system).  iters counts the
+ * updates of x (Algorithm 1's k).  x holds x_0 on entry, the solution on
+ * exit.  precond: NPCG_PREC_NONE (plain CG), NPCG_PREC_JACOBI (P = diag A),
+ * NPCG_PREC_LLT (P = L L^T with L_val [nnz_L] on tril(A), FP64).
+ * The iteration runs as a CUDA graph with a device-side while loop; the
+ * call synchronises once at the end to return the stats (host [nsys]).
+ * Returns NPCG_OK if every system converged, else the first failing
+ * system's status (per-system codes are in stats).
+ * ------------------------------------------------------------------------ */
+enum { NPCG_PREC_NONE = 0, NPCG_PREC_JACOBI = 1, NPCG_PREC_LLT = 2 };
+
+typedef struct {
+    int32_t iters;       /* updates of x                                  */
+    int32_t status;      /* npcg_status of this system                    */
+    double relres;       /* ||r_k|| / ||b|| (recursive residual)          */
+} npcg_solve_stats;
+
+NPCG_API npcg_status npcg_pcg_solve(npcg_handle h, npcg_pattern p, const double* A_val,
+                           const double* b, double* x, int32_t precond,
+                           const double* L_val, double rtol, int32_t max_iter,
+                           npcg_solve_stats* stats);
+/* Same recurrence for every system of a multi-system pattern at once, in one
+ * graph of persistent-style launches over the concatenated CSR, with
+ * per-system alpha, beta and convergence masks.  stats: host [nsys]. */
+NPCG_API npcg_status npcg_pcg_solve_batched(npcg_handle h, npcg_pattern p, const double* A_val,
+                                   const double* b, double* x, int32_t precond,
+                                   const double* L_val, double rtol, int32_t max_iter,
+                                   npcg_solve_stats* stats);
+
+/* --------------------------------------------------------------------------
+ * Building blocks of the iteration (Algorithm 1), exposed for tests and
+ * bandwidth measurement.  y = A x:
+ * ------------------------------------------------------------------------ */
+NPCG_API npcg_status npcg_spmv(npcg_handle h, npcg_pattern p, const double* A_val,
+                      const double* x, double* y);
+/* Loads L_val [nnz_L] into the pattern's level-ordered solve layouts. */
+NPCG_API npcg_status npcg_factor_load(npcg_handle h, npcg_pattern p, const double* L_val);
+/* With the loaded factor: transpose == 0 solves L y = r, transpose == 1
+ * solves L^T y = r (r, y [n], distinct). */
+NPCG_API npcg_status npcg_sptrsv(npcg_handle h, npcg_pattern p, int32_t transpose,
+                        const double* r, double* y);
+/* Same solve repeated reps times; *ms_per_launch (host) is the mean duration
+ * of the triangular-solve kernel alone, from CUDA events recorded on the
+ * handle's stream around each launch.  Synchronises. */
+NPCG_API npcg_status npcg_sptrsv_timed(npcg_handle h, npcg_pattern p, int32_t transpose,
+                              const double* r, double* y, int32_t reps, double* ms_per_launch);
+
+/* --------------------------------------------------------------------------
+ * Training loss Eq. (loss_Ab): loss = mean over pairs and systems of
+ * ||L L^T x - b||^2, each pair with its own GNN forward (node input b).
+ * X, B: [npairs][n] (row p holds pair p of every system of the pattern).
+ * loss_out: host.  grad: device [nparams] FP32, overwritten with d loss /
+ * d weights (hand-written adjoint of the loss and of the network).
+ * Synchronises.
+ * ------------------------------------------------------------------------ */
+NPCG_API npcg_status npcg_loss_and_grad(npcg_handle h, npcg_pattern p, const double* A_val,
+                               int32_t npairs, const double* X, const double* B,
+                               const npcg_gnn_config* cfg, const float* weights,
+                               double* loss_out, float* grad);
+
+/* Adam step (App. A.4: Adam, lr 1e-3) on FP32 master weights, in place.
+ * t is the 1-based step count; m, v are the moment buffers [n]. */
+NPCG_API npcg_status npcg_adam_step(npcg_handle h, int64_t n, float* w, const float* g, float* m,
+                           float* v, int32_t t, float lr, float beta1, float beta2,
+                           float eps);
+
+/* --------------------------------------------------------------------------
+ * End to end from HOST buffers (the paper's timed quantity, Sec. 5.1
+ * "Evaluation Metrics": precompute + solve).  Copies A_val_host [nnz] and
+ * b_host [n] in, builds the preconditioner (method: NPCG_METHOD_GNN with
+ * cfg + device weights, NPCG_METHOD_IC0, NPCG_METHOD_JACOBI, NPCG_METHOD_CG),
+ * runs PCG from x_0 = 0 and copies x out to x_host [n].  Host buffers should
+ * be pinned for asynchronous copies.  stats: host [nsys].  Synchronises.
+ * ------------------------------------------------------------------------ */
+enum { NPCG_METHOD_GNN = 0, NPCG_METHOD_IC0 = 1, NPCG_METHOD_JACOBI = 2, NPCG_METHOD_CG = 3 };
+
+NPCG_API npcg_status npcg_solve_host(npcg_handle h, npcg_pattern p, int32_t method,
+                            const npcg_gnn_config* cfg, const float* weights,
+                            const double* A_val_host, const double* b_host, double* x_host,
+                            double rtol, int32_t max_iter, npcg_solve_stats* stats);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NPCG_H */

@@ -1,0 +1,237 @@
+// Internal declarations of the npcg CUDA library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/npcg.h"
+
+namespace npcg {
+
+// ---------------------------------------------------------------------------
+// limits and launch shapes
+// ---------------------------------------------------------------------------
+constexpr int kWarp = 32;
+constexpr int kSlice = 32;                 // rows per SELL slice = one warp of the solve
+constexpr int kChunk = 2048;               // rows per reduction chunk (one block)
+constexpr int kChunkThreads = 256;
+constexpr long long kSpinLimit = 1LL << 22; // polls before a device wait gives up (~1-2 s)
+
+// bits of a canonical-free signalling NaN: "value not yet written"
+constexpr unsigned long long kSentinelBits = 0x7FF4DEADBEEFCAFEull;
+constexpr int kLevelUnset = -1;
+
+// status word flags (device)
+enum : int { kFlagTimeout = 1, kFlagBadPattern = 2, kFlagNotSpd = 4, kFlagAbort = 8 };
+
+// ---------------------------------------------------------------------------
+// device memory: a typed, owned allocation
+// ---------------------------------------------------------------------------
+template <class T>
+struct DevBuf {
+    T* p = nullptr;
+    size_t n = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf() { release(); }
+    cudaError_t alloc(size_t count) {
+        release();
+        n = count;
+        if (count == 0) return cudaSuccess;
+        return cudaMalloc(&p, count * sizeof(T));
+    }
+    // grow-only reuse
+    cudaError_t ensure(size_t count) { return count <= n && p ? cudaSuccess : alloc(count); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+};
+
+struct Handle;
+
+// Per-system PCG state (device).
+struct SysState {
+    double tol2;      // (rtol ||b||)^2
+    double rr;        // ||r||^2
+    double rz;        // r^T z (current)
+    double pw;        // p^T A p
+    double alpha, beta;
+    double bnorm2;
+    int iters;
+    int status;       // npcg_status
+    int active;       // 1 while iterating
+    int max_iter;
+};
+
+// Chunk of rows of one system (reductions and vector kernels).
+struct Chunk {
+    int32_t sys;
+    int32_t row0, row1;     // [row0, row1)
+    int32_t slot;           // index of this chunk's partial
+};
+
+// Level-ordered SELL-32 layout of one triangular factor (off-diagonals only).
+struct TriLayout {
+    int32_t nslices = 0;
+    int32_t nlev = 0;
+    DevBuf<int32_t> perm;        // [n] row at each position
+    DevBuf<int32_t> level;       // [n] level of each row
+    DevBuf<int64_t> slice_off;   // [nslices+1] slot offset of each slice
+    DevBuf<int32_t> slice_w;     // [nslices] width
+    DevBuf<int32_t> col;         // [slots] column, -1 = padding
+    DevBuf<int32_t> src;         // [slots] index into L_val, -1 = padding
+    DevBuf<int32_t> diag_src;    // [n by position] index of the diagonal in L_val
+    DevBuf<double> val;          // [slots] loaded factor values
+    DevBuf<double> diag;         // [n by position] loaded diagonal
+    int64_t slots = 0;
+};
+
+// graph-network feature buffers, grown on demand
+struct GnnStore {
+    DevBuf<float> v, e, s;         // node / edge features, decoder outputs
+    DevBuf<double> sc;             // per-system input scales
+    DevBuf<float> aux;             // adjoint scratch
+    DevBuf<double> dL;             // adjoint of L (loss)
+    DevBuf<double> Lv;             // L values of the current pair
+};
+
+struct Pattern {
+    Handle* h = nullptr;
+    int64_t n = 0, nnz = 0, nnzL = 0;
+    int32_t nsys = 1;
+    std::vector<int64_t> sys_ptr_h;
+    DevBuf<int64_t> sys_ptr;       // [nsys+1]
+    DevBuf<int32_t> row_sys;       // [n] system of each row
+    DevBuf<int32_t> rp, ci;        // A pattern copy
+    DevBuf<int32_t> edge_row;      // [nnz]
+    DevBuf<int32_t> mirror;        // [nnz] position of (j,i)
+    DevBuf<int32_t> adiag;         // [n] position of (i,i) in A
+    DevBuf<int32_t> a2l;           // [nnz] L position of (i,j), j <= i, else -1
+    DevBuf<int32_t> Lrp, Lci, l2a; // tril pattern and L -> A map
+    TriLayout fwd, bwd;            // L y = r and L^T z = y
+    // reduction chunks
+    std::vector<Chunk> chunks_h;
+    DevBuf<Chunk> chunks;
+    DevBuf<int32_t> sys_chunk0;    // [nsys+1] first chunk of each system
+    int32_t nchunks = 0;
+    // PCG workspace
+    DevBuf<double> x, r, z, y, w, p0, p1, b;
+    DevBuf<double> part;           // [nchunks * 4] partial sums
+    DevBuf<unsigned int> arrive;   // [nsys] arrival counters
+    DevBuf<SysState> st;           // [nsys]
+    DevBuf<npcg_solve_stats> stats_dev;  // [nsys]
+    DevBuf<int> ctl;               // [0] n_active, [1] flags, [2] fwd ticket, [3] bwd ticket
+    DevBuf<double> Aval_dev;       // host-path copy of A values
+    DevBuf<double> Lval_dev;       // host-path factor
+    // cached iteration graphs (keyed by precond)
+    cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
+    GnnStore gnn;
+    ~Pattern();
+};
+
+struct Handle {
+    cudaStream_t stream = nullptr;
+    cudaStream_t capture_stream = nullptr;   // private, for graph capture
+    int device = 0;
+    int num_sms = 0;
+    std::string last_error;
+    DevBuf<int> scratch_i;      // small device scratch
+    void* host_pinned = nullptr; // small pinned host scratch
+    size_t host_pinned_bytes = 0;
+};
+
+// ---------------------------------------------------------------------------
+// error helpers
+// ---------------------------------------------------------------------------
+npcg_status set_error(Handle* h, npcg_status s, const std::string& msg);
+npcg_status cuda_fail(Handle* h, cudaError_t e, const char* where);
+
+#define NPCG_CUDA(h, expr)                                              \
+    do {                                                                \
+        cudaError_t _e = (expr);                                        \
+        if (_e != cudaSuccess) return ::npcg::cuda_fail((h), _e, #expr); \
+    } while (0)
+
+#define NPCG_TRY(expr)                         \
+    do {                                       \
+        npcg_status _s = (expr);               \
+        if (_s != NPCG_OK) return _s;          \
+    } while (0)
+
+inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// ---------------------------------------------------------------------------
+// device helpers: relaxed / acquire / release accesses at GPU scope
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const void* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const void* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(void* p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void st_release_u64(void* p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ int ld_relaxed_s32(const int* p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_s32(int* p, int v) {
+    asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ double sentinel_f64() { return __longlong_as_double((long long)kSentinelBits); }
+
+// ---------------------------------------------------------------------------
+// cross-file host entry points
+// ---------------------------------------------------------------------------
+npcg_status pattern_build(Handle* h, int64_t n, int64_t nnz, const int32_t* rp,
+                          const int32_t* ci, int32_t nsys, const int64_t* sys_ptr, Pattern* P);
+npcg_status factor_load(Handle* h, Pattern* P, const double* L_val);
+npcg_status sptrsv_run(Handle* h, Pattern* P, int transpose, const double* r, double* y,
+                       const int32_t* sys_active);
+npcg_status spmv_run(Handle* h, Pattern* P, const double* A_val, const double* x, double* y);
+npcg_status sptrsv_timed_run(Handle* h, Pattern* P, int transpose, const double* r, double* y, int reps,
+                             double* ms_per_launch);
+npcg_status pcg_run(Handle* h, Pattern* P, const double* A_val, const double* b, double* x,
+                    int precond, const double* L_val, double rtol, int max_iter,
+                    npcg_solve_stats* stats);
+npcg_status ic0_run(Handle* h, Pattern* P, const double* A_val, double* L_val, double* alpha_out);
+npcg_status gnn_forward_run(Handle* h, Pattern* P, const double* A_val, const double* b,
+                            const npcg_gnn_config* cfg, const float* w, double* L_val);
+npcg_status loss_grad_run(Handle* h, Pattern* P, const double* A_val, int npairs,
+                          const double* X, const double* B, const npcg_gnn_config* cfg,
+                          const float* w, double* loss_out, float* grad);
+npcg_status adam_run(Handle* h, int64_t n, float* w, const float* g, float* m, float* v, int t,
+                     float lr, float b1, float b2, float eps);
+npcg_status assemble_count_run(Handle* h, const npcg_problem* p, int64_t* n, int64_t* nnz);
+npcg_status assemble_run(Handle* h, const npcg_problem* p, int32_t* rp, int32_t* ci, double* v);
+
+// exclusive scan of int32 counts into int32/int64 offsets (device), out[0..n]
+npcg_status scan_i32_to_i64(Handle* h, const int32_t* in, int64_t* out, int64_t n);
+npcg_status scan_i32_to_i32(Handle* h, const int32_t* in, int32_t* out, int64_t n);
+// read a device scalar (synchronises)
+template <class T>
+npcg_status read_scalar(Handle* h, const T* dev, T* host) {
+    NPCG_CUDA(h, cudaMemcpyAsync(host, dev, sizeof(T), cudaMemcpyDeviceToHost, h->stream));
+    NPCG_CUDA(h, cudaStreamSynchronize(h->stream));
+    return NPCG_OK;
+}
+
+}  // namespace npcg
+
+struct npcg_handle_s : npcg::Handle {};
+struct npcg_pattern_s : npcg::Pattern {};

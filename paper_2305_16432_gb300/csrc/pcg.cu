@@ -1,0 +1,629 @@
+// PCG (Algorithm 1) in FP64 on the GPU: CSR SpMV, sync-free level-ordered
+// sparse triangular solves for "Solve P z = r" with P = L L^T, fused vector
+// updates with deterministic per-system reductions, and the iteration as a
+// CUDA graph whose while-loop runs on the device until every system of the
+// pattern has converged, failed, or reached max_iter.
+#include <algorithm>
+
+#include "npcg_internal.cuh"
+
+namespace npcg {
+
+namespace {
+
+constexpr int kTrsvThreads = 256;
+constexpr int kDepChunk = 8;
+
+// ------------------------------------------------------------------ reduce
+template <int N>
+__device__ __forceinline__ void block_sum(double (&v)[N], double (*sh)[kChunkThreads / 32]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        double x = v[j];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) sh[j][warp] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            double s = 0.0;
+            for (int w = 0; w < kChunkThreads / 32; ++w) s += sh[j][w];
+            v[j] = s;
+        }
+    }
+}
+
+// Publishes this chunk's partial sums; returns true (in thread 0) for the
+// last chunk of its system to arrive, which then owns the finalisation.
+template <int N>
+__device__ __forceinline__ bool publish(const Chunk& c, const double (&v)[N], double* part,
+                                        unsigned* arrive, const int32_t* sys_chunk0) {
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int j = 0; j < N; ++j) part[(int64_t)c.slot * 4 + j] = v[j];
+        __threadfence();
+        unsigned nch = (unsigned)(sys_chunk0[c.sys + 1] - sys_chunk0[c.sys]);
+        unsigned prev = atomicAdd(&arrive[c.sys], 1u);
+        last = (prev == nch - 1);
+    }
+    __syncthreads();
+    return threadIdx.x == 0 && last;
+}
+
+template <int N>
+__device__ __forceinline__ void gather_parts(const Chunk& c, const double* part,
+                                             const int32_t* sys_chunk0, unsigned* arrive,
+                                             double (&tot)[N]) {
+    __threadfence();
+#pragma unroll
+    for (int j = 0; j < N; ++j) tot[j] = 0.0;
+    for (int q = sys_chunk0[c.sys]; q < sys_chunk0[c.sys + 1]; ++q)
+#pragma unroll
+        for (int j = 0; j < N; ++j) tot[j] += __ldcg(part + (int64_t)q * 4 + j);
+    arrive[c.sys] = 0u;
+}
+
+__device__ __forceinline__ void deactivate(SysState& s, int status, int* n_active) {
+    s.status = status;
+    s.active = 0;
+    atomicSub(n_active, 1);
+}
+
+// ------------------------------------------------------------------ kernels
+struct PcgArgs {
+    const int32_t* rp;
+    const int32_t* ci;
+    const double* av;
+    const int32_t* adiag;
+    const Chunk* chunks;
+    const int32_t* sys_chunk0;
+    SysState* st;
+    double* part;
+    unsigned* arrive;
+    int* ctl;            // [0] n_active [1] flags [2] fwd ticket [3] bwd ticket
+    double *x, *r, *z, *y, *w, *b;
+    int precond;
+};
+
+// sum_j A_ij * v_j for one row by a group of G lanes (row entries strided by G)
+template <int G>
+__device__ __forceinline__ double row_dot(const int32_t* rp, const int32_t* ci, const double* av,
+                                          const double* v, int row, int g) {
+    double s = 0.0;
+    for (int k = rp[row] + g; k < rp[row + 1]; k += G) s = fma(av[k], v[ci[k]], s);
+#pragma unroll
+    for (int o = G / 2; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, G);
+    return s;
+}
+
+// r = b - A x; partials ||b||^2, ||r||^2; finaliser sets tolerances and the
+// active mask; sentinels and p buffers are reset for the first iteration.
+__global__ void k_init(PcgArgs a, double rtol, int max_iter, double* p0, double* p1) {
+    __shared__ double sh[2][kChunkThreads / 32];
+    const Chunk c = a.chunks[blockIdx.x];
+    const int g = threadIdx.x & 7, grp = threadIdx.x >> 3;
+    double acc[2] = {0.0, 0.0};
+    for (int row = c.row0 + grp; row < c.row1; row += kChunkThreads / 8) {
+        double ax = row_dot<8>(a.rp, a.ci, a.av, a.x, row, g);
+        if (g == 0) {
+            double bi = a.b[row];
+            double ri = bi - ax;
+            a.r[row] = ri;
+            p0[row] = 0.0;
+            p1[row] = 0.0;
+            a.y[row] = sentinel_f64();
+            a.z[row] = sentinel_f64();
+            acc[0] = fma(bi, bi, acc[0]);
+            acc[1] = fma(ri, ri, acc[1]);
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) { a.ctl[2] = 0; a.ctl[3] = 0; }
+    block_sum<2>(acc, sh);
+    if (publish<2>(c, acc, a.part, a.arrive, a.sys_chunk0)) {
+        double tot[2];
+        gather_parts<2>(c, a.part, a.sys_chunk0, a.arrive, tot);
+        SysState& s = a.st[c.sys];
+        s.bnorm2 = tot[0];
+        s.tol2 = rtol * rtol * tot[0];
+        s.rr = tot[1];
+        s.iters = 0;
+        s.max_iter = max_iter;
+        s.beta = 0.0;
+        s.alpha = 0.0;
+        s.rz = 0.0;
+        s.pw = 0.0;
+        if (!(tot[1] <= s.tol2)) {
+            if (max_iter <= 0) {
+                s.status = NPCG_EMAXITER;
+                s.active = 0;
+            } else if (isfinite(tot[1])) {
+                s.status = NPCG_OK;
+                s.active = 1;
+                atomicAdd(&a.ctl[0], 1);
+            } else {
+                s.status = NPCG_EBREAKDOWN;
+                s.active = 0;
+            }
+        } else {
+            s.status = NPCG_OK;
+            s.active = 0;
+        }
+    }
+}
+
+// elementwise preconditioners (z = r / diag or z = r) with r^T z partials;
+// used for the initial z (finalise_beta = false sets rz) and, fused in
+// k_update, every iteration.
+__device__ __forceinline__ double elementwise_z(const PcgArgs& a, int row, double ri) {
+    return a.precond == NPCG_PREC_JACOBI ? ri / a.av[a.adiag[row]] : ri;
+}
+
+// r^T z; finaliser: first call (init) stores rz, later calls compute beta.
+__global__ void k_dot_rz(PcgArgs a, int init) {
+    __shared__ double sh[1][kChunkThreads / 32];
+    const Chunk c = a.chunks[blockIdx.x];
+    if (!a.st[c.sys].active) return;
+    double acc[1] = {0.0};
+    for (int row = c.row0 + threadIdx.x; row < c.row1; row += kChunkThreads) {
+        double ri = a.r[row];
+        double zi;
+        if (a.precond == NPCG_PREC_LLT) zi = a.z[row];
+        else { zi = elementwise_z(a, row, ri); a.z[row] = zi; }
+        acc[0] = fma(ri, zi, acc[0]);
+    }
+    block_sum<1>(acc, sh);
+    if (publish<1>(c, acc, a.part, a.arrive, a.sys_chunk0)) {
+        double tot[1];
+        gather_parts<1>(c, a.part, a.sys_chunk0, a.arrive, tot);
+        SysState& s = a.st[c.sys];
+        double rz = tot[0];
+        if (!(rz > 0.0) || !isfinite(rz)) {
+            deactivate(s, NPCG_EBREAKDOWN, &a.ctl[0]);
+        } else {
+            s.beta = init ? 0.0 : rz / s.rz;
+            s.rz = rz;
+        }
+    }
+}
+
+// p_new = z + beta p_old (recomputed for every neighbour, written for own
+// rows), w = A p_new, partial p_new^T w; finaliser: alpha = rz / p^T w.
+__global__ void k_spmv_p(PcgArgs a, const double* __restrict__ p_old, double* __restrict__ p_new) {
+    __shared__ double sh[1][kChunkThreads / 32];
+    const Chunk c = a.chunks[blockIdx.x];
+    const SysState& s0 = a.st[c.sys];
+    if (!s0.active) return;
+    const double beta = s0.beta;
+    const int g = threadIdx.x & 7, grp = threadIdx.x >> 3;
+    double acc[1] = {0.0};
+    for (int row = c.row0 + grp; row < c.row1; row += kChunkThreads / 8) {
+        double s = 0.0;
+        for (int k = a.rp[row] + g; k < a.rp[row + 1]; k += 8) {
+            int j = a.ci[k];
+            s = fma(a.av[k], fma(beta, p_old[j], a.z[j]), s);
+        }
+#pragma unroll
+        for (int o = 4; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, 8);
+        if (g == 0) {
+            double pi = fma(beta, p_old[row], a.z[row]);
+            p_new[row] = pi;
+            a.w[row] = s;
+            acc[0] = fma(pi, s, acc[0]);
+        }
+    }
+    block_sum<1>(acc, sh);
+    if (publish<1>(c, acc, a.part, a.arrive, a.sys_chunk0)) {
+        double tot[1];
+        gather_parts<1>(c, a.part, a.sys_chunk0, a.arrive, tot);
+        SysState& s = a.st[c.sys];
+        s.pw = tot[0];
+        if (!(tot[0] > 0.0) || !isfinite(tot[0])) deactivate(s, NPCG_EBREAKDOWN, &a.ctl[0]);
+        else s.alpha = s.rz / tot[0];
+    }
+}
+
+// x += alpha p, r -= alpha w, ||r||^2 (and, for the elementwise
+// preconditioners, z and r^T z); finaliser counts the update, tests
+// convergence (||r|| <= rtol ||b||) and max_iter, and computes beta.
+__global__ void k_update(PcgArgs a, const double* __restrict__ p) {
+    __shared__ double sh[2][kChunkThreads / 32];
+    if (blockIdx.x == 0 && threadIdx.x == 0) { a.ctl[2] = 0; a.ctl[3] = 0; }
+    const Chunk c = a.chunks[blockIdx.x];
+    const SysState& s0 = a.st[c.sys];
+    if (!s0.active) return;
+    const double alpha = s0.alpha;
+    const bool llt = a.precond == NPCG_PREC_LLT;
+    double acc[2] = {0.0, 0.0};
+    for (int row = c.row0 + threadIdx.x; row < c.row1; row += kChunkThreads) {
+        a.x[row] = fma(alpha, p[row], a.x[row]);
+        double ri = fma(-alpha, a.w[row], a.r[row]);
+        a.r[row] = ri;
+        acc[0] = fma(ri, ri, acc[0]);
+        if (llt) {
+            a.y[row] = sentinel_f64();
+            a.z[row] = sentinel_f64();
+        } else {
+            double zi = elementwise_z(a, row, ri);
+            a.z[row] = zi;
+            acc[1] = fma(ri, zi, acc[1]);
+        }
+    }
+    block_sum<2>(acc, sh);
+    if (publish<2>(c, acc, a.part, a.arrive, a.sys_chunk0)) {
+        double tot[2];
+        gather_parts<2>(c, a.part, a.sys_chunk0, a.arrive, tot);
+        SysState& s = a.st[c.sys];
+        s.rr = tot[0];
+        s.iters += 1;
+        if (tot[0] <= s.tol2) {
+            deactivate(s, NPCG_OK, &a.ctl[0]);
+        } else if (!isfinite(tot[0])) {
+            deactivate(s, NPCG_EBREAKDOWN, &a.ctl[0]);
+        } else if (s.iters >= s.max_iter) {
+            deactivate(s, NPCG_EMAXITER, &a.ctl[0]);
+        } else if (!llt) {
+            double rz = tot[1];
+            if (!(rz > 0.0) || !isfinite(rz)) deactivate(s, NPCG_EBREAKDOWN, &a.ctl[0]);
+            else { s.beta = rz / s.rz; s.rz = rz; }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ SpTRSV
+struct TriDev {
+    int64_t n;
+    int32_t nslices;
+    const int32_t* perm;
+    const int64_t* soff;
+    const int32_t* sw;
+    const int32_t* col;
+    const double* val;
+    const double* diag;
+};
+
+// One warp per 32-row slice, one lane per row, slices claimed in level order
+// by a ticket counter, so every dependency belongs to an earlier-claimed
+// (running) warp.  out[] holds the sentinel until written; a lane polls its
+// pending dependencies each round and combines them in slot order once all
+// are present, so the result does not depend on timing.
+template <bool kBatched>
+__global__ void __launch_bounds__(kTrsvThreads) k_trsv(TriDev T, const double* __restrict__ rhs,
+                                                       double* out, int* ticket, int* flags,
+                                                       const int32_t* row_sys, const SysState* st) {
+    const int lane = threadIdx.x & 31;
+    const unsigned long long kS = kSentinelBits;
+    if (!kBatched && st && !st[0].active) return;
+    for (;;) {
+        int slice = 0;
+        if (lane == 0) slice = atomicAdd(ticket, 1);
+        slice = __shfl_sync(0xffffffffu, slice, 0);
+        if (slice >= T.nslices) return;
+        const int64_t q = (int64_t)slice * kSlice + lane;
+        int row = q < T.n ? T.perm[q] : -1;
+        bool act = row >= 0;
+        if (kBatched && act) act = st[row_sys[row]].active != 0;
+        const int width = T.sw[slice];
+        const int64_t off = T.soff[slice];
+        double acc = act ? rhs[row] : 0.0;
+        const double d = act ? T.diag[q] : 1.0;
+        long long spins = 0;
+        for (int k0 = 0; k0 < width; k0 += kDepChunk) {
+            int cj[kDepChunk];
+            double lv[kDepChunk], yv[kDepChunk];
+            unsigned pend = 0;
+#pragma unroll
+            for (int k = 0; k < kDepChunk; ++k) {
+                cj[k] = -1;
+                lv[k] = 0.0;
+                yv[k] = 0.0;
+                if (act && k0 + k < width) {
+                    int64_t slot = off + (int64_t)(k0 + k) * kSlice + lane;
+                    cj[k] = T.col[slot];
+                    lv[k] = T.val[slot];
+                    if (cj[k] >= 0) pend |= 1u << k;
+                }
+            }
+            while (__any_sync(0xffffffffu, pend != 0)) {
+#pragma unroll
+                for (int k = 0; k < kDepChunk; ++k) {
+                    if (pend & (1u << k)) {
+                        unsigned long long bits = ld_relaxed_u64(out + cj[k]);
+                        if (bits != kS) {
+                            yv[k] = __longlong_as_double((long long)bits);
+                            pend &= ~(1u << k);
+                        }
+                    }
+                }
+                if (++spins > kSpinLimit) {
+                    if (pend) atomicOr(flags, kFlagTimeout | kFlagAbort);
+                    return;
+                }
+                if ((spins & 255) == 0) {
+                    int f = lane == 0 ? ld_relaxed_s32(flags) : 0;
+                    if (__shfl_sync(0xffffffffu, f, 0) & kFlagAbort) return;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < kDepChunk; ++k)
+                if (cj[k] >= 0) acc = fma(-lv[k], yv[k], acc);
+        }
+        if (act) st_relaxed_u64(out + row, (unsigned long long)__double_as_longlong(acc / d));
+    }
+}
+
+__global__ void k_load_factor(int64_t slots, const int32_t* src, const double* L, double* val,
+                              int64_t n, const int32_t* dsrc, double* diag) {
+    int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t st = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = i0; i < slots; i += st) {
+        int s = src[i];
+        val[i] = s >= 0 ? L[s] : 0.0;
+    }
+    for (int64_t i = i0; i < n; i += st) diag[i] = L[dsrc[i]];
+}
+
+__global__ void k_fill_sentinel(int64_t n, double* y) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = sentinel_f64();
+}
+
+__global__ void k_spmv_plain(int64_t n, const int32_t* rp, const int32_t* ci, const double* av,
+                             const double* x, double* y) {
+    const int g = threadIdx.x & 7;
+    int64_t grp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 3;
+    int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) >> 3;
+    for (int64_t row = grp; row < n; row += ngrp) {
+        double s = row_dot<8>(rp, ci, av, x, (int)row, g);
+        if (g == 0) y[row] = s;
+    }
+}
+
+__global__ void k_set_cond(cudaGraphConditionalHandle hd, const int* ctl) {
+    if (threadIdx.x == 0) {
+        int go = ctl[0] > 0 && !(ctl[1] & kFlagAbort);
+        cudaGraphSetConditional(hd, go ? 1u : 0u);
+    }
+}
+
+__global__ void k_stats(int nsys, const SysState* st, npcg_solve_stats* out) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < nsys) {
+        out[s].iters = st[s].iters;
+        out[s].status = st[s].status;
+        double b2 = st[s].bnorm2;
+        out[s].relres = b2 > 0.0 ? sqrt(st[s].rr / b2) : sqrt(st[s].rr);
+    }
+}
+
+TriDev tri_dev(const Pattern* P, const TriLayout& T) {
+    TriDev d;
+    d.n = P->n;
+    d.nslices = T.nslices;
+    d.perm = T.perm.p;
+    d.soff = T.slice_off.p;
+    d.sw = T.slice_w.p;
+    d.col = T.col.p;
+    d.val = T.val.p;
+    d.diag = T.diag.p;
+    return d;
+}
+
+int trsv_grid(Handle* h, const TriLayout& T) {
+    int warps_needed = T.nslices;
+    int blocks = ceil_div(warps_needed, kTrsvThreads / 32);
+    return std::max(1, std::min(blocks, h->num_sms * 4));
+}
+
+void launch_trsv(Handle* h, cudaStream_t s, Pattern* P, int transpose, const double* rhs, double* out,
+                 int* ticket, bool batched, const SysState* st) {
+    const TriLayout& T = transpose ? P->bwd : P->fwd;
+    TriDev d = tri_dev(P, T);
+    if (batched)
+        k_trsv<true><<<trsv_grid(h, T), kTrsvThreads, 0, s>>>(d, rhs, out, ticket, P->ctl.p + 1,
+                                                               P->row_sys.p, st);
+    else
+        k_trsv<false><<<trsv_grid(h, T), kTrsvThreads, 0, s>>>(d, rhs, out, ticket, P->ctl.p + 1,
+                                                                P->row_sys.p, st);
+}
+
+npcg_status ensure_pcg_workspace(Handle* h, Pattern* P) {
+    const int64_t n = P->n;
+    NPCG_CUDA(h, P->x.ensure(n));
+    NPCG_CUDA(h, P->r.ensure(n));
+    NPCG_CUDA(h, P->z.ensure(n));
+    NPCG_CUDA(h, P->y.ensure(n));
+    NPCG_CUDA(h, P->w.ensure(n));
+    NPCG_CUDA(h, P->p0.ensure(n));
+    NPCG_CUDA(h, P->p1.ensure(n));
+    NPCG_CUDA(h, P->b.ensure(n));
+    NPCG_CUDA(h, P->Aval_dev.ensure(P->nnz));
+    NPCG_CUDA(h, P->part.ensure((size_t)P->nchunks * 4));
+    if (P->arrive.n < (size_t)P->nsys) {
+        NPCG_CUDA(h, P->arrive.alloc(P->nsys));
+        NPCG_CUDA(h, cudaMemsetAsync(P->arrive.p, 0, P->nsys * sizeof(unsigned), h->stream));
+    }
+    NPCG_CUDA(h, P->st.ensure(P->nsys));
+    NPCG_CUDA(h, P->stats_dev.ensure(P->nsys));
+    return NPCG_OK;
+}
+
+PcgArgs pcg_args(Pattern* P, int precond) {
+    PcgArgs a;
+    a.rp = P->rp.p;
+    a.ci = P->ci.p;
+    a.av = P->Aval_dev.p;
+    a.adiag = P->adiag.p;
+    a.chunks = P->chunks.p;
+    a.sys_chunk0 = P->sys_chunk0.p;
+    a.st = P->st.p;
+    a.part = P->part.p;
+    a.arrive = P->arrive.p;
+    a.ctl = P->ctl.p;
+    a.x = P->x.p;
+    a.r = P->r.p;
+    a.z = P->z.p;
+    a.y = P->y.p;
+    a.w = P->w.p;
+    a.b = P->b.p;
+    a.precond = precond;
+    return a;
+}
+
+// one PCG iteration (Algorithm 1 loop body) on the stream
+void enqueue_iteration(Handle* h, cudaStream_t s, Pattern* P, const PcgArgs& a, const double* p_old,
+                       double* p_new) {
+    const bool batched = P->nsys > 1;
+    k_spmv_p<<<P->nchunks, kChunkThreads, 0, s>>>(a, p_old, p_new);
+    k_update<<<P->nchunks, kChunkThreads, 0, s>>>(a, p_new);
+    if (a.precond == NPCG_PREC_LLT) {
+        launch_trsv(h, s, P, 0, P->r.p, P->y.p, P->ctl.p + 2, batched, P->st.p);
+        launch_trsv(h, s, P, 1, P->y.p, P->z.p, P->ctl.p + 3, batched, P->st.p);
+        k_dot_rz<<<P->nchunks, kChunkThreads, 0, s>>>(a, 0);
+    }
+}
+
+npcg_status build_graph(Handle* h, Pattern* P, int precond) {
+    if (P->graph[precond]) return NPCG_OK;
+    PcgArgs a = pcg_args(P, precond);
+    cudaGraph_t g = nullptr;
+    NPCG_CUDA(h, cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle hd;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&hd, g, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) { cudaGraphDestroy(g); return cuda_fail(h, e, "cudaGraphConditionalHandleCreate"); }
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = hd;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp);
+    if (e != cudaSuccess) { cudaGraphDestroy(g); return cuda_fail(h, e, "cudaGraphAddNode(conditional)"); }
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    // captured on the handle's private stream (the caller's stream may be the
+    // legacy default stream, which cannot capture)
+    cudaStream_t cs = h->capture_stream;
+    e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) { cudaGraphDestroy(g); return cuda_fail(h, e, "cudaStreamBeginCaptureToGraph"); }
+    // two iterations per trip so the p ping-pong is static
+    enqueue_iteration(h, cs, P, a, P->p0.p, P->p1.p);
+    enqueue_iteration(h, cs, P, a, P->p1.p, P->p0.p);
+    k_set_cond<<<1, 32, 0, cs>>>(hd, P->ctl.p);
+    cudaGraph_t captured = nullptr;
+    e = cudaStreamEndCapture(cs, &captured);
+    if (e != cudaSuccess) { cudaGraphDestroy(g); return cuda_fail(h, e, "cudaStreamEndCapture"); }
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
+    P->graph[precond] = ex;
+    return NPCG_OK;
+}
+
+}  // namespace
+
+npcg_status factor_load(Handle* h, Pattern* P, const double* L_val) {
+    int blocks = h->num_sms * 4;
+    k_load_factor<<<blocks, 256, 0, h->stream>>>(P->fwd.slots, P->fwd.src.p, L_val, P->fwd.val.p, P->n,
+                                                 P->fwd.diag_src.p, P->fwd.diag.p);
+    k_load_factor<<<blocks, 256, 0, h->stream>>>(P->bwd.slots, P->bwd.src.p, L_val, P->bwd.val.p, P->n,
+                                                 P->bwd.diag_src.p, P->bwd.diag.p);
+    NPCG_CUDA(h, cudaGetLastError());
+    return NPCG_OK;
+}
+
+npcg_status sptrsv_run(Handle* h, Pattern* P, int transpose, const double* r, double* y,
+                       const int32_t*) {
+    k_fill_sentinel<<<h->num_sms * 4, 256, 0, h->stream>>>(P->n, y);
+    NPCG_CUDA(h, cudaMemsetAsync(P->ctl.p + 1, 0, 3 * sizeof(int), h->stream));
+    launch_trsv(h, h->stream, P, transpose, r, y, P->ctl.p + 2 + (transpose ? 1 : 0), false, nullptr);
+    NPCG_CUDA(h, cudaGetLastError());
+    return NPCG_OK;
+}
+
+npcg_status sptrsv_timed_run(Handle* h, Pattern* P, int transpose, const double* r, double* y, int reps,
+                             double* ms_per_launch) {
+    cudaEvent_t e0, e1;
+    NPCG_CUDA(h, cudaEventCreate(&e0));
+    NPCG_CUDA(h, cudaEventCreate(&e1));
+    double total = 0.0;
+    npcg_status st = NPCG_OK;
+    for (int k = 0; k < reps && st == NPCG_OK; ++k) {
+        k_fill_sentinel<<<h->num_sms * 4, 256, 0, h->stream>>>(P->n, y);
+        cudaMemsetAsync(P->ctl.p + 1, 0, 3 * sizeof(int), h->stream);
+        cudaEventRecord(e0, h->stream);
+        launch_trsv(h, h->stream, P, transpose, r, y, P->ctl.p + 2 + (transpose ? 1 : 0), false, nullptr);
+        cudaEventRecord(e1, h->stream);
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) { st = cuda_fail(h, e, "trsv timing"); break; }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        total += ms;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != NPCG_OK) return st;
+    int flags = 0;
+    NPCG_TRY(read_scalar(h, P->ctl.p + 1, &flags));
+    if (flags & kFlagTimeout) return set_error(h, NPCG_ETIMEOUT, "triangular solve wait timed out");
+    *ms_per_launch = reps > 0 ? total / reps : 0.0;
+    return NPCG_OK;
+}
+
+npcg_status spmv_run(Handle* h, Pattern* P, const double* A_val, const double* x, double* y) {
+    int blocks = std::min(ceil_div(P->n * 8, 256), h->num_sms * 8);
+    k_spmv_plain<<<blocks, 256, 0, h->stream>>>(P->n, P->rp.p, P->ci.p, A_val, x, y);
+    NPCG_CUDA(h, cudaGetLastError());
+    return NPCG_OK;
+}
+
+npcg_status pcg_run(Handle* h, Pattern* P, const double* A_val, const double* b, double* x,
+                    int precond, const double* L_val, double rtol, int max_iter,
+                    npcg_solve_stats* stats) {
+    if (precond < 0 || precond > 2) return set_error(h, NPCG_EINVAL, "unknown preconditioner");
+    if (precond == NPCG_PREC_LLT && !L_val) return set_error(h, NPCG_EINVAL, "L_val required for PREC_LLT");
+    if (!(rtol >= 0.0)) return set_error(h, NPCG_EINVAL, "rtol must be >= 0");
+    if (max_iter < 0) return set_error(h, NPCG_EINVAL, "max_iter must be >= 0");
+    NPCG_TRY(ensure_pcg_workspace(h, P));
+    const int64_t n = P->n;
+    if (A_val != P->Aval_dev.p)
+        NPCG_CUDA(h, cudaMemcpyAsync(P->Aval_dev.p, A_val, P->nnz * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    if (b != P->b.p)
+        NPCG_CUDA(h, cudaMemcpyAsync(P->b.p, b, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    if (x != P->x.p)
+        NPCG_CUDA(h, cudaMemcpyAsync(P->x.p, x, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    if (precond == NPCG_PREC_LLT) NPCG_TRY(factor_load(h, P, L_val));
+    NPCG_CUDA(h, cudaMemsetAsync(P->ctl.p, 0, 4 * sizeof(int), h->stream));
+    PcgArgs a = pcg_args(P, precond);
+    k_init<<<P->nchunks, kChunkThreads, 0, h->stream>>>(a, rtol, max_iter, P->p0.p, P->p1.p);
+    if (precond == NPCG_PREC_LLT) {
+        launch_trsv(h, h->stream, P, 0, P->r.p, P->y.p, P->ctl.p + 2, P->nsys > 1, P->st.p);
+        launch_trsv(h, h->stream, P, 1, P->y.p, P->z.p, P->ctl.p + 3, P->nsys > 1, P->st.p);
+    }
+    k_dot_rz<<<P->nchunks, kChunkThreads, 0, h->stream>>>(a, 1);
+    NPCG_CUDA(h, cudaGetLastError());
+    NPCG_TRY(build_graph(h, P, precond));
+    if (max_iter > 0) NPCG_CUDA(h, cudaGraphLaunch(P->graph[precond], h->stream));
+    // stats
+    k_stats<<<ceil_div(P->nsys, 128), 128, 0, h->stream>>>(P->nsys, P->st.p, P->stats_dev.p);
+    NPCG_CUDA(h, cudaMemcpyAsync(stats, P->stats_dev.p, P->nsys * sizeof(npcg_solve_stats),
+                                 cudaMemcpyDeviceToHost, h->stream));
+    if (x != P->x.p)
+        NPCG_CUDA(h, cudaMemcpyAsync(x, P->x.p, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    int ctl[2] = {0, 0};
+    NPCG_CUDA(h, cudaMemcpyAsync(ctl, P->ctl.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    NPCG_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (ctl[1] & kFlagTimeout) return set_error(h, NPCG_ETIMEOUT, "triangular solve wait timed out");
+    for (int s = 0; s < P->nsys; ++s)
+        if (stats[s].status != NPCG_OK)
+            return set_error(h, (npcg_status)stats[s].status,
+                             "system " + std::to_string(s) + " did not converge: " +
+                                 npcg_status_string((npcg_status)stats[s].status));
+    return NPCG_OK;
+}
+
+}  // namespace npcg

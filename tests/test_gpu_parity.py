@@ -1,0 +1,282 @@
+"""GPU parity: every step of the hot path through the C ABI, element by
+element against the FP64 oracle on the same seeded inputs.
+
+Tolerances (bars of the method's parity contract):
+  patterns, levels, permutations    bit-exact
+  assembled A                       1e-12 relative (GPU exp/cos differ by ulps)
+  SpMV / SpTRSV / IC(0) values      1e-12 relative
+  PCG x (same factor)               1e-8 relative, iterations +-1
+  FP32 GNN L                        ||dL||_F / ||L||_F <= 1e-5 and max|dL| <= 1e-5 max|L|
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2305_16432_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def N():
+    from paper_2305_16432_gb300 import build
+    build.build()
+    from paper_2305_16432_gb300 import npcg
+    torch.cuda.init()
+    return npcg
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+def _gpu(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+PROBLEMS = {
+    "poisson2d_32": I.poisson2d_32(),
+    "fd2d_var": I.fd2d(23, 17, sigma=1.0, seed=3),
+    "fd3d_var": I.fd3d(9, 8, 7, sigma=1.5, corr_len=0.05, seed=4),
+    "fem34": I.fem2d(34, sigma=1.0, seed=5),
+    "fem_nojit": I.fem2d(20, sigma=0.0, seed=0),
+}
+
+
+def _assemble_both(N, prob, jitter=None):
+    if prob.kind == I.FEM and jitter is None:
+        jitter = I.fem_jitter(prob)
+    om, ph = I.grf_features(prob)
+    Ao = O.assemble(prob, om, ph, jitter)
+    rp, ci, v = N.assemble_system(prob, om, ph, jitter)
+    return Ao, (rp, ci, v)
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_assembly_parity(N, name):
+    Ao, (rp, ci, v) = _assemble_both(N, PROBLEMS[name])
+    assert np.array_equal(_np(rp), Ao.row_ptr)
+    assert np.array_equal(_np(ci), Ao.col_idx)
+    assert _rel(_np(v), Ao.val) <= 1e-12
+
+
+def test_assembly_zero_jitter_pattern(N):
+    # tie case of the in-circle predicate and the dropped cot(90) edges
+    p = I.fem2d(18, sigma=0.0)
+    Ao, (rp, ci, v) = _assemble_both(N, p, I.zero_jitter(18))
+    assert np.array_equal(_np(rp), Ao.row_ptr) and np.array_equal(_np(ci), Ao.col_idx)
+    assert _rel(_np(v), Ao.val) <= 1e-12
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_pattern_and_levels_bit_exact(N, name):
+    Ao, (rp, ci, v) = _assemble_both(N, PROBLEMS[name])
+    P = N.analyse(rp, ci)
+    ex = P.export()
+    Lo, _ = O.tril(Ao)
+    lev, nf, levb, nb = O.levels(Lo)
+    assert np.array_equal(_np(ex["L_row_ptr"]), Lo.row_ptr)
+    assert np.array_equal(_np(ex["L_col_idx"]), Lo.col_idx)
+    assert np.array_equal(_np(ex["lev_fwd"]), lev)
+    assert np.array_equal(_np(ex["lev_bwd"]), levb)
+    assert P.nlev_fwd == nf and P.nlev_bwd == nb
+    perm, _ = O.level_perm(lev, nf)
+    permb, _ = O.level_perm(levb, nb)
+    assert np.array_equal(_np(ex["perm_fwd"]), perm)
+    assert np.array_equal(_np(ex["perm_bwd"]), permb)
+    assert P.nnz_L == Lo.nnz == (Ao.nnz + Ao.n) // 2
+
+
+def test_levels_closed_form_grid(N):
+    # 2-D natural order: nx + ny - 1 levels; 3-D: nx + ny + nz - 2
+    Ao, (rp, ci, v) = _assemble_both(N, I.fd3d(20, 15, 11))
+    P = N.analyse(rp, ci)
+    assert P.nlev_fwd == P.nlev_bwd == 20 + 15 + 11 - 2
+
+
+@pytest.mark.parametrize("name", ["fem34", "fd3d_var"])
+def test_spmv_parity(N, name):
+    Ao, (rp, ci, v) = _assemble_both(N, PROBLEMS[name])
+    P = N.analyse(rp, ci)
+    x = np.random.default_rng(1).standard_normal(Ao.n)
+    y = N.spmv(P, v, _gpu(x))
+    assert _rel(_np(y), O.spmv(Ao, x)) <= 1e-12
+
+
+@pytest.mark.parametrize("name", ["poisson2d_32", "fem34", "fd3d_var"])
+def test_ic0_and_sptrsv_parity(N, name):
+    Ao, (rp, ci, v) = _assemble_both(N, PROBLEMS[name])
+    P = N.analyse(rp, ci)
+    Lo, alpha_o = O.ic0(Ao)
+    Lg, alpha_g = N.ic0_factor(P, v)
+    assert alpha_g[0] == alpha_o
+    assert _rel(_np(Lg), Lo.val) <= 1e-12
+    # triangular solves with the oracle's factor
+    N.factor_load(P, _gpu(Lo.val))
+    r = np.random.default_rng(2).standard_normal(Ao.n)
+    y = N.sptrsv(P, _gpu(r), transpose=False)
+    assert _rel(_np(y), O.trsv_lower(Lo, r)) <= 1e-12
+    z = N.sptrsv(P, _gpu(r), transpose=True)
+    assert _rel(_np(z), O.trsv_upper(Lo, r)) <= 1e-12
+
+
+@pytest.mark.parametrize("name", ["poisson2d_32", "fem34", "fd3d_var", "fd2d_var"])
+@pytest.mark.parametrize("prec", ["cg", "jacobi", "ic0"])
+def test_pcg_parity(N, name, prec):
+    Ao, (rp, ci, v) = _assemble_both(N, PROBLEMS[name])
+    P = N.analyse(rp, ci)
+    b = I.rhs(Ao.n, 7)
+    Lo = None
+    if prec == "ic0":
+        Lo, _ = O.ic0(Ao)
+    pc = {"cg": O.PREC_NONE, "jacobi": O.PREC_JACOBI, "ic0": O.PREC_LLT}[prec]
+    xo, ito, rro, sto = O.pcg(Ao, b, pc, Lo, rtol=1e-8)
+    xg, st = N.pcg_solve(P, v, _gpu(b), pc, _gpu(Lo.val) if Lo is not None else None, rtol=1e-8)
+    assert sto == 0 and st[0]["status"] == 0
+    assert abs(st[0]["iters"] - ito) <= 1
+    assert np.linalg.norm(_np(xg) - xo) / np.linalg.norm(xo) <= 1e-8
+    assert st[0]["relres"] <= 1e-8
+
+
+def test_pcg_edge_cases(N):
+    Ao, (rp, ci, v) = _assemble_both(N, I.fd2d(9, 7))
+    P = N.analyse(rp, ci)
+    x, st = N.pcg_solve(P, v, torch.zeros(Ao.n, dtype=torch.float64, device="cuda"), N.PREC_NONE)
+    assert st[0]["iters"] == 0 and st[0]["status"] == 0 and float(x.abs().max()) == 0.0
+    b = I.rhs(Ao.n, 3)
+    x, st = N.pcg_solve(P, v, _gpu(b), N.PREC_NONE, rtol=1e-14, max_iter=3)
+    assert st[0]["status"] == N.NPCG_EMAXITER and st[0]["iters"] == 3
+    xo, ito, _, _ = O.pcg(Ao, b, O.PREC_NONE, rtol=1e-14, max_iter=3)
+    assert np.allclose(_np(x), xo, rtol=1e-10, atol=1e-12)
+    # x0 = exact solution: nothing to do
+    xs = np.linalg.solve(Ao.dense(), b)
+    x, st = N.pcg_solve(P, v, _gpu(b), N.PREC_NONE, rtol=1e-6, x0=_gpu(xs))
+    assert st[0]["iters"] == 0
+    # single unknown
+    rp1 = torch.tensor([0, 1], dtype=torch.int32, device="cuda")
+    ci1 = torch.tensor([0], dtype=torch.int32, device="cuda")
+    P1 = N.analyse(rp1, ci1)
+    x, st = N.pcg_solve(P1, _gpu([4.0]), _gpu([2.0]), N.PREC_JACOBI, rtol=1e-12)
+    assert st[0]["iters"] == 1 and abs(float(x[0]) - 0.5) < 1e-15
+
+
+def test_malformed_patterns_rejected(N):
+    def csr(rows):
+        rp, ci = [0], []
+        for r in rows:
+            ci += r
+            rp.append(len(ci))
+        return (torch.tensor(rp, dtype=torch.int32, device="cuda"),
+                torch.tensor(ci, dtype=torch.int32, device="cuda"))
+    bad = {
+        "unsorted": [[0, 1], [1, 0]],
+        "missing diagonal": [[0, 1], [0]],
+        "asymmetric": [[0, 1], [1]],
+        "out of range": [[0, 5], [1]],
+    }
+    for name, rows in bad.items():
+        rp, ci = csr(rows)
+        with pytest.raises(N.NpcgError):
+            N.analyse(rp, ci)
+
+
+@pytest.mark.parametrize("cfg,prob", [
+    (I.GnnConfig(n_mp=2, l=2, l_mp=2, h=16), I.poisson2d_32()),
+    (I.GnnConfig(n_mp=6, l=2, l_mp=2, h=64), I.fem2d(22, sigma=1.0, seed=9)),
+    (I.GnnConfig(n_mp=3, l=1, l_mp=3, h=32), I.fd3d(7, 6, 5, sigma=1.0, seed=2)),
+    (I.GnnConfig(n_mp=0, l=2, l_mp=2, h=16), I.fd2d(12, 9, sigma=1.0, seed=1)),
+])
+def test_gnn_fp32_parity(N, cfg, prob):
+    Ao, (rp, ci, v) = _assemble_both(N, prob)
+    P = N.analyse(rp, ci)
+    b = I.rhs(Ao.n, 11)
+    w = I.gnn_weights(cfg, 1)
+    Lo = O.gnn_forward(cfg, Ao, b, w)
+    Lg = _np(N.gnn_factor(P, v, _gpu(b), cfg, _gpu(w, torch.float32)))
+    d = Lg - Lo.val
+    assert np.linalg.norm(d) / np.linalg.norm(Lo.val) <= 1e-5
+    assert np.abs(d).max() <= 1e-5 * np.abs(Lo.val).max()
+
+
+def test_learned_pcg_parity(N):
+    # the oracle's learned factor through the GPU PCG, and the GPU factor's
+    # iteration count against the oracle's
+    cfg = I.GnnConfig(n_mp=2, l=2, l_mp=2, h=16)
+    Ao, (rp, ci, v) = _assemble_both(N, I.poisson2d_32())
+    P = N.analyse(rp, ci)
+    b = I.rhs(Ao.n, 0)
+    w = I.gnn_weights(cfg, 1)
+    Lo = O.gnn_forward(cfg, Ao, b, w)
+    xo, ito, _, sto = O.pcg(Ao, b, O.PREC_LLT, Lo, rtol=1e-8)
+    xg, st = N.pcg_solve(P, v, _gpu(b), N.PREC_LLT, _gpu(Lo.val), rtol=1e-8)
+    assert abs(st[0]["iters"] - ito) <= 1
+    assert np.linalg.norm(_np(xg) - xo) / np.linalg.norm(xo) <= 1e-8
+    Lg = N.gnn_factor(P, v, _gpu(b), cfg, _gpu(w, torch.float32))
+    xg2, st2 = N.pcg_solve(P, v, _gpu(b), N.PREC_LLT, Lg, rtol=1e-8)
+    assert abs(st2[0]["iters"] - ito) <= 1
+
+
+def test_batched_matches_individual(N):
+    probs = [I.fem2d(20, sigma=1.0, seed=1), I.fd3d(6, 5, 4, sigma=1.0, seed=2), I.fd2d(13, 11, sigma=1.0, seed=3)]
+    As, rps, cis, vs, bs = [], [], [], [], []
+    off = 0
+    sys_ptr = [0]
+    for k, p in enumerate(probs):
+        Ao, (rp, ci, v) = _assemble_both(N, p)
+        As.append(Ao)
+        cis.append(_np(ci) + off)
+        vs.append(_np(v))
+        bs.append(I.rhs(Ao.n, 20 + k))
+        off += Ao.n
+        sys_ptr.append(off)
+    nnz_off = np.cumsum([0] + [a.nnz for a in As])
+    rp_cat = np.concatenate([a.row_ptr[:-1] + nnz_off[k] for k, a in enumerate(As)] + [[nnz_off[-1]]])
+    P = N.analyse(_gpu(rp_cat, torch.int32), _gpu(np.concatenate(cis), torch.int32), sys_ptr)
+    v_cat = _gpu(np.concatenate(vs))
+    b_cat = np.concatenate(bs)
+    Lg, alpha = N.ic0_factor(P, v_cat)
+    for prec in (N.PREC_NONE, N.PREC_LLT):
+        x, st = N.pcg_solve(P, v_cat, _gpu(b_cat), prec, Lg if prec == N.PREC_LLT else None, rtol=1e-8)
+        xs = _np(x)
+        for k, Ao in enumerate(As):
+            Lo = O.ic0(Ao)[0] if prec == N.PREC_LLT else None
+            xo, ito, _, _ = O.pcg(Ao, bs[k], prec, Lo, rtol=1e-8)
+            assert st[k]["status"] == 0
+            assert abs(st[k]["iters"] - ito) <= 1
+            seg = xs[sys_ptr[k]:sys_ptr[k + 1]]
+            assert np.linalg.norm(seg - xo) / np.linalg.norm(xo) <= 1e-8
+
+
+def test_solve_host_matches_device_path(N):
+    Ao, (rp, ci, v) = _assemble_both(N, PROBLEMS["fem34"])
+    P = N.analyse(rp, ci)
+    b = I.rhs(Ao.n, 5)
+    xh, st = N.solve_host(P, Ao.val.copy(), b.copy(), method=N.METHOD_IC0, rtol=1e-8)
+    xo, ito, _, _ = O.pcg(Ao, b, O.PREC_LLT, O.ic0(Ao)[0], rtol=1e-8)
+    assert abs(st[0]["iters"] - ito) <= 1
+    assert np.linalg.norm(xh - xo) / np.linalg.norm(xo) <= 1e-8
+
+
+def test_fem256_full_size(N):
+    # the 256 x 256 FEM workload: assembly, levels and the IC(0)-PCG solve
+    p = I.fem2d_256()
+    Ao, (rp, ci, v) = _assemble_both(N, p)
+    assert np.array_equal(_np(ci), Ao.col_idx) and _rel(_np(v), Ao.val) <= 1e-12
+    P = N.analyse(rp, ci)
+    Lo, _ = O.tril(Ao)
+    lev, nf, levb, nb = O.levels(Lo)
+    ex = P.export()
+    assert np.array_equal(_np(ex["lev_fwd"]), lev) and np.array_equal(_np(ex["lev_bwd"]), levb)
+    Lic, _ = O.ic0(Ao)
+    Lg, _ = N.ic0_factor(P, v)
+    assert _rel(_np(Lg), Lic.val) <= 1e-12
+    b = I.rhs(Ao.n, 0)
+    xo, ito, _, _ = O.pcg(Ao, b, O.PREC_LLT, Lic, rtol=1e-6)
+    xg, st = N.pcg_solve(P, v, _gpu(b), N.PREC_LLT, Lg, rtol=1e-6)
+    assert abs(st[0]["iters"] - ito) <= 1
+    assert np.linalg.norm(_np(xg) - xo) / np.linalg.norm(xo) <= 1e-8
