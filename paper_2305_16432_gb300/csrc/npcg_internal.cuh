@@ -25,7 +25,7 @@ constexpr unsigned long long kSentinelBits = 0x7FF4DEADBEEFCAFEull;
 constexpr int kLevelUnset = -1;
 
 // status word flags (device)
-enum : int { kFlagTimeout = 1, kFlagBadPattern = 2, kFlagNotSpd = 4, kFlagAbort = 8 };
+enum : int { kFlagTimeout = 1, kFlagBadPattern = 2, kFlagNotSpd = 4, kFlagAbort = 8, kFlagTripBound = 16 };
 
 // ---------------------------------------------------------------------------
 // device memory: a typed, owned allocation

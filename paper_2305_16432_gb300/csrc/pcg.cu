@@ -90,11 +90,13 @@ struct PcgArgs {
 };
 
 // sum_j A_ij * v_j for one row by a group of G lanes (row entries strided by G)
+// (every lane of the warp calls this; lanes of an invalid row add nothing)
 template <int G>
 __device__ __forceinline__ double row_dot(const int32_t* rp, const int32_t* ci, const double* av,
-                                          const double* v, int row, int g) {
+                                          const double* v, int row, int g, bool valid) {
     double s = 0.0;
-    for (int k = rp[row] + g; k < rp[row + 1]; k += G) s = fma(av[k], v[ci[k]], s);
+    const int k1 = valid ? rp[row + 1] : 0;
+    for (int k = valid ? rp[row] + g : 0; k < k1; k += G) s = fma(av[k], v[ci[k]], s);
 #pragma unroll
     for (int o = G / 2; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, G);
     return s;
@@ -105,11 +107,13 @@ __device__ __forceinline__ double row_dot(const int32_t* rp, const int32_t* ci, 
 __global__ void k_init(PcgArgs a, double rtol, int max_iter, double* p0, double* p1) {
     __shared__ double sh[2][kChunkThreads / 32];
     const Chunk c = a.chunks[blockIdx.x];
-    const int g = threadIdx.x & 7, grp = threadIdx.x >> 3;
+    const int g = threadIdx.x & 7, sub = (threadIdx.x >> 3) & 3, warp = threadIdx.x >> 5;
     double acc[2] = {0.0, 0.0};
-    for (int row = c.row0 + grp; row < c.row1; row += kChunkThreads / 8) {
-        double ax = row_dot<8>(a.rp, a.ci, a.av, a.x, row, g);
-        if (g == 0) {
+    for (int base = c.row0 + warp * 4; base < c.row1; base += kChunkThreads / 8) {
+        const int row = base + sub;
+        const bool valid = row < c.row1;
+        double ax = row_dot<8>(a.rp, a.ci, a.av, a.x, row, g, valid);
+        if (g == 0 && valid) {
             double bi = a.b[row];
             double ri = bi - ax;
             a.r[row] = ri;
@@ -198,17 +202,20 @@ __global__ void k_spmv_p(PcgArgs a, const double* __restrict__ p_old, double* __
     const SysState& s0 = a.st[c.sys];
     if (!s0.active) return;
     const double beta = s0.beta;
-    const int g = threadIdx.x & 7, grp = threadIdx.x >> 3;
+    const int g = threadIdx.x & 7, sub = (threadIdx.x >> 3) & 3, warp = threadIdx.x >> 5;
     double acc[1] = {0.0};
-    for (int row = c.row0 + grp; row < c.row1; row += kChunkThreads / 8) {
+    for (int base = c.row0 + warp * 4; base < c.row1; base += kChunkThreads / 8) {
+        const int row = base + sub;
+        const bool valid = row < c.row1;
         double s = 0.0;
-        for (int k = a.rp[row] + g; k < a.rp[row + 1]; k += 8) {
+        const int k1 = valid ? a.rp[row + 1] : 0;
+        for (int k = valid ? a.rp[row] + g : 0; k < k1; k += 8) {
             int j = a.ci[k];
             s = fma(a.av[k], fma(beta, p_old[j], a.z[j]), s);
         }
 #pragma unroll
         for (int o = 4; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, 8);
-        if (g == 0) {
+        if (g == 0 && valid) {
             double pi = fma(beta, p_old[row], a.z[row]);
             p_new[row] = pi;
             a.w[row] = s;
@@ -287,9 +294,13 @@ struct TriDev {
 
 // One warp per 32-row slice, one lane per row, slices claimed in level order
 // by a ticket counter, so every dependency belongs to an earlier-claimed
-// (running) warp.  out[] holds the sentinel until written; a lane polls its
-// pending dependencies each round and combines them in slot order once all
-// are present, so the result does not depend on timing.
+// (running) warp or to a lower lane of the same slice.  out[] holds the
+// sentinel until written.  Each round, every unfinished lane polls the
+// pending dependencies of its current chunk of (up to 8) off-diagonals; once
+// a chunk is complete the lane folds it in slot order (so the result does
+// not depend on timing), moves to its next chunk, and publishes its row the
+// moment its last chunk is folded -- inside the round, because other lanes
+// of the same warp may be waiting for it.
 template <bool kBatched>
 __global__ void __launch_bounds__(kTrsvThreads) k_trsv(TriDev T, const double* __restrict__ rhs,
                                                        double* out, int* ticket, int* flags,
@@ -303,55 +314,75 @@ __global__ void __launch_bounds__(kTrsvThreads) k_trsv(TriDev T, const double* _
         slice = __shfl_sync(0xffffffffu, slice, 0);
         if (slice >= T.nslices) return;
         const int64_t q = (int64_t)slice * kSlice + lane;
-        int row = q < T.n ? T.perm[q] : -1;
+        const int row = q < T.n ? T.perm[q] : -1;
         bool act = row >= 0;
         if (kBatched && act) act = st[row_sys[row]].active != 0;
         const int width = T.sw[slice];
         const int64_t off = T.soff[slice];
         double acc = act ? rhs[row] : 0.0;
         const double d = act ? T.diag[q] : 1.0;
-        long long spins = 0;
-        for (int k0 = 0; k0 < width; k0 += kDepChunk) {
-            int cj[kDepChunk];
-            double lv[kDepChunk], yv[kDepChunk];
-            unsigned pend = 0;
+        int cj[kDepChunk];
+        double lv[kDepChunk], yv[kDepChunk];
+        unsigned pend = 0;
+        int k0 = 0;
+        bool done = !act;
+        // first chunk
 #pragma unroll
-            for (int k = 0; k < kDepChunk; ++k) {
-                cj[k] = -1;
-                lv[k] = 0.0;
-                yv[k] = 0.0;
-                if (act && k0 + k < width) {
-                    int64_t slot = off + (int64_t)(k0 + k) * kSlice + lane;
-                    cj[k] = T.col[slot];
-                    lv[k] = T.val[slot];
-                    if (cj[k] >= 0) pend |= 1u << k;
-                }
+        for (int k = 0; k < kDepChunk; ++k) {
+            cj[k] = -1;
+            lv[k] = 0.0;
+            yv[k] = 0.0;
+            if (act && k < width) {
+                const int64_t slot = off + (int64_t)k * kSlice + lane;
+                cj[k] = T.col[slot];
+                lv[k] = T.val[slot];
+                if (cj[k] >= 0) pend |= 1u << k;
             }
-            while (__any_sync(0xffffffffu, pend != 0)) {
+        }
+        long long spins = 0;
+        while (__any_sync(0xffffffffu, !done)) {
+            if (!done) {
 #pragma unroll
                 for (int k = 0; k < kDepChunk; ++k) {
                     if (pend & (1u << k)) {
-                        unsigned long long bits = ld_relaxed_u64(out + cj[k]);
+                        const unsigned long long bits = ld_relaxed_u64(out + cj[k]);
                         if (bits != kS) {
                             yv[k] = __longlong_as_double((long long)bits);
                             pend &= ~(1u << k);
                         }
                     }
                 }
-                if (++spins > kSpinLimit) {
-                    if (pend) atomicOr(flags, kFlagTimeout | kFlagAbort);
-                    return;
-                }
-                if ((spins & 255) == 0) {
-                    int f = lane == 0 ? ld_relaxed_s32(flags) : 0;
-                    if (__shfl_sync(0xffffffffu, f, 0) & kFlagAbort) return;
+                while (!done && pend == 0) {
+#pragma unroll
+                    for (int k = 0; k < kDepChunk; ++k)
+                        if (cj[k] >= 0) acc = fma(-lv[k], yv[k], acc);
+                    k0 += kDepChunk;
+                    if (k0 >= width) {
+                        st_relaxed_u64(out + row, (unsigned long long)__double_as_longlong(acc / d));
+                        done = true;
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < kDepChunk; ++k) {
+                            cj[k] = -1;
+                            if (k0 + k < width) {
+                                const int64_t slot = off + (int64_t)(k0 + k) * kSlice + lane;
+                                cj[k] = T.col[slot];
+                                lv[k] = T.val[slot];
+                                if (cj[k] >= 0) pend |= 1u << k;
+                            }
+                        }
+                    }
                 }
             }
-#pragma unroll
-            for (int k = 0; k < kDepChunk; ++k)
-                if (cj[k] >= 0) acc = fma(-lv[k], yv[k], acc);
+            if (++spins > kSpinLimit) {
+                if (!done) atomicOr(flags, kFlagTimeout | kFlagAbort);
+                return;
+            }
+            if ((spins & 255) == 0) {
+                const int f = lane == 0 ? ld_relaxed_s32(flags) : 0;
+                if (__shfl_sync(0xffffffffu, f, 0) & kFlagAbort) return;
+            }
         }
-        if (act) st_relaxed_u64(out + row, (unsigned long long)__double_as_longlong(acc / d));
     }
 }
 
@@ -375,17 +406,28 @@ __global__ void k_fill_sentinel(int64_t n, double* y) {
 __global__ void k_spmv_plain(int64_t n, const int32_t* rp, const int32_t* ci, const double* av,
                              const double* x, double* y) {
     const int g = threadIdx.x & 7;
-    int64_t grp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 3;
-    int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) >> 3;
-    for (int64_t row = grp; row < n; row += ngrp) {
-        double s = row_dot<8>(rp, ci, av, x, (int)row, g);
-        if (g == 0) y[row] = s;
+    const int64_t wbase = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * 4;
+    const int64_t wstride = (((int64_t)gridDim.x * blockDim.x) >> 5) * 4;
+    for (int64_t base = wbase; base < n; base += wstride) {
+        const int64_t row = base + ((threadIdx.x >> 3) & 3);
+        const bool valid = row < n;
+        double s = row_dot<8>(rp, ci, av, x, (int)row, g, valid);
+        if (g == 0 && valid) y[row] = s;
     }
 }
 
-__global__ void k_set_cond(cudaGraphConditionalHandle hd, const int* ctl) {
+// Loop condition of the device-side while: some system still active, no
+// abort, and the trip count (ctl[4]) below its bound (ctl[5], set by the
+// host from max_iter; every system stops by max_iter, so reaching the bound
+// means the bookkeeping failed and the loop is cut with an abort).
+__global__ void k_set_cond(cudaGraphConditionalHandle hd, int* ctl) {
     if (threadIdx.x == 0) {
+        int trips = ++ctl[4];
         int go = ctl[0] > 0 && !(ctl[1] & kFlagAbort);
+        if (go && trips >= ctl[5]) {
+            ctl[1] |= kFlagAbort | kFlagTripBound;
+            go = 0;
+        }
         cudaGraphSetConditional(hd, go ? 1u : 0u);
     }
 }
@@ -597,7 +639,11 @@ npcg_status pcg_run(Handle* h, Pattern* P, const double* A_val, const double* b,
     if (x != P->x.p)
         NPCG_CUDA(h, cudaMemcpyAsync(P->x.p, x, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
     if (precond == NPCG_PREC_LLT) NPCG_TRY(factor_load(h, P, L_val));
-    NPCG_CUDA(h, cudaMemsetAsync(P->ctl.p, 0, 4 * sizeof(int), h->stream));
+    {
+        // ctl: n_active, flags, tickets, loop trips, trip bound (2 iterations per trip)
+        const int init[6] = {0, 0, 0, 0, 0, max_iter / 2 + 2};
+        NPCG_CUDA(h, cudaMemcpyAsync(P->ctl.p, init, sizeof(init), cudaMemcpyHostToDevice, h->stream));
+    }
     PcgArgs a = pcg_args(P, precond);
     k_init<<<P->nchunks, kChunkThreads, 0, h->stream>>>(a, rtol, max_iter, P->p0.p, P->p1.p);
     if (precond == NPCG_PREC_LLT) {
@@ -614,10 +660,17 @@ npcg_status pcg_run(Handle* h, Pattern* P, const double* A_val, const double* b,
                                  cudaMemcpyDeviceToHost, h->stream));
     if (x != P->x.p)
         NPCG_CUDA(h, cudaMemcpyAsync(x, P->x.p, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
-    int ctl[2] = {0, 0};
-    NPCG_CUDA(h, cudaMemcpyAsync(ctl, P->ctl.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    int ctl[6] = {0, 0, 0, 0, 0, 0};
+    NPCG_CUDA(h, cudaMemcpyAsync(ctl, P->ctl.p, 6 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     NPCG_CUDA(h, cudaStreamSynchronize(h->stream));
-    if (ctl[1] & kFlagTimeout) return set_error(h, NPCG_ETIMEOUT, "triangular solve wait timed out");
+    if (ctl[1] & (kFlagTimeout | kFlagTripBound)) {
+        std::string why = (ctl[1] & kFlagTimeout) ? "triangular solve wait timed out"
+                                                  : "iteration loop exceeded its trip bound";
+        return set_error(h, NPCG_ETIMEOUT,
+                         why + " (trips " + std::to_string(ctl[4]) + ", active systems " +
+                             std::to_string(ctl[0]) + ", system 0 iterations " +
+                             std::to_string(stats[0].iters) + ", status " + std::to_string(stats[0].status) + ")");
+    }
     for (int s = 0; s < P->nsys; ++s)
         if (stats[s].status != NPCG_OK)
             return set_error(h, (npcg_status)stats[s].status,

@@ -125,6 +125,14 @@ def test_ic0_and_sptrsv_parity(N, name):
     assert _rel(_np(z), O.trsv_upper(Lo, r)) <= 1e-12
 
 
+def iter_tol(prec, iters):
+    """Iteration-count bar: +-1 for preconditioned solves; for plain CG the
+    spread the oracle's own recurrence shows under other summation orders
+    (tests/test_oracle_solvers.py::test_cg_iteration_spread_under_summation_order),
+    i.e. 1 % of the count."""
+    return 1 if prec != "cg" else max(1, int(np.ceil(0.01 * iters)))
+
+
 @pytest.mark.parametrize("name", ["poisson2d_32", "fem34", "fd3d_var", "fd2d_var"])
 @pytest.mark.parametrize("prec", ["cg", "jacobi", "ic0"])
 def test_pcg_parity(N, name, prec):
@@ -135,12 +143,18 @@ def test_pcg_parity(N, name, prec):
     if prec == "ic0":
         Lo, _ = O.ic0(Ao)
     pc = {"cg": O.PREC_NONE, "jacobi": O.PREC_JACOBI, "ic0": O.PREC_LLT}[prec]
+    Lg = _gpu(Lo.val) if Lo is not None else None
     xo, ito, rro, sto = O.pcg(Ao, b, pc, Lo, rtol=1e-8)
-    xg, st = N.pcg_solve(P, v, _gpu(b), pc, _gpu(Lo.val) if Lo is not None else None, rtol=1e-8)
+    xg, st = N.pcg_solve(P, v, _gpu(b), pc, Lg, rtol=1e-8)
     assert sto == 0 and st[0]["status"] == 0
-    assert abs(st[0]["iters"] - ito) <= 1
-    assert np.linalg.norm(_np(xg) - xo) / np.linalg.norm(xo) <= 1e-8
+    assert abs(st[0]["iters"] - ito) <= iter_tol(prec, ito)
     assert st[0]["relres"] <= 1e-8
+    true_res = np.linalg.norm(b - O.spmv(Ao, _np(xg))) / np.linalg.norm(b)
+    assert true_res <= 2e-8
+    # the same number of updates: the iterates agree to 1e-8
+    xk, stk = N.pcg_solve(P, v, _gpu(b), pc, Lg, rtol=0.0, max_iter=ito)
+    assert stk[0]["iters"] == ito
+    assert np.linalg.norm(_np(xk) - xo) / np.linalg.norm(xo) <= 1e-8
 
 
 def test_pcg_edge_cases(N):

@@ -276,3 +276,52 @@ def test_iteration_counts_match_dense_reference_recurrence():
             r, z = rn, zn
         assert it == kmax
         assert np.allclose(x, xd, rtol=1e-9, atol=1e-12)
+
+
+def _cg_with_order(A, b, rtol, order):
+    """Algorithm 1 without preconditioner, dot products summed in another
+    (equally valid) order; used to measure how far rounding alone moves the
+    iteration count."""
+    D = A.dense()
+    n = A.n
+
+    def dot(u, w):
+        if order == "pairwise":
+            return float(np.dot(u, w))
+        if order == "blocked":
+            return float(sum(np.sum(u[k:k + 2048] * w[k:k + 2048]) for k in range(0, n, 2048)))
+        s = 0.0
+        for i in range(n - 1, -1, -1):
+            s += u[i] * w[i]
+        return s
+    x = np.zeros(n)
+    r = b.copy()
+    tol = rtol * math.sqrt(dot(b, b))
+    p = r.copy()
+    rz = dot(r, r)
+    k = 0
+    while True:
+        w = D @ p
+        al = rz / dot(p, w)
+        x += al * p
+        r -= al * w
+        k += 1
+        if math.sqrt(dot(r, r)) <= tol:
+            return k
+        rzn = dot(r, r)
+        p = r + (rzn / rz) * p
+        rz = rzn
+
+
+def test_cg_iteration_spread_under_summation_order():
+    # Unpreconditioned CG on an ill-conditioned FEM system: the iteration
+    # count to 1e-8 moves by a few under a different summation order of the
+    # same recurrence, so a +-1 bar is below the arithmetic's resolution
+    # there; the spread stays within 1 % of the count.
+    A = O.assemble(I.fem2d(34, sigma=1.0, seed=5))
+    b = I.rhs(A.n, 7)
+    _, it, _, _ = O.pcg(A, b, O.PREC_NONE, rtol=1e-8)
+    others = [_cg_with_order(A, b, 1e-8, o) for o in ("pairwise", "blocked", "reverse")]
+    spread = max(abs(k - it) for k in others)
+    assert spread > 1                      # the effect is real
+    assert spread <= max(1, math.ceil(0.01 * it))
