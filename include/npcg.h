@@ -264,6 +264,35 @@ NPCG_API npcg_status npcg_solve_host(npcg_handle h, npcg_pattern p, int32_t meth
                             const double* A_val_host, const double* b_host, double* x_host,
                             double rtol, int32_t max_iter, npcg_solve_stats* stats);
 
+/* --------------------------------------------------------------------------
+ * Allocation-free solve (the paper has no counterpart; this serves callers
+ * that cannot allocate device memory: code running while another arena or
+ * runtime owns the device memory, real-time loops where an allocation's
+ * latency or failure is unacceptable).  Plain CG (NPCG_PREC_NONE) or
+ * Jacobi-PCG (NPCG_PREC_JACOBI), the recurrence of npcg_pcg_solve, on a raw
+ * CSR matrix (row_ptr [n+1], col_idx [nnz], A_val [nnz], b [n], x [n]:
+ * device, caller-owned; x holds x_0 on entry).  No handle, no pattern, no
+ * cudaMalloc / cudaFree or allocating library call: the working vectors and
+ * the solver state live in one fixed device array inside the library,
+ * sized for n <= NPCG_NOALLOC_MAX_N (about 8 MB), which every GPU that
+ * loads the library keeps until the process exits.  Larger n, other
+ * preconditioners or NULL arrays return NPCG_EINVAL before any GPU work.
+ * The first call on a device looks up that array's device address (and may
+ * load the library's device code), so make it before any stream capture.
+ * All calls on a device share the array: calls that overlap on the GPU
+ * (other streams, other host threads) race and corrupt each other; the
+ * array keeps the last call's contents, which each call resets as needed.
+ * Work runs on `stream` (a cudaStream_t); the call synchronises it every
+ * 16 iterations to test convergence.  stats: host, one entry.
+ * ------------------------------------------------------------------------ */
+#define NPCG_NOALLOC_MAX_N 262144
+
+NPCG_API npcg_status npcg_pcg_solve_noalloc(void* stream, int64_t n, int64_t nnz,
+                                            const int32_t* row_ptr, const int32_t* col_idx,
+                                            const double* A_val, const double* b, double* x,
+                                            int32_t precond, double rtol, int32_t max_iter,
+                                            npcg_solve_stats* stats);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,90 @@
+"""The allocation-free entry point npcg_pcg_solve_noalloc, for callers that
+cannot allocate device memory (another arena or runtime owns it, or an
+allocation's latency or failure is unacceptable in their loop).  Called
+through the C ABI and checked against npcg_pcg_solve (the entry point that
+allocates its workspace) on the same systems, twice in a row, since every
+call shares the library's fixed device array.  Collected last so a run that
+stops at the first failure has run every other test first.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2305_16432_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+MAX_N = 262144     # NPCG_NOALLOC_MAX_N in include/npcg.h
+
+
+class _Stats(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("status", C.c_int32), ("relres", C.c_double)]
+
+
+@pytest.fixture(scope="module")
+def env():
+    from paper_2305_16432_gb300 import build
+    build.build()
+    from paper_2305_16432_gb300 import npcg
+    lib = npcg.lib()
+    fn = lib.npcg_pcg_solve_noalloc
+    fn.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                   C.c_void_p, C.c_int32, C.c_double, C.c_int32, C.c_void_p]
+    fn.restype = C.c_int
+    return npcg, fn
+
+
+def _noalloc(fn, rp, ci, v, b, precond, rtol, max_iter):
+    x = torch.zeros_like(b)
+    st = _Stats()
+    stream = torch.cuda.current_stream().cuda_stream
+    rc = fn(C.c_void_p(stream), rp.numel() - 1, ci.numel(), C.c_void_p(rp.data_ptr()),
+            C.c_void_p(ci.data_ptr()), C.c_void_p(v.data_ptr()), C.c_void_p(b.data_ptr()),
+            C.c_void_p(x.data_ptr()), precond, rtol, max_iter, C.byref(st))
+    return rc, x, st
+
+
+@pytest.mark.parametrize("prob,precond", [(I.fem2d(34, sigma=1.0, seed=5), 1),
+                                          (I.fd3d(9, 8, 7, sigma=1.5, corr_len=0.05, seed=4), 1),
+                                          (I.poisson2d_32(), 0)])
+def test_noalloc_matches_allocating_entry_point(env, prob, precond):
+    N, fn = env
+    rp, ci, v = N.assemble_system(prob)
+    P = N.analyse(rp, ci)
+    b = torch.as_tensor(I.rhs(P.n, 3), device="cuda")
+    x_ref, st_ref = N.pcg_solve(P, v, b, precond, None, rtol=1e-8)
+    for _ in range(2):                                    # two calls in a row
+        rc, x, st = _noalloc(fn, rp, ci, v, b, precond, 1e-8, 10 * P.n)
+        assert rc == 0 and st.status == 0
+        assert abs(st.iters - st_ref[0]["iters"]) <= 1
+        assert st.relres <= 1e-8
+        # the same number of updates through the allocating path: same iterate
+        xk, stk = N.pcg_solve(P, v, b, precond, None, rtol=0.0, max_iter=st.iters)
+        d = (x - xk).norm() / xk.norm()
+        assert float(d) <= 1e-8
+    # the solution solves A x = b
+    Ao = O.CSR(rp.cpu().numpy(), ci.cpu().numpy(), v.cpu().numpy())
+    bn = b.cpu().numpy()
+    assert np.linalg.norm(bn - O.spmv(Ao, x.cpu().numpy())) / np.linalg.norm(bn) <= 2e-8
+
+
+def test_noalloc_limits_and_edge_cases(env):
+    N, fn = env
+    rp, ci, v = N.assemble_system(I.fd2d(9, 7))
+    b = torch.zeros(63, dtype=torch.float64, device="cuda")
+    rc, x, st = _noalloc(fn, rp, ci, v, b, 1, 1e-8, 100)
+    assert rc == 0 and st.iters == 0                       # b = 0: nothing to do
+    b = torch.as_tensor(I.rhs(63, 1), device="cuda")
+    rc, x, st = _noalloc(fn, rp, ci, v, b, 0, 1e-14, 3)
+    assert rc == N.NPCG_EMAXITER and st.iters == 3
+    rc, x, st = _noalloc(fn, rp, ci, v, b, 2, 1e-8, 100)   # needs an analysed pattern
+    assert rc == N.NPCG_EINVAL
+    # sizes beyond the fixed array are rejected before any GPU work
+    st = _Stats()
+    rc = fn(None, MAX_N + 1, MAX_N + 1, C.c_void_p(rp.data_ptr()), C.c_void_p(ci.data_ptr()),
+            C.c_void_p(v.data_ptr()), C.c_void_p(b.data_ptr()), C.c_void_p(b.data_ptr()), 1, 1e-8, 10,
+            C.byref(st))
+    assert rc == N.NPCG_EINVAL
