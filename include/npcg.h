@@ -122,12 +122,27 @@ NPCG_API npcg_status npcg_analyse(npcg_handle h, int64_t n, int64_t nnz, const i
                          npcg_pattern* out);
 NPCG_API npcg_status npcg_pattern_free(npcg_pattern p);
 
+/* Triangular-solve designs (both exact, same result up to rounding):
+ *   NPCG_TRSV_SYNCFREE: every SM; rows claimed in level order by warps, each
+ *     row waits on its dependencies' values (flag-free, bounded waits);
+ *   NPCG_TRSV_LEVELSYNC: one CTA per system walks the levels with one
+ *     barrier per level, dependencies in a shared-memory window, each level's
+ *     data prefetched by TMA bulk copies.
+ * npcg_analyse times both on the pattern and keeps the faster. */
+enum { NPCG_TRSV_AUTO = 0, NPCG_TRSV_SYNCFREE = 1, NPCG_TRSV_LEVELSYNC = 2 };
+
 typedef struct {
     int64_t n, nnz, nnz_L;
     int32_t nsys;
     int32_t nlev_fwd, nlev_bwd;   /* number of levels of L y = r / L^T z = y */
+    int32_t trsv_mode;            /* design in use (NPCG_TRSV_SYNCFREE / _LEVELSYNC) */
+    float tuned_ms_syncfree;      /* measured forward + backward solve, ms      */
+    float tuned_ms_levelsync;     /* (0 when the design does not apply)         */
 } npcg_pattern_info;
 NPCG_API npcg_status npcg_pattern_get_info(npcg_pattern p, npcg_pattern_info* out);  /* host out */
+/* Overrides the tuned design (NPCG_TRSV_AUTO restores the tuned choice).
+ * NPCG_TRSV_LEVELSYNC returns NPCG_EINVAL when its layout does not fit. */
+NPCG_API npcg_status npcg_pattern_set_trsv(npcg_pattern p, int32_t mode);
 
 /* Copies of the analysis results (device arrays, caller-allocated):
  * L_row_ptr [n+1], L_col_idx [nnz_L] (tril(A), diagonal last in each row),
@@ -192,7 +207,10 @@ NPCG_API npcg_status npcg_ic0_factor(npcg_handle h, npcg_pattern p, const double
  * Returns NPCG_OK if every system converged, else the first failing
  * system's status (per-system codes are in stats).
  * ------------------------------------------------------------------------ */
-enum { NPCG_PREC_NONE = 0, NPCG_PREC_JACOBI = 1, NPCG_PREC_LLT = 2 };
+enum { NPCG_PREC_NONE = 0, NPCG_PREC_JACOBI = 1, NPCG_PREC_LLT = 2, NPCG_PREC_LLT32 = 3 };
+/* NPCG_PREC_LLT32: P = L' L'^T with L' = L rounded to FP32 and the two
+ * triangular solves in FP32 arithmetic (right-hand side and result FP64);
+ * the PCG recurrences, dot products and SpMV stay FP64. */
 
 typedef struct {
     int32_t iters;       /* updates of x                                  */

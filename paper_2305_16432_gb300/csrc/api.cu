@@ -129,6 +129,25 @@ npcg_status npcg_pattern_get_info(npcg_pattern p, npcg_pattern_info* out) {
     out->nsys = p->nsys;
     out->nlev_fwd = p->fwd.nlev;
     out->nlev_bwd = p->bwd.nlev;
+    out->trsv_mode = p->trsv_mode == kTrsvCta ? NPCG_TRSV_LEVELSYNC : NPCG_TRSV_SYNCFREE;
+    out->tuned_ms_syncfree = p->tune_ms[0];
+    out->tuned_ms_levelsync = p->tune_ms[1];
+    return NPCG_OK;
+}
+
+npcg_status npcg_pattern_set_trsv(npcg_pattern p, int32_t mode) {
+    if (!p) return NPCG_EINVAL;
+    if (mode == NPCG_TRSV_AUTO) {
+        p->trsv_mode = (p->tune_ms[1] > 0.f && p->tune_ms[1] < p->tune_ms[0]) ? kTrsvCta : kTrsvSyncFree;
+    } else if (mode == NPCG_TRSV_SYNCFREE) {
+        p->trsv_mode = kTrsvSyncFree;
+    } else if (mode == NPCG_TRSV_LEVELSYNC) {
+        if (!p->cfwd.built || cta_stages(p->cfwd) < 2 || cta_stages(p->cbwd) < 2)
+            return set_error(p->h, NPCG_EINVAL, "level-synchronous layout does not fit shared memory");
+        p->trsv_mode = kTrsvCta;
+    } else {
+        return set_error(p->h, NPCG_EINVAL, "unknown triangular-solve mode");
+    }
     return NPCG_OK;
 }
 
@@ -216,7 +235,7 @@ npcg_status npcg_sptrsv_timed(npcg_handle h, npcg_pattern p, int32_t transpose, 
     NPCG_TRY(check_hp(h, p));
     if (!r || !y || r == y || !ms_per_launch || reps < 1)
         return set_error(H(h), NPCG_EINVAL, "bad argument");
-    return sptrsv_timed_run(H(h), PT(p), transpose ? 1 : 0, r, y, reps, ms_per_launch);
+    return sptrsv_timed_run(H(h), PT(p), transpose ? 1 : 0, r, y, reps, ms_per_launch, false);
 }
 
 npcg_status npcg_loss_and_grad(npcg_handle h, npcg_pattern p, const double* A_val, int32_t npairs,

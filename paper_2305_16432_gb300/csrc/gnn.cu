@@ -129,6 +129,12 @@ npcg_status gnn_forward_into(Handle* h, Pattern* P, const double* A_val, const d
     }
 }
 
+npcg_status gnn_scales_run(Handle* h, Pattern* P, const double* A_val, const double* b, double* sc) {
+    k_scales<<<P->nsys, 256, 0, h->stream>>>(P->sys_ptr.p, P->adiag.p, A_val, b, sc);
+    NPCG_CUDA(h, cudaGetLastError());
+    return NPCG_OK;
+}
+
 npcg_status gnn_assemble_L(Handle* h, Pattern* P, const GnnBuffers& B, double* L_val) {
     int blocks = std::max(1, std::min(ceil_div(P->nnzL, 256), h->num_sms * 16));
     k_assemble_L<<<blocks, 256, 0, h->stream>>>(P->nnzL, P->l2a.p, P->edge_row.p, P->ci.p, P->mirror.p,

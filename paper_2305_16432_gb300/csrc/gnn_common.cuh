@@ -59,6 +59,7 @@ struct MlpArgs {
     const float* vin;
     const float* ein;
     float* out;
+    float* agg_out;      // node update: optional copy of sum_j e_ij (.) v_j (training tape)
 };
 
 npcg_status gnn_check_config(Handle* h, const npcg_gnn_config* cfg);
@@ -173,6 +174,7 @@ __device__ __forceinline__ void gather_tile(const MlpArgs& a, int64_t row0, floa
             }
             X[r * LD + q] = v;
             X[r * LD + H + q] = agg;
+            if (a.agg_out && i < a.nrows) a.agg_out[i * H + q] = agg;
         }
     } else if (MODE == MODE_EDGE) {
         for (int idx = threadIdx.x; idx < R * 3 * H; idx += blockDim.x) {

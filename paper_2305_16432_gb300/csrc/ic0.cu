@@ -39,9 +39,9 @@ __global__ void __launch_bounds__(256) k_ic0(int64_t n, int nslices, const int32
         int row = q < n ? perm[q] : -1;
         int sys = row >= 0 ? row_sys[row] : 0;
         bool done = row < 0 || !todo[sys];
-        int cur = 0, end = 0;
+        int cur = 0;
         double al = 0.0;
-        if (!done) { cur = Lrp[row]; end = Lrp[row + 1]; al = alpha[sys]; }
+        if (!done) { cur = Lrp[row]; al = alpha[sys]; }
         long long spins = 0;
         while (__any_sync(0xffffffffu, !done)) {
             // advance this row as far as its dependencies allow

@@ -16,7 +16,7 @@ namespace npcg {
 // ---------------------------------------------------------------------------
 constexpr int kWarp = 32;
 constexpr int kSlice = 32;                 // rows per SELL slice = one warp of the solve
-constexpr int kChunk = 2048;               // rows per reduction chunk (one block)
+constexpr int kChunk = 512;                // rows per reduction chunk (one block)
 constexpr int kChunkThreads = 256;
 constexpr long long kSpinLimit = 1LL << 22; // polls before a device wait gives up (~1-2 s)
 
@@ -87,10 +87,28 @@ struct TriLayout {
     DevBuf<int32_t> col;         // [slots] column, -1 = padding
     DevBuf<int32_t> src;         // [slots] index into L_val, -1 = padding
     DevBuf<int32_t> diag_src;    // [n by position] index of the diagonal in L_val
-    DevBuf<double> val;          // [slots] loaded factor values
-    DevBuf<double> diag;         // [n by position] loaded diagonal
+    DevBuf<double> val, dinv;    // [slots] factor values, [n by position] 1 / diagonal (FP64)
+    DevBuf<float> val32, dinv32; // the same in FP32
     int64_t slots = 0;
 };
+
+// Per-system level-synchronous layout of one triangular solve (one CTA per
+// system, steps of <= 256 rows of one level, TMA-prefetched).
+struct CtaLayout {
+    bool built = false;
+    bool window_ok = false;        // every dependency within the shared window
+    int nsteps = 0, max_w = 0, max_np = 0;
+    int64_t sbuf_len = 0, vbuf_len = 0;
+    DevBuf<int32_t> cperm, cpos;   // processing order and its inverse
+    DevBuf<int4> steps;            // {q0, nrows, width, 0}
+    DevBuf<int64_t> soff, voff;
+    DevBuf<int32_t> sys_step0;
+    DevBuf<int32_t> sbuf, vsrc, is_diag, step_of_pos;
+    DevBuf<double> vbuf;
+    DevBuf<float> vbuf32;
+};
+
+enum TrsvMode : int { kTrsvAuto = 0, kTrsvSyncFree = 1, kTrsvCta = 2 };
 
 // graph-network feature buffers, grown on demand
 struct GnnStore {
@@ -115,6 +133,10 @@ struct Pattern {
     DevBuf<int32_t> a2l;           // [nnz] L position of (i,j), j <= i, else -1
     DevBuf<int32_t> Lrp, Lci, l2a; // tril pattern and L -> A map
     TriLayout fwd, bwd;            // L y = r and L^T z = y
+    CtaLayout cfwd, cbwd;          // level-synchronous layouts
+    int trsv_mode = kTrsvSyncFree; // chosen by the autotuner
+    float tune_ms[2] = {0.f, 0.f}; // measured fwd+bwd time per mode
+    DevBuf<double> r_cf, y_cb, yglob;  // rhs in processing order, window backing
     // reduction chunks
     std::vector<Chunk> chunks_h;
     DevBuf<Chunk> chunks;
@@ -130,7 +152,8 @@ struct Pattern {
     DevBuf<double> Aval_dev;       // host-path copy of A values
     DevBuf<double> Lval_dev;       // host-path factor
     // cached iteration graphs (keyed by precond)
-    cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
+    cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};
+    int graph_mode[4] = {0, 0, 0, 0};
     GnnStore gnn;
     ~Pattern();
 };
@@ -204,8 +227,16 @@ npcg_status factor_load(Handle* h, Pattern* P, const double* L_val);
 npcg_status sptrsv_run(Handle* h, Pattern* P, int transpose, const double* r, double* y,
                        const int32_t* sys_active);
 npcg_status spmv_run(Handle* h, Pattern* P, const double* A_val, const double* x, double* y);
+npcg_status cta_layout_build(Handle* h, Pattern* P, bool upper, CtaLayout* C);
+npcg_status cta_link(Handle* h, Pattern* P);
+int cta_stages(const CtaLayout& C);
+npcg_status cta_factor_load(Handle* h, CtaLayout* C, const double* L_val);
+npcg_status cta_gather(Handle* h, cudaStream_t s, const CtaLayout& C, int64_t n, const double* x, double* xp);
+npcg_status cta_trsv_launch(Handle* h, cudaStream_t s, Pattern* P, const CtaLayout& C, const double* rhs_perm,
+                            double* out, double* out2, const SysState* st, bool f32);
+npcg_status trsv_autotune(Handle* h, Pattern* P);
 npcg_status sptrsv_timed_run(Handle* h, Pattern* P, int transpose, const double* r, double* y, int reps,
-                             double* ms_per_launch);
+                             double* ms_per_launch, bool f32);
 npcg_status pcg_run(Handle* h, Pattern* P, const double* A_val, const double* b, double* x,
                     int precond, const double* L_val, double rtol, int max_iter,
                     npcg_solve_stats* stats);

@@ -261,8 +261,10 @@ npcg_status build_tri(Handle* h, Pattern* P, bool upper, TriLayout* T) {
     NPCG_CUDA(h, T->col.alloc(std::max<int64_t>(T->slots, 1)));
     NPCG_CUDA(h, T->src.alloc(std::max<int64_t>(T->slots, 1)));
     NPCG_CUDA(h, T->val.alloc(std::max<int64_t>(T->slots, 1)));
+    NPCG_CUDA(h, T->val32.alloc(std::max<int64_t>(T->slots, 1)));
     NPCG_CUDA(h, T->diag_src.alloc(n));
-    NPCG_CUDA(h, T->diag.alloc(n));
+    NPCG_CUDA(h, T->dinv.alloc(n));
+    NPCG_CUDA(h, T->dinv32.alloc(n));
     if (upper)
         k_slice_fill<true><<<g, thr, 0, h->stream>>>(n, T->nslices, T->perm.p, P->rp.p, P->ci.p, P->Lrp.p,
                                                      P->Lci.p, P->mirror.p, P->a2l.p, T->slice_off.p,
@@ -369,6 +371,11 @@ npcg_status pattern_build(Handle* h, int64_t n, int64_t nnz, const int32_t* rp, 
     NPCG_CUDA(h, cudaMemcpyAsync(P->sys_chunk0.p, first.data(), (nsys + 1) * sizeof(int32_t),
                                  cudaMemcpyHostToDevice, h->stream));
     NPCG_CUDA(h, cudaStreamSynchronize(h->stream));
+    // level-synchronous layouts (one CTA per system) and the choice of design
+    NPCG_TRY(cta_layout_build(h, P, false, &P->cfwd));
+    NPCG_TRY(cta_layout_build(h, P, true, &P->cbwd));
+    NPCG_TRY(cta_link(h, P));
+    NPCG_TRY(trsv_autotune(h, P));
     return NPCG_OK;
 }
 

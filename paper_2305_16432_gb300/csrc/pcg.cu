@@ -36,8 +36,9 @@ __device__ __forceinline__ void block_sum(double (&v)[N], double (*sh)[kChunkThr
     }
 }
 
-// Publishes this chunk's partial sums; returns true (in thread 0) for the
-// last chunk of its system to arrive, which then owns the finalisation.
+// Publishes this chunk's partial sums; returns true (in every thread of the
+// block) for the last chunk of its system to arrive, which then owns the
+// finalisation.
 template <int N>
 __device__ __forceinline__ bool publish(const Chunk& c, const double (&v)[N], double* part,
                                         unsigned* arrive, const int32_t* sys_chunk0) {
@@ -51,20 +52,23 @@ __device__ __forceinline__ bool publish(const Chunk& c, const double (&v)[N], do
         last = (prev == nch - 1);
     }
     __syncthreads();
-    return threadIdx.x == 0 && last;
+    return last;
 }
 
+// Sums the system's chunk partials with the whole block (fixed assignment,
+// so the result is deterministic); the total ends in thread 0.
 template <int N>
 __device__ __forceinline__ void gather_parts(const Chunk& c, const double* part,
                                              const int32_t* sys_chunk0, unsigned* arrive,
-                                             double (&tot)[N]) {
+                                             double (&tot)[N], double (*sh)[kChunkThreads / 32]) {
     __threadfence();
 #pragma unroll
     for (int j = 0; j < N; ++j) tot[j] = 0.0;
-    for (int q = sys_chunk0[c.sys]; q < sys_chunk0[c.sys + 1]; ++q)
+    for (int q = sys_chunk0[c.sys] + threadIdx.x; q < sys_chunk0[c.sys + 1]; q += kChunkThreads)
 #pragma unroll
         for (int j = 0; j < N; ++j) tot[j] += __ldcg(part + (int64_t)q * 4 + j);
-    arrive[c.sys] = 0u;
+    block_sum<N>(tot, sh);
+    if (threadIdx.x == 0) arrive[c.sys] = 0u;
 }
 
 __device__ __forceinline__ void deactivate(SysState& s, int status, int* n_active) {
@@ -86,6 +90,8 @@ struct PcgArgs {
     unsigned* arrive;
     int* ctl;            // [0] n_active [1] flags [2] fwd ticket [3] bwd ticket
     double *x, *r, *z, *y, *w, *b;
+    double* rperm;            // level-synchronous mode: r in forward processing order
+    const int32_t* cposf;     //   and the forward position of each row
     int precond;
 };
 
@@ -117,6 +123,7 @@ __global__ void k_init(PcgArgs a, double rtol, int max_iter, double* p0, double*
             double bi = a.b[row];
             double ri = bi - ax;
             a.r[row] = ri;
+            if (a.rperm) a.rperm[a.cposf[row]] = ri;
             p0[row] = 0.0;
             p1[row] = 0.0;
             a.y[row] = sentinel_f64();
@@ -129,7 +136,8 @@ __global__ void k_init(PcgArgs a, double rtol, int max_iter, double* p0, double*
     block_sum<2>(acc, sh);
     if (publish<2>(c, acc, a.part, a.arrive, a.sys_chunk0)) {
         double tot[2];
-        gather_parts<2>(c, a.part, a.sys_chunk0, a.arrive, tot);
+        gather_parts<2>(c, a.part, a.sys_chunk0, a.arrive, tot, sh);
+        if (threadIdx.x != 0) return;
         SysState& s = a.st[c.sys];
         s.bnorm2 = tot[0];
         s.tol2 = rtol * rtol * tot[0];
@@ -175,14 +183,15 @@ __global__ void k_dot_rz(PcgArgs a, int init) {
     for (int row = c.row0 + threadIdx.x; row < c.row1; row += kChunkThreads) {
         double ri = a.r[row];
         double zi;
-        if (a.precond == NPCG_PREC_LLT) zi = a.z[row];
+        if (a.precond >= NPCG_PREC_LLT) zi = a.z[row];
         else { zi = elementwise_z(a, row, ri); a.z[row] = zi; }
         acc[0] = fma(ri, zi, acc[0]);
     }
     block_sum<1>(acc, sh);
     if (publish<1>(c, acc, a.part, a.arrive, a.sys_chunk0)) {
         double tot[1];
-        gather_parts<1>(c, a.part, a.sys_chunk0, a.arrive, tot);
+        gather_parts<1>(c, a.part, a.sys_chunk0, a.arrive, tot, sh);
+        if (threadIdx.x != 0) return;
         SysState& s = a.st[c.sys];
         double rz = tot[0];
         if (!(rz > 0.0) || !isfinite(rz)) {
@@ -225,7 +234,8 @@ __global__ void k_spmv_p(PcgArgs a, const double* __restrict__ p_old, double* __
     block_sum<1>(acc, sh);
     if (publish<1>(c, acc, a.part, a.arrive, a.sys_chunk0)) {
         double tot[1];
-        gather_parts<1>(c, a.part, a.sys_chunk0, a.arrive, tot);
+        gather_parts<1>(c, a.part, a.sys_chunk0, a.arrive, tot, sh);
+        if (threadIdx.x != 0) return;
         SysState& s = a.st[c.sys];
         s.pw = tot[0];
         if (!(tot[0] > 0.0) || !isfinite(tot[0])) deactivate(s, NPCG_EBREAKDOWN, &a.ctl[0]);
@@ -243,12 +253,13 @@ __global__ void k_update(PcgArgs a, const double* __restrict__ p) {
     const SysState& s0 = a.st[c.sys];
     if (!s0.active) return;
     const double alpha = s0.alpha;
-    const bool llt = a.precond == NPCG_PREC_LLT;
+    const bool llt = a.precond >= NPCG_PREC_LLT;
     double acc[2] = {0.0, 0.0};
     for (int row = c.row0 + threadIdx.x; row < c.row1; row += kChunkThreads) {
         a.x[row] = fma(alpha, p[row], a.x[row]);
         double ri = fma(-alpha, a.w[row], a.r[row]);
         a.r[row] = ri;
+        if (a.rperm) a.rperm[a.cposf[row]] = ri;
         acc[0] = fma(ri, ri, acc[0]);
         if (llt) {
             a.y[row] = sentinel_f64();
@@ -262,7 +273,8 @@ __global__ void k_update(PcgArgs a, const double* __restrict__ p) {
     block_sum<2>(acc, sh);
     if (publish<2>(c, acc, a.part, a.arrive, a.sys_chunk0)) {
         double tot[2];
-        gather_parts<2>(c, a.part, a.sys_chunk0, a.arrive, tot);
+        gather_parts<2>(c, a.part, a.sys_chunk0, a.arrive, tot, sh);
+        if (threadIdx.x != 0) return;
         SysState& s = a.st[c.sys];
         s.rr = tot[0];
         s.iters += 1;
@@ -288,8 +300,8 @@ struct TriDev {
     const int64_t* soff;
     const int32_t* sw;
     const int32_t* col;
-    const double* val;
-    const double* diag;
+    const void* val;    // V[slots]
+    const void* dinv;   // V[n] reciprocal diagonal by position
 };
 
 // One warp per 32-row slice, one lane per row, slices claimed in level order
@@ -301,10 +313,12 @@ struct TriDev {
 // not depend on timing), moves to its next chunk, and publishes its row the
 // moment its last chunk is folded -- inside the round, because other lanes
 // of the same warp may be waiting for it.
-template <bool kBatched>
+template <bool kBatched, class V>
 __global__ void __launch_bounds__(kTrsvThreads) k_trsv(TriDev T, const double* __restrict__ rhs,
                                                        double* out, int* ticket, int* flags,
                                                        const int32_t* row_sys, const SysState* st) {
+    const V* tval = static_cast<const V*>(T.val);
+    const V* tdinv = static_cast<const V*>(T.dinv);
     const int lane = threadIdx.x & 31;
     const unsigned long long kS = kSentinelBits;
     if (!kBatched && st && !st[0].active) return;
@@ -319,10 +333,10 @@ __global__ void __launch_bounds__(kTrsvThreads) k_trsv(TriDev T, const double* _
         if (kBatched && act) act = st[row_sys[row]].active != 0;
         const int width = T.sw[slice];
         const int64_t off = T.soff[slice];
-        double acc = act ? rhs[row] : 0.0;
-        const double d = act ? T.diag[q] : 1.0;
+        V acc = act ? (V)rhs[row] : (V)0;
+        const V dinv = act ? tdinv[q] : (V)1;
         int cj[kDepChunk];
-        double lv[kDepChunk], yv[kDepChunk];
+        V lv[kDepChunk], yv[kDepChunk];
         unsigned pend = 0;
         int k0 = 0;
         bool done = !act;
@@ -330,12 +344,12 @@ __global__ void __launch_bounds__(kTrsvThreads) k_trsv(TriDev T, const double* _
 #pragma unroll
         for (int k = 0; k < kDepChunk; ++k) {
             cj[k] = -1;
-            lv[k] = 0.0;
-            yv[k] = 0.0;
+            lv[k] = (V)0;
+            yv[k] = (V)0;
             if (act && k < width) {
                 const int64_t slot = off + (int64_t)k * kSlice + lane;
                 cj[k] = T.col[slot];
-                lv[k] = T.val[slot];
+                lv[k] = tval[slot];
                 if (cj[k] >= 0) pend |= 1u << k;
             }
         }
@@ -347,7 +361,7 @@ __global__ void __launch_bounds__(kTrsvThreads) k_trsv(TriDev T, const double* _
                     if (pend & (1u << k)) {
                         const unsigned long long bits = ld_relaxed_u64(out + cj[k]);
                         if (bits != kS) {
-                            yv[k] = __longlong_as_double((long long)bits);
+                            yv[k] = (V)__longlong_as_double((long long)bits);
                             pend &= ~(1u << k);
                         }
                     }
@@ -358,7 +372,7 @@ __global__ void __launch_bounds__(kTrsvThreads) k_trsv(TriDev T, const double* _
                         if (cj[k] >= 0) acc = fma(-lv[k], yv[k], acc);
                     k0 += kDepChunk;
                     if (k0 >= width) {
-                        st_relaxed_u64(out + row, (unsigned long long)__double_as_longlong(acc / d));
+                        st_relaxed_u64(out + row, (unsigned long long)__double_as_longlong((double)(acc * dinv)));
                         done = true;
                     } else {
 #pragma unroll
@@ -367,7 +381,7 @@ __global__ void __launch_bounds__(kTrsvThreads) k_trsv(TriDev T, const double* _
                             if (k0 + k < width) {
                                 const int64_t slot = off + (int64_t)(k0 + k) * kSlice + lane;
                                 cj[k] = T.col[slot];
-                                lv[k] = T.val[slot];
+                                lv[k] = tval[slot];
                                 if (cj[k] >= 0) pend |= 1u << k;
                             }
                         }
@@ -387,14 +401,20 @@ __global__ void __launch_bounds__(kTrsvThreads) k_trsv(TriDev T, const double* _
 }
 
 __global__ void k_load_factor(int64_t slots, const int32_t* src, const double* L, double* val,
-                              int64_t n, const int32_t* dsrc, double* diag) {
+                              float* val32, int64_t n, const int32_t* dsrc, double* dinv, float* dinv32) {
     int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     int64_t st = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = i0; i < slots; i += st) {
         int s = src[i];
-        val[i] = s >= 0 ? L[s] : 0.0;
+        double v = s >= 0 ? L[s] : 0.0;
+        val[i] = v;
+        val32[i] = (float)v;
     }
-    for (int64_t i = i0; i < n; i += st) diag[i] = L[dsrc[i]];
+    for (int64_t i = i0; i < n; i += st) {
+        double d = 1.0 / L[dsrc[i]];
+        dinv[i] = d;
+        dinv32[i] = (float)d;
+    }
 }
 
 __global__ void k_fill_sentinel(int64_t n, double* y) {
@@ -442,7 +462,7 @@ __global__ void k_stats(int nsys, const SysState* st, npcg_solve_stats* out) {
     }
 }
 
-TriDev tri_dev(const Pattern* P, const TriLayout& T) {
+TriDev tri_dev(const Pattern* P, const TriLayout& T, bool f32) {
     TriDev d;
     d.n = P->n;
     d.nslices = T.nslices;
@@ -450,8 +470,8 @@ TriDev tri_dev(const Pattern* P, const TriLayout& T) {
     d.soff = T.slice_off.p;
     d.sw = T.slice_w.p;
     d.col = T.col.p;
-    d.val = T.val.p;
-    d.diag = T.diag.p;
+    d.val = f32 ? (const void*)T.val32.p : (const void*)T.val.p;
+    d.dinv = f32 ? (const void*)T.dinv32.p : (const void*)T.dinv.p;
     return d;
 }
 
@@ -462,15 +482,18 @@ int trsv_grid(Handle* h, const TriLayout& T) {
 }
 
 void launch_trsv(Handle* h, cudaStream_t s, Pattern* P, int transpose, const double* rhs, double* out,
-                 int* ticket, bool batched, const SysState* st) {
+                 int* ticket, bool batched, const SysState* st, bool f32) {
     const TriLayout& T = transpose ? P->bwd : P->fwd;
-    TriDev d = tri_dev(P, T);
-    if (batched)
-        k_trsv<true><<<trsv_grid(h, T), kTrsvThreads, 0, s>>>(d, rhs, out, ticket, P->ctl.p + 1,
-                                                               P->row_sys.p, st);
-    else
-        k_trsv<false><<<trsv_grid(h, T), kTrsvThreads, 0, s>>>(d, rhs, out, ticket, P->ctl.p + 1,
-                                                                P->row_sys.p, st);
+    TriDev d = tri_dev(P, T, f32);
+    const int g = trsv_grid(h, T);
+    int* fl = P->ctl.p + 1;
+    if (f32) {
+        if (batched) k_trsv<true, float><<<g, kTrsvThreads, 0, s>>>(d, rhs, out, ticket, fl, P->row_sys.p, st);
+        else k_trsv<false, float><<<g, kTrsvThreads, 0, s>>>(d, rhs, out, ticket, fl, P->row_sys.p, st);
+    } else {
+        if (batched) k_trsv<true, double><<<g, kTrsvThreads, 0, s>>>(d, rhs, out, ticket, fl, P->row_sys.p, st);
+        else k_trsv<false, double><<<g, kTrsvThreads, 0, s>>>(d, rhs, out, ticket, fl, P->row_sys.p, st);
+    }
 }
 
 npcg_status ensure_pcg_workspace(Handle* h, Pattern* P) {
@@ -491,6 +514,11 @@ npcg_status ensure_pcg_workspace(Handle* h, Pattern* P) {
     }
     NPCG_CUDA(h, P->st.ensure(P->nsys));
     NPCG_CUDA(h, P->stats_dev.ensure(P->nsys));
+    if (P->cfwd.built) {
+        NPCG_CUDA(h, P->r_cf.ensure(P->n + 2));
+        NPCG_CUDA(h, P->y_cb.ensure(P->n + 2));
+        NPCG_CUDA(h, P->yglob.ensure(P->n));
+    }
     return NPCG_OK;
 }
 
@@ -513,7 +541,21 @@ PcgArgs pcg_args(Pattern* P, int precond) {
     a.w = P->w.p;
     a.b = P->b.p;
     a.precond = precond;
+    const bool cta = P->trsv_mode == kTrsvCta && precond >= NPCG_PREC_LLT;
+    a.rperm = cta ? P->r_cf.p : nullptr;
+    a.cposf = cta ? P->cfwd.cpos.p : nullptr;
     return a;
+}
+
+// z = L^-T L^-1 r with the tuned triangular-solve design
+void apply_llt(Handle* h, cudaStream_t s, Pattern* P, bool batched, bool f32) {
+    if (P->trsv_mode == kTrsvCta) {
+        cta_trsv_launch(h, s, P, P->cfwd, P->r_cf.p, nullptr, P->y_cb.p, P->st.p, f32);
+        cta_trsv_launch(h, s, P, P->cbwd, P->y_cb.p, P->z.p, nullptr, P->st.p, f32);
+    } else {
+        launch_trsv(h, s, P, 0, P->r.p, P->y.p, P->ctl.p + 2, batched, P->st.p, f32);
+        launch_trsv(h, s, P, 1, P->y.p, P->z.p, P->ctl.p + 3, batched, P->st.p, f32);
+    }
 }
 
 // one PCG iteration (Algorithm 1 loop body) on the stream
@@ -522,15 +564,15 @@ void enqueue_iteration(Handle* h, cudaStream_t s, Pattern* P, const PcgArgs& a, 
     const bool batched = P->nsys > 1;
     k_spmv_p<<<P->nchunks, kChunkThreads, 0, s>>>(a, p_old, p_new);
     k_update<<<P->nchunks, kChunkThreads, 0, s>>>(a, p_new);
-    if (a.precond == NPCG_PREC_LLT) {
-        launch_trsv(h, s, P, 0, P->r.p, P->y.p, P->ctl.p + 2, batched, P->st.p);
-        launch_trsv(h, s, P, 1, P->y.p, P->z.p, P->ctl.p + 3, batched, P->st.p);
+    if (a.precond >= NPCG_PREC_LLT) {
+        apply_llt(h, s, P, batched, a.precond == NPCG_PREC_LLT32);
         k_dot_rz<<<P->nchunks, kChunkThreads, 0, s>>>(a, 0);
     }
 }
 
 npcg_status build_graph(Handle* h, Pattern* P, int precond) {
-    if (P->graph[precond]) return NPCG_OK;
+    if (P->graph[precond] && P->graph_mode[precond] == P->trsv_mode) return NPCG_OK;
+    if (P->graph[precond]) { cudaGraphExecDestroy(P->graph[precond]); P->graph[precond] = nullptr; }
     PcgArgs a = pcg_args(P, precond);
     cudaGraph_t g = nullptr;
     NPCG_CUDA(h, cudaGraphCreate(&g, 0));
@@ -563,42 +605,60 @@ npcg_status build_graph(Handle* h, Pattern* P, int precond) {
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
     P->graph[precond] = ex;
+    P->graph_mode[precond] = P->trsv_mode;
     return NPCG_OK;
 }
 
 }  // namespace
 
 npcg_status factor_load(Handle* h, Pattern* P, const double* L_val) {
+    if (P->cfwd.built) {
+        NPCG_TRY(cta_factor_load(h, &P->cfwd, L_val));
+        NPCG_TRY(cta_factor_load(h, &P->cbwd, L_val));
+    }
     int blocks = h->num_sms * 4;
-    k_load_factor<<<blocks, 256, 0, h->stream>>>(P->fwd.slots, P->fwd.src.p, L_val, P->fwd.val.p, P->n,
-                                                 P->fwd.diag_src.p, P->fwd.diag.p);
-    k_load_factor<<<blocks, 256, 0, h->stream>>>(P->bwd.slots, P->bwd.src.p, L_val, P->bwd.val.p, P->n,
-                                                 P->bwd.diag_src.p, P->bwd.diag.p);
+    for (TriLayout* T : {&P->fwd, &P->bwd})
+        k_load_factor<<<blocks, 256, 0, h->stream>>>(T->slots, T->src.p, L_val, T->val.p, T->val32.p, P->n,
+                                                     T->diag_src.p, T->dinv.p, T->dinv32.p);
     NPCG_CUDA(h, cudaGetLastError());
     return NPCG_OK;
 }
 
 npcg_status sptrsv_run(Handle* h, Pattern* P, int transpose, const double* r, double* y,
                        const int32_t*) {
-    k_fill_sentinel<<<h->num_sms * 4, 256, 0, h->stream>>>(P->n, y);
     NPCG_CUDA(h, cudaMemsetAsync(P->ctl.p + 1, 0, 3 * sizeof(int), h->stream));
-    launch_trsv(h, h->stream, P, transpose, r, y, P->ctl.p + 2 + (transpose ? 1 : 0), false, nullptr);
+    if (P->trsv_mode == kTrsvCta) {
+        NPCG_TRY(ensure_pcg_workspace(h, P));
+        const CtaLayout& C = transpose ? P->cbwd : P->cfwd;
+        NPCG_TRY(cta_gather(h, h->stream, C, P->n, r, P->r_cf.p));
+        return cta_trsv_launch(h, h->stream, P, C, P->r_cf.p, y, nullptr, nullptr, false);
+    }
+    k_fill_sentinel<<<h->num_sms * 4, 256, 0, h->stream>>>(P->n, y);
+    launch_trsv(h, h->stream, P, transpose, r, y, P->ctl.p + 2 + (transpose ? 1 : 0), false, nullptr, false);
     NPCG_CUDA(h, cudaGetLastError());
     return NPCG_OK;
 }
 
 npcg_status sptrsv_timed_run(Handle* h, Pattern* P, int transpose, const double* r, double* y, int reps,
-                             double* ms_per_launch) {
+                             double* ms_per_launch, bool f32) {
+    NPCG_TRY(ensure_pcg_workspace(h, P));
     cudaEvent_t e0, e1;
     NPCG_CUDA(h, cudaEventCreate(&e0));
     NPCG_CUDA(h, cudaEventCreate(&e1));
     double total = 0.0;
     npcg_status st = NPCG_OK;
     for (int k = 0; k < reps && st == NPCG_OK; ++k) {
-        k_fill_sentinel<<<h->num_sms * 4, 256, 0, h->stream>>>(P->n, y);
         cudaMemsetAsync(P->ctl.p + 1, 0, 3 * sizeof(int), h->stream);
-        cudaEventRecord(e0, h->stream);
-        launch_trsv(h, h->stream, P, transpose, r, y, P->ctl.p + 2 + (transpose ? 1 : 0), false, nullptr);
+        if (P->trsv_mode == kTrsvCta) {
+            const CtaLayout& C = transpose ? P->cbwd : P->cfwd;
+            cta_gather(h, h->stream, C, P->n, r, P->r_cf.p);
+            cudaEventRecord(e0, h->stream);
+            cta_trsv_launch(h, h->stream, P, C, P->r_cf.p, y, nullptr, nullptr, f32);
+        } else {
+            k_fill_sentinel<<<h->num_sms * 4, 256, 0, h->stream>>>(P->n, y);
+            cudaEventRecord(e0, h->stream);
+            launch_trsv(h, h->stream, P, transpose, r, y, P->ctl.p + 2 + (transpose ? 1 : 0), false, nullptr, f32);
+        }
         cudaEventRecord(e1, h->stream);
         cudaError_t e = cudaEventSynchronize(e1);
         if (e != cudaSuccess) { st = cuda_fail(h, e, "trsv timing"); break; }
@@ -616,6 +676,50 @@ npcg_status sptrsv_timed_run(Handle* h, Pattern* P, int transpose, const double*
     return NPCG_OK;
 }
 
+namespace {
+__global__ void k_fill_value(int64_t n, double* x, double v) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = v;
+}
+}  // namespace
+
+// Times the forward + backward solve in both designs on this pattern (with a
+// placeholder factor: timing depends on the structure only) and keeps the
+// faster.  Runs once, at analysis.
+npcg_status trsv_autotune(Handle* h, Pattern* P) {
+    if (!P->cfwd.built || cta_stages(P->cfwd) < 2 || cta_stages(P->cbwd) < 2) {
+        P->trsv_mode = kTrsvSyncFree;
+        return NPCG_OK;
+    }
+    NPCG_TRY(ensure_pcg_workspace(h, P));
+    DevBuf<double> L, r, y;
+    NPCG_CUDA(h, L.alloc(P->nnzL));
+    NPCG_CUDA(h, r.alloc(P->n));
+    NPCG_CUDA(h, y.alloc(P->n));
+    int blocks = std::max(1, std::min(ceil_div(P->n, 256), h->num_sms * 8));
+    k_fill_value<<<blocks, 256, 0, h->stream>>>(P->nnzL, L.p, 1.0);
+    k_fill_value<<<blocks, 256, 0, h->stream>>>(P->n, r.p, 1.0);
+    NPCG_CUDA(h, cudaGetLastError());
+    // all entries 1: a well-defined solve of the same structure (values do not
+    // change the timing)
+    NPCG_TRY(factor_load(h, P, L.p));
+    const int modes[2] = {kTrsvSyncFree, kTrsvCta};
+    for (int m = 0; m < 2; ++m) {
+        P->trsv_mode = modes[m];
+        double best = 1e30;
+        for (int rep = 0; rep < 3; ++rep) {
+            double f = 0.0, b = 0.0;
+            NPCG_TRY(sptrsv_timed_run(h, P, 0, r.p, y.p, 1, &f, true));
+            NPCG_TRY(sptrsv_timed_run(h, P, 1, r.p, y.p, 1, &b, true));
+            best = std::min(best, f + b);
+        }
+        P->tune_ms[m] = (float)best;
+    }
+    P->trsv_mode = P->tune_ms[1] < P->tune_ms[0] ? kTrsvCta : kTrsvSyncFree;
+    return NPCG_OK;
+}
+
 npcg_status spmv_run(Handle* h, Pattern* P, const double* A_val, const double* x, double* y) {
     int blocks = std::min(ceil_div(P->n * 8, 256), h->num_sms * 8);
     k_spmv_plain<<<blocks, 256, 0, h->stream>>>(P->n, P->rp.p, P->ci.p, A_val, x, y);
@@ -626,8 +730,8 @@ npcg_status spmv_run(Handle* h, Pattern* P, const double* A_val, const double* x
 npcg_status pcg_run(Handle* h, Pattern* P, const double* A_val, const double* b, double* x,
                     int precond, const double* L_val, double rtol, int max_iter,
                     npcg_solve_stats* stats) {
-    if (precond < 0 || precond > 2) return set_error(h, NPCG_EINVAL, "unknown preconditioner");
-    if (precond == NPCG_PREC_LLT && !L_val) return set_error(h, NPCG_EINVAL, "L_val required for PREC_LLT");
+    if (precond < 0 || precond > NPCG_PREC_LLT32) return set_error(h, NPCG_EINVAL, "unknown preconditioner");
+    if (precond >= NPCG_PREC_LLT && !L_val) return set_error(h, NPCG_EINVAL, "L_val required for PREC_LLT");
     if (!(rtol >= 0.0)) return set_error(h, NPCG_EINVAL, "rtol must be >= 0");
     if (max_iter < 0) return set_error(h, NPCG_EINVAL, "max_iter must be >= 0");
     NPCG_TRY(ensure_pcg_workspace(h, P));
@@ -638,7 +742,7 @@ npcg_status pcg_run(Handle* h, Pattern* P, const double* A_val, const double* b,
         NPCG_CUDA(h, cudaMemcpyAsync(P->b.p, b, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
     if (x != P->x.p)
         NPCG_CUDA(h, cudaMemcpyAsync(P->x.p, x, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
-    if (precond == NPCG_PREC_LLT) NPCG_TRY(factor_load(h, P, L_val));
+    if (precond >= NPCG_PREC_LLT) NPCG_TRY(factor_load(h, P, L_val));
     {
         // ctl: n_active, flags, tickets, loop trips, trip bound (2 iterations per trip)
         const int init[6] = {0, 0, 0, 0, 0, max_iter / 2 + 2};
@@ -646,9 +750,8 @@ npcg_status pcg_run(Handle* h, Pattern* P, const double* A_val, const double* b,
     }
     PcgArgs a = pcg_args(P, precond);
     k_init<<<P->nchunks, kChunkThreads, 0, h->stream>>>(a, rtol, max_iter, P->p0.p, P->p1.p);
-    if (precond == NPCG_PREC_LLT) {
-        launch_trsv(h, h->stream, P, 0, P->r.p, P->y.p, P->ctl.p + 2, P->nsys > 1, P->st.p);
-        launch_trsv(h, h->stream, P, 1, P->y.p, P->z.p, P->ctl.p + 3, P->nsys > 1, P->st.p);
+    if (precond >= NPCG_PREC_LLT) {
+        apply_llt(h, h->stream, P, P->nsys > 1, precond == NPCG_PREC_LLT32);
     }
     k_dot_rz<<<P->nchunks, kChunkThreads, 0, h->stream>>>(a, 1);
     NPCG_CUDA(h, cudaGetLastError());

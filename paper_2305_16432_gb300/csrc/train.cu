@@ -1,18 +1,557 @@
-// Training: the loss Eq. (loss_Ab) with its hand-written adjoint through the
-// graph network, and Adam (App. A.4).
+// Training: the loss Eq. (loss_Ab),
+//   loss = mean over pairs p and systems s of || L L^T x_p - b_p ||^2,
+// with each pair's L from its own network forward (the node input is b_p,
+// Sec. 4.1), and its hand-written adjoint back to the network weights; Adam
+// (App. A.4) updates the FP32 master weights.
+//
+// Adjoint of the loss in L (y = L^T x, u = L y, r = u - b, w = L^T r):
+//   d loss / d L_ij = c (r_i y_j + x_i w_j),  c = 2 / (npairs nsys),
+// then through L_ij = sqrt(s) (s_ij + s_ji)/2, L_ii = sqrt(s) softplus(s_ii),
+// the decoder, the message-passing layers in reverse, and the encoders.
+// Every MLP backward recomputes its activations per tile from the layer
+// input (kept in a feature tape), writes the per-layer output gradients and
+// activations, and the weight gradients are reduced from those by a split
+// reduction kernel.  FP32 throughout the network; the loss part is FP64.
+#include <algorithm>
+#include <vector>
+
 #include "gnn_common.cuh"
 
 namespace npcg {
 
 namespace {
 
+// ------------------------------------------------------------ loss in L (FP64)
+// y_j = sum_i L_ij x_i over column j of L = entries (j, c), c >= j, of row j of A
+__global__ void k_lt_mv(int64_t n, const int32_t* rp, const int32_t* ci, const int32_t* mirror,
+                        const int32_t* a2l, const double* Lv, const double* x, double* y) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int k = rp[j]; k < rp[j + 1]; ++k) {
+            const int c = ci[k];
+            if (c >= j) s = fma(Lv[a2l[mirror[k]]], x[c], s);
+        }
+        y[j] = s;
+    }
+}
+
+// u = L y, r = u - b, per-system sum of r^2
+__global__ void k_l_mv_res(int64_t n, const int32_t* Lrp, const int32_t* Lci, const double* Lv,
+                           const double* y, const double* b, const int32_t* row_sys, double* r,
+                           double* loss_sys) {
+    // warp-uniform loop so the whole warp takes part in the reduction
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) - lane;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = w0; base < n; base += stride) {
+        const int64_t i = base + lane;
+        const bool valid = i < n;
+        double v = 0.0;
+        int sys = row_sys[base];
+        if (valid) {
+            double u = 0.0;
+            for (int q = Lrp[i]; q < Lrp[i + 1]; ++q) u = fma(Lv[q], y[Lci[q]], u);
+            const double ri = u - b[i];
+            r[i] = ri;
+            v = ri * ri;
+            sys = row_sys[i];
+        }
+        // one atomic per warp when its rows share a system, else one per row
+        if (__all_sync(0xffffffffu, sys == __shfl_sync(0xffffffffu, sys, 0))) {
+            for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) atomicAdd(&loss_sys[sys], v);
+        } else if (valid) {
+            atomicAdd(&loss_sys[sys], v);
+        }
+    }
+}
+
+// dL_q = c (r_i y_j + x_i w_j) for q = (i, j)
+__global__ void k_dL(int64_t nnzL, const int32_t* l2a, const int32_t* erow, const int32_t* ci, double c,
+                     const double* r, const double* y, const double* x, const double* w, double* dL) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nnzL;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int ka = l2a[q];
+        const int i = erow[ka], j = ci[ka];
+        dL[q] = c * (r[i] * y[j] + x[i] * w[j]);
+    }
+}
+
+// d loss / d s_k for every A entry k = (i, j): one L entry feeds each
+__global__ void k_dS(int64_t nnz, const int32_t* erow, const int32_t* ci, const int32_t* mirror,
+                     const int32_t* a2l, const int32_t* row_sys, const double* sc, const float* S,
+                     const double* dL, float* dS) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int i = erow[k], j = ci[k];
+        const double rs = sqrt(sc[2 * row_sys[i]]);
+        double g;
+        if (i == j) g = rs * (1.0 / (1.0 + exp(-(double)S[k]))) * dL[a2l[k]];
+        else if (i > j) g = rs * 0.5 * dL[a2l[k]];
+        else g = rs * 0.5 * dL[a2l[mirror[k]]];
+        dS[k] = (float)g;
+    }
+}
+
+// ------------------------------------------------------------ MLP backward
+struct MlpBwdArgs {
+    MlpArgs f;                        // forward gather (rows, weights, depth, inputs)
+    const float* gout;                // upstream gradient [rows x OUT]
+    float* tapeA[kMaxDepth + 1];      // [l] activations A_l (input of Linear l), l = 1..depth
+    float* tapeG[kMaxDepth + 1];      // [l] gradient of Linear l's output, l = 0..depth-1
+    float* dx[3];                     // input-gradient segments (H wide each)
+};
+
+// acc[i][j] = sum_k A[(r0+i)*lda + k] * B[k*ldb_k + (c0 + o0 + j)*ldb_n]
+template <int H>
+__device__ __forceinline__ void mm_rows(const float* A, int lda, const float* B, int ldb_k, int ldb_n, int K,
+                                        int c0, float (&acc)[4][4]) {
+    const int to = threadIdx.x % Tile<H>::TO, tr = threadIdx.x / Tile<H>::TO;
+    const int r0 = tr * 4, o0 = c0 + to * 4;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+    for (int k = 0; k < K; ++k) {
+        float a[4], bb[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = A[(r0 + i) * lda + k];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) bb[j] = B[k * ldb_k + (o0 + j) * ldb_n];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], bb[j], acc[i][j]);
+    }
+}
+
+__host__ __device__ constexpr int bwd_ldw(int in) { return in + 1; }
+
+inline size_t bwd_smem_floats(int mode, int H, int depth) {
+    const int in = mode_in(mode, H), out = mode_out(mode, H), R = 4096 / H;
+    size_t w = (size_t)H * bwd_ldw(in) + H + (size_t)(depth - 1) * (H * bwd_ldw(H) + H) +
+               (size_t)out * bwd_ldw(H) + out;
+    w = (w + 3) & ~size_t(3);
+    return w + (size_t)R * (in + 1) + (size_t)depth * R * (H + 1) + 2 * (size_t)R * (H + 1) + 4;
+}
+
+template <int H, int MODE>
+__global__ void __launch_bounds__(256) k_mlp_bwd(MlpBwdArgs a) {
+    extern __shared__ __align__(16) float sm[];
+    constexpr int R = Tile<H>::R;
+    constexpr int IN = mode_in(MODE, H);
+    constexpr int OUT = mode_out(MODE, H);
+    const int depth = a.f.depth;
+    // weights row-major with padded rows (ld = in + 1), biases after each
+    float* Wl[kMaxDepth + 1];
+    float* bl[kMaxDepth + 1];
+    {
+        float* dst = sm;
+        const float* src = a.f.w;
+        for (int l = 0; l <= depth; ++l) {
+            const int fi = l == 0 ? IN : H, fo = l == depth ? OUT : H, ld = bwd_ldw(fi);
+            for (int t = threadIdx.x; t < fi * fo; t += blockDim.x) dst[(t / fi) * ld + t % fi] = src[t];
+            for (int t = threadIdx.x; t < fo; t += blockDim.x) dst[fo * ld + t] = src[fi * fo + t];
+            Wl[l] = dst;
+            bl[l] = dst + fo * ld;
+            dst += fo * ld + fo;
+            src += fi * fo + fo;
+        }
+    }
+    size_t wfl = (size_t)H * bwd_ldw(IN) + H + (size_t)(depth - 1) * (H * bwd_ldw(H) + H) +
+                 (size_t)OUT * bwd_ldw(H) + OUT;
+    wfl = (wfl + 3) & ~size_t(3);
+    float* X = sm + wfl;
+    float* Ab = X + R * (IN + 1);                 // depth buffers [R][H+1]
+    float* G0 = Ab + (size_t)depth * R * (H + 1);
+    float* G1 = G0 + R * (H + 1);
+    __syncthreads();
+    const int to = threadIdx.x % Tile<H>::TO, tr = threadIdx.x / Tile<H>::TO;
+    const int64_t ntiles = (a.f.nrows + R - 1) / R;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t row0 = tile * R;
+        gather_tile<H, MODE>(a.f, row0, X);
+        __syncthreads();
+        // forward recompute of the hidden activations A_1..A_depth
+        const float* in = X;
+        int ldin = IN + 1, kin = IN;
+        for (int l = 0; l < depth; ++l) {
+            float acc[4][4];
+            mm_rows<H>(in, ldin, Wl[l], 1, bwd_ldw(kin), kin, 0, acc);
+            float* A = Ab + (size_t)l * R * (H + 1);
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int r = tr * 4 + i, o = to * 4 + j;
+                    const float v = fmaxf(acc[i][j] + bl[l][o], 0.0f);
+                    A[r * (H + 1) + o] = v;
+                    if (row0 + r < a.f.nrows) a.tapeA[l + 1][(row0 + r) * H + o] = v;
+                }
+            __syncthreads();
+            in = A;
+            ldin = H + 1;
+            kin = H;
+        }
+        // upstream gradient of the last Linear
+        for (int t = threadIdx.x; t < R * OUT; t += blockDim.x) {
+            const int r = t / OUT, o = t % OUT;
+            G0[r * (H + 1) + o] = row0 + r < a.f.nrows ? a.gout[(row0 + r) * OUT + o] : 0.0f;
+        }
+        __syncthreads();
+        float* G = G0;
+        float* Gn = G1;
+        for (int l = depth; l >= 1; --l) {
+            // gradient at A_l: G (R x out_l) . W_l (out_l x H), masked by A_l > 0
+            const int ol = l == depth ? OUT : H;
+            float acc[4][4];
+            mm_rows<H>(G, H + 1, Wl[l], bwd_ldw(H), 1, ol, 0, acc);
+            const float* A = Ab + (size_t)(l - 1) * R * (H + 1);
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int r = tr * 4 + i, o = to * 4 + j;
+                    const float v = A[r * (H + 1) + o] > 0.0f ? acc[i][j] : 0.0f;
+                    Gn[r * (H + 1) + o] = v;
+                    if (row0 + r < a.f.nrows) a.tapeG[l - 1][(row0 + r) * H + o] = v;
+                }
+            __syncthreads();
+            float* t = G; G = Gn; Gn = t;
+        }
+        // gradient of the MLP input: G_0 (R x H) . W_0 (H x IN), by H-wide segments
+        if (MODE != MODE_ENC_NODE && MODE != MODE_ENC_EDGE) {
+            for (int seg = 0; seg < IN / H; ++seg) {
+                float acc[4][4];
+                mm_rows<H>(G, H + 1, Wl[0], bwd_ldw(IN), 1, H, seg * H, acc);
+                float* dst = a.dx[seg];
+                if (!dst) continue;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int64_t row = row0 + tr * 4 + i;
+                    if (row < a.f.nrows)
+                        *reinterpret_cast<float4*>(dst + row * H + to * 4) =
+                            make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <int H, int MODE>
+npcg_status launch_bwd_mode(Handle* h, const MlpBwdArgs& a) {
+    if (a.f.nrows == 0) return NPCG_OK;
+    const size_t smem = bwd_smem_floats(MODE, H, a.f.depth) * sizeof(float);
+    if (smem > 227 * 1024) return set_error(h, NPCG_EINVAL, "MLP too deep for the backward kernel");
+    NPCG_CUDA(h, cudaFuncSetAttribute(k_mlp_bwd<H, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = (int)std::max<size_t>(1, std::min<size_t>(8, (227 * 1024) / (smem + 1024)));
+    const int64_t ntiles = (a.f.nrows + Tile<H>::R - 1) / Tile<H>::R;
+    int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)h->num_sms * per_sm));
+    k_mlp_bwd<H, MODE><<<grid, 256, smem, h->stream>>>(a);
+    NPCG_CUDA(h, cudaGetLastError());
+    return NPCG_OK;
+}
+
+template <int H>
+npcg_status launch_bwd(Handle* h, int mode, const MlpBwdArgs& a) {
+    switch (mode) {
+        case MODE_ENC_NODE: return launch_bwd_mode<H, MODE_ENC_NODE>(h, a);
+        case MODE_ENC_EDGE: return launch_bwd_mode<H, MODE_ENC_EDGE>(h, a);
+        case MODE_NODE: return launch_bwd_mode<H, MODE_NODE>(h, a);
+        case MODE_EDGE: return launch_bwd_mode<H, MODE_EDGE>(h, a);
+        default: return launch_bwd_mode<H, MODE_DEC>(h, a);
+    }
+}
+
+// ------------------------------------------------------------ weight gradients
+// dW[o][q] += sum_k G[k][o] X[k][q], db[o] += sum_k G[k][o]; X's columns come
+// in segments, each a row-gather of a [rows x width] array (idx may be null).
+struct WSeg {
+    const float* ptr;
+    const int32_t* idx;
+    int width;
+};
+struct WgradArgs {
+    int64_t M;
+    const float* G;
+    int O;
+    WSeg seg[3];
+    int nseg;
+    int I;
+    float* dW;      // [O][I] then db[O]
+};
+
+constexpr int kWgRows = 32;
+constexpr int kWgMaxEntries = 64 * 192;
+constexpr int kWgPer = kWgMaxEntries / 256;
+
+__global__ void __launch_bounds__(256) k_wgrad(WgradArgs a) {
+    __shared__ float Gs[kWgRows][64 + 1];
+    __shared__ float Xs[kWgRows][192 + 1];
+    float acc[kWgPer];
+    float bacc = 0.0f;
+#pragma unroll
+    for (int m = 0; m < kWgPer; ++m) acc[m] = 0.0f;
+    const int64_t per = (a.M + gridDim.x - 1) / gridDim.x;
+    const int64_t m0 = blockIdx.x * per, m1 = (a.M < m0 + per ? a.M : m0 + per);
+    const int E = a.O * a.I;
+    for (int64_t t0 = m0; t0 < m1; t0 += kWgRows) {
+        const int rows = (int)(m1 - t0 < kWgRows ? m1 - t0 : kWgRows);
+        for (int t = threadIdx.x; t < kWgRows * a.O; t += blockDim.x) {
+            const int r = t / a.O, o = t % a.O;
+            Gs[r][o] = r < rows ? a.G[(t0 + r) * a.O + o] : 0.0f;
+        }
+        int c0 = 0;
+        for (int s = 0; s < a.nseg; ++s) {
+            const WSeg sg = a.seg[s];
+            for (int t = threadIdx.x; t < kWgRows * sg.width; t += blockDim.x) {
+                const int r = t / sg.width, q = t % sg.width;
+                float v = 0.0f;
+                if (r < rows) {
+                    const int64_t src = sg.idx ? sg.idx[t0 + r] : t0 + r;
+                    v = sg.ptr[src * sg.width + q];
+                }
+                Xs[r][c0 + q] = v;
+            }
+            c0 += sg.width;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int m = 0; m < kWgPer; ++m) {
+            const int e = threadIdx.x + 256 * m;
+            if (e < E) {
+                const int o = e / a.I, q = e % a.I;
+                float s = acc[m];
+                for (int r = 0; r < rows; ++r) s = fmaf(Gs[r][o], Xs[r][q], s);
+                acc[m] = s;
+            }
+        }
+        if (threadIdx.x < a.O)
+            for (int r = 0; r < rows; ++r) bacc += Gs[r][threadIdx.x];
+        __syncthreads();
+    }
+#pragma unroll
+    for (int m = 0; m < kWgPer; ++m) {
+        const int e = threadIdx.x + 256 * m;
+        if (e < E && acc[m] != 0.0f) atomicAdd(&a.dW[e], acc[m]);
+    }
+    if (threadIdx.x < a.O && bacc != 0.0f) atomicAdd(&a.dW[E + threadIdx.x], bacc);
+}
+
+npcg_status wgrad(Handle* h, const WgradArgs& a) {
+    if (a.M == 0) return NPCG_OK;
+    if (a.O > 64 || a.I > 192 || a.O * a.I > kWgMaxEntries)
+        return set_error(h, NPCG_EINVAL, "weight-gradient shape out of range");
+    int grid = (int)std::max<int64_t>(1, std::min<int64_t>((a.M + kWgRows - 1) / kWgRows, (int64_t)h->num_sms * 4));
+    k_wgrad<<<grid, 256, 0, h->stream>>>(a);
+    NPCG_CUDA(h, cudaGetLastError());
+    return NPCG_OK;
+}
+
+// ------------------------------------------------------------ node / edge adjoint glue
+// dV[i] += sum_{k in row i} Gr[k] + Gc[mirror[k]]   (edge MLP's v_i and v_j inputs)
+__global__ void k_node_from_edges(int64_t n, int H, const int32_t* rp, const int32_t* mirror,
+                                  const float* Gr, const float* Gc, float* dV) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n * H;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / H;
+        const int q = (int)(t % H);
+        float s = dV[t];
+        for (int k = rp[i]; k < rp[i + 1]; ++k) s += Gr[(int64_t)k * H + q] + Gc[(int64_t)mirror[k] * H + q];
+        dV[t] = s;
+    }
+}
+
+// aggregation agg_i = sum_j e_ij (.) v_j:
+//   dE[k] += dAgg[row_k] (.) V[col_k];  dV[j] += sum_{k in row j} dAgg[col_k] (.) E[mirror k]
+__global__ void k_agg_bwd_edges(int64_t nnz, int H, const int32_t* erow, const int32_t* ci,
+                                const float* dAgg, const float* V, float* dE) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nnz * H;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = t / H;
+        const int q = (int)(t % H);
+        dE[t] += dAgg[(int64_t)erow[k] * H + q] * V[(int64_t)ci[k] * H + q];
+    }
+}
+
+__global__ void k_agg_bwd_nodes(int64_t n, int H, const int32_t* rp, const int32_t* ci,
+                                const int32_t* mirror, const float* dAgg, const float* E, float* dV) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n * H;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = t / H;
+        const int q = (int)(t % H);
+        float s = dV[t];
+        for (int k = rp[j]; k < rp[j + 1]; ++k)
+            s = fmaf(dAgg[(int64_t)ci[k] * H + q], E[(int64_t)mirror[k] * H + q], s);
+        dV[t] = s;
+    }
+}
+
+__global__ void k_enc_inputs(int64_t n, int64_t nnz, const double* b, const double* av, const int32_t* erow,
+                             const int32_t* row_sys, const double* sc, float* xv, float* xe) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nnz;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (i < n) xv[i] = (float)(b[i] / sc[2 * row_sys[i] + 1]);
+        xe[i] = (float)(av[i] / sc[2 * row_sys[erow[i]]]);
+    }
+}
+
+// ------------------------------------------------------------ driver
+struct TrainBufs {
+    std::vector<float*> V, E, AGG;
+    float *S, *dS, *dEc, *dEp, *dVc, *dVp, *Gr, *Gc, *dAgg, *xv, *xe;
+    float* tapeA[kMaxDepth + 1];
+    float* tapeG[kMaxDepth + 1];
+    double *Lv, *dL, *y, *r, *w, *loss_sys;
+};
+
+inline int grid1(Handle* h, int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)h->num_sms * 8)); }
+
+// weight gradient of one MLP (depth Linears + output layer) from its tapes
+npcg_status mlp_wgrad(Handle* h, int64_t M, int H, int in_w, int out_w, int depth, const float* gout,
+                      const TrainBufs& T, const WSeg* inseg, int nin, float* gw) {
+    // layers depth..1: input A_l, gradient G_l (G_depth = gout)
+    float* cur = gw;
+    std::vector<float*> lay(depth + 1);
+    for (int l = 0; l <= depth; ++l) {
+        lay[l] = cur;
+        const int fi = l == 0 ? in_w : H, fo = l == depth ? out_w : H;
+        cur += (int64_t)fi * fo + fo;
+    }
+    for (int l = depth; l >= 0; --l) {
+        WgradArgs a{};
+        a.M = M;
+        a.G = l == depth ? gout : T.tapeG[l];
+        a.O = l == depth ? out_w : H;
+        a.dW = lay[l];
+        if (l == 0) {
+            for (int s = 0; s < nin; ++s) a.seg[s] = inseg[s];
+            a.nseg = nin;
+            a.I = in_w;
+        } else {
+            a.seg[0] = WSeg{T.tapeA[l], nullptr, H};
+            a.nseg = 1;
+            a.I = H;
+        }
+        NPCG_TRY(wgrad(h, a));
+    }
+    return NPCG_OK;
+}
+
+template <int H>
+npcg_status train_pair(Handle* h, Pattern* P, const double* A_val, const double* x, const double* b,
+                       const npcg_gnn_config* cfg, const float* w, float* gw, TrainBufs& T, double c) {
+    const int l = cfg->l, lm = cfg->l_mp, nmp = cfg->n_mp;
+    const int64_t n = P->n, nnz = P->nnz, nnzL = P->nnzL;
+    const GnnOffsets off = gnn_offsets(H, l, lm, nmp);
+    double* sc = P->gnn.sc.p;
+    // ---- forward with tape
+    MlpArgs a = {};
+    a.rp = P->rp.p;
+    a.ci = P->ci.p;
+    a.erow = P->edge_row.p;
+    a.row_sys = P->row_sys.p;
+    a.sc = sc;
+    a.av = A_val;
+    a.b = b;
+    a.nrows = n; a.w = w + off.enc_v; a.depth = l; a.out = T.V[0];
+    NPCG_TRY(launch_mlp<H>(h, MODE_ENC_NODE, a));
+    a.nrows = nnz; a.w = w + off.enc_e; a.depth = l; a.out = T.E[0];
+    NPCG_TRY(launch_mlp<H>(h, MODE_ENC_EDGE, a));
+    for (int t = 0; t < nmp; ++t) {
+        a.nrows = n; a.w = w + off.node[t]; a.depth = lm; a.vin = T.V[t]; a.ein = T.E[t]; a.out = T.V[t + 1];
+        a.agg_out = T.AGG[t];
+        NPCG_TRY(launch_mlp<H>(h, MODE_NODE, a));
+        a.agg_out = nullptr;
+        a.nrows = nnz; a.w = w + off.edge[t]; a.depth = lm; a.vin = T.V[t + 1]; a.ein = T.E[t]; a.out = T.E[t + 1];
+        NPCG_TRY(launch_mlp<H>(h, MODE_EDGE, a));
+    }
+    a.nrows = nnz; a.w = w + off.dec; a.depth = l; a.ein = T.E[nmp]; a.out = T.S;
+    NPCG_TRY(launch_mlp<H>(h, MODE_DEC, a));
+    GnnBuffers gb{};
+    gb.s = T.S;
+    gb.sc = sc;
+    NPCG_TRY(gnn_assemble_L(h, P, gb, T.Lv));
+    // ---- loss and its adjoint in L
+    k_lt_mv<<<grid1(h, n), 256, 0, h->stream>>>(n, P->rp.p, P->ci.p, P->mirror.p, P->a2l.p, T.Lv, x, T.y);
+    k_l_mv_res<<<grid1(h, n), 256, 0, h->stream>>>(n, P->Lrp.p, P->Lci.p, T.Lv, T.y, b, P->row_sys.p, T.r,
+                                                  T.loss_sys);
+    k_lt_mv<<<grid1(h, n), 256, 0, h->stream>>>(n, P->rp.p, P->ci.p, P->mirror.p, P->a2l.p, T.Lv, T.r, T.w);
+    k_dL<<<grid1(h, nnzL), 256, 0, h->stream>>>(nnzL, P->l2a.p, P->edge_row.p, P->ci.p, c, T.r, T.y, x, T.w, T.dL);
+    k_dS<<<grid1(h, nnz), 256, 0, h->stream>>>(nnz, P->edge_row.p, P->ci.p, P->mirror.p, P->a2l.p, P->row_sys.p,
+                                              sc, T.S, T.dL, T.dS);
+    NPCG_CUDA(h, cudaGetLastError());
+    // ---- decoder
+    MlpBwdArgs bw{};
+    for (int k = 0; k <= kMaxDepth; ++k) { bw.tapeA[k] = T.tapeA[k]; bw.tapeG[k] = T.tapeG[k]; }
+    bw.f = a;
+    bw.f.nrows = nnz; bw.f.w = w + off.dec; bw.f.depth = l; bw.f.ein = T.E[nmp];
+    bw.gout = T.dS;
+    bw.dx[0] = T.dEc; bw.dx[1] = bw.dx[2] = nullptr;
+    NPCG_TRY(launch_bwd<H>(h, MODE_DEC, bw));
+    {
+        WSeg s0{T.E[nmp], nullptr, H};
+        NPCG_TRY(mlp_wgrad(h, nnz, H, H, 1, l, T.dS, T, &s0, 1, gw + off.dec));
+    }
+    NPCG_CUDA(h, cudaMemsetAsync(T.dVc, 0, (size_t)n * H * sizeof(float), h->stream));
+    for (int t = nmp - 1; t >= 0; --t) {
+        // edge update t: input [E_t | V_{t+1}(row) | V_{t+1}(col)], upstream dE_{t+1}
+        bw.f = a;
+        bw.f.nrows = nnz; bw.f.w = w + off.edge[t]; bw.f.depth = lm; bw.f.vin = T.V[t + 1]; bw.f.ein = T.E[t];
+        bw.gout = T.dEc;
+        bw.dx[0] = T.dEp; bw.dx[1] = T.Gr; bw.dx[2] = T.Gc;
+        NPCG_TRY(launch_bwd<H>(h, MODE_EDGE, bw));
+        {
+            WSeg s[3] = {{T.E[t], nullptr, H}, {T.V[t + 1], P->edge_row.p, H}, {T.V[t + 1], P->ci.p, H}};
+            NPCG_TRY(mlp_wgrad(h, nnz, H, 3 * H, H, lm, T.dEc, T, s, 3, gw + off.edge[t]));
+        }
+        k_node_from_edges<<<grid1(h, n * H), 256, 0, h->stream>>>(n, H, P->rp.p, P->mirror.p, T.Gr, T.Gc, T.dVc);
+        // node update t: input [V_t | agg_t], upstream dV_{t+1}
+        bw.f = a;
+        bw.f.nrows = n; bw.f.w = w + off.node[t]; bw.f.depth = lm; bw.f.vin = T.V[t]; bw.f.ein = T.E[t];
+        bw.gout = T.dVc;
+        bw.dx[0] = T.dVp; bw.dx[1] = T.dAgg; bw.dx[2] = nullptr;
+        NPCG_TRY(launch_bwd<H>(h, MODE_NODE, bw));
+        {
+            WSeg s[2] = {{T.V[t], nullptr, H}, {T.AGG[t], nullptr, H}};
+            NPCG_TRY(mlp_wgrad(h, n, H, 2 * H, H, lm, T.dVc, T, s, 2, gw + off.node[t]));
+        }
+        k_agg_bwd_edges<<<grid1(h, nnz * H), 256, 0, h->stream>>>(nnz, H, P->edge_row.p, P->ci.p, T.dAgg, T.V[t], T.dEp);
+        k_agg_bwd_nodes<<<grid1(h, n * H), 256, 0, h->stream>>>(n, H, P->rp.p, P->ci.p, P->mirror.p, T.dAgg, T.E[t], T.dVp);
+        NPCG_CUDA(h, cudaGetLastError());
+        std::swap(T.dEc, T.dEp);
+        std::swap(T.dVc, T.dVp);
+    }
+    // encoders: weight gradients only
+    k_enc_inputs<<<grid1(h, nnz), 256, 0, h->stream>>>(n, nnz, b, A_val, P->edge_row.p, P->row_sys.p, sc, T.xv, T.xe);
+    bw.f = a;
+    bw.f.nrows = n; bw.f.w = w + off.enc_v; bw.f.depth = l;
+    bw.gout = T.dVc;
+    bw.dx[0] = bw.dx[1] = bw.dx[2] = nullptr;
+    NPCG_TRY(launch_bwd<H>(h, MODE_ENC_NODE, bw));
+    {
+        WSeg s0{T.xv, nullptr, 1};
+        NPCG_TRY(mlp_wgrad(h, n, H, 1, H, l, T.dVc, T, &s0, 1, gw + off.enc_v));
+    }
+    bw.f.nrows = nnz; bw.f.w = w + off.enc_e;
+    bw.gout = T.dEc;
+    NPCG_TRY(launch_bwd<H>(h, MODE_ENC_EDGE, bw));
+    {
+        WSeg s0{T.xe, nullptr, 1};
+        NPCG_TRY(mlp_wgrad(h, nnz, H, 1, H, l, T.dEc, T, &s0, 1, gw + off.enc_e));
+    }
+    return NPCG_OK;
+}
+
 __global__ void k_adam(int64_t n, float* w, const float* g, float* m, float* v, float lr, float b1,
                        float b2, float eps, float c1, float c2) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        float gi = g[i];
-        float mi = fmaf(b1, m[i], (1.0f - b1) * gi);
-        float vi = fmaf(b2, v[i], (1.0f - b2) * gi * gi);
+        const float gi = g[i];
+        const float mi = fmaf(b1, m[i], (1.0f - b1) * gi);
+        const float vi = fmaf(b2, v[i], (1.0f - b2) * gi * gi);
         m[i] = mi;
         v[i] = vi;
         w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
@@ -21,19 +560,75 @@ __global__ void k_adam(int64_t n, float* w, const float* g, float* m, float* v, 
 
 }  // namespace
 
-npcg_status adam_run(Handle* h, int64_t n, float* w, const float* g, float* m, float* v, int t,
-                     float lr, float b1, float b2, float eps) {
-    if (n == 0) return NPCG_OK;
-    float c1 = (float)(1.0 - pow((double)b1, t)), c2 = (float)(1.0 - pow((double)b2, t));
-    int blocks = std::max(1, std::min(ceil_div(n, 256), h->num_sms * 8));
-    k_adam<<<blocks, 256, 0, h->stream>>>(n, w, g, m, v, lr, b1, b2, eps, c1, c2);
-    NPCG_CUDA(h, cudaGetLastError());
+npcg_status gnn_scales_run(Handle* h, Pattern* P, const double* A_val, const double* b, double* sc);
+
+npcg_status loss_grad_run(Handle* h, Pattern* P, const double* A_val, int npairs, const double* X,
+                          const double* B, const npcg_gnn_config* cfg, const float* w, double* loss_out,
+                          float* grad) {
+    NPCG_TRY(gnn_check_config(h, cfg));
+    if (cfg->precision != NPCG_FP32)
+        return set_error(h, NPCG_EINVAL, "the training adjoint runs in FP32 (precision NPCG_FP32)");
+    const int H = cfg->h, nmp = cfg->n_mp;
+    const int64_t n = P->n, nnz = P->nnz, nnzL = P->nnzL;
+    const int dmax = std::max(cfg->l, cfg->l_mp);
+    const GnnOffsets off = gnn_offsets(H, cfg->l, cfg->l_mp, nmp);
+    GnnStore& S = P->gnn;
+    const size_t fe = (size_t)nnz * H, fv = (size_t)n * H;
+    // tape: V_0..V_nmp, E_0..E_nmp, AGG_0..AGG_{nmp-1}; adjoint buffers
+    const size_t need = (size_t)(nmp + 1) * (fe + fv) + (size_t)std::max(nmp, 1) * fv + 4 * fe + 5 * fv +
+                        2 * (size_t)nnz + (size_t)(2 * dmax + 2) * std::max(fe, fv) + 2 * (size_t)nnz;
+    NPCG_CUDA(h, S.aux.ensure(need));
+    NPCG_CUDA(h, S.sc.ensure((size_t)2 * P->nsys));
+    NPCG_CUDA(h, S.Lv.ensure((size_t)nnzL));
+    NPCG_CUDA(h, S.dL.ensure((size_t)nnzL + 3 * (size_t)n + P->nsys));
+    TrainBufs T;
+    float* p = S.aux.p;
+    auto take = [&](size_t k) { float* r = p; p += k; return r; };
+    for (int t = 0; t <= nmp; ++t) T.V.push_back(take(fv));
+    for (int t = 0; t <= nmp; ++t) T.E.push_back(take(fe));
+    for (int t = 0; t < std::max(nmp, 1); ++t) T.AGG.push_back(take(fv));
+    T.dEc = take(fe); T.dEp = take(fe); T.Gr = take(fe); T.Gc = take(fe);
+    T.dVc = take(fv); T.dVp = take(fv); T.dAgg = take(fv); T.xv = take(fv); T.xe = take(nnz);
+    T.S = take(nnz); T.dS = take(nnz);
+    for (int k = 0; k <= kMaxDepth; ++k) { T.tapeA[k] = nullptr; T.tapeG[k] = nullptr; }
+    for (int k = 0; k <= dmax; ++k) { T.tapeA[k] = take(std::max(fe, fv)); T.tapeG[k] = take(std::max(fe, fv)); }
+    T.Lv = S.Lv.p;
+    T.dL = S.dL.p;
+    T.y = T.dL + nnzL;
+    T.r = T.y + n;
+    T.w = T.r + n;
+    T.loss_sys = T.w + n;
+    NPCG_CUDA(h, cudaMemsetAsync(grad, 0, off.total * sizeof(float), h->stream));
+    NPCG_CUDA(h, cudaMemsetAsync(T.loss_sys, 0, P->nsys * sizeof(double), h->stream));
+    const double c = 2.0 / ((double)npairs * (double)P->nsys);
+    for (int pp = 0; pp < npairs; ++pp) {
+        const double* x = X + (size_t)pp * n;
+        const double* b = B + (size_t)pp * n;
+        NPCG_TRY(gnn_scales_run(h, P, A_val, b, S.sc.p));
+        npcg_status st;
+        switch (H) {
+            case 16: st = train_pair<16>(h, P, A_val, x, b, cfg, w, grad, T, c); break;
+            case 32: st = train_pair<32>(h, P, A_val, x, b, cfg, w, grad, T, c); break;
+            default: st = train_pair<64>(h, P, A_val, x, b, cfg, w, grad, T, c); break;
+        }
+        if (st != NPCG_OK) return st;
+    }
+    std::vector<double> ls(P->nsys);
+    NPCG_CUDA(h, cudaMemcpyAsync(ls.data(), T.loss_sys, P->nsys * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    NPCG_CUDA(h, cudaStreamSynchronize(h->stream));
+    double tot = 0.0;
+    for (double v : ls) tot += v;
+    *loss_out = tot / ((double)npairs * (double)P->nsys);
     return NPCG_OK;
 }
 
-npcg_status loss_grad_run(Handle* h, Pattern*, const double*, int, const double*, const double*,
-                          const npcg_gnn_config*, const float*, double*, float*) {
-    return set_error(h, NPCG_EINVAL, "loss_and_grad is not available in this build");
+npcg_status adam_run(Handle* h, int64_t n, float* w, const float* g, float* m, float* v, int t,
+                     float lr, float b1, float b2, float eps) {
+    if (n == 0) return NPCG_OK;
+    const float c1 = (float)(1.0 - pow((double)b1, t)), c2 = (float)(1.0 - pow((double)b2, t));
+    k_adam<<<grid1(h, n), 256, 0, h->stream>>>(n, w, g, m, v, lr, b1, b2, eps, c1, c2);
+    NPCG_CUDA(h, cudaGetLastError());
+    return NPCG_OK;
 }
 
 npcg_status gnn_forward_bf16_run(Handle* h, Pattern*, const double*, const double*,

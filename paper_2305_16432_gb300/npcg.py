@@ -23,8 +23,9 @@ LIB_PATH = os.path.join(_HERE, "_build", "libnpcg.so")
 NPCG_OK, NPCG_EINVAL, NPCG_ENOMEM, NPCG_ECUDA, NPCG_ENOTSPD, NPCG_EBREAKDOWN, NPCG_EMAXITER, NPCG_ETIMEOUT = range(8)
 FD, FEM = 0, 1
 FP32, BF16 = 0, 1
-PREC_NONE, PREC_JACOBI, PREC_LLT = 0, 1, 2
+PREC_NONE, PREC_JACOBI, PREC_LLT, PREC_LLT32 = 0, 1, 2, 3
 METHOD_GNN, METHOD_IC0, METHOD_JACOBI, METHOD_CG = 0, 1, 2, 3
+TRSV_AUTO, TRSV_SYNCFREE, TRSV_LEVELSYNC = 0, 1, 2
 
 
 class NpcgError(RuntimeError):
@@ -41,7 +42,8 @@ class _Problem(C.Structure):
 
 class _Info(C.Structure):
     _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("nnz_L", C.c_int64), ("nsys", C.c_int32),
-                ("nlev_fwd", C.c_int32), ("nlev_bwd", C.c_int32)]
+                ("nlev_fwd", C.c_int32), ("nlev_bwd", C.c_int32), ("trsv_mode", C.c_int32),
+                ("tuned_ms_syncfree", C.c_float), ("tuned_ms_levelsync", C.c_float)]
 
 
 class _Cfg(C.Structure):
@@ -74,6 +76,7 @@ def lib():
                 "npcg_analyse": [vp, i64, i64, vp, vp, i32, vp, C.POINTER(vp)],
                 "npcg_pattern_free": [vp],
                 "npcg_pattern_get_info": [vp, C.POINTER(_Info)],
+                "npcg_pattern_set_trsv": [vp, i32],
                 "npcg_pattern_export": [vp, vp, vp, vp, vp, vp, vp, vp],
                 "npcg_gnn_nparams": [C.POINTER(_Cfg), C.POINTER(i64)],
                 "npcg_gnn_factor": [vp, vp, vp, vp, C.POINTER(_Cfg), vp, vp],
@@ -199,7 +202,17 @@ class Pattern:
         lib().npcg_pattern_get_info(p, C.byref(info))
         self.n, self.nnz, self.nnz_L = info.n, info.nnz, info.nnz_L
         self.nsys, self.nlev_fwd, self.nlev_bwd = info.nsys, info.nlev_fwd, info.nlev_bwd
+        self.trsv_mode = info.trsv_mode
+        self.tuned_ms = {"syncfree": info.tuned_ms_syncfree, "levelsync": info.tuned_ms_levelsync}
         self.sys_ptr = np.asarray(sys_ptr if sys_ptr is not None else [0, n], dtype=np.int64)
+
+    def set_trsv(self, mode):
+        """Force a triangular-solve design (TRSV_SYNCFREE / TRSV_LEVELSYNC) or
+        restore the tuned one (TRSV_AUTO)."""
+        self.h.check(lib().npcg_pattern_set_trsv(self.p, int(mode)))
+        info = _Info()
+        lib().npcg_pattern_get_info(self.p, C.byref(info))
+        self.trsv_mode = info.trsv_mode
 
     def export(self):
         dev = torch.device("cuda", self.h.device)

@@ -294,3 +294,69 @@ def test_fem256_full_size(N):
     xg, st = N.pcg_solve(P, v, _gpu(b), N.PREC_LLT, Lg, rtol=1e-6)
     assert abs(st[0]["iters"] - ito) <= 1
     assert np.linalg.norm(_np(xg) - xo) / np.linalg.norm(xo) <= 1e-8
+
+
+@pytest.mark.parametrize("mode", ["syncfree", "levelsync"])
+@pytest.mark.parametrize("name", ["poisson2d_32", "fem34", "fd3d_var"])
+def test_trsv_designs_parity(N, name, mode):
+    # both triangular-solve designs against the oracle, alone and inside PCG
+    Ao, (rp, ci, v) = _assemble_both(N, PROBLEMS[name])
+    P = N.analyse(rp, ci)
+    P.set_trsv(N.TRSV_SYNCFREE if mode == "syncfree" else N.TRSV_LEVELSYNC)
+    Lo, _ = O.ic0(Ao)
+    N.factor_load(P, _gpu(Lo.val))
+    r = np.random.default_rng(5).standard_normal(Ao.n)
+    assert _rel(_np(N.sptrsv(P, _gpu(r))), O.trsv_lower(Lo, r)) <= 1e-12
+    assert _rel(_np(N.sptrsv(P, _gpu(r), transpose=True)), O.trsv_upper(Lo, r)) <= 1e-12
+    b = I.rhs(Ao.n, 8)
+    xo, ito, _, _ = O.pcg(Ao, b, O.PREC_LLT, Lo, rtol=1e-8)
+    xg, st = N.pcg_solve(P, v, _gpu(b), N.PREC_LLT, _gpu(Lo.val), rtol=1e-8)
+    assert st[0]["status"] == 0 and abs(st[0]["iters"] - ito) <= 1
+    assert np.linalg.norm(_np(xg) - xo) / np.linalg.norm(xo) <= 1e-8
+
+
+@pytest.mark.parametrize("mode", ["syncfree", "levelsync"])
+def test_batched_trsv_designs(N, mode):
+    probs = [I.fem2d(26, sigma=1.0, seed=11), I.fd3d(7, 6, 5, sigma=1.0, seed=12), I.fd2d(17, 9, sigma=1.0, seed=13),
+             I.fem2d(12, sigma=1.0, seed=14)]
+    As, cis, vs, bs = [], [], [], []
+    off, sys_ptr = 0, [0]
+    for k, p in enumerate(probs):
+        Ao, (rp, ci, v) = _assemble_both(N, p)
+        As.append(Ao)
+        cis.append(_np(ci) + off)
+        vs.append(_np(v))
+        bs.append(I.rhs(Ao.n, 40 + k))
+        off += Ao.n
+        sys_ptr.append(off)
+    nnz_off = np.cumsum([0] + [a.nnz for a in As])
+    rp_cat = np.concatenate([a.row_ptr[:-1] + nnz_off[k] for k, a in enumerate(As)] + [[nnz_off[-1]]])
+    P = N.analyse(_gpu(rp_cat, torch.int32), _gpu(np.concatenate(cis), torch.int32), sys_ptr)
+    P.set_trsv(N.TRSV_SYNCFREE if mode == "syncfree" else N.TRSV_LEVELSYNC)
+    v_cat = _gpu(np.concatenate(vs))
+    Lg, _ = N.ic0_factor(P, v_cat)
+    x, st = N.pcg_solve(P, v_cat, _gpu(np.concatenate(bs)), N.PREC_LLT, Lg, rtol=1e-8)
+    xs = _np(x)
+    for k, Ao in enumerate(As):
+        xo, ito, _, _ = O.pcg(Ao, bs[k], O.PREC_LLT, O.ic0(Ao)[0], rtol=1e-8)
+        assert st[k]["status"] == 0 and abs(st[k]["iters"] - ito) <= 1
+        seg = xs[sys_ptr[k]:sys_ptr[k + 1]]
+        assert np.linalg.norm(seg - xo) / np.linalg.norm(xo) <= 1e-8
+
+
+@pytest.mark.parametrize("mode", ["syncfree", "levelsync"])
+@pytest.mark.parametrize("name", ["fem34", "fd3d_var"])
+def test_fp32_preconditioner_apply(N, name, mode):
+    # P = L' L'^T with L' = fl32(L), solves in FP32: the PCG recurrences stay
+    # FP64, so the solve still reaches the FP64 tolerance; the iteration count
+    # stays within 5 % of the FP64-preconditioned oracle
+    Ao, (rp, ci, v) = _assemble_both(N, PROBLEMS[name])
+    P = N.analyse(rp, ci)
+    P.set_trsv(N.TRSV_SYNCFREE if mode == "syncfree" else N.TRSV_LEVELSYNC)
+    Lo, _ = O.ic0(Ao)
+    b = I.rhs(Ao.n, 9)
+    xo, ito, _, _ = O.pcg(Ao, b, O.PREC_LLT, Lo, rtol=1e-8)
+    xg, st = N.pcg_solve(P, v, _gpu(b), N.PREC_LLT32, _gpu(Lo.val), rtol=1e-8)
+    assert st[0]["status"] == 0
+    assert abs(st[0]["iters"] - ito) <= max(1, int(np.ceil(0.05 * ito)))
+    assert np.linalg.norm(b - O.spmv(Ao, _np(xg))) / np.linalg.norm(b) <= 2e-8

@@ -1,0 +1,102 @@
+"""GPU parity of the training path: the loss Eq. (loss_Ab) and its
+hand-written adjoint through the network (FP32) against the FP64 oracle, and
+Adam against the oracle's step.
+
+Tolerance: the adjoint runs in FP32 (unit roundoff 6e-8) through chains of
+about ten MLP layers and reductions of up to a few hundred terms, so the
+gradient is compared in relative 2-norm at 1e-4 and the loss at 1e-5.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2305_16432_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def N():
+    from paper_2305_16432_gb300 import build
+    build.build()
+    from paper_2305_16432_gb300 import npcg
+    return npcg
+
+
+def _gpu(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def _pairs(A, k, seed):
+    B = I.rhs(A.n, seed, count=k)
+    X = np.linalg.solve(A.dense(), B.T).T
+    return X, B
+
+
+@pytest.mark.parametrize("cfg,prob", [
+    (I.GnnConfig(n_mp=2, l=2, l_mp=2, h=16), I.fem2d(7, sigma=1.0, seed=3)),
+    (I.GnnConfig(n_mp=3, l=1, l_mp=2, h=32), I.fd2d(6, 5, sigma=1.0, seed=4)),
+    (I.GnnConfig(n_mp=2, l=2, l_mp=2, h=64), I.fem2d(12, sigma=1.0, seed=5)),
+    (I.GnnConfig(n_mp=0, l=2, l_mp=2, h=16), I.fd3d(4, 3, 3, sigma=1.0, seed=6)),
+])
+def test_loss_and_grad_parity(N, cfg, prob):
+    om, ph = I.grf_features(prob)
+    Ao = O.assemble(prob, om, ph)
+    rp, ci, v = N.assemble_system(prob, om, ph)
+    P = N.analyse(rp, ci)
+    X, B = _pairs(Ao, 3, 17)
+    w = I.gnn_weights(cfg, 2, scale=1.5)
+    lo, go = O.loss_and_grad(cfg, Ao, X, B, w.astype(np.float64))
+    lg, gg = N.loss_and_grad(P, v, _gpu(X), _gpu(B), cfg, _gpu(w, torch.float32))
+    gg = gg.cpu().numpy().astype(np.float64)
+    assert abs(lg - lo) <= 1e-5 * abs(lo)
+    assert np.linalg.norm(gg - go) / np.linalg.norm(go) <= 1e-4
+
+
+def test_loss_and_grad_batched_is_mean_over_systems(N):
+    cfg = I.GnnConfig(n_mp=2, l=2, l_mp=2, h=16)
+    probs = [I.fem2d(8, sigma=1.0, seed=8), I.fd2d(7, 5, sigma=1.0, seed=9)]
+    w = I.gnn_weights(cfg, 3)
+    As, cis, vs, Xs, Bs = [], [], [], [], []
+    off, sys_ptr = 0, [0]
+    for k, p in enumerate(probs):
+        om, ph = I.grf_features(p)
+        Ao = O.assemble(p, om, ph)
+        rp, ci, v = N.assemble_system(p, om, ph)
+        As.append(Ao)
+        cis.append(ci.cpu().numpy() + off)
+        vs.append(v.cpu().numpy())
+        X, B = _pairs(Ao, 2, 30 + k)
+        Xs.append(X)
+        Bs.append(B)
+        off += Ao.n
+        sys_ptr.append(off)
+    nnz_off = np.cumsum([0] + [a.nnz for a in As])
+    rp_cat = np.concatenate([a.row_ptr[:-1] + nnz_off[k] for k, a in enumerate(As)] + [[nnz_off[-1]]])
+    P = N.analyse(_gpu(rp_cat, torch.int32), _gpu(np.concatenate(cis), torch.int32), sys_ptr)
+    Xc = np.concatenate(Xs, axis=1)
+    Bc = np.concatenate(Bs, axis=1)
+    lg, gg = N.loss_and_grad(P, _gpu(np.concatenate(vs)), _gpu(Xc), _gpu(Bc), cfg, _gpu(w, torch.float32))
+    ref = [O.loss_and_grad(cfg, As[k], Xs[k], Bs[k], w.astype(np.float64)) for k in range(2)]
+    lo = np.mean([r[0] for r in ref])
+    go = np.mean([r[1] for r in ref], axis=0)
+    assert abs(lg - lo) <= 1e-5 * abs(lo)
+    gg = gg.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(gg - go) / np.linalg.norm(go) <= 1e-4
+
+
+def test_adam_matches_oracle(N):
+    g = np.random.default_rng(0)
+    w = g.standard_normal(1000).astype(np.float32)
+    wo = w.astype(np.float64)
+    m, v = np.zeros(1000), np.zeros(1000)
+    wg = _gpu(w, torch.float32)
+    mg = torch.zeros_like(wg)
+    vg = torch.zeros_like(wg)
+    for t in range(1, 6):
+        grad = g.standard_normal(1000).astype(np.float32)
+        O.adam(wo, grad.astype(np.float64), m, v, t)
+        N.adam_step(wg, _gpu(grad, torch.float32), mg, vg, t)
+    torch.cuda.synchronize()
+    assert np.abs(wg.cpu().numpy() - wo).max() <= 1e-6
