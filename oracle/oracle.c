@@ -483,7 +483,10 @@ done:
  *   v_i <- MLP_v([v_i || sum_j e_ij (.) v_j])   (sum over row i incl. j = i)
  *   e_ij <- MLP_e([e_ij || v_i || v_j])         (new v; every directed edge)
  *   s_ij = MLP_dec(e_ij)
- *   L_ij = sqrt(s) (s_ij + s_ji)/2 (i > j),  L_ii = sqrt(s) softplus(s_ii)
+ *   diag_mode 0: L_ij = sqrt(s) (s_ij + s_ji)/2 (i > j),  L_ii = sqrt(s) softplus(s_ii)
+ *   diag_mode 1 (App. A.3, L D L^T with D = diag(A)): L = L' D^{1/2} with a
+ *     unit-diagonal L', L'_ij = (s_ij + s_ji)/2, i.e. L_ii = sqrt(A_ii),
+ *     L_ij = sqrt(A_jj) (s_ij + s_ji)/2
  * Flat weights: node encoder, edge encoder, n_mp x (node MLP, edge MLP),
  * decoder; each Linear W[out][in] then b[out].
  * ==================================================================== */
@@ -667,8 +670,18 @@ static void gnn_forward_tape(const or_gnn_cfg* c, int32_t n, const int32_t* rp, 
         for (int32_t kk = Lrp[i]; kk < Lrp[i + 1]; ++kk) {
             int32_t j = Lci[kk];
             int32_t kij = find_entry(rp, ci, i, j);
-            if (j == i) Lv[kk] = rs * softplus(T->s[kij]);
-            else {
+            if (c->diag_mode == 1) {
+                /* App. A.3: P = L' D L'^T with D = diag(A) and unit-diagonal L',
+                 * L'_ij = (s_ij + s_ji)/2; stored as L = L' D^{1/2} */
+                double djj = av[find_entry(rp, ci, j, j)];
+                if (j == i) Lv[kk] = sqrt(djj);
+                else {
+                    int32_t kji = find_entry(rp, ci, j, i);
+                    Lv[kk] = sqrt(djj) * 0.5 * (T->s[kij] + T->s[kji]);
+                }
+            } else if (j == i) {
+                Lv[kk] = rs * softplus(T->s[kij]);
+            } else {
                 int32_t kji = find_entry(rp, ci, j, i);
                 Lv[kk] = rs * 0.5 * (T->s[kij] + T->s[kji]);
             }
@@ -705,8 +718,17 @@ static void gnn_backward(const or_gnn_cfg* c, int32_t n, const int32_t* rp, cons
         for (int32_t kk = Lrp[i]; kk < Lrp[i + 1]; ++kk) {
             int32_t j = Lci[kk];
             int32_t kij = find_entry(rp, ci, i, j);
-            if (j == i) ds[kij] += rs * sigmoid(T->s[kij]) * dL[kk];
-            else {
+            if (c->diag_mode == 1) {
+                /* L_ii = sqrt(A_ii) is fixed; L_ij = sqrt(A_jj) (s_ij + s_ji)/2 */
+                if (j != i) {
+                    int32_t kji = find_entry(rp, ci, j, i);
+                    double g = sqrt(av[find_entry(rp, ci, j, j)]) * 0.5 * dL[kk];
+                    ds[kij] += g;
+                    ds[kji] += g;
+                }
+            } else if (j == i) {
+                ds[kij] += rs * sigmoid(T->s[kij]) * dL[kk];
+            } else {
                 int32_t kji = find_entry(rp, ci, j, i);
                 ds[kij] += rs * 0.5 * dL[kk];
                 ds[kji] += rs * 0.5 * dL[kk];

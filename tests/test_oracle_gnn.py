@@ -39,6 +39,10 @@ def _mlp(layers, X):
 
 
 def _dense_gnn(cfg, D, b, w):
+    return _dense_gnn_impl(cfg, D, b, w)
+
+
+def _dense_gnn_impl(cfg, D, b, w):
     """Independent dense-tensor formulation: node features V [n, h], edge
     features E [n, n, h] on the nonzeros of D; message passing as a masked
     einsum.  Returns the lower-triangular L as a dense matrix."""
@@ -58,6 +62,10 @@ def _dense_gnn(cfg, D, b, w):
     S = _mlp(mlps[-1], E)[:, :, 0] * mask
     sym = 0.5 * (S + S.T)
     L = np.tril(sym, -1)
+    if cfg.diag_mode == 1:
+        # L' unit lower triangular, P = L' D L'^T with D = diag(A): L = L' D^1/2
+        L[np.diag_indices(n)] = 1.0
+        return (L @ np.diag(np.sqrt(np.diag(D)))) * np.tril(mask)
     sp = np.maximum(np.diag(S), 0) + np.log1p(np.exp(-np.abs(np.diag(S))))
     L[np.diag_indices(n)] = sp
     return math.sqrt(s) * L * np.tril(mask)
@@ -65,7 +73,8 @@ def _dense_gnn(cfg, D, b, w):
 
 @pytest.mark.parametrize("cfg", [I.GnnConfig(n_mp=2, l=2, l_mp=2, h=4),
                                  I.GnnConfig(n_mp=3, l=1, l_mp=2, h=5),
-                                 I.GnnConfig(n_mp=0, l=2, l_mp=2, h=3)])
+                                 I.GnnConfig(n_mp=0, l=2, l_mp=2, h=3),
+                                 I.GnnConfig(n_mp=2, l=2, l_mp=1, h=4, diag_mode=1)])
 def test_gnn_matches_dense_formulation(cfg):
     A = O.assemble(I.fem2d(6, sigma=1.0, seed=2))
     b = I.rhs(A.n, 3)
@@ -84,6 +93,18 @@ def test_gnn_zero_weights():
     s = A.dense().diagonal().max()
     assert np.allclose(np.diag(D), math.sqrt(s) * math.log(2.0), rtol=1e-15)
     assert np.all(np.tril(D, -1) == 0)
+
+
+def test_ldlt_mode_zero_weights_is_jacobi():
+    # App. A.3 variant: with zero weights L' = I, so P = diag(A) (Jacobi)
+    cfg = I.GnnConfig(n_mp=2, l=2, l_mp=2, h=8, diag_mode=1)
+    A = O.assemble(I.fem2d(9, sigma=1.0, seed=4))
+    L = O.gnn_forward(cfg, A, I.rhs(A.n, 1), np.zeros(cfg.nparams))
+    assert np.allclose(L.dense() @ L.dense().T, np.diag(np.diag(A.dense())), rtol=1e-15, atol=0)
+    b = I.rhs(A.n, 2)
+    _, it_l, _, _ = O.pcg(A, b, O.PREC_LLT, L, rtol=1e-8)
+    _, it_j, _, _ = O.pcg(A, b, O.PREC_JACOBI, rtol=1e-8)
+    assert it_l == it_j
 
 
 def test_gnn_no_message_passing_is_elementwise():
@@ -183,7 +204,8 @@ def test_loss_gradient_wrt_L_by_finite_differences():
 
 
 @pytest.mark.parametrize("cfg", [I.GnnConfig(n_mp=2, l=2, l_mp=2, h=3),
-                                 I.GnnConfig(n_mp=1, l=1, l_mp=1, h=4)])
+                                 I.GnnConfig(n_mp=1, l=1, l_mp=1, h=4),
+                                 I.GnnConfig(n_mp=1, l=2, l_mp=1, h=3, diag_mode=1)])
 def test_loss_and_grad_central_differences(cfg):
     # central differences, eps = 1e-6, FP64, on every weight
     A = _tiny_system()
