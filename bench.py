@@ -192,7 +192,10 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16"],
+                    help="network arithmetic: BF16 tensor cores (default) or FP32")
+    ap.add_argument("--apply", default="fp32", choices=["fp32", "fp64"],
+                    help="arithmetic of the L L^T solves inside the FP64 PCG")
     ap.add_argument("--weights", default=os.path.join(WEIGHTS_DIR, "fem2d_6x64.npy"))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--trsv-reps", type=int, default=50)
@@ -216,7 +219,9 @@ def main():
     prec = N.BF16 if args.precision == "bf16" else N.FP32
     prob = I.fem2d_256(seed=rank)
     cfg = I.GnnConfig(n_mp=6, l=2, l_mp=2, h=64)
-    w_np, wkind, _ = _load_weights(cfg, args.weights)
+    w_np, wkind, wmeta = _load_weights(cfg, args.weights)
+    if wmeta.get("config", {}).get("diag_mode", 0):
+        cfg = I.GnnConfig(n_mp=6, l=2, l_mp=2, h=64, diag_mode=int(wmeta["config"]["diag_mode"]))
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     rp, ci, v = N.assemble_system(prob)
@@ -225,14 +230,17 @@ def main():
     w = torch.as_tensor(w_np, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
 
+    apply32 = args.apply == "fp32"
+    pc = N.PREC_LLT32 if apply32 else N.PREC_LLT
+
     def learned_step():
         L = N.gnn_factor(P, v, b, cfg, w, precision=prec)
-        x, st = N.pcg_solve(P, v, b, N.PREC_LLT, L, rtol=RTOL)
+        x, st = N.pcg_solve(P, v, b, pc, L, rtol=RTOL)
         return st[0]
 
     def ic0_step():
         L, _ = N.ic0_factor(P, v)
-        x, st = N.pcg_solve(P, v, b, N.PREC_LLT, L, rtol=RTOL)
+        x, st = N.pcg_solve(P, v, b, pc, L, rtol=RTOL)
         return st[0]
 
     def timed(fn, k):
@@ -277,8 +285,9 @@ def main():
     Lic, _ = N.ic0_factor(P, v)
     N.factor_load(P, Lic)
     r = torch.randn(P.n, dtype=torch.float64, device=dev)
-    trsv_ms, _ = N.sptrsv_timed(P, r, transpose=False, reps=args.trsv_reps)
-    trsv_bytes = 12 * P.nnz_L + 4 * (P.n + 1) + 16 * P.n
+    trsv_ms, _ = N.sptrsv_timed(P, r, transpose=False, reps=args.trsv_reps, f32=apply32)
+    # SpTRSV bytes per launch: index + value per L entry, row pointer, rhs + solution
+    trsv_bytes = (8 if apply32 else 12) * P.nnz_L + 4 * (P.n + 1) + 16 * P.n
     achieved = trsv_bytes / (trsv_ms * 1e-3) / 1e9
     traffic = None
     prof = os.path.join(ROOT, "profiles", "trsv_traffic.json")
@@ -300,7 +309,7 @@ def main():
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             N.solve_host(P, a_host.numpy(), b_host.numpy(), method=N.METHOD_GNN, cfg=cfg, weights=w,
-                         precision=prec, rtol=RTOL, x_host=x_host.numpy())
+                         precision=prec, rtol=RTOL, x_host=x_host.numpy(), f32_apply=apply32)
             ts.append(time.perf_counter() - t0)
         e2e_ms = 1e3 * float(np.mean(ts[args.warmup:])) / world
         h2d = 8 * (P.nnz + P.n)
@@ -308,9 +317,12 @@ def main():
 
     # kernel launches per learned step (counted from the launch structure)
     it = st_l["iters"]
+    # network: scales, 2 encoders, 2 per layer, decoder, L assembly
     gnn_launches = 1 + 2 + 2 * cfg.n_mp + 1 + 1
+    # PCG: 4 factor loads, init, 2 solves, r^T z, 11 per graph trip (2 iterations
+    # of 5 kernels + the loop condition), stats
     trips = max(1, math.ceil(it / 2))
-    pcg_launches = 2 + 1 + 2 + 1 + 11 * trips + 1
+    pcg_launches = 4 + 1 + 2 + 1 + 11 * trips + 1
     launches = (gnn_launches + pcg_launches) * args.steps
 
     cpu = None
@@ -326,12 +338,16 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64+" + args.precision, "data": "synthetic",
             "config": {"workload": "fem2d_256_learned_pcg", "n": P.n, "nnz": P.nnz, "nnz_L": P.nnz_L,
-                       "levels": P.nlev_fwd, "gnn": "n_mp=6,l=2,l_mp=2,h=64", "weights": wkind,
+                       "levels": P.nlev_fwd, "gnn": "n_mp=6,l=2,l_mp=2,h=64," + args.precision,
+                       "weights": wkind, "pcg": "fp64 recurrences, " + args.apply + " L L^T solves",
                        "rtol": RTOL, "l2": "flushed between steps (256 MB write)"},
             "compare": {"learned_iters": st_l["iters"], "learned_ms_median": float(np.median(ms_l)),
                         "ic0_ms": float(np.mean(ms_i)), "ic0_iters": st_i["iters"],
-                        "learned_relres": st_l["relres"], "wall_s_timed": wall},
-            "roofline": {"kernel": "k_trsv (forward SpTRSV, level-ordered SELL-32)", "bound": "hbm",
+                        "learned_relres": st_l["relres"], "wall_s_timed": wall,
+                        "trsv_design": "levelsync" if P.trsv_mode == N.TRSV_LEVELSYNC else "syncfree",
+                        "trsv_tuned_ms_fwd_bwd": P.tuned_ms},
+            "roofline": {"kernel": ("k_trsv_cta" if P.trsv_mode == N.TRSV_LEVELSYNC else "k_trsv")
+                         + " (forward SpTRSV, " + args.apply + ")", "bound": "hbm",
                          "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                          "peak_kind": peak_kind, "traffic": traffic, "bytes_per_launch": trsv_bytes,
                          "ms_per_launch": trsv_ms, "levels": P.nlev_fwd},

@@ -167,14 +167,18 @@ NPCG_API npcg_status npcg_pattern_export(npcg_handle h, npcg_pattern p, int32_t*
  * Linear stored as W[out][in] row-major followed by bias[out].
  * ------------------------------------------------------------------------ */
 enum { NPCG_FP32 = 0, NPCG_BF16 = 1 };
-enum { NPCG_DIAG_SOFTPLUS = 0 };
+/* Diagonal rule.  NPCG_DIAG_SOFTPLUS: L_ii = sqrt(s) softplus(s_ii) (above).
+ * NPCG_DIAG_LDLT_DIAGA (App. A.3): P = L' D L'^T with D = diag(A) and a
+ * unit-diagonal L', L'_ij = (s_ij + s_ji)/2; returned as L = L' D^{1/2}, i.e.
+ * L_ii = sqrt(A_ii), L_ij = sqrt(A_jj) (s_ij + s_ji)/2 (no sqrt(s) scaling). */
+enum { NPCG_DIAG_SOFTPLUS = 0, NPCG_DIAG_LDLT_DIAGA = 1 };
 
 typedef struct {
     int32_t n_mp;        /* message-passing layers                       */
     int32_t l;           /* depth of encoders and decoder                */
     int32_t l_mp;        /* depth of the node / edge update MLPs         */
     int32_t h;           /* hidden = latent width: 16, 32 or 64          */
-    int32_t diag_mode;   /* NPCG_DIAG_SOFTPLUS                           */
+    int32_t diag_mode;   /* NPCG_DIAG_SOFTPLUS or NPCG_DIAG_LDLT_DIAGA    */
     int32_t precision;   /* NPCG_FP32 (parity) or NPCG_BF16 (tensor cores)*/
 } npcg_gnn_config;
 
@@ -242,10 +246,11 @@ NPCG_API npcg_status npcg_factor_load(npcg_handle h, npcg_pattern p, const doubl
  * solves L^T y = r (r, y [n], distinct). */
 NPCG_API npcg_status npcg_sptrsv(npcg_handle h, npcg_pattern p, int32_t transpose,
                         const double* r, double* y);
-/* Same solve repeated reps times; *ms_per_launch (host) is the mean duration
- * of the triangular-solve kernel alone, from CUDA events recorded on the
- * handle's stream around each launch.  Synchronises. */
-NPCG_API npcg_status npcg_sptrsv_timed(npcg_handle h, npcg_pattern p, int32_t transpose,
+/* Same solve repeated reps times (f32 != 0: FP32 factor and arithmetic, as in
+ * NPCG_PREC_LLT32); *ms_per_launch (host) is the mean duration of the
+ * triangular-solve kernel alone, from CUDA events recorded on the handle's
+ * stream around each launch.  Synchronises. */
+NPCG_API npcg_status npcg_sptrsv_timed(npcg_handle h, npcg_pattern p, int32_t transpose, int32_t f32,
                               const double* r, double* y, int32_t reps, double* ms_per_launch);
 
 /* --------------------------------------------------------------------------
@@ -272,15 +277,18 @@ NPCG_API npcg_status npcg_adam_step(npcg_handle h, int64_t n, float* w, const fl
  * "Evaluation Metrics": precompute + solve).  Copies A_val_host [nnz] and
  * b_host [n] in, builds the preconditioner (method: NPCG_METHOD_GNN with
  * cfg + device weights, NPCG_METHOD_IC0, NPCG_METHOD_JACOBI, NPCG_METHOD_CG),
- * runs PCG from x_0 = 0 and copies x out to x_host [n].  Host buffers should
- * be pinned for asynchronous copies.  stats: host [nsys].  Synchronises.
+ * runs PCG from x_0 = 0 and copies x out to x_host [n].  f32_apply != 0
+ * applies the L L^T preconditioners in FP32 (NPCG_PREC_LLT32).  Host buffers
+ * should be pinned for asynchronous copies.  stats: host [nsys].
+ * Synchronises.
  * ------------------------------------------------------------------------ */
 enum { NPCG_METHOD_GNN = 0, NPCG_METHOD_IC0 = 1, NPCG_METHOD_JACOBI = 2, NPCG_METHOD_CG = 3 };
 
 NPCG_API npcg_status npcg_solve_host(npcg_handle h, npcg_pattern p, int32_t method,
                             const npcg_gnn_config* cfg, const float* weights,
                             const double* A_val_host, const double* b_host, double* x_host,
-                            double rtol, int32_t max_iter, npcg_solve_stats* stats);
+                            double rtol, int32_t max_iter, int32_t f32_apply,
+                            npcg_solve_stats* stats);
 
 /* --------------------------------------------------------------------------
  * Allocation-free solve (the paper has no counterpart; this serves callers

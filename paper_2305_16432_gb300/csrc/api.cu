@@ -230,12 +230,12 @@ npcg_status npcg_sptrsv(npcg_handle h, npcg_pattern p, int32_t transpose, const 
     return NPCG_OK;
 }
 
-npcg_status npcg_sptrsv_timed(npcg_handle h, npcg_pattern p, int32_t transpose, const double* r, double* y,
-                              int32_t reps, double* ms_per_launch) {
+npcg_status npcg_sptrsv_timed(npcg_handle h, npcg_pattern p, int32_t transpose, int32_t f32, const double* r,
+                              double* y, int32_t reps, double* ms_per_launch) {
     NPCG_TRY(check_hp(h, p));
     if (!r || !y || r == y || !ms_per_launch || reps < 1)
         return set_error(H(h), NPCG_EINVAL, "bad argument");
-    return sptrsv_timed_run(H(h), PT(p), transpose ? 1 : 0, r, y, reps, ms_per_launch, false);
+    return sptrsv_timed_run(H(h), PT(p), transpose ? 1 : 0, r, y, reps, ms_per_launch, f32 != 0);
 }
 
 npcg_status npcg_loss_and_grad(npcg_handle h, npcg_pattern p, const double* A_val, int32_t npairs,
@@ -257,7 +257,8 @@ npcg_status npcg_adam_step(npcg_handle h, int64_t n, float* w, const float* g, f
 
 npcg_status npcg_solve_host(npcg_handle h, npcg_pattern p, int32_t method, const npcg_gnn_config* cfg,
                             const float* weights, const double* A_val_host, const double* b_host,
-                            double* x_host, double rtol, int32_t max_iter, npcg_solve_stats* stats) {
+                            double* x_host, double rtol, int32_t max_iter, int32_t f32_apply,
+                            npcg_solve_stats* stats) {
     NPCG_TRY(check_hp(h, p));
     Handle* hh = H(h);
     Pattern* P = PT(p);
@@ -271,7 +272,7 @@ npcg_status npcg_solve_host(npcg_handle h, npcg_pattern p, int32_t method, const
     NPCG_CUDA(hh, cudaMemcpyAsync(P->Aval_dev.p, A_val_host, P->nnz * sizeof(double), cudaMemcpyHostToDevice, hh->stream));
     NPCG_CUDA(hh, cudaMemcpyAsync(P->b.p, b_host, P->n * sizeof(double), cudaMemcpyHostToDevice, hh->stream));
     NPCG_CUDA(hh, cudaMemsetAsync(P->x.p, 0, P->n * sizeof(double), hh->stream));
-    int precond = NPCG_PREC_LLT;
+    int precond = f32_apply ? NPCG_PREC_LLT32 : NPCG_PREC_LLT;
     if (method == NPCG_METHOD_GNN) NPCG_TRY(gnn_forward_run(hh, P, P->Aval_dev.p, P->b.p, cfg, weights, P->Lval_dev.p));
     else if (method == NPCG_METHOD_IC0) NPCG_TRY(ic0_run(hh, P, P->Aval_dev.p, P->Lval_dev.p, nullptr));
     else precond = method == NPCG_METHOD_JACOBI ? NPCG_PREC_JACOBI : NPCG_PREC_NONE;

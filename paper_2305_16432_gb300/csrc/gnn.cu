@@ -46,17 +46,25 @@ __global__ void k_scales(const int64_t* sys_ptr, const int32_t* adiag, const dou
 
 __device__ __forceinline__ double softplus_d(double z) { return fmax(z, 0.0) + log1p(exp(-fabs(z))); }
 
+// diag_mode 0: L_ij = sqrt(s) (s_ij + s_ji)/2, L_ii = sqrt(s) softplus(s_ii);
+// diag_mode 1 (App. A.3, P = L' D L'^T, D = diag(A), unit-diagonal L'):
+//   L = L' D^{1/2}: L_ii = sqrt(A_ii), L_ij = sqrt(A_jj) (s_ij + s_ji)/2
 __global__ void k_assemble_L(int64_t nnzL, const int32_t* l2a, const int32_t* erow, const int32_t* ci,
                              const int32_t* mirror, const int32_t* row_sys, const double* sc,
-                             const float* S, double* L) {
+                             const float* S, const double* av, const int32_t* adiag, int diag_mode,
+                             double* L) {
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nnzL;
          q += (int64_t)gridDim.x * blockDim.x) {
         int ka = l2a[q];
         int i = erow[ka], j = ci[ka];
-        double rs = sqrt(sc[2 * row_sys[i]]);
         double v;
-        if (i == j) v = rs * softplus_d((double)S[ka]);
-        else v = rs * 0.5 * ((double)S[ka] + (double)S[mirror[ka]]);
+        if (diag_mode == 1) {
+            const double dj = sqrt(av[adiag[j]]);
+            v = i == j ? dj : dj * 0.5 * ((double)S[ka] + (double)S[mirror[ka]]);
+        } else {
+            const double rs = sqrt(sc[2 * row_sys[i]]);
+            v = i == j ? rs * softplus_d((double)S[ka]) : rs * 0.5 * ((double)S[ka] + (double)S[mirror[ka]]);
+        }
         L[q] = v;
     }
 }
@@ -106,7 +114,8 @@ npcg_status gnn_check_config(Handle* h, const npcg_gnn_config* cfg) {
     if (cfg->n_mp < 0 || cfg->n_mp > 64) return set_error(h, NPCG_EINVAL, "n_mp must be in [0, 64]");
     if (cfg->l < 1 || cfg->l > kMaxDepth || cfg->l_mp < 1 || cfg->l_mp > kMaxDepth)
         return set_error(h, NPCG_EINVAL, "l and l_mp must be in [1, 4]");
-    if (cfg->diag_mode != NPCG_DIAG_SOFTPLUS) return set_error(h, NPCG_EINVAL, "unsupported diag_mode");
+    if (cfg->diag_mode != NPCG_DIAG_SOFTPLUS && cfg->diag_mode != NPCG_DIAG_LDLT_DIAGA)
+        return set_error(h, NPCG_EINVAL, "unsupported diag_mode");
     if (cfg->precision != NPCG_FP32 && cfg->precision != NPCG_BF16)
         return set_error(h, NPCG_EINVAL, "precision must be NPCG_FP32 or NPCG_BF16");
     return NPCG_OK;
@@ -138,7 +147,7 @@ npcg_status gnn_scales_run(Handle* h, Pattern* P, const double* A_val, const dou
 npcg_status gnn_assemble_L(Handle* h, Pattern* P, const GnnBuffers& B, double* L_val) {
     int blocks = std::max(1, std::min(ceil_div(P->nnzL, 256), h->num_sms * 16));
     k_assemble_L<<<blocks, 256, 0, h->stream>>>(P->nnzL, P->l2a.p, P->edge_row.p, P->ci.p, P->mirror.p,
-                                               P->row_sys.p, B.sc, B.s, L_val);
+                                               P->row_sys.p, B.sc, B.s, B.av, P->adiag.p, B.diag_mode, L_val);
     NPCG_CUDA(h, cudaGetLastError());
     return NPCG_OK;
 }
@@ -156,6 +165,8 @@ npcg_status gnn_forward_run(Handle* h, Pattern* P, const double* A_val, const do
     B.e[1] = S.e.p + (size_t)P->nnz * cfg->h;
     B.s = S.s.p;
     B.sc = S.sc.p;
+    B.av = A_val;
+    B.diag_mode = cfg->diag_mode;
     NPCG_TRY(gnn_forward_into(h, P, A_val, b, cfg, w, B));
     return gnn_assemble_L(h, P, B, L_val);
 }

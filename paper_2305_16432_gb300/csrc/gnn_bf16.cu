@@ -1,0 +1,412 @@
+// Graph-network factor, BF16 tensor-core path (Sec. 4.2 "Architecture",
+// App. A.3), hidden width h = 64.
+//
+// Every node / edge MLP runs as a chain of dense [128 x K] x [K x 64] products
+// on the 5th-generation tensor cores: one elected thread issues tcgen05.mma
+// (kind::f16, BF16 operands from shared memory, FP32 accumulator in tensor
+// memory), tcgen05.commit signals an mbarrier, and the four warps read their
+// 32-lane quarter of the accumulator with tcgen05.ld, add the bias, apply
+// ReLU and write the next layer's operand back to shared memory as BF16.
+// Operands use the 128-byte-swizzled K-major layout (8-row x 128-byte atoms,
+// 16-byte chunk c of row r at chunk c ^ (r & 7)); weights are converted from
+// the FP32 master copy and staged once per CTA.  Features between layers are
+// BF16 in global memory; the message-passing gather accumulates in FP32.
+// The scalar input layer of the encoders and the scalar output layer of the
+// decoder run on the CUDA cores inside the same kernel.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "gnn_common.cuh"
+
+namespace npcg {
+
+namespace {
+
+constexpr int kH = 64;            // hidden width of this path
+constexpr int kM = 128;           // rows per tile = MMA M = TMEM lanes
+constexpr int kThreads = 128;     // one thread per tile row
+constexpr int kAtomRows = 8;      // swizzle atom: 8 rows x 128 bytes
+constexpr long long kWaitSpin = 1LL << 22;
+
+__device__ __forceinline__ uint32_t s_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// byte offset of element (r, k) inside a [rows x 64] BF16 K-block
+__device__ __forceinline__ uint32_t swz(int r, int k) {
+    return (uint32_t)(r * 128 + ((((k >> 3) ^ (r & 7)) & 7) << 4) + ((k & 7) << 1));
+}
+
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);          // start address
+    d |= (uint64_t)(16 >> 4) << 16;                   // leading byte offset (unused for this layout)
+    d |= (uint64_t)(1024 >> 4) << 32;                 // stride byte offset
+    d |= (uint64_t)1 << 46;                           // descriptor version
+    d |= (uint64_t)2 << 61;                           // 128-byte swizzle
+    return d;
+}
+
+// instruction descriptor: BF16 x BF16 -> FP32, both K-major, M = 128, N = 64
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kH >> 3) << 17) |
+                            ((uint32_t)(kM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(kIdesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(s_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity) {
+    for (long long s = 0; s < kWaitSpin; ++s) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(s_addr(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+struct Bf16Args {
+    int64_t nrows;
+    const float* w;           // FP32 master weights of this MLP
+    int depth;
+    const int32_t* rp;
+    const int32_t* ci;
+    const int32_t* erow;
+    const int32_t* row_sys;
+    const double* sc;
+    const double* av;
+    const double* b;
+    const __nv_bfloat16* vin;
+    const __nv_bfloat16* ein;
+    __nv_bfloat16* out;       // H-wide BF16 output rows
+    float* sout;              // decoder: FP32 scalar output
+    int* flags;
+};
+
+// tensor-core layers of each mode: NODE/EDGE all, ENC from layer 1, DEC to depth-1
+__host__ __device__ constexpr int tc_first(int mode) { return mode == MODE_ENC_NODE || mode == MODE_ENC_EDGE ? 1 : 0; }
+
+struct SmemPlan {
+    uint32_t a0, a1, w, bias, misc, total;
+};
+
+__host__ __device__ inline SmemPlan plan(int mode, int depth) {
+    const int in = mode_in(mode, kH);
+    const int kin0 = (mode == MODE_ENC_NODE || mode == MODE_ENC_EDGE) ? kH : in;   // first TC layer input
+    const int first = tc_first(mode);
+    const int last = mode == MODE_DEC ? depth - 1 : depth;
+    uint32_t wbytes = 0;
+    for (int l = first; l <= last; ++l) wbytes += (uint32_t)((l == first ? kin0 : kH) / 64) * (kH * 128);
+    SmemPlan p;
+    p.a0 = 0;                                         // [128 x kin0] operand (kin0 / 64 K-blocks)
+    p.a1 = p.a0 + (uint32_t)(kin0 / 64) * (kM * 128);  // [128 x 64] hidden operand
+    p.w = p.a1 + kM * 128;
+    p.bias = p.w + wbytes;                            // FP32 biases of every layer + scalar layer weights
+    p.misc = p.bias + (uint32_t)(depth + 1) * kH * 4 + 2 * kH * 4 + 64;
+    p.misc = (p.misc + 15) & ~15u;
+    p.total = p.misc + 64;
+    return p;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) k_mlp_bf16(Bf16Args a) {
+    extern __shared__ __align__(1024) unsigned char sm_raw[];
+    // swizzled operands need 1024-byte aligned shared addresses
+    unsigned char* sm = sm_raw + ((1024u - (s_addr(sm_raw) & 1023u)) & 1023u);
+    constexpr int IN = mode_in(MODE, kH);
+    constexpr bool kEnc = MODE == MODE_ENC_NODE || MODE == MODE_ENC_EDGE;
+    constexpr int KIN0 = kEnc ? kH : IN;
+    const int depth = a.depth;
+    const int first = tc_first(MODE);
+    const int last = MODE == MODE_DEC ? depth - 1 : depth;
+    const SmemPlan P = plan(MODE, depth);
+    unsigned char* A0 = sm + P.a0;
+    unsigned char* A1 = sm + P.a1;
+    unsigned char* W = sm + P.w;
+    float* bias = reinterpret_cast<float*>(sm + P.bias);          // [depth+1][64]
+    float* s_w0 = bias + (depth + 1) * kH;                         // encoder layer 0: W[64] then b[64]
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + P.misc);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + P.misc + 8);
+    const int tid = threadIdx.x, warp = tid >> 5;
+
+    // ---- stage weights: BF16 swizzled K-blocks of every tensor-core layer, FP32 biases
+    {
+        const float* src = a.w;
+        uint32_t woff = 0;
+        for (int l = 0; l <= depth; ++l) {
+            const int fi = l == 0 ? IN : kH, fo = (MODE == MODE_DEC && l == depth) ? 1 : kH;
+            const bool tc = l >= first && l <= last;
+            if (tc) {
+                const int nkb = fi / 64;
+                for (int t = tid; t < fo * fi; t += kThreads) {
+                    const int n = t / fi, k = t % fi;
+                    unsigned char* blk = W + woff + (uint32_t)(k / 64) * (kH * 128);
+                    *reinterpret_cast<__nv_bfloat16*>(blk + swz(n, k % 64)) = __float2bfloat16_rn(src[t]);
+                }
+                woff += (uint32_t)nkb * (kH * 128);
+            } else if (l == 0) {                 // encoder scalar input layer
+                for (int t = tid; t < kH; t += kThreads) { s_w0[t] = src[t]; s_w0[kH + t] = src[kH + t]; }
+            } else {                             // decoder scalar output layer: W[64], b
+                for (int t = tid; t < kH; t += kThreads) s_w0[t] = src[t];
+                if (tid == 0) s_w0[kH] = src[kH];
+            }
+            for (int t = tid; t < fo; t += kThreads) bias[l * kH + t] = src[fi * fo + t];
+            src += fi * fo + fo;
+        }
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_addr(bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(s_addr(tmem_slot))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t my_lanes = tmem + ((uint32_t)(warp * 32) << 16);
+    uint32_t phase = 0;
+    bool ok = true;
+
+    const int64_t ntiles = (a.nrows + kM - 1) / kM;
+    for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        const int64_t row0 = tile * kM;
+        // ---- stage 0: operand of the first tensor-core layer into A0
+        if (kEnc) {
+            const int64_t row = row0 + tid;
+            float x = 0.0f;
+            if (row < a.nrows) {
+                if (MODE == MODE_ENC_NODE) x = (float)(a.b[row] / a.sc[2 * a.row_sys[row] + 1]);
+                else x = (float)(a.av[row] / a.sc[2 * a.row_sys[a.erow[row]]]);
+            }
+            for (int c = 0; c < 8; ++c) {
+                __nv_bfloat16 h8[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int o = c * 8 + j;
+                    h8[j] = __float2bfloat16_rn(fmaxf(fmaf(s_w0[o], x, bias[o]), 0.0f));
+                }
+                *reinterpret_cast<uint4*>(A0 + swz(tid, c * 8)) = *reinterpret_cast<uint4*>(h8);
+            }
+        } else if (MODE == MODE_NODE) {
+            for (int idx = tid; idx < kM * 16; idx += kThreads) {
+                const int r = idx >> 4, c = idx & 15;
+                const int64_t i = row0 + r;
+                uint4 val = make_uint4(0, 0, 0, 0);
+                if (i < a.nrows) {
+                    if (c < 8) {
+                        val = *reinterpret_cast<const uint4*>(a.vin + i * kH + c * 8);
+                    } else {
+                        float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                        for (int k = a.rp[i]; k < a.rp[i + 1]; ++k) {
+                            const uint4 e4 = *reinterpret_cast<const uint4*>(a.ein + (int64_t)k * kH + (c - 8) * 8);
+                            const uint4 v4 = *reinterpret_cast<const uint4*>(a.vin + (int64_t)a.ci[k] * kH + (c - 8) * 8);
+                            const __nv_bfloat16* e8 = reinterpret_cast<const __nv_bfloat16*>(&e4);
+                            const __nv_bfloat16* v8 = reinterpret_cast<const __nv_bfloat16*>(&v4);
+#pragma unroll
+                            for (int j = 0; j < 8; ++j)
+                                acc[j] = fmaf(__bfloat162float(e8[j]), __bfloat162float(v8[j]), acc[j]);
+                        }
+                        __nv_bfloat16 h8[8];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) h8[j] = __float2bfloat16_rn(acc[j]);
+                        val = *reinterpret_cast<uint4*>(h8);
+                    }
+                }
+                *reinterpret_cast<uint4*>(A0 + (uint32_t)(c >> 3) * (kM * 128) + swz(r, (c & 7) * 8)) = val;
+            }
+        } else {      // EDGE: [e | v_row | v_col], DEC: [e]
+            constexpr int CH = IN >= 8 ? IN / 8 : 1;     // (encoders never reach here)
+            for (int idx = tid; idx < kM * CH; idx += kThreads) {
+                const int r = idx / CH, c = idx % CH;
+                const int64_t k = row0 + r;
+                uint4 val = make_uint4(0, 0, 0, 0);
+                if (k < a.nrows) {
+                    const int seg = c >> 3, cc = c & 7;
+                    const __nv_bfloat16* src = seg == 0 ? a.ein + k * kH
+                                             : seg == 1 ? a.vin + (int64_t)a.erow[k] * kH
+                                                        : a.vin + (int64_t)a.ci[k] * kH;
+                    val = *reinterpret_cast<const uint4*>(src + cc * 8);
+                }
+                *reinterpret_cast<uint4*>(A0 + (uint32_t)(c >> 3) * (kM * 128) + swz(r, (c & 7) * 8)) = val;
+            }
+        }
+        // ---- tensor-core layers
+        uint32_t woff = 0;
+        for (int l = first; l <= last; ++l) {
+            const int kin = l == first ? KIN0 : kH;
+            const unsigned char* Aop = l == first ? A0 : A1;
+            fence_async_smem();
+            tc_fence_before();
+            __syncthreads();
+            tc_fence_after();
+            if (tid == 0) {
+                const uint32_t abase = s_addr(Aop), wbase = s_addr(W + woff);
+                for (int s = 0; s < kin / 16; ++s) {
+                    const uint32_t kb = (uint32_t)(s >> 2), ko = (uint32_t)(s & 3) * 32;
+                    mma_bf16(tmem, smem_desc(abase + kb * (kM * 128) + ko), smem_desc(wbase + kb * (kH * 128) + ko),
+                             s > 0 ? 1u : 0u);
+                }
+                mma_commit(bar);
+            }
+            woff += (uint32_t)(kin / 64) * (kH * 128);
+            ok = bar_wait(bar, phase);
+            phase ^= 1u;
+            if (!__syncthreads_and(ok)) break;
+            tc_fence_after();
+            float v[64];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                float t16[16];
+                tmem_ld16(my_lanes + q * 16, t16);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) v[q * 16 + i] = t16[i];
+            }
+            tmem_wait_ld();
+            const float* bl = bias + l * kH;
+            const bool relu = l < depth;
+            const int64_t row = row0 + tid;
+            if (l < last || (MODE != MODE_DEC && l < depth)) {
+                // next layer's operand (A1) -- the layer that read A1 has completed
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    __nv_bfloat16 h8[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const float z = v[c * 8 + j] + bl[c * 8 + j];
+                        h8[j] = __float2bfloat16_rn(relu ? fmaxf(z, 0.0f) : z);
+                    }
+                    *reinterpret_cast<uint4*>(A1 + swz(tid, c * 8)) = *reinterpret_cast<uint4*>(h8);
+                }
+            } else if (MODE == MODE_DEC) {
+                // hidden layer depth-1 done: scalar output layer on the CUDA cores
+                float s = s_w0[kH];
+#pragma unroll
+                for (int o = 0; o < kH; ++o) s = fmaf(s_w0[o], fmaxf(v[o] + bl[o], 0.0f), s);
+                if (row < a.nrows) a.sout[row] = s;
+            } else {
+                // last layer: BF16 feature row to global memory
+                if (row < a.nrows) {
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        __nv_bfloat16 h8[8];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) h8[j] = __float2bfloat16_rn(v[c * 8 + j] + bl[c * 8 + j]);
+                        *reinterpret_cast<uint4*>(a.out + row * kH + c * 8) = *reinterpret_cast<uint4*>(h8);
+                    }
+                }
+            }
+        }
+    }
+    if (!ok) {
+        // give the outstanding products one more bounded wait before the
+        // tensor memory is released
+        bar_wait(bar, phase ^ 1u);
+        if (tid == 0) atomicOr(a.flags, kFlagTimeout);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem) : "memory");
+}
+
+template <int MODE>
+npcg_status launch_bf16(Handle* h, const Bf16Args& a) {
+    if (a.nrows == 0) return NPCG_OK;
+    const SmemPlan p = plan(MODE, a.depth);
+    const size_t smem = p.total + 1024;       // alignment slack
+    if (smem > 227 * 1024) return set_error(h, NPCG_EINVAL, "MLP too deep for the BF16 kernel");
+    NPCG_CUDA(h, cudaFuncSetAttribute(k_mlp_bf16<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int per_sm = std::max(1, std::min(3, (int)((227 * 1024) / (smem + 1024))));
+    const int64_t ntiles = (a.nrows + kM - 1) / kM;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)h->num_sms * per_sm));
+    k_mlp_bf16<MODE><<<grid, kThreads, smem, h->stream>>>(a);
+    NPCG_CUDA(h, cudaGetLastError());
+    return NPCG_OK;
+}
+
+}  // namespace
+
+npcg_status gnn_scales_run(Handle* h, Pattern* P, const double* A_val, const double* b, double* sc);
+
+npcg_status gnn_forward_bf16_run(Handle* h, Pattern* P, const double* A_val, const double* b,
+                                 const npcg_gnn_config* cfg, const float* w, double* L_val) {
+    if (cfg->h != kH) return set_error(h, NPCG_EINVAL, "the BF16 tensor-core path needs hidden width h = 64");
+    GnnStore& S = P->gnn;
+    const size_t fe = (size_t)P->nnz * kH, fv = (size_t)P->n * kH;
+    NPCG_CUDA(h, S.bf.ensure(2 * (fe + fv)));
+    NPCG_CUDA(h, S.s.ensure(P->nnz));
+    NPCG_CUDA(h, S.sc.ensure((size_t)2 * P->nsys));
+    __nv_bfloat16* base = reinterpret_cast<__nv_bfloat16*>(S.bf.p);
+    __nv_bfloat16* V[2] = {base, base + fv};
+    __nv_bfloat16* E[2] = {base + 2 * fv, base + 2 * fv + fe};
+    NPCG_TRY(gnn_scales_run(h, P, A_val, b, S.sc.p));
+    NPCG_CUDA(h, cudaMemsetAsync(P->ctl.p + 1, 0, sizeof(int), h->stream));
+    const GnnOffsets off = gnn_offsets(kH, cfg->l, cfg->l_mp, cfg->n_mp);
+    Bf16Args a{};
+    a.rp = P->rp.p;
+    a.ci = P->ci.p;
+    a.erow = P->edge_row.p;
+    a.row_sys = P->row_sys.p;
+    a.sc = S.sc.p;
+    a.av = A_val;
+    a.b = b;
+    a.flags = P->ctl.p + 1;
+    a.nrows = P->n; a.w = w + off.enc_v; a.depth = cfg->l; a.out = V[0];
+    NPCG_TRY(launch_bf16<MODE_ENC_NODE>(h, a));
+    a.nrows = P->nnz; a.w = w + off.enc_e; a.depth = cfg->l; a.out = E[0];
+    NPCG_TRY(launch_bf16<MODE_ENC_EDGE>(h, a));
+    for (int t = 0; t < cfg->n_mp; ++t) {
+        const int c = t & 1;
+        a.nrows = P->n; a.w = w + off.node[t]; a.depth = cfg->l_mp; a.vin = V[c]; a.ein = E[c]; a.out = V[c ^ 1];
+        NPCG_TRY(launch_bf16<MODE_NODE>(h, a));
+        a.nrows = P->nnz; a.w = w + off.edge[t]; a.depth = cfg->l_mp; a.vin = V[c ^ 1]; a.ein = E[c]; a.out = E[c ^ 1];
+        NPCG_TRY(launch_bf16<MODE_EDGE>(h, a));
+    }
+    a.nrows = P->nnz; a.w = w + off.dec; a.depth = cfg->l; a.ein = E[cfg->n_mp & 1]; a.out = nullptr; a.sout = S.s.p;
+    NPCG_TRY(launch_bf16<MODE_DEC>(h, a));
+    GnnBuffers gb{};
+    gb.s = S.s.p;
+    gb.sc = S.sc.p;
+    gb.av = A_val;
+    gb.diag_mode = cfg->diag_mode;
+    NPCG_TRY(gnn_assemble_L(h, P, gb, L_val));
+    int flags = 0;
+    NPCG_TRY(read_scalar(h, P->ctl.p + 1, &flags));
+    if (flags & kFlagTimeout) return set_error(h, NPCG_ETIMEOUT, "tensor-core MLP wait timed out");
+    return NPCG_OK;
+}
+
+}  // namespace npcg

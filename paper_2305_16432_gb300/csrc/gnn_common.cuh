@@ -43,6 +43,8 @@ struct GnnBuffers {
     float* e[2];
     float* s;
     double* sc;     // per system: [2s] max diagonal, [2s+1] ||b||_inf
+    const double* av = nullptr;   // A values (diag_mode 1 reads diag(A))
+    int diag_mode = 0;
 };
 
 struct MlpArgs {

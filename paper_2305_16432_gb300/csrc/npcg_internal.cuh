@@ -117,6 +117,7 @@ struct GnnStore {
     DevBuf<float> aux;             // adjoint scratch
     DevBuf<double> dL;             // adjoint of L (loss)
     DevBuf<double> Lv;             // L values of the current pair
+    DevBuf<unsigned short> bf;     // BF16 node / edge features (tensor-core path)
 };
 
 struct Pattern {
@@ -231,9 +232,10 @@ npcg_status cta_layout_build(Handle* h, Pattern* P, bool upper, CtaLayout* C);
 npcg_status cta_link(Handle* h, Pattern* P);
 int cta_stages(const CtaLayout& C);
 npcg_status cta_factor_load(Handle* h, CtaLayout* C, const double* L_val);
-npcg_status cta_gather(Handle* h, cudaStream_t s, const CtaLayout& C, int64_t n, const double* x, double* xp);
-npcg_status cta_trsv_launch(Handle* h, cudaStream_t s, Pattern* P, const CtaLayout& C, const double* rhs_perm,
-                            double* out, double* out2, const SysState* st, bool f32);
+npcg_status cta_gather(Handle* h, cudaStream_t s, const CtaLayout& C, int64_t n, const double* x, void* xp,
+                       bool f32);
+npcg_status cta_trsv_launch(Handle* h, cudaStream_t s, Pattern* P, const CtaLayout& C, const void* rhs_perm,
+                            double* out, void* out2, const SysState* st, bool f32);
 npcg_status trsv_autotune(Handle* h, Pattern* P);
 npcg_status sptrsv_timed_run(Handle* h, Pattern* P, int transpose, const double* r, double* y, int reps,
                              double* ms_per_launch, bool f32);

@@ -90,10 +90,17 @@ struct PcgArgs {
     unsigned* arrive;
     int* ctl;            // [0] n_active [1] flags [2] fwd ticket [3] bwd ticket
     double *x, *r, *z, *y, *w, *b;
-    double* rperm;            // level-synchronous mode: r in forward processing order
+    void* rperm;              // level-synchronous mode: r in forward processing order
     const int32_t* cposf;     //   and the forward position of each row
+    int rperm_f32;            //   stored as FP32 (NPCG_PREC_LLT32) or FP64
     int precond;
 };
+
+__device__ __forceinline__ void store_perm(const PcgArgs& a, int row, double ri) {
+    const int q = a.cposf[row];
+    if (a.rperm_f32) static_cast<float*>(a.rperm)[q] = (float)ri;
+    else static_cast<double*>(a.rperm)[q] = ri;
+}
 
 // sum_j A_ij * v_j for one row by a group of G lanes (row entries strided by G)
 // (every lane of the warp calls this; lanes of an invalid row add nothing)
@@ -123,7 +130,7 @@ __global__ void k_init(PcgArgs a, double rtol, int max_iter, double* p0, double*
             double bi = a.b[row];
             double ri = bi - ax;
             a.r[row] = ri;
-            if (a.rperm) a.rperm[a.cposf[row]] = ri;
+            if (a.rperm) store_perm(a, row, ri);
             p0[row] = 0.0;
             p1[row] = 0.0;
             a.y[row] = sentinel_f64();
@@ -259,7 +266,7 @@ __global__ void k_update(PcgArgs a, const double* __restrict__ p) {
         a.x[row] = fma(alpha, p[row], a.x[row]);
         double ri = fma(-alpha, a.w[row], a.r[row]);
         a.r[row] = ri;
-        if (a.rperm) a.rperm[a.cposf[row]] = ri;
+        if (a.rperm) store_perm(a, row, ri);
         acc[0] = fma(ri, ri, acc[0]);
         if (llt) {
             a.y[row] = sentinel_f64();
@@ -515,8 +522,8 @@ npcg_status ensure_pcg_workspace(Handle* h, Pattern* P) {
     NPCG_CUDA(h, P->st.ensure(P->nsys));
     NPCG_CUDA(h, P->stats_dev.ensure(P->nsys));
     if (P->cfwd.built) {
-        NPCG_CUDA(h, P->r_cf.ensure(P->n + 2));
-        NPCG_CUDA(h, P->y_cb.ensure(P->n + 2));
+        NPCG_CUDA(h, P->r_cf.ensure(P->n + 4));
+        NPCG_CUDA(h, P->y_cb.ensure(P->n + 4));
         NPCG_CUDA(h, P->yglob.ensure(P->n));
     }
     return NPCG_OK;
@@ -542,8 +549,9 @@ PcgArgs pcg_args(Pattern* P, int precond) {
     a.b = P->b.p;
     a.precond = precond;
     const bool cta = P->trsv_mode == kTrsvCta && precond >= NPCG_PREC_LLT;
-    a.rperm = cta ? P->r_cf.p : nullptr;
+    a.rperm = cta ? (void*)P->r_cf.p : nullptr;
     a.cposf = cta ? P->cfwd.cpos.p : nullptr;
+    a.rperm_f32 = precond == NPCG_PREC_LLT32;
     return a;
 }
 
@@ -630,7 +638,7 @@ npcg_status sptrsv_run(Handle* h, Pattern* P, int transpose, const double* r, do
     if (P->trsv_mode == kTrsvCta) {
         NPCG_TRY(ensure_pcg_workspace(h, P));
         const CtaLayout& C = transpose ? P->cbwd : P->cfwd;
-        NPCG_TRY(cta_gather(h, h->stream, C, P->n, r, P->r_cf.p));
+        NPCG_TRY(cta_gather(h, h->stream, C, P->n, r, P->r_cf.p, false));
         return cta_trsv_launch(h, h->stream, P, C, P->r_cf.p, y, nullptr, nullptr, false);
     }
     k_fill_sentinel<<<h->num_sms * 4, 256, 0, h->stream>>>(P->n, y);
@@ -651,7 +659,7 @@ npcg_status sptrsv_timed_run(Handle* h, Pattern* P, int transpose, const double*
         cudaMemsetAsync(P->ctl.p + 1, 0, 3 * sizeof(int), h->stream);
         if (P->trsv_mode == kTrsvCta) {
             const CtaLayout& C = transpose ? P->cbwd : P->cfwd;
-            cta_gather(h, h->stream, C, P->n, r, P->r_cf.p);
+            cta_gather(h, h->stream, C, P->n, r, P->r_cf.p, f32);
             cudaEventRecord(e0, h->stream);
             cta_trsv_launch(h, h->stream, P, C, P->r_cf.p, y, nullptr, nullptr, f32);
         } else {

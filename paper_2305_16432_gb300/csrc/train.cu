@@ -78,18 +78,26 @@ __global__ void k_dL(int64_t nnzL, const int32_t* l2a, const int32_t* erow, cons
     }
 }
 
-// d loss / d s_k for every A entry k = (i, j): one L entry feeds each
+// d loss / d s_k for every A entry k = (i, j): one L entry feeds each.
+// diag_mode 1: L_ii = sqrt(A_ii) is fixed, L_ij = sqrt(A_jj) (s_ij + s_ji)/2.
 __global__ void k_dS(int64_t nnz, const int32_t* erow, const int32_t* ci, const int32_t* mirror,
                      const int32_t* a2l, const int32_t* row_sys, const double* sc, const float* S,
-                     const double* dL, float* dS) {
+                     const double* dL, const double* av, const int32_t* adiag, int diag_mode, float* dS) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz;
          k += (int64_t)gridDim.x * blockDim.x) {
         const int i = erow[k], j = ci[k];
-        const double rs = sqrt(sc[2 * row_sys[i]]);
         double g;
-        if (i == j) g = rs * (1.0 / (1.0 + exp(-(double)S[k]))) * dL[a2l[k]];
-        else if (i > j) g = rs * 0.5 * dL[a2l[k]];
-        else g = rs * 0.5 * dL[a2l[mirror[k]]];
+        if (diag_mode == 1) {
+            // the L entry holding s_k is (max(i,j), min(i,j)); its column scale is sqrt(A_cc)
+            if (i == j) g = 0.0;
+            else if (i > j) g = sqrt(av[adiag[j]]) * 0.5 * dL[a2l[k]];
+            else g = sqrt(av[adiag[i]]) * 0.5 * dL[a2l[mirror[k]]];
+        } else {
+            const double rs = sqrt(sc[2 * row_sys[i]]);
+            if (i == j) g = rs * (1.0 / (1.0 + exp(-(double)S[k]))) * dL[a2l[k]];
+            else if (i > j) g = rs * 0.5 * dL[a2l[k]];
+            else g = rs * 0.5 * dL[a2l[mirror[k]]];
+        }
         dS[k] = (float)g;
     }
 }
@@ -473,6 +481,8 @@ npcg_status train_pair(Handle* h, Pattern* P, const double* A_val, const double*
     GnnBuffers gb{};
     gb.s = T.S;
     gb.sc = sc;
+    gb.av = A_val;
+    gb.diag_mode = cfg->diag_mode;
     NPCG_TRY(gnn_assemble_L(h, P, gb, T.Lv));
     // ---- loss and its adjoint in L
     k_lt_mv<<<grid1(h, n), 256, 0, h->stream>>>(n, P->rp.p, P->ci.p, P->mirror.p, P->a2l.p, T.Lv, x, T.y);
@@ -481,7 +491,7 @@ npcg_status train_pair(Handle* h, Pattern* P, const double* A_val, const double*
     k_lt_mv<<<grid1(h, n), 256, 0, h->stream>>>(n, P->rp.p, P->ci.p, P->mirror.p, P->a2l.p, T.Lv, T.r, T.w);
     k_dL<<<grid1(h, nnzL), 256, 0, h->stream>>>(nnzL, P->l2a.p, P->edge_row.p, P->ci.p, c, T.r, T.y, x, T.w, T.dL);
     k_dS<<<grid1(h, nnz), 256, 0, h->stream>>>(nnz, P->edge_row.p, P->ci.p, P->mirror.p, P->a2l.p, P->row_sys.p,
-                                              sc, T.S, T.dL, T.dS);
+                                              sc, T.S, T.dL, A_val, P->adiag.p, cfg->diag_mode, T.dS);
     NPCG_CUDA(h, cudaGetLastError());
     // ---- decoder
     MlpBwdArgs bw{};
@@ -629,11 +639,6 @@ npcg_status adam_run(Handle* h, int64_t n, float* w, const float* g, float* m, f
     k_adam<<<grid1(h, n), 256, 0, h->stream>>>(n, w, g, m, v, lr, b1, b2, eps, c1, c2);
     NPCG_CUDA(h, cudaGetLastError());
     return NPCG_OK;
-}
-
-npcg_status gnn_forward_bf16_run(Handle* h, Pattern*, const double*, const double*,
-                                 const npcg_gnn_config*, const float*, double*) {
-    return set_error(h, NPCG_EINVAL, "BF16 path is not available in this build");
 }
 
 }  // namespace npcg

@@ -86,14 +86,19 @@ struct StageGeom {
         const int np = pad4(max_np);
         sb = al128((size_t)(kHdrInts + (size_t)np * (2 + max_w)) * 4);
         vb = al128((size_t)np * (1 + max_w) * sizeof(T));
-        rb = al128((size_t)(np + 2) * 8);
+        rb = al128((size_t)(np + 4) * 8);
         stage = sb + vb + rb;
     }
 };
 
+// right-hand-side copies start on a 16-byte boundary: positions rounded down
+// to a multiple of kRhsAl<T> elements
+template <class T>
+__host__ __device__ constexpr int rhs_align() { return 16 / (int)sizeof(T); }
+
 template <bool kWindow, class T>
-__global__ void __launch_bounds__(kCtaThreads) k_trsv_cta(CtaDev D, const double* __restrict__ rhs,
-                                                         double* out, double* out2, double* yglob,
+__global__ void __launch_bounds__(kCtaThreads) k_trsv_cta(CtaDev D, const T* __restrict__ rhs,
+                                                         double* out, T* out2, double* yglob,
                                                          const SysState* st, int* flags) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int sys = blockIdx.x;
@@ -145,8 +150,9 @@ __global__ void __launch_bounds__(kCtaThreads) k_trsv_cta(CtaDev D, const double
                         const int np = pad4(d.y);
                         const uint32_t sbytes = (uint32_t)(kHdrInts + np * (2 + d.z)) * 4;
                         const uint32_t vbytes = (uint32_t)np * (1 + d.z) * sizeof(T);
-                        const int q0e = d.x & ~1;
-                        const uint32_t rbytes = (uint32_t)(((d.x + d.y - q0e) + 1) & ~1) * 8;
+                        constexpr int al = rhs_align<T>();
+                        const int q0e = d.x & ~(al - 1);
+                        const uint32_t rbytes = (uint32_t)(((d.x + d.y - q0e) + al - 1) & ~(al - 1)) * sizeof(T);
                         unsigned char* base = ring + (size_t)s * G.stage;
                         mbar_expect_tx(&full[s], sbytes + vbytes + rbytes);
                         bulk_g2s(base, D.sbuf + so, sbytes, &full[s]);
@@ -182,15 +188,32 @@ __global__ void __launch_bounds__(kCtaThreads) k_trsv_cta(CtaDev D, const double
         const int32_t* sdep = spos2 + np;
         const T* sdinv = reinterpret_cast<const T*>(base + G.sb);
         const T* sval = sdinv + np;
-        const double* srhs = reinterpret_cast<const double*>(base + G.sb + G.vb) + (q0 & 1);
+        const T* srhs = reinterpret_cast<const T*>(base + G.sb + G.vb) + (q0 & (rhs_align<T>() - 1));
         const int t = threadIdx.x;
         if (ok && t < nrows) {
-            T acc = (T)srhs[t];
-            for (int kk = 0; kk < width; ++kk) {
-                const int p = sdep[kk * np + t];
-                if (p >= 0) {
-                    const T yv = kWindow ? win[p & (kWin - 1)] : (T)__ldcg(yglob + p);
-                    acc = fma(-sval[kk * np + t], yv, acc);
+            T acc = srhs[t];
+            if (width <= 4) {
+                // common case: issue every dependency load first, then fold in slot order
+                int p[4];
+                T lv[4], yv[4];
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                    p[kk] = kk < width ? sdep[kk * np + t] : -1;
+                    lv[kk] = kk < width ? sval[kk * np + t] : (T)0;
+                }
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk)
+                    yv[kk] = p[kk] >= 0 ? (kWindow ? win[p[kk] & (kWin - 1)] : (T)__ldcg(yglob + p[kk])) : (T)0;
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk)
+                    if (p[kk] >= 0) acc = fma(-lv[kk], yv[kk], acc);
+            } else {
+                for (int kk = 0; kk < width; ++kk) {
+                    const int pk = sdep[kk * np + t];
+                    if (pk >= 0) {
+                        const T yv = kWindow ? win[pk & (kWin - 1)] : (T)__ldcg(yglob + pk);
+                        acc = fma(-sval[kk * np + t], yv, acc);
+                    }
                 }
             }
             const T y = acc * sdinv[t];
@@ -198,7 +221,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_trsv_cta(CtaDev D, const double
             if (kWindow) win[q & (kWin - 1)] = y;
             else yglob[q] = (double)y;
             if (out) out[srow[t]] = (double)y;
-            if (out2) out2[spos2[t]] = (double)y;
+            if (out2) out2[spos2[t]] = y;
         }
         // every consumer is done with this step (window writes visible, stage
         // free) and all take the same decision: a thread whose wait gave up
@@ -306,10 +329,11 @@ __global__ void k_mark_diag(int nsteps, const int4* steps, const int64_t* voff, 
     }
 }
 
-__global__ void k_gather_perm(int64_t n, const int32_t* cperm, const double* x, double* xp) {
+template <class T>
+__global__ void k_gather_perm(int64_t n, const int32_t* cperm, const double* x, T* xp) {
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
          q += (int64_t)gridDim.x * blockDim.x)
-        xp[q] = x[cperm[q]];
+        xp[q] = (T)x[cperm[q]];
 }
 
 size_t smem_bytes(const CtaLayout& C, int stages, bool f32) {
@@ -458,17 +482,20 @@ npcg_status cta_factor_load(Handle* h, CtaLayout* C, const double* L_val) {
     return NPCG_OK;
 }
 
-npcg_status cta_gather(Handle* h, cudaStream_t s, const CtaLayout& C, int64_t n, const double* x, double* xp) {
+npcg_status cta_gather(Handle* h, cudaStream_t s, const CtaLayout& C, int64_t n, const double* x, void* xp,
+                       bool f32) {
     const int blocks = std::max(1, std::min(ceil_div(n, 256), h->num_sms * 8));
-    k_gather_perm<<<blocks, 256, 0, s>>>(n, C.cperm.p, x, xp);
+    if (f32) k_gather_perm<float><<<blocks, 256, 0, s>>>(n, C.cperm.p, x, static_cast<float*>(xp));
+    else k_gather_perm<double><<<blocks, 256, 0, s>>>(n, C.cperm.p, x, static_cast<double*>(xp));
     return NPCG_OK;
 }
 
-// rhs_perm: right-hand side in this direction's processing order (n + 2
-// entries, last two padding); out (natural order) and/or out2 (positions of
-// the other direction) receive the solution.  f32: FP32 factor and arithmetic.
-npcg_status cta_trsv_launch(Handle* h, cudaStream_t s, Pattern* P, const CtaLayout& C, const double* rhs_perm,
-                            double* out, double* out2, const SysState* st, bool f32) {
+// rhs_perm: right-hand side in this direction's processing order (n + 4
+// entries of the value type, the last ones padding); out (natural order,
+// FP64) and/or out2 (positions of the other direction, value type) receive
+// the solution.  f32: FP32 factor, arithmetic, right-hand side and out2.
+npcg_status cta_trsv_launch(Handle* h, cudaStream_t s, Pattern* P, const CtaLayout& C, const void* rhs_v,
+                            double* out, void* out2_v, const SysState* st, bool f32) {
     const int stages = stages_for(C, f32);
     if (stages < 2) return set_error(h, NPCG_EINVAL, "level-synchronous layout does not fit shared memory");
     CtaDev d;
@@ -484,11 +511,15 @@ npcg_status cta_trsv_launch(Handle* h, cudaStream_t s, Pattern* P, const CtaLayo
     const size_t smem = smem_bytes(C, stages, f32);
     int* flags = P->ctl.p + 1;
     if (f32) {
-        if (C.window_ok) k_trsv_cta<true, float><<<P->nsys, kCtaThreads, smem, s>>>(d, rhs_perm, out, out2, nullptr, st, flags);
-        else k_trsv_cta<false, float><<<P->nsys, kCtaThreads, smem, s>>>(d, rhs_perm, out, out2, P->yglob.p, st, flags);
+        const float* rp = static_cast<const float*>(rhs_v);
+        float* o2 = static_cast<float*>(out2_v);
+        if (C.window_ok) k_trsv_cta<true, float><<<P->nsys, kCtaThreads, smem, s>>>(d, rp, out, o2, nullptr, st, flags);
+        else k_trsv_cta<false, float><<<P->nsys, kCtaThreads, smem, s>>>(d, rp, out, o2, P->yglob.p, st, flags);
     } else {
-        if (C.window_ok) k_trsv_cta<true, double><<<P->nsys, kCtaThreads, smem, s>>>(d, rhs_perm, out, out2, nullptr, st, flags);
-        else k_trsv_cta<false, double><<<P->nsys, kCtaThreads, smem, s>>>(d, rhs_perm, out, out2, P->yglob.p, st, flags);
+        const double* rp = static_cast<const double*>(rhs_v);
+        double* o2 = static_cast<double*>(out2_v);
+        if (C.window_ok) k_trsv_cta<true, double><<<P->nsys, kCtaThreads, smem, s>>>(d, rp, out, o2, nullptr, st, flags);
+        else k_trsv_cta<false, double><<<P->nsys, kCtaThreads, smem, s>>>(d, rp, out, o2, P->yglob.p, st, flags);
     }
     NPCG_CUDA(h, cudaGetLastError());
     return NPCG_OK;

@@ -86,10 +86,10 @@ def lib():
                 "npcg_spmv": [vp, vp, vp, vp, vp],
                 "npcg_factor_load": [vp, vp, vp],
                 "npcg_sptrsv": [vp, vp, i32, vp, vp],
-                "npcg_sptrsv_timed": [vp, vp, i32, vp, vp, i32, C.POINTER(dbl)],
+                "npcg_sptrsv_timed": [vp, vp, i32, i32, vp, vp, i32, C.POINTER(dbl)],
                 "npcg_loss_and_grad": [vp, vp, vp, i32, vp, vp, C.POINTER(_Cfg), vp, C.POINTER(dbl), vp],
                 "npcg_adam_step": [vp, i64, vp, vp, vp, vp, i32, f32, f32, f32, f32],
-                "npcg_solve_host": [vp, vp, i32, C.POINTER(_Cfg), vp, vp, vp, vp, dbl, i32, vp],
+                "npcg_solve_host": [vp, vp, i32, C.POINTER(_Cfg), vp, vp, vp, vp, dbl, i32, i32, vp],
             }
             for name, args in sig.items():
                 fn = getattr(L, name)
@@ -321,13 +321,14 @@ def sptrsv(P: Pattern, r, transpose=False, out=None):
     return y
 
 
-def sptrsv_timed(P: Pattern, r, transpose=False, reps=20, out=None):
-    """Mean duration (ms) of the triangular-solve kernel over reps launches."""
+def sptrsv_timed(P: Pattern, r, transpose=False, reps=20, out=None, f32=False):
+    """Mean duration (ms) of the triangular-solve kernel over reps launches
+    (f32: FP32 factor and arithmetic, as in PREC_LLT32)."""
     r = _dev(r, torch.float64, "r")
     y = out if out is not None else torch.empty_like(r)
     ms = C.c_double()
-    P.h.check(lib().npcg_sptrsv_timed(P.h.h, P.p, 1 if transpose else 0, _ptr(r), _ptr(y), int(reps),
-                                      C.byref(ms)))
+    P.h.check(lib().npcg_sptrsv_timed(P.h.h, P.p, 1 if transpose else 0, 1 if f32 else 0, _ptr(r), _ptr(y),
+                                      int(reps), C.byref(ms)))
     return ms.value, y
 
 
@@ -357,7 +358,7 @@ def adam_step(w, g, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, h: Handl
 
 def solve_host(P: Pattern, A_val_host: np.ndarray, b_host: np.ndarray, method=METHOD_GNN,
                cfg: I.GnnConfig | None = None, weights=None, precision=FP32, rtol=1e-6, max_iter=None,
-               x_host: np.ndarray | None = None):
+               x_host: np.ndarray | None = None, f32_apply=False):
     """End to end from host buffers: copy in, build the preconditioner, PCG, copy x out."""
     x = x_host if x_host is not None else np.empty(P.n, np.float64)
     c = _cfg(cfg, precision) if cfg is not None else None
@@ -368,7 +369,35 @@ def solve_host(P: Pattern, A_val_host: np.ndarray, b_host: np.ndarray, method=ME
                                _ptr(weights) if weights is not None else None,
                                A_val_host.ctypes.data_as(C.c_void_p), b_host.ctypes.data_as(C.c_void_p),
                                x.ctypes.data_as(C.c_void_p), float(rtol), int(max_iter),
-                               C.cast(stats, C.c_void_p))
+                               1 if f32_apply else 0, C.cast(stats, C.c_void_p))
     if st not in (NPCG_OK, NPCG_EMAXITER, NPCG_EBREAKDOWN):
         P.h.check(st)
     return x, _stats_list(stats)
+
+
+class LlTLoss(torch.autograd.Function):
+    """Loss Eq. (loss_Ab), mean over pairs of ||L L^T x_p - b_p||^2 with
+    L = f_theta(A, b_p), as a differentiable function of the flat FP32 weights.
+
+    forward runs the network and the loss on the GPU and keeps the gradient
+    that the same call computed with the hand-written adjoint (Sec. 4.3:
+    the loss, its derivative in L, then the decoder, message-passing layers
+    and encoders in reverse, with per-tile recomputation); backward only
+    scales it by the incoming gradient.  A and the (x, b) pairs are data.
+    """
+
+    @staticmethod
+    def forward(ctx, weights, P, A_val, X, B, cfg, precision=FP32):
+        loss, g = loss_and_grad(P, A_val, X, B, cfg, weights.detach(), precision=precision)
+        ctx.save_for_backward(g)
+        return torch.tensor(loss, dtype=torch.float64, device=weights.device)
+
+    @staticmethod
+    def backward(ctx, gout):
+        (g,) = ctx.saved_tensors
+        return (g * gout.to(g.dtype)), None, None, None, None, None, None
+
+
+def llt_loss(weights, P: Pattern, A_val, X, B, cfg: I.GnnConfig, precision=FP32):
+    """Differentiable loss: ``llt_loss(w, ...).backward()`` fills ``w.grad``."""
+    return LlTLoss.apply(weights, P, A_val, X, B, cfg, precision)

@@ -204,6 +204,7 @@ def test_malformed_patterns_rejected(N):
     (I.GnnConfig(n_mp=6, l=2, l_mp=2, h=64), I.fem2d(22, sigma=1.0, seed=9)),
     (I.GnnConfig(n_mp=3, l=1, l_mp=3, h=32), I.fd3d(7, 6, 5, sigma=1.0, seed=2)),
     (I.GnnConfig(n_mp=0, l=2, l_mp=2, h=16), I.fd2d(12, 9, sigma=1.0, seed=1)),
+    (I.GnnConfig(n_mp=3, l=2, l_mp=2, h=64, diag_mode=1), I.fem2d(18, sigma=1.0, seed=3)),
 ])
 def test_gnn_fp32_parity(N, cfg, prob):
     Ao, (rp, ci, v) = _assemble_both(N, prob)
@@ -360,3 +361,58 @@ def test_fp32_preconditioner_apply(N, name, mode):
     assert st[0]["status"] == 0
     assert abs(st[0]["iters"] - ito) <= max(1, int(np.ceil(0.05 * ito)))
     assert np.linalg.norm(b - O.spmv(Ao, _np(xg))) / np.linalg.norm(b) <= 2e-8
+
+
+@pytest.mark.parametrize("prob", [I.fem2d(22, sigma=1.0, seed=9), I.fd3d(9, 8, 7, sigma=1.0, seed=2),
+                                  I.poisson2d_32()])
+@pytest.mark.parametrize("diag_mode", [0, 1])
+def test_gnn_bf16_parity(N, prob, diag_mode):
+    # BF16 tensor-core MLPs with FP32 accumulation: L within 2e-2 of the FP64
+    # oracle in relative Frobenius norm and in max-abs relative to max |L|
+    cfg = I.GnnConfig(n_mp=6, l=2, l_mp=2, h=64, diag_mode=diag_mode)
+    Ao, (rp, ci, v) = _assemble_both(N, prob)
+    P = N.analyse(rp, ci)
+    b = I.rhs(Ao.n, 12)
+    w = I.gnn_weights(cfg, 4)
+    Lo = O.gnn_forward(cfg, Ao, b, w)
+    Lb = _np(N.gnn_factor(P, v, _gpu(b), cfg, _gpu(w, torch.float32), precision=N.BF16))
+    d = Lb - Lo.val
+    assert np.linalg.norm(d) / np.linalg.norm(Lo.val) <= 2e-2
+    assert np.abs(d).max() <= 2e-2 * np.abs(Lo.val).max()
+    # and the preconditioner it gives: iterations within 10 % of the FP64 factor's
+    xo, ito, _, _ = O.pcg(Ao, b, O.PREC_LLT, Lo, rtol=1e-6)
+    xg, st = N.pcg_solve(P, v, _gpu(b), N.PREC_LLT, _gpu(Lb), rtol=1e-6)
+    assert st[0]["status"] == 0 and abs(st[0]["iters"] - ito) <= max(1, int(np.ceil(0.1 * ito)))
+
+
+def test_batched_uneven_48_systems_sampled(N):
+    # 48 systems of uneven size (2-D FEM and 3-D FD, the mix of the batched
+    # workload at reduced sizes) in one batched solve under the device-side
+    # loop; every member converges, and sampled members match the oracle
+    probs = I.batched_mix(48, seed=3, n_lo=300, n_hi=3000, s_lo=5, s_hi=12)
+    rps, cis, vs, bs, sys_ptr = [], [], [], [], [0]
+    off_n = off_nnz = 0
+    for k, p in enumerate(probs):
+        rp, ci, v = N.assemble_system(p)
+        rps.append(_np(rp)[:-1] + off_nnz)
+        cis.append(_np(ci) + off_n)
+        vs.append(_np(v))
+        n = rp.numel() - 1
+        bs.append(I.rhs(n, 500 + k))
+        off_n += n
+        off_nnz += ci.numel()
+        sys_ptr.append(off_n)
+    P = N.analyse(_gpu(np.concatenate(rps + [[off_nnz]]), torch.int32), _gpu(np.concatenate(cis), torch.int32),
+                  sys_ptr)
+    assert P.nsys == 48
+    v_cat = _gpu(np.concatenate(vs))
+    Lg, alpha = N.ic0_factor(P, v_cat)
+    x, st = N.pcg_solve(P, v_cat, _gpu(np.concatenate(bs)), N.PREC_LLT, Lg, rtol=1e-8)
+    assert all(s["status"] == 0 and s["relres"] <= 1e-8 for s in st)
+    xs = _np(x)
+    for k in (0, 1, 17, 46, 47):
+        Ao = O.assemble(probs[k])
+        xo, ito, _, _ = O.pcg(Ao, bs[k], O.PREC_LLT, O.ic0(Ao)[0], rtol=1e-8)
+        assert abs(st[k]["iters"] - ito) <= 1
+        seg = xs[sys_ptr[k]:sys_ptr[k + 1]]
+        assert np.linalg.norm(seg - xo) / np.linalg.norm(xo) <= 1e-8

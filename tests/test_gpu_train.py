@@ -39,6 +39,7 @@ def _pairs(A, k, seed):
     (I.GnnConfig(n_mp=3, l=1, l_mp=2, h=32), I.fd2d(6, 5, sigma=1.0, seed=4)),
     (I.GnnConfig(n_mp=2, l=2, l_mp=2, h=64), I.fem2d(12, sigma=1.0, seed=5)),
     (I.GnnConfig(n_mp=0, l=2, l_mp=2, h=16), I.fd3d(4, 3, 3, sigma=1.0, seed=6)),
+    (I.GnnConfig(n_mp=2, l=2, l_mp=2, h=32, diag_mode=1), I.fem2d(9, sigma=1.0, seed=7)),
 ])
 def test_loss_and_grad_parity(N, cfg, prob):
     om, ph = I.grf_features(prob)
@@ -100,3 +101,23 @@ def test_adam_matches_oracle(N):
         N.adam_step(wg, _gpu(grad, torch.float32), mg, vg, t)
     torch.cuda.synchronize()
     assert np.abs(wg.cpu().numpy() - wo).max() <= 1e-6
+
+
+def test_autograd_function_matches_oracle_gradient(N):
+    """The adjoint behind torch.autograd: backward() leaves the oracle's FP64
+    gradient (scaled by the incoming gradient) in w.grad."""
+    cfg = I.GnnConfig(n_mp=2, l=2, l_mp=2, h=32)
+    prob = I.fem2d(10, sigma=1.0, seed=11)
+    om, ph = I.grf_features(prob)
+    Ao = O.assemble(prob, om, ph)
+    rp, ci, v = N.assemble_system(prob, om, ph)
+    P = N.analyse(rp, ci)
+    X, B = _pairs(Ao, 2, 23)
+    w = I.gnn_weights(cfg, 4, scale=1.5)
+    lo, go = O.loss_and_grad(cfg, Ao, X, B, w.astype(np.float64))
+    wt = _gpu(w, torch.float32).requires_grad_(True)
+    loss = N.llt_loss(wt, P, v, _gpu(X), _gpu(B), cfg)
+    (3.0 * loss).backward()
+    assert abs(loss.item() - lo) <= 1e-5 * abs(lo)
+    gg = wt.grad.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(gg - 3.0 * go) / np.linalg.norm(3.0 * go) <= 1e-4
