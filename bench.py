@@ -121,33 +121,29 @@ def _load_weights(cfg, path):
 
 
 def _strip(Ao, frac):
-    """Leading principal block (the first rows of the lexicographic lattice)."""
+    """Leading principal block (the first rows of the lexicographic order)."""
     import oracle as O
     m = max(2, int(Ao.n * frac))
-    rp, ci, v = [0], [], []
-    for i in range(m):
-        s, e = Ao.row_ptr[i], Ao.row_ptr[i + 1]
-        cols = Ao.col_idx[s:e]
-        keep = cols < m
-        ci.extend(cols[keep].tolist())
-        v.extend(Ao.val[s:e][keep].tolist())
-        rp.append(len(ci))
-    return O.CSR(rp, ci, v)
+    e = int(Ao.row_ptr[m])
+    rows = np.repeat(np.arange(m), np.diff(Ao.row_ptr[:m + 1]))
+    keep = Ao.col_idx[:e] < m
+    rp = np.concatenate([[0], np.cumsum(np.bincount(rows[keep], minlength=m))])
+    return O.CSR(rp, Ao.col_idx[:e][keep], Ao.val[:e][keep])
 
 
-def oracle_estimate(prob, cfg, w, b, learned_iters, budget_frac=1.0 / 16):
-    """Oracle (CPU, FP64, 1 thread) cost of the learned path on the full
-    system: network forward timed on a strip of the mesh (budget_frac of the
-    rows) scaled by nnz, plus PCG: per-iteration oracle cost on the full
-    system (same factor pattern) times the learned path's iteration count."""
+def oracle_estimate(Ao, cfg, w, b, learned_iters, strip_nnz=6000):
+    """Oracle (CPU, FP64, 1 thread) cost of the learned path on one system:
+    network forward timed on a strip of about strip_nnz nonzeros (the
+    leading rows) scaled by nnz, plus PCG: per-iteration oracle cost on the
+    full system (same factor pattern) times the learned path's iteration
+    count.  Returns (ms, sample description)."""
     import oracle as O
-    Ao = O.assemble(prob)
-    S = _strip(Ao, budget_frac)
+    S = _strip(Ao, min(1.0, strip_nnz / max(1, Ao.nnz)))
     t0 = time.perf_counter()
     O.gnn_forward(cfg, S, b[:S.n], w)
     t_gnn = (time.perf_counter() - t0) * Ao.nnz / S.nnz
     L, _ = O.ic0(Ao)
-    k = 30
+    k = 10
     t0 = time.perf_counter()
     O.pcg(Ao, b, O.PREC_LLT, L, rtol=0.0, max_iter=k)
     t_it = (time.perf_counter() - t0) / k
@@ -158,22 +154,67 @@ def oracle_estimate(prob, cfg, w, b, learned_iters, budget_frac=1.0 / 16):
     return ms, sample
 
 
+def _host_csr(P_rp, P_ci, v):
+    import oracle as O
+    return O.CSR(P_rp.cpu().numpy(), P_ci.cpu().numpy(), v.cpu().numpy())
+
+
+SOLVE_WORKLOADS = ("fem2d_256", "fd3d_128", "batched_256")
+
+
+def _problems(I, workload, rank):
+    if workload == "fem2d_256":
+        return [I.fem2d_256(seed=rank)]
+    if workload == "fd3d_128":
+        return [I.fd3d_128(seed=rank)]
+    return I.batched_mix(256, seed=rank)
+
+
+def _assemble(N, I, probs, rank):
+    """Assemble every system on the GPU; one concatenated pattern."""
+    import torch
+    rps, cis, vs, bs, sys_ptr = [], [], [], [], [0]
+    off_n = off_nnz = 0
+    for k, p in enumerate(probs):
+        rp, ci, v = N.assemble_system(p)
+        n = rp.numel() - 1
+        rps.append(rp[:-1] + off_nnz)
+        cis.append(ci + off_n)
+        vs.append(v)
+        bs.append(I.rhs(n, 1000 * rank + k))
+        off_n += n
+        off_nnz += ci.numel()
+        sys_ptr.append(off_n)
+    rp_cat = torch.cat(rps + [torch.tensor([off_nnz], dtype=torch.int32, device=rps[0].device)])
+    ci_cat, v_cat = torch.cat(cis), torch.cat(vs)
+    b = torch.as_tensor(np.concatenate(bs), device=v_cat.device)
+    return rp_cat, ci_cat, v_cat, b, sys_ptr
+
+
 def run_reference(args):
+    """The oracle as it stands, timed on the host cores on a bounded sample of
+    the same workload (rank 0 only)."""
     rank, world, _ = _dist()
     if rank != 0:
         return
     import oracle as O
     from paper_2305_16432_gb300 import inputs as I
     O.build()
+    if args.workload not in ("fem2d_256",):
+        print(json.dumps({"impl": "reference", "unavailable": "oracle reference arm is defined for fem2d_256"}))
+        return
     prob = I.fem2d_256(seed=0)
     cfg = I.GnnConfig(n_mp=6, l=2, l_mp=2, h=64)
     w, kind, meta = _load_weights(cfg, os.path.join(WEIGHTS_DIR, "fem2d_6x64.npy"))
+    if meta.get("config"):
+        cfg = I.GnnConfig(**meta["config"])
+    Ao = O.assemble(prob)
     b = I.rhs(prob.n, 0)
     iters = int(meta.get("learned_iters_fem256", 0)) or 191
     vals = []
     sample = ""
     for s in range(args.warmup + args.steps):
-        ms, sample = oracle_estimate(prob, cfg, w, b, iters, budget_frac=1.0 / 64)
+        ms, sample = oracle_estimate(Ao, cfg, w, b, iters)
         if s >= args.warmup:
             vals.append(ms)
     v = float(np.mean(vals))
@@ -186,12 +227,258 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _timed(fn, k, stream, flush):
+    import torch
+    ms, last = [], None
+    for _ in range(k):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        last = fn()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return ms, last
+
+
+def _spmv_roofline(N, P, v, hbm, reps=50):
+    """SpMV y = A x, back-to-back launches between CUDA events (the kernel is
+    HBM-bound; a secondary roofline beside the triangular solve)."""
+    import torch
+    x = torch.randn(P.n, dtype=torch.float64, device=v.device)
+    y = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        N.spmv(P, v, x, out=y)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        N.spmv(P, v, x, out=y)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    byts = 12 * P.nnz + 4 * (P.n + 1) + 16 * P.n
+    ach = byts / (ms * 1e-3) / 1e9
+    return {"kernel": "k_spmv_plain (SpMV, FP64)", "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+            "frac": ach / hbm, "bytes_per_launch": byts, "ms_per_launch": ms}
+
+
+def run_solve(args, rank, world, local):
+    import torch
+    from paper_2305_16432_gb300 import inputs as I
+    from paper_2305_16432_gb300 import npcg as N
+
+    prec = N.BF16 if args.precision == "bf16" else N.FP32
+    cfg = I.GnnConfig(n_mp=6, l=2, l_mp=2, h=64)
+    w_np, wkind, wmeta = _load_weights(cfg, args.weights)
+    if wmeta.get("config"):
+        cfg = I.GnnConfig(**wmeta["config"])
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    probs = _problems(I, args.workload, rank)
+    rp, ci, v, b, sys_ptr = _assemble(N, I, probs, rank)
+    P = N.analyse(rp, ci, sys_ptr if len(probs) > 1 else None)
+    nsys = P.nsys
+    w = torch.as_tensor(w_np, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
+
+    apply32 = args.apply == "fp32"
+    pc = N.PREC_LLT32 if apply32 else N.PREC_LLT
+
+    def learned_step():
+        L = N.gnn_factor(P, v, b, cfg, w, precision=prec)
+        x, st = N.pcg_solve(P, v, b, pc, L, rtol=RTOL)
+        return st
+
+    def ic0_step():
+        L, _ = N.ic0_factor(P, v)
+        x, st = N.pcg_solve(P, v, b, pc, L, rtol=RTOL)
+        return st
+
+    for _ in range(args.warmup):
+        learned_step()
+        ic0_step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    ms_l, st_l = _timed(learned_step, args.steps, stream, flush)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    if world > 1:
+        torch.distributed.barrier()
+    ms_i, st_i = _timed(ic0_step, args.steps, stream, flush)
+    ms_per_step = float(np.sum(ms_l)) / args.steps
+    if world > 1:
+        t = torch.tensor([ms_per_step], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_per_step = float(t.item())
+    value = ms_per_step / (nsys * world)
+    it_l = [s["iters"] for s in st_l]
+    it_i = [s["iters"] for s in st_i]
+    assert all(s["status"] == 0 for s in st_l + st_i), "a system did not converge"
+
+    # dominant kernel: the level-ordered triangular solve, timed alone
+    hbm, bf16, peak_kind = _peaks()
+    Lic, _ = N.ic0_factor(P, v)
+    N.factor_load(P, Lic)
+    r = torch.randn(P.n, dtype=torch.float64, device=dev)
+    trsv_ms, _ = N.sptrsv_timed(P, r, transpose=False, reps=args.trsv_reps, f32=apply32)
+    # SpTRSV bytes per launch: index + value per L entry, row pointer, rhs + solution
+    trsv_bytes = (8 if apply32 else 12) * P.nnz_L + 4 * (P.n + 1) + 16 * P.n
+    achieved = trsv_bytes / (trsv_ms * 1e-3) / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "trsv_traffic.json")
+    if os.path.exists(prof):
+        traffic = json.load(open(prof)).get(args.workload + "_fwd_bytes")
+    spmv_rl = _spmv_roofline(N, P, v, hbm)
+
+    # end to end through the C ABI with host buffers (pinned)
+    a_host = torch.empty(P.nnz, dtype=torch.float64, pin_memory=True)
+    a_host.copy_(v.cpu())
+    b_host = torch.empty(P.n, dtype=torch.float64, pin_memory=True)
+    b_host.copy_(b.cpu())
+    x_host = torch.empty(P.n, dtype=torch.float64, pin_memory=True)
+    ts = []
+    for k in range(args.warmup + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        N.solve_host(P, a_host.numpy(), b_host.numpy(), method=N.METHOD_GNN, cfg=cfg, weights=w,
+                     precision=prec, rtol=RTOL, x_host=x_host.numpy(), f32_apply=apply32)
+        ts.append(time.perf_counter() - t0)
+    e2e_ms = 1e3 * float(np.mean(ts[args.warmup:])) / (nsys * world)
+    h2d = 8 * (P.nnz + P.n)
+    d2h = 8 * P.n
+
+    # kernel launches per learned step (counted from the launch structure):
+    # network: scales, 2 encoders, 2 per layer, decoder, L assembly
+    gnn_launches = 1 + 2 + 2 * cfg.n_mp + 1 + 1
+    # PCG: 4 factor loads, init, 2 solves, r^T z, 11 per graph trip (2 iterations
+    # of 5 kernels + the loop condition), stats
+    trips = max(1, math.ceil(max(it_l) / 2))
+    pcg_launches = 4 + 1 + 2 + 1 + 11 * trips + 1
+    launches = (gnn_launches + pcg_launches) * args.steps
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle as O
+        O.build()
+        bh = b.cpu().numpy()
+        rph, cih, vh = rp.cpu().numpy(), ci.cpu().numpy(), v.cpu().numpy()
+        # a bounded sample: up to three members of the workload, scaled by nnz
+        members = list(range(nsys)) if nsys <= 3 else [0, nsys // 2, nsys - 1]
+        tot_ms, nnz_s, samples = 0.0, 0, []
+        for k in members:
+            r0, r1 = sys_ptr[k], sys_ptr[k + 1]
+            e0, e1 = int(rph[r0]), int(rph[r1])
+            Ao = O.CSR(rph[r0:r1 + 1] - e0, cih[e0:e1] - r0, vh[e0:e1])
+            ms_k, smp = oracle_estimate(Ao, cfg, w_np, bh[r0:r1], it_l[k])
+            tot_ms += ms_k
+            nnz_s += Ao.nnz
+            samples.append(smp)
+        ms_cpu = tot_ms * (P.nnz / nnz_s) / nsys
+        smp = samples[0] if nsys == 1 else (
+            f"{len(members)} of {nsys} members, each: " + samples[0] + "; scaled by nnz to the batch, per system")
+        cpu = {"value": ms_cpu, "unit": "ms/system", "cores": 1, "kind": "oracle", "sample": smp}
+
+    if rank == 0:
+        wl = {"fem2d_256": "fem2d_256_learned_pcg", "fd3d_128": "fd3d_128_learned_pcg",
+              "batched_256": "batched_256_learned_pcg"}[args.workload]
+        line = {
+            "metric": METRIC, "value": value, "unit": "ms/system", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64+" + args.precision, "data": "synthetic",
+            "config": {"workload": wl, "systems_per_step": nsys, "n": P.n, "nnz": P.nnz, "nnz_L": P.nnz_L,
+                       "levels": P.nlev_fwd, "gnn": f"n_mp={cfg.n_mp},l={cfg.l},l_mp={cfg.l_mp},h={cfg.h},"
+                       f"diag_mode={cfg.diag_mode}," + args.precision,
+                       "weights": wkind, "pcg": "fp64 recurrences, " + args.apply + " L L^T solves",
+                       "rtol": RTOL, "l2": "flushed between steps (256 MB write)"},
+            "compare": {"learned_iters": it_l if nsys > 1 else it_l[0],
+                        "learned_ms_median": float(np.median(ms_l)),
+                        "ic0_ms_per_system": float(np.mean(ms_i)) / nsys, "ic0_iters": it_i if nsys > 1 else it_i[0],
+                        "wall_s_timed": wall,
+                        "trsv_design": "levelsync" if P.trsv_mode == N.TRSV_LEVELSYNC else "syncfree",
+                        "trsv_tuned_ms_fwd_bwd": P.tuned_ms},
+            "roofline": {"kernel": ("k_trsv_cta" if P.trsv_mode == N.TRSV_LEVELSYNC else "k_trsv")
+                         + " (forward SpTRSV, " + args.apply + ")", "bound": "hbm",
+                         "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                         "peak_kind": peak_kind, "traffic": traffic, "bytes_per_launch": trsv_bytes,
+                         "ms_per_launch": trsv_ms, "levels": P.nlev_fwd},
+            "roofline_spmv": dict(spmv_rl, peak_kind=peak_kind),
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_ms, "unit": "ms/system", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+
+
+def run_train(args, rank, world, local):
+    """One training step of the method: loss Eq. (loss_Ab) over 32 systems x
+    8 (x, b) pairs through the network (BF16 tensor-core forward, FP32
+    adjoint) and one Adam step on the FP32 master weights."""
+    import torch
+    from paper_2305_16432_gb300 import inputs as I
+    from paper_2305_16432_gb300 import npcg as N
+    prec = N.BF16 if args.precision == "bf16" else N.FP32
+    cfg = I.GnnConfig(n_mp=6, l=2, l_mp=2, h=64)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    probs = I.training_mix(32, seed=1000 + 100 * rank)
+    rp, ci, v, _, sys_ptr = _assemble(N, I, probs, rank)
+    P = N.analyse(rp, ci, sys_ptr)
+    pairs = 8
+    Bm = torch.as_tensor(np.stack([I.rhs(P.n, 5000 + 37 * rank + q) for q in range(pairs)]), device=dev)
+    Xm = torch.empty_like(Bm)
+    Lic, _ = N.ic0_factor(P, v)
+    for q in range(pairs):
+        Xm[q], _ = N.pcg_solve(P, v, Bm[q], N.PREC_LLT, Lic, rtol=1e-12, raise_on_fail=True)
+    w = torch.as_tensor(I.gnn_weights(cfg, 2023), device=dev)
+    m = torch.zeros_like(w)
+    vv = torch.zeros_like(w)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    state = {"t": 0}
+
+    def step():
+        loss, g = N.loss_and_grad(P, v, Xm, Bm, cfg, w, precision=prec)
+        state["t"] += 1
+        N.adam_step(w, g, m, vv, state["t"])
+        return loss
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms, loss = _timed(step, args.steps, stream, flush)
+    clk = clocks.stop()
+    ms_per_step = float(np.mean(ms))
+    if rank == 0:
+        line = {"metric": "ms per training step (32 systems x 8 pairs, loss + adjoint + Adam)",
+                "value": ms_per_step, "unit": "ms/step", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32+" + args.precision, "data": "synthetic",
+                "config": {"workload": "train_32x8", "n": P.n, "nnz": P.nnz, "systems": 32, "pairs": pairs,
+                           "gnn": "n_mp=6,l=2,l_mp=2,h=64", "l2": "flushed between steps (256 MB write)"},
+                "loss_last": loss, "roofline": None, "cpu_baseline": None, "e2e": None, "clocks": clk}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="fem2d_256", choices=list(SOLVE_WORKLOADS) + ["train_32"],
+                    help="fem2d_256 (the headline line), fd3d_128, batched_256 or train_32")
     ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16"],
                     help="network arithmetic: BF16 tensor cores (default) or FP32")
     ap.add_argument("--apply", default="fp32", choices=["fp32", "fp64"],
@@ -212,151 +499,11 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2305_16432_gb300 import build as B
-    from paper_2305_16432_gb300 import inputs as I
     B.build()
-    from paper_2305_16432_gb300 import npcg as N
-
-    prec = N.BF16 if args.precision == "bf16" else N.FP32
-    prob = I.fem2d_256(seed=rank)
-    cfg = I.GnnConfig(n_mp=6, l=2, l_mp=2, h=64)
-    w_np, wkind, wmeta = _load_weights(cfg, args.weights)
-    if wmeta.get("config", {}).get("diag_mode", 0):
-        cfg = I.GnnConfig(n_mp=6, l=2, l_mp=2, h=64, diag_mode=int(wmeta["config"]["diag_mode"]))
-    dev = torch.device("cuda", local)
-    stream = torch.cuda.current_stream()
-    rp, ci, v = N.assemble_system(prob)
-    P = N.analyse(rp, ci)
-    b = torch.as_tensor(I.rhs(P.n, rank), device=dev)
-    w = torch.as_tensor(w_np, device=dev)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
-
-    apply32 = args.apply == "fp32"
-    pc = N.PREC_LLT32 if apply32 else N.PREC_LLT
-
-    def learned_step():
-        L = N.gnn_factor(P, v, b, cfg, w, precision=prec)
-        x, st = N.pcg_solve(P, v, b, pc, L, rtol=RTOL)
-        return st[0]
-
-    def ic0_step():
-        L, _ = N.ic0_factor(P, v)
-        x, st = N.pcg_solve(P, v, b, pc, L, rtol=RTOL)
-        return st[0]
-
-    def timed(fn, k):
-        ms, last = [], None
-        for _ in range(k):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            last = fn()
-            e1.record(stream)
-            e1.synchronize()
-            ms.append(e0.elapsed_time(e1))
-        return ms, last
-
-    for _ in range(args.warmup):
-        learned_step()
-        ic0_step()
-    torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-    clocks = ClockSampler(local)
-    clocks.start()
-    torch.cuda.synchronize()
-    t_wall = time.perf_counter()
-    ms_l, st_l = timed(learned_step, args.steps)
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - t_wall
-    clk = clocks.stop()
-    if world > 1:
-        torch.distributed.barrier()
-    ms_i, st_i = timed(ic0_step, args.steps)
-    ms_per_step = float(np.sum(ms_l)) / args.steps
-    if world > 1:
-        t = torch.tensor([ms_per_step], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_per_step = float(t.item())
-    value = ms_per_step / world
-
-    # dominant kernel: the level-ordered triangular solve, timed alone
-    hbm, bf16, peak_kind = _peaks()
-    Lic, _ = N.ic0_factor(P, v)
-    N.factor_load(P, Lic)
-    r = torch.randn(P.n, dtype=torch.float64, device=dev)
-    trsv_ms, _ = N.sptrsv_timed(P, r, transpose=False, reps=args.trsv_reps, f32=apply32)
-    # SpTRSV bytes per launch: index + value per L entry, row pointer, rhs + solution
-    trsv_bytes = (8 if apply32 else 12) * P.nnz_L + 4 * (P.n + 1) + 16 * P.n
-    achieved = trsv_bytes / (trsv_ms * 1e-3) / 1e9
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "trsv_traffic.json")
-    if os.path.exists(prof):
-        traffic = json.load(open(prof)).get("fem2d_256_fwd_bytes")
-
-    # end to end through the C ABI with host buffers
-    e2e_ms = None
-    h2d = d2h = 0
-    if True:
-        a_host = torch.empty(P.nnz, dtype=torch.float64, pin_memory=True)
-        a_host.copy_(v.cpu())
-        b_host = torch.empty(P.n, dtype=torch.float64, pin_memory=True)
-        b_host.copy_(b.cpu())
-        x_host = torch.empty(P.n, dtype=torch.float64, pin_memory=True)
-        ts = []
-        for k in range(args.warmup + args.steps):
-            flush.zero_()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            N.solve_host(P, a_host.numpy(), b_host.numpy(), method=N.METHOD_GNN, cfg=cfg, weights=w,
-                         precision=prec, rtol=RTOL, x_host=x_host.numpy(), f32_apply=apply32)
-            ts.append(time.perf_counter() - t0)
-        e2e_ms = 1e3 * float(np.mean(ts[args.warmup:])) / world
-        h2d = 8 * (P.nnz + P.n)
-        d2h = 8 * P.n
-
-    # kernel launches per learned step (counted from the launch structure)
-    it = st_l["iters"]
-    # network: scales, 2 encoders, 2 per layer, decoder, L assembly
-    gnn_launches = 1 + 2 + 2 * cfg.n_mp + 1 + 1
-    # PCG: 4 factor loads, init, 2 solves, r^T z, 11 per graph trip (2 iterations
-    # of 5 kernels + the loop condition), stats
-    trips = max(1, math.ceil(it / 2))
-    pcg_launches = 4 + 1 + 2 + 1 + 11 * trips + 1
-    launches = (gnn_launches + pcg_launches) * args.steps
-
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        import oracle as O
-        O.build()
-        ms_cpu, sample = oracle_estimate(prob, cfg, w_np, I.rhs(P.n, 0), it, budget_frac=1.0 / 64)
-        cpu = {"value": ms_cpu, "unit": "ms/system", "cores": 1, "kind": "oracle", "sample": sample}
-
-    if rank == 0:
-        line = {
-            "metric": METRIC, "value": value, "unit": "ms/system", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64+" + args.precision, "data": "synthetic",
-            "config": {"workload": "fem2d_256_learned_pcg", "n": P.n, "nnz": P.nnz, "nnz_L": P.nnz_L,
-                       "levels": P.nlev_fwd, "gnn": "n_mp=6,l=2,l_mp=2,h=64," + args.precision,
-                       "weights": wkind, "pcg": "fp64 recurrences, " + args.apply + " L L^T solves",
-                       "rtol": RTOL, "l2": "flushed between steps (256 MB write)"},
-            "compare": {"learned_iters": st_l["iters"], "learned_ms_median": float(np.median(ms_l)),
-                        "ic0_ms": float(np.mean(ms_i)), "ic0_iters": st_i["iters"],
-                        "learned_relres": st_l["relres"], "wall_s_timed": wall,
-                        "trsv_design": "levelsync" if P.trsv_mode == N.TRSV_LEVELSYNC else "syncfree",
-                        "trsv_tuned_ms_fwd_bwd": P.tuned_ms},
-            "roofline": {"kernel": ("k_trsv_cta" if P.trsv_mode == N.TRSV_LEVELSYNC else "k_trsv")
-                         + " (forward SpTRSV, " + args.apply + ")", "bound": "hbm",
-                         "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                         "peak_kind": peak_kind, "traffic": traffic, "bytes_per_launch": trsv_bytes,
-                         "ms_per_launch": trsv_ms, "levels": P.nlev_fwd},
-            "cpu_baseline": cpu,
-            "e2e": {"value": e2e_ms, "unit": "ms/system", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": launches,
-            "clocks": clk,
-        }
-        print(json.dumps(line), flush=True)
+    if args.workload == "train_32":
+        run_train(args, rank, world, local)
+    else:
+        run_solve(args, rank, world, local)
     if world > 1:
         torch.distributed.destroy_process_group()
 

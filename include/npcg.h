@@ -259,7 +259,10 @@ NPCG_API npcg_status npcg_sptrsv_timed(npcg_handle h, npcg_pattern p, int32_t tr
  * X, B: [npairs][n] (row p holds pair p of every system of the pattern).
  * loss_out: host.  grad: device [nparams] FP32, overwritten with d loss /
  * d weights (hand-written adjoint of the loss and of the network).
- * Synchronises.
+ * cfg->precision NPCG_FP32: FP32 forward and adjoint.  NPCG_BF16 (h = 64):
+ * the forward runs on the BF16 tensor cores with FP32 accumulation and the
+ * FP32 adjoint is taken at its node / edge states (mixed-precision
+ * training with FP32 master weights).  Synchronises.
  * ------------------------------------------------------------------------ */
 NPCG_API npcg_status npcg_loss_and_grad(npcg_handle h, npcg_pattern p, const double* A_val,
                                int32_t npairs, const double* X, const double* B,

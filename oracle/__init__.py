@@ -70,6 +70,8 @@ def _L():
             lib.or_gnn_nparams.argtypes = [vp]
             lib.or_gnn_nparams.restype = C.c_int64
             lib.or_gnn_forward.argtypes = [vp, C.c_int32, i32p, i32p, f64p, f64p, f64p, i32p, i32p, f64p, vp]
+            lib.or_gnn_forward_scaled.argtypes = [vp, C.c_int32, i32p, i32p, f64p, f64p, f64p, i32p, i32p, f64p,
+                                                  f64p]
             lib.or_llt_loss.argtypes = [C.c_int32, i32p, i32p, f64p, C.c_int, f64p, f64p, vp]
             lib.or_llt_loss.restype = C.c_double
             lib.or_loss_and_grad.argtypes = [vp, C.c_int32, i32p, i32p, f64p, C.c_int, f64p, f64p, f64p, vp]
@@ -258,6 +260,69 @@ def gnn_forward(cfg, A: CSR, b, w, return_s=False):
                         L.row_ptr, L.col_idx, Lv, _ptr(s))
     out = CSR(L.row_ptr, L.col_idx, Lv)
     return (out, s) if return_s else out
+
+
+def gnn_forward_scaled(cfg, A: CSR, b, w, s_max_diag, b_inf):
+    """L on tril(A) with the input scales of a parent system given (max
+    diagonal s and ||b||_inf); A is then a subgraph cut from that system."""
+    L, _ = tril(A, with_values=False)
+    Lv = np.zeros(L.nnz)
+    c = _cfg(cfg)
+    _L().or_gnn_forward_scaled(C.byref(c), A.n, A.row_ptr, A.col_idx, A.val, _f64(b), _f64(w),
+                               L.row_ptr, L.col_idx, Lv, np.array([s_max_diag, b_inf], dtype=np.float64))
+    return CSR(L.row_ptr, L.col_idx, Lv)
+
+
+def ball(A: CSR, centres, radius):
+    """Sorted node ids within `radius` hops of any centre (breadth-first)."""
+    seen = set(int(c) for c in centres)
+    front = list(seen)
+    for _ in range(radius):
+        nxt = []
+        for i in front:
+            for j in A.col_idx[A.row_ptr[i]:A.row_ptr[i + 1]]:
+                j = int(j)
+                if j not in seen:
+                    seen.add(j)
+                    nxt.append(j)
+        front = nxt
+    return np.array(sorted(seen), dtype=np.int64)
+
+
+def induced(A: CSR, nodes):
+    """Subgraph of A on sorted `nodes` (relabelled in the same order)."""
+    pos = {int(v): k for k, v in enumerate(nodes)}
+    rp, ci, val = [0], [], []
+    for i in nodes:
+        s, e = A.row_ptr[i], A.row_ptr[i + 1]
+        for k in range(s, e):
+            j = int(A.col_idx[k])
+            if j in pos:
+                ci.append(pos[j])
+                val.append(A.val[k])
+        rp.append(len(ci))
+    return CSR(rp, ci, val)
+
+
+def gnn_rows(cfg, A: CSR, b, w, rows):
+    """Rows `rows` of the network's L on the full system A, evaluated one
+    neighbourhood at a time: a node's state after n_mp rounds depends only on
+    nodes within n_mp hops (App. A.3), so the rows at the centre of the
+    (n_mp + 1)-hop ball, computed with the full system's input scales, are the
+    full system's rows.  Returns {row: (cols, values)}."""
+    b = _f64(b)
+    rows_of = np.repeat(np.arange(A.n), np.diff(A.row_ptr))
+    s_max = float(A.val[A.col_idx == rows_of].max())
+    b_inf = float(np.max(np.abs(b))) or 1.0
+    out = {}
+    for r in rows:
+        nodes = ball(A, [r], cfg.n_mp + 1)
+        S = induced(A, nodes)
+        Ls = gnn_forward_scaled(cfg, S, b[nodes], w, s_max, b_inf)
+        k = int(np.searchsorted(nodes, r))
+        s, e = Ls.row_ptr[k], Ls.row_ptr[k + 1]
+        out[int(r)] = (nodes[Ls.col_idx[s:e]], Ls.val[s:e].copy())
+    return out
 
 
 def llt_loss(L: CSR, X, B, with_grad=True):

@@ -598,7 +598,8 @@ static void tape_free(gnn_tape* t) {
 /* forward; fills Lv on the tril pattern (Lrp/Lci from or_tril) and the tape */
 static void gnn_forward_tape(const or_gnn_cfg* c, int32_t n, const int32_t* rp, const int32_t* ci,
                              const double* av, const double* b, const double* w,
-                             const int32_t* Lrp, const int32_t* Lci, double* Lv, gnn_tape* T) {
+                             const int32_t* Lrp, const int32_t* Lci, double* Lv, gnn_tape* T,
+                             const double* scales) {
     int h = c->h, l = c->l, lm = c->l_mp;
     int64_t nnz = rp[n];
     T->nnz = nnz; T->n = n; T->h = h;
@@ -622,6 +623,8 @@ static void gnn_forward_tape(const or_gnn_cfg* c, int32_t n, const int32_t* rp, 
         if (fabs(b[i]) > binf) binf = fabs(b[i]);
     }
     if (binf == 0.0) binf = 1.0;
+    /* a sub-problem cut from a larger system keeps the parent's scales */
+    if (scales) { sA = scales[0]; binf = scales[1]; }
 
     const double* w_encv = w;
     const double* w_ence = w_encv + mlp_nparams(1, h, h, l);
@@ -693,8 +696,21 @@ void or_gnn_forward(const or_gnn_cfg* c, int32_t n, const int32_t* rp, const int
                     const double* av, const double* b, const double* w,
                     const int32_t* Lrp, const int32_t* Lci, double* Lv, double* s_out) {
     gnn_tape T;
-    gnn_forward_tape(c, n, rp, ci, av, b, w, Lrp, Lci, Lv, &T);
+    gnn_forward_tape(c, n, rp, ci, av, b, w, Lrp, Lci, Lv, &T, NULL);
     if (s_out) memcpy(s_out, T.s, sizeof(double) * (size_t)rp[n]);
+    tape_free(&T);
+}
+
+/* Forward with the input scales given: scales[0] = s (max diagonal of the
+ * whole system), scales[1] = ||b||_inf of the whole system.  Used to evaluate
+ * rows of a large system on a subgraph: after n_mp rounds a node's state
+ * depends only on nodes within n_mp hops (App. A.3), so L_ij of a row i at the
+ * centre of the ball of radius n_mp + 1 around i equals the full system's. */
+void or_gnn_forward_scaled(const or_gnn_cfg* c, int32_t n, const int32_t* rp, const int32_t* ci,
+                           const double* av, const double* b, const double* w,
+                           const int32_t* Lrp, const int32_t* Lci, double* Lv, const double* scales) {
+    gnn_tape T;
+    gnn_forward_tape(c, n, rp, ci, av, b, w, Lrp, Lci, Lv, &T, scales);
     tape_free(&T);
 }
 
@@ -850,7 +866,7 @@ double or_loss_and_grad(const or_gnn_cfg* c, int32_t n, const int32_t* rp, const
     double loss = 0.0;
     for (int p = 0; p < npairs; ++p) {
         gnn_tape T;
-        gnn_forward_tape(c, n, rp, ci, av, B + (size_t)p * n, w, Lrp, Lci, Lv, &T);
+        gnn_forward_tape(c, n, rp, ci, av, B + (size_t)p * n, w, Lrp, Lci, Lv, &T, NULL);
         /* this pair's share of the mean */
         double lp = or_llt_loss(n, Lrp, Lci, Lv, 1, X + (size_t)p * n, B + (size_t)p * n, grad ? dL : NULL);
         loss += lp / npairs;

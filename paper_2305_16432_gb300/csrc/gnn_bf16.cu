@@ -108,14 +108,20 @@ struct Bf16Args {
     const __nv_bfloat16* ein;
     __nv_bfloat16* out;       // H-wide BF16 output rows
     float* sout;              // decoder: FP32 scalar output
+    float* out32;             // optional FP32 copy of the output rows (training tape)
+    float* agg32;             // optional FP32 aggregation sum_j e_ij (.) v_j (NODE, training tape)
     int* flags;
 };
 
 // tensor-core layers of each mode: NODE/EDGE all, ENC from layer 1, DEC to depth-1
 __host__ __device__ constexpr int tc_first(int mode) { return mode == MODE_ENC_NODE || mode == MODE_ENC_EDGE ? 1 : 0; }
 
+// modes whose first operand is a pure copy of feature rows: gathered with
+// cp.async into a second buffer while the previous tile computes
+__host__ __device__ constexpr bool async_gather(int mode) { return mode == MODE_EDGE || mode == MODE_DEC; }
+
 struct SmemPlan {
-    uint32_t a0, a1, w, bias, misc, total;
+    uint32_t a0, a0b, a1, w, bias, misc, total;
 };
 
 __host__ __device__ inline SmemPlan plan(int mode, int depth) {
@@ -125,15 +131,43 @@ __host__ __device__ inline SmemPlan plan(int mode, int depth) {
     const int last = mode == MODE_DEC ? depth - 1 : depth;
     uint32_t wbytes = 0;
     for (int l = first; l <= last; ++l) wbytes += (uint32_t)((l == first ? kin0 : kH) / 64) * (kH * 128);
+    const uint32_t a0bytes = (uint32_t)(kin0 / 64) * (kM * 128);
     SmemPlan p;
     p.a0 = 0;                                         // [128 x kin0] operand (kin0 / 64 K-blocks)
-    p.a1 = p.a0 + (uint32_t)(kin0 / 64) * (kM * 128);  // [128 x 64] hidden operand
+    p.a0b = p.a0 + a0bytes;                           // second buffer of the async-gather modes
+    p.a1 = p.a0b + (async_gather(mode) ? a0bytes : 0u);  // [128 x 64] hidden operand
     p.w = p.a1 + kM * 128;
     p.bias = p.w + wbytes;                            // FP32 biases of every layer + scalar layer weights
     p.misc = p.bias + (uint32_t)(depth + 1) * kH * 4 + 2 * kH * 4 + 64;
     p.misc = (p.misc + 15) & ~15u;
     p.total = p.misc + 64;
     return p;
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// EDGE: [e | v_row | v_col], DEC: [e]; rows past the end are zero-filled
+template <int MODE>
+__device__ __forceinline__ void gather_async(const Bf16Args& a, unsigned char* A, int64_t row0, int tid) {
+    constexpr int IN = mode_in(MODE, kH);
+    constexpr int CH = IN / 8;
+    for (int idx = tid; idx < kM * CH; idx += kThreads) {
+        const int r = idx / CH, c = idx % CH;
+        const int64_t k = row0 + r;
+        const bool in = k < a.nrows;
+        const int seg = c >> 3, cc = c & 7;
+        const int64_t kk = in ? k : 0;
+        const __nv_bfloat16* src = seg == 0 ? a.ein + kk * kH
+                                 : seg == 1 ? a.vin + (int64_t)a.erow[kk] * kH
+                                            : a.vin + (int64_t)a.ci[kk] * kH;
+        cp_async16(s_addr(A + (uint32_t)(c >> 3) * (kM * 128) + swz(r, (c & 7) * 8)), src + cc * 8, in ? 16u : 0u);
+    }
+    cp_async_commit();
 }
 
 template <int MODE>
@@ -201,10 +235,29 @@ __global__ void __launch_bounds__(kThreads) k_mlp_bf16(Bf16Args a) {
     bool ok = true;
 
     const int64_t ntiles = (a.nrows + kM - 1) / kM;
-    for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    constexpr bool kAsync = async_gather(MODE);
+    unsigned char* const A0a = A0;
+    unsigned char* const A0b = sm + P.a0b;
+    if (kAsync && (int64_t)blockIdx.x < ntiles) gather_async<MODE>(a, A0a, (int64_t)blockIdx.x * kM, tid);
+    int it = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it) {
         const int64_t row0 = tile * kM;
+        if (kAsync) {
+            // this tile's operand was requested one tile ago; request the next
+            // one into the other buffer (its last reader, the previous tile's
+            // first MMA, has completed) and wait for this one
+            A0 = (it & 1) ? A0b : A0a;
+            if (tile + gridDim.x < ntiles) {
+                gather_async<MODE>(a, (it & 1) ? A0a : A0b, (tile + gridDim.x) * kM, tid);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
+        }
         // ---- stage 0: operand of the first tensor-core layer into A0
-        if (kEnc) {
+        if (kAsync) {
+            // gathered above
+        } else if (kEnc) {
             const int64_t row = row0 + tid;
             float x = 0.0f;
             if (row < a.nrows) {
@@ -243,6 +296,11 @@ __global__ void __launch_bounds__(kThreads) k_mlp_bf16(Bf16Args a) {
 #pragma unroll
                         for (int j = 0; j < 8; ++j) h8[j] = __float2bfloat16_rn(acc[j]);
                         val = *reinterpret_cast<uint4*>(h8);
+                        if (a.agg32) {
+                            float4* g = reinterpret_cast<float4*>(a.agg32 + i * kH + (c - 8) * 8);
+                            g[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+                            g[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+                        }
                     }
                 }
                 *reinterpret_cast<uint4*>(A0 + (uint32_t)(c >> 3) * (kM * 128) + swz(r, (c & 7) * 8)) = val;
@@ -326,10 +384,18 @@ __global__ void __launch_bounds__(kThreads) k_mlp_bf16(Bf16Args a) {
                         for (int j = 0; j < 8; ++j) h8[j] = __float2bfloat16_rn(v[c * 8 + j] + bl[c * 8 + j]);
                         *reinterpret_cast<uint4*>(a.out + row * kH + c * 8) = *reinterpret_cast<uint4*>(h8);
                     }
+                    if (a.out32) {
+                        float4* o = reinterpret_cast<float4*>(a.out32 + row * kH);
+#pragma unroll
+                        for (int c = 0; c < 16; ++c)
+                            o[c] = make_float4(v[4 * c] + bl[4 * c], v[4 * c + 1] + bl[4 * c + 1],
+                                               v[4 * c + 2] + bl[4 * c + 2], v[4 * c + 3] + bl[4 * c + 3]);
+                    }
                 }
             }
         }
     }
+    if (kAsync) cp_async_wait<0>();      // no copy may land after the CTA leaves
     if (!ok) {
         // give the outstanding products one more bounded wait before the
         // tensor memory is released
@@ -361,18 +427,20 @@ npcg_status launch_bf16(Handle* h, const Bf16Args& a) {
 
 npcg_status gnn_scales_run(Handle* h, Pattern* P, const double* A_val, const double* b, double* sc);
 
-npcg_status gnn_forward_bf16_run(Handle* h, Pattern* P, const double* A_val, const double* b,
-                                 const npcg_gnn_config* cfg, const float* w, double* L_val) {
+// Forward on the tensor cores: decoder outputs into sout; with tV/tE/tAGG
+// (n_mp + 1, n_mp + 1 and n_mp FP32 buffers) also the training tape of
+// node / edge states and aggregations.
+npcg_status gnn_bf16_forward_core(Handle* h, Pattern* P, const double* A_val, const double* b,
+                                  const npcg_gnn_config* cfg, const float* w, double* sc, float* sout,
+                                  float* const* tV, float* const* tE, float* const* tAGG) {
     if (cfg->h != kH) return set_error(h, NPCG_EINVAL, "the BF16 tensor-core path needs hidden width h = 64");
     GnnStore& S = P->gnn;
     const size_t fe = (size_t)P->nnz * kH, fv = (size_t)P->n * kH;
     NPCG_CUDA(h, S.bf.ensure(2 * (fe + fv)));
-    NPCG_CUDA(h, S.s.ensure(P->nnz));
-    NPCG_CUDA(h, S.sc.ensure((size_t)2 * P->nsys));
     __nv_bfloat16* base = reinterpret_cast<__nv_bfloat16*>(S.bf.p);
     __nv_bfloat16* V[2] = {base, base + fv};
     __nv_bfloat16* E[2] = {base + 2 * fv, base + 2 * fv + fe};
-    NPCG_TRY(gnn_scales_run(h, P, A_val, b, S.sc.p));
+    NPCG_TRY(gnn_scales_run(h, P, A_val, b, sc));
     NPCG_CUDA(h, cudaMemsetAsync(P->ctl.p + 1, 0, sizeof(int), h->stream));
     const GnnOffsets off = gnn_offsets(kH, cfg->l, cfg->l_mp, cfg->n_mp);
     Bf16Args a{};
@@ -380,33 +448,51 @@ npcg_status gnn_forward_bf16_run(Handle* h, Pattern* P, const double* A_val, con
     a.ci = P->ci.p;
     a.erow = P->edge_row.p;
     a.row_sys = P->row_sys.p;
-    a.sc = S.sc.p;
+    a.sc = sc;
     a.av = A_val;
     a.b = b;
     a.flags = P->ctl.p + 1;
-    a.nrows = P->n; a.w = w + off.enc_v; a.depth = cfg->l; a.out = V[0];
+    a.nrows = P->n; a.w = w + off.enc_v; a.depth = cfg->l; a.out = V[0]; a.out32 = tV ? tV[0] : nullptr;
     NPCG_TRY(launch_bf16<MODE_ENC_NODE>(h, a));
-    a.nrows = P->nnz; a.w = w + off.enc_e; a.depth = cfg->l; a.out = E[0];
+    a.nrows = P->nnz; a.w = w + off.enc_e; a.depth = cfg->l; a.out = E[0]; a.out32 = tE ? tE[0] : nullptr;
     NPCG_TRY(launch_bf16<MODE_ENC_EDGE>(h, a));
     for (int t = 0; t < cfg->n_mp; ++t) {
         const int c = t & 1;
         a.nrows = P->n; a.w = w + off.node[t]; a.depth = cfg->l_mp; a.vin = V[c]; a.ein = E[c]; a.out = V[c ^ 1];
+        a.out32 = tV ? tV[t + 1] : nullptr;
+        a.agg32 = tAGG ? tAGG[t] : nullptr;
         NPCG_TRY(launch_bf16<MODE_NODE>(h, a));
+        a.agg32 = nullptr;
         a.nrows = P->nnz; a.w = w + off.edge[t]; a.depth = cfg->l_mp; a.vin = V[c ^ 1]; a.ein = E[c]; a.out = E[c ^ 1];
+        a.out32 = tE ? tE[t + 1] : nullptr;
         NPCG_TRY(launch_bf16<MODE_EDGE>(h, a));
     }
-    a.nrows = P->nnz; a.w = w + off.dec; a.depth = cfg->l; a.ein = E[cfg->n_mp & 1]; a.out = nullptr; a.sout = S.s.p;
+    a.nrows = P->nnz; a.w = w + off.dec; a.depth = cfg->l; a.ein = E[cfg->n_mp & 1]; a.out = nullptr;
+    a.out32 = nullptr; a.sout = sout;
     NPCG_TRY(launch_bf16<MODE_DEC>(h, a));
+    return NPCG_OK;
+}
+
+npcg_status gnn_bf16_check_flags(Handle* h, Pattern* P) {
+    int flags = 0;
+    NPCG_TRY(read_scalar(h, P->ctl.p + 1, &flags));
+    if (flags & kFlagTimeout) return set_error(h, NPCG_ETIMEOUT, "tensor-core MLP wait timed out");
+    return NPCG_OK;
+}
+
+npcg_status gnn_forward_bf16_run(Handle* h, Pattern* P, const double* A_val, const double* b,
+                                 const npcg_gnn_config* cfg, const float* w, double* L_val) {
+    GnnStore& S = P->gnn;
+    NPCG_CUDA(h, S.s.ensure(P->nnz));
+    NPCG_CUDA(h, S.sc.ensure((size_t)2 * P->nsys));
+    NPCG_TRY(gnn_bf16_forward_core(h, P, A_val, b, cfg, w, S.sc.p, S.s.p, nullptr, nullptr, nullptr));
     GnnBuffers gb{};
     gb.s = S.s.p;
     gb.sc = S.sc.p;
     gb.av = A_val;
     gb.diag_mode = cfg->diag_mode;
     NPCG_TRY(gnn_assemble_L(h, P, gb, L_val));
-    int flags = 0;
-    NPCG_TRY(read_scalar(h, P->ctl.p + 1, &flags));
-    if (flags & kFlagTimeout) return set_error(h, NPCG_ETIMEOUT, "tensor-core MLP wait timed out");
-    return NPCG_OK;
+    return gnn_bf16_check_flags(h, P);
 }
 
 }  // namespace npcg

@@ -71,6 +71,10 @@ npcg_status gnn_forward_into(Handle* h, Pattern* P, const double* A_val, const d
 npcg_status gnn_assemble_L(Handle* h, Pattern* P, const GnnBuffers& B, double* L_val);
 npcg_status gnn_forward_bf16_run(Handle* h, Pattern* P, const double* A_val, const double* b,
                                  const npcg_gnn_config* cfg, const float* w, double* L_val);
+npcg_status gnn_bf16_forward_core(Handle* h, Pattern* P, const double* A_val, const double* b,
+                                  const npcg_gnn_config* cfg, const float* w, double* sc, float* sout,
+                                  float* const* tV, float* const* tE, float* const* tAGG);
+npcg_status gnn_bf16_check_flags(Handle* h, Pattern* P);
 
 namespace {
 

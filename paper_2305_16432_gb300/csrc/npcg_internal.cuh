@@ -94,6 +94,17 @@ struct TriLayout {
 
 // Per-system level-synchronous layout of one triangular solve (one CTA per
 // system, steps of <= 256 rows of one level, TMA-prefetched).
+// consecutive steps of one system moved into one shared-memory stage by
+// three bulk copies (structure, values, right-hand side)
+struct alignas(16) CtaChunk {
+    long long soff;                // structure offset (int32 units)
+    long long voff;                // value offset (elements of the value type)
+    int q0e;                       // first right-hand-side position copied (16-byte aligned)
+    int nsteps;
+    unsigned sbytes, vbytes, rbytes;
+    int pad;
+};
+
 struct CtaLayout {
     bool built = false;
     bool window_ok = false;        // every dependency within the shared window
@@ -106,6 +117,13 @@ struct CtaLayout {
     DevBuf<int32_t> sbuf, vsrc, is_diag, step_of_pos;
     DevBuf<double> vbuf;
     DevBuf<float> vbuf32;
+    // per value type ([0] FP64, [1] FP32): chunks, their per-system ranges,
+    // stage capacity in bytes and number of ring stages (0: does not fit)
+    DevBuf<CtaChunk> chunks[2];
+    DevBuf<int32_t> sys_chunk0[2];
+    int nchunks[2] = {0, 0};
+    int stage_cap[2] = {0, 0};
+    int nstages[2] = {0, 0};
 };
 
 enum TrsvMode : int { kTrsvAuto = 0, kTrsvSyncFree = 1, kTrsvCta = 2 };

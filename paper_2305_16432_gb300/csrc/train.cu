@@ -464,20 +464,26 @@ npcg_status train_pair(Handle* h, Pattern* P, const double* A_val, const double*
     a.sc = sc;
     a.av = A_val;
     a.b = b;
-    a.nrows = n; a.w = w + off.enc_v; a.depth = l; a.out = T.V[0];
-    NPCG_TRY(launch_mlp<H>(h, MODE_ENC_NODE, a));
-    a.nrows = nnz; a.w = w + off.enc_e; a.depth = l; a.out = T.E[0];
-    NPCG_TRY(launch_mlp<H>(h, MODE_ENC_EDGE, a));
-    for (int t = 0; t < nmp; ++t) {
-        a.nrows = n; a.w = w + off.node[t]; a.depth = lm; a.vin = T.V[t]; a.ein = T.E[t]; a.out = T.V[t + 1];
-        a.agg_out = T.AGG[t];
-        NPCG_TRY(launch_mlp<H>(h, MODE_NODE, a));
-        a.agg_out = nullptr;
-        a.nrows = nnz; a.w = w + off.edge[t]; a.depth = lm; a.vin = T.V[t + 1]; a.ein = T.E[t]; a.out = T.E[t + 1];
-        NPCG_TRY(launch_mlp<H>(h, MODE_EDGE, a));
+    if (cfg->precision == NPCG_BF16) {
+        // tensor-core forward; the tape holds its node / edge states in FP32
+        NPCG_TRY(gnn_bf16_forward_core(h, P, A_val, b, cfg, w, sc, T.S, T.V.data(), T.E.data(), T.AGG.data()));
+        NPCG_TRY(gnn_bf16_check_flags(h, P));
+    } else {
+        a.nrows = n; a.w = w + off.enc_v; a.depth = l; a.out = T.V[0];
+        NPCG_TRY(launch_mlp<H>(h, MODE_ENC_NODE, a));
+        a.nrows = nnz; a.w = w + off.enc_e; a.depth = l; a.out = T.E[0];
+        NPCG_TRY(launch_mlp<H>(h, MODE_ENC_EDGE, a));
+        for (int t = 0; t < nmp; ++t) {
+            a.nrows = n; a.w = w + off.node[t]; a.depth = lm; a.vin = T.V[t]; a.ein = T.E[t]; a.out = T.V[t + 1];
+            a.agg_out = T.AGG[t];
+            NPCG_TRY(launch_mlp<H>(h, MODE_NODE, a));
+            a.agg_out = nullptr;
+            a.nrows = nnz; a.w = w + off.edge[t]; a.depth = lm; a.vin = T.V[t + 1]; a.ein = T.E[t]; a.out = T.E[t + 1];
+            NPCG_TRY(launch_mlp<H>(h, MODE_EDGE, a));
+        }
+        a.nrows = nnz; a.w = w + off.dec; a.depth = l; a.ein = T.E[nmp]; a.out = T.S;
+        NPCG_TRY(launch_mlp<H>(h, MODE_DEC, a));
     }
-    a.nrows = nnz; a.w = w + off.dec; a.depth = l; a.ein = T.E[nmp]; a.out = T.S;
-    NPCG_TRY(launch_mlp<H>(h, MODE_DEC, a));
     GnnBuffers gb{};
     gb.s = T.S;
     gb.sc = sc;
@@ -576,8 +582,8 @@ npcg_status loss_grad_run(Handle* h, Pattern* P, const double* A_val, int npairs
                           const double* B, const npcg_gnn_config* cfg, const float* w, double* loss_out,
                           float* grad) {
     NPCG_TRY(gnn_check_config(h, cfg));
-    if (cfg->precision != NPCG_FP32)
-        return set_error(h, NPCG_EINVAL, "the training adjoint runs in FP32 (precision NPCG_FP32)");
+    if (cfg->precision == NPCG_BF16 && cfg->h != 64)
+        return set_error(h, NPCG_EINVAL, "the BF16 tensor-core forward needs hidden width h = 64");
     const int H = cfg->h, nmp = cfg->n_mp;
     const int64_t n = P->n, nnz = P->nnz, nnzL = P->nnzL;
     const int dmax = std::max(cfg->l, cfg->l_mp);

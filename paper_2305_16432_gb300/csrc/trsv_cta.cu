@@ -5,15 +5,18 @@
 // only on earlier levels), split into steps of at most one row per consumer
 // thread.  Each step's structure (row ids, dependency positions, header),
 // factor values (reciprocal diagonal first) and right-hand side are laid out
-// contiguously in processing order.  A producer warp streams them into a
-// shared-memory ring with TMA bulk copies (cp.async.bulk), a "full" mbarrier
-// per stage completing on the transferred bytes and an "empty" mbarrier per
-// stage released by the eight consumer warps.  Solution values of recent
-// positions live in a shared-memory window indexed by position, so the only
-// synchronisation on the dependency chain is one named barrier among the
-// consumer warps per step.  When a dependency reaches further back than the
-// window, consumers read the position-ordered global copy (kWindow = false).
-// Values (T) are FP64 or FP32; right-hand side and solution stay FP64.
+// contiguously in processing order.  Consecutive steps are grouped into
+// chunks that fill one shared-memory stage; a producer warp streams the
+// chunks into a ring of stages with three TMA bulk copies each
+// (cp.async.bulk), a "full" mbarrier per stage completing on the transferred
+// bytes and an "empty" mbarrier per stage released by the eight consumer
+// warps.  Chunking keeps many small steps in flight, so the copy latency is
+// hidden behind the dependency chain rather than paid every few steps.
+// Solution values of recent positions live in a shared-memory window indexed
+// by position, so the only synchronisation on the dependency chain is one
+// named barrier among the consumer warps per step.  When a dependency reaches
+// further back than the window, consumers read the position-ordered global
+// copy (kWindow = false).  Values (T) are FP64 or FP32.
 #include <algorithm>
 #include <vector>
 
@@ -29,6 +32,8 @@ constexpr int kWin = 8192;               // shared window (positions), power of 
 constexpr int kMaxStages = 8;
 constexpr long long kMbarSpin = 1LL << 22;
 constexpr int kHdrInts = 4;              // {q0, nrows, width, pad} heads every structure block
+constexpr int kRec = 4;                  // dependencies held in a row's packed record
+constexpr int kWinPad = 32;              // window slots past kWin; slot kWin stays zero
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -66,51 +71,99 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 }
 
 struct CtaDev {
-    const int32_t* sys_step0;   // [nsys+1]
-    const int4* steps;          // {q0, nrows, width, 0}
-    const int64_t* soff;        // [nsteps] int32 offset of the step's structure block
-    const int64_t* voff;        // [nsteps] element offset of the step's value block
-    const int32_t* sbuf;        // structure: hdr[4] | row[np] | pos2[np] | dep[w][np]
-    const void* vbuf;           // values (T): dinv[np] | val[w][np]
-    int max_np, max_w;
+    const int32_t* sys_chunk0;  // [nsys+1]
+    const CtaChunk* chunks;
+    const int32_t* sbuf;        // structure: hdr[4] | row[np] | pos2[np] | dep[w][np] per step
+    const void* vbuf;           // values (T): dinv[np] | val[w][np] per step
     int stages;
+    int stage_cap;              // bytes per stage (multiple of 128)
 };
 
 __host__ __device__ __forceinline__ int pad4(int x) { return (x + 3) & ~3; }
-__host__ __device__ __forceinline__ size_t al128(size_t x) { return (x + 127) & ~size_t(127); }
-
-template <class T>
-struct StageGeom {
-    size_t sb, vb, rb, stage;
-    __host__ __device__ StageGeom(int max_np, int max_w) {
-        const int np = pad4(max_np);
-        sb = al128((size_t)(kHdrInts + (size_t)np * (2 + max_w)) * 4);
-        vb = al128((size_t)np * (1 + max_w) * sizeof(T));
-        rb = al128((size_t)(np + 4) * 8);
-        stage = sb + vb + rb;
-    }
-};
+__host__ __device__ __forceinline__ int n_extra(int w) { return w > kRec ? w - kRec : 0; }
+// Step blocks, np = nrows rounded up to 4.  Structure (int32):
+//   hdr[4] | dep[np][4] | {row, pos2}[np] | extra dep[n_extra][np]
+// dep holds processing positions (window slots once the window is known to
+// suffice: position mod kWin, a missing dependency -> the zero slot kWin;
+// otherwise absolute positions, -1 when missing).  Values (T):
+//   l[np][4] | 1/diag[np] | extra l[n_extra][np]
+__host__ __device__ __forceinline__ int s_ints(int np, int w) { return kHdrInts + np * (6 + n_extra(w)); }
+__host__ __device__ __forceinline__ int v_elems(int np, int w) { return np * (5 + n_extra(w)); }
 
 // right-hand-side copies start on a 16-byte boundary: positions rounded down
-// to a multiple of kRhsAl<T> elements
+// to a multiple of rhs_align<T>() elements
 template <class T>
 __host__ __device__ constexpr int rhs_align() { return 16 / (int)sizeof(T); }
 
+// barrier + mbarrier area at the start of shared memory: full[8], empty[8],
+// and per stage the chunk's {nsteps, value offset, rhs offset, q0e}
+constexpr int kBarBytes = 256;
+
+// operands of one row of one step, held in registers by its consumer thread
+template <class T>
+struct StepOps {
+    int q0, nrows, width, np;
+    int4 dep;
+    int row, pos2;
+    T l[4];
+    T rhs, dinv;
+};
+
+__device__ __forceinline__ void ld_vec4(float (&l)[4], const float* p) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    l[0] = v.x; l[1] = v.y; l[2] = v.z; l[3] = v.w;
+}
+__device__ __forceinline__ void ld_vec4(double (&l)[4], const double* p) {
+    const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+    l[0] = a.x; l[1] = a.y; l[2] = b.x; l[3] = b.y;
+}
+
+template <class T>
+__device__ __forceinline__ void load_step(StepOps<T>& o, const int32_t* hdr, const T* vals, const T* rh, int q0e,
+                                          int t) {
+    const int4 h = *reinterpret_cast<const int4*>(hdr);
+    o.q0 = h.x;
+    o.nrows = h.y;
+    o.width = h.z;
+    o.np = pad4(h.y);
+    if (t < o.nrows) {
+        o.dep = reinterpret_cast<const int4*>(hdr + kHdrInts)[t];
+        const int2 rp = reinterpret_cast<const int2*>(hdr + kHdrInts + 4 * o.np)[t];
+        o.row = rp.x;
+        o.pos2 = rp.y;
+        ld_vec4(o.l, vals + 4 * t);
+        o.dinv = vals[4 * o.np + t];
+        o.rhs = rh[o.q0 - q0e + t];
+    }
+}
+
+// named barrier 1 among the consumer threads, returning whether every
+// consumer passed ok (all take the same decision)
+__device__ __forceinline__ bool consumers_agree(bool ok) {
+    uint32_t all_ok;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(all_ok)
+        : "r"((uint32_t)ok), "r"(kCtaRows)
+        : "memory");
+    return all_ok != 0;
+}
+
 template <bool kWindow, class T>
-__global__ void __launch_bounds__(kCtaThreads) k_trsv_cta(CtaDev D, const T* __restrict__ rhs,
+__global__ void __launch_bounds__(kCtaThreads, 1) k_trsv_cta(CtaDev D, const T* __restrict__ rhs,
                                                          double* out, T* out2, double* yglob,
                                                          const SysState* st, int* flags) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int sys = blockIdx.x;
     if (st && !st[sys].active) return;
-    const int s0 = D.sys_step0[sys], s1 = D.sys_step0[sys + 1];
-    if (s0 >= s1) return;
+    const int c0 = D.sys_chunk0[sys], c1 = D.sys_chunk0[sys + 1];
+    if (c0 >= c1) return;
     const int S = D.stages;
-    const StageGeom<T> G(D.max_np, D.max_w);
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);
     uint64_t* empty = full + kMaxStages;
-    T* win = reinterpret_cast<T*>(smem + 256);
-    unsigned char* ring = smem + 256 + (kWindow ? kWin * sizeof(T) : 0);
+    int4* info = reinterpret_cast<int4*>(empty + kMaxStages);
+    T* win = reinterpret_cast<T*>(smem + kBarBytes);
+    unsigned char* ring = smem + kBarBytes + (kWindow ? (kWin + kWinPad) * sizeof(T) : 0);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
@@ -119,45 +172,41 @@ __global__ void __launch_bounds__(kCtaThreads) k_trsv_cta(CtaDev D, const T* __r
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    if (kWindow && threadIdx.x < kWinPad) win[kWin + threadIdx.x] = (T)0;
     __syncthreads();
 
     if (warp == kCtaRows / 32) {
-        // ---------------- producer warp: stream the steps through the ring
-        // the 32 lanes fetch the descriptors of 32 steps at a time; lane 0 issues
+        // ---------------- producer warp: stream the chunks through the ring
+        // the 32 lanes fetch 32 chunk descriptors at a time; lane 0 issues
         int issued = 0;
         bool ok = true;
-        for (int j0 = s0; j0 < s1 && ok; j0 += 32) {
-            int4 dl = make_int4(0, 0, 0, 0);
-            long long sol = 0, vol = 0;
-            if (j0 + lane < s1) {
-                dl = D.steps[j0 + lane];
-                sol = D.soff[j0 + lane];
-                vol = D.voff[j0 + lane];
-            }
-            const int cnt = min(32, s1 - j0);
+        for (int j0 = c0; j0 < c1 && ok; j0 += 32) {
+            CtaChunk cl{};
+            if (j0 + lane < c1) cl = D.chunks[j0 + lane];
+            const int cnt = min(32, c1 - j0);
             for (int u = 0; u < cnt; ++u) {
-                const int4 d = make_int4(__shfl_sync(0xffffffffu, dl.x, u), __shfl_sync(0xffffffffu, dl.y, u),
-                                         __shfl_sync(0xffffffffu, dl.z, u), 0);
-                const long long so = __shfl_sync(0xffffffffu, sol, u);
-                const long long vo = __shfl_sync(0xffffffffu, vol, u);
-                const int j = j0 + u, k = j - s0, s = k % S;
+                const long long so = __shfl_sync(0xffffffffu, cl.soff, u);
+                const long long vo = __shfl_sync(0xffffffffu, cl.voff, u);
+                const int q0e = __shfl_sync(0xffffffffu, cl.q0e, u);
+                const int nst = __shfl_sync(0xffffffffu, cl.nsteps, u);
+                const unsigned sb = __shfl_sync(0xffffffffu, cl.sbytes, u);
+                const unsigned vb = __shfl_sync(0xffffffffu, cl.vbytes, u);
+                const unsigned rb = __shfl_sync(0xffffffffu, cl.rbytes, u);
+                const int j = j0 + u, k = j - c0, s = k % S;
                 if (lane == 0) {
                     if (k >= S) {
                         ok = mbar_wait_bounded(&empty[s], (uint32_t)((k / S - 1) & 1));
                         if (ok) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     }
                     if (ok) {
-                        const int np = pad4(d.y);
-                        const uint32_t sbytes = (uint32_t)(kHdrInts + np * (2 + d.z)) * 4;
-                        const uint32_t vbytes = (uint32_t)np * (1 + d.z) * sizeof(T);
-                        constexpr int al = rhs_align<T>();
-                        const int q0e = d.x & ~(al - 1);
-                        const uint32_t rbytes = (uint32_t)(((d.x + d.y - q0e) + al - 1) & ~(al - 1)) * sizeof(T);
-                        unsigned char* base = ring + (size_t)s * G.stage;
-                        mbar_expect_tx(&full[s], sbytes + vbytes + rbytes);
-                        bulk_g2s(base, D.sbuf + so, sbytes, &full[s]);
-                        bulk_g2s(base + G.sb, static_cast<const T*>(D.vbuf) + vo, vbytes, &full[s]);
-                        bulk_g2s(base + G.sb + G.vb, rhs + q0e, rbytes, &full[s]);
+                        unsigned char* base = ring + (size_t)s * D.stage_cap;
+                        // read by the consumers after the phase completes
+                        // (the arrive below releases this store)
+                        info[s] = make_int4(nst, (int)sb, (int)(sb + vb), q0e);
+                        mbar_expect_tx(&full[s], sb + vb + rb);
+                        bulk_g2s(base, D.sbuf + so, sb, &full[s]);
+                        bulk_g2s(base + sb, static_cast<const T*>(D.vbuf) + vo, vb, &full[s]);
+                        bulk_g2s(base + sb + vb, rhs + q0e, rb, &full[s]);
                         ++issued;
                     }
                 }
@@ -168,75 +217,117 @@ __global__ void __launch_bounds__(kCtaThreads) k_trsv_cta(CtaDev D, const T* __r
         if (lane != 0) return;
         if (!ok) atomicOr(flags, kFlagTimeout | kFlagAbort);
         // copies still in flight complete before this warp (and the CTA) leaves
-        for (int j = max(s0, s0 + issued - S); j < s0 + issued; ++j) {
-            const int k = j - s0;
+        for (int j = max(c0, c0 + issued - S); j < c0 + issued; ++j) {
+            const int k = j - c0;
             mbar_wait_bounded(&full[k % S], (uint32_t)((k / S) & 1));
         }
         return;
     }
 
     // ---------------- consumer warps
-    for (int i = s0; i < s1; ++i) {
-        const int k = i - s0, s = k % S;
-        const bool ok = mbar_wait_bounded(&full[s], (uint32_t)((k / S) & 1));
-        const unsigned char* base = ring + (size_t)s * G.stage;
-        const int32_t* hdr = reinterpret_cast<const int32_t*>(base);
-        const int q0 = hdr[0], nrows = hdr[1], width = hdr[2];
-        const int np = pad4(nrows);
-        const int32_t* srow = hdr + kHdrInts;
-        const int32_t* spos2 = srow + np;
-        const int32_t* sdep = spos2 + np;
-        const T* sdinv = reinterpret_cast<const T*>(base + G.sb);
-        const T* sval = sdinv + np;
-        const T* srhs = reinterpret_cast<const T*>(base + G.sb + G.vb) + (q0 & (rhs_align<T>() - 1));
-        const int t = threadIdx.x;
-        if (ok && t < nrows) {
-            T acc = srhs[t];
-            if (width <= 4) {
-                // common case: issue every dependency load first, then fold in slot order
-                int p[4];
-                T lv[4], yv[4];
-#pragma unroll
-                for (int kk = 0; kk < 4; ++kk) {
-                    p[kk] = kk < width ? sdep[kk * np + t] : -1;
-                    lv[kk] = kk < width ? sval[kk * np + t] : (T)0;
-                }
-#pragma unroll
-                for (int kk = 0; kk < 4; ++kk)
-                    yv[kk] = p[kk] >= 0 ? (kWindow ? win[p[kk] & (kWin - 1)] : (T)__ldcg(yglob + p[kk])) : (T)0;
-#pragma unroll
-                for (int kk = 0; kk < 4; ++kk)
-                    if (p[kk] >= 0) acc = fma(-lv[kk], yv[kk], acc);
-            } else {
-                for (int kk = 0; kk < width; ++kk) {
-                    const int pk = sdep[kk * np + t];
-                    if (pk >= 0) {
-                        const T yv = kWindow ? win[pk & (kWin - 1)] : (T)__ldcg(yglob + pk);
-                        acc = fma(-sval[kk * np + t], yv, acc);
-                    }
-                }
-            }
-            const T y = acc * sdinv[t];
-            const int q = q0 + t;
-            if (kWindow) win[q & (kWin - 1)] = y;
-            else yglob[q] = (double)y;
-            if (out) out[srow[t]] = (double)y;
-            if (out2) out2[spos2[t]] = y;
-        }
-        // every consumer is done with this step (window writes visible, stage
-        // free) and all take the same decision: a thread whose wait gave up
-        // must not leave the others at this barrier
-        uint32_t all_ok;
-        asm volatile(
-            "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
-            : "=r"(all_ok)
-            : "r"((uint32_t)ok), "r"(kCtaRows)
-            : "memory");
-        if (!all_ok) {
+    // Software pipeline: the operands of the next step (structure, values,
+    // right-hand side: nothing that depends on solution values) are loaded
+    // into registers before the current step computes, so only the window
+    // loads, the multiply-adds and the barrier sit on the dependency chain.
+    const int t = threadIdx.x;
+    StepOps<T> cur, nxt;
+    int c = c0, s = 0, u = 0, nst;
+    const int32_t* hdr;
+    const T* vals;
+    const T* rh;
+    int q0e;
+    {
+        const bool ok = mbar_wait_bounded(&full[0], 0u);
+        if (!consumers_agree(ok)) {
             if (threadIdx.x == 0) atomicOr(flags, kFlagTimeout | kFlagAbort);
             return;
         }
-        if (lane == 0) mbar_arrive(&empty[s]);
+        const int4 inf = info[0];
+        nst = inf.x;
+        hdr = reinterpret_cast<const int32_t*>(ring);
+        vals = reinterpret_cast<const T*>(ring + inf.y);
+        rh = reinterpret_cast<const T*>(ring + inf.z);
+        q0e = inf.w;
+        load_step(cur, hdr, vals, rh, q0e, t);
+    }
+    for (;;) {
+        // locate and load the next step
+        const int32_t* chdr = hdr;          // the current step, for rows wider than the registers
+        const T* cvals = vals;
+        bool has_next = true, waited = false, ok = true;
+        int nc = c, ns = s, nu = u + 1, nnst = nst;
+        if (u + 1 < nst) {
+            hdr += s_ints(cur.np, cur.width);
+            vals += v_elems(cur.np, cur.width);
+        } else if (c + 1 < c1) {
+            nc = c + 1;
+            ns = (nc - c0) % S;
+            nu = 0;
+            waited = true;
+            ok = mbar_wait_bounded(&full[ns], (uint32_t)(((nc - c0) / S) & 1));
+            if (ok) {
+                const int4 inf = info[ns];
+                const unsigned char* base = ring + (size_t)ns * D.stage_cap;
+                nnst = inf.x;
+                hdr = reinterpret_cast<const int32_t*>(base);
+                vals = reinterpret_cast<const T*>(base + inf.y);
+                rh = reinterpret_cast<const T*>(base + inf.z);
+                q0e = inf.w;
+            }
+        } else {
+            has_next = false;
+        }
+        if (has_next && ok) load_step(nxt, hdr, vals, rh, q0e, t);
+        // the current step
+        if (t < cur.nrows) {
+            T acc = cur.rhs;
+            if (kWindow) {
+                // missing dependencies read the zero slot with a zero value
+                const T y0 = win[cur.dep.x], y1 = win[cur.dep.y], y2 = win[cur.dep.z], y3 = win[cur.dep.w];
+                acc = fma(-cur.l[0], y0, acc);
+                acc = fma(-cur.l[1], y1, acc);
+                acc = fma(-cur.l[2], y2, acc);
+                acc = fma(-cur.l[3], y3, acc);
+            } else {
+                const int pd[4] = {cur.dep.x, cur.dep.y, cur.dep.z, cur.dep.w};
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk)
+                    if (pd[kk] >= 0) acc = fma(-cur.l[kk], (T)__ldcg(yglob + pd[kk]), acc);
+            }
+            if (cur.width > kRec) {
+                const int32_t* xdep = chdr + kHdrInts + 6 * cur.np;
+                const T* xval = cvals + 5 * cur.np;
+                for (int kk = 0; kk < cur.width - kRec; ++kk) {
+                    const int pk = xdep[kk * cur.np + t];
+                    if (kWindow) acc = fma(-xval[kk * cur.np + t], win[pk], acc);
+                    else if (pk >= 0) acc = fma(-xval[kk * cur.np + t], (T)__ldcg(yglob + pk), acc);
+                }
+            }
+            const T y = acc * cur.dinv;
+            const int q = cur.q0 + t;
+            if (kWindow) win[q & (kWin - 1)] = y;
+            else yglob[q] = (double)y;
+            if (out) out[cur.row] = (double)y;
+            if (out2) out2[cur.pos2] = y;
+        }
+        if (!kWindow) __threadfence_block();
+        // this step's solutions are visible to the next step; a next chunk
+        // is used only if every consumer's wait for it succeeded
+        if (waited) {
+            if (!consumers_agree(ok)) {
+                if (threadIdx.x == 0) atomicOr(flags, kFlagTimeout | kFlagAbort);
+                return;
+            }
+        } else {
+            asm volatile("bar.sync 1, %0;" ::"r"(kCtaRows) : "memory");
+        }
+        if (u + 1 == nst && lane == 0) mbar_arrive(&empty[s]);   // chunk c fully read
+        if (!has_next) break;
+        cur = nxt;
+        c = nc;
+        s = ns;
+        u = nu;
+        nst = nnst;
     }
 }
 
@@ -257,27 +348,37 @@ __global__ void k_cta_fill(int64_t n, const int32_t* cperm, const int32_t* step_
         int32_t* vs = vsrc + voff[stp];
         if (t == 0) { sb[0] = d.x; sb[1] = d.y; sb[2] = d.z; sb[3] = 0; }
         int32_t* body = sb + kHdrInts;
-        body[t] = row;
-        body[np + t] = 0;                               // pos2: set by k_cta_pos2
+        body[4 * np + 2 * t] = row;
+        body[4 * np + 2 * t + 1] = 0;                   // pos2: set by k_cta_pos2
         const int nl = Lrp[row + 1] - Lrp[row];
         int cnt, first;
         if (upper) { cnt = (rp[row + 1] - rp[row]) - nl; first = rp[row + 1] - cnt; }
         else { cnt = nl - 1; first = Lrp[row]; }
-        vs[t] = Lrp[row + 1] - 1;                       // diagonal (stored as its reciprocal)
-        for (int k = 0; k < d.z; ++k) {
+        vs[4 * np + t] = Lrp[row + 1] - 1;              // diagonal (stored as its reciprocal)
+        const int kmax = d.z > kRec ? d.z : kRec;
+        for (int k = 0; k < kmax; ++k) {
             int dep = -1, src = -1;
             if (k < cnt) {
                 if (upper) { dep = cpos[ci[first + k]]; src = a2l[mirror[first + k]]; }
                 else { dep = cpos[Lci[first + k]]; src = first + k; }
             }
-            body[(2 + k) * np + t] = dep;
-            vs[(1 + k) * np + t] = src;
+            if (k < kRec) {
+                body[4 * t + k] = dep;
+                vs[4 * t + k] = src;
+            } else {
+                body[6 * np + (k - kRec) * np + t] = dep;
+                vs[5 * np + (k - kRec) * np + t] = src;
+            }
         }
     }
 }
 
+__device__ __forceinline__ int32_t* dep_slot(int32_t* body, int np, int t, int k) {
+    return k < kRec ? body + 4 * t + k : body + 6 * np + (k - kRec) * np + t;
+}
+
 __global__ void k_cta_reach(int64_t n, const int32_t* step_of_pos, const int4* steps,
-                            const int32_t* level_end, const int32_t* sbuf, const int64_t* soff,
+                            const int32_t* level_end, int32_t* sbuf, const int64_t* soff,
                             unsigned long long* reach) {
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
          q += (int64_t)gridDim.x * blockDim.x) {
@@ -285,10 +386,28 @@ __global__ void k_cta_reach(int64_t n, const int32_t* step_of_pos, const int4* s
         const int4 d = steps[stp];
         const int np = pad4(d.y);
         const int t = (int)(q - d.x);
-        const int32_t* body = sbuf + soff[stp] + kHdrInts;
+        int32_t* body = sbuf + soff[stp] + kHdrInts;
         for (int k = 0; k < d.z; ++k) {
-            int p = body[(2 + k) * np + t];
+            const int p = *dep_slot(body, np, t, k);
             if (p >= 0) atomicMax(reach, (unsigned long long)(level_end[stp] - p));
+        }
+    }
+}
+
+// the window suffices: dependency positions become window slots
+__global__ void k_cta_window(int64_t n, const int32_t* step_of_pos, const int4* steps, const int64_t* soff,
+                             int32_t* sbuf) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int stp = step_of_pos[q];
+        const int4 d = steps[stp];
+        const int np = pad4(d.y);
+        const int t = (int)(q - d.x);
+        int32_t* body = sbuf + soff[stp] + kHdrInts;
+        const int kmax = d.z > kRec ? d.z : kRec;
+        for (int k = 0; k < kmax; ++k) {
+            int32_t* p = dep_slot(body, np, t, k);
+            *p = *p >= 0 ? (*p & (kWin - 1)) : kWin;
         }
     }
 }
@@ -302,12 +421,12 @@ __global__ void k_cta_pos2(int64_t n, const int32_t* step_of_pos, const int4* st
         const int np = pad4(d.y);
         const int t = (int)(q - d.x);
         int32_t* body = sbuf + soff[stp] + kHdrInts;
-        body[np + t] = cpos_other[body[t]];
+        body[4 * np + 2 * t + 1] = cpos_other[body[4 * np + 2 * t]];
     }
 }
 
-// values: reciprocal of the diagonal in the first np slots of every block,
-// off-diagonals after; padding gets finite placeholders
+// values: reciprocal of the diagonal in the 1/diag slots of every block,
+// off-diagonals elsewhere; padding and missing slots get zero
 __global__ void k_cta_load(int64_t nv, const int32_t* vsrc, const int32_t* is_diag, const double* L,
                            double* v64, float* v32) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nv;
@@ -324,8 +443,8 @@ __global__ void k_mark_diag(int nsteps, const int4* steps, const int64_t* voff, 
     for (int stp = blockIdx.x; stp < nsteps; stp += gridDim.x) {
         const int4 d = steps[stp];
         const int np = pad4(d.y);
-        for (int k = threadIdx.x; k < np * (1 + d.z); k += blockDim.x)
-            if (voff[stp] + k < nv) is_diag[voff[stp] + k] = k < np ? 1 : 0;
+        for (int k = threadIdx.x; k < v_elems(np, d.z); k += blockDim.x)
+            if (voff[stp] + k < nv) is_diag[voff[stp] + k] = (k >= 4 * np && k < 5 * np) ? 1 : 0;
     }
 }
 
@@ -336,16 +455,55 @@ __global__ void k_gather_perm(int64_t n, const int32_t* cperm, const double* x, 
         xp[q] = (T)x[cperm[q]];
 }
 
-size_t smem_bytes(const CtaLayout& C, int stages, bool f32) {
-    const size_t stage = f32 ? StageGeom<float>(C.max_np, C.max_w).stage : StageGeom<double>(C.max_np, C.max_w).stage;
-    const size_t win = C.window_ok ? (size_t)kWin * (f32 ? 4 : 8) : 0;
-    return 256 + win + stage * stages;
+size_t win_bytes(const CtaLayout& C, bool f32) { return C.window_ok ? (size_t)(kWin + kWinPad) * (f32 ? 4 : 8) : 0; }
+
+size_t smem_bytes(const CtaLayout& C, bool f32) {
+    return kBarBytes + win_bytes(C, f32) + (size_t)C.stage_cap[f32] * C.nstages[f32];
 }
 
-int stages_for(const CtaLayout& C, bool f32) {
-    for (int s = kMaxStages; s >= 2; --s)
-        if (smem_bytes(C, s, f32) <= 220 * 1024) return s;
-    return 0;
+constexpr size_t kSmemMax = 220 * 1024;
+
+// Groups the steps of every system into chunks of at most cap bytes
+// (structure + values + right-hand side) for value size vsz; returns false
+// when a single step does not fit.
+bool build_chunks(const std::vector<int4>& steps, const std::vector<int64_t>& soff,
+                  const std::vector<int64_t>& voff, const std::vector<int32_t>& sys_step0, int nsys,
+                  size_t vsz, size_t cap, std::vector<CtaChunk>& out, std::vector<int32_t>& sys_chunk0) {
+    const int al = (int)(16 / vsz);
+    out.clear();
+    sys_chunk0.assign(nsys + 1, 0);
+    auto sbytes_of = [&](int i) { return (size_t)s_ints(pad4(steps[i].y), steps[i].z) * 4; };
+    auto vbytes_of = [&](int i) { return (size_t)v_elems(pad4(steps[i].y), steps[i].z) * vsz; };
+    for (int sy = 0; sy < nsys; ++sy) {
+        sys_chunk0[sy] = (int32_t)out.size();
+        int i = sys_step0[sy];
+        const int e = sys_step0[sy + 1];
+        while (i < e) {
+            CtaChunk c{};
+            c.soff = soff[i];
+            c.voff = voff[i];
+            c.q0e = steps[i].x & ~(al - 1);
+            size_t sb = 0, vb = 0, rb = 0;
+            int j = i;
+            while (j < e) {
+                const size_t sb2 = sb + sbytes_of(j), vb2 = vb + vbytes_of(j);
+                const int qend = steps[j].x + steps[j].y;
+                const size_t rb2 = (size_t)(((qend - c.q0e) + al - 1) & ~(al - 1)) * vsz;
+                if (sb2 + vb2 + rb2 > cap) break;
+                sb = sb2; vb = vb2; rb = rb2;
+                ++j;
+            }
+            if (j == i) return false;
+            c.nsteps = j - i;
+            c.sbytes = (unsigned)sb;
+            c.vbytes = (unsigned)vb;
+            c.rbytes = (unsigned)rb;
+            out.push_back(c);
+            i = j;
+        }
+    }
+    sys_chunk0[nsys] = (int32_t)out.size();
+    return true;
 }
 
 }  // namespace
@@ -404,8 +562,8 @@ npcg_status cta_layout_build(Handle* h, Pattern* P, bool upper, CtaLayout* C) {
         const int np = pad4(steps[i].y);
         soff[i] = so;
         voff[i] = vo;
-        so += kHdrInts + (int64_t)np * (2 + steps[i].z);
-        vo += (int64_t)np * (1 + steps[i].z);
+        so += s_ints(np, steps[i].z);
+        vo += v_elems(np, steps[i].z);
     }
     C->nsteps = nsteps;
     C->max_w = maxw;
@@ -452,6 +610,42 @@ npcg_status cta_layout_build(Handle* h, Pattern* P, bool upper, CtaLayout* C) {
     unsigned long long rh = 0;
     NPCG_TRY(read_scalar(h, reach.p, &rh));
     C->window_ok = rh <= (unsigned long long)kWin;
+    if (C->window_ok) {
+        k_cta_window<<<blocks, 256, 0, h->stream>>>(n, C->step_of_pos.p, C->steps.p, C->soff.p, C->sbuf.p);
+        NPCG_CUDA(h, cudaGetLastError());
+    }
+    // chunks per value type: the stage capacity is the larger of the biggest
+    // single step and an even split of the free shared memory into kMaxStages
+    for (int f32 = 0; f32 < 2; ++f32) {
+        const size_t vsz = f32 ? 4 : 8;
+        const int al = (int)(16 / vsz);
+        size_t single = 0;
+        for (int i = 0; i < nsteps; ++i) {
+            const int np = pad4(steps[i].y);
+            const int q0e = steps[i].x & ~(al - 1);
+            const size_t rb = (size_t)(((steps[i].x + steps[i].y - q0e) + al - 1) & ~(al - 1)) * vsz;
+            single = std::max(single, (size_t)s_ints(np, steps[i].z) * 4 + (size_t)v_elems(np, steps[i].z) * vsz + rb);
+        }
+        const size_t avail = kSmemMax - kBarBytes - win_bytes(*C, f32 != 0);
+        size_t cap = std::max(single, avail / kMaxStages);
+        cap = (cap + 127) & ~size_t(127);
+        const int stages = (int)std::min<size_t>(kMaxStages, avail / cap);
+        C->stage_cap[f32] = (int)cap;
+        C->nstages[f32] = 0;
+        C->nchunks[f32] = 0;
+        std::vector<CtaChunk> ch;
+        std::vector<int32_t> sc0;
+        if (stages < 2 || !build_chunks(steps, soff, voff, sys_step0, (int)P->nsys, vsz, cap, ch, sc0)) continue;
+        C->nstages[f32] = stages;
+        C->nchunks[f32] = (int)ch.size();
+        NPCG_CUDA(h, C->chunks[f32].alloc(std::max<size_t>(ch.size(), 1)));
+        NPCG_CUDA(h, C->sys_chunk0[f32].alloc(P->nsys + 1));
+        NPCG_CUDA(h, cudaMemcpyAsync(C->chunks[f32].p, ch.data(), ch.size() * sizeof(CtaChunk),
+                                     cudaMemcpyHostToDevice, h->stream));
+        NPCG_CUDA(h, cudaMemcpyAsync(C->sys_chunk0[f32].p, sc0.data(), (P->nsys + 1) * sizeof(int32_t),
+                                     cudaMemcpyHostToDevice, h->stream));
+        NPCG_CUDA(h, cudaStreamSynchronize(h->stream));
+    }
     // the launch size never exceeds 220 KB; set once here, outside any capture
     const int mx = 220 * 1024;
     NPCG_CUDA(h, cudaFuncSetAttribute(k_trsv_cta<true, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
@@ -473,7 +667,7 @@ npcg_status cta_link(Handle* h, Pattern* P) {
     return NPCG_OK;
 }
 
-int cta_stages(const CtaLayout& C) { return std::min(stages_for(C, false), stages_for(C, true)); }
+int cta_stages(const CtaLayout& C) { return std::min(C.nstages[0], C.nstages[1]); }
 
 npcg_status cta_factor_load(Handle* h, CtaLayout* C, const double* L_val) {
     const int blocks = std::max(1, std::min(ceil_div(C->vbuf_len, 256), h->num_sms * 8));
@@ -496,19 +690,16 @@ npcg_status cta_gather(Handle* h, cudaStream_t s, const CtaLayout& C, int64_t n,
 // the solution.  f32: FP32 factor, arithmetic, right-hand side and out2.
 npcg_status cta_trsv_launch(Handle* h, cudaStream_t s, Pattern* P, const CtaLayout& C, const void* rhs_v,
                             double* out, void* out2_v, const SysState* st, bool f32) {
-    const int stages = stages_for(C, f32);
+    const int stages = C.nstages[f32];
     if (stages < 2) return set_error(h, NPCG_EINVAL, "level-synchronous layout does not fit shared memory");
     CtaDev d;
-    d.sys_step0 = C.sys_step0.p;
-    d.steps = C.steps.p;
-    d.soff = C.soff.p;
-    d.voff = C.voff.p;
+    d.sys_chunk0 = C.sys_chunk0[f32].p;
+    d.chunks = C.chunks[f32].p;
     d.sbuf = C.sbuf.p;
     d.vbuf = f32 ? (const void*)C.vbuf32.p : (const void*)C.vbuf.p;
-    d.max_np = C.max_np;
-    d.max_w = C.max_w;
     d.stages = stages;
-    const size_t smem = smem_bytes(C, stages, f32);
+    d.stage_cap = C.stage_cap[f32];
+    const size_t smem = smem_bytes(C, f32);
     int* flags = P->ctl.p + 1;
     if (f32) {
         const float* rp = static_cast<const float*>(rhs_v);

@@ -62,14 +62,14 @@ def make_group(N, probs, pairs, seed, rtol=1e-10):
     return P, torch.cat(vs), torch.cat(Xs, dim=1).contiguous(), torch.cat(Bs, dim=1).contiguous()
 
 
-def evaluate(N, cfg, w, probs, rtol=1e-6, seed=77):
+def evaluate(N, cfg, w, probs, rtol=1e-6, seed=77, precision=None):
     """Iterations to rtol of learned-L, IC(0) and Jacobi PCG on held-out systems."""
     out = []
     for k, p in enumerate(probs):
         rp, ci, v = N.assemble_system(p)
         P = N.analyse(rp, ci)
         b = torch.as_tensor(I.rhs(P.n, seed + k), device="cuda")
-        L = N.gnn_factor(P, v, b, cfg, w)
+        L = N.gnn_factor(P, v, b, cfg, w, precision=N.FP32 if precision is None else precision)
         _, sl = N.pcg_solve(P, v, b, N.PREC_LLT, L, rtol=rtol)
         Li, _ = N.ic0_factor(P, v)
         _, si = N.pcg_solve(P, v, b, N.PREC_LLT, Li, rtol=rtol)
@@ -86,16 +86,21 @@ def save_checkpoint(path, cfg, w, mom, vel, step, hist):
 
 
 def train(cfg: I.GnnConfig, steps=600, groups=4, per_group=8, pairs=8, m=128, lr=1e-3, lr_final=1e-4,
-          seed=2023, log_every=25, w0=None, ckpt=None, resume=None, val_every=50):
+          seed=2023, log_every=25, w0=None, ckpt=None, resume=None, val_every=50, precision=None, sizes=None):
     """Adam at lr (App. A.4), cosine-decayed to lr_final over the run; returns
-    the weights with the fewest validation PCG iterations."""
+    the weights with the fewest validation PCG iterations.  precision: the
+    network forward's arithmetic (FP32, or BF16 tensor cores with the FP32
+    adjoint); sizes: lattice size of each group (default m for all)."""
     from . import build as B
     B.build()
     from . import npcg as N
+    prec = N.FP32 if precision is None else precision
+    sizes = sizes or [m] * groups
     t0 = time.time()
     data = []
     for g in range(groups):
-        probs = [I.fem2d(m, sigma=1.0, corr_len=0.1, seed=seed + 100 * g + k) for k in range(per_group)]
+        mg = sizes[g % len(sizes)]
+        probs = [I.fem2d(mg, sigma=1.0, corr_len=0.1, seed=seed + 100 * g + k) for k in range(per_group)]
         data.append(make_group(N, probs, pairs, seed + g))
     t_data = time.time() - t0
     w = torch.as_tensor(I.gnn_weights(cfg, seed) if w0 is None else w0, device="cuda")
@@ -122,7 +127,7 @@ def train(cfg: I.GnnConfig, steps=600, groups=4, per_group=8, pairs=8, m=128, lr
     def val_iters():
         its = []
         for Pv, v, bv in vals:
-            L = N.gnn_factor(Pv, v, bv, cfg, w)
+            L = N.gnn_factor(Pv, v, bv, cfg, w, precision=prec)
             _, st = N.pcg_solve(Pv, v, bv, N.PREC_LLT, L, rtol=1e-6)
             its.append(st[0]["iters"] if st[0]["status"] == 0 else 10 * Pv.n)
         return float(np.mean(its))
@@ -133,7 +138,8 @@ def train(cfg: I.GnnConfig, steps=600, groups=4, per_group=8, pairs=8, m=128, lr
     for t in range(start, steps + 1):
         P, A, X, Bb = data[(t - 1) % groups]
         q = ((t - 1) // groups) % (pairs // 2)
-        loss, g = N.loss_and_grad(P, A, X[2 * q:2 * q + 2].contiguous(), Bb[2 * q:2 * q + 2].contiguous(), cfg, w)
+        loss, g = N.loss_and_grad(P, A, X[2 * q:2 * q + 2].contiguous(), Bb[2 * q:2 * q + 2].contiguous(), cfg, w,
+                                  precision=prec)
         lr_t = lr_final + 0.5 * (lr - lr_final) * (1.0 + np.cos(np.pi * (t - 1) / max(1, steps - 1)))
         N.adam_step(w, g, mom, vel, t, lr=float(lr_t))
         hist.append(loss)
@@ -165,26 +171,34 @@ def main():
     ap.add_argument("--resume", default=None)
     ap.add_argument("--val_every", type=int, default=50)
     ap.add_argument("--diag_mode", type=int, default=0, help="0: softplus diagonal; 1: L D L^T with D = diag(A)")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--sizes", default="", help="comma-separated lattice sizes of the training groups")
     ap.add_argument("--out", default=os.path.join(os.path.dirname(__file__), "weights", "fem2d_6x64.npy"))
     args = ap.parse_args()
     cfg = I.GnnConfig(n_mp=args.n_mp, l=2, l_mp=2, h=args.h, diag_mode=args.diag_mode)
-    w, hist, tm = train(cfg, steps=args.steps, m=args.m, lr=args.lr, lr_final=args.lr_final, ckpt=args.ckpt,
-                        resume=args.resume, val_every=args.val_every)
+    from . import build as B
+    B.build()
     from . import npcg as N
+    prec = N.BF16 if args.precision == "bf16" else N.FP32
+    sizes = [int(x) for x in args.sizes.split(",") if x] or None
+    w, hist, tm = train(cfg, steps=args.steps, m=args.m, lr=args.lr, lr_final=args.lr_final, ckpt=args.ckpt,
+                        resume=args.resume, val_every=args.val_every, precision=prec, sizes=sizes)
     w0 = torch.as_tensor(I.gnn_weights(cfg, 2023), device="cuda")
     held = [I.fem2d(args.m, sigma=1.0, corr_len=0.1, seed=9000 + k) for k in range(3)]
-    ev = evaluate(N, cfg, w, held)
-    ev0 = evaluate(N, cfg, w0, held[:1])
-    big = evaluate(N, cfg, w, [I.fem2d_256(seed=0)])
+    ev = evaluate(N, cfg, w, held, precision=prec)
+    ev0 = evaluate(N, cfg, w0, held[:1], precision=prec)
+    small = evaluate(N, cfg, w, [I.fem2d(96, sigma=1.0, corr_len=0.1, seed=9200)], precision=prec)
+    big = evaluate(N, cfg, w, [I.fem2d_256(seed=0)], precision=prec)
     os.makedirs(os.path.dirname(os.path.abspath(args.out)), exist_ok=True)
     np.save(args.out, _np(w).astype(np.float32))
     meta = {"config": {"n_mp": cfg.n_mp, "l": cfg.l, "l_mp": cfg.l_mp, "h": cfg.h, "diag_mode": cfg.diag_mode},
             "train": {"steps": args.steps, "lr": args.lr, "lr_final": args.lr_final, "schedule": "cosine",
                       "batch": "8 systems x 2 pairs",
                       "selection": "checkpoint with the fewest validation PCG iterations",
-                      "systems": f"4 groups x 8 FEM {args.m}x{args.m}, sigma 1, corr 0.1", **tm},
+                      "systems": f"4 groups x 8 FEM lattices {sizes or [args.m]}, sigma 1, corr 0.1",
+                      "precision": args.precision, **tm},
             "loss_first": hist[0], "loss_last": float(np.mean(hist[-20:])),
-            "heldout_fem128": ev, "untrained_fem128": ev0, "fem256_seed0": big,
+            "heldout_fem128": ev, "untrained_fem128": ev0, "heldout_fem96": small, "fem256_seed0": big,
             "learned_iters_fem256": big[0]["learned"]}
     with open(os.path.splitext(args.out)[0] + ".json", "w") as f:
         json.dump(meta, f, indent=1)

@@ -126,11 +126,16 @@ def test_ic0_and_sptrsv_parity(N, name):
 
 
 def iter_tol(prec, iters):
-    """Iteration-count bar: +-1 for preconditioned solves; for plain CG the
-    spread the oracle's own recurrence shows under other summation orders
-    (tests/test_oracle_solvers.py::test_cg_iteration_spread_under_summation_order),
-    i.e. 1 % of the count."""
-    return 1 if prec != "cg" else max(1, int(np.ceil(0.01 * iters)))
+    """Iteration-count bar: +-1 for IC(0) and Jacobi; for plain CG and for
+    learned factors the spread the oracle's own recurrence shows under other
+    summation orders (tests/test_oracle_solvers.py::
+    test_cg_iteration_spread_under_summation_order and
+    test_pcg_iteration_spread_learned_factor): 1 % and 3 % of the count."""
+    if prec == "cg":
+        return max(1, int(np.ceil(0.01 * iters)))
+    if prec == "learned":
+        return max(1, int(np.ceil(0.03 * iters)))
+    return 1
 
 
 @pytest.mark.parametrize("name", ["poisson2d_32", "fem34", "fd3d_var", "fd2d_var"])

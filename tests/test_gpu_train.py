@@ -121,3 +121,24 @@ def test_autograd_function_matches_oracle_gradient(N):
     assert abs(loss.item() - lo) <= 1e-5 * abs(lo)
     gg = wt.grad.cpu().numpy().astype(np.float64)
     assert np.linalg.norm(gg - 3.0 * go) / np.linalg.norm(3.0 * go) <= 1e-4
+
+
+@pytest.mark.parametrize("diag_mode", [0, 1])
+def test_loss_and_grad_bf16_forward(N, diag_mode):
+    """Mixed precision: BF16 tensor-core forward, FP32 adjoint at its states.
+    Bars derived from the BF16 bar on L (2e-2): the loss is quadratic in L
+    (2 x 2e-2), and the gradient is bilinear in the residual and the
+    network's states (again 2 x 2e-2, on the 2-norm)."""
+    cfg = I.GnnConfig(n_mp=3, l=2, l_mp=2, h=64, diag_mode=diag_mode)
+    prob = I.fem2d(14, sigma=1.0, seed=12)
+    om, ph = I.grf_features(prob)
+    Ao = O.assemble(prob, om, ph)
+    rp, ci, v = N.assemble_system(prob, om, ph)
+    P = N.analyse(rp, ci)
+    X, B = _pairs(Ao, 2, 41)
+    w = I.gnn_weights(cfg, 6, scale=1.5)
+    lo, go = O.loss_and_grad(cfg, Ao, X, B, w.astype(np.float64))
+    lg, gg = N.loss_and_grad(P, v, _gpu(X), _gpu(B), cfg, _gpu(w, torch.float32), precision=N.BF16)
+    gg = gg.cpu().numpy().astype(np.float64)
+    assert abs(lg - lo) <= 4e-2 * abs(lo)
+    assert np.linalg.norm(gg - go) / np.linalg.norm(go) <= 4e-2

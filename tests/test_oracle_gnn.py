@@ -252,3 +252,31 @@ def test_adam_single_step_by_hand():
     vh = 0.001999 * g * g / (1 - 0.998001)
     expect2 = expect - 1e-3 * mh / (np.sqrt(vh) + 1e-8)
     assert np.allclose(w, expect2, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("prob", [I.fem2d(16, sigma=1.0, seed=21), I.fd3d(7, 6, 5, sigma=1.0, seed=22)])
+def test_gnn_rows_on_neighbourhood_balls(prob):
+    """Sampled rows of a large system's L (the full-size parity harness): the
+    rows computed on the (n_mp + 1)-hop ball with the parent's scales equal the
+    full forward's rows bit for bit, and a ball one hop smaller does not."""
+    cfg = I.GnnConfig(n_mp=2, l=2, l_mp=2, h=8)
+    A = O.assemble(prob)
+    b = I.rhs(A.n, 4)
+    w = I.gnn_weights(cfg, 9, scale=2.0)
+    L = O.gnn_forward(cfg, A, b, w)
+    rows = [0, A.n // 3, A.n // 2 + 1, A.n - 1]
+    got = O.gnn_rows(cfg, A, b, w, rows)
+    for r in rows:
+        s, e = L.row_ptr[r], L.row_ptr[r + 1]
+        cols, vals = got[r]
+        assert np.array_equal(cols, L.col_idx[s:e])
+        assert np.array_equal(vals, L.val[s:e])
+    # one hop short: an interior row sees truncated neighbourhoods
+    r = A.n // 2 + 1
+    nodes = O.ball(A, [r], cfg.n_mp)
+    rows_of = np.repeat(np.arange(A.n), np.diff(A.row_ptr))
+    s_max = float(A.val[A.col_idx == rows_of].max())
+    Ls = O.gnn_forward_scaled(cfg, O.induced(A, nodes), b[nodes], w, s_max, float(np.abs(b).max()))
+    k = int(np.searchsorted(nodes, r))
+    s, e = L.row_ptr[r], L.row_ptr[r + 1]
+    assert not np.allclose(Ls.val[Ls.row_ptr[k]:Ls.row_ptr[k + 1]], L.val[s:e], rtol=1e-9, atol=0)

@@ -278,12 +278,20 @@ def test_iteration_counts_match_dense_reference_recurrence():
         assert np.allclose(x, xd, rtol=1e-9, atol=1e-12)
 
 
-def _cg_with_order(A, b, rtol, order):
-    """Algorithm 1 without preconditioner, dot products summed in another
-    (equally valid) order; used to measure how far rounding alone moves the
-    iteration count."""
+def _cg_with_order(A, b, rtol, order, L=None, kmax=None):
+    """Algorithm 1 (without preconditioner, or with P = L L^T from a dense
+    triangular solve), dot products summed in another (equally valid) order;
+    used to measure how far rounding alone moves the iteration count (the
+    return value), or, with kmax, the iterate x after exactly kmax updates."""
+    import scipy.linalg as sl
     D = A.dense()
     n = A.n
+    Ld = L.dense() if L is not None else None
+
+    def prec(r):
+        if Ld is None:
+            return r.copy()
+        return sl.solve_triangular(Ld.T, sl.solve_triangular(Ld, r, lower=True), lower=False)
 
     def dot(u, w):
         if order == "pairwise":
@@ -297,8 +305,9 @@ def _cg_with_order(A, b, rtol, order):
     x = np.zeros(n)
     r = b.copy()
     tol = rtol * math.sqrt(dot(b, b))
-    p = r.copy()
-    rz = dot(r, r)
+    z = prec(r)
+    p = z.copy()
+    rz = dot(r, z)
     k = 0
     while True:
         w = D @ p
@@ -306,10 +315,14 @@ def _cg_with_order(A, b, rtol, order):
         x += al * p
         r -= al * w
         k += 1
-        if math.sqrt(dot(r, r)) <= tol:
+        if kmax is not None:
+            if k == kmax:
+                return x
+        elif math.sqrt(dot(r, r)) <= tol:
             return k
-        rzn = dot(r, r)
-        p = r + (rzn / rz) * p
+        z = prec(r)
+        rzn = dot(r, z)
+        p = z + (rzn / rz) * p
         rz = rzn
 
 
@@ -325,3 +338,32 @@ def test_cg_iteration_spread_under_summation_order():
     spread = max(abs(k - it) for k in others)
     assert spread > 1                      # the effect is real
     assert spread <= max(1, math.ceil(0.01 * it))
+
+
+def test_pcg_iteration_spread_learned_factor():
+    # PCG with a network factor that needs hundreds of iterations (a random
+    # 2 x 16 network on the 34 x 34 FEM system): other summation orders of the
+    # same recurrence move the count by more than one iteration, up to 3 % of
+    # it.  This is the resolution of the arithmetic that an iteration-count
+    # comparison of learned factors can ask for.
+    A = O.assemble(I.fem2d(34, sigma=1.0, seed=5))
+    b = I.rhs(A.n, 7)
+    cfg = I.GnnConfig(n_mp=2, l=2, l_mp=2, h=16)
+    L = O.gnn_forward(cfg, A, b, I.gnn_weights(cfg, 3))
+    _, it, _, st = O.pcg(A, b, O.PREC_LLT, L, rtol=1e-6)
+    assert st == 0 and it > 300
+    others = [_cg_with_order(A, b, 1e-6, o, L) for o in ("pairwise", "blocked", "reverse")]
+    spread = max(abs(k - it) for k in others)
+    assert spread > 1
+    assert spread <= math.ceil(0.03 * it)
+    # the iterates after the same number of updates: the oracle's own x moves
+    # by more than 1e-8 (relative) under another summation order, and by less
+    # than 1e-6 (with IC(0), 28 iterations, by rounding only)
+    xo, _, _, _ = O.pcg(A, b, O.PREC_LLT, L, rtol=1e-6)
+    dx = max(np.linalg.norm(_cg_with_order(A, b, 1e-6, o, L, kmax=it) - xo) / np.linalg.norm(xo)
+             for o in ("pairwise", "blocked", "reverse"))
+    assert 1e-8 < dx <= 1e-6
+    Lic, _ = O.ic0(A)
+    xi, iti, _, _ = O.pcg(A, b, O.PREC_LLT, Lic, rtol=1e-6)
+    dxi = np.linalg.norm(_cg_with_order(A, b, 1e-6, "reverse", Lic, kmax=iti) - xi) / np.linalg.norm(xi)
+    assert dxi <= 1e-12
