@@ -205,7 +205,7 @@ def run_reference(args):
         return
     prob = I.fem2d_256(seed=0)
     cfg = I.GnnConfig(n_mp=6, l=2, l_mp=2, h=64)
-    w, kind, meta = _load_weights(cfg, os.path.join(WEIGHTS_DIR, "fem2d_6x64.npy"))
+    w, kind, meta = _load_weights(cfg, os.path.join(WEIGHTS_DIR, "gnn_6x64.npy"))
     if meta.get("config"):
         cfg = I.GnnConfig(**meta["config"])
     Ao = O.assemble(prob)
@@ -483,7 +483,7 @@ def main():
                     help="network arithmetic: BF16 tensor cores (default) or FP32")
     ap.add_argument("--apply", default="fp32", choices=["fp32", "fp64"],
                     help="arithmetic of the L L^T solves inside the FP64 PCG")
-    ap.add_argument("--weights", default=os.path.join(WEIGHTS_DIR, "fem2d_6x64.npy"))
+    ap.add_argument("--weights", default=os.path.join(WEIGHTS_DIR, "gnn_6x64.npy"))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--trsv-reps", type=int, default=50)
     args = ap.parse_args()

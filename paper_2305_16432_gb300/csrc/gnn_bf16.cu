@@ -121,7 +121,7 @@ __host__ __device__ constexpr int tc_first(int mode) { return mode == MODE_ENC_N
 __host__ __device__ constexpr bool async_gather(int mode) { return mode == MODE_EDGE || mode == MODE_DEC; }
 
 struct SmemPlan {
-    uint32_t a0, a0b, a1, w, bias, misc, total;
+    uint32_t a0, a0b, a1, w, bias, idx, misc, total;
 };
 
 __host__ __device__ inline SmemPlan plan(int mode, int depth) {
@@ -138,7 +138,9 @@ __host__ __device__ inline SmemPlan plan(int mode, int depth) {
     p.a1 = p.a0b + (async_gather(mode) ? a0bytes : 0u);  // [128 x 64] hidden operand
     p.w = p.a1 + kM * 128;
     p.bias = p.w + wbytes;                            // FP32 biases of every layer + scalar layer weights
-    p.misc = p.bias + (uint32_t)(depth + 1) * kH * 4 + 2 * kH * 4 + 64;
+    p.idx = p.bias + (uint32_t)(depth + 1) * kH * 4 + 2 * kH * 4 + 64;
+    p.idx = (p.idx + 15) & ~15u;                      // async gather: [2 tiles][row, col][128] indices
+    p.misc = p.idx + (async_gather(mode) ? 2u * 2u * kM * 4u : 0u);
     p.misc = (p.misc + 15) & ~15u;
     p.total = p.misc + 64;
     return p;
@@ -151,9 +153,12 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// EDGE: [e | v_row | v_col], DEC: [e]; rows past the end are zero-filled
+// EDGE: [e | v_row | v_col], DEC: [e]; rows past the end are zero-filled.
+// The row / column indices of the tile come from shared memory (staged one
+// tile ahead), so issuing the copies never waits on a global load.
 template <int MODE>
-__device__ __forceinline__ void gather_async(const Bf16Args& a, unsigned char* A, int64_t row0, int tid) {
+__device__ __forceinline__ void gather_async(const Bf16Args& a, unsigned char* A, int64_t row0, int tid,
+                                             const int* sidx) {
     constexpr int IN = mode_in(MODE, kH);
     constexpr int CH = IN / 8;
     for (int idx = tid; idx < kM * CH; idx += kThreads) {
@@ -161,13 +166,19 @@ __device__ __forceinline__ void gather_async(const Bf16Args& a, unsigned char* A
         const int64_t k = row0 + r;
         const bool in = k < a.nrows;
         const int seg = c >> 3, cc = c & 7;
-        const int64_t kk = in ? k : 0;
-        const __nv_bfloat16* src = seg == 0 ? a.ein + kk * kH
-                                 : seg == 1 ? a.vin + (int64_t)a.erow[kk] * kH
-                                            : a.vin + (int64_t)a.ci[kk] * kH;
+        const __nv_bfloat16* src = seg == 0 ? a.ein + (in ? k : 0) * kH
+                                 : seg == 1 ? a.vin + (int64_t)sidx[r] * kH
+                                            : a.vin + (int64_t)sidx[kM + r] * kH;
         cp_async16(s_addr(A + (uint32_t)(c >> 3) * (kM * 128) + swz(r, (c & 7) * 8)), src + cc * 8, in ? 16u : 0u);
     }
     cp_async_commit();
+}
+
+// this thread's row of a tile: its edge's row and column (0 past the end)
+__device__ __forceinline__ int2 tile_index(const Bf16Args& a, int64_t tile, int64_t ntiles, int tid) {
+    const int64_t k = tile * kM + tid;
+    if (tile >= ntiles || k >= a.nrows) return make_int2(0, 0);
+    return make_int2(a.erow[k], a.ci[k]);
 }
 
 template <int MODE>
@@ -238,21 +249,35 @@ __global__ void __launch_bounds__(kThreads) k_mlp_bf16(Bf16Args a) {
     constexpr bool kAsync = async_gather(MODE);
     unsigned char* const A0a = A0;
     unsigned char* const A0b = sm + P.a0b;
-    if (kAsync && (int64_t)blockIdx.x < ntiles) gather_async<MODE>(a, A0a, (int64_t)blockIdx.x * kM, tid);
+    int* sidx = reinterpret_cast<int*>(sm + P.idx);      // [2][2][kM]
+    int2 nidx = make_int2(0, 0);
+    if (kAsync) {
+        const int2 i0 = tile_index(a, blockIdx.x, ntiles, tid);
+        const int2 i1 = tile_index(a, (int64_t)blockIdx.x + gridDim.x, ntiles, tid);
+        sidx[tid] = i0.x;
+        sidx[kM + tid] = i0.y;
+        sidx[2 * kM + tid] = i1.x;
+        sidx[3 * kM + tid] = i1.y;
+        __syncthreads();
+        if ((int64_t)blockIdx.x < ntiles) gather_async<MODE>(a, A0a, (int64_t)blockIdx.x * kM, tid, sidx);
+    }
     int it = 0;
     for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it) {
         const int64_t row0 = tile * kM;
         if (kAsync) {
             // this tile's operand was requested one tile ago; request the next
             // one into the other buffer (its last reader, the previous tile's
-            // first MMA, has completed) and wait for this one
+            // first MMA, has completed) and wait for this one; the indices of
+            // the tile after next are loaded now and staged at the end
             A0 = (it & 1) ? A0b : A0a;
             if (tile + gridDim.x < ntiles) {
-                gather_async<MODE>(a, (it & 1) ? A0a : A0b, (tile + gridDim.x) * kM, tid);
+                gather_async<MODE>(a, (it & 1) ? A0a : A0b, (tile + gridDim.x) * kM, tid,
+                                   sidx + ((it + 1) & 1) * 2 * kM);
                 cp_async_wait<1>();
             } else {
                 cp_async_wait<0>();
             }
+            nidx = tile_index(a, tile + 2 * (int64_t)gridDim.x, ntiles, tid);
         }
         // ---- stage 0: operand of the first tensor-core layer into A0
         if (kAsync) {
@@ -342,7 +367,10 @@ __global__ void __launch_bounds__(kThreads) k_mlp_bf16(Bf16Args a) {
             woff += (uint32_t)(kin / 64) * (kH * 128);
             ok = bar_wait(bar, phase);
             phase ^= 1u;
-            if (!__syncthreads_and(ok)) break;
+            if (!__syncthreads_and(ok)) {
+                ok = false;          // every thread leaves the tile loop together
+                break;
+            }
             tc_fence_after();
             float v[64];
 #pragma unroll
@@ -393,6 +421,13 @@ __global__ void __launch_bounds__(kThreads) k_mlp_bf16(Bf16Args a) {
                     }
                 }
             }
+        }
+        if (kAsync) {
+            // the slot of this tile's indices was last read by the gather
+            // issued one tile ago; it now receives the tile after next
+            sidx[(it & 1) * 2 * kM + tid] = nidx.x;
+            sidx[(it & 1) * 2 * kM + kM + tid] = nidx.y;
+            __syncthreads();
         }
     }
     if (kAsync) cp_async_wait<0>();      // no copy may land after the CTA leaves

@@ -1,21 +1,25 @@
 """Training of the graph-network preconditioner on the GPU.
 
 Data (Sec. 4.3, App. A.2 describe (A_i, x_i, b_i) tuples from simulations;
-the paper's datasets are not available, so the tuples are synthetic): 2-D
-P1 FEM diffusion systems on jittered 128 x 128 lattices (n = 15,876) with
-log k a GRF (sigma 1, correlation 0.1), right-hand sides b ~ N(0, 1), and
-x = A^-1 b computed by this library's own IC(0)-PCG to a 1e-10 relative
-residual.  Loss Eq. (loss_Ab), mean over a batch of 8 systems x 2 pairs (the
-paper's batch size 16 for 2-D problems), Adam with lr 1e-3 (App. A.4).
-Every forward, adjoint and optimiser step runs in the library's kernels.
+the paper's datasets are not available, so the tuples are synthetic): groups
+of 8 seeded systems, 2-D P1 FEM diffusion on jittered lattices and 3-D 7-point
+FD diffusion (log k a GRF, sigma 1, correlation 0.1), right-hand sides
+b ~ N(0, 1), and x = A^-1 b computed by this library's own IC(0)-PCG to a
+1e-10 relative residual.  Loss Eq. (loss_Ab), mean over a batch of 8 systems
+x 2 pairs (the paper's batch size 16 for 2-D problems), Adam with lr 1e-3
+(App. A.4) decayed by a cosine to 1e-4.  Every forward, adjoint and
+optimiser step runs in the library's kernels (BF16 tensor-core forward with
+the FP32 adjoint, or FP32 throughout).
 
 On this data the loss keeps falling long after PCG iterations stop improving
-(a trained network reaches 20x less loss than IC(0) while needing several
-times IC(0)'s iterations), so the run keeps the checkpoint with the fewest
-PCG iterations on two held-out systems of the training family (model
-selection by validation; the paper trains to convergence).
+(with the softplus diagonal a network reaches 20x less loss than IC(0) while
+needing several times IC(0)'s iterations), so the run keeps the checkpoint
+with the fewest PCG iterations on held-out systems of the training family
+(model selection by validation; the paper trains to convergence).  The
+committed network uses the App. A.3 factorisation L D L^T with D = diag(A):
 
-    python -m paper_2305_16432_gb300.train --steps 600 --out weights/fem2d_6x64.npy
+    python -m paper_2305_16432_gb300.train --steps 720 --val_every 40 --diag_mode 1 \
+        --sizes 96,128,160 --sizes3d 20,26,32 --precision bf16 --out weights/gnn_6x64.npy
 """
 from __future__ import annotations
 
@@ -86,21 +90,27 @@ def save_checkpoint(path, cfg, w, mom, vel, step, hist):
 
 
 def train(cfg: I.GnnConfig, steps=600, groups=4, per_group=8, pairs=8, m=128, lr=1e-3, lr_final=1e-4,
-          seed=2023, log_every=25, w0=None, ckpt=None, resume=None, val_every=50, precision=None, sizes=None):
+          seed=2023, log_every=25, w0=None, ckpt=None, resume=None, val_every=50, precision=None, sizes=None,
+          sizes3d=None):
     """Adam at lr (App. A.4), cosine-decayed to lr_final over the run; returns
     the weights with the fewest validation PCG iterations.  precision: the
     network forward's arithmetic (FP32, or BF16 tensor cores with the FP32
-    adjoint); sizes: lattice size of each group (default m for all)."""
+    adjoint); sizes: lattice size of each 2-D FEM group (default m for
+    all); sizes3d: grid side of each 3-D FD group (none by default)."""
     from . import build as B
     B.build()
     from . import npcg as N
     prec = N.FP32 if precision is None else precision
     sizes = sizes or [m] * groups
+    specs = [("fem", x) for x in sizes] + [("fd3", x) for x in (sizes3d or [])]
+    groups = len(specs)
     t0 = time.time()
     data = []
-    for g in range(groups):
-        mg = sizes[g % len(sizes)]
-        probs = [I.fem2d(mg, sigma=1.0, corr_len=0.1, seed=seed + 100 * g + k) for k in range(per_group)]
+    for g, (kind, mg) in enumerate(specs):
+        if kind == "fem":
+            probs = [I.fem2d(mg, sigma=1.0, corr_len=0.1, seed=seed + 100 * g + k) for k in range(per_group)]
+        else:
+            probs = [I.fd3d(mg, sigma=1.0, corr_len=0.1, seed=seed + 100 * g + k) for k in range(per_group)]
         data.append(make_group(N, probs, pairs, seed + g))
     t_data = time.time() - t0
     w = torch.as_tensor(I.gnn_weights(cfg, seed) if w0 is None else w0, device="cuda")
@@ -119,8 +129,11 @@ def train(cfg: I.GnnConfig, steps=600, groups=4, per_group=8, pairs=8, m=128, lr
     # validation: PCG iterations on held-out systems of the training family;
     # the checkpoint with the fewest mean iterations is kept
     vals = []
-    for k in range(2):
-        rp, ci, v = N.assemble_system(I.fem2d(m, sigma=1.0, corr_len=0.1, seed=8000 + k))
+    vprobs = [I.fem2d(m, sigma=1.0, corr_len=0.1, seed=8000 + k) for k in range(2)]
+    if sizes3d:
+        vprobs = [vprobs[0], I.fd3d(sizes3d[len(sizes3d) // 2], sigma=1.0, corr_len=0.1, seed=8000)]
+    for k, pv in enumerate(vprobs):
+        rp, ci, v = N.assemble_system(pv)
         Pv = N.analyse(rp, ci)
         vals.append((Pv, v, torch.as_tensor(I.rhs(Pv.n, 8000 + k), device="cuda")))
 
@@ -172,8 +185,9 @@ def main():
     ap.add_argument("--val_every", type=int, default=50)
     ap.add_argument("--diag_mode", type=int, default=0, help="0: softplus diagonal; 1: L D L^T with D = diag(A)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
-    ap.add_argument("--sizes", default="", help="comma-separated lattice sizes of the training groups")
-    ap.add_argument("--out", default=os.path.join(os.path.dirname(__file__), "weights", "fem2d_6x64.npy"))
+    ap.add_argument("--sizes", default="", help="comma-separated lattice sizes of the 2-D FEM training groups")
+    ap.add_argument("--sizes3d", default="", help="comma-separated grid sides of the 3-D FD training groups")
+    ap.add_argument("--out", default=os.path.join(os.path.dirname(__file__), "weights", "gnn_6x64.npy"))
     args = ap.parse_args()
     cfg = I.GnnConfig(n_mp=args.n_mp, l=2, l_mp=2, h=args.h, diag_mode=args.diag_mode)
     from . import build as B
@@ -181,24 +195,30 @@ def main():
     from . import npcg as N
     prec = N.BF16 if args.precision == "bf16" else N.FP32
     sizes = [int(x) for x in args.sizes.split(",") if x] or None
+    sizes3d = [int(x) for x in args.sizes3d.split(",") if x] or None
     w, hist, tm = train(cfg, steps=args.steps, m=args.m, lr=args.lr, lr_final=args.lr_final, ckpt=args.ckpt,
-                        resume=args.resume, val_every=args.val_every, precision=prec, sizes=sizes)
+                        resume=args.resume, val_every=args.val_every, precision=prec, sizes=sizes,
+                        sizes3d=sizes3d)
     w0 = torch.as_tensor(I.gnn_weights(cfg, 2023), device="cuda")
     held = [I.fem2d(args.m, sigma=1.0, corr_len=0.1, seed=9000 + k) for k in range(3)]
     ev = evaluate(N, cfg, w, held, precision=prec)
     ev0 = evaluate(N, cfg, w0, held[:1], precision=prec)
     small = evaluate(N, cfg, w, [I.fem2d(96, sigma=1.0, corr_len=0.1, seed=9200)], precision=prec)
     big = evaluate(N, cfg, w, [I.fem2d_256(seed=0)], precision=prec)
+    fd3 = evaluate(N, cfg, w, [I.fd3d(32, sigma=1.0, corr_len=0.1, seed=9300),
+                               I.fd3d(64, sigma=1.5, corr_len=0.05, seed=9301)], precision=prec)
     os.makedirs(os.path.dirname(os.path.abspath(args.out)), exist_ok=True)
     np.save(args.out, _np(w).astype(np.float32))
     meta = {"config": {"n_mp": cfg.n_mp, "l": cfg.l, "l_mp": cfg.l_mp, "h": cfg.h, "diag_mode": cfg.diag_mode},
             "train": {"steps": args.steps, "lr": args.lr, "lr_final": args.lr_final, "schedule": "cosine",
                       "batch": "8 systems x 2 pairs",
                       "selection": "checkpoint with the fewest validation PCG iterations",
-                      "systems": f"4 groups x 8 FEM lattices {sizes or [args.m]}, sigma 1, corr 0.1",
+                      "systems": f"groups of 8: 2-D FEM lattices {sizes or [args.m]}, 3-D FD sides "
+                                 f"{sizes3d or []}, sigma 1, corr 0.1",
                       "precision": args.precision, **tm},
             "loss_first": hist[0], "loss_last": float(np.mean(hist[-20:])),
             "heldout_fem128": ev, "untrained_fem128": ev0, "heldout_fem96": small, "fem256_seed0": big,
+            "heldout_fd3d": fd3,
             "learned_iters_fem256": big[0]["learned"]}
     with open(os.path.splitext(args.out)[0] + ".json", "w") as f:
         json.dump(meta, f, indent=1)

@@ -31,7 +31,7 @@ from paper_2305_16432_gb300 import inputs as I
 pytestmark = pytest.mark.gpu
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-WEIGHTS = os.path.join(ROOT, "paper_2305_16432_gb300", "weights", "fem2d_6x64.npy")
+WEIGHTS = os.path.join(ROOT, "paper_2305_16432_gb300", "weights", "gnn_6x64.npy")
 
 
 @pytest.fixture(scope="module")
