@@ -360,10 +360,12 @@ def run_solve(args, rank, world, local):
     # kernel launches per learned step (counted from the launch structure):
     # network: scales, 2 encoders, 2 per layer, decoder, L assembly
     gnn_launches = 1 + 2 + 2 * cfg.n_mp + 1 + 1
-    # PCG: 4 factor loads, init, 2 solves, r^T z, 11 per graph trip (2 iterations
-    # of 5 kernels + the loop condition), stats
+    # PCG: 4 factor loads, init, preconditioner apply, r^T z, per graph trip 2
+    # iterations (SpMV, update, r^T z and the apply) + the loop condition, stats;
+    # the level-synchronous apply is 2 solves + 2 gathers, the sync-free one 2 solves
+    apply = 4 if P.trsv_mode == N.TRSV_LEVELSYNC else 2
     trips = max(1, math.ceil(max(it_l) / 2))
-    pcg_launches = 4 + 1 + 2 + 1 + 11 * trips + 1
+    pcg_launches = 4 + 1 + apply + 1 + (2 * (3 + apply) + 1) * trips + 1
     launches = (gnn_launches + pcg_launches) * args.steps
 
     cpu = None

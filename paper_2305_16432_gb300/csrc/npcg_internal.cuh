@@ -108,9 +108,11 @@ struct alignas(16) CtaChunk {
 struct CtaLayout {
     bool built = false;
     bool window_ok = false;        // every dependency within the shared window
+    int win_slots = 0;             // window size (power of two) when window_ok
     int nsteps = 0, max_w = 0, max_np = 0;
     int64_t sbuf_len = 0, vbuf_len = 0;
     DevBuf<int32_t> cperm, cpos;   // processing order and its inverse
+    DevBuf<int32_t> other;         // backward layout: forward position of the row at each position
     DevBuf<int4> steps;            // {q0, nrows, width, 0}
     DevBuf<int64_t> soff, voff;
     DevBuf<int32_t> sys_step0;
@@ -156,6 +158,7 @@ struct Pattern {
     int trsv_mode = kTrsvSyncFree; // chosen by the autotuner
     float tune_ms[2] = {0.f, 0.f}; // measured fwd+bwd time per mode
     DevBuf<double> r_cf, y_cb, yglob;  // rhs in processing order, window backing
+    DevBuf<double> yq;             // solution of a level-synchronous solve in processing order
     // reduction chunks
     std::vector<Chunk> chunks_h;
     DevBuf<Chunk> chunks;
@@ -253,7 +256,9 @@ npcg_status cta_factor_load(Handle* h, CtaLayout* C, const double* L_val);
 npcg_status cta_gather(Handle* h, cudaStream_t s, const CtaLayout& C, int64_t n, const double* x, void* xp,
                        bool f32);
 npcg_status cta_trsv_launch(Handle* h, cudaStream_t s, Pattern* P, const CtaLayout& C, const void* rhs_perm,
-                            double* out, void* out2, const SysState* st, bool f32);
+                            void* outq, const SysState* st, bool f32);
+npcg_status cta_permute(Handle* h, cudaStream_t s, Pattern* P, const CtaLayout& C, void* outq, bool f32,
+                        const int32_t* idx, void* dst, bool dst_f32);
 npcg_status trsv_autotune(Handle* h, Pattern* P);
 npcg_status sptrsv_timed_run(Handle* h, Pattern* P, int transpose, const double* r, double* y, int reps,
                              double* ms_per_launch, bool f32);

@@ -525,6 +525,7 @@ npcg_status ensure_pcg_workspace(Handle* h, Pattern* P) {
         NPCG_CUDA(h, P->r_cf.ensure(P->n + 4));
         NPCG_CUDA(h, P->y_cb.ensure(P->n + 4));
         NPCG_CUDA(h, P->yglob.ensure(P->n));
+        NPCG_CUDA(h, P->yq.ensure(P->n + 4));
     }
     return NPCG_OK;
 }
@@ -558,8 +559,10 @@ PcgArgs pcg_args(Pattern* P, int precond) {
 // z = L^-T L^-1 r with the tuned triangular-solve design
 void apply_llt(Handle* h, cudaStream_t s, Pattern* P, bool batched, bool f32) {
     if (P->trsv_mode == kTrsvCta) {
-        cta_trsv_launch(h, s, P, P->cfwd, P->r_cf.p, nullptr, P->y_cb.p, P->st.p, f32);
-        cta_trsv_launch(h, s, P, P->cbwd, P->y_cb.p, P->z.p, nullptr, P->st.p, f32);
+        cta_trsv_launch(h, s, P, P->cfwd, P->r_cf.p, P->yq.p, P->st.p, f32);
+        cta_permute(h, s, P, P->cfwd, P->yq.p, f32, P->cbwd.other.p, P->y_cb.p, f32);
+        cta_trsv_launch(h, s, P, P->cbwd, P->y_cb.p, P->yq.p, P->st.p, f32);
+        cta_permute(h, s, P, P->cbwd, P->yq.p, f32, P->cbwd.cpos.p, P->z.p, false);
     } else {
         launch_trsv(h, s, P, 0, P->r.p, P->y.p, P->ctl.p + 2, batched, P->st.p, f32);
         launch_trsv(h, s, P, 1, P->y.p, P->z.p, P->ctl.p + 3, batched, P->st.p, f32);
@@ -639,7 +642,8 @@ npcg_status sptrsv_run(Handle* h, Pattern* P, int transpose, const double* r, do
         NPCG_TRY(ensure_pcg_workspace(h, P));
         const CtaLayout& C = transpose ? P->cbwd : P->cfwd;
         NPCG_TRY(cta_gather(h, h->stream, C, P->n, r, P->r_cf.p, false));
-        return cta_trsv_launch(h, h->stream, P, C, P->r_cf.p, y, nullptr, nullptr, false);
+        NPCG_TRY(cta_trsv_launch(h, h->stream, P, C, P->r_cf.p, P->yq.p, nullptr, false));
+        return cta_permute(h, h->stream, P, C, P->yq.p, false, C.cpos.p, y, false);
     }
     k_fill_sentinel<<<h->num_sms * 4, 256, 0, h->stream>>>(P->n, y);
     launch_trsv(h, h->stream, P, transpose, r, y, P->ctl.p + 2 + (transpose ? 1 : 0), false, nullptr, false);
@@ -661,13 +665,15 @@ npcg_status sptrsv_timed_run(Handle* h, Pattern* P, int transpose, const double*
             const CtaLayout& C = transpose ? P->cbwd : P->cfwd;
             cta_gather(h, h->stream, C, P->n, r, P->r_cf.p, f32);
             cudaEventRecord(e0, h->stream);
-            cta_trsv_launch(h, h->stream, P, C, P->r_cf.p, y, nullptr, nullptr, f32);
+            cta_trsv_launch(h, h->stream, P, C, P->r_cf.p, P->yq.p, nullptr, f32);
+            cudaEventRecord(e1, h->stream);
+            cta_permute(h, h->stream, P, C, P->yq.p, f32, C.cpos.p, y, false);
         } else {
             k_fill_sentinel<<<h->num_sms * 4, 256, 0, h->stream>>>(P->n, y);
             cudaEventRecord(e0, h->stream);
             launch_trsv(h, h->stream, P, transpose, r, y, P->ctl.p + 2 + (transpose ? 1 : 0), false, nullptr, f32);
+            cudaEventRecord(e1, h->stream);
         }
-        cudaEventRecord(e1, h->stream);
         cudaError_t e = cudaEventSynchronize(e1);
         if (e != cudaSuccess) { st = cuda_fail(h, e, "trsv timing"); break; }
         float ms = 0.0f;

@@ -2,24 +2,21 @@
 // two solves of "Solve P z = r" (Algorithm 1) with P = L L^T.
 //
 // The rows of a system are visited level by level (a level's rows depend
-// only on earlier levels), in steps of at most 256 rows of one level.  Each
-// step's structure (header, packed per-row records of four dependency slots
-// and the row's destinations), factor values (four per row, then the
-// reciprocal diagonal) and right-hand side are laid out contiguously in
-// processing order.  Consecutive steps are grouped into chunks that fill one
-// shared-memory stage; a producer warp streams the chunks into a ring of
-// stages with three TMA bulk copies each (cp.async.bulk), a "full" mbarrier
-// per stage completing on the transferred bytes and an "empty" mbarrier per
-// stage released by the consumer.  Chunking keeps many small steps in
-// flight, so the copy latency is hidden behind the dependency chain.
-//
-// One consumer warp solves the system.  Solution values of recent positions
-// live in a shared-memory window indexed by position (missing dependencies
-// point at a zero slot), so consecutive steps are ordered by __syncwarp()
-// alone: no CTA barrier sits on the dependency chain.  When a dependency
-// reaches further back than the window, the consumer reads the
-// position-ordered global copy (kWindow = false).  Values (T) are FP64 or
-// FP32.
+// only on earlier levels), split into steps of at most one row per consumer
+// thread.  Each step's structure (row ids, dependency positions, header),
+// factor values (reciprocal diagonal first) and right-hand side are laid out
+// contiguously in processing order.  Consecutive steps are grouped into
+// chunks that fill one shared-memory stage; a producer warp streams the
+// chunks into a ring of stages with three TMA bulk copies each
+// (cp.async.bulk), a "full" mbarrier per stage completing on the transferred
+// bytes and an "empty" mbarrier per stage released by the eight consumer
+// warps.  Chunking keeps many small steps in flight, so the copy latency is
+// hidden behind the dependency chain rather than paid every few steps.
+// Solution values of recent positions live in a shared-memory window indexed
+// by position, so the only synchronisation on the dependency chain is one
+// named barrier among the consumer warps per step.  When a dependency reaches
+// further back than the window, consumers read the position-ordered global
+// copy (kWindow = false).  Values (T) are FP64 or FP32.
 #include <algorithm>
 #include <vector>
 
@@ -29,15 +26,15 @@ namespace npcg {
 
 namespace {
 
-constexpr int kCtaRows = 256;            // rows per step (at most)
-constexpr int kGroup = 4;                // rows a lane processes together (4 x 32 = 128 rows)
-constexpr int kCtaThreads = 64;          // one consumer warp + one producer warp
-constexpr int kWin = 8192;               // shared window (positions), power of two
+constexpr int kCtaRows = 256;            // rows per step = consumer threads per CTA
+constexpr int kCtaThreads = kCtaRows + 32;   // + one producer warp
+constexpr int kWinMax = 8192;            // largest shared window (positions), power of two
+constexpr int kWinMin = 1024;            // smallest window
 constexpr int kMaxStages = 8;
 constexpr long long kMbarSpin = 1LL << 22;
 constexpr int kHdrInts = 4;              // {q0, nrows, width, pad} heads every structure block
 constexpr int kRec = 4;                  // dependencies held in a row's packed record
-constexpr int kWinPad = 32;              // window slots past kWin; slot kWin stays zero
+constexpr int kWinPad = 32;              // window slots past the window; the first stays zero
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -81,6 +78,7 @@ struct CtaDev {
     const void* vbuf;           // values (T): dinv[np] | val[w][np] per step
     int stages;
     int stage_cap;              // bytes per stage (multiple of 128)
+    int win;                    // window slots (power of two)
 };
 
 __host__ __device__ __forceinline__ int pad4(int x) { return (x + 3) & ~3; }
@@ -88,7 +86,8 @@ __host__ __device__ __forceinline__ int n_extra(int w) { return w > kRec ? w - k
 // Step blocks, np = nrows rounded up to 4.  Structure (int32):
 //   hdr[4] | dep[np][4] | {row, pos2}[np] | extra dep[n_extra][np]
 // dep holds processing positions (window slots once the window is known to
-// suffice: position mod kWin, a missing dependency -> the zero slot kWin;
+// suffice: position mod W, a missing dependency -> the zero slot W, where W
+// is the window size, the smallest power of two >= max(kWinMin, reach);
 // otherwise absolute positions, -1 when missing).  Values (T):
 //   l[np][4] | 1/diag[np] | extra l[n_extra][np]
 __host__ __device__ __forceinline__ int s_ints(int np, int w) { return kHdrInts + np * (6 + n_extra(w)); }
@@ -103,6 +102,15 @@ __host__ __device__ constexpr int rhs_align() { return 16 / (int)sizeof(T); }
 // and per stage the chunk's {nsteps, value offset, rhs offset, q0e}
 constexpr int kBarBytes = 256;
 
+// operands of one row of one step, held in registers by its consumer thread
+template <class T>
+struct StepOps {
+    int q0, nrows, width, np;
+    int4 dep;
+    T l[4];
+    T rhs, dinv;
+};
+
 __device__ __forceinline__ void ld_vec4(float (&l)[4], const float* p) {
     const float4 v = *reinterpret_cast<const float4*>(p);
     l[0] = v.x; l[1] = v.y; l[2] = v.z; l[3] = v.w;
@@ -112,9 +120,37 @@ __device__ __forceinline__ void ld_vec4(double (&l)[4], const double* p) {
     l[0] = a.x; l[1] = a.y; l[2] = b.x; l[3] = b.y;
 }
 
+template <class T>
+__device__ __forceinline__ void load_step(StepOps<T>& o, const int32_t* hdr, const T* vals, const T* rh, int q0e,
+                                          int t) {
+    const int4 h = *reinterpret_cast<const int4*>(hdr);
+    o.q0 = h.x;
+    o.nrows = h.y;
+    o.width = h.z;
+    o.np = pad4(h.y);
+    if (t < o.nrows) {
+        o.dep = reinterpret_cast<const int4*>(hdr + kHdrInts)[t];
+        ld_vec4(o.l, vals + 4 * t);
+        o.dinv = vals[4 * o.np + t];
+        o.rhs = rh[o.q0 - q0e + t];
+    }
+}
+
+// named barrier 1 among the consumer threads, returning whether every
+// consumer passed ok (all take the same decision)
+__device__ __forceinline__ bool consumers_agree(bool ok) {
+    uint32_t all_ok;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(all_ok)
+        : "r"((uint32_t)ok), "r"(kCtaRows)
+        : "memory");
+    return all_ok != 0;
+}
+
 template <bool kWindow, class T>
 __global__ void __launch_bounds__(kCtaThreads, 1) k_trsv_cta(CtaDev D, const T* __restrict__ rhs,
-                                                         double* out, T* out2, double* yglob,
+                                                         T* outq, double* yglob,
                                                          const SysState* st, int* flags) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int sys = blockIdx.x;
@@ -126,19 +162,20 @@ __global__ void __launch_bounds__(kCtaThreads, 1) k_trsv_cta(CtaDev D, const T* 
     uint64_t* empty = full + kMaxStages;
     int4* info = reinterpret_cast<int4*>(empty + kMaxStages);
     T* win = reinterpret_cast<T*>(smem + kBarBytes);
-    unsigned char* ring = smem + kBarBytes + (kWindow ? (kWin + kWinPad) * sizeof(T) : 0);
+    const int W = D.win;
+    unsigned char* ring = smem + kBarBytes + (kWindow ? (size_t)(W + kWinPad) * sizeof(T) : 0);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
+            mbar_init(&empty[s], kCtaRows / 32);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (kWindow && threadIdx.x < kWinPad) win[kWin + threadIdx.x] = (T)0;
+    if (kWindow && threadIdx.x < kWinPad) win[W + threadIdx.x] = (T)0;
     __syncthreads();
 
-    if (warp == 1) {
+    if (warp == kCtaRows / 32) {
         // ---------------- producer warp: stream the chunks through the ring
         // the 32 lanes fetch 32 chunk descriptors at a time; lane 0 issues
         int issued = 0;
@@ -187,105 +224,114 @@ __global__ void __launch_bounds__(kCtaThreads, 1) k_trsv_cta(CtaDev D, const T* 
         return;
     }
 
-    // ---------------- consumer warp
-    // One warp solves the system: lane l owns rows l, l + 32, ... of every
-    // step.  The rows of a step belong to one level, so they are independent:
-    // a lane loads the operands of up to kGroup rows, then their window
-    // values, then folds and stores them, overlapping the rows' latencies.
-    // Steps are separated by __syncwarp(), which orders the window writes of
-    // one step before the reads of the next.
-    int c = c0, k = 0;
-    for (;;) {
-        const int s = k % S;
-        const bool ok = mbar_wait_bounded(&full[s], (uint32_t)((k / S) & 1));
-        if (!__all_sync(0xffffffffu, ok)) {
-            if (lane == 0) atomicOr(flags, kFlagTimeout | kFlagAbort);
+    // ---------------- consumer warps
+    // Software pipeline: the operands of the next step (structure, values,
+    // right-hand side: nothing that depends on solution values) are loaded
+    // into registers before the current step computes, so only the window
+    // loads, the multiply-adds and the barrier sit on the dependency chain.
+    const int t = threadIdx.x;
+    StepOps<T> cur, nxt;
+    int c = c0, s = 0, u = 0, nst;
+    const int32_t* hdr;
+    const T* vals;
+    const T* rh;
+    int q0e;
+    {
+        const bool ok = mbar_wait_bounded(&full[0], 0u);
+        if (!consumers_agree(ok)) {
+            if (threadIdx.x == 0) atomicOr(flags, kFlagTimeout | kFlagAbort);
             return;
         }
-        const int4 inf = info[s];
-        const unsigned char* base = ring + (size_t)s * D.stage_cap;
-        const int32_t* hdr = reinterpret_cast<const int32_t*>(base);
-        const T* vals = reinterpret_cast<const T*>(base + inf.y);
-        const T* rh = reinterpret_cast<const T*>(base + inf.z);
-        const int q0e = inf.w;
-        for (int u = 0; u < inf.x; ++u) {
-            const int4 h = *reinterpret_cast<const int4*>(hdr);
-            const int q0 = h.x, nrows = h.y, width = h.z, np = pad4(h.y);
-            const int4* dep4 = reinterpret_cast<const int4*>(hdr + kHdrInts);
-            const int2* rp2 = reinterpret_cast<const int2*>(hdr + kHdrInts + 4 * np);
-            const T* dinv = vals + 4 * np;
-            const T* rhs_s = rh + (q0 - q0e);
-            for (int r0 = 0; r0 < nrows; r0 += 32 * kGroup) {
-                int4 d[kGroup];
-                int2 rp[kGroup];
-                T l[kGroup][4], di[kGroup], acc[kGroup], y[kGroup][4];
-                bool act[kGroup];
+        const int4 inf = info[0];
+        nst = inf.x;
+        hdr = reinterpret_cast<const int32_t*>(ring);
+        vals = reinterpret_cast<const T*>(ring + inf.y);
+        rh = reinterpret_cast<const T*>(ring + inf.z);
+        q0e = inf.w;
+        load_step(cur, hdr, vals, rh, q0e, t);
+    }
+    for (;;) {
+        // locate and load the next step
+        const int32_t* chdr = hdr;          // the current step, for rows wider than the registers
+        const T* cvals = vals;
+        bool has_next = true, waited = false, ok = true;
+        int nc = c, ns = s, nu = u + 1, nnst = nst;
+        if (u + 1 < nst) {
+            hdr += s_ints(cur.np, cur.width);
+            vals += v_elems(cur.np, cur.width);
+        } else if (c + 1 < c1) {
+            nc = c + 1;
+            ns = (nc - c0) % S;
+            nu = 0;
+            waited = true;
+            ok = mbar_wait_bounded(&full[ns], (uint32_t)(((nc - c0) / S) & 1));
+            if (ok) {
+                const int4 inf = info[ns];
+                const unsigned char* base = ring + (size_t)ns * D.stage_cap;
+                nnst = inf.x;
+                hdr = reinterpret_cast<const int32_t*>(base);
+                vals = reinterpret_cast<const T*>(base + inf.y);
+                rh = reinterpret_cast<const T*>(base + inf.z);
+                q0e = inf.w;
+            }
+        } else {
+            has_next = false;
+        }
+        if (has_next && ok) load_step(nxt, hdr, vals, rh, q0e, t);
+        // the current step
+        if (t < cur.nrows) {
+            T acc = cur.rhs;
+            if (kWindow) {
+                // missing dependencies read the zero slot with a zero value
+                const T y0 = win[cur.dep.x], y1 = win[cur.dep.y], y2 = win[cur.dep.z], y3 = win[cur.dep.w];
+                acc = fma(-cur.l[0], y0, acc);
+                acc = fma(-cur.l[1], y1, acc);
+                acc = fma(-cur.l[2], y2, acc);
+                acc = fma(-cur.l[3], y3, acc);
+            } else {
+                const int pd[4] = {cur.dep.x, cur.dep.y, cur.dep.z, cur.dep.w};
 #pragma unroll
-                for (int j = 0; j < kGroup; ++j) {
-                    const int tr = r0 + 32 * j + lane;
-                    act[j] = tr < nrows;
-                    if (act[j]) {
-                        d[j] = dep4[tr];
-                        rp[j] = rp2[tr];
-                        ld_vec4(l[j], vals + 4 * tr);
-                        di[j] = dinv[tr];
-                        acc[j] = rhs_s[tr];
-                    }
-                }
-#pragma unroll
-                for (int j = 0; j < kGroup; ++j) {
-                    if (act[j]) {
-                        if (kWindow) {
-                            // missing dependencies read the zero slot with a zero value
-                            y[j][0] = win[d[j].x];
-                            y[j][1] = win[d[j].y];
-                            y[j][2] = win[d[j].z];
-                            y[j][3] = win[d[j].w];
-                        } else {
-                            y[j][0] = d[j].x >= 0 ? (T)__ldcg(yglob + d[j].x) : (T)0;
-                            y[j][1] = d[j].y >= 0 ? (T)__ldcg(yglob + d[j].y) : (T)0;
-                            y[j][2] = d[j].z >= 0 ? (T)__ldcg(yglob + d[j].z) : (T)0;
-                            y[j][3] = d[j].w >= 0 ? (T)__ldcg(yglob + d[j].w) : (T)0;
-                        }
-                    }
-                }
-#pragma unroll
-                for (int j = 0; j < kGroup; ++j) {
-                    if (act[j]) {
-#pragma unroll
-                        for (int kk = 0; kk < 4; ++kk) acc[j] = fma(-l[j][kk], y[j][kk], acc[j]);
-                        if (width > kRec) {
-                            const int tr = r0 + 32 * j + lane;
-                            const int32_t* xdep = hdr + kHdrInts + 6 * np;
-                            const T* xval = vals + 5 * np;
-                            for (int kk = 0; kk < width - kRec; ++kk) {
-                                const int pk = xdep[kk * np + tr];
-                                if (kWindow) acc[j] = fma(-xval[kk * np + tr], win[pk], acc[j]);
-                                else if (pk >= 0) acc[j] = fma(-xval[kk * np + tr], (T)__ldcg(yglob + pk), acc[j]);
-                            }
-                        }
-                    }
-                }
-#pragma unroll
-                for (int j = 0; j < kGroup; ++j) {
-                    if (act[j]) {
-                        const T yv = acc[j] * di[j];
-                        const int q = q0 + r0 + 32 * j + lane;
-                        if (kWindow) win[q & (kWin - 1)] = yv;
-                        else yglob[q] = (double)yv;
-                        if (out) out[rp[j].x] = (double)yv;
-                        if (out2) out2[rp[j].y] = yv;
-                    }
+                for (int kk = 0; kk < 4; ++kk)
+                    if (pd[kk] >= 0) acc = fma(-cur.l[kk], (T)__ldcg(yglob + pd[kk]), acc);
+            }
+            if (cur.width > kRec) {
+                const int32_t* xdep = chdr + kHdrInts + 6 * cur.np;
+                const T* xval = cvals + 5 * cur.np;
+                for (int kk = 0; kk < cur.width - kRec; ++kk) {
+                    const int pk = xdep[kk * cur.np + t];
+                    if (kWindow) acc = fma(-xval[kk * cur.np + t], win[pk], acc);
+                    else if (pk >= 0) acc = fma(-xval[kk * cur.np + t], (T)__ldcg(yglob + pk), acc);
                 }
             }
-            if (!kWindow) __threadfence_block();
-            __syncwarp();
-            hdr += h.w >> 16;
-            vals += h.w & 0xFFFF;
+            const T y = acc * cur.dinv;
+            const int q = cur.q0 + t;
+            // the solution in processing order (coalesced); a gather moves it
+            // to the order its reader needs
+            if (kWindow) {
+                win[q & (W - 1)] = y;
+                outq[q] = y;
+            } else {
+                yglob[q] = (double)y;
+            }
         }
-        if (lane == 0) mbar_arrive(&empty[s]);   // every lane is past its reads of this stage
-        if (++c == c1) break;
-        ++k;
+        if (!kWindow) __threadfence_block();
+        // this step's solutions are visible to the next step; a next chunk
+        // is used only if every consumer's wait for it succeeded
+        if (waited) {
+            if (!consumers_agree(ok)) {
+                if (threadIdx.x == 0) atomicOr(flags, kFlagTimeout | kFlagAbort);
+                return;
+            }
+        } else {
+            asm volatile("bar.sync 1, %0;" ::"r"(kCtaRows) : "memory");
+        }
+        if (u + 1 == nst && lane == 0) mbar_arrive(&empty[s]);   // chunk c fully read
+        if (!has_next) break;
+        cur = nxt;
+        c = nc;
+        s = ns;
+        u = nu;
+        nst = nnst;
     }
 }
 
@@ -304,12 +350,7 @@ __global__ void k_cta_fill(int64_t n, const int32_t* cperm, const int32_t* step_
         const int t = (int)(q - d.x);
         int32_t* sb = sbuf + soff[stp];
         int32_t* vs = vsrc + voff[stp];
-        if (t == 0) {
-            sb[0] = d.x;
-            sb[1] = d.y;
-            sb[2] = d.z;
-            sb[3] = (s_ints(np, d.z) << 16) | v_elems(np, d.z);   // block sizes (checked < 2^16 on the host)
-        }
+        if (t == 0) { sb[0] = d.x; sb[1] = d.y; sb[2] = d.z; sb[3] = 0; }
         int32_t* body = sb + kHdrInts;
         body[4 * np + 2 * t] = row;
         body[4 * np + 2 * t + 1] = 0;                   // pos2: set by k_cta_pos2
@@ -359,7 +400,7 @@ __global__ void k_cta_reach(int64_t n, const int32_t* step_of_pos, const int4* s
 
 // the window suffices: dependency positions become window slots
 __global__ void k_cta_window(int64_t n, const int32_t* step_of_pos, const int4* steps, const int64_t* soff,
-                             int32_t* sbuf) {
+                             int W, int32_t* sbuf) {
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
          q += (int64_t)gridDim.x * blockDim.x) {
         const int stp = step_of_pos[q];
@@ -370,7 +411,7 @@ __global__ void k_cta_window(int64_t n, const int32_t* step_of_pos, const int4* 
         const int kmax = d.z > kRec ? d.z : kRec;
         for (int k = 0; k < kmax; ++k) {
             int32_t* p = dep_slot(body, np, t, k);
-            *p = *p >= 0 ? (*p & (kWin - 1)) : kWin;
+            *p = *p >= 0 ? (*p & (W - 1)) : W;
         }
     }
 }
@@ -411,6 +452,19 @@ __global__ void k_mark_diag(int nsteps, const int4* steps, const int64_t* voff, 
     }
 }
 
+__global__ void k_compose(int64_t n, const int32_t* perm, const int32_t* pos, int32_t* out) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
+         q += (int64_t)gridDim.x * blockDim.x)
+        out[q] = pos[perm[q]];
+}
+
+template <class S, class D>
+__global__ void k_permute(int64_t n, const int32_t* idx, const S* __restrict__ src, D* __restrict__ dst) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = (D)src[idx[i]];
+}
+
 template <class T>
 __global__ void k_gather_perm(int64_t n, const int32_t* cperm, const double* x, T* xp) {
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
@@ -418,13 +472,18 @@ __global__ void k_gather_perm(int64_t n, const int32_t* cperm, const double* x, 
         xp[q] = (T)x[cperm[q]];
 }
 
-size_t win_bytes(const CtaLayout& C, bool f32) { return C.window_ok ? (size_t)(kWin + kWinPad) * (f32 ? 4 : 8) : 0; }
+size_t win_bytes(const CtaLayout& C, bool f32) {
+    return C.window_ok ? (size_t)(C.win_slots + kWinPad) * (f32 ? 4 : 8) : 0;
+}
 
 size_t smem_bytes(const CtaLayout& C, bool f32) {
     return kBarBytes + win_bytes(C, f32) + (size_t)C.stage_cap[f32] * C.nstages[f32];
 }
 
+// shared memory per CTA: everything when each system has an SM of its own,
+// half when more systems than SMs share the GPU (two CTAs per SM)
 constexpr size_t kSmemMax = 220 * 1024;
+constexpr size_t kSmemHalf = 110 * 1024;
 
 // Groups the steps of every system into chunks of at most cap bytes
 // (structure + values + right-hand side) for value size vsz; returns false
@@ -572,20 +631,18 @@ npcg_status cta_layout_build(Handle* h, Pattern* P, bool upper, CtaLayout* C) {
     NPCG_CUDA(h, cudaGetLastError());
     unsigned long long rh = 0;
     NPCG_TRY(read_scalar(h, reach.p, &rh));
-    C->window_ok = rh <= (unsigned long long)kWin;
+    C->window_ok = rh <= (unsigned long long)kWinMax;
+    C->win_slots = kWinMin;
+    if (C->window_ok)
+        while ((unsigned long long)C->win_slots < rh) C->win_slots *= 2;
     if (C->window_ok) {
-        k_cta_window<<<blocks, 256, 0, h->stream>>>(n, C->step_of_pos.p, C->steps.p, C->soff.p, C->sbuf.p);
+        k_cta_window<<<blocks, 256, 0, h->stream>>>(n, C->step_of_pos.p, C->steps.p, C->soff.p, C->win_slots,
+                                                    C->sbuf.p);
         NPCG_CUDA(h, cudaGetLastError());
     }
-    // step headers carry their block sizes in 16 bits each; a step with
-    // extremely many dependencies per row leaves this design unusable
-    bool sizes_ok = true;
-    for (int i = 0; i < nsteps; ++i)
-        if (s_ints(pad4(steps[i].y), steps[i].z) >= 65536 || v_elems(pad4(steps[i].y), steps[i].z) >= 65536)
-            sizes_ok = false;
     // chunks per value type: the stage capacity is the larger of the biggest
     // single step and an even split of the free shared memory into kMaxStages
-    for (int f32 = 0; f32 < 2 && sizes_ok; ++f32) {
+    for (int f32 = 0; f32 < 2; ++f32) {
         const size_t vsz = f32 ? 4 : 8;
         const int al = (int)(16 / vsz);
         size_t single = 0;
@@ -595,7 +652,8 @@ npcg_status cta_layout_build(Handle* h, Pattern* P, bool upper, CtaLayout* C) {
             const size_t rb = (size_t)(((steps[i].x + steps[i].y - q0e) + al - 1) & ~(al - 1)) * vsz;
             single = std::max(single, (size_t)s_ints(np, steps[i].z) * 4 + (size_t)v_elems(np, steps[i].z) * vsz + rb);
         }
-        const size_t avail = kSmemMax - kBarBytes - win_bytes(*C, f32 != 0);
+        const size_t budget = P->nsys > h->num_sms ? kSmemHalf : kSmemMax;
+        const size_t avail = budget - kBarBytes - win_bytes(*C, f32 != 0);
         size_t cap = std::max(single, avail / kMaxStages);
         cap = (cap + 127) & ~size_t(127);
         const int stages = (int)std::min<size_t>(kMaxStages, avail / cap);
@@ -632,7 +690,36 @@ npcg_status cta_link(Handle* h, Pattern* P) {
     const int blocks = std::max(1, std::min(ceil_div(P->n, 256), h->num_sms * 8));
     k_cta_pos2<<<blocks, 256, 0, h->stream>>>(P->n, P->cfwd.step_of_pos.p, P->cfwd.steps.p, P->cfwd.soff.p,
                                               P->cbwd.cpos.p, P->cfwd.sbuf.p);
+    NPCG_CUDA(h, P->cbwd.other.alloc(P->n));
+    k_compose<<<blocks, 256, 0, h->stream>>>(P->n, P->cbwd.cperm.p, P->cfwd.cpos.p, P->cbwd.other.p);
     NPCG_CUDA(h, cudaGetLastError());
+    return NPCG_OK;
+}
+
+// where the direction's solution is in processing order: the output buffer
+// (value type) with the window, else the FP64 global copy
+static void out_source(Pattern* P, const CtaLayout& C, void* outq, bool f32, const void** src, int* src_kind) {
+    if (C.window_ok) { *src = outq; *src_kind = f32 ? 1 : 0; }
+    else { *src = P->yglob.p; *src_kind = 0; }
+}
+
+// dst[i] = src[idx[i]]: the solution of a solve (processing order) into the
+// order its reader needs (idx = positions); dst FP64 or the value type
+npcg_status cta_permute(Handle* h, cudaStream_t s, Pattern* P, const CtaLayout& C, void* outq, bool f32,
+                        const int32_t* idx, void* dst, bool dst_f32) {
+    const void* src;
+    int kind;
+    out_source(P, C, outq, f32, &src, &kind);
+    const int blocks = std::max(1, std::min(ceil_div(P->n, 256), h->num_sms * 8));
+    const int64_t n = P->n;
+    if (kind == 1 && dst_f32)
+        k_permute<float, float><<<blocks, 256, 0, s>>>(n, idx, static_cast<const float*>(src), static_cast<float*>(dst));
+    else if (kind == 1)
+        k_permute<float, double><<<blocks, 256, 0, s>>>(n, idx, static_cast<const float*>(src), static_cast<double*>(dst));
+    else if (dst_f32)
+        k_permute<double, float><<<blocks, 256, 0, s>>>(n, idx, static_cast<const double*>(src), static_cast<float*>(dst));
+    else
+        k_permute<double, double><<<blocks, 256, 0, s>>>(n, idx, static_cast<const double*>(src), static_cast<double*>(dst));
     return NPCG_OK;
 }
 
@@ -657,8 +744,13 @@ npcg_status cta_gather(Handle* h, cudaStream_t s, const CtaLayout& C, int64_t n,
 // entries of the value type, the last ones padding); out (natural order,
 // FP64) and/or out2 (positions of the other direction, value type) receive
 // the solution.  f32: FP32 factor, arithmetic, right-hand side and out2.
+// rhs_perm: right-hand side in this direction's processing order (n + 4
+// entries of the value type, the last ones padding); outq (n entries of the
+// value type) receives the solution in processing order when the shared
+// window suffices, otherwise the solution is in P->yglob (FP64); cta_permute
+// moves it on.  f32: FP32 factor, arithmetic, right-hand side and outq.
 npcg_status cta_trsv_launch(Handle* h, cudaStream_t s, Pattern* P, const CtaLayout& C, const void* rhs_v,
-                            double* out, void* out2_v, const SysState* st, bool f32) {
+                            void* outq, const SysState* st, bool f32) {
     const int stages = C.nstages[f32];
     if (stages < 2) return set_error(h, NPCG_EINVAL, "level-synchronous layout does not fit shared memory");
     CtaDev d;
@@ -668,18 +760,19 @@ npcg_status cta_trsv_launch(Handle* h, cudaStream_t s, Pattern* P, const CtaLayo
     d.vbuf = f32 ? (const void*)C.vbuf32.p : (const void*)C.vbuf.p;
     d.stages = stages;
     d.stage_cap = C.stage_cap[f32];
+    d.win = C.win_slots;
     const size_t smem = smem_bytes(C, f32);
     int* flags = P->ctl.p + 1;
     if (f32) {
         const float* rp = static_cast<const float*>(rhs_v);
-        float* o2 = static_cast<float*>(out2_v);
-        if (C.window_ok) k_trsv_cta<true, float><<<P->nsys, kCtaThreads, smem, s>>>(d, rp, out, o2, nullptr, st, flags);
-        else k_trsv_cta<false, float><<<P->nsys, kCtaThreads, smem, s>>>(d, rp, out, o2, P->yglob.p, st, flags);
+        float* oq = static_cast<float*>(outq);
+        if (C.window_ok) k_trsv_cta<true, float><<<P->nsys, kCtaThreads, smem, s>>>(d, rp, oq, nullptr, st, flags);
+        else k_trsv_cta<false, float><<<P->nsys, kCtaThreads, smem, s>>>(d, rp, nullptr, P->yglob.p, st, flags);
     } else {
         const double* rp = static_cast<const double*>(rhs_v);
-        double* o2 = static_cast<double*>(out2_v);
-        if (C.window_ok) k_trsv_cta<true, double><<<P->nsys, kCtaThreads, smem, s>>>(d, rp, out, o2, nullptr, st, flags);
-        else k_trsv_cta<false, double><<<P->nsys, kCtaThreads, smem, s>>>(d, rp, out, o2, P->yglob.p, st, flags);
+        double* oq = static_cast<double*>(outq);
+        if (C.window_ok) k_trsv_cta<true, double><<<P->nsys, kCtaThreads, smem, s>>>(d, rp, oq, nullptr, st, flags);
+        else k_trsv_cta<false, double><<<P->nsys, kCtaThreads, smem, s>>>(d, rp, nullptr, P->yglob.p, st, flags);
     }
     NPCG_CUDA(h, cudaGetLastError());
     return NPCG_OK;
