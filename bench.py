@@ -163,11 +163,28 @@ SOLVE_WORKLOADS = ("fem2d_256", "fd3d_128", "batched_256")
 
 
 def _problems(I, workload, rank):
+    """The systems rank `rank` solves: independent problems, seeded by rank
+    (weak scaling, no data-path collective)."""
     if workload == "fem2d_256":
         return [I.fem2d_256(seed=rank)]
     if workload == "fd3d_128":
         return [I.fd3d_128(seed=rank)]
     return I.batched_mix(256, seed=rank)
+
+
+def job_ms_per_step(local_ms, world, device=None):
+    """Slowest rank's ms per step (the job ends when the last rank ends)."""
+    if world <= 1:
+        return float(local_ms)
+    import torch
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(ms_per_step, systems_per_rank, world):
+    """Whole-job metric: ms per system over the systems all ranks solved."""
+    return ms_per_step / (systems_per_rank * world)
 
 
 def _assemble(N, I, probs, rank):
@@ -314,12 +331,8 @@ def run_solve(args, rank, world, local):
     if world > 1:
         torch.distributed.barrier()
     ms_i, st_i = _timed(ic0_step, args.steps, stream, flush)
-    ms_per_step = float(np.sum(ms_l)) / args.steps
-    if world > 1:
-        t = torch.tensor([ms_per_step], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_per_step = float(t.item())
-    value = ms_per_step / (nsys * world)
+    ms_per_step = job_ms_per_step(float(np.sum(ms_l)) / args.steps, world, dev)
+    value = job_value(ms_per_step, nsys, world)
     it_l = [s["iters"] for s in st_l]
     it_i = [s["iters"] for s in st_i]
     assert all(s["status"] == 0 for s in st_l + st_i), "a system did not converge"

@@ -15,7 +15,10 @@
 #include <algorithm>
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "gnn_common.cuh"
+#include "tc_common.cuh"
 
 namespace npcg {
 
@@ -273,6 +276,269 @@ npcg_status launch_bwd(Handle* h, int mode, const MlpBwdArgs& a) {
     }
 }
 
+// ---- MLP backward on the tensor cores (BF16 operands, FP32 accumulate)
+// Per 128-row tile: the layer input is gathered from the FP32 tapes into the
+// swizzled K-major BF16 operand (the forward's BF16 operands are the BF16
+// roundings of these tapes, so the recompute reproduces them); the hidden
+// activations A_1..A_depth are recomputed (tapeA, ReLU masks kept as bits);
+// then G_{l-1} = (G_l W_l) (.) [A_l > 0] down the layers (tapeG) and the
+// input gradient G_0 W_0 by 64-wide segments.  Backward products use W_l^T,
+// staged once per CTA: B[i][o] = W_l[o][i] (K = o).  The node update reads
+// its aggregation from the forward's tape.
+struct BtPlan {
+    uint32_t a0, ah, g, wf, wb, bias, misc, total;
+};
+__host__ __device__ inline BtPlan bt_plan(int in, int depth, bool dec) {
+    BtPlan p;
+    const uint32_t blk = kM * 128;                                  // [128 x 64] BF16
+    const uint32_t wblk = kH * 128;                                 // [64 x 64] BF16
+    p.a0 = 0;
+    p.ah = p.a0 + (uint32_t)(in / 64) * blk;                        // A_1..A_depth
+    p.g = p.ah + (uint32_t)depth * blk;                             // gradient operand
+    p.wf = p.g + blk;                                               // forward W_0..W_{depth-1}
+    p.wb = p.wf + (uint32_t)(in / 64) * wblk + (uint32_t)(depth - 1) * wblk;
+    // backward W_l^T: l = 0 (in/64 blocks), 1..depth-1, depth (unless scalar)
+    p.bias = p.wb + (uint32_t)(in / 64) * wblk + (uint32_t)(depth - 1 + (dec ? 0 : 1)) * wblk;
+    p.misc = p.bias + (uint32_t)(depth + 1) * kH * 4;
+    p.total = p.misc + 64;
+    return p;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) k_mlp_bwd_tc(MlpBwdArgs a, const float* agg_in, int* flags) {
+    extern __shared__ __align__(1024) unsigned char sm_raw[];
+    unsigned char* sm = sm_raw + ((1024u - (s_addr(sm_raw) & 1023u)) & 1023u);
+    constexpr int IN = mode_in(MODE, kH);
+    constexpr bool kDec = MODE == MODE_DEC;
+    constexpr int NKB = IN / 64;
+    const int depth = a.f.depth;
+    const BtPlan P = bt_plan(IN, depth, kDec);
+    unsigned char* A0 = sm + P.a0;
+    unsigned char* Ah = sm + P.ah;
+    unsigned char* Gop = sm + P.g;
+    unsigned char* Wf = sm + P.wf;
+    unsigned char* Wb = sm + P.wb;
+    float* bias = reinterpret_cast<float*>(sm + P.bias);       // [depth][64]; [depth] = scalar layer W (DEC)
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + P.misc);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + P.misc + 8);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t blk = kM * 128, wblk = kH * 128;
+
+    // ---- stage weights (BF16, K-major) and biases
+    {
+        const float* src = a.f.w;
+        for (int l = 0; l <= depth; ++l) {
+            const int fi = l == 0 ? IN : kH, fo = (kDec && l == depth) ? 1 : kH;
+            if (l < depth) {
+                // forward: B rows = output o, K = input i
+                unsigned char* base = Wf + (l == 0 ? 0u : (uint32_t)NKB * wblk + (uint32_t)(l - 1) * wblk);
+                for (int t = tid; t < fo * fi; t += kThreads) {
+                    const int o = t / fi, i = t % fi;
+                    *reinterpret_cast<__nv_bfloat16*>(base + (uint32_t)(i / 64) * wblk + swz(o, i % 64)) =
+                        __float2bfloat16_rn(src[t]);
+                }
+                for (int t = tid; t < kH; t += kThreads) bias[l * kH + t] = src[fi * fo + t];
+            }
+            if (!(kDec && l == depth)) {
+                // backward: B rows = input i, K = output o
+                unsigned char* base = Wb + (l == 0 ? 0u : (uint32_t)NKB * wblk + (uint32_t)(l - 1) * wblk);
+                for (int t = tid; t < fo * fi; t += kThreads) {
+                    const int o = t / fi, i = t % fi;
+                    *reinterpret_cast<__nv_bfloat16*>(base + (uint32_t)(i / 64) * wblk + swz(i % 64, o)) =
+                        __float2bfloat16_rn(src[t]);
+                }
+            } else {
+                for (int t = tid; t < kH; t += kThreads) bias[depth * kH + t] = src[t];   // W_depth[0][i]
+            }
+            src += fi * fo + fo;
+        }
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_addr(bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(s_addr(tmem_slot))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t my_lanes = tmem + ((uint32_t)(warp * 32) << 16);
+    uint32_t phase = 0;
+    bool ok = true;
+
+    // one MMA chain D = A (128 x 64*nkb) . B^T, then wait; false on timeout
+    auto mma_wait = [&](const unsigned char* Aop, const unsigned char* Bop, int nkb) -> bool {
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (tid == 0) {
+            const uint32_t abase = s_addr(Aop), bbase = s_addr(Bop);
+            for (int s = 0; s < nkb * 4; ++s) {
+                const uint32_t kb = (uint32_t)(s >> 2), ko = (uint32_t)(s & 3) * 32;
+                mma_bf16(tmem, smem_desc(abase + kb * blk + ko), smem_desc(bbase + kb * wblk + ko), s > 0 ? 1u : 0u);
+            }
+            mma_commit(bar);
+        }
+        bool w = bar_wait(bar, phase);
+        phase ^= 1u;
+        if (!__syncthreads_and(w)) return false;
+        tc_fence_after();
+        return true;
+    };
+    auto ld64 = [&](float (&v)[64]) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float t16[16];
+            tmem_ld16(my_lanes + q * 16, t16);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[q * 16 + i] = t16[i];
+        }
+        tmem_wait_ld();
+    };
+    // row tid of a [128 x 64] operand from 64 FP32 values
+    auto put_row = [&](unsigned char* Op, const float (&v)[64]) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            __nv_bfloat162 h2[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) h2[j] = __floats2bfloat162_rn(v[c * 8 + 2 * j], v[c * 8 + 2 * j + 1]);
+            *reinterpret_cast<uint4*>(Op + swz(tid, c * 8)) = *reinterpret_cast<uint4*>(h2);
+        }
+    };
+    auto store_row = [&](float* dst, int64_t row, const float (&v)[64]) {
+        float4* o = reinterpret_cast<float4*>(dst + row * kH);
+#pragma unroll
+        for (int c = 0; c < 16; ++c) o[c] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+    };
+
+    const int64_t ntiles = (a.f.nrows + kM - 1) / kM;
+    for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        const int64_t row0 = tile * kM, row = row0 + tid;
+        const bool live = row < a.f.nrows;
+        // ---- layer input: 8-feature chunks of the FP32 tapes -> BF16 operand
+        for (int idx = tid; idx < kM * (IN / 8); idx += kThreads) {
+            const int r = idx / (IN / 8), c = idx % (IN / 8);
+            const int64_t k = row0 + r;
+            float4 x0 = make_float4(0.f, 0.f, 0.f, 0.f), x1 = x0;
+            if (k < a.f.nrows) {
+                const int seg = c >> 3, cc = c & 7;
+                const float* src;
+                if (MODE == MODE_EDGE)
+                    src = seg == 0 ? a.f.ein + k * kH : seg == 1 ? a.f.vin + (int64_t)a.f.erow[k] * kH
+                                                                 : a.f.vin + (int64_t)a.f.ci[k] * kH;
+                else if (MODE == MODE_NODE)
+                    src = seg == 0 ? a.f.vin + k * kH : agg_in + k * kH;
+                else
+                    src = a.f.ein + k * kH;
+                x0 = *reinterpret_cast<const float4*>(src + cc * 8);
+                x1 = *reinterpret_cast<const float4*>(src + cc * 8 + 4);
+            }
+            __nv_bfloat162 h2[4] = {__floats2bfloat162_rn(x0.x, x0.y), __floats2bfloat162_rn(x0.z, x0.w),
+                                    __floats2bfloat162_rn(x1.x, x1.y), __floats2bfloat162_rn(x1.z, x1.w)};
+            *reinterpret_cast<uint4*>(A0 + (uint32_t)(c >> 3) * blk + swz(r, (c & 7) * 8)) =
+                *reinterpret_cast<uint4*>(h2);
+        }
+        // ---- forward recompute of A_1..A_depth
+        uint64_t mask[kMaxDepth + 1];
+        for (int l = 0; l < depth && ok; ++l) {
+            const unsigned char* Aop = l == 0 ? A0 : Ah + (uint32_t)(l - 1) * blk;
+            const unsigned char* Bop = Wf + (l == 0 ? 0u : (uint32_t)NKB * wblk + (uint32_t)(l - 1) * wblk);
+            if (!mma_wait(Aop, Bop, l == 0 ? NKB : 1)) { ok = false; break; }
+            float v[64];
+            ld64(v);
+            uint64_t m = 0;
+#pragma unroll
+            for (int o = 0; o < 64; ++o) {
+                v[o] = fmaxf(v[o] + bias[l * kH + o], 0.0f);
+                m |= (uint64_t)(v[o] > 0.0f) << o;
+            }
+            mask[l + 1] = m;
+            put_row(Ah + (uint32_t)l * blk, v);
+            if (live) store_row(a.tapeA[l + 1], row, v);
+        }
+        if (!ok) break;
+        // ---- G_{depth-1}
+        {
+            float v[64];
+            if (kDec) {
+                const float g = live ? a.gout[row] : 0.0f;
+#pragma unroll
+                for (int i = 0; i < 64; ++i) v[i] = g * bias[depth * kH + i];
+            } else {
+                if (live) {
+                    const float4* gp = reinterpret_cast<const float4*>(a.gout + row * kH);
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) {
+                        const float4 q = gp[c];
+                        v[4 * c] = q.x; v[4 * c + 1] = q.y; v[4 * c + 2] = q.z; v[4 * c + 3] = q.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 64; ++i) v[i] = 0.0f;
+                }
+                put_row(Gop, v);
+                const unsigned char* Bop = Wb + (uint32_t)NKB * wblk + (uint32_t)(depth - 1) * wblk;
+                if (!mma_wait(Gop, Bop, 1)) { ok = false; break; }
+                ld64(v);
+            }
+            const uint64_t m = mask[depth];
+#pragma unroll
+            for (int i = 0; i < 64; ++i) v[i] = (m >> i) & 1 ? v[i] : 0.0f;
+            put_row(Gop, v);
+            if (live) store_row(a.tapeG[depth - 1], row, v);
+        }
+        // ---- G_{l-1} = (G_l W_l) (.) [A_l > 0], l = depth-1 .. 1
+        for (int l = depth - 1; l >= 1 && ok; --l) {
+            const unsigned char* Bop = Wb + (uint32_t)NKB * wblk + (uint32_t)(l - 1) * wblk;
+            if (!mma_wait(Gop, Bop, 1)) { ok = false; break; }
+            float v[64];
+            ld64(v);
+            const uint64_t m = mask[l];
+#pragma unroll
+            for (int i = 0; i < 64; ++i) v[i] = (m >> i) & 1 ? v[i] : 0.0f;
+            put_row(Gop, v);
+            if (live) store_row(a.tapeG[l - 1], row, v);
+        }
+        if (!ok) break;
+        // ---- input gradient G_0 W_0, one 64-wide segment per product
+        for (int s = 0; s < NKB && ok; ++s) {
+            if (!mma_wait(Gop, Wb + (uint32_t)s * wblk, 1)) { ok = false; break; }
+            float v[64];
+            ld64(v);
+            if (live && a.dx[s]) store_row(a.dx[s], row, v);
+        }
+    }
+    if (!ok) {
+        bar_wait(bar, phase ^ 1u);
+        if (tid == 0) atomicOr(flags, kFlagTimeout);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem) : "memory");
+}
+
+template <int MODE>
+npcg_status launch_bwd_tc(Handle* h, const MlpBwdArgs& a, const float* agg_in, int* flags) {
+    if (a.f.nrows == 0) return NPCG_OK;
+    const BtPlan p = bt_plan(mode_in(MODE, kH), a.f.depth, MODE == MODE_DEC);
+    const size_t smem = p.total + 1024;
+    if (smem > 227 * 1024) return set_error(h, NPCG_EINVAL, "MLP too deep for the tensor-core backward");
+    NPCG_CUDA(h, cudaFuncSetAttribute(k_mlp_bwd_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int per_sm = std::max(1, std::min(2, (int)((227 * 1024) / (smem + 1024))));
+    const int64_t ntiles = (a.f.nrows + kM - 1) / kM;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)h->num_sms * per_sm));
+    k_mlp_bwd_tc<MODE><<<grid, kThreads, smem, h->stream>>>(a, agg_in, flags);
+    NPCG_CUDA(h, cudaGetLastError());
+    return NPCG_OK;
+}
+
 // ------------------------------------------------------------ weight gradients
 // dW[o][q] += sum_k G[k][o] X[k][q], db[o] += sum_k G[k][o]; X's columns come
 // in segments, each a row-gather of a [rows x width] array (idx may be null).
@@ -289,6 +555,8 @@ struct WgradArgs {
     int nseg;
     int I;
     float* dW;      // [O][I] then db[O]
+    int bf16;       // BF16 tensor-core path allowed
+    int* flags;     // device status word (tensor-core path)
 };
 
 constexpr int kWgRows = 32;
@@ -348,8 +616,212 @@ __global__ void __launch_bounds__(256) k_wgrad(WgradArgs a) {
     if (threadIdx.x < a.O && bacc != 0.0f) atomicAdd(&a.dW[E + threadIdx.x], bacc);
 }
 
+// ---- weight gradients on the tensor cores (BF16 operands, FP32 accumulate)
+// dW^T = X^T G over the rows: one CTA per slice of the rows; per 128-row
+// tile the FP32 tapes are read with coalesced float4 loads into a row-major
+// BF16 staging area, transposed into the K-major swizzled operands
+// (A = X^T: 128 q-rows per M-tile, B = G^T: 64 o-rows; K = the tile's rows)
+// and multiplied into tensor memory.  Row q = I of A holds ones, so the
+// bias gradient sum_r G[r][o] comes out of the same product.  The CTA's
+// partial dW is added to the FP32 gradient at the end.
+constexpr int kWtRows = 128;                 // rows (K) per tile
+constexpr int kWtIMax = 192;                 // input width
+constexpr int kWtLd = kWtIMax + 8;           // staging row stride (BF16)
+struct WtPlan {
+    uint32_t a, b, xs, gs, misc, total;
+};
+__host__ __device__ inline WtPlan wt_plan() {
+    WtPlan p;
+    p.a = 0;                                         // 2 M-tiles x 2 K-blocks x [128 x 64] BF16
+    p.b = p.a + 2 * 2 * kM * 128;                    // 2 K-blocks x [64 x 64] BF16
+    p.xs = p.b + 2 * kH * 128;                       // staging X [128][kWtLd] BF16
+    p.gs = p.xs + kWtRows * kWtLd * 2;               // staging G [128][72] BF16
+    p.misc = p.gs + kWtRows * 72 * 2;
+    p.total = p.misc + 64;
+    return p;
+}
+
+// eight BF16 values a column apart (stride ld) packed into one 16-byte chunk
+__device__ __forceinline__ uint4 gather8(const unsigned short* p, int ld) {
+    uint32_t w[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) w[i] = (uint32_t)p[(2 * i) * ld] | ((uint32_t)p[(2 * i + 1) * ld] << 16);
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+constexpr int kWtThreads = 256;
+
+// 128 rows x 64 FP32 (row r of ptr, or of ptr[idx[r]]) -> row-major BF16
+// staging with row stride ld; eight float4 loads per thread are issued
+// before any is converted
+__device__ __forceinline__ void stage64(const float* ptr, const int32_t* idx, int64_t t0, int rows, int tid,
+                                        __nv_bfloat16* dst, int ld) {
+    float4 v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int t = tid + k * kWtThreads, r = t >> 4, q4 = t & 15;
+        v[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (r < rows) {
+            const int64_t src = idx ? idx[t0 + r] : t0 + r;
+            v[k] = *reinterpret_cast<const float4*>(ptr + src * 64 + q4 * 4);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int t = tid + k * kWtThreads, r = t >> 4, q4 = t & 15;
+        __nv_bfloat162 lo = __floats2bfloat162_rn(v[k].x, v[k].y), hi = __floats2bfloat162_rn(v[k].z, v[k].w);
+        uint2 pk;
+        pk.x = *reinterpret_cast<uint32_t*>(&lo);
+        pk.y = *reinterpret_cast<uint32_t*>(&hi);
+        *reinterpret_cast<uint2*>(dst + r * ld + q4 * 4) = pk;
+    }
+}
+
+__global__ void __launch_bounds__(kWtThreads) k_wgrad_tc(WgradArgs a) {
+    extern __shared__ __align__(1024) unsigned char sm_raw[];
+    unsigned char* sm = sm_raw + ((1024u - (s_addr(sm_raw) & 1023u)) & 1023u);
+    const WtPlan P = wt_plan();
+    unsigned char* Aop = sm + P.a;
+    unsigned char* Bop = sm + P.b;
+    __nv_bfloat16* xs = reinterpret_cast<__nv_bfloat16*>(sm + P.xs);
+    __nv_bfloat16* gs = reinterpret_cast<__nv_bfloat16*>(sm + P.gs);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + P.misc);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + P.misc + 8);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int I = a.I;
+    const int nmt = (I + 1 + kM - 1) / kM;           // M-tiles of q (with the ones row)
+    // A rows past the ones row stay zero
+    for (int t = tid; t < 2 * 2 * kM * 128 / 16; t += kWtThreads)
+        reinterpret_cast<uint4*>(Aop)[t] = make_uint4(0, 0, 0, 0);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_addr(bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(s_addr(tmem_slot))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int64_t per = ((a.M + gridDim.x - 1) / gridDim.x + kWtRows - 1) / kWtRows * kWtRows;
+    const int64_t m0 = blockIdx.x * per, m1 = a.M < m0 + per ? a.M : m0 + per;
+    uint32_t phase = 0;
+    bool ok = true, issued = false;
+    for (int64_t t0 = m0; t0 < m1 && ok; t0 += kWtRows) {
+        const int rows = (int)(m1 - t0 < kWtRows ? m1 - t0 : kWtRows);
+        // ---- stage the tile row-major in BF16 (coalesced float4 loads)
+        {
+            int c0 = 0;
+#pragma unroll
+            for (int sidx = 0; sidx < 3; ++sidx) {
+                if (sidx >= a.nseg) break;
+                const WSeg sg = a.seg[sidx];
+                stage64(sg.ptr, sg.idx, t0, rows, tid, xs + c0, kWtLd);
+                c0 += 64;
+            }
+            stage64(a.G, nullptr, t0, rows, tid, gs, 72);
+        }
+        // ---- the previous tile's products must be done before the operands change
+        if (issued) {
+            ok = bar_wait(bar, phase);
+            phase ^= 1u;
+            if (!__syncthreads_and(ok)) {
+                ok = false;
+                break;
+            }
+        } else {
+            __syncthreads();
+        }
+        // ---- transpose into K-major operands: chunk = 8 consecutive rows of one column
+        for (int t = tid; t < (I + 1) * (kWtRows / 8); t += kWtThreads) {
+            const int q = t % (I + 1), r8 = t / (I + 1);
+            uint4 val;
+            if (q == I) {
+                const uint32_t one2 = 0x3F803F80u;              // two BF16 ones
+                val = make_uint4(one2, one2, one2, one2);
+            } else {
+                val = gather8(reinterpret_cast<const unsigned short*>(xs) + (r8 * 8) * kWtLd + q, kWtLd);
+            }
+            const int mt = q / kM, qq = q % kM, kb = r8 / 8;
+            *reinterpret_cast<uint4*>(Aop + (uint32_t)(mt * 2 + kb) * (kM * 128) + swz(qq, (r8 % 8) * 8)) = val;
+        }
+        for (int t = tid; t < 64 * (kWtRows / 8); t += kWtThreads) {
+            const int o = t % 64, r8 = t / 64;
+            const int kb = r8 / 8;
+            *reinterpret_cast<uint4*>(Bop + (uint32_t)kb * (kH * 128) + swz(o, (r8 % 8) * 8)) =
+                gather8(reinterpret_cast<const unsigned short*>(gs) + (r8 * 8) * 72 + o, 72);
+        }
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (tid == 0) {
+            for (int mt = 0; mt < nmt; ++mt)
+                for (int s = 0; s < kWtRows / 16; ++s) {
+                    const uint32_t kb = (uint32_t)(s >> 2), ko = (uint32_t)(s & 3) * 32;
+                    mma_bf16(tmem + (uint32_t)mt * 64,
+                             smem_desc(s_addr(Aop) + (uint32_t)(mt * 2 + kb) * (kM * 128) + ko),
+                             smem_desc(s_addr(Bop) + kb * (kH * 128) + ko), (t0 > m0 || s > 0) ? 1u : 0u);
+                }
+            mma_commit(bar);
+        }
+        issued = true;
+    }
+    if (issued && ok) {
+        ok = bar_wait(bar, phase);
+        ok = __syncthreads_and(ok);
+        tc_fence_after();
+        if (ok) {
+            // lane quarter of each M-tile: q = mt * 128 + 32 * warp + lane, 64 o columns
+            // warps 0-3 read M-tile 0, warps 4-7 M-tile 1 (lane quarter = warp % 4)
+            const int mt = warp >> 2, wq = warp & 3;
+            if (mt < nmt) {
+                const int q = mt * kM + wq * 32 + (tid & 31);
+                for (int c4 = 0; c4 < 4; ++c4) {
+                    float v[16];
+                    tmem_ld16(tmem + (uint32_t)mt * 64 + ((uint32_t)(wq * 32) << 16) + c4 * 16, v);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const int o = c4 * 16 + i;
+                        if (v[i] == 0.0f) continue;
+                        if (q < I) atomicAdd(&a.dW[o * I + q], v[i]);
+                        else if (q == I) atomicAdd(&a.dW[64 * I + o], v[i]);
+                    }
+                }
+            }
+        }
+    } else if (issued) {
+        bar_wait(bar, phase);        // one more bounded wait for products in flight
+    }
+    if (!ok && tid == 0) atomicOr(a.flags, kFlagTimeout);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem) : "memory");
+}
+
+npcg_status wgrad_tc(Handle* h, const WgradArgs& a) {
+    const size_t smem = wt_plan().total + 1024;
+    NPCG_CUDA(h, cudaFuncSetAttribute(k_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int64_t tiles = (a.M + kWtRows - 1) / kWtRows;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)h->num_sms));
+    k_wgrad_tc<<<grid, kWtThreads, smem, h->stream>>>(a);
+    NPCG_CUDA(h, cudaGetLastError());
+    return NPCG_OK;
+}
+
 npcg_status wgrad(Handle* h, const WgradArgs& a) {
     if (a.M == 0) return NPCG_OK;
+    // tensor cores for the BF16 path when the shape fits the MMA tiles
+    if (a.bf16 && a.O == 64 && (a.I == 64 || a.I == 128 || a.I == 192)) {
+        bool w64 = true;
+        for (int s = 0; s < a.nseg; ++s) w64 = w64 && a.seg[s].width == 64;
+        if (w64) return wgrad_tc(h, a);
+    }
     if (a.O > 64 || a.I > 192 || a.O * a.I > kWgMaxEntries)
         return set_error(h, NPCG_EINVAL, "weight-gradient shape out of range");
     int grid = (int)std::max<int64_t>(1, std::min<int64_t>((a.M + kWgRows - 1) / kWgRows, (int64_t)h->num_sms * 4));
@@ -413,6 +885,8 @@ struct TrainBufs {
     float* tapeA[kMaxDepth + 1];
     float* tapeG[kMaxDepth + 1];
     double *Lv, *dL, *y, *r, *w, *loss_sys;
+    int bf16;          // weight gradients on the tensor cores
+    int* flags;        // device status word
 };
 
 inline int grid1(Handle* h, int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)h->num_sms * 8)); }
@@ -430,6 +904,8 @@ npcg_status mlp_wgrad(Handle* h, int64_t M, int H, int in_w, int out_w, int dept
     }
     for (int l = depth; l >= 0; --l) {
         WgradArgs a{};
+        a.bf16 = T.bf16;
+        a.flags = T.flags;
         a.M = M;
         a.G = l == depth ? gout : T.tapeG[l];
         a.O = l == depth ? out_w : H;
@@ -446,6 +922,20 @@ npcg_status mlp_wgrad(Handle* h, int64_t M, int H, int in_w, int out_w, int dept
         NPCG_TRY(wgrad(h, a));
     }
     return NPCG_OK;
+}
+
+// MLP backward: tensor cores on the BF16 path (h = 64, node / edge / decoder),
+// FP32 CUDA cores otherwise
+template <int H>
+npcg_status run_bwd(Handle* h, int mode, const MlpBwdArgs& bw, const float* agg_in, const TrainBufs& T) {
+    if constexpr (H == 64) {
+        if (T.bf16) {
+            if (mode == MODE_EDGE) return launch_bwd_tc<MODE_EDGE>(h, bw, agg_in, T.flags);
+            if (mode == MODE_NODE) return launch_bwd_tc<MODE_NODE>(h, bw, agg_in, T.flags);
+            if (mode == MODE_DEC) return launch_bwd_tc<MODE_DEC>(h, bw, agg_in, T.flags);
+        }
+    }
+    return launch_bwd<H>(h, mode, bw);
 }
 
 template <int H>
@@ -506,7 +996,7 @@ npcg_status train_pair(Handle* h, Pattern* P, const double* A_val, const double*
     bw.f.nrows = nnz; bw.f.w = w + off.dec; bw.f.depth = l; bw.f.ein = T.E[nmp];
     bw.gout = T.dS;
     bw.dx[0] = T.dEc; bw.dx[1] = bw.dx[2] = nullptr;
-    NPCG_TRY(launch_bwd<H>(h, MODE_DEC, bw));
+    NPCG_TRY(run_bwd<H>(h, MODE_DEC, bw, nullptr, T));
     {
         WSeg s0{T.E[nmp], nullptr, H};
         NPCG_TRY(mlp_wgrad(h, nnz, H, H, 1, l, T.dS, T, &s0, 1, gw + off.dec));
@@ -518,7 +1008,7 @@ npcg_status train_pair(Handle* h, Pattern* P, const double* A_val, const double*
         bw.f.nrows = nnz; bw.f.w = w + off.edge[t]; bw.f.depth = lm; bw.f.vin = T.V[t + 1]; bw.f.ein = T.E[t];
         bw.gout = T.dEc;
         bw.dx[0] = T.dEp; bw.dx[1] = T.Gr; bw.dx[2] = T.Gc;
-        NPCG_TRY(launch_bwd<H>(h, MODE_EDGE, bw));
+        NPCG_TRY(run_bwd<H>(h, MODE_EDGE, bw, nullptr, T));
         {
             WSeg s[3] = {{T.E[t], nullptr, H}, {T.V[t + 1], P->edge_row.p, H}, {T.V[t + 1], P->ci.p, H}};
             NPCG_TRY(mlp_wgrad(h, nnz, H, 3 * H, H, lm, T.dEc, T, s, 3, gw + off.edge[t]));
@@ -529,7 +1019,7 @@ npcg_status train_pair(Handle* h, Pattern* P, const double* A_val, const double*
         bw.f.nrows = n; bw.f.w = w + off.node[t]; bw.f.depth = lm; bw.f.vin = T.V[t]; bw.f.ein = T.E[t];
         bw.gout = T.dVc;
         bw.dx[0] = T.dVp; bw.dx[1] = T.dAgg; bw.dx[2] = nullptr;
-        NPCG_TRY(launch_bwd<H>(h, MODE_NODE, bw));
+        NPCG_TRY(run_bwd<H>(h, MODE_NODE, bw, T.AGG[t], T));
         {
             WSeg s[2] = {{T.V[t], nullptr, H}, {T.AGG[t], nullptr, H}};
             NPCG_TRY(mlp_wgrad(h, n, H, 2 * H, H, lm, T.dVc, T, s, 2, gw + off.node[t]));
@@ -558,6 +1048,8 @@ npcg_status train_pair(Handle* h, Pattern* P, const double* A_val, const double*
         WSeg s0{T.xe, nullptr, 1};
         NPCG_TRY(mlp_wgrad(h, nnz, H, 1, H, l, T.dEc, T, &s0, 1, gw + off.enc_e));
     }
+    // tensor-core waits of this pair (the next pair's forward clears the word)
+    if (T.bf16) NPCG_TRY(gnn_bf16_check_flags(h, P));
     return NPCG_OK;
 }
 
@@ -591,15 +1083,17 @@ npcg_status loss_grad_run(Handle* h, Pattern* P, const double* A_val, int npairs
     GnnStore& S = P->gnn;
     const size_t fe = (size_t)nnz * H, fv = (size_t)n * H;
     // tape: V_0..V_nmp, E_0..E_nmp, AGG_0..AGG_{nmp-1}; adjoint buffers
-    const size_t need = (size_t)(nmp + 1) * (fe + fv) + (size_t)std::max(nmp, 1) * fv + 4 * fe + 5 * fv +
-                        2 * (size_t)nnz + (size_t)(2 * dmax + 2) * std::max(fe, fv) + 2 * (size_t)nnz;
+    // every buffer starts on a 256-byte boundary (vector loads of the tapes)
+    auto al64 = [](size_t k) { return (k + 63) & ~size_t(63); };
+    const size_t need = (size_t)(nmp + 1) * (al64(fe) + al64(fv)) + (size_t)std::max(nmp, 1) * al64(fv) +
+                        4 * al64(fe) + 5 * al64(fv) + 4 * al64(nnz) + (size_t)(2 * dmax + 2) * al64(std::max(fe, fv));
     NPCG_CUDA(h, S.aux.ensure(need));
     NPCG_CUDA(h, S.sc.ensure((size_t)2 * P->nsys));
     NPCG_CUDA(h, S.Lv.ensure((size_t)nnzL));
     NPCG_CUDA(h, S.dL.ensure((size_t)nnzL + 3 * (size_t)n + P->nsys));
     TrainBufs T;
     float* p = S.aux.p;
-    auto take = [&](size_t k) { float* r = p; p += k; return r; };
+    auto take = [&](size_t k) { float* r = p; p += al64(k); return r; };
     for (int t = 0; t <= nmp; ++t) T.V.push_back(take(fv));
     for (int t = 0; t <= nmp; ++t) T.E.push_back(take(fe));
     for (int t = 0; t < std::max(nmp, 1); ++t) T.AGG.push_back(take(fv));
@@ -608,6 +1102,8 @@ npcg_status loss_grad_run(Handle* h, Pattern* P, const double* A_val, int npairs
     T.S = take(nnz); T.dS = take(nnz);
     for (int k = 0; k <= kMaxDepth; ++k) { T.tapeA[k] = nullptr; T.tapeG[k] = nullptr; }
     for (int k = 0; k <= dmax; ++k) { T.tapeA[k] = take(std::max(fe, fv)); T.tapeG[k] = take(std::max(fe, fv)); }
+    T.bf16 = cfg->precision == NPCG_BF16;
+    T.flags = P->ctl.p + 1;
     T.Lv = S.Lv.p;
     T.dL = S.dL.p;
     T.y = T.dL + nnzL;
@@ -632,6 +1128,7 @@ npcg_status loss_grad_run(Handle* h, Pattern* P, const double* A_val, int npairs
     std::vector<double> ls(P->nsys);
     NPCG_CUDA(h, cudaMemcpyAsync(ls.data(), T.loss_sys, P->nsys * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     NPCG_CUDA(h, cudaStreamSynchronize(h->stream));
+
     double tot = 0.0;
     for (double v : ls) tot += v;
     *loss_out = tot / ((double)npairs * (double)P->nsys);
