@@ -107,6 +107,16 @@ def _dist():
     return rank, world, local
 
 
+# the network trained for each workload's family (the paper trains one per
+# task); the mixed 2-D / 3-D network serves the uneven batch and is the fallback
+TASK_WEIGHTS = {"fem2d_256": "gnn_6x64_fem2d.npy", "fd3d_128": "gnn_6x64_fd3d.npy", "batched_256": "gnn_6x64.npy"}
+
+
+def weights_for(workload):
+    p = os.path.join(WEIGHTS_DIR, TASK_WEIGHTS.get(workload, "gnn_6x64.npy"))
+    return p if os.path.exists(p) else os.path.join(WEIGHTS_DIR, "gnn_6x64.npy")
+
+
 def _load_weights(cfg, path):
     from paper_2305_16432_gb300 import inputs as I
     if path and os.path.exists(path):
@@ -222,7 +232,7 @@ def run_reference(args):
         return
     prob = I.fem2d_256(seed=0)
     cfg = I.GnnConfig(n_mp=6, l=2, l_mp=2, h=64)
-    w, kind, meta = _load_weights(cfg, os.path.join(WEIGHTS_DIR, "gnn_6x64.npy"))
+    w, kind, meta = _load_weights(cfg, weights_for("fem2d_256"))
     if meta.get("config"):
         cfg = I.GnnConfig(**meta["config"])
     Ao = O.assemble(prob)
@@ -498,11 +508,13 @@ def main():
                     help="network arithmetic: BF16 tensor cores (default) or FP32")
     ap.add_argument("--apply", default="fp32", choices=["fp32", "fp64"],
                     help="arithmetic of the L L^T solves inside the FP64 PCG")
-    ap.add_argument("--weights", default=os.path.join(WEIGHTS_DIR, "gnn_6x64.npy"))
+    ap.add_argument("--weights", default=None, help="network weights (.npy); default: the workload's own")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--trsv-reps", type=int, default=50)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.weights is None:
+        args.weights = weights_for(args.workload)
     if args.impl == "reference":
         run_reference(args)
         return

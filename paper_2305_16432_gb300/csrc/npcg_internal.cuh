@@ -108,6 +108,8 @@ struct alignas(16) CtaChunk {
 struct CtaLayout {
     bool built = false;
     bool window_ok = false;        // every dependency within the shared window
+    bool blocked = false;          // one large system in per-SM row blocks (remote dependencies)
+    int nunits = 0;                // CTAs of a solve: systems, or row blocks
     int win_slots = 0;             // window size (power of two) when window_ok
     int nsteps = 0, max_w = 0, max_np = 0;
     int64_t sbuf_len = 0, vbuf_len = 0;
@@ -256,7 +258,8 @@ npcg_status cta_factor_load(Handle* h, CtaLayout* C, const double* L_val);
 npcg_status cta_gather(Handle* h, cudaStream_t s, const CtaLayout& C, int64_t n, const double* x, void* xp,
                        bool f32);
 npcg_status cta_trsv_launch(Handle* h, cudaStream_t s, Pattern* P, const CtaLayout& C, const void* rhs_perm,
-                            void* outq, const SysState* st, bool f32);
+                            void* outq, const SysState* st, bool f32, int* ticket = nullptr,
+                            double* pub = nullptr);
 npcg_status cta_permute(Handle* h, cudaStream_t s, Pattern* P, const CtaLayout& C, void* outq, bool f32,
                         const int32_t* idx, void* dst, bool dst_f32);
 npcg_status trsv_autotune(Handle* h, Pattern* P);

@@ -559,10 +559,18 @@ PcgArgs pcg_args(Pattern* P, int precond) {
 // z = L^-T L^-1 r with the tuned triangular-solve design
 void apply_llt(Handle* h, cudaStream_t s, Pattern* P, bool batched, bool f32) {
     if (P->trsv_mode == kTrsvCta) {
-        cta_trsv_launch(h, s, P, P->cfwd, P->r_cf.p, P->yq.p, P->st.p, f32);
-        cta_permute(h, s, P, P->cfwd, P->yq.p, f32, P->cbwd.other.p, P->y_cb.p, f32);
-        cta_trsv_launch(h, s, P, P->cbwd, P->y_cb.p, P->yq.p, P->st.p, f32);
-        cta_permute(h, s, P, P->cbwd, P->yq.p, f32, P->cbwd.cpos.p, P->z.p, false);
+        if (P->cfwd.blocked) {
+            // row blocks publish to y and z (natural order; the update kernel
+            // resets them to the sentinel and the tickets to zero every iteration)
+            cta_trsv_launch(h, s, P, P->cfwd, P->r_cf.p, P->yq.p, P->st.p, f32, P->ctl.p + 2, P->y.p);
+            cta_permute(h, s, P, P->cfwd, P->yq.p, f32, P->cbwd.other.p, P->y_cb.p, f32);
+            cta_trsv_launch(h, s, P, P->cbwd, P->y_cb.p, P->yq.p, P->st.p, f32, P->ctl.p + 3, P->z.p);
+        } else {
+            cta_trsv_launch(h, s, P, P->cfwd, P->r_cf.p, P->yq.p, P->st.p, f32);
+            cta_permute(h, s, P, P->cfwd, P->yq.p, f32, P->cbwd.other.p, P->y_cb.p, f32);
+            cta_trsv_launch(h, s, P, P->cbwd, P->y_cb.p, P->yq.p, P->st.p, f32);
+            cta_permute(h, s, P, P->cbwd, P->yq.p, f32, P->cbwd.cpos.p, P->z.p, false);
+        }
     } else {
         launch_trsv(h, s, P, 0, P->r.p, P->y.p, P->ctl.p + 2, batched, P->st.p, f32);
         launch_trsv(h, s, P, 1, P->y.p, P->z.p, P->ctl.p + 3, batched, P->st.p, f32);
@@ -642,7 +650,9 @@ npcg_status sptrsv_run(Handle* h, Pattern* P, int transpose, const double* r, do
         NPCG_TRY(ensure_pcg_workspace(h, P));
         const CtaLayout& C = transpose ? P->cbwd : P->cfwd;
         NPCG_TRY(cta_gather(h, h->stream, C, P->n, r, P->r_cf.p, false));
-        NPCG_TRY(cta_trsv_launch(h, h->stream, P, C, P->r_cf.p, P->yq.p, nullptr, false));
+        if (C.blocked) k_fill_sentinel<<<h->num_sms * 4, 256, 0, h->stream>>>(P->n, P->y.p);
+        NPCG_TRY(cta_trsv_launch(h, h->stream, P, C, P->r_cf.p, P->yq.p, nullptr, false,
+                                 P->ctl.p + 2 + (transpose ? 1 : 0), P->y.p));
         return cta_permute(h, h->stream, P, C, P->yq.p, false, C.cpos.p, y, false);
     }
     k_fill_sentinel<<<h->num_sms * 4, 256, 0, h->stream>>>(P->n, y);
@@ -664,8 +674,10 @@ npcg_status sptrsv_timed_run(Handle* h, Pattern* P, int transpose, const double*
         if (P->trsv_mode == kTrsvCta) {
             const CtaLayout& C = transpose ? P->cbwd : P->cfwd;
             cta_gather(h, h->stream, C, P->n, r, P->r_cf.p, f32);
+            if (C.blocked) k_fill_sentinel<<<h->num_sms * 4, 256, 0, h->stream>>>(P->n, P->y.p);
             cudaEventRecord(e0, h->stream);
-            cta_trsv_launch(h, h->stream, P, C, P->r_cf.p, P->yq.p, nullptr, f32);
+            cta_trsv_launch(h, h->stream, P, C, P->r_cf.p, P->yq.p, nullptr, f32, P->ctl.p + 2 + (transpose ? 1 : 0),
+                            P->y.p);
             cudaEventRecord(e1, h->stream);
             cta_permute(h, h->stream, P, C, P->yq.p, f32, C.cpos.p, y, false);
         } else {

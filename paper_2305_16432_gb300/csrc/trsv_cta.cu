@@ -35,6 +35,7 @@ constexpr long long kMbarSpin = 1LL << 22;
 constexpr int kHdrInts = 4;              // {q0, nrows, width, pad} heads every structure block
 constexpr int kRec = 4;                  // dependencies held in a row's packed record
 constexpr int kWinPad = 32;              // window slots past the window; the first stays zero
+constexpr int64_t kBlockedRows = 1 << 18;  // one system this large is split into per-SM row blocks
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -100,13 +101,14 @@ __host__ __device__ constexpr int rhs_align() { return 16 / (int)sizeof(T); }
 
 // barrier + mbarrier area at the start of shared memory: full[8], empty[8],
 // and per stage the chunk's {nsteps, value offset, rhs offset, q0e}
-constexpr int kBarBytes = 256;
+constexpr int kBarBytes = 512;           // + the claimed unit (blocked layouts) at byte 256
 
 // operands of one row of one step, held in registers by its consumer thread
 template <class T>
 struct StepOps {
     int q0, nrows, width, np;
     int4 dep;
+    int row;
     T l[4];
     T rhs, dinv;
 };
@@ -120,7 +122,7 @@ __device__ __forceinline__ void ld_vec4(double (&l)[4], const double* p) {
     l[0] = a.x; l[1] = a.y; l[2] = b.x; l[3] = b.y;
 }
 
-template <class T>
+template <bool kRow, class T>
 __device__ __forceinline__ void load_step(StepOps<T>& o, const int32_t* hdr, const T* vals, const T* rh, int q0e,
                                           int t) {
     const int4 h = *reinterpret_cast<const int4*>(hdr);
@@ -130,6 +132,7 @@ __device__ __forceinline__ void load_step(StepOps<T>& o, const int32_t* hdr, con
     o.np = pad4(h.y);
     if (t < o.nrows) {
         o.dep = reinterpret_cast<const int4*>(hdr + kHdrInts)[t];
+        if (kRow) o.row = reinterpret_cast<const int2*>(hdr + kHdrInts + 4 * o.np)[t].x;
         ld_vec4(o.l, vals + 4 * t);
         o.dinv = vals[4 * o.np + t];
         o.rhs = rh[o.q0 - q0e + t];
@@ -148,13 +151,43 @@ __device__ __forceinline__ bool consumers_agree(bool ok) {
     return all_ok != 0;
 }
 
-template <bool kWindow, class T>
+// value of a dependency on a row of an earlier unit (blocked layouts): the
+// unit that owns it publishes it to pub (FP64, sentinel until written)
+__device__ __forceinline__ double remote_dep(const double* pub, int row, int* flags) {
+    long long spins = 0;
+    unsigned long long bits;
+    while ((bits = ld_relaxed_u64(pub + row)) == kSentinelBits) {
+        // a solve that already gave up does not wait again
+        if ((++spins & 255) == 0 && (ld_relaxed_s32(flags) & kFlagAbort)) return 0.0;
+        if (spins > kSpinLimit) {
+            atomicOr(flags, kFlagTimeout | kFlagAbort);
+            return 0.0;
+        }
+    }
+    return __longlong_as_double((long long)bits);
+}
+
+// kRemote: blocked layout of one large system.  CTAs claim units (contiguous
+// row blocks) in dependency order from a ticket, so every unit a CTA polls
+// on is owned by a CTA that is already running; dependencies outside the
+// unit are encoded -(row + 2) and read from pub, and every row's value is
+// published there.
+template <bool kWindow, bool kRemote, class T>
 __global__ void __launch_bounds__(kCtaThreads, 1) k_trsv_cta(CtaDev D, const T* __restrict__ rhs,
                                                          T* outq, double* yglob,
-                                                         const SysState* st, int* flags) {
+                                                         const SysState* st, int* flags,
+                                                         int* ticket, double* pub) {
     extern __shared__ __align__(128) unsigned char smem[];
-    const int sys = blockIdx.x;
-    if (st && !st[sys].active) return;
+    int sys = blockIdx.x;
+    if (kRemote) {
+        int* s_unit = reinterpret_cast<int*>(smem + 256);
+        if (threadIdx.x == 0) *s_unit = atomicAdd(ticket, 1);
+        __syncthreads();
+        sys = *s_unit;
+        if (st && !st[0].active) return;
+    } else if (st && !st[sys].active) {
+        return;
+    }
     const int c0 = D.sys_chunk0[sys], c1 = D.sys_chunk0[sys + 1];
     if (c0 >= c1) return;
     const int S = D.stages;
@@ -248,7 +281,7 @@ __global__ void __launch_bounds__(kCtaThreads, 1) k_trsv_cta(CtaDev D, const T* 
         vals = reinterpret_cast<const T*>(ring + inf.y);
         rh = reinterpret_cast<const T*>(ring + inf.z);
         q0e = inf.w;
-        load_step(cur, hdr, vals, rh, q0e, t);
+        load_step<kRemote>(cur, hdr, vals, rh, q0e, t);
     }
     for (;;) {
         // locate and load the next step
@@ -277,11 +310,11 @@ __global__ void __launch_bounds__(kCtaThreads, 1) k_trsv_cta(CtaDev D, const T* 
         } else {
             has_next = false;
         }
-        if (has_next && ok) load_step(nxt, hdr, vals, rh, q0e, t);
+        if (has_next && ok) load_step<kRemote>(nxt, hdr, vals, rh, q0e, t);
         // the current step
         if (t < cur.nrows) {
             T acc = cur.rhs;
-            if (kWindow) {
+            if (kWindow && !kRemote) {
                 // missing dependencies read the zero slot with a zero value
                 const T y0 = win[cur.dep.x], y1 = win[cur.dep.y], y2 = win[cur.dep.z], y3 = win[cur.dep.w];
                 acc = fma(-cur.l[0], y0, acc);
@@ -291,15 +324,20 @@ __global__ void __launch_bounds__(kCtaThreads, 1) k_trsv_cta(CtaDev D, const T* 
             } else {
                 const int pd[4] = {cur.dep.x, cur.dep.y, cur.dep.z, cur.dep.w};
 #pragma unroll
-                for (int kk = 0; kk < 4; ++kk)
-                    if (pd[kk] >= 0) acc = fma(-cur.l[kk], (T)__ldcg(yglob + pd[kk]), acc);
+                for (int kk = 0; kk < 4; ++kk) {
+                    const int p = pd[kk];
+                    if (kRemote && p <= -2) acc = fma(-cur.l[kk], (T)remote_dep(pub, -p - 2, flags), acc);
+                    else if (kWindow) acc = fma(-cur.l[kk], win[p], acc);
+                    else if (p >= 0) acc = fma(-cur.l[kk], (T)__ldcg(yglob + p), acc);
+                }
             }
             if (cur.width > kRec) {
                 const int32_t* xdep = chdr + kHdrInts + 6 * cur.np;
                 const T* xval = cvals + 5 * cur.np;
                 for (int kk = 0; kk < cur.width - kRec; ++kk) {
                     const int pk = xdep[kk * cur.np + t];
-                    if (kWindow) acc = fma(-xval[kk * cur.np + t], win[pk], acc);
+                    if (kRemote && pk <= -2) acc = fma(-xval[kk * cur.np + t], (T)remote_dep(pub, -pk - 2, flags), acc);
+                    else if (kWindow) acc = fma(-xval[kk * cur.np + t], win[pk], acc);
                     else if (pk >= 0) acc = fma(-xval[kk * cur.np + t], (T)__ldcg(yglob + pk), acc);
                 }
             }
@@ -313,6 +351,7 @@ __global__ void __launch_bounds__(kCtaThreads, 1) k_trsv_cta(CtaDev D, const T* 
             } else {
                 yglob[q] = (double)y;
             }
+            if (kRemote) st_relaxed_u64(pub + cur.row, (unsigned long long)__double_as_longlong((double)y));
         }
         if (!kWindow) __threadfence_block();
         // this step's solutions are visible to the next step; a next chunk
@@ -398,6 +437,25 @@ __global__ void k_cta_reach(int64_t n, const int32_t* step_of_pos, const int4* s
     }
 }
 
+// blocked layouts: a dependency outside the row's unit becomes -(row + 2)
+__global__ void k_cta_remote(int64_t n, const int32_t* step_of_pos, const int4* steps, const int2* step_unit,
+                             const int64_t* soff, const int32_t* cperm, int32_t* sbuf) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int stp = step_of_pos[q];
+        const int4 d = steps[stp];
+        const int2 u = step_unit[stp];
+        const int np = pad4(d.y);
+        const int t = (int)(q - d.x);
+        int32_t* body = sbuf + soff[stp] + kHdrInts;
+        const int kmax = d.z > kRec ? d.z : kRec;
+        for (int k = 0; k < kmax; ++k) {
+            int32_t* p = dep_slot(body, np, t, k);
+            if (*p >= 0 && (*p < u.x || *p >= u.y)) *p = -(cperm[*p] + 2);
+        }
+    }
+}
+
 // the window suffices: dependency positions become window slots
 __global__ void k_cta_window(int64_t n, const int32_t* step_of_pos, const int4* steps, const int64_t* soff,
                              int W, int32_t* sbuf) {
@@ -411,7 +469,8 @@ __global__ void k_cta_window(int64_t n, const int32_t* step_of_pos, const int4* 
         const int kmax = d.z > kRec ? d.z : kRec;
         for (int k = 0; k < kmax; ++k) {
             int32_t* p = dep_slot(body, np, t, k);
-            *p = *p >= 0 ? (*p & (W - 1)) : W;
+            if (*p >= 0) *p &= W - 1;
+            else if (*p == -1) *p = W;              // missing: the zero slot; <= -2 (remote) stays
         }
     }
 }
@@ -541,17 +600,32 @@ npcg_status cta_layout_build(Handle* h, Pattern* P, bool upper, CtaLayout* C) {
     NPCG_CUDA(h, cudaMemcpyAsync(rp_h.data(), P->rp.p, (n + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
     NPCG_CUDA(h, cudaMemcpyAsync(Lrp_h.data(), P->Lrp.p, (n + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
     NPCG_CUDA(h, cudaStreamSynchronize(h->stream));
-    std::vector<int32_t> cperm(n), cpos(n), step_of_pos(n), sys_step0(P->nsys + 1, 0), level_end;
+    // units: one per system, or (one large system) contiguous row blocks,
+    // one per SM, listed in dependency order (the backward solve runs from
+    // the last row, so its blocks come last-first)
+    std::vector<std::pair<int64_t, int64_t>> units;
+    C->blocked = P->nsys == 1 && n >= kBlockedRows;
+    if (C->blocked) {
+        const int64_t B = (n + h->num_sms - 1) / h->num_sms;
+        for (int64_t r0 = 0; r0 < n; r0 += B) units.push_back({r0, std::min<int64_t>(n, r0 + B)});
+        if (upper) std::reverse(units.begin(), units.end());
+    } else {
+        for (int s = 0; s < P->nsys; ++s) units.push_back({P->sys_ptr_h[s], P->sys_ptr_h[s + 1]});
+    }
+    const int nunits = (int)units.size();
+    C->nunits = nunits;
+    std::vector<int32_t> cperm(n), cpos(n), step_of_pos(n), sys_step0(nunits + 1, 0), level_end;
     std::vector<int4> steps;
+    std::vector<int2> step_unit;                   // processing-position range of each step's unit
     auto offdiag = [&](int row) {
         int nl = Lrp_h[row + 1] - Lrp_h[row];
         return upper ? (rp_h[row + 1] - rp_h[row]) - nl : nl - 1;
     };
     int64_t q = 0;
     int maxw = 0, maxnp = 0;
-    for (int s = 0; s < P->nsys; ++s) {
+    for (int s = 0; s < nunits; ++s) {
         sys_step0[s] = (int32_t)steps.size();
-        const int64_t r0 = P->sys_ptr_h[s], r1 = P->sys_ptr_h[s + 1];
+        const int64_t r0 = units[s].first, r1 = units[s].second;
         int nl = 0;
         for (int64_t r = r0; r < r1; ++r) nl = std::max(nl, lev[r] + 1);
         std::vector<int64_t> cnt(nl + 1, 0);
@@ -567,6 +641,7 @@ npcg_status cta_layout_build(Handle* h, Pattern* P, bool upper, CtaLayout* C) {
                 for (int64_t p = c0; p < c1; ++p) w = std::max(w, offdiag(cperm[p]));
                 const int sid = (int)steps.size();
                 steps.push_back(make_int4((int)c0, (int)(c1 - c0), w, 0));
+                step_unit.push_back(make_int2((int)q, (int)(q + (r1 - r0))));
                 level_end.push_back((int32_t)b);
                 for (int64_t p = c0; p < c1; ++p) step_of_pos[p] = sid;
                 maxw = std::max(maxw, w);
@@ -575,7 +650,7 @@ npcg_status cta_layout_build(Handle* h, Pattern* P, bool upper, CtaLayout* C) {
         }
         q += r1 - r0;
     }
-    sys_step0[P->nsys] = (int32_t)steps.size();
+    sys_step0[nunits] = (int32_t)steps.size();
     for (int64_t p = 0; p < n; ++p) cpos[cperm[p]] = (int32_t)p;
     const int nsteps = (int)steps.size();
     std::vector<int64_t> soff(nsteps), voff(nsteps);
@@ -597,7 +672,7 @@ npcg_status cta_layout_build(Handle* h, Pattern* P, bool upper, CtaLayout* C) {
     NPCG_CUDA(h, C->steps.alloc(nsteps));
     NPCG_CUDA(h, C->soff.alloc(nsteps));
     NPCG_CUDA(h, C->voff.alloc(nsteps));
-    NPCG_CUDA(h, C->sys_step0.alloc(P->nsys + 1));
+    NPCG_CUDA(h, C->sys_step0.alloc(nunits + 1));
     NPCG_CUDA(h, C->sbuf.alloc(std::max<int64_t>(so, 4)));
     NPCG_CUDA(h, C->vbuf.alloc(std::max<int64_t>(vo, 4)));
     NPCG_CUDA(h, C->vbuf32.alloc(std::max<int64_t>(vo, 4)));
@@ -611,7 +686,7 @@ npcg_status cta_layout_build(Handle* h, Pattern* P, bool upper, CtaLayout* C) {
     NPCG_CUDA(h, cudaMemcpyAsync(C->steps.p, steps.data(), nsteps * sizeof(int4), cudaMemcpyHostToDevice, h->stream));
     NPCG_CUDA(h, cudaMemcpyAsync(C->soff.p, soff.data(), nsteps * 8, cudaMemcpyHostToDevice, h->stream));
     NPCG_CUDA(h, cudaMemcpyAsync(C->voff.p, voff.data(), nsteps * 8, cudaMemcpyHostToDevice, h->stream));
-    NPCG_CUDA(h, cudaMemcpyAsync(C->sys_step0.p, sys_step0.data(), (P->nsys + 1) * 4, cudaMemcpyHostToDevice, h->stream));
+    NPCG_CUDA(h, cudaMemcpyAsync(C->sys_step0.p, sys_step0.data(), (nunits + 1) * 4, cudaMemcpyHostToDevice, h->stream));
     NPCG_CUDA(h, cudaMemcpyAsync(C->step_of_pos.p, step_of_pos.data(), n * 4, cudaMemcpyHostToDevice, h->stream));
     NPCG_CUDA(h, cudaMemcpyAsync(lend.p, level_end.data(), nsteps * 4, cudaMemcpyHostToDevice, h->stream));
     NPCG_CUDA(h, cudaMemsetAsync(C->sbuf.p, 0, C->sbuf.n * 4, h->stream));
@@ -623,6 +698,15 @@ npcg_status cta_layout_build(Handle* h, Pattern* P, bool upper, CtaLayout* C) {
     k_mark_diag<<<std::max(1, std::min(nsteps, h->num_sms * 8)), 256, 0, h->stream>>>(
         nsteps, C->steps.p, C->voff.p, C->is_diag.p, vo);
     NPCG_CUDA(h, cudaGetLastError());
+    if (C->blocked) {
+        DevBuf<int2> su;
+        NPCG_CUDA(h, su.alloc(nsteps));
+        NPCG_CUDA(h, cudaMemcpyAsync(su.p, step_unit.data(), nsteps * sizeof(int2), cudaMemcpyHostToDevice, h->stream));
+        k_cta_remote<<<blocks, 256, 0, h->stream>>>(n, C->step_of_pos.p, C->steps.p, su.p, C->soff.p, C->cperm.p,
+                                                    C->sbuf.p);
+        NPCG_CUDA(h, cudaGetLastError());
+        NPCG_CUDA(h, cudaStreamSynchronize(h->stream));
+    }
     DevBuf<unsigned long long> reach;
     NPCG_CUDA(h, reach.alloc(1));
     NPCG_CUDA(h, cudaMemsetAsync(reach.p, 0, 8, h->stream));
@@ -652,7 +736,7 @@ npcg_status cta_layout_build(Handle* h, Pattern* P, bool upper, CtaLayout* C) {
             const size_t rb = (size_t)(((steps[i].x + steps[i].y - q0e) + al - 1) & ~(al - 1)) * vsz;
             single = std::max(single, (size_t)s_ints(np, steps[i].z) * 4 + (size_t)v_elems(np, steps[i].z) * vsz + rb);
         }
-        const size_t budget = P->nsys > h->num_sms ? kSmemHalf : kSmemMax;
+        const size_t budget = nunits > h->num_sms ? kSmemHalf : kSmemMax;
         const size_t avail = budget - kBarBytes - win_bytes(*C, f32 != 0);
         size_t cap = std::max(single, avail / kMaxStages);
         cap = (cap + 127) & ~size_t(127);
@@ -662,23 +746,27 @@ npcg_status cta_layout_build(Handle* h, Pattern* P, bool upper, CtaLayout* C) {
         C->nchunks[f32] = 0;
         std::vector<CtaChunk> ch;
         std::vector<int32_t> sc0;
-        if (stages < 2 || !build_chunks(steps, soff, voff, sys_step0, (int)P->nsys, vsz, cap, ch, sc0)) continue;
+        if (stages < 2 || !build_chunks(steps, soff, voff, sys_step0, nunits, vsz, cap, ch, sc0)) continue;
         C->nstages[f32] = stages;
         C->nchunks[f32] = (int)ch.size();
         NPCG_CUDA(h, C->chunks[f32].alloc(std::max<size_t>(ch.size(), 1)));
-        NPCG_CUDA(h, C->sys_chunk0[f32].alloc(P->nsys + 1));
+        NPCG_CUDA(h, C->sys_chunk0[f32].alloc(nunits + 1));
         NPCG_CUDA(h, cudaMemcpyAsync(C->chunks[f32].p, ch.data(), ch.size() * sizeof(CtaChunk),
                                      cudaMemcpyHostToDevice, h->stream));
-        NPCG_CUDA(h, cudaMemcpyAsync(C->sys_chunk0[f32].p, sc0.data(), (P->nsys + 1) * sizeof(int32_t),
+        NPCG_CUDA(h, cudaMemcpyAsync(C->sys_chunk0[f32].p, sc0.data(), (nunits + 1) * sizeof(int32_t),
                                      cudaMemcpyHostToDevice, h->stream));
         NPCG_CUDA(h, cudaStreamSynchronize(h->stream));
     }
     // the launch size never exceeds 220 KB; set once here, outside any capture
     const int mx = 220 * 1024;
-    NPCG_CUDA(h, cudaFuncSetAttribute(k_trsv_cta<true, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-    NPCG_CUDA(h, cudaFuncSetAttribute(k_trsv_cta<false, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-    NPCG_CUDA(h, cudaFuncSetAttribute(k_trsv_cta<true, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-    NPCG_CUDA(h, cudaFuncSetAttribute(k_trsv_cta<false, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    NPCG_CUDA(h, cudaFuncSetAttribute(k_trsv_cta<true, false, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    NPCG_CUDA(h, cudaFuncSetAttribute(k_trsv_cta<false, false, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    NPCG_CUDA(h, cudaFuncSetAttribute(k_trsv_cta<true, false, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    NPCG_CUDA(h, cudaFuncSetAttribute(k_trsv_cta<false, false, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    NPCG_CUDA(h, cudaFuncSetAttribute(k_trsv_cta<true, true, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    NPCG_CUDA(h, cudaFuncSetAttribute(k_trsv_cta<false, true, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    NPCG_CUDA(h, cudaFuncSetAttribute(k_trsv_cta<true, true, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    NPCG_CUDA(h, cudaFuncSetAttribute(k_trsv_cta<false, true, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
     NPCG_CUDA(h, cudaStreamSynchronize(h->stream));
     C->built = true;
     return NPCG_OK;
@@ -750,9 +838,10 @@ npcg_status cta_gather(Handle* h, cudaStream_t s, const CtaLayout& C, int64_t n,
 // window suffices, otherwise the solution is in P->yglob (FP64); cta_permute
 // moves it on.  f32: FP32 factor, arithmetic, right-hand side and outq.
 npcg_status cta_trsv_launch(Handle* h, cudaStream_t s, Pattern* P, const CtaLayout& C, const void* rhs_v,
-                            void* outq, const SysState* st, bool f32) {
+                            void* outq, const SysState* st, bool f32, int* ticket, double* pub) {
     const int stages = C.nstages[f32];
     if (stages < 2) return set_error(h, NPCG_EINVAL, "level-synchronous layout does not fit shared memory");
+    if (C.blocked && (!ticket || !pub)) return set_error(h, NPCG_EINVAL, "blocked solve needs a ticket and pub");
     CtaDev d;
     d.sys_chunk0 = C.sys_chunk0[f32].p;
     d.chunks = C.chunks[f32].p;
@@ -763,17 +852,20 @@ npcg_status cta_trsv_launch(Handle* h, cudaStream_t s, Pattern* P, const CtaLayo
     d.win = C.win_slots;
     const size_t smem = smem_bytes(C, f32);
     int* flags = P->ctl.p + 1;
+    const int g = C.nunits;
+    double* yg = P->yglob.p;
+#define NPCG_CTA_LAUNCH(W, R, TT)                                                                           \
+    k_trsv_cta<W, R, TT><<<g, kCtaThreads, smem, s>>>(d, static_cast<const TT*>(rhs_v),                      \
+                                                      W ? static_cast<TT*>(outq) : nullptr, W ? nullptr : yg, \
+                                                      st, flags, ticket, pub)
     if (f32) {
-        const float* rp = static_cast<const float*>(rhs_v);
-        float* oq = static_cast<float*>(outq);
-        if (C.window_ok) k_trsv_cta<true, float><<<P->nsys, kCtaThreads, smem, s>>>(d, rp, oq, nullptr, st, flags);
-        else k_trsv_cta<false, float><<<P->nsys, kCtaThreads, smem, s>>>(d, rp, nullptr, P->yglob.p, st, flags);
+        if (C.blocked) { if (C.window_ok) NPCG_CTA_LAUNCH(true, true, float); else NPCG_CTA_LAUNCH(false, true, float); }
+        else { if (C.window_ok) NPCG_CTA_LAUNCH(true, false, float); else NPCG_CTA_LAUNCH(false, false, float); }
     } else {
-        const double* rp = static_cast<const double*>(rhs_v);
-        double* oq = static_cast<double*>(outq);
-        if (C.window_ok) k_trsv_cta<true, double><<<P->nsys, kCtaThreads, smem, s>>>(d, rp, oq, nullptr, st, flags);
-        else k_trsv_cta<false, double><<<P->nsys, kCtaThreads, smem, s>>>(d, rp, nullptr, P->yglob.p, st, flags);
+        if (C.blocked) { if (C.window_ok) NPCG_CTA_LAUNCH(true, true, double); else NPCG_CTA_LAUNCH(false, true, double); }
+        else { if (C.window_ok) NPCG_CTA_LAUNCH(true, false, double); else NPCG_CTA_LAUNCH(false, false, double); }
     }
+#undef NPCG_CTA_LAUNCH
     NPCG_CUDA(h, cudaGetLastError());
     return NPCG_OK;
 }

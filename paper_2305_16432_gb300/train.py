@@ -91,17 +91,19 @@ def save_checkpoint(path, cfg, w, mom, vel, step, hist):
 
 def train(cfg: I.GnnConfig, steps=600, groups=4, per_group=8, pairs=8, m=128, lr=1e-3, lr_final=1e-4,
           seed=2023, log_every=25, w0=None, ckpt=None, resume=None, val_every=50, precision=None, sizes=None,
-          sizes3d=None):
+          sizes3d=None, sigma3d=1.0, corr3d=0.1):
     """Adam at lr (App. A.4), cosine-decayed to lr_final over the run; returns
     the weights with the fewest validation PCG iterations.  precision: the
     network forward's arithmetic (FP32, or BF16 tensor cores with the FP32
     adjoint); sizes: lattice size of each 2-D FEM group (default m for
-    all); sizes3d: grid side of each 3-D FD group (none by default)."""
+    all, [] for none); sizes3d: grid side of each 3-D FD group (none by
+    default), with log k a GRF of sigma3d and correlation length corr3d."""
     from . import build as B
     B.build()
     from . import npcg as N
     prec = N.FP32 if precision is None else precision
-    sizes = sizes or [m] * groups
+    if sizes is None:
+        sizes = [m] * groups
     specs = [("fem", x) for x in sizes] + [("fd3", x) for x in (sizes3d or [])]
     groups = len(specs)
     t0 = time.time()
@@ -110,7 +112,7 @@ def train(cfg: I.GnnConfig, steps=600, groups=4, per_group=8, pairs=8, m=128, lr
         if kind == "fem":
             probs = [I.fem2d(mg, sigma=1.0, corr_len=0.1, seed=seed + 100 * g + k) for k in range(per_group)]
         else:
-            probs = [I.fd3d(mg, sigma=1.0, corr_len=0.1, seed=seed + 100 * g + k) for k in range(per_group)]
+            probs = [I.fd3d(mg, sigma=sigma3d, corr_len=corr3d, seed=seed + 100 * g + k) for k in range(per_group)]
         data.append(make_group(N, probs, pairs, seed + g))
     t_data = time.time() - t0
     w = torch.as_tensor(I.gnn_weights(cfg, seed) if w0 is None else w0, device="cuda")
@@ -129,9 +131,10 @@ def train(cfg: I.GnnConfig, steps=600, groups=4, per_group=8, pairs=8, m=128, lr
     # validation: PCG iterations on held-out systems of the training family;
     # the checkpoint with the fewest mean iterations is kept
     vals = []
-    vprobs = [I.fem2d(m, sigma=1.0, corr_len=0.1, seed=8000 + k) for k in range(2)]
+    vprobs = [I.fem2d(m, sigma=1.0, corr_len=0.1, seed=8000 + k) for k in range(2)] if sizes else []
     if sizes3d:
-        vprobs = [vprobs[0], I.fd3d(sizes3d[len(sizes3d) // 2], sigma=1.0, corr_len=0.1, seed=8000)]
+        v3 = I.fd3d(sizes3d[len(sizes3d) // 2], sigma=sigma3d, corr_len=corr3d, seed=8000)
+        vprobs = [vprobs[0], v3] if vprobs else [v3]
     for k, pv in enumerate(vprobs):
         rp, ci, v = N.assemble_system(pv)
         Pv = N.analyse(rp, ci)
@@ -140,8 +143,9 @@ def train(cfg: I.GnnConfig, steps=600, groups=4, per_group=8, pairs=8, m=128, lr
     def val_iters():
         its = []
         for Pv, v, bv in vals:
+            # the deployed configuration: FP32 triangular solves with a BF16 network
             L = N.gnn_factor(Pv, v, bv, cfg, w, precision=prec)
-            _, st = N.pcg_solve(Pv, v, bv, N.PREC_LLT, L, rtol=1e-6)
+            _, st = N.pcg_solve(Pv, v, bv, N.PREC_LLT32 if prec == N.BF16 else N.PREC_LLT, L, rtol=1e-6)
             its.append(st[0]["iters"] if st[0]["status"] == 0 else 10 * Pv.n)
         return float(np.mean(its))
 
@@ -187,6 +191,8 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
     ap.add_argument("--sizes", default="", help="comma-separated lattice sizes of the 2-D FEM training groups")
     ap.add_argument("--sizes3d", default="", help="comma-separated grid sides of the 3-D FD training groups")
+    ap.add_argument("--sigma3d", type=float, default=1.0, help="GRF sigma of the 3-D groups")
+    ap.add_argument("--corr3d", type=float, default=0.1, help="GRF correlation length of the 3-D groups")
     ap.add_argument("--out", default=os.path.join(os.path.dirname(__file__), "weights", "gnn_6x64.npy"))
     args = ap.parse_args()
     cfg = I.GnnConfig(n_mp=args.n_mp, l=2, l_mp=2, h=args.h, diag_mode=args.diag_mode)
@@ -194,11 +200,11 @@ def main():
     B.build()
     from . import npcg as N
     prec = N.BF16 if args.precision == "bf16" else N.FP32
-    sizes = [int(x) for x in args.sizes.split(",") if x] or None
+    sizes = [] if args.sizes == "none" else ([int(x) for x in args.sizes.split(",") if x] or None)
     sizes3d = [int(x) for x in args.sizes3d.split(",") if x] or None
     w, hist, tm = train(cfg, steps=args.steps, m=args.m, lr=args.lr, lr_final=args.lr_final, ckpt=args.ckpt,
                         resume=args.resume, val_every=args.val_every, precision=prec, sizes=sizes,
-                        sizes3d=sizes3d)
+                        sizes3d=sizes3d, sigma3d=args.sigma3d, corr3d=args.corr3d)
     w0 = torch.as_tensor(I.gnn_weights(cfg, 2023), device="cuda")
     held = [I.fem2d(args.m, sigma=1.0, corr_len=0.1, seed=9000 + k) for k in range(3)]
     ev = evaluate(N, cfg, w, held, precision=prec)
@@ -213,8 +219,9 @@ def main():
             "train": {"steps": args.steps, "lr": args.lr, "lr_final": args.lr_final, "schedule": "cosine",
                       "batch": "8 systems x 2 pairs",
                       "selection": "checkpoint with the fewest validation PCG iterations",
-                      "systems": f"groups of 8: 2-D FEM lattices {sizes or [args.m]}, 3-D FD sides "
-                                 f"{sizes3d or []}, sigma 1, corr 0.1",
+                      "systems": f"groups of 8: 2-D FEM lattices {sizes if sizes is not None else [args.m]} "
+                                 f"(sigma 1, corr 0.1), 3-D FD sides {sizes3d or []} (sigma {args.sigma3d}, "
+                                 f"corr {args.corr3d})",
                       "precision": args.precision, **tm},
             "loss_first": hist[0], "loss_last": float(np.mean(hist[-20:])),
             "heldout_fem128": ev, "untrained_fem128": ev0, "heldout_fem96": small, "fem256_seed0": big,
