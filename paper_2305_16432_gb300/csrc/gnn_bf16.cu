@@ -65,8 +65,8 @@ __host__ __device__ inline SmemPlan plan(int mode, int depth) {
     const uint32_t a0bytes = (uint32_t)(kin0 / 64) * (kM * 128);
     SmemPlan p;
     p.a0 = 0;                                         // [128 x kin0] operand (kin0 / 64 K-blocks)
-    p.a0b = p.a0 + a0bytes;                           // second buffer of the async-gather modes
-    p.a1 = p.a0b + (async_gather(mode) ? a0bytes : 0u);  // [128 x 64] hidden operand
+    p.a0b = p.a0;                                     // (single operand buffer)
+    p.a1 = p.a0 + a0bytes;                            // [128 x 64] hidden operand
     p.w = p.a1 + kM * 128;
     p.bias = p.w + wbytes;                            // FP32 biases of every layer + scalar layer weights
     p.idx = p.bias + (uint32_t)(depth + 1) * kH * 4 + 2 * kH * 4 + 64;
@@ -178,8 +178,6 @@ __global__ void __launch_bounds__(kThreads) k_mlp_bf16(Bf16Args a) {
 
     const int64_t ntiles = (a.nrows + kM - 1) / kM;
     constexpr bool kAsync = async_gather(MODE);
-    unsigned char* const A0a = A0;
-    unsigned char* const A0b = sm + P.a0b;
     int* sidx = reinterpret_cast<int*>(sm + P.idx);      // [2][2][kM]
     int2 nidx = make_int2(0, 0);
     if (kAsync) {
@@ -190,24 +188,18 @@ __global__ void __launch_bounds__(kThreads) k_mlp_bf16(Bf16Args a) {
         sidx[2 * kM + tid] = i1.x;
         sidx[3 * kM + tid] = i1.y;
         __syncthreads();
-        if ((int64_t)blockIdx.x < ntiles) gather_async<MODE>(a, A0a, (int64_t)blockIdx.x * kM, tid, sidx);
+        if constexpr (kAsync)
+            if ((int64_t)blockIdx.x < ntiles) gather_async<MODE>(a, A0, (int64_t)blockIdx.x * kM, tid, sidx);
     }
     int it = 0;
     for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it) {
         const int64_t row0 = tile * kM;
         if (kAsync) {
-            // this tile's operand was requested one tile ago; request the next
-            // one into the other buffer (its last reader, the previous tile's
-            // first MMA, has completed) and wait for this one; the indices of
-            // the tile after next are loaded now and staged at the end
-            A0 = (it & 1) ? A0b : A0a;
-            if (tile + gridDim.x < ntiles) {
-                gather_async<MODE>(a, (it & 1) ? A0a : A0b, (tile + gridDim.x) * kM, tid,
-                                   sidx + ((it + 1) & 1) * 2 * kM);
-                cp_async_wait<1>();
-            } else {
-                cp_async_wait<0>();
-            }
+            // this tile's operand was requested while the previous tile was
+            // still computing (right after its first layer had read the
+            // buffer); the indices of the tile after next are loaded now and
+            // staged at the end
+            cp_async_wait<0>();
             nidx = tile_index(a, tile + 2 * (int64_t)gridDim.x, ntiles, tid);
         }
         // ---- stage 0: operand of the first tensor-core layer into A0
@@ -303,6 +295,13 @@ __global__ void __launch_bounds__(kThreads) k_mlp_bf16(Bf16Args a) {
                 break;
             }
             tc_fence_after();
+            if constexpr (kAsync) {
+                if (l == first && tile + gridDim.x < ntiles) {
+                    // the first layer has read the operand buffer: the next
+                    // tile's rows stream in while this tile finishes
+                    gather_async<MODE>(a, A0, (tile + gridDim.x) * kM, tid, sidx + ((it + 1) & 1) * 2 * kM);
+                }
+            }
             float v[64];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {

@@ -35,6 +35,10 @@ import torch
 from . import inputs as I
 
 
+# a checkpoint whose PCG has not converged by then counts as failed
+VAL_MAX_ITER = 5000
+
+
 def _np(t):
     return t.detach().cpu().numpy()
 
@@ -74,7 +78,7 @@ def evaluate(N, cfg, w, probs, rtol=1e-6, seed=77, precision=None):
         P = N.analyse(rp, ci)
         b = torch.as_tensor(I.rhs(P.n, seed + k), device="cuda")
         L = N.gnn_factor(P, v, b, cfg, w, precision=N.FP32 if precision is None else precision)
-        _, sl = N.pcg_solve(P, v, b, N.PREC_LLT, L, rtol=rtol)
+        _, sl = N.pcg_solve(P, v, b, N.PREC_LLT, L, rtol=rtol, max_iter=VAL_MAX_ITER)
         Li, _ = N.ic0_factor(P, v)
         _, si = N.pcg_solve(P, v, b, N.PREC_LLT, Li, rtol=rtol)
         _, sj = N.pcg_solve(P, v, b, N.PREC_JACOBI, None, rtol=rtol)
@@ -145,8 +149,9 @@ def train(cfg: I.GnnConfig, steps=600, groups=4, per_group=8, pairs=8, m=128, lr
         for Pv, v, bv in vals:
             # the deployed configuration: FP32 triangular solves with a BF16 network
             L = N.gnn_factor(Pv, v, bv, cfg, w, precision=prec)
-            _, st = N.pcg_solve(Pv, v, bv, N.PREC_LLT32 if prec == N.BF16 else N.PREC_LLT, L, rtol=1e-6)
-            its.append(st[0]["iters"] if st[0]["status"] == 0 else 10 * Pv.n)
+            _, st = N.pcg_solve(Pv, v, bv, N.PREC_LLT32 if prec == N.BF16 else N.PREC_LLT, L, rtol=1e-6,
+                                max_iter=VAL_MAX_ITER)
+            its.append(st[0]["iters"] if st[0]["status"] == 0 else 2 * VAL_MAX_ITER)
         return float(np.mean(its))
 
     best = (val_iters(), 0, w.clone())

@@ -51,3 +51,36 @@ def test_trained_beats_untrained_and_jacobi(N, prob):
     assert it["trained"] < it["untrained"]
     assert it["trained"] < sj[0]["iters"]
     assert it["trained"] <= 1.5 * si[0]["iters"]
+
+
+FEM2D = os.path.join(os.path.dirname(WEIGHTS), "gnn_6x64_fem2d.npy")
+
+
+@pytest.mark.skipif(not os.path.exists(FEM2D), reason="no 2-D FEM network")
+@pytest.mark.parametrize("seed", [9600, 9601])
+def test_fem2d_network_beats_ic0_in_the_oracle(N, seed):
+    """The network trained on 2-D FEM systems, on held-out 256 x 256 FEM
+    systems: its factor (computed on the GPU, FP32 network) handed to the
+    oracle's FP64 PCG needs fewer iterations than the oracle's IC(0)-PCG,
+    and the GPU's PCG with the benchmark's configuration (BF16 network, FP32
+    apply) agrees within 10 % and reaches the true residual."""
+    import oracle as O
+    meta = json.load(open(os.path.splitext(FEM2D)[0] + ".json"))
+    cfg = I.GnnConfig(**meta["config"])
+    w = torch.as_tensor(np.load(FEM2D), device="cuda")
+    p = I.fem2d(256, sigma=1.0, corr_len=0.1, seed=seed)
+    Ao = O.assemble(p)
+    rp, ci, v = N.assemble_system(p)
+    P = N.analyse(rp, ci)
+    b = I.rhs(P.n, seed)
+    bg = torch.as_tensor(b, device="cuda")
+    L32 = N.gnn_factor(P, v, bg, cfg, w, precision=N.FP32)
+    Lpat, _ = O.tril(Ao, with_values=False)
+    _, it_learned, _, st = O.pcg(Ao, b, O.PREC_LLT, O.CSR(Lpat.row_ptr, Lpat.col_idx, L32.cpu().numpy()), rtol=1e-6)
+    _, it_ic0, _, st0 = O.pcg(Ao, b, O.PREC_LLT, O.ic0(Ao)[0], rtol=1e-6)
+    assert st == 0 and st0 == 0
+    assert it_learned < it_ic0
+    L16 = N.gnn_factor(P, v, bg, cfg, w, precision=N.BF16)
+    x, sg = N.pcg_solve(P, v, bg, N.PREC_LLT32, L16, rtol=1e-6)
+    assert sg[0]["status"] == 0 and abs(sg[0]["iters"] - it_learned) <= 0.1 * it_learned
+    assert np.linalg.norm(b - O.spmv(Ao, x.cpu().numpy())) / np.linalg.norm(b) <= 1e-6 * (1 + 1e-3)
