@@ -72,6 +72,7 @@ def _L():
             lib.or_gnn_forward.argtypes = [vp, C.c_int32, i32p, i32p, f64p, f64p, f64p, i32p, i32p, f64p, vp]
             lib.or_gnn_forward_scaled.argtypes = [vp, C.c_int32, i32p, i32p, f64p, f64p, f64p, i32p, i32p, f64p,
                                                   f64p]
+            lib.or_gnn_x0.argtypes = [vp, C.c_int32, i32p, i32p, f64p, f64p, f64p, i32p, i32p, f64p, f64p]
             lib.or_llt_loss.argtypes = [C.c_int32, i32p, i32p, f64p, C.c_int, f64p, f64p, vp]
             lib.or_llt_loss.restype = C.c_double
             lib.or_loss_and_grad.argtypes = [vp, C.c_int32, i32p, i32p, f64p, C.c_int, f64p, f64p, f64p, vp]
@@ -238,11 +239,12 @@ def pcg(A: CSR, b, precond=PREC_NONE, L: CSR | None = None, rtol=1e-8, max_iter=
 
 # ------------------------------------------------------------------ GNN
 class _Cfg(C.Structure):
-    _fields_ = [("n_mp", C.c_int), ("l", C.c_int), ("l_mp", C.c_int), ("h", C.c_int), ("diag_mode", C.c_int)]
+    _fields_ = [("n_mp", C.c_int), ("l", C.c_int), ("l_mp", C.c_int), ("h", C.c_int), ("diag_mode", C.c_int),
+                ("x0_head", C.c_int)]
 
 
 def _cfg(cfg):
-    return _Cfg(cfg.n_mp, cfg.l, cfg.l_mp, cfg.h, cfg.diag_mode)
+    return _Cfg(cfg.n_mp, cfg.l, cfg.l_mp, cfg.h, cfg.diag_mode, int(getattr(cfg, "x0_head", 0)))
 
 
 def gnn_nparams(cfg):
@@ -260,6 +262,16 @@ def gnn_forward(cfg, A: CSR, b, w, return_s=False):
                         L.row_ptr, L.col_idx, Lv, _ptr(s))
     out = CSR(L.row_ptr, L.col_idx, Lv)
     return (out, s) if return_s else out
+
+
+def gnn_x0(cfg, A: CSR, b, w):
+    """Initial guess of the x0 head (cfg.x0_head): x0_i = (||b||_inf / s) MLP_x(v_i)."""
+    L, _ = tril(A, with_values=False)
+    Lv = np.zeros(L.nnz)
+    x0 = np.zeros(A.n)
+    c = _cfg(cfg)
+    _L().or_gnn_x0(C.byref(c), A.n, A.row_ptr, A.col_idx, A.val, _f64(b), _f64(w), L.row_ptr, L.col_idx, Lv, x0)
+    return x0
 
 
 def gnn_forward_scaled(cfg, A: CSR, b, w, s_max_diag, b_inf):

@@ -490,7 +490,9 @@ done:
  * Flat weights: node encoder, edge encoder, n_mp x (node MLP, edge MLP),
  * decoder; each Linear W[out][in] then b[out].
  * ==================================================================== */
-typedef struct { int n_mp, l, l_mp, h, diag_mode; } or_gnn_cfg;
+/* x0_head: the initial-guess head of Sec. 4.2 ("surrogate" use): an MLP of
+ * depth l on the final node features, x0_i = (||b||_inf / s) MLP_x(v_i) */
+typedef struct { int n_mp, l, l_mp, h, diag_mode, x0_head; } or_gnn_cfg;
 
 static int64_t mlp_nparams(int in, int h, int out, int depth) {
     int64_t s = (int64_t)in * h + h;
@@ -504,6 +506,7 @@ int64_t or_gnn_nparams(const or_gnn_cfg* c) {
     int64_t s = 2 * mlp_nparams(1, h, h, c->l);
     s += c->n_mp * (mlp_nparams(2 * h, h, h, c->l_mp) + mlp_nparams(3 * h, h, h, c->l_mp));
     s += mlp_nparams(h, h, 1, c->l);
+    if (c->x0_head) s += mlp_nparams(h, h, 1, c->l);
     return s;
 }
 
@@ -588,11 +591,14 @@ typedef struct {
     double *tev, *tee;       /* encoder tapes */
     double *td;              /* decoder tapes */
     double *s;               /* decoder outputs [nnz] */
+    double *xo, *tx;         /* initial-guess head: outputs [n], tapes [n][Td] */
+    double sA, binf;         /* input scales */
 } gnn_tape;
 
 static void tape_free(gnn_tape* t) {
     free(t->v); free(t->e); free(t->agg); free(t->tv); free(t->te);
     free(t->tev); free(t->tee); free(t->td); free(t->s);
+    free(t->xo); free(t->tx);
 }
 
 /* forward; fills Lv on the tril pattern (Lrp/Lci from or_tril) and the tape */
@@ -614,6 +620,8 @@ static void gnn_forward_tape(const or_gnn_cfg* c, int32_t n, const int32_t* rp, 
     T->tee = (double*)calloc((size_t)nnz * Tenc, sizeof(double));
     T->td = (double*)calloc((size_t)nnz * T->Td, sizeof(double));
     T->s = (double*)calloc((size_t)nnz, sizeof(double));
+    T->xo = c->x0_head ? (double*)calloc((size_t)n, sizeof(double)) : NULL;
+    T->tx = c->x0_head ? (double*)calloc((size_t)n * T->Td, sizeof(double)) : NULL;
 
     /* input scaling */
     double sA = 0.0, binf = 0.0;
@@ -668,6 +676,15 @@ static void gnn_forward_tape(const or_gnn_cfg* c, int32_t n, const int32_t* rp, 
     double* eL = T->e + (size_t)c->n_mp * nnz * h;
     for (int64_t k = 0; k < nnz; ++k)
         mlp_fwd(w_dec, h, h, 1, l, eL + (size_t)k * h, T->s + k, T->td + (size_t)k * T->Td);
+    T->sA = sA;
+    T->binf = binf;
+    if (c->x0_head) {
+        /* initial-guess head on the final node features (weights after the decoder's) */
+        const double* w_x = w_dec + mlp_nparams(h, h, 1, l);
+        const double* vL = T->v + (size_t)c->n_mp * n * h;
+        for (int32_t i = 0; i < n; ++i)
+            mlp_fwd(w_x, h, h, 1, l, vL + (size_t)i * h, T->xo + i, T->tx + (size_t)i * T->Td);
+    }
     double rs = sqrt(sA);
     for (int32_t i = 0; i < n; ++i)
         for (int32_t kk = Lrp[i]; kk < Lrp[i + 1]; ++kk) {
@@ -706,6 +723,15 @@ void or_gnn_forward(const or_gnn_cfg* c, int32_t n, const int32_t* rp, const int
  * rows of a large system on a subgraph: after n_mp rounds a node's state
  * depends only on nodes within n_mp hops (App. A.3), so L_ij of a row i at the
  * centre of the ball of radius n_mp + 1 around i equals the full system's. */
+/* Initial guess of the head: x0_i = (||b||_inf / s) MLP_x(v_i) (needs x0_head). */
+void or_gnn_x0(const or_gnn_cfg* c, int32_t n, const int32_t* rp, const int32_t* ci, const double* av,
+               const double* b, const double* w, const int32_t* Lrp, const int32_t* Lci, double* Lv, double* x0) {
+    gnn_tape T;
+    gnn_forward_tape(c, n, rp, ci, av, b, w, Lrp, Lci, Lv, &T, NULL);
+    for (int32_t i = 0; i < n; ++i) x0[i] = c->x0_head ? T.binf / T.sA * T.xo[i] : 0.0;
+    tape_free(&T);
+}
+
 void or_gnn_forward_scaled(const or_gnn_cfg* c, int32_t n, const int32_t* rp, const int32_t* ci,
                            const double* av, const double* b, const double* w,
                            const int32_t* Lrp, const int32_t* Lci, double* Lv, const double* scales) {
@@ -873,6 +899,26 @@ double or_loss_and_grad(const or_gnn_cfg* c, int32_t n, const int32_t* rp, const
         if (grad) {
             for (int64_t k = 0; k < nnzL; ++k) dL[k] /= npairs;
             gnn_backward(c, n, rp, ci, av, w, Lrp, Lci, dL, &T, grad);
+        }
+        if (c->x0_head) {
+            /* regression of the head to x in its own output units,
+             * sum_i (MLP_x(v_i) - x_i s / ||b||_inf)^2; the trunk is not
+             * differentiated through (the preconditioner is trained by the
+             * loss above alone) */
+            const int h = c->h, l = c->l;
+            int64_t off_x = or_gnn_nparams(c) - mlp_nparams(h, h, 1, l);
+            const double t_scale = T.sA / T.binf;
+            const double* xp = X + (size_t)p * n;
+            double lx = 0.0;
+            for (int32_t i = 0; i < n; ++i) {
+                const double d = T.xo[i] - xp[i] * t_scale;
+                lx += d * d;
+                if (grad) {
+                    const double dy = 2.0 * d / npairs;
+                    mlp_bwd(w + off_x, grad + off_x, h, h, 1, l, T.tx + (size_t)i * T.Td, &dy, NULL);
+                }
+            }
+            loss += lx / npairs;
         }
         tape_free(&T);
     }

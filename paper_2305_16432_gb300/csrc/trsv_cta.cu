@@ -284,6 +284,16 @@ __global__ void __launch_bounds__(kCtaThreads, 1) k_trsv_cta(CtaDev D, const T* 
         load_step<kRemote>(cur, hdr, vals, rh, q0e, t);
     }
     for (;;) {
+        // the current step's window reads are issued first: their latency
+        // overlaps the bookkeeping and the next step's operand loads (the
+        // warp issues in order)
+        T yw0 = (T)0, yw1 = (T)0, yw2 = (T)0, yw3 = (T)0;
+        if (kWindow && !kRemote && t < cur.nrows) {
+            yw0 = win[cur.dep.x];
+            yw1 = win[cur.dep.y];
+            yw2 = win[cur.dep.z];
+            yw3 = win[cur.dep.w];
+        }
         // locate and load the next step
         const int32_t* chdr = hdr;          // the current step, for rows wider than the registers
         const T* cvals = vals;
@@ -316,11 +326,10 @@ __global__ void __launch_bounds__(kCtaThreads, 1) k_trsv_cta(CtaDev D, const T* 
             T acc = cur.rhs;
             if (kWindow && !kRemote) {
                 // missing dependencies read the zero slot with a zero value
-                const T y0 = win[cur.dep.x], y1 = win[cur.dep.y], y2 = win[cur.dep.z], y3 = win[cur.dep.w];
-                acc = fma(-cur.l[0], y0, acc);
-                acc = fma(-cur.l[1], y1, acc);
-                acc = fma(-cur.l[2], y2, acc);
-                acc = fma(-cur.l[3], y3, acc);
+                acc = fma(-cur.l[0], yw0, acc);
+                acc = fma(-cur.l[1], yw1, acc);
+                acc = fma(-cur.l[2], yw2, acc);
+                acc = fma(-cur.l[3], yw3, acc);
             } else {
                 const int pd[4] = {cur.dep.x, cur.dep.y, cur.dep.z, cur.dep.w};
 #pragma unroll

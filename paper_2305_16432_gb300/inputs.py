@@ -137,6 +137,7 @@ class GnnConfig:
     l_mp: int = 2
     h: int = 16
     diag_mode: int = 0     # 0: L_ii = softplus(s_ii)
+    x0_head: int = 0       # 1: initial-guess head (node MLP of depth l after the decoder)
 
     def linears(self):
         """(fan_in, fan_out) of every Linear in flat-layout order."""
@@ -152,6 +153,8 @@ class GnnConfig:
             out += mlp(2 * h, h, self.l_mp)   # node update
             out += mlp(3 * h, h, self.l_mp)   # edge update
         out += mlp(h, 1, self.l)              # decoder
+        if self.x0_head:
+            out += mlp(h, 1, self.l)          # initial-guess head
         return out
 
     @property

@@ -1,5 +1,6 @@
 """Pins of the oracle's GNN (Sec. 4.2 "Architecture", App. A.3), the loss
 Eq. (loss_Ab) with its gradient, and Adam (App. A.4)."""
+import dataclasses
 import math
 
 import numpy as np
@@ -21,6 +22,8 @@ def _unpack(cfg, w):
         k += fo
         mats.append((W, b))
     sizes = [cfg.l + 1] * 2 + [cfg.l_mp + 1, cfg.l_mp + 1] * cfg.n_mp + [cfg.l + 1]
+    if cfg.x0_head:
+        sizes += [cfg.l + 1]
     out, k = [], 0
     for s in sizes:
         out.append(mats[k:k + s])
@@ -59,7 +62,7 @@ def _dense_gnn_impl(cfg, D, b, w):
         X = np.concatenate([E, np.broadcast_to(V[:, None, :], E.shape),
                             np.broadcast_to(V[None, :, :], E.shape)], 2)
         E = _mlp(mlps[3 + 2 * t], X) * mask[:, :, None]
-    S = _mlp(mlps[-1], E)[:, :, 0] * mask
+    S = _mlp(mlps[2 + 2 * cfg.n_mp], E)[:, :, 0] * mask
     sym = 0.5 * (S + S.T)
     L = np.tril(sym, -1)
     if cfg.diag_mode == 1:
@@ -280,3 +283,80 @@ def test_gnn_rows_on_neighbourhood_balls(prob):
     k = int(np.searchsorted(nodes, r))
     s, e = L.row_ptr[r], L.row_ptr[r + 1]
     assert not np.allclose(Ls.val[Ls.row_ptr[k]:Ls.row_ptr[k + 1]], L.val[s:e], rtol=1e-9, atol=0)
+
+
+def _dense_x0(cfg, D, b, w):
+    """Initial guess of the head in the dense formulation: the final node
+    features V through the head MLP, scaled by ||b||_inf / s."""
+    n = D.shape[0]
+    mask = D != 0
+    mlps = _unpack(cfg, w)
+    s = np.max(np.diag(D))
+    binf = np.max(np.abs(b)) or 1.0
+    V = _mlp(mlps[0], (b / binf)[:, None])
+    E = _mlp(mlps[1], (D / s)[:, :, None]) * mask[:, :, None]
+    for t in range(cfg.n_mp):
+        agg = np.einsum("ijh,jh->ih", E, V)
+        V = _mlp(mlps[2 + 2 * t], np.concatenate([V, agg], 1))
+        X = np.concatenate([E, np.broadcast_to(V[:, None, :], E.shape),
+                            np.broadcast_to(V[None, :, :], E.shape)], 2)
+        E = _mlp(mlps[3 + 2 * t], X) * mask[:, :, None]
+    return binf / s * _mlp(mlps[-1], V)[:, 0]
+
+
+@pytest.mark.parametrize("cfg", [I.GnnConfig(n_mp=2, l=2, l_mp=2, h=4, diag_mode=1, x0_head=1),
+                                 I.GnnConfig(n_mp=0, l=1, l_mp=2, h=3, x0_head=1)])
+def test_x0_head_matches_dense_formulation(cfg):
+    A = _tiny_system()
+    b = np.random.default_rng(3).standard_normal(A.n)
+    w = I.gnn_weights(cfg, 5, scale=1.5).astype(np.float64)
+    assert np.allclose(O.gnn_x0(cfg, A, b, w), _dense_x0(cfg, A.dense(), b, w), rtol=1e-12, atol=1e-13)
+    # the factor does not depend on the head
+    base = dataclasses.replace(cfg, x0_head=0)
+    nb = base.nparams
+    assert np.array_equal(O.gnn_forward(cfg, A, b, w).val, O.gnn_forward(base, A, b, w[:nb]).val)
+
+
+def test_x0_head_constant_output():
+    # head weights zero except the last bias c: x0 = (||b||_inf / s) c everywhere
+    cfg = I.GnnConfig(n_mp=2, l=2, l_mp=1, h=4, x0_head=1)
+    A = _tiny_system()
+    b = np.random.default_rng(4).standard_normal(A.n)
+    w = I.gnn_weights(cfg, 6).astype(np.float64)
+    nb = dataclasses.replace(cfg, x0_head=0).nparams
+    w[nb:] = 0.0
+    w[-1] = 0.75
+    s = np.max(np.diag(A.dense()))
+    assert np.allclose(O.gnn_x0(cfg, A, b, w), np.max(np.abs(b)) / s * 0.75, rtol=1e-14)
+
+
+def test_x0_head_gradient():
+    # the head is trained by regression to x in its output units; the trunk
+    # is not differentiated through it: head weights match central
+    # differences of the total loss, trunk weights match the gradient of the
+    # network without the head
+    cfg = I.GnnConfig(n_mp=1, l=2, l_mp=1, h=3, diag_mode=1, x0_head=1)
+    base = dataclasses.replace(cfg, x0_head=0)
+    nb = base.nparams
+    A = _tiny_system()
+    g = np.random.default_rng(7)
+    B = g.standard_normal((2, A.n))
+    X = np.linalg.solve(A.dense(), B.T).T
+    w = I.gnn_weights(cfg, 8, scale=1.5).astype(np.float64)
+    loss, grad = O.loss_and_grad(cfg, A, X, B, w)
+    lb, gb = O.loss_and_grad(base, A, X, B, w[:nb])
+    assert np.allclose(grad[:nb], gb, rtol=1e-12, atol=1e-14 * np.abs(gb).max())
+    s = np.max(np.diag(A.dense()))
+    lx = np.mean([np.sum((_dense_x0(cfg, A.dense(), B[p], w) - X[p]) ** 2) * (s / np.max(np.abs(B[p]))) ** 2
+                  for p in range(2)])
+    assert math.isclose(loss, lb + lx, rel_tol=1e-10)
+    eps = 1e-6
+    floor = 1e-3 * np.abs(grad[nb:]).max()
+    err = 0.0
+    for k in range(nb, len(w)):
+        wp, wm = w.copy(), w.copy()
+        wp[k] += eps
+        wm[k] -= eps
+        fd = (O.loss_and_grad(cfg, A, X, B, wp, False)[0] - O.loss_and_grad(cfg, A, X, B, wm, False)[0]) / (2 * eps)
+        err = max(err, abs(fd - grad[k]) / max(floor, abs(grad[k])))
+    assert err < 1e-6, err
