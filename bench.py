@@ -112,8 +112,12 @@ def _dist():
 TASK_WEIGHTS = {"fem2d_256": "gnn_6x64_fem2d.npy", "fd3d_128": "gnn_6x64_fd3d.npy", "batched_256": "gnn_6x64.npy"}
 
 
-def weights_for(workload):
-    p = os.path.join(WEIGHTS_DIR, TASK_WEIGHTS.get(workload, "gnn_6x64.npy"))
+def weights_for(workload, x0=False):
+    name = TASK_WEIGHTS.get(workload, "gnn_6x64.npy")
+    if x0:
+        # the same network with a trained initial-guess head
+        name = name.replace(".npy", "_x0.npy")
+    p = os.path.join(WEIGHTS_DIR, name)
     return p if os.path.exists(p) else os.path.join(WEIGHTS_DIR, "gnn_6x64.npy")
 
 
@@ -121,11 +125,13 @@ def _load_weights(cfg, path):
     from paper_2305_16432_gb300 import inputs as I
     if path and os.path.exists(path):
         w = np.load(path).astype(np.float32)
+        meta = {}
+        mp = os.path.splitext(path)[0] + ".json"
+        if os.path.exists(mp):
+            meta = json.load(open(mp))
+        if meta.get("config"):
+            cfg = I.GnnConfig(**meta["config"])
         if len(w) == cfg.nparams:
-            meta = {}
-            mp = os.path.splitext(path)[0] + ".json"
-            if os.path.exists(mp):
-                meta = json.load(open(mp))
             return w, "trained", meta
     return I.gnn_weights(cfg, 1), "random-init", {}
 
@@ -314,9 +320,16 @@ def run_solve(args, rank, world, local):
     apply32 = args.apply == "fp32"
     pc = N.PREC_LLT32 if apply32 else N.PREC_LLT
 
+    use_x0 = bool(args.x0)
+    if use_x0 and not cfg.x0_head:
+        raise SystemExit("--x0 needs weights with an initial-guess head")
+
     def learned_step():
-        L = N.gnn_factor(P, v, b, cfg, w, precision=prec)
-        x, st = N.pcg_solve(P, v, b, pc, L, rtol=RTOL)
+        if use_x0:
+            L, x0 = N.gnn_factor_x0(P, v, b, cfg, w, precision=prec)
+        else:
+            L, x0 = N.gnn_factor(P, v, b, cfg, w, precision=prec), None
+        x, st = N.pcg_solve(P, v, b, pc, L, rtol=RTOL, x0=x0)
         return st
 
     def ic0_step():
@@ -356,10 +369,13 @@ def run_solve(args, rank, world, local):
     # SpTRSV bytes per launch: index + value per L entry, row pointer, rhs + solution
     trsv_bytes = (8 if apply32 else 12) * P.nnz_L + 4 * (P.n + 1) + 16 * P.n
     achieved = trsv_bytes / (trsv_ms * 1e-3) / 1e9
+    trsv_kernel = {N.TRSV_LEVELSYNC: "k_trsv_cta",
+                   N.TRSV_LEVELFLAG: "k_trsv_flag" if apply32 else "k_trsv_cta"}.get(P.trsv_mode, "k_trsv")
+    # DRAM bytes of one forward launch from an ncu capture of this kernel
     traffic = None
     prof = os.path.join(ROOT, "profiles", "trsv_traffic.json")
     if os.path.exists(prof):
-        traffic = json.load(open(prof)).get(args.workload + "_fwd_bytes")
+        traffic = json.load(open(prof)).get(f"{args.workload}_{trsv_kernel}_fwd_bytes")
     spmv_rl = _spmv_roofline(N, P, v, hbm)
 
     # end to end through the C ABI with host buffers (pinned)
@@ -386,7 +402,7 @@ def run_solve(args, rank, world, local):
     # PCG: 4 factor loads, init, preconditioner apply, r^T z, per graph trip 2
     # iterations (SpMV, update, r^T z and the apply) + the loop condition, stats;
     # the level-synchronous apply is 2 solves + 2 gathers, the sync-free one 2 solves
-    apply = 4 if P.trsv_mode == N.TRSV_LEVELSYNC else 2
+    apply = 4 if P.trsv_mode in (N.TRSV_LEVELSYNC, N.TRSV_LEVELFLAG) else 2
     trips = max(1, math.ceil(max(it_l) / 2))
     pcg_launches = 4 + 1 + apply + 1 + (2 * (3 + apply) + 1) * trips + 1
     launches = (gnn_launches + pcg_launches) * args.steps
@@ -422,17 +438,17 @@ def run_solve(args, rank, world, local):
             "vs_baseline": None, "dtype": "f64+" + args.precision, "data": "synthetic",
             "config": {"workload": wl, "systems_per_step": nsys, "n": P.n, "nnz": P.nnz, "nnz_L": P.nnz_L,
                        "levels": P.nlev_fwd, "gnn": f"n_mp={cfg.n_mp},l={cfg.l},l_mp={cfg.l_mp},h={cfg.h},"
-                       f"diag_mode={cfg.diag_mode}," + args.precision,
+                       f"diag_mode={cfg.diag_mode}," + args.precision + (",x0_head" if use_x0 else ""),
                        "weights": wkind, "pcg": "fp64 recurrences, " + args.apply + " L L^T solves",
                        "rtol": RTOL, "l2": "flushed between steps (256 MB write)"},
             "compare": {"learned_iters": it_l if nsys > 1 else it_l[0],
                         "learned_ms_median": float(np.median(ms_l)),
                         "ic0_ms_per_system": float(np.mean(ms_i)) / nsys, "ic0_iters": it_i if nsys > 1 else it_i[0],
                         "wall_s_timed": wall,
-                        "trsv_design": "levelsync" if P.trsv_mode == N.TRSV_LEVELSYNC else "syncfree",
+                        "trsv_design": {N.TRSV_LEVELSYNC: "levelsync", N.TRSV_LEVELFLAG: "levelflag"}.get(
+                            P.trsv_mode, "syncfree"),
                         "trsv_tuned_ms_fwd_bwd": P.tuned_ms},
-            "roofline": {"kernel": ("k_trsv_cta" if P.trsv_mode == N.TRSV_LEVELSYNC else "k_trsv")
-                         + " (forward SpTRSV, " + args.apply + ")", "bound": "hbm",
+            "roofline": {"kernel": trsv_kernel + " (forward SpTRSV, " + args.apply + ")", "bound": "hbm",
                          "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                          "peak_kind": peak_kind, "traffic": traffic, "bytes_per_launch": trsv_bytes,
                          "ms_per_launch": trsv_ms, "levels": P.nlev_fwd},
@@ -509,12 +525,14 @@ def main():
     ap.add_argument("--apply", default="fp32", choices=["fp32", "fp64"],
                     help="arithmetic of the L L^T solves inside the FP64 PCG")
     ap.add_argument("--weights", default=None, help="network weights (.npy); default: the workload's own")
+    ap.add_argument("--x0", action="store_true",
+                    help="start PCG from the network's initial guess (weights with an initial-guess head)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--trsv-reps", type=int, default=50)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.weights is None:
-        args.weights = weights_for(args.workload)
+        args.weights = weights_for(args.workload, args.x0)
     if args.impl == "reference":
         run_reference(args)
         return

@@ -122,26 +122,33 @@ NPCG_API npcg_status npcg_analyse(npcg_handle h, int64_t n, int64_t nnz, const i
                          npcg_pattern* out);
 NPCG_API npcg_status npcg_pattern_free(npcg_pattern p);
 
-/* Triangular-solve designs (both exact, same result up to rounding):
+/* Triangular-solve designs (all exact, same result up to rounding):
  *   NPCG_TRSV_SYNCFREE: every SM; rows claimed in level order by warps, each
  *     row waits on its dependencies' values (flag-free, bounded waits);
  *   NPCG_TRSV_LEVELSYNC: one CTA per system walks the levels with one
  *     barrier per level, dependencies in a shared-memory window, each level's
- *     data prefetched by TMA bulk copies.
- * npcg_analyse times both on the pattern and keeps the faster. */
-enum { NPCG_TRSV_AUTO = 0, NPCG_TRSV_SYNCFREE = 1, NPCG_TRSV_LEVELSYNC = 2 };
+ *     data prefetched by TMA bulk copies;
+ *   NPCG_TRSV_LEVELFLAG: the same layout and prefetch without the barrier:
+ *     each window slot carries its row's position next to the value and a
+ *     row polls its dependencies' slots (FP32 solves, NPCG_PREC_LLT32; FP64
+ *     solves use NPCG_TRSV_LEVELSYNC).  Available when the window also
+ *     covers how far one warp can run ahead of another.
+ * npcg_analyse times the designs on the pattern and keeps the fastest. */
+enum { NPCG_TRSV_AUTO = 0, NPCG_TRSV_SYNCFREE = 1, NPCG_TRSV_LEVELSYNC = 2, NPCG_TRSV_LEVELFLAG = 3 };
 
 typedef struct {
     int64_t n, nnz, nnz_L;
     int32_t nsys;
     int32_t nlev_fwd, nlev_bwd;   /* number of levels of L y = r / L^T z = y */
-    int32_t trsv_mode;            /* design in use (NPCG_TRSV_SYNCFREE / _LEVELSYNC) */
-    float tuned_ms_syncfree;      /* measured forward + backward solve, ms      */
+    int32_t trsv_mode;            /* design in use (NPCG_TRSV_SYNCFREE / _LEVELSYNC / _LEVELFLAG) */
+    float tuned_ms_syncfree;      /* measured forward + backward FP32 solve, ms */
     float tuned_ms_levelsync;     /* (0 when the design does not apply)         */
+    float tuned_ms_levelflag;
 } npcg_pattern_info;
 NPCG_API npcg_status npcg_pattern_get_info(npcg_pattern p, npcg_pattern_info* out);  /* host out */
 /* Overrides the tuned design (NPCG_TRSV_AUTO restores the tuned choice).
- * NPCG_TRSV_LEVELSYNC returns NPCG_EINVAL when its layout does not fit. */
+ * NPCG_TRSV_LEVELSYNC / _LEVELFLAG return NPCG_EINVAL when the layout does
+ * not fit (or, for _LEVELFLAG, its window does not cover the drift). */
 NPCG_API npcg_status npcg_pattern_set_trsv(npcg_pattern p, int32_t mode);
 
 /* Copies of the analysis results (device arrays, caller-allocated):
@@ -180,6 +187,9 @@ typedef struct {
     int32_t h;           /* hidden = latent width: 16, 32 or 64          */
     int32_t diag_mode;   /* NPCG_DIAG_SOFTPLUS or NPCG_DIAG_LDLT_DIAGA    */
     int32_t precision;   /* NPCG_FP32 (parity) or NPCG_BF16 (tensor cores)*/
+    int32_t x0_head;     /* 1: the weights end with the initial-guess head
+                            (an MLP of depth l, h -> 1, on the final node
+                            features; Sec. 4.4 surrogate use), else 0     */
 } npcg_gnn_config;
 
 /* Number of FP32 parameters of the flat weight vector (host out). */
@@ -189,6 +199,16 @@ NPCG_API npcg_status npcg_gnn_nparams(const npcg_gnn_config* cfg, int64_t* out);
 NPCG_API npcg_status npcg_gnn_factor(npcg_handle h, npcg_pattern p, const double* A_val,
                             const double* b, const npcg_gnn_config* cfg,
                             const float* weights, double* L_val);
+/* Factor and initial guess from one network pass (cfg->x0_head must be 1):
+ * L_val as npcg_gnn_factor; x0 [n] (device, FP64) receives
+ * x0_i = (||b||_inf / s) MLP_x(v_i) with s the largest diagonal of A and
+ * ||b||_inf of the row's system (the head's output scale), to be passed to
+ * npcg_pcg_solve as the starting iterate.  Both outputs are caller-owned
+ * device buffers.  NPCG_EINVAL for a NULL argument or cfg->x0_head != 1;
+ * otherwise the statuses of npcg_gnn_factor. */
+NPCG_API npcg_status npcg_gnn_factor_x0(npcg_handle h, npcg_pattern p, const double* A_val, const double* b,
+                                        const npcg_gnn_config* cfg, const float* weights, double* L_val,
+                                        double* x0);
 
 /* --------------------------------------------------------------------------
  * IC(0) (Sec. 5.1 baseline "IC"), textbook row-oriented form on tril(A):

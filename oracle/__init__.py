@@ -265,7 +265,7 @@ def gnn_forward(cfg, A: CSR, b, w, return_s=False):
 
 
 def gnn_x0(cfg, A: CSR, b, w):
-    """Initial guess of the x0 head (cfg.x0_head): x0_i = (||b||_inf / s) MLP_x(v_i)."""
+    """Initial guess of the x0 head (Sec. 4.4, cfg.x0_head): x0_i = (||b||_inf / s) MLP_x(v_i)."""
     L, _ = tril(A, with_values=False)
     Lv = np.zeros(L.nnz)
     x0 = np.zeros(A.n)

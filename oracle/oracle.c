@@ -490,7 +490,7 @@ done:
  * Flat weights: node encoder, edge encoder, n_mp x (node MLP, edge MLP),
  * decoder; each Linear W[out][in] then b[out].
  * ==================================================================== */
-/* x0_head: the initial-guess head of Sec. 4.2 ("surrogate" use): an MLP of
+/* x0_head: the initial-guess head of Sec. 4.4 ("surrogate" use): an MLP of
  * depth l on the final node features, x0_i = (||b||_inf / s) MLP_x(v_i) */
 typedef struct { int n_mp, l, l_mp, h, diag_mode, x0_head; } or_gnn_cfg;
 

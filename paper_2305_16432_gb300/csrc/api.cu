@@ -129,22 +129,28 @@ npcg_status npcg_pattern_get_info(npcg_pattern p, npcg_pattern_info* out) {
     out->nsys = p->nsys;
     out->nlev_fwd = p->fwd.nlev;
     out->nlev_bwd = p->bwd.nlev;
-    out->trsv_mode = p->trsv_mode == kTrsvCta ? NPCG_TRSV_LEVELSYNC : NPCG_TRSV_SYNCFREE;
+    out->trsv_mode = p->trsv_mode != kTrsvCta ? NPCG_TRSV_SYNCFREE
+                   : p->cta_flag ? NPCG_TRSV_LEVELFLAG : NPCG_TRSV_LEVELSYNC;
     out->tuned_ms_syncfree = p->tune_ms[0];
     out->tuned_ms_levelsync = p->tune_ms[1];
+    out->tuned_ms_levelflag = p->tune_ms[2];
     return NPCG_OK;
 }
 
 npcg_status npcg_pattern_set_trsv(npcg_pattern p, int32_t mode) {
     if (!p) return NPCG_EINVAL;
     if (mode == NPCG_TRSV_AUTO) {
-        p->trsv_mode = (p->tune_ms[1] > 0.f && p->tune_ms[1] < p->tune_ms[0]) ? kTrsvCta : kTrsvSyncFree;
+        trsv_pick_tuned(p);
     } else if (mode == NPCG_TRSV_SYNCFREE) {
         p->trsv_mode = kTrsvSyncFree;
-    } else if (mode == NPCG_TRSV_LEVELSYNC) {
+        p->cta_flag = false;
+    } else if (mode == NPCG_TRSV_LEVELSYNC || mode == NPCG_TRSV_LEVELFLAG) {
         if (!p->cfwd.built || cta_stages(p->cfwd) < 2 || cta_stages(p->cbwd) < 2)
             return set_error(p->h, NPCG_EINVAL, "level-synchronous layout does not fit shared memory");
+        if (mode == NPCG_TRSV_LEVELFLAG && !(p->cfwd.flag_ok && p->cbwd.flag_ok))
+            return set_error(p->h, NPCG_EINVAL, "flag-synchronised solve: the window does not cover its drift");
         p->trsv_mode = kTrsvCta;
+        p->cta_flag = mode == NPCG_TRSV_LEVELFLAG;
     } else {
         return set_error(p->h, NPCG_EINVAL, "unknown triangular-solve mode");
     }
@@ -172,7 +178,7 @@ npcg_status npcg_pattern_export(npcg_handle h, npcg_pattern p, int32_t* L_row_pt
 npcg_status npcg_gnn_nparams(const npcg_gnn_config* cfg, int64_t* out) {
     if (!cfg || !out) return NPCG_EINVAL;
     if (cfg->n_mp < 0 || cfg->n_mp > kMaxMp || cfg->h <= 0 || cfg->l < 1 || cfg->l_mp < 1) return NPCG_EINVAL;
-    *out = gnn_offsets(cfg->h, cfg->l, cfg->l_mp, cfg->n_mp).total;
+    *out = gnn_offsets(cfg->h, cfg->l, cfg->l_mp, cfg->n_mp, cfg->x0_head).total;
     return NPCG_OK;
 }
 
@@ -181,6 +187,14 @@ npcg_status npcg_gnn_factor(npcg_handle h, npcg_pattern p, const double* A_val, 
     NPCG_TRY(check_hp(h, p));
     if (!A_val || !b || !weights || !L_val) return set_error(H(h), NPCG_EINVAL, "NULL array argument");
     return gnn_forward_run(H(h), PT(p), A_val, b, cfg, weights, L_val);
+}
+
+npcg_status npcg_gnn_factor_x0(npcg_handle h, npcg_pattern p, const double* A_val, const double* b,
+                               const npcg_gnn_config* cfg, const float* weights, double* L_val, double* x0) {
+    NPCG_TRY(check_hp(h, p));
+    if (!A_val || !b || !cfg || !weights || !L_val || !x0) return set_error(H(h), NPCG_EINVAL, "NULL argument");
+    if (cfg->x0_head != 1) return set_error(H(h), NPCG_EINVAL, "npcg_gnn_factor_x0 needs cfg->x0_head = 1");
+    return gnn_factor_x0_run(H(h), PT(p), A_val, b, cfg, weights, L_val, x0);
 }
 
 npcg_status npcg_ic0_factor(npcg_handle h, npcg_pattern p, const double* A_val, double* L_val,

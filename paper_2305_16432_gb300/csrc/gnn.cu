@@ -105,6 +105,15 @@ npcg_status run_forward(Handle* h, Pattern* P, const double* A_val, const double
     return NPCG_OK;
 }
 
+// x0_i = (||b||_inf / s) * head output, with the row's system scales
+__global__ void k_x0_scale(int64_t n, const int32_t* row_sys, const double* sc, const float* out, double* x0) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int s = row_sys[i];
+        x0[i] = sc[2 * s + 1] / sc[2 * s] * (double)out[i];
+    }
+}
+
 }  // namespace
 
 npcg_status gnn_check_config(Handle* h, const npcg_gnn_config* cfg) {
@@ -118,6 +127,7 @@ npcg_status gnn_check_config(Handle* h, const npcg_gnn_config* cfg) {
         return set_error(h, NPCG_EINVAL, "unsupported diag_mode");
     if (cfg->precision != NPCG_FP32 && cfg->precision != NPCG_BF16)
         return set_error(h, NPCG_EINVAL, "precision must be NPCG_FP32 or NPCG_BF16");
+    if (cfg->x0_head != 0 && cfg->x0_head != 1) return set_error(h, NPCG_EINVAL, "x0_head must be 0 or 1");
     return NPCG_OK;
 }
 
@@ -169,6 +179,47 @@ npcg_status gnn_forward_run(Handle* h, Pattern* P, const double* A_val, const do
     B.diag_mode = cfg->diag_mode;
     NPCG_TRY(gnn_forward_into(h, P, A_val, b, cfg, w, B));
     return gnn_assemble_L(h, P, B, L_val);
+}
+
+}  // namespace npcg
+
+namespace npcg {
+
+// Factor and initial guess: the trunk runs once; the head (the decoder's MLP
+// shape, h -> 1) runs over the node rows of the final node features.
+npcg_status gnn_factor_x0_run(Handle* h, Pattern* P, const double* A_val, const double* b,
+                              const npcg_gnn_config* cfg, const float* w, double* L_val, double* x0) {
+    NPCG_TRY(gnn_check_config(h, cfg));
+    const GnnOffsets off = gnn_offsets(cfg->h, cfg->l, cfg->l_mp, cfg->n_mp, 1);
+    GnnStore& S = P->gnn;
+    NPCG_TRY(gnn_forward_run(h, P, A_val, b, cfg, w, L_val));     // decoder outputs in S.s are consumed
+    if (cfg->precision == NPCG_BF16) {
+        NPCG_TRY(gnn_bf16_head_run(h, P, cfg, w + off.x0, S.s.p));
+    } else {
+        const size_t fv = (size_t)P->n * cfg->h;
+        MlpArgs a = {};
+        a.rp = P->rp.p;
+        a.ci = P->ci.p;
+        a.erow = P->edge_row.p;
+        a.row_sys = P->row_sys.p;
+        a.sc = S.sc.p;
+        a.av = A_val;
+        a.b = b;
+        a.nrows = P->n;
+        a.w = w + off.x0;
+        a.depth = cfg->l;
+        a.ein = S.v.p + (cfg->n_mp % 2) * fv;                       // final node features
+        a.out = S.s.p;
+        switch (cfg->h) {
+            case 16: NPCG_TRY(launch_mlp<16>(h, MODE_DEC, a)); break;
+            case 32: NPCG_TRY(launch_mlp<32>(h, MODE_DEC, a)); break;
+            default: NPCG_TRY(launch_mlp<64>(h, MODE_DEC, a)); break;
+        }
+    }
+    const int blocks = std::max(1, std::min(ceil_div(P->n, 256), h->num_sms * 8));
+    k_x0_scale<<<blocks, 256, 0, h->stream>>>(P->n, P->row_sys.p, S.sc.p, S.s.p, x0);
+    NPCG_CUDA(h, cudaGetLastError());
+    return NPCG_OK;
 }
 
 }  // namespace npcg

@@ -445,6 +445,29 @@ npcg_status gnn_bf16_check_flags(Handle* h, Pattern* P) {
     return NPCG_OK;
 }
 
+// initial-guess head on the final BF16 node features of the last forward
+// (the decoder's tensor-core MLP over node rows)
+npcg_status gnn_bf16_head_run(Handle* h, Pattern* P, const npcg_gnn_config* cfg, const float* w_head, float* out) {
+    GnnStore& S = P->gnn;
+    const size_t fv = (size_t)P->n * kH;
+    const __nv_bfloat16* V = reinterpret_cast<const __nv_bfloat16*>(S.bf.p) + (cfg->n_mp & 1) * fv;
+    NPCG_CUDA(h, cudaMemsetAsync(P->ctl.p + 1, 0, sizeof(int), h->stream));
+    Bf16Args a{};
+    a.rp = P->rp.p;
+    a.ci = P->ci.p;
+    a.erow = P->edge_row.p;
+    a.row_sys = P->row_sys.p;
+    a.sc = S.sc.p;
+    a.flags = P->ctl.p + 1;
+    a.nrows = P->n;
+    a.w = w_head;
+    a.depth = cfg->l;
+    a.ein = V;
+    a.sout = out;
+    NPCG_TRY(launch_bf16<MODE_DEC>(h, a));
+    return gnn_bf16_check_flags(h, P);
+}
+
 npcg_status gnn_forward_bf16_run(Handle* h, Pattern* P, const double* A_val, const double* b,
                                  const npcg_gnn_config* cfg, const float* w, double* L_val) {
     GnnStore& S = P->gnn;

@@ -17,14 +17,15 @@ enum MlpMode { MODE_ENC_NODE = 0, MODE_ENC_EDGE = 1, MODE_NODE = 2, MODE_EDGE = 
 // encoder, edge encoder, n_mp x (node MLP, edge MLP), decoder; every Linear
 // W[out][in] then bias[out].
 struct GnnOffsets {
-    int64_t enc_v, enc_e, node[kMaxMp], edge[kMaxMp], dec, total;
+    int64_t enc_v, enc_e, node[kMaxMp], edge[kMaxMp], dec, x0, total;
 };
 
 inline int64_t mlp_size(int in, int h, int out, int depth) {
     return (int64_t)in * h + h + (int64_t)(depth - 1) * (h * h + h) + (int64_t)h * out + out;
 }
 
-inline GnnOffsets gnn_offsets(int h, int l, int lm, int n_mp) {
+// x0_head: the initial-guess head (an MLP of depth l, h -> 1) after the decoder
+inline GnnOffsets gnn_offsets(int h, int l, int lm, int n_mp, int x0_head = 0) {
     GnnOffsets o{};
     int64_t p = 0;
     o.enc_v = p; p += mlp_size(1, h, h, l);
@@ -34,6 +35,8 @@ inline GnnOffsets gnn_offsets(int h, int l, int lm, int n_mp) {
         o.edge[t] = p; p += mlp_size(3 * h, h, h, lm);
     }
     o.dec = p; p += mlp_size(h, h, 1, l);
+    o.x0 = p;
+    if (x0_head) p += mlp_size(h, h, 1, l);
     o.total = p;
     return o;
 }
@@ -75,6 +78,9 @@ npcg_status gnn_bf16_forward_core(Handle* h, Pattern* P, const double* A_val, co
                                   const npcg_gnn_config* cfg, const float* w, double* sc, float* sout,
                                   float* const* tV, float* const* tE, float* const* tAGG);
 npcg_status gnn_bf16_check_flags(Handle* h, Pattern* P);
+npcg_status gnn_bf16_head_run(Handle* h, Pattern* P, const npcg_gnn_config* cfg, const float* w_head, float* out);
+npcg_status gnn_factor_x0_run(Handle* h, Pattern* P, const double* A_val, const double* b,
+                              const npcg_gnn_config* cfg, const float* w, double* L_val, double* x0);
 
 namespace {
 

@@ -121,13 +121,15 @@ struct CtaLayout {
     DevBuf<int32_t> sbuf, vsrc, is_diag, step_of_pos;
     DevBuf<double> vbuf;
     DevBuf<float> vbuf32;
-    // per value type ([0] FP64, [1] FP32): chunks, their per-system ranges,
-    // stage capacity in bytes and number of ring stages (0: does not fit)
-    DevBuf<CtaChunk> chunks[2];
-    DevBuf<int32_t> sys_chunk0[2];
-    int nchunks[2] = {0, 0};
-    int stage_cap[2] = {0, 0};
-    int nstages[2] = {0, 0};
+    // per kernel ([0] FP64 and [1] FP32 with a barrier per step, [2] FP32
+    // flag-synchronised): chunks, their per-system ranges, stage capacity in
+    // bytes and number of ring stages (0: does not fit)
+    DevBuf<CtaChunk> chunks[3];
+    DevBuf<int32_t> sys_chunk0[3];
+    int nchunks[3] = {0, 0, 0};
+    int stage_cap[3] = {0, 0, 0};
+    int nstages[3] = {0, 0, 0};
+    bool flag_ok = false;          // the window also covers the drift of the flag-synchronised kernel
 };
 
 enum TrsvMode : int { kTrsvAuto = 0, kTrsvSyncFree = 1, kTrsvCta = 2 };
@@ -158,7 +160,8 @@ struct Pattern {
     TriLayout fwd, bwd;            // L y = r and L^T z = y
     CtaLayout cfwd, cbwd;          // level-synchronous layouts
     int trsv_mode = kTrsvSyncFree; // chosen by the autotuner
-    float tune_ms[2] = {0.f, 0.f}; // measured fwd+bwd time per mode
+    float tune_ms[3] = {0.f, 0.f, 0.f}; // measured fwd+bwd time: sync-free, level barrier, level flags
+    bool cta_flag = false;         // level-ordered solves use the flag-synchronised FP32 kernel
     DevBuf<double> r_cf, y_cb, yglob;  // rhs in processing order, window backing
     DevBuf<double> yq;             // solution of a level-synchronous solve in processing order
     // reduction chunks
@@ -254,6 +257,7 @@ npcg_status spmv_run(Handle* h, Pattern* P, const double* A_val, const double* x
 npcg_status cta_layout_build(Handle* h, Pattern* P, bool upper, CtaLayout* C);
 npcg_status cta_link(Handle* h, Pattern* P);
 int cta_stages(const CtaLayout& C);
+void trsv_pick_tuned(Pattern* P);
 npcg_status cta_factor_load(Handle* h, CtaLayout* C, const double* L_val);
 npcg_status cta_gather(Handle* h, cudaStream_t s, const CtaLayout& C, int64_t n, const double* x, void* xp,
                        bool f32);

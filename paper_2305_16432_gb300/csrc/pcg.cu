@@ -590,7 +590,9 @@ void enqueue_iteration(Handle* h, cudaStream_t s, Pattern* P, const PcgArgs& a, 
 }
 
 npcg_status build_graph(Handle* h, Pattern* P, int precond) {
-    if (P->graph[precond] && P->graph_mode[precond] == P->trsv_mode) return NPCG_OK;
+    // the graph is specific to the triangular-solve design
+    const int mode_key = P->trsv_mode | (P->cta_flag ? 16 : 0);
+    if (P->graph[precond] && P->graph_mode[precond] == mode_key) return NPCG_OK;
     if (P->graph[precond]) { cudaGraphExecDestroy(P->graph[precond]); P->graph[precond] = nullptr; }
     PcgArgs a = pcg_args(P, precond);
     cudaGraph_t g = nullptr;
@@ -624,7 +626,7 @@ npcg_status build_graph(Handle* h, Pattern* P, int precond) {
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
     P->graph[precond] = ex;
-    P->graph_mode[precond] = P->trsv_mode;
+    P->graph_mode[precond] = mode_key;
     return NPCG_OK;
 }
 
@@ -730,9 +732,15 @@ npcg_status trsv_autotune(Handle* h, Pattern* P) {
     // all entries 1: a well-defined solve of the same structure (values do not
     // change the timing)
     NPCG_TRY(factor_load(h, P, L.p));
-    const int modes[2] = {kTrsvSyncFree, kTrsvCta};
-    for (int m = 0; m < 2; ++m) {
+    // sync-free, level order with a barrier per step, level order with
+    // per-slot flags (FP32 solves; when the window covers its drift)
+    const int modes[3] = {kTrsvSyncFree, kTrsvCta, kTrsvCta};
+    const bool flag_ok = P->cfwd.flag_ok && P->cbwd.flag_ok;
+    P->tune_ms[2] = 0.f;
+    for (int m = 0; m < 3; ++m) {
+        if (m == 2 && !flag_ok) break;
         P->trsv_mode = modes[m];
+        P->cta_flag = m == 2;
         double best = 1e30;
         for (int rep = 0; rep < 3; ++rep) {
             double f = 0.0, b = 0.0;
@@ -742,8 +750,17 @@ npcg_status trsv_autotune(Handle* h, Pattern* P) {
         }
         P->tune_ms[m] = (float)best;
     }
-    P->trsv_mode = P->tune_ms[1] < P->tune_ms[0] ? kTrsvCta : kTrsvSyncFree;
+    trsv_pick_tuned(P);
     return NPCG_OK;
+}
+
+// the fastest measured design (a zero time: the design does not apply)
+void trsv_pick_tuned(Pattern* P) {
+    int m = 0;
+    for (int k = 1; k < 3; ++k)
+        if (P->tune_ms[k] > 0.f && P->tune_ms[k] < P->tune_ms[m]) m = k;
+    P->trsv_mode = m == 0 ? kTrsvSyncFree : kTrsvCta;
+    P->cta_flag = m == 2;
 }
 
 npcg_status spmv_run(Handle* h, Pattern* P, const double* A_val, const double* x, double* y) {

@@ -869,6 +869,31 @@ __global__ void k_agg_bwd_nodes(int64_t n, int H, const int32_t* rp, const int32
     }
 }
 
+// regression of the initial-guess head: d_i = out_i - x_i s / ||b||_inf,
+// loss_sys += d_i^2, dout_i = c d_i (c = 2 / (pairs * systems))
+__global__ void k_x0_loss(int64_t n, const int32_t* row_sys, const double* sc, const double* x, const float* out,
+                          double c, float* dout, double* loss_sys) {
+    const unsigned full = 0xffffffffu;
+    for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x; i0 < n; i0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = i0 + threadIdx.x;
+        double d2 = 0.0;
+        int sys = -1;
+        if (i < n) {
+            sys = row_sys[i];
+            const double d = (double)out[i] - x[i] * sc[2 * sys] / sc[2 * sys + 1];
+            dout[i] = (float)(c * d);
+            d2 = d * d;
+        }
+        const int s0 = __shfl_sync(full, sys, 0);
+        if (__all_sync(full, sys == s0 || sys < 0)) {
+            for (int o = 16; o; o >>= 1) d2 += __shfl_xor_sync(full, d2, o);
+            if ((threadIdx.x & 31) == 0 && s0 >= 0) atomicAdd(&loss_sys[s0], d2);
+        } else if (sys >= 0) {
+            atomicAdd(&loss_sys[sys], d2);
+        }
+    }
+}
+
 __global__ void k_enc_inputs(int64_t n, int64_t nnz, const double* b, const double* av, const int32_t* erow,
                              const int32_t* row_sys, const double* sc, float* xv, float* xe) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nnz;
@@ -887,6 +912,7 @@ struct TrainBufs {
     double *Lv, *dL, *y, *r, *w, *loss_sys;
     int bf16;          // weight gradients on the tensor cores
     int* flags;        // device status word
+    float *xh, *dxh;   // initial-guess head: outputs and their adjoint [n]
 };
 
 inline int grid1(Handle* h, int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)h->num_sms * 8)); }
@@ -943,7 +969,7 @@ npcg_status train_pair(Handle* h, Pattern* P, const double* A_val, const double*
                        const npcg_gnn_config* cfg, const float* w, float* gw, TrainBufs& T, double c) {
     const int l = cfg->l, lm = cfg->l_mp, nmp = cfg->n_mp;
     const int64_t n = P->n, nnz = P->nnz, nnzL = P->nnzL;
-    const GnnOffsets off = gnn_offsets(H, l, lm, nmp);
+    const GnnOffsets off = gnn_offsets(H, l, lm, nmp, cfg->x0_head);
     double* sc = P->gnn.sc.p;
     // ---- forward with tape
     MlpArgs a = {};
@@ -1048,6 +1074,23 @@ npcg_status train_pair(Handle* h, Pattern* P, const double* A_val, const double*
         WSeg s0{T.xe, nullptr, 1};
         NPCG_TRY(mlp_wgrad(h, nnz, H, 1, H, l, T.dEc, T, &s0, 1, gw + off.enc_e));
     }
+    if (cfg->x0_head) {
+        // initial-guess head: regression to x on the final node features; the
+        // trunk is not differentiated through it (no input gradient)
+        MlpArgs ax = a;
+        ax.nrows = n; ax.w = w + off.x0; ax.depth = l; ax.ein = T.V[nmp]; ax.out = T.xh;
+        NPCG_TRY(launch_mlp<H>(h, MODE_DEC, ax));
+        k_x0_loss<<<grid1(h, n), 256, 0, h->stream>>>(n, P->row_sys.p, sc, x, T.xh, c, T.dxh, T.loss_sys);
+        NPCG_CUDA(h, cudaGetLastError());
+        MlpBwdArgs bx{};
+        for (int k = 0; k <= kMaxDepth; ++k) { bx.tapeA[k] = T.tapeA[k]; bx.tapeG[k] = T.tapeG[k]; }
+        bx.f = ax;
+        bx.gout = T.dxh;
+        bx.dx[0] = bx.dx[1] = bx.dx[2] = nullptr;
+        NPCG_TRY(run_bwd<H>(h, MODE_DEC, bx, nullptr, T));
+        WSeg s0{T.V[nmp], nullptr, H};
+        NPCG_TRY(mlp_wgrad(h, n, H, H, 1, l, T.dxh, T, &s0, 1, gw + off.x0));
+    }
     // tensor-core waits of this pair (the next pair's forward clears the word)
     if (T.bf16) NPCG_TRY(gnn_bf16_check_flags(h, P));
     return NPCG_OK;
@@ -1079,14 +1122,15 @@ npcg_status loss_grad_run(Handle* h, Pattern* P, const double* A_val, int npairs
     const int H = cfg->h, nmp = cfg->n_mp;
     const int64_t n = P->n, nnz = P->nnz, nnzL = P->nnzL;
     const int dmax = std::max(cfg->l, cfg->l_mp);
-    const GnnOffsets off = gnn_offsets(H, cfg->l, cfg->l_mp, nmp);
+    const GnnOffsets off = gnn_offsets(H, cfg->l, cfg->l_mp, nmp, cfg->x0_head);
     GnnStore& S = P->gnn;
     const size_t fe = (size_t)nnz * H, fv = (size_t)n * H;
     // tape: V_0..V_nmp, E_0..E_nmp, AGG_0..AGG_{nmp-1}; adjoint buffers
     // every buffer starts on a 256-byte boundary (vector loads of the tapes)
     auto al64 = [](size_t k) { return (k + 63) & ~size_t(63); };
     const size_t need = (size_t)(nmp + 1) * (al64(fe) + al64(fv)) + (size_t)std::max(nmp, 1) * al64(fv) +
-                        4 * al64(fe) + 5 * al64(fv) + 4 * al64(nnz) + (size_t)(2 * dmax + 2) * al64(std::max(fe, fv));
+                        4 * al64(fe) + 5 * al64(fv) + 4 * al64(nnz) + (size_t)(2 * dmax + 2) * al64(std::max(fe, fv)) +
+                        2 * al64((size_t)n);
     NPCG_CUDA(h, S.aux.ensure(need));
     NPCG_CUDA(h, S.sc.ensure((size_t)2 * P->nsys));
     NPCG_CUDA(h, S.Lv.ensure((size_t)nnzL));
@@ -1102,6 +1146,8 @@ npcg_status loss_grad_run(Handle* h, Pattern* P, const double* A_val, int npairs
     T.S = take(nnz); T.dS = take(nnz);
     for (int k = 0; k <= kMaxDepth; ++k) { T.tapeA[k] = nullptr; T.tapeG[k] = nullptr; }
     for (int k = 0; k <= dmax; ++k) { T.tapeA[k] = take(std::max(fe, fv)); T.tapeG[k] = take(std::max(fe, fv)); }
+    T.xh = take((size_t)n);
+    T.dxh = take((size_t)n);
     T.bf16 = cfg->precision == NPCG_BF16;
     T.flags = P->ctl.p + 1;
     T.Lv = S.Lv.p;

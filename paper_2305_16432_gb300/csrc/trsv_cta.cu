@@ -167,6 +167,58 @@ __device__ __forceinline__ double remote_dep(const double* pub, int row, int* fl
     return __longlong_as_double((long long)bits);
 }
 
+// Producer warp: streams the system's chunks through the ring of stages.
+// The 32 lanes fetch 32 chunk descriptors at a time; lane 0 issues the three
+// bulk copies of a chunk once every consumer warp has released the stage.
+// Copies still in flight complete before the warp leaves.
+template <class T>
+__device__ __forceinline__ void ring_producer(const CtaDev& D, const T* rhs, unsigned char* ring, uint64_t* full,
+                                              uint64_t* empty, int4* info, int c0, int c1, int* flags) {
+    const int S = D.stages, lane = threadIdx.x & 31;
+    int issued = 0;
+    bool ok = true;
+    for (int j0 = c0; j0 < c1 && ok; j0 += 32) {
+        CtaChunk cl{};
+        if (j0 + lane < c1) cl = D.chunks[j0 + lane];
+        const int cnt = min(32, c1 - j0);
+        for (int u = 0; u < cnt; ++u) {
+            const long long so = __shfl_sync(0xffffffffu, cl.soff, u);
+            const long long vo = __shfl_sync(0xffffffffu, cl.voff, u);
+            const int q0e = __shfl_sync(0xffffffffu, cl.q0e, u);
+            const int nst = __shfl_sync(0xffffffffu, cl.nsteps, u);
+            const unsigned sb = __shfl_sync(0xffffffffu, cl.sbytes, u);
+            const unsigned vb = __shfl_sync(0xffffffffu, cl.vbytes, u);
+            const unsigned rb = __shfl_sync(0xffffffffu, cl.rbytes, u);
+            const int j = j0 + u, k = j - c0, s = k % S;
+            if (lane == 0) {
+                if (k >= S) {
+                    ok = mbar_wait_bounded(&empty[s], (uint32_t)((k / S - 1) & 1));
+                    if (ok) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                }
+                if (ok) {
+                    unsigned char* base = ring + (size_t)s * D.stage_cap;
+                    // read by the consumers after the phase completes
+                    // (the arrive below releases this store)
+                    info[s] = make_int4(nst, (int)sb, (int)(sb + vb), q0e);
+                    mbar_expect_tx(&full[s], sb + vb + rb);
+                    bulk_g2s(base, D.sbuf + so, sb, &full[s]);
+                    bulk_g2s(base + sb, static_cast<const T*>(D.vbuf) + vo, vb, &full[s]);
+                    bulk_g2s(base + sb + vb, rhs + q0e, rb, &full[s]);
+                    ++issued;
+                }
+            }
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) break;
+        }
+    }
+    if (lane != 0) return;
+    if (!ok) atomicOr(flags, kFlagTimeout | kFlagAbort);
+    for (int j = max(c0, c0 + issued - S); j < c0 + issued; ++j) {
+        const int k = j - c0;
+        mbar_wait_bounded(&full[k % S], (uint32_t)((k / S) & 1));
+    }
+}
+
 // kRemote: blocked layout of one large system.  CTAs claim units (contiguous
 // row blocks) in dependency order from a ticket, so every unit a CTA polls
 // on is owned by a CTA that is already running; dependencies outside the
@@ -209,51 +261,7 @@ __global__ void __launch_bounds__(kCtaThreads, 1) k_trsv_cta(CtaDev D, const T* 
     __syncthreads();
 
     if (warp == kCtaRows / 32) {
-        // ---------------- producer warp: stream the chunks through the ring
-        // the 32 lanes fetch 32 chunk descriptors at a time; lane 0 issues
-        int issued = 0;
-        bool ok = true;
-        for (int j0 = c0; j0 < c1 && ok; j0 += 32) {
-            CtaChunk cl{};
-            if (j0 + lane < c1) cl = D.chunks[j0 + lane];
-            const int cnt = min(32, c1 - j0);
-            for (int u = 0; u < cnt; ++u) {
-                const long long so = __shfl_sync(0xffffffffu, cl.soff, u);
-                const long long vo = __shfl_sync(0xffffffffu, cl.voff, u);
-                const int q0e = __shfl_sync(0xffffffffu, cl.q0e, u);
-                const int nst = __shfl_sync(0xffffffffu, cl.nsteps, u);
-                const unsigned sb = __shfl_sync(0xffffffffu, cl.sbytes, u);
-                const unsigned vb = __shfl_sync(0xffffffffu, cl.vbytes, u);
-                const unsigned rb = __shfl_sync(0xffffffffu, cl.rbytes, u);
-                const int j = j0 + u, k = j - c0, s = k % S;
-                if (lane == 0) {
-                    if (k >= S) {
-                        ok = mbar_wait_bounded(&empty[s], (uint32_t)((k / S - 1) & 1));
-                        if (ok) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    }
-                    if (ok) {
-                        unsigned char* base = ring + (size_t)s * D.stage_cap;
-                        // read by the consumers after the phase completes
-                        // (the arrive below releases this store)
-                        info[s] = make_int4(nst, (int)sb, (int)(sb + vb), q0e);
-                        mbar_expect_tx(&full[s], sb + vb + rb);
-                        bulk_g2s(base, D.sbuf + so, sb, &full[s]);
-                        bulk_g2s(base + sb, static_cast<const T*>(D.vbuf) + vo, vb, &full[s]);
-                        bulk_g2s(base + sb + vb, rhs + q0e, rb, &full[s]);
-                        ++issued;
-                    }
-                }
-                ok = __shfl_sync(0xffffffffu, ok, 0);
-                if (!ok) break;
-            }
-        }
-        if (lane != 0) return;
-        if (!ok) atomicOr(flags, kFlagTimeout | kFlagAbort);
-        // copies still in flight complete before this warp (and the CTA) leaves
-        for (int j = max(c0, c0 + issued - S); j < c0 + issued; ++j) {
-            const int k = j - c0;
-            mbar_wait_bounded(&full[k % S], (uint32_t)((k / S) & 1));
-        }
+        ring_producer<T>(D, rhs, ring, full, empty, info, c0, c1, flags);
         return;
     }
 
@@ -380,6 +388,229 @@ __global__ void __launch_bounds__(kCtaThreads, 1) k_trsv_cta(CtaDev D, const T* 
         s = ns;
         u = nu;
         nst = nnst;
+    }
+}
+
+// ------------------------------------------------------------ flag-synchronised variant
+// FP32 only.  The same layout and ring, without the barrier per step: every
+// window slot is one 64-bit word {position, value} written with a single
+// store, and a consumer polls its dependencies' slots until each holds the
+// position it expects (slot and position agree modulo the window).  The
+// ring, released per warp, lets a warp run at most (stages - 1) chunks
+// ahead of the slowest; the window is sized to that drift plus the
+// dependency reach, so a slot is never rewritten while a reader still needs
+// it.  The dependency chain is then one shared-memory store and load per
+// level instead of a CTA barrier.
+__device__ __forceinline__ unsigned long long ld_slot(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.cta.shared.b64 %0, [%1];" : "=l"(v) : "r"(smem_u32(p)));
+    return v;
+}
+__device__ __forceinline__ void st_slot(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.relaxed.cta.shared.b64 [%0], %1;" ::"r"(smem_u32(p)), "l"(v));
+}
+__device__ __forceinline__ unsigned long long slot_word(int pos, float y) {
+    return ((unsigned long long)(unsigned)pos << 32) | (unsigned long long)__float_as_uint(y);
+}
+__device__ __forceinline__ int slot_pos(unsigned long long w) { return (int)(w >> 32); }
+__device__ __forceinline__ float slot_val(unsigned long long w) { return __uint_as_float((unsigned)w); }
+
+// position held by dependency slot sl of the row at position q (the zero
+// slot W stands for a missing dependency and carries position -1)
+__device__ __forceinline__ int dep_pos(int q, int sl, int W) { return sl == W ? -1 : q - ((q - sl) & (W - 1)); }
+
+__global__ void __launch_bounds__(kCtaThreads, 1) k_trsv_flag(CtaDev D, const float* __restrict__ rhs,
+                                                             float* outq, const SysState* st, int* flags) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int sys = blockIdx.x;
+    if (st && !st[sys].active) return;
+    const int c0 = D.sys_chunk0[sys], c1 = D.sys_chunk0[sys + 1];
+    if (c0 >= c1) return;
+    const int S = D.stages;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem);
+    uint64_t* empty = full + kMaxStages;
+    int4* info = reinterpret_cast<int4*>(empty + kMaxStages);
+    unsigned long long* win = reinterpret_cast<unsigned long long*>(smem + kBarBytes);
+    const int W = D.win;
+    unsigned char* ring = smem + kBarBytes + (size_t)(W + kWinPad) * sizeof(unsigned long long);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kCtaRows / 32);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // no slot holds a position yet; the zero slot (and the padding) holds
+    // position -1 with value 0
+    for (int i = threadIdx.x; i < W + kWinPad; i += blockDim.x) win[i] = slot_word(i >= W ? -1 : -2, 0.0f);
+    __syncthreads();
+
+    if (warp == kCtaRows / 32) {
+        ring_producer<float>(D, rhs, ring, full, empty, info, c0, c1, flags);
+        return;
+    }
+
+    // ---------------- consumer warps
+    // Steps rotate over the warps: a step of nrows rows takes ceil(nrows/32)
+    // consecutive warps (mod 8), starting where the previous step's ended,
+    // so consecutive levels run on different warps and a warp's bookkeeping
+    // for its next step overlaps the other warps' work on the levels before.
+    // Each warp walks every step header (a "walker"), takes part in the
+    // steps that reach it, and loads the operands of its next step before it
+    // computes the current one.  It releases a chunk once it holds no step
+    // of it any more; the walker enters a new chunk only when the ring can
+    // hold it without this warp's own release (else it resumes after the
+    // current step is done).
+    const unsigned kAll = 0xffffffffu;
+    int wc = c0, wu = 0, wnst, wq0e, wrb = 0;
+    const int32_t* whdr;
+    const float* wvals;
+    const float* wrh;
+    int4 wh;
+    {
+        const bool ok = mbar_wait_bounded(&full[0], 0u);
+        if (!__all_sync(kAll, ok)) {
+            if (lane == 0) atomicOr(flags, kFlagTimeout | kFlagAbort);
+            return;
+        }
+        const int4 inf = info[0];
+        wnst = inf.x;
+        whdr = reinterpret_cast<const int32_t*>(ring);
+        wvals = reinterpret_cast<const float*>(ring + inf.y);
+        wrh = reinterpret_cast<const float*>(ring + inf.z);
+        wq0e = inf.w;
+        wh = *reinterpret_cast<const int4*>(whdr);
+    }
+    bool wdone = false, wexam = false, dead = false;
+    int rel = c0;                         // chunks below rel are released by this warp
+    StepOps<float> cur, nxt;
+    bool have_cur = false;
+    int cur_c = c0, cur_e = 0, nxt_c = c0, nxt_e = 0;
+    const int32_t* cur_hdr = whdr;
+    const float* cur_vals = wvals;
+    const int32_t* nxt_hdr = whdr;
+    const float* nxt_vals = wvals;
+    for (;;) {
+        const bool live = have_cur && cur_e < cur.nrows;
+        const int q = cur.q0 + cur_e;
+        int e0 = 0, e1 = 0, e2 = 0, e3 = 0;
+        unsigned long long w0 = 0, w1 = 0, w2 = 0, w3 = 0;
+        if (live) {
+            // first poll of the current row's dependencies, before the walk
+            e0 = dep_pos(q, cur.dep.x, W);
+            e1 = dep_pos(q, cur.dep.y, W);
+            e2 = dep_pos(q, cur.dep.z, W);
+            e3 = dep_pos(q, cur.dep.w, W);
+            w0 = ld_slot(win + cur.dep.x);
+            w1 = ld_slot(win + cur.dep.y);
+            w2 = ld_slot(win + cur.dep.z);
+            w3 = ld_slot(win + cur.dep.w);
+        }
+        // ---- walk to the next step this warp takes part in
+        bool have_nxt = false;
+        while (!wdone) {
+            const int nw = (wh.y + 31) >> 5;
+            if (!wexam) {
+                wexam = true;
+                const int slot = (warp - wrb) & 7;
+                if (slot < nw) {
+                    nxt_e = slot * 32 + lane;
+                    load_step<false>(nxt, whdr, wvals, wrh, wq0e, nxt_e);
+                    nxt_c = wc;
+                    nxt_hdr = whdr;
+                    nxt_vals = wvals;
+                    have_nxt = true;
+                }
+            }
+            // advance past the examined step
+            if (wu + 1 < wnst) {
+                const int np = pad4(wh.y);
+                whdr += s_ints(np, wh.z);
+                wvals += v_elems(np, wh.z);
+                ++wu;
+            } else if (wc + 1 >= c1) {
+                wdone = true;
+                break;
+            } else {
+                // the stage of chunk wc + 1 is refilled only after every warp
+                // released chunk wc + 1 - S
+                if (wc + 1 - S >= rel) break;
+                ++wc;
+                const int ws = (wc - c0) % S;
+                const bool ok = mbar_wait_bounded(&full[ws], (uint32_t)(((wc - c0) / S) & 1));
+                if (!__all_sync(kAll, ok)) {
+                    if (lane == 0) atomicOr(flags, kFlagTimeout | kFlagAbort);
+                    return;
+                }
+                const int4 inf = info[ws];
+                const unsigned char* base = ring + (size_t)ws * D.stage_cap;
+                wnst = inf.x;
+                whdr = reinterpret_cast<const int32_t*>(base);
+                wvals = reinterpret_cast<const float*>(base + inf.y);
+                wrh = reinterpret_cast<const float*>(base + inf.z);
+                wq0e = inf.w;
+                wu = 0;
+            }
+            wrb = (wrb + nw) & 7;
+            wh = *reinterpret_cast<const int4*>(whdr);
+            wexam = false;
+            if (have_nxt) break;
+        }
+        // ---- the current row
+        if (live) {
+            long long spins = 0;
+            while (!dead && (slot_pos(w0) != e0 || slot_pos(w1) != e1 || slot_pos(w2) != e2 || slot_pos(w3) != e3)) {
+                if (slot_pos(w0) != e0) w0 = ld_slot(win + cur.dep.x);
+                if (slot_pos(w1) != e1) w1 = ld_slot(win + cur.dep.y);
+                if (slot_pos(w2) != e2) w2 = ld_slot(win + cur.dep.z);
+                if (slot_pos(w3) != e3) w3 = ld_slot(win + cur.dep.w);
+                if ((++spins & 255) == 0) {
+                    if (ld_relaxed_s32(flags) & kFlagAbort) dead = true;
+                    else if (spins > kSpinLimit) { atomicOr(flags, kFlagTimeout | kFlagAbort); dead = true; }
+                }
+            }
+            float acc = cur.rhs;
+            acc = fmaf(-cur.l[0], slot_val(w0), acc);
+            acc = fmaf(-cur.l[1], slot_val(w1), acc);
+            acc = fmaf(-cur.l[2], slot_val(w2), acc);
+            acc = fmaf(-cur.l[3], slot_val(w3), acc);
+            if (cur.width > kRec) {
+                const int32_t* xdep = cur_hdr + kHdrInts + 6 * cur.np;
+                const float* xval = cur_vals + 5 * cur.np;
+                for (int kk = 0; kk < cur.width - kRec; ++kk) {
+                    const int sl = xdep[kk * cur.np + cur_e];
+                    const int e = dep_pos(q, sl, W);
+                    unsigned long long wx = ld_slot(win + sl);
+                    while (!dead && slot_pos(wx) != e) {
+                        wx = ld_slot(win + sl);
+                        if ((++spins & 255) == 0) {
+                            if (ld_relaxed_s32(flags) & kFlagAbort) dead = true;
+                            else if (spins > kSpinLimit) { atomicOr(flags, kFlagTimeout | kFlagAbort); dead = true; }
+                        }
+                    }
+                    acc = fmaf(-xval[kk * cur.np + cur_e], slot_val(wx), acc);
+                }
+            }
+            const float y = acc * cur.dinv;
+            st_slot(win + (q & (W - 1)), slot_word(q, y));
+            outq[q] = y;
+        }
+        __syncwarp();
+        // release the chunks this warp no longer reads: below the walker's
+        // chunk and below its next step's chunk
+        int lim = wdone ? c1 : wc;
+        if (have_nxt) lim = min(lim, nxt_c);
+        for (; rel < lim; ++rel)
+            if (lane == 0) mbar_arrive(&empty[(rel - c0) % S]);
+        if (__any_sync(kAll, dead)) return;
+        if (!have_nxt && wdone) break;
+        have_cur = have_nxt;
+        cur = nxt;
+        cur_c = nxt_c;
+        cur_e = nxt_e;
+        cur_hdr = nxt_hdr;
+        cur_vals = nxt_vals;
     }
 }
 
@@ -546,6 +777,11 @@ size_t win_bytes(const CtaLayout& C, bool f32) {
 
 size_t smem_bytes(const CtaLayout& C, bool f32) {
     return kBarBytes + win_bytes(C, f32) + (size_t)C.stage_cap[f32] * C.nstages[f32];
+}
+
+size_t smem_bytes_flag(const CtaLayout& C) {
+    return kBarBytes + (size_t)(C.win_slots + kWinPad) * sizeof(unsigned long long) +
+           (size_t)C.stage_cap[2] * C.nstages[2];
 }
 
 // shared memory per CTA: everything when each system has an SM of its own,
@@ -728,6 +964,61 @@ npcg_status cta_layout_build(Handle* h, Pattern* P, bool upper, CtaLayout* C) {
     C->win_slots = kWinMin;
     if (C->window_ok)
         while ((unsigned long long)C->win_slots < rh) C->win_slots *= 2;
+    const size_t budget = nunits > h->num_sms ? kSmemHalf : kSmemMax;
+    // largest single step (structure + values + right-hand side) for value size vsz
+    auto single_bytes = [&](size_t vsz) {
+        const int al = (int)(16 / vsz);
+        size_t single = 0;
+        for (int i = 0; i < nsteps; ++i) {
+            const int np = pad4(steps[i].y);
+            const int q0e = steps[i].x & ~(al - 1);
+            const size_t rb = (size_t)(((steps[i].x + steps[i].y - q0e) + al - 1) & ~(al - 1)) * vsz;
+            single = std::max(single, (size_t)s_ints(np, steps[i].z) * 4 + (size_t)v_elems(np, steps[i].z) * vsz + rb);
+        }
+        return single;
+    };
+    // Flag-synchronised kernel: the smallest window, up to kWinMax, that
+    // holds the dependency reach plus the positions of the ring's stages
+    // (how far one consumer warp can run ahead of another); its chunks are
+    // kernel [2].  The barrier kernels share that window size.
+    std::vector<CtaChunk> fch;
+    std::vector<int32_t> fsc0;
+    size_t fcap = 0;
+    int fstages = 0;
+    C->flag_ok = false;
+    if (C->window_ok && !C->blocked) {
+        const size_t single = single_bytes(4);
+        for (int W = C->win_slots; W <= kWinMax; W *= 2) {
+            const size_t wb = (size_t)(W + kWinPad) * sizeof(unsigned long long);
+            if (budget <= kBarBytes + wb) break;
+            const size_t avail = budget - kBarBytes - wb;
+            size_t cap = std::max(single, avail / kMaxStages);
+            cap = (cap + 127) & ~size_t(127);
+            const int stages = (int)std::min<size_t>(kMaxStages, avail / cap);
+            if (stages < 2 || !build_chunks(steps, soff, voff, sys_step0, nunits, 4, cap, fch, fsc0)) break;
+            // positions spanned by any `stages` consecutive chunks of a unit
+            int64_t drift = 0;
+            for (int un = 0; un < nunits; ++un) {
+                std::vector<int64_t> cs, ce;
+                int i = sys_step0[un];
+                for (int j = fsc0[un]; j < fsc0[un + 1]; ++j) {
+                    const int last = i + fch[j].nsteps - 1;
+                    cs.push_back(steps[i].x);
+                    ce.push_back((int64_t)steps[last].x + steps[last].y);
+                    i = last + 1;
+                }
+                for (size_t k = 0; k < cs.size(); ++k)
+                    drift = std::max(drift, ce[std::min(cs.size() - 1, k + stages - 1)] - cs[k]);
+            }
+            if ((int64_t)rh + drift + kCtaRows <= (int64_t)W) {
+                C->win_slots = W;
+                C->flag_ok = true;
+                fcap = cap;
+                fstages = stages;
+                break;
+            }
+        }
+    }
     if (C->window_ok) {
         k_cta_window<<<blocks, 256, 0, h->stream>>>(n, C->step_of_pos.p, C->steps.p, C->soff.p, C->win_slots,
                                                     C->sbuf.p);
@@ -737,15 +1028,7 @@ npcg_status cta_layout_build(Handle* h, Pattern* P, bool upper, CtaLayout* C) {
     // single step and an even split of the free shared memory into kMaxStages
     for (int f32 = 0; f32 < 2; ++f32) {
         const size_t vsz = f32 ? 4 : 8;
-        const int al = (int)(16 / vsz);
-        size_t single = 0;
-        for (int i = 0; i < nsteps; ++i) {
-            const int np = pad4(steps[i].y);
-            const int q0e = steps[i].x & ~(al - 1);
-            const size_t rb = (size_t)(((steps[i].x + steps[i].y - q0e) + al - 1) & ~(al - 1)) * vsz;
-            single = std::max(single, (size_t)s_ints(np, steps[i].z) * 4 + (size_t)v_elems(np, steps[i].z) * vsz + rb);
-        }
-        const size_t budget = nunits > h->num_sms ? kSmemHalf : kSmemMax;
+        const size_t single = single_bytes(vsz);
         const size_t avail = budget - kBarBytes - win_bytes(*C, f32 != 0);
         size_t cap = std::max(single, avail / kMaxStages);
         cap = (cap + 127) & ~size_t(127);
@@ -766,8 +1049,23 @@ npcg_status cta_layout_build(Handle* h, Pattern* P, bool upper, CtaLayout* C) {
                                      cudaMemcpyHostToDevice, h->stream));
         NPCG_CUDA(h, cudaStreamSynchronize(h->stream));
     }
+    C->nstages[2] = 0;
+    C->nchunks[2] = 0;
+    if (C->flag_ok) {
+        C->stage_cap[2] = (int)fcap;
+        C->nstages[2] = fstages;
+        C->nchunks[2] = (int)fch.size();
+        NPCG_CUDA(h, C->chunks[2].alloc(std::max<size_t>(fch.size(), 1)));
+        NPCG_CUDA(h, C->sys_chunk0[2].alloc(nunits + 1));
+        NPCG_CUDA(h, cudaMemcpyAsync(C->chunks[2].p, fch.data(), fch.size() * sizeof(CtaChunk),
+                                     cudaMemcpyHostToDevice, h->stream));
+        NPCG_CUDA(h, cudaMemcpyAsync(C->sys_chunk0[2].p, fsc0.data(), (nunits + 1) * sizeof(int32_t),
+                                     cudaMemcpyHostToDevice, h->stream));
+        NPCG_CUDA(h, cudaStreamSynchronize(h->stream));
+    }
     // the launch size never exceeds 220 KB; set once here, outside any capture
     const int mx = 220 * 1024;
+    NPCG_CUDA(h, cudaFuncSetAttribute(k_trsv_flag, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
     NPCG_CUDA(h, cudaFuncSetAttribute(k_trsv_cta<true, false, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
     NPCG_CUDA(h, cudaFuncSetAttribute(k_trsv_cta<false, false, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
     NPCG_CUDA(h, cudaFuncSetAttribute(k_trsv_cta<true, false, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
@@ -848,6 +1146,20 @@ npcg_status cta_gather(Handle* h, cudaStream_t s, const CtaLayout& C, int64_t n,
 // moves it on.  f32: FP32 factor, arithmetic, right-hand side and outq.
 npcg_status cta_trsv_launch(Handle* h, cudaStream_t s, Pattern* P, const CtaLayout& C, const void* rhs_v,
                             void* outq, const SysState* st, bool f32, int* ticket, double* pub) {
+    if (f32 && P->cta_flag && C.flag_ok && C.nstages[2] >= 2) {
+        CtaDev d;
+        d.sys_chunk0 = C.sys_chunk0[2].p;
+        d.chunks = C.chunks[2].p;
+        d.sbuf = C.sbuf.p;
+        d.vbuf = C.vbuf32.p;
+        d.stages = C.nstages[2];
+        d.stage_cap = C.stage_cap[2];
+        d.win = C.win_slots;
+        k_trsv_flag<<<C.nunits, kCtaThreads, smem_bytes_flag(C), s>>>(d, static_cast<const float*>(rhs_v),
+                                                                      static_cast<float*>(outq), st, P->ctl.p + 1);
+        NPCG_CUDA(h, cudaGetLastError());
+        return NPCG_OK;
+    }
     const int stages = C.nstages[f32];
     if (stages < 2) return set_error(h, NPCG_EINVAL, "level-synchronous layout does not fit shared memory");
     if (C.blocked && (!ticket || !pub)) return set_error(h, NPCG_EINVAL, "blocked solve needs a ticket and pub");

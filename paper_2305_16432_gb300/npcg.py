@@ -25,7 +25,7 @@ FD, FEM = 0, 1
 FP32, BF16 = 0, 1
 PREC_NONE, PREC_JACOBI, PREC_LLT, PREC_LLT32 = 0, 1, 2, 3
 METHOD_GNN, METHOD_IC0, METHOD_JACOBI, METHOD_CG = 0, 1, 2, 3
-TRSV_AUTO, TRSV_SYNCFREE, TRSV_LEVELSYNC = 0, 1, 2
+TRSV_AUTO, TRSV_SYNCFREE, TRSV_LEVELSYNC, TRSV_LEVELFLAG = 0, 1, 2, 3
 
 
 class NpcgError(RuntimeError):
@@ -43,12 +43,13 @@ class _Problem(C.Structure):
 class _Info(C.Structure):
     _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("nnz_L", C.c_int64), ("nsys", C.c_int32),
                 ("nlev_fwd", C.c_int32), ("nlev_bwd", C.c_int32), ("trsv_mode", C.c_int32),
-                ("tuned_ms_syncfree", C.c_float), ("tuned_ms_levelsync", C.c_float)]
+                ("tuned_ms_syncfree", C.c_float), ("tuned_ms_levelsync", C.c_float),
+                ("tuned_ms_levelflag", C.c_float)]
 
 
 class _Cfg(C.Structure):
     _fields_ = [("n_mp", C.c_int32), ("l", C.c_int32), ("l_mp", C.c_int32), ("h", C.c_int32),
-                ("diag_mode", C.c_int32), ("precision", C.c_int32)]
+                ("diag_mode", C.c_int32), ("precision", C.c_int32), ("x0_head", C.c_int32)]
 
 
 class _Stats(C.Structure):
@@ -80,6 +81,7 @@ def lib():
                 "npcg_pattern_export": [vp, vp, vp, vp, vp, vp, vp, vp],
                 "npcg_gnn_nparams": [C.POINTER(_Cfg), C.POINTER(i64)],
                 "npcg_gnn_factor": [vp, vp, vp, vp, C.POINTER(_Cfg), vp, vp],
+                "npcg_gnn_factor_x0": [vp, vp, vp, vp, C.POINTER(_Cfg), vp, vp, vp],
                 "npcg_ic0_factor": [vp, vp, vp, vp, vp],
                 "npcg_pcg_solve": [vp, vp, vp, vp, vp, i32, vp, dbl, i32, vp],
                 "npcg_pcg_solve_batched": [vp, vp, vp, vp, vp, i32, vp, dbl, i32, vp],
@@ -203,12 +205,13 @@ class Pattern:
         self.n, self.nnz, self.nnz_L = info.n, info.nnz, info.nnz_L
         self.nsys, self.nlev_fwd, self.nlev_bwd = info.nsys, info.nlev_fwd, info.nlev_bwd
         self.trsv_mode = info.trsv_mode
-        self.tuned_ms = {"syncfree": info.tuned_ms_syncfree, "levelsync": info.tuned_ms_levelsync}
+        self.tuned_ms = {"syncfree": info.tuned_ms_syncfree, "levelsync": info.tuned_ms_levelsync,
+                         "levelflag": info.tuned_ms_levelflag}
         self.sys_ptr = np.asarray(sys_ptr if sys_ptr is not None else [0, n], dtype=np.int64)
 
     def set_trsv(self, mode):
-        """Force a triangular-solve design (TRSV_SYNCFREE / TRSV_LEVELSYNC) or
-        restore the tuned one (TRSV_AUTO)."""
+        """Force a triangular-solve design (TRSV_SYNCFREE / TRSV_LEVELSYNC /
+        TRSV_LEVELFLAG) or restore the tuned one (TRSV_AUTO)."""
         self.h.check(lib().npcg_pattern_set_trsv(self.p, int(mode)))
         info = _Info()
         lib().npcg_pattern_get_info(self.p, C.byref(info))
@@ -245,7 +248,7 @@ def analyse(row_ptr, col_idx, sys_ptr=None, h: Handle | None = None) -> Pattern:
 
 # ------------------------------------------------------------------ factors
 def _cfg(cfg: I.GnnConfig, precision=FP32):
-    return _Cfg(cfg.n_mp, cfg.l, cfg.l_mp, cfg.h, cfg.diag_mode, precision)
+    return _Cfg(cfg.n_mp, cfg.l, cfg.l_mp, cfg.h, cfg.diag_mode, precision, int(getattr(cfg, "x0_head", 0)))
 
 
 def gnn_nparams(cfg: I.GnnConfig) -> int:
@@ -266,6 +269,20 @@ def gnn_factor(P: Pattern, A_val, b, cfg: I.GnnConfig, weights, precision=FP32, 
     c = _cfg(cfg, precision)
     P.h.check(lib().npcg_gnn_factor(P.h.h, P.p, _ptr(A_val), _ptr(b), C.byref(c), _ptr(weights), _ptr(L)))
     return L
+
+
+def gnn_factor_x0(P: Pattern, A_val, b, cfg: I.GnnConfig, weights, precision=FP32):
+    """(L, x0): the factor and the initial-guess head's x0 [n] from one pass
+    (cfg.x0_head must be 1)."""
+    A_val = _dev(A_val, torch.float64, "A_val")
+    b = _dev(b, torch.float64, "b")
+    weights = _dev(weights, torch.float32, "weights")
+    L = torch.empty(P.nnz_L, dtype=torch.float64, device=A_val.device)
+    x0 = torch.empty(P.n, dtype=torch.float64, device=A_val.device)
+    c = _cfg(cfg, precision)
+    P.h.check(lib().npcg_gnn_factor_x0(P.h.h, P.p, _ptr(A_val), _ptr(b), C.byref(c), _ptr(weights), _ptr(L),
+                                       _ptr(x0)))
+    return L, x0
 
 
 def ic0_factor(P: Pattern, A_val, out=None):

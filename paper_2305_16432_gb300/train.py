@@ -24,6 +24,7 @@ committed network uses the App. A.3 factorisation L D L^T with D = diag(A):
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import sys
@@ -82,8 +83,15 @@ def evaluate(N, cfg, w, probs, rtol=1e-6, seed=77, precision=None):
         Li, _ = N.ic0_factor(P, v)
         _, si = N.pcg_solve(P, v, b, N.PREC_LLT, Li, rtol=rtol)
         _, sj = N.pcg_solve(P, v, b, N.PREC_JACOBI, None, rtol=rtol)
-        out.append({"n": P.n, "learned": sl[0]["iters"], "ic0": si[0]["iters"], "jacobi": sj[0]["iters"],
-                    "learned_status": sl[0]["status"]})
+        rec = {"n": P.n, "learned": sl[0]["iters"], "ic0": si[0]["iters"], "jacobi": sj[0]["iters"],
+               "learned_status": sl[0]["status"]}
+        if cfg.x0_head:
+            # the same factor, PCG started from the head's initial guess
+            L2, x0 = N.gnn_factor_x0(P, v, b, cfg, w, precision=N.FP32 if precision is None else precision)
+            _, sx = N.pcg_solve(P, v, b, N.PREC_LLT, L2, rtol=rtol, max_iter=VAL_MAX_ITER, x0=x0)
+            rec["learned_x0"] = sx[0]["iters"]
+            rec["x0_relres"] = float(torch.linalg.norm(b - N.spmv(P, v, x0)) / torch.linalg.norm(b))
+        out.append(rec)
     return out
 
 
@@ -95,13 +103,15 @@ def save_checkpoint(path, cfg, w, mom, vel, step, hist):
 
 def train(cfg: I.GnnConfig, steps=600, groups=4, per_group=8, pairs=8, m=128, lr=1e-3, lr_final=1e-4,
           seed=2023, log_every=25, w0=None, ckpt=None, resume=None, val_every=50, precision=None, sizes=None,
-          sizes3d=None, sigma3d=1.0, corr3d=0.1):
+          sizes3d=None, sigma3d=1.0, corr3d=0.1, head_only=False):
     """Adam at lr (App. A.4), cosine-decayed to lr_final over the run; returns
     the weights with the fewest validation PCG iterations.  precision: the
     network forward's arithmetic (FP32, or BF16 tensor cores with the FP32
     adjoint); sizes: lattice size of each 2-D FEM group (default m for
     all, [] for none); sizes3d: grid side of each 3-D FD group (none by
-    default), with log k a GRF of sigma3d and correlation length corr3d."""
+    default), with log k a GRF of sigma3d and correlation length corr3d.
+    head_only: train the initial-guess head alone (the trunk's gradient is
+    zeroed, so Adam leaves it unchanged) and validate PCG started from x0."""
     from . import build as B
     B.build()
     from . import npcg as N
@@ -144,13 +154,18 @@ def train(cfg: I.GnnConfig, steps=600, groups=4, per_group=8, pairs=8, m=128, lr
         Pv = N.analyse(rp, ci)
         vals.append((Pv, v, torch.as_tensor(I.rhs(Pv.n, 8000 + k), device="cuda")))
 
+    n_trunk = N.gnn_nparams(dataclasses.replace(cfg, x0_head=0))
+
     def val_iters():
         its = []
         for Pv, v, bv in vals:
             # the deployed configuration: FP32 triangular solves with a BF16 network
-            L = N.gnn_factor(Pv, v, bv, cfg, w, precision=prec)
+            if cfg.x0_head:
+                L, x0 = N.gnn_factor_x0(Pv, v, bv, cfg, w, precision=prec)
+            else:
+                L, x0 = N.gnn_factor(Pv, v, bv, cfg, w, precision=prec), None
             _, st = N.pcg_solve(Pv, v, bv, N.PREC_LLT32 if prec == N.BF16 else N.PREC_LLT, L, rtol=1e-6,
-                                max_iter=VAL_MAX_ITER)
+                                max_iter=VAL_MAX_ITER, x0=x0)
             its.append(st[0]["iters"] if st[0]["status"] == 0 else 2 * VAL_MAX_ITER)
         return float(np.mean(its))
 
@@ -162,6 +177,8 @@ def train(cfg: I.GnnConfig, steps=600, groups=4, per_group=8, pairs=8, m=128, lr
         q = ((t - 1) // groups) % (pairs // 2)
         loss, g = N.loss_and_grad(P, A, X[2 * q:2 * q + 2].contiguous(), Bb[2 * q:2 * q + 2].contiguous(), cfg, w,
                                   precision=prec)
+        if head_only:
+            g[:n_trunk] = 0
         lr_t = lr_final + 0.5 * (lr - lr_final) * (1.0 + np.cos(np.pi * (t - 1) / max(1, steps - 1)))
         N.adam_step(w, g, mom, vel, t, lr=float(lr_t))
         hist.append(loss)
@@ -198,18 +215,29 @@ def main():
     ap.add_argument("--sizes3d", default="", help="comma-separated grid sides of the 3-D FD training groups")
     ap.add_argument("--sigma3d", type=float, default=1.0, help="GRF sigma of the 3-D groups")
     ap.add_argument("--corr3d", type=float, default=0.1, help="GRF correlation length of the 3-D groups")
+    ap.add_argument("--x0_from", default=None,
+                    help="weights of a trained network: add the initial-guess head and train it alone")
     ap.add_argument("--out", default=os.path.join(os.path.dirname(__file__), "weights", "gnn_6x64.npy"))
     args = ap.parse_args()
     cfg = I.GnnConfig(n_mp=args.n_mp, l=2, l_mp=2, h=args.h, diag_mode=args.diag_mode)
     from . import build as B
     B.build()
     from . import npcg as N
+    w_init = None
+    if args.x0_from:
+        # trained trunk + a freshly initialised head (the tail of the flat layout)
+        trunk = np.load(args.x0_from).astype(np.float32)
+        cfg = dataclasses.replace(cfg, x0_head=1)
+        w_init = I.gnn_weights(cfg, 2023)
+        assert trunk.size == N.gnn_nparams(dataclasses.replace(cfg, x0_head=0)), "trunk of another network"
+        w_init[:trunk.size] = trunk
     prec = N.BF16 if args.precision == "bf16" else N.FP32
     sizes = [] if args.sizes == "none" else ([int(x) for x in args.sizes.split(",") if x] or None)
     sizes3d = [int(x) for x in args.sizes3d.split(",") if x] or None
     w, hist, tm = train(cfg, steps=args.steps, m=args.m, lr=args.lr, lr_final=args.lr_final, ckpt=args.ckpt,
                         resume=args.resume, val_every=args.val_every, precision=prec, sizes=sizes,
-                        sizes3d=sizes3d, sigma3d=args.sigma3d, corr3d=args.corr3d)
+                        sizes3d=sizes3d, sigma3d=args.sigma3d, corr3d=args.corr3d, w0=w_init,
+                        head_only=bool(args.x0_from))
     w0 = torch.as_tensor(I.gnn_weights(cfg, 2023), device="cuda")
     held = [I.fem2d(args.m, sigma=1.0, corr_len=0.1, seed=9000 + k) for k in range(3)]
     ev = evaluate(N, cfg, w, held, precision=prec)
@@ -220,14 +248,15 @@ def main():
                                I.fd3d(64, sigma=1.5, corr_len=0.05, seed=9301)], precision=prec)
     os.makedirs(os.path.dirname(os.path.abspath(args.out)), exist_ok=True)
     np.save(args.out, _np(w).astype(np.float32))
-    meta = {"config": {"n_mp": cfg.n_mp, "l": cfg.l, "l_mp": cfg.l_mp, "h": cfg.h, "diag_mode": cfg.diag_mode},
+    meta = {"config": {"n_mp": cfg.n_mp, "l": cfg.l, "l_mp": cfg.l_mp, "h": cfg.h, "diag_mode": cfg.diag_mode,
+                       "x0_head": cfg.x0_head},
             "train": {"steps": args.steps, "lr": args.lr, "lr_final": args.lr_final, "schedule": "cosine",
                       "batch": "8 systems x 2 pairs",
                       "selection": "checkpoint with the fewest validation PCG iterations",
                       "systems": f"groups of 8: 2-D FEM lattices {sizes if sizes is not None else [args.m]} "
                                  f"(sigma 1, corr 0.1), 3-D FD sides {sizes3d or []} (sigma {args.sigma3d}, "
                                  f"corr {args.corr3d})",
-                      "precision": args.precision, **tm},
+                      "precision": args.precision, "head_only_from": os.path.basename(args.x0_from) if args.x0_from else None, **tm},
             "loss_first": hist[0], "loss_last": float(np.mean(hist[-20:])),
             "heldout_fem128": ev, "untrained_fem128": ev0, "heldout_fem96": small, "fem256_seed0": big,
             "heldout_fd3d": fd3,

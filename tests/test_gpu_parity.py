@@ -449,3 +449,119 @@ def test_blocked_level_synchronous_solve(N):
     x32, s32 = N.pcg_solve(P, v, _gpu(b), N.PREC_LLT32, _gpu(Lo.val), rtol=1e-8)
     assert s32[0]["status"] == 0 and abs(s32[0]["iters"] - ito) <= max(1, int(np.ceil(0.05 * ito)))
     assert np.linalg.norm(b - O.spmv(Ao, _np(x32))) / np.linalg.norm(b) <= 2e-8
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-5), ("bf16", 2e-2)])
+def test_x0_head_parity(N, prec, tol):
+    # initial-guess head: x0 against the oracle's, the factor unchanged by the
+    # head, and PCG started from x0 reaching the tolerance
+    cfg = I.GnnConfig(n_mp=3, l=2, l_mp=2, h=64, diag_mode=1, x0_head=1)
+    Ao, (rp, ci, v) = _assemble_both(N, I.fem2d(20, sigma=1.0, seed=15))
+    P = N.analyse(rp, ci)
+    b = I.rhs(Ao.n, 15)
+    w = I.gnn_weights(cfg, 7)
+    pc = N.FP32 if prec == "fp32" else N.BF16
+    L, x0 = N.gnn_factor_x0(P, v, _gpu(b), cfg, _gpu(w, torch.float32), precision=pc)
+    xo = O.gnn_x0(cfg, Ao, b, w.astype(np.float64))
+    d = _np(x0) - xo
+    assert np.linalg.norm(d) <= tol * np.linalg.norm(xo) and np.abs(d).max() <= tol * np.abs(xo).max()
+    L_plain = N.gnn_factor(P, v, _gpu(b), cfg, _gpu(w, torch.float32), precision=pc)
+    assert torch.equal(L, L_plain)
+    x, st = N.pcg_solve(P, v, _gpu(b), N.PREC_LLT, L, rtol=1e-8, x0=x0)
+    assert st[0]["status"] == 0
+    assert np.linalg.norm(b - O.spmv(Ao, _np(x))) / np.linalg.norm(b) <= 2e-8
+
+
+def _wide_spd(n, seed):
+    # 2-D 5-point grid plus random symmetric long-range couplings, strictly
+    # diagonally dominant: rows with up to ~10 lower neighbours (dependencies
+    # beyond the four held in a row's packed record)
+    g = np.random.default_rng(seed)
+    m = int(np.sqrt(n))
+    n = m * m
+    rows, cols = [], []
+    for i in range(n):
+        x, y = i % m, i // m
+        if x > 0:
+            rows.append(i); cols.append(i - 1)
+        if y > 0:
+            rows.append(i); cols.append(i - m)
+        k = int(g.integers(0, 7))
+        for j in (g.integers(max(0, i - 3 * m), i, size=k) if i > 0 else []):
+            if j != i - 1 and j != i - m:
+                rows.append(i); cols.append(int(j))
+    adj = [dict() for _ in range(n)]
+    for i, j in sorted(set(zip(rows, cols))):
+        w = -float(g.uniform(0.1, 1.0))
+        adj[i][j] = w
+        adj[j][i] = w
+    rp, ci, val = [0], [], []
+    for i in range(n):
+        adj[i][i] = 1.1 + sum(-w for w in adj[i].values())
+        for j in sorted(adj[i]):
+            ci.append(j)
+            val.append(adj[i][j])
+        rp.append(len(ci))
+    return O.CSR(np.array(rp), np.array(ci), np.array(val))
+
+
+@pytest.mark.parametrize("case", ["fem130", "fd2d_var", "wide"])
+def test_flag_trsv_matches_barrier_bit_exact(N, case):
+    # the flag-synchronised FP32 solve performs the barrier kernel's FP32
+    # operations in the same order: both directions bit-identical, and both
+    # within FP32 rounding of the FP64 oracle on fl32(L)
+    if case == "wide":
+        Ao = _wide_spd(4900, 3)
+        P = N.analyse(_gpu(Ao.row_ptr, torch.int32), _gpu(Ao.col_idx, torch.int32))
+    else:
+        prob = I.fem2d(130, sigma=1.0, seed=3) if case == "fem130" else PROBLEMS[case]
+        Ao, (rp, ci, v) = _assemble_both(N, prob)
+        P = N.analyse(rp, ci)
+    Lo, _ = O.ic0(Ao)
+    N.factor_load(P, _gpu(Lo.val))
+    L32 = O.CSR(Lo.row_ptr, Lo.col_idx, Lo.val.astype(np.float32).astype(np.float64))
+    r = np.random.default_rng(7).standard_normal(Ao.n)
+    r32 = r.astype(np.float32).astype(np.float64)
+    for tr in (False, True):
+        P.set_trsv(N.TRSV_LEVELSYNC)
+        _, yb = N.sptrsv_timed(P, _gpu(r), transpose=tr, reps=1, f32=True)
+        P.set_trsv(N.TRSV_LEVELFLAG)
+        _, yf = N.sptrsv_timed(P, _gpu(r), transpose=tr, reps=1, f32=True)
+        assert torch.equal(yb, yf)
+        yo = O.trsv_upper(L32, r32) if tr else O.trsv_lower(L32, r32)
+        assert _rel(_np(yf), yo) <= 1e-4
+
+
+def test_flag_trsv_batched_pcg(N):
+    # one CTA per system: PCG with the FP32 apply in the flag design against
+    # the oracle (the bar of test_fp32_preconditioner_apply), and the same
+    # iterations as the barrier design
+    probs = [I.fem2d(60, sigma=1.0, seed=31), I.fd3d(12, 10, 9, sigma=1.0, seed=32), I.fd2d(40, 23, sigma=1.0, seed=33)]
+    As, cis, vs, bs = [], [], [], []
+    off, sys_ptr = 0, [0]
+    for k, p in enumerate(probs):
+        Ao, (rp, ci, v) = _assemble_both(N, p)
+        As.append(Ao)
+        cis.append(_np(ci) + off)
+        vs.append(_np(v))
+        bs.append(I.rhs(Ao.n, 60 + k))
+        off += Ao.n
+        sys_ptr.append(off)
+    nnz_off = np.cumsum([0] + [a.nnz for a in As])
+    rp_cat = np.concatenate([a.row_ptr[:-1] + nnz_off[k] for k, a in enumerate(As)] + [[nnz_off[-1]]])
+    P = N.analyse(_gpu(rp_cat, torch.int32), _gpu(np.concatenate(cis), torch.int32), sys_ptr)
+    v_cat = _gpu(np.concatenate(vs))
+    b_cat = _gpu(np.concatenate(bs))
+    Lg, _ = N.ic0_factor(P, v_cat)
+    P.set_trsv(N.TRSV_LEVELSYNC)
+    xb, sb = N.pcg_solve(P, v_cat, b_cat, N.PREC_LLT32, Lg, rtol=1e-8)
+    P.set_trsv(N.TRSV_LEVELFLAG)
+    xf, sf = N.pcg_solve(P, v_cat, b_cat, N.PREC_LLT32, Lg, rtol=1e-8)
+    assert torch.equal(xb, xf)
+    xs = _np(xf)
+    for k, Ao in enumerate(As):
+        _, ito, _, _ = O.pcg(Ao, bs[k], O.PREC_LLT, O.ic0(Ao)[0], rtol=1e-8)
+        assert sf[k]["status"] == 0 and sf[k]["iters"] == sb[k]["iters"]
+        assert abs(sf[k]["iters"] - ito) <= max(1, int(np.ceil(0.05 * ito)))
+        seg = xs[sys_ptr[k]:sys_ptr[k + 1]]
+        assert np.linalg.norm(bs[k] - O.spmv(Ao, seg)) / np.linalg.norm(bs[k]) <= 2e-8

@@ -142,3 +142,24 @@ def test_loss_and_grad_bf16_forward(N, diag_mode):
     gg = gg.cpu().numpy().astype(np.float64)
     assert abs(lg - lo) <= 4e-2 * abs(lo)
     assert np.linalg.norm(gg - go) / np.linalg.norm(go) <= 4e-2
+
+
+@pytest.mark.parametrize("prec,tl,tg", [("fp32", 1e-5, 1e-4), ("bf16", 4e-2, 4e-2)])
+def test_loss_and_grad_x0_head(N, prec, tl, tg):
+    """The loss with the initial-guess head's regression term and the
+    gradient (head by its regression, trunk by Eq. (loss_Ab) alone) against
+    the oracle; FP32 and the BF16 bars of the tests above."""
+    cfg = I.GnnConfig(n_mp=2, l=2, l_mp=2, h=64, diag_mode=1, x0_head=1)
+    prob = I.fem2d(12, sigma=1.0, seed=13)
+    om, ph = I.grf_features(prob)
+    Ao = O.assemble(prob, om, ph)
+    rp, ci, v = N.assemble_system(prob, om, ph)
+    P = N.analyse(rp, ci)
+    X, B = _pairs(Ao, 2, 51)
+    w = I.gnn_weights(cfg, 9, scale=1.5)
+    lo, go = O.loss_and_grad(cfg, Ao, X, B, w.astype(np.float64))
+    lg, gg = N.loss_and_grad(P, v, _gpu(X), _gpu(B), cfg, _gpu(w, torch.float32),
+                             precision=N.FP32 if prec == "fp32" else N.BF16)
+    gg = gg.cpu().numpy().astype(np.float64)
+    assert abs(lg - lo) <= tl * abs(lo)
+    assert np.linalg.norm(gg - go) / np.linalg.norm(go) <= tg
