@@ -64,6 +64,8 @@ def _L():
             lib.or_trsv_upper.argtypes = [C.c_int32, i32p, i32p, f64p, f64p, f64p]
             lib.or_ic0.argtypes = [C.c_int32, i32p, i32p, f64p, f64p, C.POINTER(C.c_double)]
             lib.or_ic0.restype = C.c_int
+            lib.or_sgs_factor.argtypes = [C.c_int32, i32p, i32p, f64p, f64p]
+            lib.or_sgs_factor.restype = None
             lib.or_pcg.argtypes = [C.c_int32, i32p, i32p, f64p, f64p, f64p, C.c_int, vp, vp, vp,
                                    C.c_double, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)]
             lib.or_pcg.restype = C.c_int
@@ -217,6 +219,16 @@ def ic0(A: CSR):
     if rc != 0:
         raise RuntimeError("IC(0) failed for every shift")
     return CSR(L.row_ptr, L.col_idx, Lv), alpha.value
+
+
+def sgs(A: CSR):
+    """Symmetric Gauss-Seidel (Sec. 5.1 baseline, read as the symmetric
+    sweep): L = (D + L_A) D^{-1/2} on tril(A), so that L L^T =
+    (D + L_A) D^-1 (D + L_A)^T."""
+    L, _ = tril(A)
+    Lv = np.zeros(L.nnz)
+    _L().or_sgs_factor(L.n, L.row_ptr, L.col_idx, L.val, Lv)
+    return CSR(L.row_ptr, L.col_idx, Lv)
 
 
 PREC_NONE, PREC_JACOBI, PREC_LLT = 0, 1, 2

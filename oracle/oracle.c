@@ -405,6 +405,23 @@ int or_ic0(int32_t n, const int32_t* Lrp, const int32_t* Lci, const double* Atri
 }
 
 /* ======================================================================
+ * Symmetric Gauss-Seidel preconditioner (Sec. 5.1 baseline "Gauss-Seidel",
+ * printed as P = L + U, which is not SPD; read as the symmetric sweep)
+ *   P = (D + L_A) D^-1 (D + L_A)^T,  L_A the strict lower triangle of A,
+ * handed to PCG as P = L L^T with L = (D + L_A) D^{-1/2} on tril(A):
+ *   L_ii = sqrt(A_ii),  L_ij = A_ij / sqrt(A_jj)  (j < i).
+ * Atril_v: A's values on the tril pattern (diagonal last in each row).
+ * ==================================================================== */
+void or_sgs_factor(int32_t n, const int32_t* Lrp, const int32_t* Lci, const double* Atril_v, double* Lv) {
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t k = Lrp[i]; k < Lrp[i + 1]; ++k) {
+            const int32_t j = Lci[k];
+            const double ajj = Atril_v[Lrp[j + 1] - 1];
+            Lv[k] = j == i ? sqrt(ajj) : Atril_v[k] / sqrt(ajj);
+        }
+}
+
+/* ======================================================================
  * PCG, Algorithm 1.  Stops when ||r_k||_2 <= rtol ||b||_2 (relative form of
  * the printed absolute epsilon).  iters = number of x updates (Algorithm 1's
  * k; its pre-loop update counts as 1).  If ||r_0|| is already below the

@@ -367,3 +367,47 @@ def test_pcg_iteration_spread_learned_factor():
     xi, iti, _, _ = O.pcg(A, b, O.PREC_LLT, Lic, rtol=1e-6)
     dxi = np.linalg.norm(_cg_with_order(A, b, 1e-6, "reverse", Lic, kmax=iti) - xi) / np.linalg.norm(xi)
     assert dxi <= 1e-12
+
+
+# ------------------------------------------------------------------ symmetric Gauss-Seidel
+def test_sgs_tridiagonal_closed_form():
+    # tridiag(-1, 2, -1): (D + L)(D^-1)(D + U) = A + L D^-1 U = A + diag(0, 1/2, ..., 1/2)
+    n = 8
+    D = 2 * np.eye(n) - np.eye(n, k=1) - np.eye(n, k=-1)
+    L = O.sgs(_csr_from_dense(D)).dense()
+    P = L @ L.T
+    assert np.allclose(P, D + np.diag([0.0] + [0.5] * (n - 1)), rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_sgs_equals_symmetric_sweep(seed):
+    # the L L^T form against the sweep product assembled from A's triangles
+    A = _random_spd_sparse(40, 0.15, seed)
+    L = O.sgs(_csr_from_dense(A)).dense()
+    Dg = np.diag(np.diag(A))
+    Lo = np.tril(A, -1)
+    P_sweep = (Dg + Lo) @ np.linalg.inv(Dg) @ (Dg + Lo).T
+    assert np.allclose(L @ L.T, P_sweep, rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("prob", [I.fd2d(9, 7, sigma=1.0, seed=1), I.fem2d(11, sigma=1.0, seed=2),
+                                  I.fd3d(5, 4, 4, sigma=1.5, corr_len=0.05, seed=3)])
+def test_sgs_spectrum_in_unit_interval(prob):
+    # for SPD A, the symmetric Gauss-Seidel (SSOR, omega = 1) preconditioned
+    # operator has its eigenvalues in (0, 1]: P - A = L_A D^-1 L_A^T >= 0
+    A = O.assemble(prob)
+    L = O.sgs(A).dense()
+    lam = sla.eigh(A.dense(), L @ L.T, eigvals_only=True)
+    assert lam.min() > 0 and lam.max() <= 1 + 1e-10
+    # and the largest is 1 exactly when L_A D^-1 L_A^T is singular (n > rank
+    # of L_A): here the first row of L_A is empty, so P - A has a zero row
+    assert abs(lam.max() - 1.0) <= 1e-10
+
+
+def test_sgs_pcg_between_jacobi_and_ic0_on_poisson():
+    A = O.assemble(I.poisson2d_32())
+    b = I.rhs(A.n, 0)
+    _, it_j, _, _ = O.pcg(A, b, O.PREC_JACOBI, rtol=1e-8)
+    _, it_s, _, st = O.pcg(A, b, O.PREC_LLT, O.sgs(A), rtol=1e-8)
+    _, it_i, _, _ = O.pcg(A, b, O.PREC_LLT, O.ic0(A)[0], rtol=1e-8)
+    assert st == 0 and it_i < it_s < it_j
