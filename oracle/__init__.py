@@ -47,9 +47,12 @@ def _L():
             vp = C.c_void_p
             lib.or_grf_eval.argtypes = [C.c_int, C.c_int64, f64p, C.c_int, f64p, f64p, C.c_double, f64p]
             lib.or_assemble_fd.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, f64p, f64p,
-                                           C.c_double, vp, vp, vp]
+                                           C.c_double, C.c_double, vp, vp, vp]
             lib.or_assemble_fd.restype = C.c_int64
-            lib.or_assemble_fem.argtypes = [C.c_int, i32p, C.c_int, f64p, f64p, C.c_double, vp, vp, vp]
+            lib.or_assemble_fem.argtypes = [C.c_int, i32p, C.c_int, f64p, f64p, C.c_double, C.c_double,
+                                            C.c_int32, C.c_int32, vp, vp, vp]
+            lib.or_fem_unknowns.argtypes = [C.c_int, C.c_int32, C.c_int32, i32p]
+            lib.or_fem_unknowns.restype = C.c_int32
             lib.or_assemble_fem.restype = C.c_int64
             lib.or_fem_diagonals.argtypes = [C.c_int, i32p, i8p]
             lib.or_spmv.argtypes = [C.c_int32, i32p, i32p, f64p, f64p, f64p]
@@ -132,7 +135,10 @@ def grf_eval(points, omega, phase, sigma):
 
 def assemble(problem, omega=None, phase=None, jitter=None) -> CSR:
     """Stiffness matrix of -div(k grad u) (Sec. 3 Discretization) for a
-    ``paper_2305_16432_gb300.inputs.Problem`` and its random inputs."""
+    ``paper_2305_16432_gb300.inputs.Problem`` and its random inputs; with
+    problem.tau > 0 the implicit time-step matrix M + tau K (FEM: consistent
+    mass; FD: h^2 I), with problem.dir_len > 0 only an arc of the FEM
+    boundary Dirichlet (see oracle.c)."""
     from paper_2305_16432_gb300 import inputs as I
     if omega is None:
         omega, phase = I.grf_features(problem)
@@ -141,7 +147,7 @@ def assemble(problem, omega=None, phase=None, jitter=None) -> CSR:
     lib = _L()
     if problem.kind == I.FD:
         args = (problem.dim, problem.nx, problem.ny, problem.nz, M, omega.reshape(-1), phase,
-                float(problem.sigma))
+                float(problem.sigma), float(problem.tau))
         nnz = lib.or_assemble_fd(*args, None, None, None)
         n = problem.n
         rp, ci, v = np.zeros(n + 1, np.int32), np.zeros(nnz, np.int32), np.zeros(nnz)
@@ -150,12 +156,20 @@ def assemble(problem, omega=None, phase=None, jitter=None) -> CSR:
         if jitter is None:
             jitter = I.fem_jitter(problem)
         jitter = _i32(jitter)
-        args = (problem.nx, jitter, M, omega.reshape(-1), phase, float(problem.sigma))
+        args = (problem.nx, jitter, M, omega.reshape(-1), phase, float(problem.sigma), float(problem.tau),
+                int(problem.dir_start), int(problem.dir_len))
         nnz = lib.or_assemble_fem(*args, None, None, None)
         n = problem.n
         rp, ci, v = np.zeros(n + 1, np.int32), np.zeros(nnz, np.int32), np.zeros(nnz)
         lib.or_assemble_fem(*args, _ptr(rp), _ptr(ci), _ptr(v))
     return CSR(rp, ci, v)
+
+
+def fem_unknowns(m, dir_start=0, dir_len=0):
+    """(unknown index of every lattice point, -1 for Dirichlet; n)."""
+    uid = np.zeros(m * m, np.int32)
+    n = _L().or_fem_unknowns(m, dir_start, dir_len, uid)
+    return uid, n
 
 
 def fem_diagonals(m, jitter):

@@ -113,8 +113,11 @@ static double fd_k(int dim, int i, int j, int l, int nx, int ny, int nz,
 }
 
 int64_t or_assemble_fd(int dim, int nx, int ny, int nz, int M, const double* omega,
-                       const double* phase, double sigma,
+                       const double* phase, double sigma, double tau,
                        int32_t* row_ptr, int32_t* col_idx, double* val) {
+    /* tau > 0: implicit time step A = h^2 I + tau K (lumped mass in the units
+     * of the h-free stencil, h = 1 / (nx + 1)) */
+    const double ks = tau > 0.0 ? tau : 1.0;
     if (dim == 2) nz = 1;
     int32_t n = nx * ny * nz;
     /* k at every grid point including the boundary layer: index (i+1,j+1,l+1) */
@@ -139,12 +142,16 @@ int64_t or_assemble_fd(int dim, int nx, int ny, int nz, int M, const double* ome
                     int lb = (dim == 3) ? l2 + 1 : 0;
                     double kb = kk[((int64_t)lb * ey + (j2 + 1)) * ex + (i2 + 1)];
                     double kf = 2.0 * ka * kb / (ka + kb);
-                    coo_add(&c, a, a, kf, 1);
+                    coo_add(&c, a, a, ks * kf, 1);
                     int interior = i2 >= 0 && i2 < nx && j2 >= 0 && j2 < ny && l2 >= 0 && l2 < nz;
                     if (interior) {
                         int32_t b = (int32_t)(((int64_t)l2 * ny + j2) * nx + i2);
-                        coo_add(&c, a, b, -kf, 1);
+                        coo_add(&c, a, b, -ks * kf, 1);
                     }
+                }
+                if (tau > 0.0) {
+                    const double h = 1.0 / (double)(nx + 1);
+                    coo_add(&c, a, a, h * h, 1);
                 }
             }
     int64_t nnz = coo_to_csr(&c, n, 0, row_ptr, col_idx, val);
@@ -157,8 +164,18 @@ int64_t or_assemble_fd(int dim, int nx, int ny, int nz, int M, const double* ome
  * lattice on [0,1]^2 in integer units X = a*1024 + jx, Y = c*1024 + jy,
  * coordinates X / (1024 (m-1)).  Each lattice cell is split by the diagonal
  * that passes the in-circle test (exact in int64); a tie takes the
- * (a,c)-(a+1,c+1) diagonal.  Boundary points are Dirichlet and eliminated.
- * Unknown index of interior point (a,c): (a-1) + (m-2)(c-1).
+ * (a,c)-(a+1,c+1) diagonal.  Dirichlet points are eliminated: the whole
+ * boundary (dir_len = 0), or an arc of dir_len consecutive boundary points
+ * starting at perimeter index dir_start, the other boundary points being
+ * unknowns (natural boundary).  Perimeter index k walks the boundary
+ * counter-clockwise from (0,0): bottom (k, 0), right (m-1, k-(m-1)), top
+ * (m-1-(k-2(m-1)), m-1), left (0, m-1-(k-3(m-1))).  Unknowns are numbered
+ * in point order a + m c; with the whole boundary Dirichlet the index of
+ * (a,c) is (a-1) + (m-2)(c-1).
+ * tau > 0 (implicit time step of the heat / wave equation, Sec. 5.1
+ * environments): A = M + tau K with the consistent P1 mass matrix
+ * M_T[s][t] = area (1 + [s == t]) / 12; every vertex pair of an element is
+ * then part of the pattern.
  * Element matrix K_T[s][t] = k_T (e_s . e_t) / (4 area), e_s the edge
  * opposite vertex s; k_T = exp(mean of the nodal g).  An off-diagonal entry
  * whose every contribution has an exactly-zero integer dot e_s . e_t is not
@@ -193,10 +210,36 @@ void or_fem_diagonals(int m, const int32_t* jitter, int8_t* diag) {
         }
 }
 
+/* point id a + m c of perimeter index k */
+static int64_t perimeter_point(int m, int64_t k) {
+    const int64_t e = m - 1;
+    if (k < e) return k;
+    if (k < 2 * e) return (m - 1) + (int64_t)m * (k - e);
+    if (k < 3 * e) return (m - 1 - (k - 2 * e)) + (int64_t)m * (m - 1);
+    return (int64_t)m * (m - 1 - (k - 3 * e));
+}
+
+/* unknown index of every lattice point (-1: Dirichlet); returns n */
+int32_t or_fem_unknowns(int m, int32_t dir_start, int32_t dir_len, int32_t* uid) {
+    const int64_t np = (int64_t)m * m, per = 4 * (int64_t)(m - 1);
+    char* dir = (char*)calloc((size_t)np, 1);
+    for (int c = 0; c < m; ++c)
+        for (int a = 0; a < m; ++a)
+            if (dir_len == 0 && (a == 0 || a == m - 1 || c == 0 || c == m - 1)) dir[a + (int64_t)m * c] = 1;
+    for (int64_t t = 0; t < (dir_len > 0 ? dir_len : 0); ++t)
+        dir[perimeter_point(m, (dir_start + t) % per)] = 1;
+    int32_t n = 0;
+    for (int64_t p = 0; p < np; ++p) uid[p] = dir[p] ? -1 : n++;
+    free(dir);
+    return n;
+}
+
 int64_t or_assemble_fem(int m, const int32_t* jitter, int M, const double* omega,
-                        const double* phase, double sigma,
+                        const double* phase, double sigma, double tau, int32_t dir_start, int32_t dir_len,
                         int32_t* row_ptr, int32_t* col_idx, double* val) {
     int64_t np = (int64_t)m * m;
+    int32_t* uid = (int32_t*)malloc(sizeof(int32_t) * (size_t)np);
+    const int32_t n = or_fem_unknowns(m, dir_start, dir_len, uid);
     int64_t* XY = (int64_t*)malloc(sizeof(int64_t) * 2 * np);
     double* pos = (double*)malloc(sizeof(double) * 2 * np);
     double* g = (double*)malloc(sizeof(double) * np);
@@ -212,7 +255,6 @@ int64_t or_assemble_fem(int m, const int32_t* jitter, int M, const double* omega
     or_grf_eval(2, np, pos, M, omega, phase, sigma, g);
     int8_t* dg = (int8_t*)malloc((size_t)(m - 1) * (m - 1));
     or_fem_diagonals(m, jitter, dg);
-    int32_t n = (int32_t)((m - 2) * (m - 2));
     coo_list cl = {0};
     for (int c = 0; c < m - 1; ++c)
         for (int a = 0; a < m - 1; ++a) {
@@ -238,24 +280,24 @@ int64_t or_assemble_fem(int m, const int32_t* jitter, int M, const double* omega
                 double area = 0.5 * (e[2][0] * (-e[1][1]) - e[2][1] * (-e[1][0]));
                 double kT = exp((g[tri[t][0]] + g[tri[t][1]] + g[tri[t][2]]) / 3.0);
                 for (int s = 0; s < 3; ++s) {
-                    int64_t ps = tri[t][s];
-                    int as = (int)(ps % m), cs = (int)(ps / m);
-                    if (as == 0 || as == m - 1 || cs == 0 || cs == m - 1) continue;
-                    int32_t is = (int32_t)((as - 1) + (int64_t)(m - 2) * (cs - 1));
+                    int32_t is = uid[tri[t][s]];
+                    if (is < 0) continue;
                     for (int u = 0; u < 3; ++u) {
-                        int64_t pu = tri[t][u];
-                        int au = (int)(pu % m), cu = (int)(pu / m);
-                        if (au == 0 || au == m - 1 || cu == 0 || cu == m - 1) continue;
-                        int32_t iu = (int32_t)((au - 1) + (int64_t)(m - 2) * (cu - 1));
+                        int32_t iu = uid[tri[t][u]];
+                        if (iu < 0) continue;
                         double dot = e[s][0] * e[u][0] + e[s][1] * e[u][1];
                         int64_t doti = ei[s][0] * ei[u][0] + ei[s][1] * ei[u][1];
-                        coo_add(&cl, is, iu, kT * dot / (4.0 * area), doti != 0);
+                        double kst = kT * dot / (4.0 * area);
+                        if (tau > 0.0)
+                            coo_add(&cl, is, iu, tau * kst + area * (s == u ? 2.0 : 1.0) / 12.0, 1);
+                        else
+                            coo_add(&cl, is, iu, kst, doti != 0);
                     }
                 }
             }
         }
     int64_t nnz = coo_to_csr(&cl, n, 1, row_ptr, col_idx, val);
-    free(cl.e); free(XY); free(pos); free(g); free(dg);
+    free(cl.e); free(XY); free(pos); free(g); free(dg); free(uid);
     return nnz;
 }
 

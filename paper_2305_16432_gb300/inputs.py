@@ -13,6 +13,8 @@ an input, so the two sides see the same bytes:
   lattice spacing, |jitter| <= 204, i.e. just under 0.2 h; boundary points
   are not jittered).
 * right-hand sides ``b ~ N(0, 1)`` (the node input of the GNN, Sec. 4.1).
+* for the implicit time-step systems, the position and length of the
+  Dirichlet arc on the FEM boundary.
 * GNN weights, PyTorch-style ``U(-1/sqrt(fan_in), 1/sqrt(fan_in))`` for W and
   bias, in the flat layout documented in ``include/npcg.h``.
 
@@ -32,7 +34,7 @@ JITTER_UNITS = 1024          # lattice spacing in integer units
 JITTER_MAX = 204             # max |jitter| in integer units (< 0.2 * 1024)
 
 # stream offsets so different quantities drawn from one seed are independent
-_S_GRF, _S_JIT, _S_RHS, _S_W, _S_MIX = 0x1000, 0x2000, 0x3000, 0x4000, 0x5000
+_S_GRF, _S_JIT, _S_RHS, _S_W, _S_MIX, _S_ARC = 0x1000, 0x2000, 0x3000, 0x4000, 0x5000, 0x6000
 
 
 def _rng(seed: int, stream: int) -> np.random.Generator:
@@ -54,6 +56,11 @@ class Problem:
     kind FEM: m x m lattice points on the unit square, (m-2)^2 unknowns.
     sigma / corr_len: GRF standard deviation and correlation length of log k
     (sigma == 0 gives k == 1).
+    tau > 0: the implicit time-step matrix M + tau K of the heat / wave
+    equation instead of K.
+    dir_start / dir_len (FEM): with dir_len > 0 only dir_len consecutive
+    boundary points from perimeter index dir_start are Dirichlet; the other
+    boundary points are unknowns.
     """
     kind: int
     dim: int
@@ -63,11 +70,16 @@ class Problem:
     sigma: float = 0.0
     corr_len: float = 0.1
     seed: int = 0
+    tau: float = 0.0
+    dir_start: int = 0
+    dir_len: int = 0
 
     @property
     def n(self) -> int:
         if self.kind == FEM:
-            return (self.nx - 2) ** 2
+            per = 4 * (self.nx - 1)
+            free = per - min(self.dir_len, per) if self.dir_len > 0 else 0
+            return (self.nx - 2) ** 2 + free
         return self.nx * self.ny * (self.nz if self.dim == 3 else 1)
 
 
@@ -108,6 +120,20 @@ def fem_jitter(p: Problem) -> np.ndarray:
     j[:, m - 1, :] = 0
     # array index [c, a, xy] -> point a + m*c
     return np.ascontiguousarray(j.reshape(-1), dtype=np.int32)
+
+
+def heat2d(m, seed=0, steps_over_explicit=100.0, sigma=1.0, corr_len=0.1) -> Problem:
+    """Implicit time step of the heat equation on the jittered-lattice FEM
+    mesh: A = M + tau K with tau = steps_over_explicit * h^2 / 4 (h = 1/(m-1),
+    a step that many times the explicit stability limit), and a Dirichlet
+    arc whose position and length (1/8 to 1/2 of the boundary) are drawn from
+    the seed, as in the paper's varying-boundary heat / wave environments."""
+    g = _rng(seed, _S_ARC)
+    per = 4 * (m - 1)
+    start = int(g.integers(0, per))
+    length = int(g.integers(per // 8, per // 2 + 1))
+    h = 1.0 / (m - 1)
+    return Problem(FEM, 2, m, m, 0, sigma, corr_len, seed, steps_over_explicit * h * h / 4.0, start, length)
 
 
 def zero_jitter(m: int) -> np.ndarray:

@@ -203,3 +203,132 @@ def test_fem_256_size():
     assert A.n == 64516
     # interior points: 1 + 4 lattice + 2 diagonal neighbours on average
     assert 440_000 < A.nnz < 460_000
+
+
+# ------------------------------------------------------------------ implicit time-step systems
+def _perimeter(m):
+    # boundary points counter-clockwise from (0, 0), written out edge by edge
+    pts = [(a, 0) for a in range(m - 1)] + [(m - 1, c) for c in range(m - 1)]
+    pts += [(a, m - 1) for a in range(m - 1, 0, -1)] + [(0, c) for c in range(m - 1, 0, -1)]
+    return [a + m * c for a, c in pts]
+
+
+def _unknown_ids(m, start, length):
+    per = _perimeter(m)
+    if length == 0:
+        dirich = set(per)
+    else:
+        dirich = {per[(start + t) % len(per)] for t in range(length)}
+    ids, k = {}, 0
+    for p in range(m * m):
+        if p not in dirich:
+            ids[p] = k
+            k += 1
+    return ids, k
+
+
+@pytest.mark.parametrize("start,length", [(0, 0), (5, 9), (30, 20), (0, 36), (17, 1)])
+def test_fem_dirichlet_arc_numbering(start, length):
+    m = 10
+    ids, n = _unknown_ids(m, start, length)
+    uid, n_o = O.fem_unknowns(m, start, length)
+    assert n_o == n
+    for p in range(m * m):
+        assert uid[p] == ids.get(p, -1)
+    assert I.Problem(I.FEM, 2, m, m, 0, 0.0, 0.1, 0, 0.0, start, length).n == n
+
+
+def _fem_dense_heat(m, jit, g, tau, ids, n):
+    """Independent M + tau K: barycentric gradients from a 3x3 solve for K,
+    edge-midpoint quadrature (exact for quadratics) for M = int lambda_s lambda_t."""
+    X, Y = _lattice(m, jit)
+    x, y = X / (1024.0 * (m - 1)), Y / (1024.0 * (m - 1))
+    A = np.zeros((n, n))
+    for t in _triangles(m, O.fem_diagonals(m, jit)):
+        Mt = np.array([[x[v], y[v], 1.0] for v in t])
+        grads = np.linalg.solve(Mt, np.eye(3))[:2, :].T
+        area = 0.5 * abs(np.linalg.det(Mt))
+        kT = math.exp(sum(g[v] for v in t) / 3.0)
+        lam_mid = [np.array([0.5 if q != e else 0.0 for q in range(3)]) for e in range(3)]
+        for s in range(3):
+            for u in range(3):
+                a, b = ids.get(t[s], -1), ids.get(t[u], -1)
+                if a < 0 or b < 0:
+                    continue
+                mass = area / 3.0 * sum(lm[s] * lm[u] for lm in lam_mid)
+                A[a, b] += tau * kT * area * grads[s] @ grads[u] + mass
+    return A
+
+
+@pytest.mark.parametrize("start,length", [(0, 0), (5, 9), (30, 20)])
+def test_heat_fem_matches_bruteforce(start, length):
+    m = 10
+    p = I.Problem(I.FEM, 2, m, m, 0, 1.0, 0.1, 6, 0.37, start, length)
+    jit = I.fem_jitter(p)
+    om, ph = I.grf_features(p)
+    A = O.assemble(p, om, ph, jit)
+    X, Y = _lattice(m, jit)
+    g = O.grf_eval(np.stack([X / (1024.0 * (m - 1)), Y / (1024.0 * (m - 1))], 1), om, ph, 1.0)
+    ids, n = _unknown_ids(m, start, length)
+    B = _fem_dense_heat(m, jit, g, 0.37, ids, n)
+    D = A.dense()
+    assert A.n == n and np.allclose(D, B, rtol=1e-11, atol=1e-11 * np.abs(B).max())
+    # every element pair is stored (the mass entries are positive)
+    assert A.nnz == np.count_nonzero(B)
+    assert np.array_equal(D, D.T) and np.linalg.eigvalsh(D).min() > 0
+
+
+def test_heat_fem_uniform_lattice_mass():
+    # zero jitter, right triangles of legs h: M_ii = h^2/2 (six incident
+    # triangles), M_ij = h^2/12 on every element edge; tau = 0 part is K
+    m = 12
+    h = 1.0 / (m - 1)
+    tau = 1e-3
+    P = I.Problem(I.FEM, 2, m, m, 0, 0.0, 0.1, 0, tau)
+    A = O.assemble(P, jitter=I.zero_jitter(m)).dense()
+    K = O.assemble(I.fem2d(m, sigma=0.0), jitter=I.zero_jitter(m)).dense()
+    M = A - tau * K
+    mi = m - 2
+    for c in range(mi):
+        for a in range(mi):
+            i = a + mi * c
+            assert abs(M[i, i] - h * h / 2) < 1e-15
+            for (da, dc) in [(1, 0), (0, 1), (1, 1)]:       # axis edges and the (a,c)-(a+1,c+1) diagonal
+                if a + da < mi and c + dc < mi:
+                    j = (a + da) + mi * (c + dc)
+                    assert abs(M[i, j] - h * h / 12) < 1e-15 and abs(M[j, i] - h * h / 12) < 1e-15
+            if a + 1 < mi and c >= 1:                       # the other diagonal is not an edge
+                assert M[i, (a + 1) + mi * (c - 1)] == 0.0
+
+
+def test_heat_fd_lumped_mass():
+    p0 = I.fd3d(5, 4, 3, sigma=1.0, seed=2)
+    p1 = I.Problem(I.FD, 3, 5, 4, 3, 1.0, 0.1, 2, 0.25)
+    K = O.assemble(p0)
+    A = O.assemble(p1)
+    assert np.array_equal(A.row_ptr, K.row_ptr) and np.array_equal(A.col_idx, K.col_idx)
+    expect = 0.25 * K.dense() + np.eye(K.n) / 36.0          # h = 1 / (nx + 1)
+    assert np.allclose(A.dense(), expect, rtol=1e-14, atol=1e-15)
+
+
+def test_stiffness_with_dirichlet_arc():
+    # pure stiffness, only an arc Dirichlet: rows of points with no
+    # Dirichlet element neighbour keep zero row sums (the Neumann operator
+    # annihilates constants); the matrix stays SPD
+    m = 12
+    p = I.Problem(I.FEM, 2, m, m, 0, 1.0, 0.1, 3, 0.0, 7, 10)
+    A = O.assemble(p)
+    D = A.dense()
+    ids, n = _unknown_ids(m, 7, 10)
+    dirich = {q for q in range(m * m) if q not in ids}
+    tris = _triangles(m, O.fem_diagonals(m, I.fem_jitter(p)))
+    touches = set()
+    for t in tris:
+        if any(v in dirich for v in t):
+            touches.update(t)
+    for q, i in ids.items():
+        if q not in touches:
+            assert abs(D[i].sum()) < 1e-12 * D[i, i]
+        else:
+            assert D[i].sum() > 0
+    assert np.linalg.eigvalsh(D).min() > 0
