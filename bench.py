@@ -109,7 +109,8 @@ def _dist():
 
 # the network trained for each workload's family (the paper trains one per
 # task); the mixed 2-D / 3-D network serves the uneven batch and is the fallback
-TASK_WEIGHTS = {"fem2d_256": "gnn_6x64_fem2d.npy", "fd3d_128": "gnn_6x64_fd3d.npy", "batched_256": "gnn_6x64.npy"}
+TASK_WEIGHTS = {"fem2d_256": "gnn_6x64_fem2d.npy", "fd3d_128": "gnn_6x64_fd3d.npy", "batched_256": "gnn_6x64.npy",
+                "heat2d_256": "gnn_6x64_heat2d.npy"}
 
 
 def weights_for(workload, x0=False):
@@ -175,7 +176,7 @@ def _host_csr(P_rp, P_ci, v):
     return O.CSR(P_rp.cpu().numpy(), P_ci.cpu().numpy(), v.cpu().numpy())
 
 
-SOLVE_WORKLOADS = ("fem2d_256", "fd3d_128", "batched_256")
+SOLVE_WORKLOADS = ("fem2d_256", "fd3d_128", "batched_256", "heat2d_256")
 
 
 def _problems(I, workload, rank):
@@ -185,6 +186,8 @@ def _problems(I, workload, rank):
         return [I.fem2d_256(seed=rank)]
     if workload == "fd3d_128":
         return [I.fd3d_128(seed=rank)]
+    if workload == "heat2d_256":
+        return [I.heat2d(256, seed=rank)]
     return I.batched_mix(256, seed=rank)
 
 
@@ -337,6 +340,10 @@ def run_solve(args, rank, world, local):
         x, st = N.pcg_solve(P, v, b, pc, L, rtol=RTOL)
         return st
 
+    def sgs_step():
+        x, st = N.pcg_solve(P, v, b, pc, N.sgs_factor(P, v), rtol=RTOL)
+        return st
+
     for _ in range(args.warmup):
         learned_step()
         ic0_step()
@@ -354,6 +361,8 @@ def run_solve(args, rank, world, local):
     if world > 1:
         torch.distributed.barrier()
     ms_i, st_i = _timed(ic0_step, args.steps, stream, flush)
+    sgs_step()
+    ms_g, st_g = _timed(sgs_step, args.steps, stream, flush)
     ms_per_step = job_ms_per_step(float(np.sum(ms_l)) / args.steps, world, dev)
     value = job_value(ms_per_step, nsys, world)
     it_l = [s["iters"] for s in st_l]
@@ -431,7 +440,7 @@ def run_solve(args, rank, world, local):
 
     if rank == 0:
         wl = {"fem2d_256": "fem2d_256_learned_pcg", "fd3d_128": "fd3d_128_learned_pcg",
-              "batched_256": "batched_256_learned_pcg"}[args.workload]
+              "batched_256": "batched_256_learned_pcg", "heat2d_256": "heat2d_256_learned_pcg"}[args.workload]
         line = {
             "metric": METRIC, "value": value, "unit": "ms/system", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
@@ -444,6 +453,8 @@ def run_solve(args, rank, world, local):
             "compare": {"learned_iters": it_l if nsys > 1 else it_l[0],
                         "learned_ms_median": float(np.median(ms_l)),
                         "ic0_ms_per_system": float(np.mean(ms_i)) / nsys, "ic0_iters": it_i if nsys > 1 else it_i[0],
+                        "sgs_ms_per_system": float(np.mean(ms_g)) / nsys,
+                        "sgs_iters": [x["iters"] for x in st_g] if nsys > 1 else st_g[0]["iters"],
                         "wall_s_timed": wall,
                         "trsv_design": {N.TRSV_LEVELSYNC: "levelsync", N.TRSV_LEVELFLAG: "levelflag"}.get(
                             P.trsv_mode, "syncfree"),

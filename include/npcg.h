@@ -97,6 +97,19 @@ typedef struct {
     const double* omega;      /* device [M * dim] frequencies                   */
     const double* phase;      /* device [M] phases                              */
     const int32_t* jitter;    /* device [m * m * 2] (FEM only; NULL for FD)     */
+    /* Implicit time step of the heat / wave equation (Sec. 5.1 environments):
+     * tau > 0 assembles A = M + tau K instead of K, M the consistent P1 mass
+     * matrix (FEM, M_T[s][t] = area (1 + [s == t]) / 12) or h^2 I (FD, in the
+     * units of the h-free stencil, h = 1 / (nx + 1)).  tau = 0: A = K.     */
+    double tau;
+    /* FEM boundary: dir_len = 0 makes every boundary point Dirichlet; with
+     * dir_len > 0 only dir_len consecutive points from perimeter index
+     * dir_start are, and the other boundary points are unknowns (natural
+     * boundary).  Perimeter index k runs counter-clockwise from (0,0):
+     * bottom (k, 0), right (m-1, k-(m-1)), top (m-1-(k-2(m-1)), m-1), left
+     * (0, m-1-(k-3(m-1))).  Unknowns are numbered in point order a + m c.
+     * FD: both must be 0.                                                   */
+    int32_t dir_start, dir_len;
 } npcg_problem;
 
 /* Size of the assembled system: *n_out, *nnz_out (host).  Synchronises. */
@@ -221,6 +234,20 @@ NPCG_API npcg_status npcg_ic0_factor(npcg_handle h, npcg_pattern p, const double
                             double* L_val, double* alpha_out);
 
 /* --------------------------------------------------------------------------
+ * Symmetric Gauss-Seidel (Sec. 5.1 baseline "Gauss-Seidel"; printed as
+ * P = L + U, which is not SPD, and read as the symmetric sweep
+ *   P = (D + L_A) D^-1 (D + L_A)^T,  L_A the strict lower triangle of A).
+ * Writes L = (D + L_A) D^{-1/2} on the tril(A) pattern, so that P = L L^T:
+ *   L_ii = sqrt(A_ii),  L_ij = A_ij / sqrt(A_jj)  (j < i),
+ * FP64 [nnz_L] in the order of npcg_pattern_export's L arrays, for
+ * npcg_pcg_solve with NPCG_PREC_LLT / _LLT32.  A_val [nnz] device, L_val
+ * caller-owned device buffer.  NPCG_EINVAL for a NULL argument; A must have
+ * a positive diagonal (not checked: a non-positive one gives NaN entries and
+ * PCG then reports NPCG_EBREAKDOWN).  Asynchronous on the handle's stream.
+ * ------------------------------------------------------------------------ */
+NPCG_API npcg_status npcg_sgs_factor(npcg_handle h, npcg_pattern p, const double* A_val, double* L_val);
+
+/* --------------------------------------------------------------------------
  * Preconditioned conjugate gradient, Algorithm 1, in FP64.
  * Stops when ||r_k||_2 <= rtol ||b||_2 (per system).  iters counts the
  * updates of x (Algorithm 1's k).  x holds x_0 on entry, the solution on
@@ -299,13 +326,15 @@ NPCG_API npcg_status npcg_adam_step(npcg_handle h, int64_t n, float* w, const fl
  * End to end from HOST buffers (the paper's timed quantity, Sec. 5.1
  * "Evaluation Metrics": precompute + solve).  Copies A_val_host [nnz] and
  * b_host [n] in, builds the preconditioner (method: NPCG_METHOD_GNN with
- * cfg + device weights, NPCG_METHOD_IC0, NPCG_METHOD_JACOBI, NPCG_METHOD_CG),
+ * cfg + device weights, NPCG_METHOD_IC0, NPCG_METHOD_JACOBI, NPCG_METHOD_CG,
+ * NPCG_METHOD_SGS),
  * runs PCG from x_0 = 0 and copies x out to x_host [n].  f32_apply != 0
  * applies the L L^T preconditioners in FP32 (NPCG_PREC_LLT32).  Host buffers
  * should be pinned for asynchronous copies.  stats: host [nsys].
  * Synchronises.
  * ------------------------------------------------------------------------ */
-enum { NPCG_METHOD_GNN = 0, NPCG_METHOD_IC0 = 1, NPCG_METHOD_JACOBI = 2, NPCG_METHOD_CG = 3 };
+enum { NPCG_METHOD_GNN = 0, NPCG_METHOD_IC0 = 1, NPCG_METHOD_JACOBI = 2, NPCG_METHOD_CG = 3,
+       NPCG_METHOD_SGS = 4 };
 
 NPCG_API npcg_status npcg_solve_host(npcg_handle h, npcg_pattern p, int32_t method,
                             const npcg_gnn_config* cfg, const float* weights,

@@ -197,6 +197,12 @@ npcg_status npcg_gnn_factor_x0(npcg_handle h, npcg_pattern p, const double* A_va
     return gnn_factor_x0_run(H(h), PT(p), A_val, b, cfg, weights, L_val, x0);
 }
 
+npcg_status npcg_sgs_factor(npcg_handle h, npcg_pattern p, const double* A_val, double* L_val) {
+    NPCG_TRY(check_hp(h, p));
+    if (!A_val || !L_val) return set_error(H(h), NPCG_EINVAL, "NULL argument");
+    return sgs_run(H(h), PT(p), A_val, L_val);
+}
+
 npcg_status npcg_ic0_factor(npcg_handle h, npcg_pattern p, const double* A_val, double* L_val,
                             double* alpha_out) {
     NPCG_TRY(check_hp(h, p));
@@ -277,7 +283,7 @@ npcg_status npcg_solve_host(npcg_handle h, npcg_pattern p, int32_t method, const
     Handle* hh = H(h);
     Pattern* P = PT(p);
     if (!A_val_host || !b_host || !x_host || !stats) return set_error(hh, NPCG_EINVAL, "NULL argument");
-    if (method < NPCG_METHOD_GNN || method > NPCG_METHOD_CG) return set_error(hh, NPCG_EINVAL, "unknown method");
+    if (method < NPCG_METHOD_GNN || method > NPCG_METHOD_SGS) return set_error(hh, NPCG_EINVAL, "unknown method");
     if (method == NPCG_METHOD_GNN && (!cfg || !weights)) return set_error(hh, NPCG_EINVAL, "GNN method needs cfg and weights");
     NPCG_CUDA(hh, P->Aval_dev.ensure(P->nnz));
     NPCG_CUDA(hh, P->b.ensure(P->n));
@@ -289,6 +295,7 @@ npcg_status npcg_solve_host(npcg_handle h, npcg_pattern p, int32_t method, const
     int precond = f32_apply ? NPCG_PREC_LLT32 : NPCG_PREC_LLT;
     if (method == NPCG_METHOD_GNN) NPCG_TRY(gnn_forward_run(hh, P, P->Aval_dev.p, P->b.p, cfg, weights, P->Lval_dev.p));
     else if (method == NPCG_METHOD_IC0) NPCG_TRY(ic0_run(hh, P, P->Aval_dev.p, P->Lval_dev.p, nullptr));
+    else if (method == NPCG_METHOD_SGS) NPCG_TRY(sgs_run(hh, P, P->Aval_dev.p, P->Lval_dev.p));
     else precond = method == NPCG_METHOD_JACOBI ? NPCG_PREC_JACOBI : NPCG_PREC_NONE;
     npcg_status s = pcg_run(hh, P, P->Aval_dev.p, P->b.p, P->x.p, precond, P->Lval_dev.p, rtol, max_iter, stats);
     cudaError_t e = cudaMemcpyAsync(x_host, P->x.p, P->n * sizeof(double), cudaMemcpyDeviceToHost, hh->stream);

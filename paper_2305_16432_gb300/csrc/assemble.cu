@@ -1,5 +1,7 @@
 // Assembly of the stiffness matrix A of -div(k grad u) = f with homogeneous
-// Dirichlet boundary (Sec. 3 "Discretization", standard Galerkin).  The
+// Dirichlet boundary (Sec. 3 "Discretization", standard Galerkin), or of the
+// implicit time-step matrix M + tau K of the heat / wave equation with a
+// Dirichlet arc of the FEM boundary (Sec. 5.1 environments).  The
 // paper's meshes and simulator are not available; the problems are
 // synthetic stand-ins on the unit square / cube:
 //   FD : 5/7-point stencil, face coefficient = harmonic mean of nodal k.
@@ -55,8 +57,11 @@ __global__ void k_fd_points(int dim, int nx, int ny, int nz, double* pts) {
     }
 }
 
-__global__ void k_fd_rows(int dim, int nx, int ny, int nz, const double* g, int32_t* rp,
+__global__ void k_fd_rows(int dim, int nx, int ny, int nz, const double* g, double tau, int32_t* rp,
                           int32_t* ci, double* val, int pass) {
+    // tau > 0: h^2 I + tau K (lumped mass in the units of the h-free stencil)
+    const double ks = tau > 0.0 ? tau : 1.0;
+    const double hh = tau > 0.0 ? 1.0 / ((double)(nx + 1) * (double)(nx + 1)) : 0.0;
     const int ex = nx + 2, ey = ny + 2;
     const int nzz = dim == 3 ? nz : 1;
     const int64_t n = (int64_t)nx * ny * nzz;
@@ -91,7 +96,7 @@ __global__ void k_fd_rows(int dim, int nx, int ny, int nz, const double* g, int3
             if (pass == 1) {
                 int32_t pos = rp[a] + cnt;
                 ci[pos] = (int32_t)(((int64_t)l2 * ny + j2) * nx + i2);
-                val[pos] = d == 3 ? diag : -kf[d];
+                val[pos] = d == 3 ? ks * diag + hh : -ks * kf[d];
             }
             ++cnt;
         }
@@ -138,13 +143,56 @@ __global__ void k_fem_diag(int m, const int32_t* jit, int8_t* dg) {
     }
 }
 
-// Row of interior point (a, c): accumulates the 3x3 stencil slots
-// (dc, da) in {-1,0,1}^2 over the two triangles of each incident cell.
+// perimeter index k -> point id a + m c (counter-clockwise from (0,0))
+__device__ __forceinline__ int64_t perimeter_point(int m, int64_t k) {
+    const int64_t e = m - 1;
+    if (k < e) return k;
+    if (k < 2 * e) return (m - 1) + (int64_t)m * (k - e);
+    if (k < 3 * e) return (m - 1 - (k - 2 * e)) + (int64_t)m * (m - 1);
+    return (int64_t)m * (m - 1 - (k - 3 * e));
+}
+
+// free[p] = 1 for an unknown point: interior, or a boundary point outside
+// the Dirichlet arc (dir_len = 0: the whole boundary is Dirichlet).  One
+// block: the arc is cleared after the whole lattice is marked.
+__global__ void k_fem_free(int m, int dir_start, int dir_len, int32_t* fr) {
+    const int64_t np = (int64_t)m * m, per = 4 * (int64_t)(m - 1);
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < np;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int a = (int)(p % m), c = (int)(p / m);
+        const bool bnd = a == 0 || a == m - 1 || c == 0 || c == m - 1;
+        fr[p] = bnd && dir_len == 0 ? 0 : 1;
+    }
+    __syncthreads();
+    // the arc (a point may be listed once only: dir_len <= perimeter)
+    const int64_t len = dir_len < per ? dir_len : per;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < len;
+         t += (int64_t)gridDim.x * blockDim.x)
+        fr[perimeter_point(m, (dir_start + t) % per)] = 0;
+}
+
+// uid[p] = unknown index of point p (-1: Dirichlet) and rowpt[uid] = p,
+// from the exclusive scan of free[]
+__global__ void k_fem_uid(int64_t np, int64_t n, const int32_t* fr, const int32_t* scan, int32_t* uid,
+                          int32_t* rowpt) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < np;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int u = fr[p] ? scan[p] : -1;
+        uid[p] = u < n ? u : -1;
+        if (u >= 0 && u < n) rowpt[u] = (int32_t)p;
+    }
+}
+
+// Row of unknown point (a, c): accumulates the 3x3 stencil slots
+// (dc, da) in {-1,0,1}^2 over the two triangles of each incident cell
+// (cells inside the lattice only); vertices that are Dirichlet are skipped.
+// tau > 0: tau K + M, every vertex pair of an element in the pattern.
 __device__ void fem_row(int m, int a, int c, const int32_t* jit, const double* pts, const double* g,
-                        const int8_t* dg, double* sv, int* sf) {
+                        const int8_t* dg, const int32_t* uid, double tau, double* sv, int* sf) {
     for (int s = 0; s < 9; ++s) { sv[s] = 0.0; sf[s] = 0; }
     for (int cc = c - 1; cc <= c; ++cc)
         for (int ca = a - 1; ca <= a; ++ca) {
+            if (ca < 0 || cc < 0 || ca > m - 2 || cc > m - 2) continue;
             int64_t p00 = ca + (int64_t)m * cc;
             int64_t v[2][3];
             if (dg[ca + (int64_t)(m - 1) * cc] == 0) {
@@ -175,42 +223,58 @@ __device__ void fem_row(int m, int a, int c, const int32_t* jit, const double* p
                 double kT = exp((g[v[t][0]] + g[v[t][1]] + g[v[t][2]]) / 3.0);
                 for (int u = 0; u < 3; ++u) {
                     int64_t pu = v[t][u];
+                    if (uid[pu] < 0) continue;
                     int au = (int)(pu % m), cu = (int)(pu / m);
-                    if (au == 0 || au == m - 1 || cu == 0 || cu == m - 1) continue;
                     int slot = (cu - c + 1) * 3 + (au - a + 1);
                     double dot = ex[s] * ex[u] + ey[s] * ey[u];
                     long long doti = ix[s] * ix[u] + iy[s] * iy[u];
-                    sv[slot] += kT * dot / (4.0 * area);
-                    sf[slot] |= doti != 0;
+                    const double kst = kT * dot / (4.0 * area);
+                    if (tau > 0.0) {
+                        sv[slot] += tau * kst + area * (s == u ? 2.0 : 1.0) / 12.0;
+                        sf[slot] = 1;
+                    } else {
+                        sv[slot] += kst;
+                        sf[slot] |= doti != 0;
+                    }
                 }
             }
         }
 }
 
-__global__ void k_fem_rows(int m, const int32_t* jit, const double* pts, const double* g,
-                           const int8_t* dg, int32_t* rp, int32_t* ci, double* val, int pass) {
-    const int mi = m - 2;
-    const int64_t n = (int64_t)mi * mi;
+__global__ void k_fem_rows(int m, int64_t n, const int32_t* rowpt, const int32_t* uid, const int32_t* jit,
+                           const double* pts, const double* g, const int8_t* dg, double tau, int32_t* rp,
+                           int32_t* ci, double* val, int pass) {
     for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < n;
          row += (int64_t)gridDim.x * blockDim.x) {
-        int a = (int)(row % mi) + 1, c = (int)(row / mi) + 1;
+        const int64_t p = rowpt[row];
+        int a = (int)(p % m), c = (int)(p / m);
         double sv[9];
         int sf[9];
-        fem_row(m, a, c, jit, pts, g, dg, sv, sf);
+        fem_row(m, a, c, jit, pts, g, dg, uid, tau, sv, sf);
+        // slots in ascending point order, hence ascending unknown index
         int cnt = 0;
         for (int s = 0; s < 9; ++s) {
             if (s != 4 && !sf[s]) continue;
             int au = a + s % 3 - 1, cu = c + s / 3 - 1;
-            if (au == 0 || au == m - 1 || cu == 0 || cu == m - 1) continue;
+            if (au < 0 || au > m - 1 || cu < 0 || cu > m - 1) continue;
+            const int32_t col = uid[au + (int64_t)m * cu];
+            if (col < 0) continue;
             if (pass == 1) {
                 int32_t pos = rp[row] + cnt;
-                ci[pos] = (int32_t)((au - 1) + (int64_t)mi * (cu - 1));
+                ci[pos] = col;
                 val[pos] = sv[s];
             }
             ++cnt;
         }
         if (pass == 0) rp[row] = cnt;
     }
+}
+
+// number of FEM unknowns: interior points plus the boundary points off the arc
+int64_t fem_unknowns(const npcg_problem* p) {
+    const int64_t m = p->nx, per = 4 * (m - 1);
+    if (p->dir_len == 0) return (m - 2) * (m - 2);
+    return (m - 2) * (m - 2) + per - std::min<int64_t>(p->dir_len, per);
 }
 
 int grid_of(int64_t n, int cap) {
@@ -224,7 +288,11 @@ npcg_status check_problem(Handle* h, const npcg_problem* p) {
         return set_error(h, NPCG_EINVAL, "n_features must be in [0, 2048]");
     if (p->sigma != 0.0 && (!p->omega || !p->phase || p->n_features == 0))
         return set_error(h, NPCG_EINVAL, "sigma != 0 needs omega and phase");
+    if (!(p->tau >= 0.0) || p->tau > 1e300) return set_error(h, NPCG_EINVAL, "tau must be finite and >= 0");
+    if (p->dir_len < 0 || p->dir_start < 0) return set_error(h, NPCG_EINVAL, "dir_start and dir_len must be >= 0");
     if (p->kind == NPCG_FD) {
+        if (p->dir_len != 0 || p->dir_start != 0)
+            return set_error(h, NPCG_EINVAL, "Dirichlet arcs are defined for FEM problems only");
         if (p->dim != 2 && p->dim != 3) return set_error(h, NPCG_EINVAL, "FD dim must be 2 or 3");
         if (p->nx < 1 || p->ny < 1 || (p->dim == 3 && p->nz < 1))
             return set_error(h, NPCG_EINVAL, "FD grid sizes must be >= 1");
@@ -258,12 +326,14 @@ npcg_status assemble_impl(Handle* h, const npcg_problem* p, int32_t* rp_counts, 
         NPCG_CUDA(h, g.alloc(np));
         k_fd_points<<<grid_of(np, cap), 256, 0, h->stream>>>(p->dim, p->nx, p->ny, p->nz, pts.p);
         k_grf<<<grid_of(np, cap), 256, grf_smem, h->stream>>>(p->dim, np, pts.p, M, p->omega, p->phase, p->sigma, g.p);
-        k_fd_rows<<<grid_of(n, cap), 256, 0, h->stream>>>(p->dim, p->nx, p->ny, p->nz, g.p, rp_counts, nullptr, nullptr, 0);
+        k_fd_rows<<<grid_of(n, cap), 256, 0, h->stream>>>(p->dim, p->nx, p->ny, p->nz, g.p, p->tau, rp_counts,
+                                                          nullptr, nullptr, 0);
         NPCG_CUDA(h, cudaGetLastError());
         if (n_out) *n_out = n;
         if (rp) {
             NPCG_TRY(scan_i32_to_i32(h, rp_counts, rp, n));
-            k_fd_rows<<<grid_of(n, cap), 256, 0, h->stream>>>(p->dim, p->nx, p->ny, p->nz, g.p, rp, ci, val, 1);
+            k_fd_rows<<<grid_of(n, cap), 256, 0, h->stream>>>(p->dim, p->nx, p->ny, p->nz, g.p, p->tau, rp, ci,
+                                                              val, 1);
             NPCG_CUDA(h, cudaGetLastError());
         }
         NPCG_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -276,21 +346,32 @@ npcg_status assemble_impl(Handle* h, const npcg_problem* p, int32_t* rp_counts, 
         return NPCG_OK;
     }
     const int m = p->nx;
-    const int64_t np = (int64_t)m * m, n = (int64_t)(m - 2) * (m - 2);
+    const int64_t np = (int64_t)m * m, n = fem_unknowns(p);
     DevBuf<double> pts, g;
     DevBuf<int8_t> dg;
+    DevBuf<int32_t> fr, scan, uid, rowpt;
     NPCG_CUDA(h, pts.alloc(np * 2));
     NPCG_CUDA(h, g.alloc(np));
     NPCG_CUDA(h, dg.alloc((size_t)(m - 1) * (m - 1)));
+    NPCG_CUDA(h, fr.alloc(np));
+    NPCG_CUDA(h, scan.alloc(np + 1));
+    NPCG_CUDA(h, uid.alloc(np));
+    NPCG_CUDA(h, rowpt.alloc(std::max<int64_t>(n, 1)));
+    k_fem_free<<<1, 256, 0, h->stream>>>(m, p->dir_start, p->dir_len, fr.p);
+    NPCG_TRY(scan_i32_to_i32(h, fr.p, scan.p, np));
+    NPCG_CUDA(h, cudaMemsetAsync(rowpt.p, 0, std::max<int64_t>(n, 1) * sizeof(int32_t), h->stream));
+    k_fem_uid<<<grid_of(np, cap), 256, 0, h->stream>>>(np, n, fr.p, scan.p, uid.p, rowpt.p);
     k_fem_points<<<grid_of(np, cap), 256, 0, h->stream>>>(m, p->jitter, pts.p);
     k_grf<<<grid_of(np, cap), 256, grf_smem, h->stream>>>(2, np, pts.p, M, p->omega, p->phase, p->sigma, g.p);
     k_fem_diag<<<grid_of((int64_t)(m - 1) * (m - 1), cap), 256, 0, h->stream>>>(m, p->jitter, dg.p);
-    k_fem_rows<<<grid_of(n, cap), 256, 0, h->stream>>>(m, p->jitter, pts.p, g.p, dg.p, rp_counts, nullptr, nullptr, 0);
+    k_fem_rows<<<grid_of(n, cap), 256, 0, h->stream>>>(m, n, rowpt.p, uid.p, p->jitter, pts.p, g.p, dg.p, p->tau,
+                                                       rp_counts, nullptr, nullptr, 0);
     NPCG_CUDA(h, cudaGetLastError());
     if (n_out) *n_out = n;
     if (rp) {
         NPCG_TRY(scan_i32_to_i32(h, rp_counts, rp, n));
-        k_fem_rows<<<grid_of(n, cap), 256, 0, h->stream>>>(m, p->jitter, pts.p, g.p, dg.p, rp, ci, val, 1);
+        k_fem_rows<<<grid_of(n, cap), 256, 0, h->stream>>>(m, n, rowpt.p, uid.p, p->jitter, pts.p, g.p, dg.p,
+                                                           p->tau, rp, ci, val, 1);
         NPCG_CUDA(h, cudaGetLastError());
     }
     if (nnz_out) {
@@ -309,8 +390,7 @@ npcg_status assemble_impl(Handle* h, const npcg_problem* p, int32_t* rp_counts, 
 
 npcg_status assemble_count_run(Handle* h, const npcg_problem* p, int64_t* n, int64_t* nnz) {
     NPCG_TRY(check_problem(h, p));
-    int64_t nn = p->kind == NPCG_FD ? (int64_t)p->nx * p->ny * (p->dim == 3 ? p->nz : 1)
-                                    : (int64_t)(p->nx - 2) * (p->nx - 2);
+    int64_t nn = p->kind == NPCG_FD ? (int64_t)p->nx * p->ny * (p->dim == 3 ? p->nz : 1) : fem_unknowns(p);
     DevBuf<int32_t> counts;
     NPCG_CUDA(h, counts.alloc(nn + 1));
     return assemble_impl(h, p, counts.p, nullptr, nullptr, nullptr, n, nnz);
@@ -318,8 +398,7 @@ npcg_status assemble_count_run(Handle* h, const npcg_problem* p, int64_t* n, int
 
 npcg_status assemble_run(Handle* h, const npcg_problem* p, int32_t* rp, int32_t* ci, double* v) {
     NPCG_TRY(check_problem(h, p));
-    int64_t nn = p->kind == NPCG_FD ? (int64_t)p->nx * p->ny * (p->dim == 3 ? p->nz : 1)
-                                    : (int64_t)(p->nx - 2) * (p->nx - 2);
+    int64_t nn = p->kind == NPCG_FD ? (int64_t)p->nx * p->ny * (p->dim == 3 ? p->nz : 1) : fem_unknowns(p);
     DevBuf<int32_t> counts;
     NPCG_CUDA(h, counts.alloc(nn + 1));
     return assemble_impl(h, p, counts.p, rp, ci, v, nullptr, nullptr);

@@ -134,4 +134,26 @@ npcg_status ic0_run(Handle* h, Pattern* P, const double* A_val, double* L_val, d
     return set_error(h, NPCG_ENOTSPD, "IC(0) broke down for every shift up to 1e-3 * 2^30");
 }
 
+// Symmetric Gauss-Seidel (Sec. 5.1 baseline "Gauss-Seidel", read as the
+// symmetric sweep P = (D + L_A) D^-1 (D + L_A)^T): as P = L L^T with
+// L = (D + L_A) D^{-1/2} on tril(A), i.e. L_ii = sqrt(A_ii) and
+// L_ij = A_ij / sqrt(A_jj).  One thread per entry of L.
+__global__ void k_sgs_factor(int64_t nnzL, const int32_t* Lci, const int32_t* l2a, const int32_t* adiag,
+                             const double* A_val, double* L_val) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnzL;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int j = Lci[k];
+        const int a = l2a[k], dj = adiag[j];
+        const double ajj = A_val[dj];
+        L_val[k] = a == dj ? sqrt(ajj) : A_val[a] / sqrt(ajj);
+    }
+}
+
+npcg_status sgs_run(Handle* h, Pattern* P, const double* A_val, double* L_val) {
+    const int blocks = std::max(1, std::min(ceil_div(P->nnzL, 256), h->num_sms * 8));
+    k_sgs_factor<<<blocks, 256, 0, h->stream>>>(P->nnzL, P->Lci.p, P->l2a.p, P->adiag.p, A_val, L_val);
+    NPCG_CUDA(h, cudaGetLastError());
+    return NPCG_OK;
+}
+
 }  // namespace npcg

@@ -109,6 +109,7 @@ struct CtaLayout {
     bool built = false;
     bool window_ok = false;        // every dependency within the shared window
     bool blocked = false;          // one large system in per-SM row blocks (remote dependencies)
+    bool far = false;              // hybrid window: dependencies beyond it read the output (-(pos + 2))
     int nunits = 0;                // CTAs of a solve: systems, or row blocks
     int win_slots = 0;             // window size (power of two) when window_ok
     int nsteps = 0, max_w = 0, max_np = 0;
@@ -273,6 +274,7 @@ npcg_status pcg_run(Handle* h, Pattern* P, const double* A_val, const double* b,
                     int precond, const double* L_val, double rtol, int max_iter,
                     npcg_solve_stats* stats);
 npcg_status ic0_run(Handle* h, Pattern* P, const double* A_val, double* L_val, double* alpha_out);
+npcg_status sgs_run(Handle* h, Pattern* P, const double* A_val, double* L_val);
 npcg_status gnn_forward_run(Handle* h, Pattern* P, const double* A_val, const double* b,
                             const npcg_gnn_config* cfg, const float* w, double* L_val);
 npcg_status loss_grad_run(Handle* h, Pattern* P, const double* A_val, int npairs,

@@ -224,7 +224,10 @@ __device__ __forceinline__ void ring_producer(const CtaDev& D, const T* rhs, uns
 // on is owned by a CTA that is already running; dependencies outside the
 // unit are encoded -(row + 2) and read from pub, and every row's value is
 // published there.
-template <bool kWindow, bool kRemote, class T>
+// kFar: hybrid window; a dependency encoded -(position + 2) lies beyond the
+// window and is read from the processing-order output (written in an earlier
+// step, before a consumer barrier).
+template <bool kWindow, bool kRemote, bool kFar, class T>
 __global__ void __launch_bounds__(kCtaThreads, 1) k_trsv_cta(CtaDev D, const T* __restrict__ rhs,
                                                          T* outq, double* yglob,
                                                          const SysState* st, int* flags,
@@ -297,10 +300,17 @@ __global__ void __launch_bounds__(kCtaThreads, 1) k_trsv_cta(CtaDev D, const T* 
         // warp issues in order)
         T yw0 = (T)0, yw1 = (T)0, yw2 = (T)0, yw3 = (T)0;
         if (kWindow && !kRemote && t < cur.nrows) {
-            yw0 = win[cur.dep.x];
-            yw1 = win[cur.dep.y];
-            yw2 = win[cur.dep.z];
-            yw3 = win[cur.dep.w];
+            if (kFar) {
+                yw0 = cur.dep.x >= 0 ? win[cur.dep.x] : __ldcg(outq + (-cur.dep.x - 2));
+                yw1 = cur.dep.y >= 0 ? win[cur.dep.y] : __ldcg(outq + (-cur.dep.y - 2));
+                yw2 = cur.dep.z >= 0 ? win[cur.dep.z] : __ldcg(outq + (-cur.dep.z - 2));
+                yw3 = cur.dep.w >= 0 ? win[cur.dep.w] : __ldcg(outq + (-cur.dep.w - 2));
+            } else {
+                yw0 = win[cur.dep.x];
+                yw1 = win[cur.dep.y];
+                yw2 = win[cur.dep.z];
+                yw3 = win[cur.dep.w];
+            }
         }
         // locate and load the next step
         const int32_t* chdr = hdr;          // the current step, for rows wider than the registers
@@ -354,6 +364,7 @@ __global__ void __launch_bounds__(kCtaThreads, 1) k_trsv_cta(CtaDev D, const T* 
                 for (int kk = 0; kk < cur.width - kRec; ++kk) {
                     const int pk = xdep[kk * cur.np + t];
                     if (kRemote && pk <= -2) acc = fma(-xval[kk * cur.np + t], (T)remote_dep(pub, -pk - 2, flags), acc);
+                    else if (kFar && pk <= -2) acc = fma(-xval[kk * cur.np + t], __ldcg(outq + (-pk - 2)), acc);
                     else if (kWindow) acc = fma(-xval[kk * cur.np + t], win[pk], acc);
                     else if (pk >= 0) acc = fma(-xval[kk * cur.np + t], (T)__ldcg(yglob + pk), acc);
                 }
@@ -365,6 +376,7 @@ __global__ void __launch_bounds__(kCtaThreads, 1) k_trsv_cta(CtaDev D, const T* 
             if (kWindow) {
                 win[q & (W - 1)] = y;
                 outq[q] = y;
+                if (kFar) __threadfence_block();
             } else {
                 yglob[q] = (double)y;
             }
@@ -696,9 +708,11 @@ __global__ void k_cta_remote(int64_t n, const int32_t* step_of_pos, const int4* 
     }
 }
 
-// the window suffices: dependency positions become window slots
+// dependency positions become window slots; with lend (hybrid window) a
+// dependency further back than the window (level end - position > W) is
+// read from the processing-order output instead and encoded -(position + 2)
 __global__ void k_cta_window(int64_t n, const int32_t* step_of_pos, const int4* steps, const int64_t* soff,
-                             int W, int32_t* sbuf) {
+                             int W, const int32_t* lend, int32_t* sbuf) {
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
          q += (int64_t)gridDim.x * blockDim.x) {
         const int stp = step_of_pos[q];
@@ -709,7 +723,7 @@ __global__ void k_cta_window(int64_t n, const int32_t* step_of_pos, const int4* 
         const int kmax = d.z > kRec ? d.z : kRec;
         for (int k = 0; k < kmax; ++k) {
             int32_t* p = dep_slot(body, np, t, k);
-            if (*p >= 0) *p &= W - 1;
+            if (*p >= 0) *p = lend && lend[stp] - *p > W ? -(*p + 2) : (*p & (W - 1));
             else if (*p == -1) *p = W;              // missing: the zero slot; <= -2 (remote) stays
         }
     }
@@ -964,6 +978,15 @@ npcg_status cta_layout_build(Handle* h, Pattern* P, bool upper, CtaLayout* C) {
     C->win_slots = kWinMin;
     if (C->window_ok)
         while ((unsigned long long)C->win_slots < rh) C->win_slots *= 2;
+    // Hybrid window: a dependency-free row sits at level 0 wherever it is in
+    // the mesh, so one late reader can stretch the reach of a whole system.
+    // One system per CTA then keeps the largest window and reads only the
+    // dependencies beyond it from the processing-order output.
+    C->far = !C->window_ok && !C->blocked;
+    if (C->far) {
+        C->window_ok = true;
+        C->win_slots = kWinMax;
+    }
     const size_t budget = nunits > h->num_sms ? kSmemHalf : kSmemMax;
     // largest single step (structure + values + right-hand side) for value size vsz
     auto single_bytes = [&](size_t vsz) {
@@ -986,7 +1009,7 @@ npcg_status cta_layout_build(Handle* h, Pattern* P, bool upper, CtaLayout* C) {
     size_t fcap = 0;
     int fstages = 0;
     C->flag_ok = false;
-    if (C->window_ok && !C->blocked) {
+    if (C->window_ok && !C->blocked && !C->far) {
         const size_t single = single_bytes(4);
         for (int W = C->win_slots; W <= kWinMax; W *= 2) {
             const size_t wb = (size_t)(W + kWinPad) * sizeof(unsigned long long);
@@ -1021,7 +1044,7 @@ npcg_status cta_layout_build(Handle* h, Pattern* P, bool upper, CtaLayout* C) {
     }
     if (C->window_ok) {
         k_cta_window<<<blocks, 256, 0, h->stream>>>(n, C->step_of_pos.p, C->steps.p, C->soff.p, C->win_slots,
-                                                    C->sbuf.p);
+                                                    C->far ? lend.p : nullptr, C->sbuf.p);
         NPCG_CUDA(h, cudaGetLastError());
     }
     // chunks per value type: the stage capacity is the larger of the biggest
@@ -1066,14 +1089,16 @@ npcg_status cta_layout_build(Handle* h, Pattern* P, bool upper, CtaLayout* C) {
     // the launch size never exceeds 220 KB; set once here, outside any capture
     const int mx = 220 * 1024;
     NPCG_CUDA(h, cudaFuncSetAttribute(k_trsv_flag, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-    NPCG_CUDA(h, cudaFuncSetAttribute(k_trsv_cta<true, false, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-    NPCG_CUDA(h, cudaFuncSetAttribute(k_trsv_cta<false, false, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-    NPCG_CUDA(h, cudaFuncSetAttribute(k_trsv_cta<true, false, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-    NPCG_CUDA(h, cudaFuncSetAttribute(k_trsv_cta<false, false, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-    NPCG_CUDA(h, cudaFuncSetAttribute(k_trsv_cta<true, true, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-    NPCG_CUDA(h, cudaFuncSetAttribute(k_trsv_cta<false, true, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-    NPCG_CUDA(h, cudaFuncSetAttribute(k_trsv_cta<true, true, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-    NPCG_CUDA(h, cudaFuncSetAttribute(k_trsv_cta<false, true, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    NPCG_CUDA(h, cudaFuncSetAttribute(k_trsv_cta<true, false, false, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    NPCG_CUDA(h, cudaFuncSetAttribute(k_trsv_cta<false, false, false, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    NPCG_CUDA(h, cudaFuncSetAttribute(k_trsv_cta<true, false, false, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    NPCG_CUDA(h, cudaFuncSetAttribute(k_trsv_cta<false, false, false, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    NPCG_CUDA(h, cudaFuncSetAttribute(k_trsv_cta<true, true, false, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    NPCG_CUDA(h, cudaFuncSetAttribute(k_trsv_cta<false, true, false, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    NPCG_CUDA(h, cudaFuncSetAttribute(k_trsv_cta<true, true, false, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    NPCG_CUDA(h, cudaFuncSetAttribute(k_trsv_cta<false, true, false, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    NPCG_CUDA(h, cudaFuncSetAttribute(k_trsv_cta<true, false, true, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    NPCG_CUDA(h, cudaFuncSetAttribute(k_trsv_cta<true, false, true, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
     NPCG_CUDA(h, cudaStreamSynchronize(h->stream));
     C->built = true;
     return NPCG_OK;
@@ -1175,16 +1200,18 @@ npcg_status cta_trsv_launch(Handle* h, cudaStream_t s, Pattern* P, const CtaLayo
     int* flags = P->ctl.p + 1;
     const int g = C.nunits;
     double* yg = P->yglob.p;
-#define NPCG_CTA_LAUNCH(W, R, TT)                                                                           \
-    k_trsv_cta<W, R, TT><<<g, kCtaThreads, smem, s>>>(d, static_cast<const TT*>(rhs_v),                      \
-                                                      W ? static_cast<TT*>(outq) : nullptr, W ? nullptr : yg, \
-                                                      st, flags, ticket, pub)
+#define NPCG_CTA_LAUNCH(W, R, F, TT)                                                                        \
+    k_trsv_cta<W, R, F, TT><<<g, kCtaThreads, smem, s>>>(d, static_cast<const TT*>(rhs_v),                   \
+                                                         W ? static_cast<TT*>(outq) : nullptr, W ? nullptr : yg, \
+                                                         st, flags, ticket, pub)
     if (f32) {
-        if (C.blocked) { if (C.window_ok) NPCG_CTA_LAUNCH(true, true, float); else NPCG_CTA_LAUNCH(false, true, float); }
-        else { if (C.window_ok) NPCG_CTA_LAUNCH(true, false, float); else NPCG_CTA_LAUNCH(false, false, float); }
+        if (C.blocked) { if (C.window_ok) NPCG_CTA_LAUNCH(true, true, false, float); else NPCG_CTA_LAUNCH(false, true, false, float); }
+        else if (C.far) NPCG_CTA_LAUNCH(true, false, true, float);
+        else { if (C.window_ok) NPCG_CTA_LAUNCH(true, false, false, float); else NPCG_CTA_LAUNCH(false, false, false, float); }
     } else {
-        if (C.blocked) { if (C.window_ok) NPCG_CTA_LAUNCH(true, true, double); else NPCG_CTA_LAUNCH(false, true, double); }
-        else { if (C.window_ok) NPCG_CTA_LAUNCH(true, false, double); else NPCG_CTA_LAUNCH(false, false, double); }
+        if (C.blocked) { if (C.window_ok) NPCG_CTA_LAUNCH(true, true, false, double); else NPCG_CTA_LAUNCH(false, true, false, double); }
+        else if (C.far) NPCG_CTA_LAUNCH(true, false, true, double);
+        else { if (C.window_ok) NPCG_CTA_LAUNCH(true, false, false, double); else NPCG_CTA_LAUNCH(false, false, false, double); }
     }
 #undef NPCG_CTA_LAUNCH
     NPCG_CUDA(h, cudaGetLastError());

@@ -24,7 +24,7 @@ NPCG_OK, NPCG_EINVAL, NPCG_ENOMEM, NPCG_ECUDA, NPCG_ENOTSPD, NPCG_EBREAKDOWN, NP
 FD, FEM = 0, 1
 FP32, BF16 = 0, 1
 PREC_NONE, PREC_JACOBI, PREC_LLT, PREC_LLT32 = 0, 1, 2, 3
-METHOD_GNN, METHOD_IC0, METHOD_JACOBI, METHOD_CG = 0, 1, 2, 3
+METHOD_GNN, METHOD_IC0, METHOD_JACOBI, METHOD_CG, METHOD_SGS = 0, 1, 2, 3, 4
 TRSV_AUTO, TRSV_SYNCFREE, TRSV_LEVELSYNC, TRSV_LEVELFLAG = 0, 1, 2, 3
 
 
@@ -37,7 +37,8 @@ class NpcgError(RuntimeError):
 class _Problem(C.Structure):
     _fields_ = [("kind", C.c_int32), ("dim", C.c_int32), ("nx", C.c_int32), ("ny", C.c_int32),
                 ("nz", C.c_int32), ("n_features", C.c_int32), ("sigma", C.c_double),
-                ("omega", C.c_void_p), ("phase", C.c_void_p), ("jitter", C.c_void_p)]
+                ("omega", C.c_void_p), ("phase", C.c_void_p), ("jitter", C.c_void_p), ("tau", C.c_double),
+                ("dir_start", C.c_int32), ("dir_len", C.c_int32)]
 
 
 class _Info(C.Structure):
@@ -83,6 +84,7 @@ def lib():
                 "npcg_gnn_factor": [vp, vp, vp, vp, C.POINTER(_Cfg), vp, vp],
                 "npcg_gnn_factor_x0": [vp, vp, vp, vp, C.POINTER(_Cfg), vp, vp, vp],
                 "npcg_ic0_factor": [vp, vp, vp, vp, vp],
+                "npcg_sgs_factor": [vp, vp, vp, vp],
                 "npcg_pcg_solve": [vp, vp, vp, vp, vp, i32, vp, dbl, i32, vp],
                 "npcg_pcg_solve_batched": [vp, vp, vp, vp, vp, i32, vp, dbl, i32, vp],
                 "npcg_spmv": [vp, vp, vp, vp, vp],
@@ -173,7 +175,8 @@ def assemble_system(problem: I.Problem, omega=None, phase=None, jitter=None, h: 
     ph = torch.as_tensor(np.ascontiguousarray(phase), dtype=torch.float64, device=dev)
     jt = torch.as_tensor(np.ascontiguousarray(jitter), dtype=torch.int32, device=dev) if jitter is not None else None
     pr = _Problem(problem.kind, problem.dim, problem.nx, problem.ny, problem.nz, len(ph),
-                  float(problem.sigma), om.data_ptr(), ph.data_ptr(), jt.data_ptr() if jt is not None else None)
+                  float(problem.sigma), om.data_ptr(), ph.data_ptr(), jt.data_ptr() if jt is not None else None,
+                  float(problem.tau), int(problem.dir_start), int(problem.dir_len))
     n, nnz = C.c_int64(), C.c_int64()
     h.check(lib().npcg_assemble_count(h.h, C.byref(pr), C.byref(n), C.byref(nnz)))
     rp = torch.empty(n.value + 1, dtype=torch.int32, device=dev)
@@ -291,6 +294,14 @@ def ic0_factor(P: Pattern, A_val, out=None):
     alpha = np.zeros(P.nsys, np.float64)
     P.h.check(lib().npcg_ic0_factor(P.h.h, P.p, _ptr(A_val), _ptr(L), alpha.ctypes.data_as(C.c_void_p)))
     return L, alpha
+
+
+def sgs_factor(P: Pattern, A_val, out=None):
+    """Symmetric Gauss-Seidel as P = L L^T: L = (D + L_A) D^{-1/2} on tril(A)."""
+    A_val = _dev(A_val, torch.float64, "A_val")
+    L = out if out is not None else torch.empty(P.nnz_L, dtype=torch.float64, device=A_val.device)
+    P.h.check(lib().npcg_sgs_factor(P.h.h, P.p, _ptr(A_val), _ptr(L)))
+    return L
 
 
 # ------------------------------------------------------------------ solve

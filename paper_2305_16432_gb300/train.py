@@ -103,7 +103,7 @@ def save_checkpoint(path, cfg, w, mom, vel, step, hist):
 
 def train(cfg: I.GnnConfig, steps=600, groups=4, per_group=8, pairs=8, m=128, lr=1e-3, lr_final=1e-4,
           seed=2023, log_every=25, w0=None, ckpt=None, resume=None, val_every=50, precision=None, sizes=None,
-          sizes3d=None, sigma3d=1.0, corr3d=0.1, head_only=False):
+          sizes3d=None, sigma3d=1.0, corr3d=0.1, head_only=False, heat=False):
     """Adam at lr (App. A.4), cosine-decayed to lr_final over the run; returns
     the weights with the fewest validation PCG iterations.  precision: the
     network forward's arithmetic (FP32, or BF16 tensor cores with the FP32
@@ -111,7 +111,10 @@ def train(cfg: I.GnnConfig, steps=600, groups=4, per_group=8, pairs=8, m=128, lr
     all, [] for none); sizes3d: grid side of each 3-D FD group (none by
     default), with log k a GRF of sigma3d and correlation length corr3d.
     head_only: train the initial-guess head alone (the trunk's gradient is
-    zeroed, so Adam leaves it unchanged) and validate PCG started from x0."""
+    zeroed, so Adam leaves it unchanged) and validate PCG started from x0.
+    heat: the 2-D groups and validation systems are implicit heat steps
+    M + tau K with Dirichlet arcs (inputs.heat2d) instead of stiffness
+    matrices."""
     from . import build as B
     B.build()
     from . import npcg as N
@@ -119,12 +122,14 @@ def train(cfg: I.GnnConfig, steps=600, groups=4, per_group=8, pairs=8, m=128, lr
     if sizes is None:
         sizes = [m] * groups
     specs = [("fem", x) for x in sizes] + [("fd3", x) for x in (sizes3d or [])]
+    family2d = (lambda mm, sd: I.heat2d(mm, seed=sd)) if heat else \
+        (lambda mm, sd: I.fem2d(mm, sigma=1.0, corr_len=0.1, seed=sd))
     groups = len(specs)
     t0 = time.time()
     data = []
     for g, (kind, mg) in enumerate(specs):
         if kind == "fem":
-            probs = [I.fem2d(mg, sigma=1.0, corr_len=0.1, seed=seed + 100 * g + k) for k in range(per_group)]
+            probs = [family2d(mg, seed + 100 * g + k) for k in range(per_group)]
         else:
             probs = [I.fd3d(mg, sigma=sigma3d, corr_len=corr3d, seed=seed + 100 * g + k) for k in range(per_group)]
         data.append(make_group(N, probs, pairs, seed + g))
@@ -145,7 +150,7 @@ def train(cfg: I.GnnConfig, steps=600, groups=4, per_group=8, pairs=8, m=128, lr
     # validation: PCG iterations on held-out systems of the training family;
     # the checkpoint with the fewest mean iterations is kept
     vals = []
-    vprobs = [I.fem2d(m, sigma=1.0, corr_len=0.1, seed=8000 + k) for k in range(2)] if sizes else []
+    vprobs = [family2d(m, 8000 + k) for k in range(2)] if sizes else []
     if sizes3d:
         v3 = I.fd3d(sizes3d[len(sizes3d) // 2], sigma=sigma3d, corr_len=corr3d, seed=8000)
         vprobs = [vprobs[0], v3] if vprobs else [v3]
@@ -215,6 +220,9 @@ def main():
     ap.add_argument("--sizes3d", default="", help="comma-separated grid sides of the 3-D FD training groups")
     ap.add_argument("--sigma3d", type=float, default=1.0, help="GRF sigma of the 3-D groups")
     ap.add_argument("--corr3d", type=float, default=0.1, help="GRF correlation length of the 3-D groups")
+    ap.add_argument("--init", default=None, help="start from these weights (same network shape)")
+    ap.add_argument("--heat", action="store_true",
+                    help="2-D systems are implicit heat steps M + tau K with Dirichlet arcs")
     ap.add_argument("--x0_from", default=None,
                     help="weights of a trained network: add the initial-guess head and train it alone")
     ap.add_argument("--out", default=os.path.join(os.path.dirname(__file__), "weights", "gnn_6x64.npy"))
@@ -224,6 +232,9 @@ def main():
     B.build()
     from . import npcg as N
     w_init = None
+    if args.init:
+        w_init = np.load(args.init).astype(np.float32)
+        assert w_init.size == cfg.nparams, "initial weights of another network"
     if args.x0_from:
         # trained trunk + a freshly initialised head (the tail of the flat layout)
         trunk = np.load(args.x0_from).astype(np.float32)
@@ -237,13 +248,16 @@ def main():
     w, hist, tm = train(cfg, steps=args.steps, m=args.m, lr=args.lr, lr_final=args.lr_final, ckpt=args.ckpt,
                         resume=args.resume, val_every=args.val_every, precision=prec, sizes=sizes,
                         sizes3d=sizes3d, sigma3d=args.sigma3d, corr3d=args.corr3d, w0=w_init,
-                        head_only=bool(args.x0_from))
+                        head_only=bool(args.x0_from), heat=args.heat)
     w0 = torch.as_tensor(I.gnn_weights(cfg, 2023), device="cuda")
-    held = [I.fem2d(args.m, sigma=1.0, corr_len=0.1, seed=9000 + k) for k in range(3)]
+    fam = (lambda mm, sd: I.heat2d(mm, seed=sd)) if args.heat else \
+        (lambda mm, sd: I.fem2d(mm, sigma=1.0, corr_len=0.1, seed=sd))
+    held = [fam(args.m, 9000 + k) for k in range(3)]
+    fam_name = "heat" if args.heat else "fem"
     ev = evaluate(N, cfg, w, held, precision=prec)
     ev0 = evaluate(N, cfg, w0, held[:1], precision=prec)
-    small = evaluate(N, cfg, w, [I.fem2d(96, sigma=1.0, corr_len=0.1, seed=9200)], precision=prec)
-    big = evaluate(N, cfg, w, [I.fem2d_256(seed=0)], precision=prec)
+    small = evaluate(N, cfg, w, [fam(96, 9200)], precision=prec)
+    big = evaluate(N, cfg, w, [I.heat2d(256, seed=0) if args.heat else I.fem2d_256(seed=0)], precision=prec)
     fd3 = evaluate(N, cfg, w, [I.fd3d(32, sigma=1.0, corr_len=0.1, seed=9300),
                                I.fd3d(64, sigma=1.5, corr_len=0.05, seed=9301)], precision=prec)
     os.makedirs(os.path.dirname(os.path.abspath(args.out)), exist_ok=True)
@@ -253,14 +267,17 @@ def main():
             "train": {"steps": args.steps, "lr": args.lr, "lr_final": args.lr_final, "schedule": "cosine",
                       "batch": "8 systems x 2 pairs",
                       "selection": "checkpoint with the fewest validation PCG iterations",
-                      "systems": f"groups of 8: 2-D FEM lattices {sizes if sizes is not None else [args.m]} "
+                      "systems": f"groups of 8: 2-D FEM {'heat steps (inputs.heat2d) ' if args.heat else ''}"
+                                 f"lattices {sizes if sizes is not None else [args.m]} "
                                  f"(sigma 1, corr 0.1), 3-D FD sides {sizes3d or []} (sigma {args.sigma3d}, "
                                  f"corr {args.corr3d})",
-                      "precision": args.precision, "head_only_from": os.path.basename(args.x0_from) if args.x0_from else None, **tm},
+                      "precision": args.precision, "head_only_from": os.path.basename(args.x0_from) if args.x0_from else None,
+                      "initialised_from": os.path.basename(args.init) if args.init else None, **tm},
             "loss_first": hist[0], "loss_last": float(np.mean(hist[-20:])),
-            "heldout_fem128": ev, "untrained_fem128": ev0, "heldout_fem96": small, "fem256_seed0": big,
+            f"heldout_{fam_name}{args.m}": ev, f"untrained_{fam_name}{args.m}": ev0, f"heldout_{fam_name}96": small,
+            f"{fam_name}256_seed0": big,
             "heldout_fd3d": fd3,
-            "learned_iters_fem256": big[0]["learned"]}
+            f"learned_iters_{fam_name}256": big[0]["learned"]}
     with open(os.path.splitext(args.out)[0] + ".json", "w") as f:
         json.dump(meta, f, indent=1)
     print(json.dumps(meta), flush=True)

@@ -565,3 +565,104 @@ def test_flag_trsv_batched_pcg(N):
         assert abs(sf[k]["iters"] - ito) <= max(1, int(np.ceil(0.05 * ito)))
         seg = xs[sys_ptr[k]:sys_ptr[k + 1]]
         assert np.linalg.norm(bs[k] - O.spmv(Ao, seg)) / np.linalg.norm(bs[k]) <= 2e-8
+
+
+@pytest.mark.parametrize("name", ["poisson2d_32", "fd2d_var", "fd3d_var", "fem34"])
+def test_sgs_factor_and_pcg_parity(N, name):
+    # the factor from the oracle's A values: one correctly rounded square root
+    # and division per entry on both sides, so bit-identical; PCG with it
+    # within one iteration of the oracle's, in the FP64 and the FP32 apply
+    Ao, (rp, ci, v) = _assemble_both(N, PROBLEMS[name])
+    P = N.analyse(rp, ci)
+    Lo = O.sgs(Ao)
+    Lg = N.sgs_factor(P, _gpu(Ao.val))
+    assert np.array_equal(_np(Lg), Lo.val)
+    b = I.rhs(Ao.n, 12)
+    xo, ito, _, _ = O.pcg(Ao, b, O.PREC_LLT, Lo, rtol=1e-8)
+    xg, st = N.pcg_solve(P, _gpu(Ao.val), _gpu(b), N.PREC_LLT, Lg, rtol=1e-8)
+    assert st[0]["status"] == 0 and abs(st[0]["iters"] - ito) <= 1
+    assert np.linalg.norm(_np(xg) - xo) / np.linalg.norm(xo) <= 1e-8
+    x32, s32 = N.pcg_solve(P, _gpu(Ao.val), _gpu(b), N.PREC_LLT32, Lg, rtol=1e-8)
+    assert s32[0]["status"] == 0 and abs(s32[0]["iters"] - ito) <= max(1, int(np.ceil(0.05 * ito)))
+    assert np.linalg.norm(b - O.spmv(Ao, _np(x32))) / np.linalg.norm(b) <= 2e-8
+
+
+def test_sgs_solve_host(N):
+    # the host-buffer entry point with the SGS method matches the device path
+    Ao, (rp, ci, v) = _assemble_both(N, PROBLEMS["fem34"])
+    P = N.analyse(rp, ci)
+    b = I.rhs(Ao.n, 13)
+    xd, sd = N.pcg_solve(P, v, _gpu(b), N.PREC_LLT, N.sgs_factor(P, v), rtol=1e-8)
+    xh, sh = N.solve_host(P, _np(v), b, method=N.METHOD_SGS, rtol=1e-8)
+    assert sh[0]["iters"] == sd[0]["iters"]
+    assert np.array_equal(np.asarray(xh), _np(xd))
+
+
+TIME_STEP = {
+    "heat_fem_arc": I.heat2d(40, seed=3),
+    "heat_fem_arc_wrap": I.Problem(I.FEM, 2, 24, 24, 0, 1.0, 0.1, 7, 2e-3, 80, 30),
+    "heat_fem_all": I.Problem(I.FEM, 2, 30, 30, 0, 1.0, 0.1, 4, 1e-2),
+    "stiff_fem_arc": I.Problem(I.FEM, 2, 26, 26, 0, 1.0, 0.1, 6, 0.0, 11, 30),
+    "heat_fd3d": I.Problem(I.FD, 3, 9, 8, 7, 1.0, 0.1, 5, 0.05),
+}
+
+
+@pytest.mark.parametrize("name", list(TIME_STEP))
+def test_time_step_assembly_parity(N, name):
+    # M + tau K and Dirichlet arcs: pattern and numbering bit-exact, values
+    # to the bar of the stiffness assembly
+    prob = TIME_STEP[name]
+    Ao, (rp, ci, v) = _assemble_both(N, prob)
+    assert Ao.n == prob.n
+    assert np.array_equal(_np(rp), Ao.row_ptr)
+    assert np.array_equal(_np(ci), Ao.col_idx)
+    assert _rel(_np(v), Ao.val) <= 1e-12
+
+
+@pytest.mark.parametrize("name", list(TIME_STEP))
+def test_time_step_pcg_parity(N, name):
+    # IC(0) and symmetric Gauss-Seidel PCG on the time-step systems against
+    # the oracle (the bars of the stiffness systems)
+    prob = TIME_STEP[name]
+    Ao, (rp, ci, v) = _assemble_both(N, prob)
+    P = N.analyse(rp, ci)
+    b = I.rhs(Ao.n, 14)
+    for Lo, Lg in ((O.ic0(Ao)[0], N.ic0_factor(P, _gpu(Ao.val))[0]), (O.sgs(Ao), N.sgs_factor(P, _gpu(Ao.val)))):
+        xo, ito, _, _ = O.pcg(Ao, b, O.PREC_LLT, Lo, rtol=1e-8)
+        xg, st = N.pcg_solve(P, _gpu(Ao.val), _gpu(b), N.PREC_LLT, Lg, rtol=1e-8)
+        assert st[0]["status"] == 0 and abs(st[0]["iters"] - ito) <= 1
+        assert np.linalg.norm(_np(xg) - xo) / np.linalg.norm(xo) <= 1e-8
+
+
+def test_time_step_rejects_bad_arcs(N):
+    with pytest.raises(N.NpcgError):
+        N.assemble_system(I.Problem(I.FD, 2, 8, 8, 0, 0.0, 0.1, 0, 0.1, 3, 4))
+    with pytest.raises(N.NpcgError):
+        N.assemble_system(I.Problem(I.FEM, 2, 8, 8, 0, 0.0, 0.1, 0, -1.0))
+
+
+@pytest.mark.parametrize("prob", [I.heat2d(130, seed=0), I.heat2d(110, seed=2)])
+def test_hybrid_window_far_dependencies(N, prob):
+    # free boundary points of these heat systems have no upper neighbours
+    # and sit at backward level 0 while a reader comes thousands of
+    # positions later (reach 11,332 and 8,507 > the 8,192-slot window): the
+    # level-synchronous solve keeps the window and reads those dependencies
+    # from its output; both directions against the oracle, and PCG
+    Ao, (rp, ci, v) = _assemble_both(N, prob)
+    P = N.analyse(rp, ci)
+    P.set_trsv(N.TRSV_LEVELSYNC)
+    Lo, _ = O.ic0(Ao)
+    N.factor_load(P, _gpu(Lo.val))
+    r = np.random.default_rng(8).standard_normal(Ao.n)
+    assert _rel(_np(N.sptrsv(P, _gpu(r))), O.trsv_lower(Lo, r)) <= 1e-12
+    assert _rel(_np(N.sptrsv(P, _gpu(r), transpose=True)), O.trsv_upper(Lo, r)) <= 1e-12
+    L32 = O.CSR(Lo.row_ptr, Lo.col_idx, Lo.val.astype(np.float32).astype(np.float64))
+    r32 = r.astype(np.float32).astype(np.float64)
+    _, y32 = N.sptrsv_timed(P, _gpu(r), transpose=True, reps=1, f32=True)
+    assert _rel(_np(y32), O.trsv_upper(L32, r32)) <= 1e-4
+    b = I.rhs(Ao.n, 15)
+    xo, ito, _, _ = O.pcg(Ao, b, O.PREC_LLT, Lo, rtol=1e-8)
+    for pc in (N.PREC_LLT, N.PREC_LLT32):
+        xg, st = N.pcg_solve(P, _gpu(Ao.val), _gpu(b), pc, _gpu(Lo.val), rtol=1e-8)
+        assert st[0]["status"] == 0 and abs(st[0]["iters"] - ito) <= max(1, int(np.ceil(0.05 * ito)))
+        assert np.linalg.norm(b - O.spmv(Ao, _np(xg))) / np.linalg.norm(b) <= 2e-8
