@@ -80,6 +80,8 @@ def _L():
             lib.or_gnn_x0.argtypes = [vp, C.c_int32, i32p, i32p, f64p, f64p, f64p, i32p, i32p, f64p, f64p]
             lib.or_llt_loss.argtypes = [C.c_int32, i32p, i32p, f64p, C.c_int, f64p, f64p, vp]
             lib.or_llt_loss.restype = C.c_double
+            lib.or_frob_loss.argtypes = [C.c_int32, i32p, i32p, f64p, i32p, i32p, f64p, vp]
+            lib.or_frob_loss.restype = C.c_double
             lib.or_loss_and_grad.argtypes = [vp, C.c_int32, i32p, i32p, f64p, C.c_int, f64p, f64p, f64p, vp]
             lib.or_loss_and_grad.restype = C.c_double
             lib.or_adam.argtypes = [C.c_int64, f64p, f64p, f64p, f64p, C.c_int, C.c_double, C.c_double,
@@ -266,11 +268,12 @@ def pcg(A: CSR, b, precond=PREC_NONE, L: CSR | None = None, rtol=1e-8, max_iter=
 # ------------------------------------------------------------------ GNN
 class _Cfg(C.Structure):
     _fields_ = [("n_mp", C.c_int), ("l", C.c_int), ("l_mp", C.c_int), ("h", C.c_int), ("diag_mode", C.c_int),
-                ("x0_head", C.c_int)]
+                ("x0_head", C.c_int), ("loss", C.c_int)]
 
 
 def _cfg(cfg):
-    return _Cfg(cfg.n_mp, cfg.l, cfg.l_mp, cfg.h, cfg.diag_mode, int(getattr(cfg, "x0_head", 0)))
+    return _Cfg(cfg.n_mp, cfg.l, cfg.l_mp, cfg.h, cfg.diag_mode, int(getattr(cfg, "x0_head", 0)),
+                int(getattr(cfg, "loss", 0)))
 
 
 def gnn_nparams(cfg):
@@ -372,8 +375,16 @@ def llt_loss(L: CSR, X, B, with_grad=True):
     return loss, dL
 
 
+def frob_loss(A: CSR, L: CSR, with_grad=True):
+    """||L L^T - A||_F^2 (Eq. loss_A for one L) and d/dL on the pattern of L."""
+    dL = np.zeros(L.nnz) if with_grad else None
+    loss = _L().or_frob_loss(A.n, A.row_ptr, A.col_idx, A.val, L.row_ptr, L.col_idx, L.val, _ptr(dL))
+    return loss, dL
+
+
 def loss_and_grad(cfg, A: CSR, X, B, w, with_grad=True):
-    """Loss Eq. (loss_Ab) through the GNN and its gradient w.r.t. the weights."""
+    """Loss through the GNN (Eq. loss_Ab, or Eq. loss_A when cfg.loss == 1)
+    and its gradient w.r.t. the weights."""
     X, B = np.atleast_2d(_f64(X)), np.atleast_2d(_f64(B))
     w = _f64(w)
     g = np.zeros(len(w)) if with_grad else None

@@ -551,7 +551,8 @@ done:
  * ==================================================================== */
 /* x0_head: the initial-guess head of Sec. 4.4 ("surrogate" use): an MLP of
  * depth l on the final node features, x0_i = (||b||_inf / s) MLP_x(v_i) */
-typedef struct { int n_mp, l, l_mp, h, diag_mode, x0_head; } or_gnn_cfg;
+/* loss: 0 Eq. (loss_Ab), 1 Eq. (loss_A) (training only; no weights) */
+typedef struct { int n_mp, l, l_mp, h, diag_mode, x0_head, loss; } or_gnn_cfg;
 
 static int64_t mlp_nparams(int in, int h, int out, int depth) {
     int64_t s = (int64_t)in * h + h;
@@ -939,6 +940,44 @@ double or_llt_loss(int32_t n, const int32_t* Lrp, const int32_t* Lci, const doub
     return loss;
 }
 
+/* Frobenius loss of Eq. (loss_A) for one L and its system A:
+ *   l = ||L L^T - A||_F^2 over the full n x n matrices (the fill-in of L L^T
+ *   outside the pattern of A included),
+ *   dl/dL_ik = 4 ((L L^T - A) L)_ik on the pattern of L (R symmetric).
+ * Written out densely: R and L as n x n arrays (test sizes only). */
+double or_frob_loss(int32_t n, const int32_t* rp, const int32_t* ci, const double* av,
+                    const int32_t* Lrp, const int32_t* Lci, const double* Lv, double* dL) {
+    double* Ld = (double*)calloc((size_t)n * n, sizeof(double));
+    double* R = (double*)calloc((size_t)n * n, sizeof(double));
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t k = Lrp[i]; k < Lrp[i + 1]; ++k) Ld[(size_t)i * n + Lci[k]] = Lv[k];
+    /* (L L^T)_ij = sum_k L_ik L_jk */
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t j = 0; j < n; ++j) {
+            double sum = 0.0;
+            for (int32_t k = Lrp[i]; k < Lrp[i + 1]; ++k) sum += Lv[k] * Ld[(size_t)j * n + Lci[k]];
+            R[(size_t)i * n + j] = sum;
+        }
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t k = rp[i]; k < rp[i + 1]; ++k) R[(size_t)i * n + ci[k]] -= av[k];
+    double loss = 0.0;
+    for (size_t e = 0; e < (size_t)n * n; ++e) loss += R[e] * R[e];
+    if (dL)
+        for (int32_t i = 0; i < n; ++i)
+            for (int32_t k = Lrp[i]; k < Lrp[i + 1]; ++k) {
+                const int32_t col = Lci[k];
+                double sum = 0.0;
+                for (int32_t j = 0; j < n; ++j) sum += R[(size_t)i * n + j] * Ld[(size_t)j * n + col];
+                dL[k] = 4.0 * sum;
+            }
+    free(Ld); free(R);
+    return loss;
+}
+
+/* Loss over the (x, b) pairs of one system and its gradient in the flat
+ * weights.  c->loss = 0: Eq. (loss_Ab), ||L L^T x - b||^2; 1: Eq. (loss_A),
+ * ||L L^T - A||_F^2 with L = f(A, b_p) (the node input is b_p, so each
+ * pair still has its own L).  Mean over the pairs. */
 double or_loss_and_grad(const or_gnn_cfg* c, int32_t n, const int32_t* rp, const int32_t* ci,
                         const double* av, int npairs, const double* X, const double* B,
                         const double* w, double* grad) {
@@ -953,7 +992,8 @@ double or_loss_and_grad(const or_gnn_cfg* c, int32_t n, const int32_t* rp, const
         gnn_tape T;
         gnn_forward_tape(c, n, rp, ci, av, B + (size_t)p * n, w, Lrp, Lci, Lv, &T, NULL);
         /* this pair's share of the mean */
-        double lp = or_llt_loss(n, Lrp, Lci, Lv, 1, X + (size_t)p * n, B + (size_t)p * n, grad ? dL : NULL);
+        double lp = c->loss == 1 ? or_frob_loss(n, rp, ci, av, Lrp, Lci, Lv, grad ? dL : NULL)
+                                 : or_llt_loss(n, Lrp, Lci, Lv, 1, X + (size_t)p * n, B + (size_t)p * n, grad ? dL : NULL);
         loss += lp / npairs;
         if (grad) {
             for (int64_t k = 0; k < nnzL; ++k) dL[k] /= npairs;

@@ -164,6 +164,7 @@ class GnnConfig:
     h: int = 16
     diag_mode: int = 0     # 0: L_ii = softplus(s_ii)
     x0_head: int = 0       # 1: initial-guess head (node MLP of depth l after the decoder)
+    loss: int = 0          # training loss: 0 Eq. (loss_Ab), 1 the Frobenius loss Eq. (loss_A)
 
     def linears(self):
         """(fan_in, fan_out) of every Linear in flat-layout order."""

@@ -360,3 +360,94 @@ def test_x0_head_gradient():
         fd = (O.loss_and_grad(cfg, A, X, B, wp, False)[0] - O.loss_and_grad(cfg, A, X, B, wm, False)[0]) / (2 * eps)
         err = max(err, abs(fd - grad[k]) / max(floor, abs(grad[k])))
     assert err < 1e-6, err
+
+
+# ------------------------------------------------------------------ Frobenius loss Eq. (loss_A)
+def _csr(D):
+    rp, ci, v = [0], [], []
+    for i in range(D.shape[0]):
+        nz = np.nonzero(D[i])[0]
+        ci += list(nz)
+        v += list(D[i, nz])
+        rp.append(len(ci))
+    return O.CSR(rp, ci, v)
+
+
+def test_frob_loss_zero_at_exact_factor():
+    # tridiagonal A has a fill-free Cholesky factor on tril(A): L L^T = A,
+    # so the loss and its gradient vanish
+    n = 9
+    D = 2.5 * np.eye(n) - np.eye(n, k=1) - np.eye(n, k=-1)
+    A = _csr(D)
+    Lc = np.linalg.cholesky(D)
+    L = _csr(np.where(np.tril(D) != 0, Lc, 0.0))
+    loss, dL = O.frob_loss(A, L)
+    assert loss < 1e-26 and np.abs(dL).max() < 1e-13
+
+
+def test_frob_loss_closed_form_diagonal_factor():
+    # L = c I: ||c^2 I - A||_F^2 = sum_i (c^2 - a_ii)^2 + sum_{i != j} a_ij^2,
+    # dl/dL_ii = 4 ((c^2 I - A) c I)_ii = 4 c (c^2 - a_ii)
+    A = O.assemble(I.fem2d(7, sigma=1.0, seed=2))
+    D = A.dense()
+    c = 1.7
+    L = _csr(np.diag(np.full(A.n, c)))
+    loss, dL = O.frob_loss(A, L)
+    d = np.diag(D)
+    expect = np.sum((c * c - d) ** 2) + np.sum(D ** 2) - np.sum(d ** 2)
+    assert math.isclose(loss, expect, rel_tol=1e-13)
+    assert np.allclose(dL, 4 * c * (c * c - d), rtol=1e-13)
+
+
+def test_frob_loss_includes_fill_in():
+    # the product L L^T of a 2-D FEM factor has entries outside pattern(A)
+    # (two-hop fill); the loss counts them: against the same loss taken on
+    # pattern(A) only it is strictly larger
+    A = O.assemble(I.fem2d(8, sigma=1.0, seed=3))
+    Lic, _ = O.ic0(A)
+    loss, _ = O.frob_loss(A, Lic)
+    P = Lic.dense() @ Lic.dense().T - A.dense()
+    on_pattern = np.sum((P * (A.dense() != 0)) ** 2)
+    assert math.isclose(loss, np.sum(P ** 2), rel_tol=1e-12) and loss > on_pattern * (1 + 1e-6)
+
+
+def test_frob_loss_gradient_central_differences():
+    A = O.assemble(I.fd2d(5, 4, sigma=1.0, seed=4))
+    L0, _ = O.ic0(A)
+    g = np.random.default_rng(2)
+    L = O.CSR(L0.row_ptr, L0.col_idx, L0.val * (1 + 0.2 * g.standard_normal(L0.nnz)))
+    loss, dL = O.frob_loss(A, L)
+    eps = 1e-6
+    for k in range(L.nnz):
+        vp, vm = L.val.copy(), L.val.copy()
+        vp[k] += eps
+        vm[k] -= eps
+        fd = (O.frob_loss(A, O.CSR(L.row_ptr, L.col_idx, vp), False)[0] -
+              O.frob_loss(A, O.CSR(L.row_ptr, L.col_idx, vm), False)[0]) / (2 * eps)
+        assert abs(fd - dL[k]) <= 1e-6 * max(1.0, abs(dL[k]))
+
+
+def test_frob_network_gradient_central_differences():
+    # through the network: the weights' gradient of the mean Frobenius loss
+    # over two pairs (each pair has its own L = f(A, b_p)) matches central
+    # differences; with cfg.loss = 1 the (x, b) data enter only as the input b
+    cfg = I.GnnConfig(n_mp=1, l=2, l_mp=1, h=3, diag_mode=1, loss=1)
+    A = _tiny_system()
+    g = np.random.default_rng(9)
+    B = g.standard_normal((2, A.n))
+    X = g.standard_normal((2, A.n))
+    w = I.gnn_weights(cfg, 3, scale=1.5).astype(np.float64)
+    loss, grad = O.loss_and_grad(cfg, A, X, B, w)
+    Ls = [O.gnn_forward(cfg, A, B[p], w) for p in range(2)]
+    assert math.isclose(loss, np.mean([O.frob_loss(A, L, False)[0] for L in Ls]), rel_tol=1e-13)
+    assert O.loss_and_grad(cfg, A, X + 1.0, B, w, False)[0] == loss
+    eps = 1e-6
+    floor = 1e-3 * np.abs(grad).max()
+    err = 0.0
+    for k in range(len(w)):
+        wp, wm = w.copy(), w.copy()
+        wp[k] += eps
+        wm[k] -= eps
+        fd = (O.loss_and_grad(cfg, A, X, B, wp, False)[0] - O.loss_and_grad(cfg, A, X, B, wm, False)[0]) / (2 * eps)
+        err = max(err, abs(fd - grad[k]) / max(floor, abs(grad[k])))
+    assert err < 1e-6, err
