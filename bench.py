@@ -480,7 +480,7 @@ def run_train(args, rank, world, local):
     from paper_2305_16432_gb300 import inputs as I
     from paper_2305_16432_gb300 import npcg as N
     prec = N.BF16 if args.precision == "bf16" else N.FP32
-    cfg = I.GnnConfig(n_mp=6, l=2, l_mp=2, h=64)
+    cfg = I.GnnConfig(n_mp=6, l=2, l_mp=2, h=64, loss=N.LOSS_FROB if args.loss == "frob" else N.LOSS_AB)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     probs = I.training_mix(32, seed=1000 + 100 * rank)
@@ -517,7 +517,9 @@ def run_train(args, rank, world, local):
                 "value": ms_per_step, "unit": "ms/step", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32+" + args.precision, "data": "synthetic",
-                "config": {"workload": "train_32x8", "n": P.n, "nnz": P.nnz, "systems": 32, "pairs": pairs,
+                "config": {"workload": "train_32x8" + ("_frobenius" if args.loss == "frob" else ""), "n": P.n,
+                           "nnz": P.nnz, "systems": 32, "pairs": pairs,
+                           "loss": "Eq. loss_A (Frobenius)" if args.loss == "frob" else "Eq. loss_Ab",
                            "gnn": "n_mp=6,l=2,l_mp=2,h=64", "l2": "flushed between steps (256 MB write)"},
                 "loss_last": loss, "roofline": None, "cpu_baseline": None, "e2e": None, "clocks": clk}
         print(json.dumps(line), flush=True)
@@ -536,6 +538,8 @@ def main():
     ap.add_argument("--apply", default="fp32", choices=["fp32", "fp64"],
                     help="arithmetic of the L L^T solves inside the FP64 PCG")
     ap.add_argument("--weights", default=None, help="network weights (.npy); default: the workload's own")
+    ap.add_argument("--loss", default="ab", choices=["ab", "frob"],
+                    help="train_32: the method's loss Eq. (loss_Ab) or the Frobenius ablation Eq. (loss_A)")
     ap.add_argument("--x0", action="store_true",
                     help="start PCG from the network's initial guess (weights with an initial-guess head)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

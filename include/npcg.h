@@ -203,7 +203,12 @@ typedef struct {
     int32_t x0_head;     /* 1: the weights end with the initial-guess head
                             (an MLP of depth l, h -> 1, on the final node
                             features; Sec. 4.4 surrogate use), else 0     */
+    int32_t loss;        /* training loss of npcg_loss_and_grad:
+                            NPCG_LOSS_AB (Eq. loss_Ab, the method's) or
+                            NPCG_LOSS_FROB (Eq. loss_A, the Frobenius
+                            ablation); ignored by the forward calls        */
 } npcg_gnn_config;
+enum { NPCG_LOSS_AB = 0, NPCG_LOSS_FROB = 1 };
 
 /* Number of FP32 parameters of the flat weight vector (host out). */
 NPCG_API npcg_status npcg_gnn_nparams(const npcg_gnn_config* cfg, int64_t* out);
@@ -309,7 +314,13 @@ NPCG_API npcg_status npcg_sptrsv_timed(npcg_handle h, npcg_pattern p, int32_t tr
  * cfg->precision NPCG_FP32: FP32 forward and adjoint.  NPCG_BF16 (h = 64):
  * the forward runs on the BF16 tensor cores with FP32 accumulation and the
  * FP32 adjoint is taken at its node / edge states (mixed-precision
- * training with FP32 master weights).  Synchronises.
+ * training with FP32 master weights).
+ * cfg->loss NPCG_LOSS_FROB: the Frobenius loss Eq. (loss_A) instead, mean
+ * over pairs and systems of ||L L^T - A||_F^2 with L = f(A, b_p) (X unused;
+ * the full matrices, fill-in of L L^T included); d/dL = 4 (L L^T - A) L on
+ * the pattern of L, by a product structure built on the first call for the
+ * pattern.  With cfg->x0_head the head's regression to x is added (both
+ * losses).  Synchronises.
  * ------------------------------------------------------------------------ */
 NPCG_API npcg_status npcg_loss_and_grad(npcg_handle h, npcg_pattern p, const double* A_val,
                                int32_t npairs, const double* X, const double* B,

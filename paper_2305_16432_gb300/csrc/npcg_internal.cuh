@@ -145,6 +145,20 @@ struct GnnStore {
     DevBuf<unsigned short> bf;     // BF16 node / edge features (tensor-core path)
 };
 
+// Product structure of L L^T for the Frobenius loss Eq. (loss_A): the
+// lower triangle (with diagonal) of pattern(L L^T), per entry the pairs of L
+// entries whose product it sums, its A entry, and per L entry the (L entry,
+// product entry) pairs of (R L).  Built on first use.
+struct FrobLayout {
+    bool built = false;
+    int64_t nS = 0;
+    DevBuf<int32_t> sptr, s2a, srow;      // [nS + 1], [nS], [nS] (srow < 0: off-diagonal entry of row -srow - 1)
+    DevBuf<int2> spairs;                  // (a, b): L_a L_b
+    DevBuf<int32_t> gptr;                 // [nnzL + 1]
+    DevBuf<int2> gpairs;                  // (b, s): R_s L_b
+    DevBuf<double> R;                     // [nS]
+};
+
 struct Pattern {
     Handle* h = nullptr;
     int64_t n = 0, nnz = 0, nnzL = 0;
@@ -183,6 +197,7 @@ struct Pattern {
     cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};
     int graph_mode[4] = {0, 0, 0, 0};
     GnnStore gnn;
+    FrobLayout frob;
     ~Pattern();
 };
 

@@ -13,6 +13,7 @@
 // activations, and the weight gradients are reduced from those by a split
 // reduction kernel.  FP32 throughout the network; the loss part is FP64.
 #include <algorithm>
+#include <array>
 #include <vector>
 
 #include <cuda_bf16.h>
@@ -904,6 +905,56 @@ __global__ void k_enc_inputs(int64_t n, int64_t nnz, const double* b, const doub
 }
 
 // ------------------------------------------------------------ driver
+// Frobenius loss Eq. (loss_A): R = L L^T - A on the lower triangle of
+// pattern(L L^T), R_e = sum of its L products (k ascending) - A_e, and the
+// system's loss += w_e R_e^2 (w = 1 on the diagonal, 2 off it: R is
+// symmetric and both triangles count)
+__global__ void k_frob_R(int64_t nS, const int32_t* sptr, const int2* spairs, const int32_t* s2a,
+                         const int32_t* srow, const int32_t* row_sys, const double* Lv, const double* A_val,
+                         double* R, double* loss_sys) {
+    const unsigned full = 0xffffffffu;
+    for (int64_t e0 = blockIdx.x * (int64_t)blockDim.x; e0 < nS; e0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = e0 + threadIdx.x;
+        double v = 0.0;
+        int sys = -1;
+        if (e < nS) {
+            double sum = 0.0;
+            for (int q = sptr[e]; q < sptr[e + 1]; ++q) {
+                const int2 ab = spairs[q];
+                sum = fma(Lv[ab.x], Lv[ab.y], sum);
+            }
+            const int a = s2a[e];
+            const double r = sum - (a >= 0 ? A_val[a] : 0.0);
+            R[e] = r;
+            const int sr = srow[e];
+            sys = row_sys[sr >= 0 ? sr : -sr - 1];
+            v = (sr >= 0 ? 1.0 : 2.0) * r * r;
+        }
+        const int s0 = __shfl_sync(full, sys, 0);
+        if (__all_sync(full, sys == s0 || sys < 0)) {
+            for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(full, v, o);
+            if ((threadIdx.x & 31) == 0 && s0 >= 0) atomicAdd(&loss_sys[s0], v);
+        } else if (sys >= 0) {
+            atomicAdd(&loss_sys[sys], v);
+        }
+    }
+}
+
+// dL_a = c2 (R L)_a: for L entry a = (i, k), the sum over the entries b of
+// column k (rows j ascending) of R_(i,j) L_b
+__global__ void k_frob_dL(int64_t nnzL, const int32_t* gptr, const int2* gpairs, const double* Lv,
+                          const double* R, double c2, double* dL) {
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < nnzL;
+         a += (int64_t)gridDim.x * blockDim.x) {
+        double sum = 0.0;
+        for (int q = gptr[a]; q < gptr[a + 1]; ++q) {
+            const int2 bs = gpairs[q];
+            sum = fma(R[bs.y], Lv[bs.x], sum);
+        }
+        dL[a] = c2 * sum;
+    }
+}
+
 struct TrainBufs {
     std::vector<float*> V, E, AGG;
     float *S, *dS, *dEc, *dEp, *dVc, *dVp, *Gr, *Gc, *dAgg, *xv, *xe;
@@ -1007,11 +1058,19 @@ npcg_status train_pair(Handle* h, Pattern* P, const double* A_val, const double*
     gb.diag_mode = cfg->diag_mode;
     NPCG_TRY(gnn_assemble_L(h, P, gb, T.Lv));
     // ---- loss and its adjoint in L
-    k_lt_mv<<<grid1(h, n), 256, 0, h->stream>>>(n, P->rp.p, P->ci.p, P->mirror.p, P->a2l.p, T.Lv, x, T.y);
-    k_l_mv_res<<<grid1(h, n), 256, 0, h->stream>>>(n, P->Lrp.p, P->Lci.p, T.Lv, T.y, b, P->row_sys.p, T.r,
-                                                  T.loss_sys);
-    k_lt_mv<<<grid1(h, n), 256, 0, h->stream>>>(n, P->rp.p, P->ci.p, P->mirror.p, P->a2l.p, T.Lv, T.r, T.w);
-    k_dL<<<grid1(h, nnzL), 256, 0, h->stream>>>(nnzL, P->l2a.p, P->edge_row.p, P->ci.p, c, T.r, T.y, x, T.w, T.dL);
+    if (cfg->loss == NPCG_LOSS_FROB) {
+        const FrobLayout& F = P->frob;
+        k_frob_R<<<grid1(h, F.nS), 256, 0, h->stream>>>(F.nS, F.sptr.p, F.spairs.p, F.s2a.p, F.srow.p,
+                                                        P->row_sys.p, T.Lv, A_val, F.R.p, T.loss_sys);
+        k_frob_dL<<<grid1(h, nnzL), 256, 0, h->stream>>>(nnzL, F.gptr.p, F.gpairs.p, T.Lv, F.R.p, 2.0 * c, T.dL);
+    } else {
+        k_lt_mv<<<grid1(h, n), 256, 0, h->stream>>>(n, P->rp.p, P->ci.p, P->mirror.p, P->a2l.p, T.Lv, x, T.y);
+        k_l_mv_res<<<grid1(h, n), 256, 0, h->stream>>>(n, P->Lrp.p, P->Lci.p, T.Lv, T.y, b, P->row_sys.p, T.r,
+                                                      T.loss_sys);
+        k_lt_mv<<<grid1(h, n), 256, 0, h->stream>>>(n, P->rp.p, P->ci.p, P->mirror.p, P->a2l.p, T.Lv, T.r, T.w);
+        k_dL<<<grid1(h, nnzL), 256, 0, h->stream>>>(nnzL, P->l2a.p, P->edge_row.p, P->ci.p, c, T.r, T.y, x, T.w,
+                                                    T.dL);
+    }
     k_dS<<<grid1(h, nnz), 256, 0, h->stream>>>(nnz, P->edge_row.p, P->ci.p, P->mirror.p, P->a2l.p, P->row_sys.p,
                                               sc, T.S, T.dL, A_val, P->adiag.p, cfg->diag_mode, T.dS);
     NPCG_CUDA(h, cudaGetLastError());
@@ -1113,10 +1172,104 @@ __global__ void k_adam(int64_t n, float* w, const float* g, float* m, float* v, 
 
 npcg_status gnn_scales_run(Handle* h, Pattern* P, const double* A_val, const double* b, double* sc);
 
+// Builds the product structure of L L^T (host, once per pattern): the
+// entries (i, j), j <= i, of pattern(L L^T) row by row with their product
+// pairs (L_ik, L_jk) in ascending k, the A entry of each, and for every L
+// entry (i, k) the pairs (L_jk, entry (max(i,j), min(i,j))) over the rows j
+// of column k in ascending order.
+static npcg_status frob_build(Handle* h, Pattern* P) {
+    FrobLayout& F = P->frob;
+    if (F.built) return NPCG_OK;
+    const int64_t n = P->n, nnzL = P->nnzL, nnz = P->nnz;
+    std::vector<int32_t> Lrp(n + 1), Lci(nnzL), rp(n + 1), ci(nnz);
+    NPCG_CUDA(h, cudaMemcpyAsync(Lrp.data(), P->Lrp.p, (n + 1) * 4, cudaMemcpyDeviceToHost, h->stream));
+    NPCG_CUDA(h, cudaMemcpyAsync(Lci.data(), P->Lci.p, nnzL * 4, cudaMemcpyDeviceToHost, h->stream));
+    NPCG_CUDA(h, cudaMemcpyAsync(rp.data(), P->rp.p, (n + 1) * 4, cudaMemcpyDeviceToHost, h->stream));
+    NPCG_CUDA(h, cudaMemcpyAsync(ci.data(), P->ci.p, nnz * 4, cudaMemcpyDeviceToHost, h->stream));
+    NPCG_CUDA(h, cudaStreamSynchronize(h->stream));
+    // columns of L: entries in ascending row order
+    std::vector<int32_t> cptr(n + 1, 0), cent(nnzL), Lrow(nnzL);
+    for (int64_t i = 0; i < n; ++i)
+        for (int32_t a = Lrp[i]; a < Lrp[i + 1]; ++a) { cptr[Lci[a] + 1]++; Lrow[a] = (int32_t)i; }
+    for (int64_t k = 0; k < n; ++k) cptr[k + 1] += cptr[k];
+    {
+        std::vector<int32_t> fill(cptr.begin(), cptr.end() - 1);
+        for (int64_t i = 0; i < n; ++i)
+            for (int32_t a = Lrp[i]; a < Lrp[i + 1]; ++a) cent[fill[Lci[a]]++] = a;
+    }
+    // entries of the lower triangle of L L^T, row by row
+    std::vector<int32_t> srp(n + 1, 0), scol, sptr(1, 0), s2a, srow;
+    std::vector<int2> spairs;
+    std::vector<std::array<int32_t, 3>> cand;     // (j, a, b)
+    for (int64_t i = 0; i < n; ++i) {
+        cand.clear();
+        for (int32_t a = Lrp[i]; a < Lrp[i + 1]; ++a) {
+            const int32_t k = Lci[a];
+            for (int32_t q = cptr[k]; q < cptr[k + 1]; ++q) {
+                const int32_t b = cent[q];
+                if (Lrow[b] <= i) cand.push_back({Lrow[b], a, b});
+            }
+        }
+        std::sort(cand.begin(), cand.end());
+        for (size_t t = 0; t < cand.size();) {
+            const int32_t j = cand[t][0];
+            for (; t < cand.size() && cand[t][0] == j; ++t) spairs.push_back(make_int2(cand[t][1], cand[t][2]));
+            scol.push_back(j);
+            sptr.push_back((int32_t)spairs.size());
+            const int32_t* lo = ci.data() + rp[i];
+            const int32_t* hi = ci.data() + rp[i + 1];
+            const int32_t* f = std::lower_bound(lo, hi, j);
+            s2a.push_back(f != hi && *f == j ? (int32_t)(f - ci.data()) : -1);
+            srow.push_back(j == i ? (int32_t)i : (int32_t)(-i - 1));
+        }
+        srp[i + 1] = (int32_t)scol.size();
+    }
+    auto sidx = [&](int32_t p, int32_t q) {       // entry (p, q), q <= p
+        const int32_t* lo = scol.data() + srp[p];
+        const int32_t* hi = scol.data() + srp[p + 1];
+        return (int32_t)(std::lower_bound(lo, hi, q) - scol.data());
+    };
+    // (R L) pairs per L entry
+    std::vector<int32_t> gptr(nnzL + 1, 0);
+    std::vector<int2> gpairs;
+    for (int64_t a = 0; a < nnzL; ++a) {
+        const int32_t i = Lrow[a], k = Lci[a];
+        for (int32_t q = cptr[k]; q < cptr[k + 1]; ++q) {
+            const int32_t b = cent[q], j = Lrow[b];
+            gpairs.push_back(make_int2(b, i >= j ? sidx(i, j) : sidx(j, i)));
+        }
+        gptr[a + 1] = (int32_t)gpairs.size();
+    }
+    if (spairs.size() >= (size_t)INT32_MAX || gpairs.size() >= (size_t)INT32_MAX)
+        return set_error(h, NPCG_EINVAL, "pattern too large for the Frobenius loss structure");
+    F.nS = (int64_t)scol.size();
+    NPCG_CUDA(h, F.sptr.alloc(sptr.size()));
+    NPCG_CUDA(h, F.s2a.alloc(std::max<size_t>(s2a.size(), 1)));
+    NPCG_CUDA(h, F.srow.alloc(std::max<size_t>(srow.size(), 1)));
+    NPCG_CUDA(h, F.spairs.alloc(std::max<size_t>(spairs.size(), 1)));
+    NPCG_CUDA(h, F.gptr.alloc(gptr.size()));
+    NPCG_CUDA(h, F.gpairs.alloc(std::max<size_t>(gpairs.size(), 1)));
+    NPCG_CUDA(h, F.R.alloc(std::max<int64_t>(F.nS, 1)));
+    NPCG_CUDA(h, cudaMemcpyAsync(F.sptr.p, sptr.data(), sptr.size() * 4, cudaMemcpyHostToDevice, h->stream));
+    NPCG_CUDA(h, cudaMemcpyAsync(F.s2a.p, s2a.data(), s2a.size() * 4, cudaMemcpyHostToDevice, h->stream));
+    NPCG_CUDA(h, cudaMemcpyAsync(F.srow.p, srow.data(), srow.size() * 4, cudaMemcpyHostToDevice, h->stream));
+    NPCG_CUDA(h, cudaMemcpyAsync(F.spairs.p, spairs.data(), spairs.size() * sizeof(int2), cudaMemcpyHostToDevice,
+                                 h->stream));
+    NPCG_CUDA(h, cudaMemcpyAsync(F.gptr.p, gptr.data(), gptr.size() * 4, cudaMemcpyHostToDevice, h->stream));
+    NPCG_CUDA(h, cudaMemcpyAsync(F.gpairs.p, gpairs.data(), gpairs.size() * sizeof(int2), cudaMemcpyHostToDevice,
+                                 h->stream));
+    NPCG_CUDA(h, cudaStreamSynchronize(h->stream));
+    F.built = true;
+    return NPCG_OK;
+}
+
 npcg_status loss_grad_run(Handle* h, Pattern* P, const double* A_val, int npairs, const double* X,
                           const double* B, const npcg_gnn_config* cfg, const float* w, double* loss_out,
                           float* grad) {
     NPCG_TRY(gnn_check_config(h, cfg));
+    if (cfg->loss != NPCG_LOSS_AB && cfg->loss != NPCG_LOSS_FROB)
+        return set_error(h, NPCG_EINVAL, "loss must be NPCG_LOSS_AB or NPCG_LOSS_FROB");
+    if (cfg->loss == NPCG_LOSS_FROB) NPCG_TRY(frob_build(h, P));
     if (cfg->precision == NPCG_BF16 && cfg->h != 64)
         return set_error(h, NPCG_EINVAL, "the BF16 tensor-core forward needs hidden width h = 64");
     const int H = cfg->h, nmp = cfg->n_mp;

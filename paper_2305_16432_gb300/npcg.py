@@ -23,6 +23,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libnpcg.so")
 NPCG_OK, NPCG_EINVAL, NPCG_ENOMEM, NPCG_ECUDA, NPCG_ENOTSPD, NPCG_EBREAKDOWN, NPCG_EMAXITER, NPCG_ETIMEOUT = range(8)
 FD, FEM = 0, 1
 FP32, BF16 = 0, 1
+LOSS_AB, LOSS_FROB = 0, 1
 PREC_NONE, PREC_JACOBI, PREC_LLT, PREC_LLT32 = 0, 1, 2, 3
 METHOD_GNN, METHOD_IC0, METHOD_JACOBI, METHOD_CG, METHOD_SGS = 0, 1, 2, 3, 4
 TRSV_AUTO, TRSV_SYNCFREE, TRSV_LEVELSYNC, TRSV_LEVELFLAG = 0, 1, 2, 3
@@ -50,7 +51,7 @@ class _Info(C.Structure):
 
 class _Cfg(C.Structure):
     _fields_ = [("n_mp", C.c_int32), ("l", C.c_int32), ("l_mp", C.c_int32), ("h", C.c_int32),
-                ("diag_mode", C.c_int32), ("precision", C.c_int32), ("x0_head", C.c_int32)]
+                ("diag_mode", C.c_int32), ("precision", C.c_int32), ("x0_head", C.c_int32), ("loss", C.c_int32)]
 
 
 class _Stats(C.Structure):
@@ -251,7 +252,8 @@ def analyse(row_ptr, col_idx, sys_ptr=None, h: Handle | None = None) -> Pattern:
 
 # ------------------------------------------------------------------ factors
 def _cfg(cfg: I.GnnConfig, precision=FP32):
-    return _Cfg(cfg.n_mp, cfg.l, cfg.l_mp, cfg.h, cfg.diag_mode, precision, int(getattr(cfg, "x0_head", 0)))
+    return _Cfg(cfg.n_mp, cfg.l, cfg.l_mp, cfg.h, cfg.diag_mode, precision, int(getattr(cfg, "x0_head", 0)),
+                int(getattr(cfg, "loss", 0)))
 
 
 def gnn_nparams(cfg: I.GnnConfig) -> int:

@@ -220,6 +220,8 @@ def main():
     ap.add_argument("--sizes3d", default="", help="comma-separated grid sides of the 3-D FD training groups")
     ap.add_argument("--sigma3d", type=float, default=1.0, help="GRF sigma of the 3-D groups")
     ap.add_argument("--corr3d", type=float, default=0.1, help="GRF correlation length of the 3-D groups")
+    ap.add_argument("--loss", default="ab", choices=["ab", "frob"],
+                    help="Eq. (loss_Ab) (the method) or the Frobenius loss Eq. (loss_A) (ablation)")
     ap.add_argument("--init", default=None, help="start from these weights (same network shape)")
     ap.add_argument("--heat", action="store_true",
                     help="2-D systems are implicit heat steps M + tau K with Dirichlet arcs")
@@ -227,7 +229,8 @@ def main():
                     help="weights of a trained network: add the initial-guess head and train it alone")
     ap.add_argument("--out", default=os.path.join(os.path.dirname(__file__), "weights", "gnn_6x64.npy"))
     args = ap.parse_args()
-    cfg = I.GnnConfig(n_mp=args.n_mp, l=2, l_mp=2, h=args.h, diag_mode=args.diag_mode)
+    cfg = I.GnnConfig(n_mp=args.n_mp, l=2, l_mp=2, h=args.h, diag_mode=args.diag_mode,
+                      loss=1 if args.loss == "frob" else 0)
     from . import build as B
     B.build()
     from . import npcg as N
@@ -264,6 +267,7 @@ def main():
     np.save(args.out, _np(w).astype(np.float32))
     meta = {"config": {"n_mp": cfg.n_mp, "l": cfg.l, "l_mp": cfg.l_mp, "h": cfg.h, "diag_mode": cfg.diag_mode,
                        "x0_head": cfg.x0_head},
+            "loss": "Eq. loss_A (Frobenius)" if cfg.loss else "Eq. loss_Ab",
             "train": {"steps": args.steps, "lr": args.lr, "lr_final": args.lr_final, "schedule": "cosine",
                       "batch": "8 systems x 2 pairs",
                       "selection": "checkpoint with the fewest validation PCG iterations",

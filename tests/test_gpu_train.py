@@ -163,3 +163,55 @@ def test_loss_and_grad_x0_head(N, prec, tl, tg):
     gg = gg.cpu().numpy().astype(np.float64)
     assert abs(lg - lo) <= tl * abs(lo)
     assert np.linalg.norm(gg - go) / np.linalg.norm(go) <= tg
+
+
+@pytest.mark.parametrize("cfg,prob", [
+    (I.GnnConfig(n_mp=2, l=2, l_mp=2, h=16, diag_mode=1, loss=1), I.fem2d(9, sigma=1.0, seed=21)),
+    (I.GnnConfig(n_mp=2, l=2, l_mp=2, h=32, diag_mode=0, loss=1), I.fd2d(8, 7, sigma=1.0, seed=22)),
+    (I.GnnConfig(n_mp=1, l=2, l_mp=2, h=64, diag_mode=1, loss=1), I.heat2d(12, seed=23)),
+])
+def test_frobenius_loss_and_grad_parity(N, cfg, prob):
+    """The Frobenius loss Eq. (loss_A), fill-in of L L^T included, and its
+    gradient through the network against the oracle (the FP32 bars)."""
+    om, ph = I.grf_features(prob)
+    Ao = O.assemble(prob, om, ph)
+    rp, ci, v = N.assemble_system(prob, om, ph)
+    P = N.analyse(rp, ci)
+    X, B = _pairs(Ao, 2, 61)
+    w = I.gnn_weights(cfg, 4, scale=1.5)
+    lo, go = O.loss_and_grad(cfg, Ao, X, B, w.astype(np.float64))
+    lg, gg = N.loss_and_grad(P, v, _gpu(X), _gpu(B), cfg, _gpu(w, torch.float32))
+    gg = gg.cpu().numpy().astype(np.float64)
+    assert abs(lg - lo) <= 1e-5 * abs(lo)
+    assert np.linalg.norm(gg - go) / np.linalg.norm(go) <= 1e-4
+
+
+def test_frobenius_loss_batched_is_mean_over_systems(N):
+    cfg = I.GnnConfig(n_mp=2, l=2, l_mp=2, h=16, diag_mode=1, loss=1)
+    probs = [I.fem2d(8, sigma=1.0, seed=24), I.fd2d(7, 5, sigma=1.0, seed=25)]
+    As, rps, cis, vs = [], [], [], []
+    for p in probs:
+        Ao = O.assemble(p)
+        As.append(Ao)
+    off, sys_ptr = 0, [0]
+    for Ao in As:
+        cis.append(Ao.col_idx + off)
+        vs.append(Ao.val)
+        off += Ao.n
+        sys_ptr.append(off)
+    nnz_off = np.cumsum([0] + [a.nnz for a in As])
+    rp_cat = np.concatenate([a.row_ptr[:-1] + nnz_off[k] for k, a in enumerate(As)] + [[nnz_off[-1]]])
+    P = N.analyse(_gpu(rp_cat, torch.int32), _gpu(np.concatenate(cis), torch.int32), sys_ptr)
+    B = np.concatenate([I.rhs(a.n, 70 + k, count=2) for k, a in enumerate(As)], axis=1)
+    X = np.zeros_like(B)
+    w = I.gnn_weights(cfg, 5, scale=1.5)
+    lg, gg = N.loss_and_grad(P, _gpu(np.concatenate(vs)), _gpu(X), _gpu(B), cfg, _gpu(w, torch.float32))
+    los, gos = [], []
+    for k, Ao in enumerate(As):
+        Bk = B[:, sys_ptr[k]:sys_ptr[k + 1]]
+        l, g = O.loss_and_grad(cfg, Ao, np.zeros_like(Bk), Bk, w.astype(np.float64))
+        los.append(l)
+        gos.append(g)
+    lo, go = np.mean(los), np.mean(gos, axis=0)
+    assert abs(lg - lo) <= 1e-5 * abs(lo)
+    assert np.linalg.norm(gg.cpu().numpy() - go) / np.linalg.norm(go) <= 1e-4
