@@ -1,6 +1,7 @@
-"""The N > 1 path of bench.py on the CPU (gloo, world size 2): each rank
-solves its own seeded systems (no data-path collective), the job time is the
-slowest rank's, and the whole-job value counts every rank's systems."""
+"""The N > 1 paths of bench.py on the CPU (gloo, world size 2): for solves
+each rank takes its own seeded systems (no data-path collective), the job
+time is the slowest rank's, and the whole-job value counts every rank's
+systems; for training the ranks average their gradients before Adam."""
 import os
 import socket
 import sys
@@ -48,3 +49,33 @@ def test_two_ranks_shard_and_reduce():
     assert n0 == n1 == 256
     assert ms0 == ms1 == 150.0                          # max over ranks
     assert v0 == v1 == pytest.approx(150.0 / (256 * 2))
+
+
+def _train_rank(rank, world, port, out):
+    # data-parallel training step: each rank's gradient (the mean over its
+    # own systems) is averaged over the ranks before Adam, so the weights
+    # stay identical on every rank
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import torch
+    import bench
+    import oracle as O
+    g = torch.arange(6, dtype=torch.float64) * (1.0 + rank)      # rank-dependent gradients
+    bench.grad_allreduce_mean_(g, world)
+    w = np.linspace(-1.0, 1.0, 6)
+    m, v = np.zeros(6), np.zeros(6)
+    O.adam(w, g.numpy().copy(), m, v, 1)
+    out[rank] = (g.numpy().tolist(), w.tolist())
+    dist.destroy_process_group()
+
+
+def test_two_ranks_average_gradients():
+    world, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as m:
+        out = m.dict()
+        mp.start_processes(_train_rank, args=(world, port, out), nprocs=world, join=True, start_method="spawn")
+        res = dict(out)
+    (g0, w0), (g1, w1) = res[0], res[1]
+    assert g0 == g1 == pytest.approx([1.5 * k for k in range(6)])
+    assert w0 == w1
