@@ -407,7 +407,7 @@ def run_solve(args, rank, world, local):
     # SpTRSV bytes per launch: index + value per L entry, row pointer, rhs + solution
     trsv_bytes = (8 if apply32 else 12) * P.nnz_L + 4 * (P.n + 1) + 16 * P.n
     achieved = trsv_bytes / (trsv_ms * 1e-3) / 1e9
-    trsv_kernel = {N.TRSV_LEVELSYNC: "k_trsv_cta",
+    trsv_kernel = {N.TRSV_LEVELSYNC: "k_trsv_cta", N.TRSV_LEVELSPLIT: "k_trsv_split",
                    N.TRSV_LEVELFLAG: "k_trsv_flag" if apply32 else "k_trsv_cta"}.get(P.trsv_mode, "k_trsv")
     # DRAM bytes of one forward launch from an ncu capture of this kernel
     traffic = None
@@ -440,7 +440,7 @@ def run_solve(args, rank, world, local):
     # PCG: 4 factor loads, init, preconditioner apply, r^T z, per graph trip 2
     # iterations (SpMV, update, r^T z and the apply) + the loop condition, stats;
     # the level-synchronous apply is 2 solves + 2 gathers, the sync-free one 2 solves
-    apply = 4 if P.trsv_mode in (N.TRSV_LEVELSYNC, N.TRSV_LEVELFLAG) else 2
+    apply = 4 if P.trsv_mode in (N.TRSV_LEVELSYNC, N.TRSV_LEVELFLAG, N.TRSV_LEVELSPLIT) else 2
     trips = max(1, math.ceil(max(it_l) / 2))
     pcg_launches = 4 + 1 + apply + 1 + (2 * (3 + apply) + 1) * trips + 1
     launches = (gnn_launches + pcg_launches) * args.steps
@@ -489,7 +489,8 @@ def run_solve(args, rank, world, local):
                         "sgs_ms_per_system": float(np.mean(ms_g)) / nsys,
                         "sgs_iters": [x["iters"] for x in st_g] if nsys > 1 else st_g[0]["iters"],
                         "wall_s_timed": wall,
-                        "trsv_design": {N.TRSV_LEVELSYNC: "levelsync", N.TRSV_LEVELFLAG: "levelflag"}.get(
+                        "trsv_design": {N.TRSV_LEVELSYNC: "levelsync", N.TRSV_LEVELFLAG: "levelflag",
+                                        N.TRSV_LEVELSPLIT: "levelsplit"}.get(
                             P.trsv_mode, "syncfree"),
                         "trsv_tuned_ms_fwd_bwd": P.tuned_ms},
             "roofline": {"kernel": trsv_kernel + " (forward SpTRSV, " + args.apply + ")", "bound": "hbm",

@@ -145,9 +145,13 @@ NPCG_API npcg_status npcg_pattern_free(npcg_pattern p);
  *     each window slot carries its row's position next to the value and a
  *     row polls its dependencies' slots (FP32 solves, NPCG_PREC_LLT32; FP64
  *     solves use NPCG_TRSV_LEVELSYNC).  Available when the window also
- *     covers how far one warp can run ahead of another.
+ *     covers how far one warp can run ahead of another;
+ *   NPCG_TRSV_LEVELSPLIT: the level-synchronous design with the step
+ *     bookkeeping on separate warps: operand warps stage step k+1 while
+ *     compute warps solve step k (one system per SM).
  * npcg_analyse times the designs on the pattern and keeps the fastest. */
-enum { NPCG_TRSV_AUTO = 0, NPCG_TRSV_SYNCFREE = 1, NPCG_TRSV_LEVELSYNC = 2, NPCG_TRSV_LEVELFLAG = 3 };
+enum { NPCG_TRSV_AUTO = 0, NPCG_TRSV_SYNCFREE = 1, NPCG_TRSV_LEVELSYNC = 2, NPCG_TRSV_LEVELFLAG = 3,
+       NPCG_TRSV_LEVELSPLIT = 4 };
 
 typedef struct {
     int64_t n, nnz, nnz_L;
@@ -157,11 +161,13 @@ typedef struct {
     float tuned_ms_syncfree;      /* measured forward + backward FP32 solve, ms */
     float tuned_ms_levelsync;     /* (0 when the design does not apply)         */
     float tuned_ms_levelflag;
+    float tuned_ms_levelsplit;
 } npcg_pattern_info;
 NPCG_API npcg_status npcg_pattern_get_info(npcg_pattern p, npcg_pattern_info* out);  /* host out */
 /* Overrides the tuned design (NPCG_TRSV_AUTO restores the tuned choice).
- * NPCG_TRSV_LEVELSYNC / _LEVELFLAG return NPCG_EINVAL when the layout does
- * not fit (or, for _LEVELFLAG, its window does not cover the drift). */
+ * NPCG_TRSV_LEVELSYNC / _LEVELFLAG / _LEVELSPLIT return NPCG_EINVAL when the
+ * layout does not fit (for _LEVELFLAG: its window does not cover the drift;
+ * for _LEVELSPLIT: no ring of two stages fits beside the staging slots). */
 NPCG_API npcg_status npcg_pattern_set_trsv(npcg_pattern p, int32_t mode);
 
 /* Copies of the analysis results (device arrays, caller-allocated):

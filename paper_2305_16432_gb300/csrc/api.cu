@@ -130,10 +130,12 @@ npcg_status npcg_pattern_get_info(npcg_pattern p, npcg_pattern_info* out) {
     out->nlev_fwd = p->fwd.nlev;
     out->nlev_bwd = p->bwd.nlev;
     out->trsv_mode = p->trsv_mode != kTrsvCta ? NPCG_TRSV_SYNCFREE
-                   : p->cta_flag ? NPCG_TRSV_LEVELFLAG : NPCG_TRSV_LEVELSYNC;
+                   : p->cta_flag ? NPCG_TRSV_LEVELFLAG
+                   : p->cta_split ? NPCG_TRSV_LEVELSPLIT : NPCG_TRSV_LEVELSYNC;
     out->tuned_ms_syncfree = p->tune_ms[0];
     out->tuned_ms_levelsync = p->tune_ms[1];
     out->tuned_ms_levelflag = p->tune_ms[2];
+    out->tuned_ms_levelsplit = p->tune_ms[3];
     return NPCG_OK;
 }
 
@@ -144,13 +146,19 @@ npcg_status npcg_pattern_set_trsv(npcg_pattern p, int32_t mode) {
     } else if (mode == NPCG_TRSV_SYNCFREE) {
         p->trsv_mode = kTrsvSyncFree;
         p->cta_flag = false;
-    } else if (mode == NPCG_TRSV_LEVELSYNC || mode == NPCG_TRSV_LEVELFLAG) {
+        p->cta_split = false;
+    } else if (mode == NPCG_TRSV_LEVELSYNC || mode == NPCG_TRSV_LEVELFLAG || mode == NPCG_TRSV_LEVELSPLIT) {
         if (!p->cfwd.built || cta_stages(p->cfwd) < 2 || cta_stages(p->cbwd) < 2)
             return set_error(p->h, NPCG_EINVAL, "level-synchronous layout does not fit shared memory");
         if (mode == NPCG_TRSV_LEVELFLAG && !(p->cfwd.flag_ok && p->cbwd.flag_ok))
             return set_error(p->h, NPCG_EINVAL, "flag-synchronised solve: the window does not cover its drift");
+        if (mode == NPCG_TRSV_LEVELSPLIT &&
+            !(p->cfwd.split_stages[0] >= 2 && p->cfwd.split_stages[1] >= 2 && p->cbwd.split_stages[0] >= 2 &&
+              p->cbwd.split_stages[1] >= 2))
+            return set_error(p->h, NPCG_EINVAL, "split-role solve: the layout does not fit beside the staging slots");
         p->trsv_mode = kTrsvCta;
         p->cta_flag = mode == NPCG_TRSV_LEVELFLAG;
+        p->cta_split = mode == NPCG_TRSV_LEVELSPLIT;
     } else {
         return set_error(p->h, NPCG_EINVAL, "unknown triangular-solve mode");
     }

@@ -131,6 +131,7 @@ struct CtaLayout {
     int stage_cap[3] = {0, 0, 0};
     int nstages[3] = {0, 0, 0};
     bool flag_ok = false;          // the window also covers the drift of the flag-synchronised kernel
+    int split_stages[2] = {0, 0};  // ring stages of the split-role kernel per value type (0: not offered)
 };
 
 enum TrsvMode : int { kTrsvAuto = 0, kTrsvSyncFree = 1, kTrsvCta = 2 };
@@ -175,8 +176,9 @@ struct Pattern {
     TriLayout fwd, bwd;            // L y = r and L^T z = y
     CtaLayout cfwd, cbwd;          // level-synchronous layouts
     int trsv_mode = kTrsvSyncFree; // chosen by the autotuner
-    float tune_ms[3] = {0.f, 0.f, 0.f}; // measured fwd+bwd time: sync-free, level barrier, level flags
+    float tune_ms[4] = {0.f, 0.f, 0.f, 0.f}; // measured fwd+bwd time: sync-free, level barrier, level flags, split roles
     bool cta_flag = false;         // level-ordered solves use the flag-synchronised FP32 kernel
+    bool cta_split = false;        // level-ordered solves use the split-role kernel
     DevBuf<double> r_cf, y_cb, yglob;  // rhs in processing order, window backing
     DevBuf<double> yq;             // solution of a level-synchronous solve in processing order
     // reduction chunks

@@ -591,7 +591,7 @@ void enqueue_iteration(Handle* h, cudaStream_t s, Pattern* P, const PcgArgs& a, 
 
 npcg_status build_graph(Handle* h, Pattern* P, int precond) {
     // the graph is specific to the triangular-solve design
-    const int mode_key = P->trsv_mode | (P->cta_flag ? 16 : 0);
+    const int mode_key = P->trsv_mode | (P->cta_flag ? 16 : 0) | (P->cta_split ? 32 : 0);
     if (P->graph[precond] && P->graph_mode[precond] == mode_key) return NPCG_OK;
     if (P->graph[precond]) { cudaGraphExecDestroy(P->graph[precond]); P->graph[precond] = nullptr; }
     PcgArgs a = pcg_args(P, precond);
@@ -734,13 +734,16 @@ npcg_status trsv_autotune(Handle* h, Pattern* P) {
     NPCG_TRY(factor_load(h, P, L.p));
     // sync-free, level order with a barrier per step, level order with
     // per-slot flags (FP32 solves; when the window covers its drift)
-    const int modes[3] = {kTrsvSyncFree, kTrsvCta, kTrsvCta};
+    const int modes[4] = {kTrsvSyncFree, kTrsvCta, kTrsvCta, kTrsvCta};
     const bool flag_ok = P->cfwd.flag_ok && P->cbwd.flag_ok;
+    const bool split_ok = P->cfwd.split_stages[1] >= 2 && P->cbwd.split_stages[1] >= 2;
     P->tune_ms[2] = 0.f;
-    for (int m = 0; m < 3; ++m) {
-        if (m == 2 && !flag_ok) break;
+    P->tune_ms[3] = 0.f;
+    for (int m = 0; m < 4; ++m) {
+        if ((m == 2 && !flag_ok) || (m == 3 && !split_ok)) continue;
         P->trsv_mode = modes[m];
         P->cta_flag = m == 2;
+        P->cta_split = m == 3;
         double best = 1e30;
         for (int rep = 0; rep < 3; ++rep) {
             double f = 0.0, b = 0.0;
@@ -757,10 +760,11 @@ npcg_status trsv_autotune(Handle* h, Pattern* P) {
 // the fastest measured design (a zero time: the design does not apply)
 void trsv_pick_tuned(Pattern* P) {
     int m = 0;
-    for (int k = 1; k < 3; ++k)
+    for (int k = 1; k < 4; ++k)
         if (P->tune_ms[k] > 0.f && P->tune_ms[k] < P->tune_ms[m]) m = k;
     P->trsv_mode = m == 0 ? kTrsvSyncFree : kTrsvCta;
     P->cta_flag = m == 2;
+    P->cta_split = m == 3;
 }
 
 npcg_status spmv_run(Handle* h, Pattern* P, const double* A_val, const double* x, double* y) {

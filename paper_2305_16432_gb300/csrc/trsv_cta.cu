@@ -403,6 +403,206 @@ __global__ void __launch_bounds__(kCtaThreads, 1) k_trsv_cta(CtaDev D, const T* 
     }
 }
 
+// ------------------------------------------------------------ split-role variant
+// The same layout, ring and window, with the two instruction streams of a
+// step on different warps: eight operand warps walk the step headers and
+// stage step k+1's operands (dependency slots, factor values, reciprocal
+// diagonal, right-hand side) into a double-buffered shared-memory slot while
+// eight compute warps solve step k from the slot staged during step k-1.
+// One named barrier per step (with the AND of the operand warps' waits)
+// separates the steps; a compute warp's step is then five independent slot
+// loads, the window loads, four FMAs and the stores.  Chunks are released
+// by the compute warps once the last step of a chunk is solved (its extra
+// dependencies are read from the ring during that step).
+constexpr int kSplitThreads = 2 * kCtaRows + 32;
+constexpr int kMetaInts = 8;   // {nrows, q0, np, width, header offset, values offset, release stage, last}
+
+template <class T>
+__host__ __device__ constexpr size_t split_staging_bytes() {
+    return 2 * (size_t)kCtaRows * (16 + 6 * sizeof(T)) + 128;
+}
+
+// named barrier 1 among the compute and operand warps, returning the AND of ok
+__device__ __forceinline__ bool split_agree(bool ok) {
+    uint32_t all_ok;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(all_ok)
+        : "r"((uint32_t)ok), "r"(2 * kCtaRows)
+        : "memory");
+    return all_ok != 0;
+}
+
+__device__ __forceinline__ void st_vec4(float* p, const float (&l)[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(l[0], l[1], l[2], l[3]);
+}
+__device__ __forceinline__ void st_vec4(double* p, const double (&l)[4]) {
+    reinterpret_cast<double2*>(p)[0] = make_double2(l[0], l[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(l[2], l[3]);
+}
+
+template <bool kFar, class T>
+__global__ void __launch_bounds__(kSplitThreads, 1) k_trsv_split(CtaDev D, const T* __restrict__ rhs, T* outq,
+                                                                 const SysState* st, int* flags) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int sys = blockIdx.x;
+    if (st && !st[sys].active) return;
+    const int c0 = D.sys_chunk0[sys], c1 = D.sys_chunk0[sys + 1];
+    if (c0 >= c1) return;
+    const int S = D.stages;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem);
+    uint64_t* empty = full + kMaxStages;
+    int4* info = reinterpret_cast<int4*>(empty + kMaxStages);
+    T* win = reinterpret_cast<T*>(smem + kBarBytes);
+    const int W = D.win;
+    unsigned char* stg = smem + kBarBytes + (size_t)(W + kWinPad) * sizeof(T);
+    int4* s_dep = reinterpret_cast<int4*>(stg);                          // [2][kCtaRows]
+    T* s_l = reinterpret_cast<T*>(stg + 2 * kCtaRows * 16);               // [2][kCtaRows][4]
+    T* s_dinv = s_l + 2 * kCtaRows * 4;                                   // [2][kCtaRows]
+    T* s_rhs = s_dinv + 2 * kCtaRows;                                     // [2][kCtaRows]
+    int* s_meta = reinterpret_cast<int*>(s_rhs + 2 * kCtaRows);           // [2][kMetaInts]
+    unsigned char* ring = stg + split_staging_bytes<T>();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kCtaRows / 32);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (threadIdx.x < kWinPad) win[W + threadIdx.x] = (T)0;
+    __syncthreads();
+
+    if (warp == 2 * kCtaRows / 32) {
+        ring_producer<T>(D, rhs, ring, full, empty, info, c0, c1, flags);
+        return;
+    }
+
+    if (threadIdx.x >= kCtaRows) {
+        // ---------------- operand warps: stage step j during step j - 1
+        const int t2 = threadIdx.x - kCtaRows;
+        bool ok = mbar_wait_bounded(&full[0], 0u);
+        int c = c0, s = 0, u = 0, nst = 0, q0e = 0;
+        const int32_t* hdr = nullptr;
+        const T* vals = nullptr;
+        const T* rh = nullptr;
+        if (ok) {
+            const int4 inf = info[0];
+            nst = inf.x;
+            hdr = reinterpret_cast<const int32_t*>(ring);
+            vals = reinterpret_cast<const T*>(ring + inf.y);
+            rh = reinterpret_cast<const T*>(ring + inf.z);
+            q0e = inf.w;
+        }
+        bool have = true;
+        for (int j = 0;; ++j) {
+            const bool prep = have;
+            if (prep && ok) {
+                const int sl = j & 1;
+                const int4 h = *reinterpret_cast<const int4*>(hdr);
+                const int nrows = h.y, np = pad4(h.y), width = h.z;
+                if (t2 < nrows) {
+                    s_dep[sl * kCtaRows + t2] = reinterpret_cast<const int4*>(hdr + kHdrInts)[t2];
+                    T l[4];
+                    ld_vec4(l, vals + 4 * t2);
+                    st_vec4(s_l + 4 * (sl * kCtaRows + t2), l);
+                    s_dinv[sl * kCtaRows + t2] = vals[4 * np + t2];
+                    s_rhs[sl * kCtaRows + t2] = rh[h.x - q0e + t2];
+                }
+                const bool chunk_end = u + 1 == nst;
+                if (t2 == 0) {
+                    int* m = s_meta + sl * kMetaInts;
+                    m[0] = nrows;
+                    m[1] = h.x;
+                    m[2] = np;
+                    m[3] = width;
+                    m[4] = (int)(reinterpret_cast<const unsigned char*>(hdr) - ring);
+                    m[5] = (int)(reinterpret_cast<const unsigned char*>(vals) - ring);
+                    m[6] = chunk_end ? s : -1;
+                    m[7] = chunk_end && c + 1 == c1;
+                }
+                // advance to the next step
+                if (!chunk_end) {
+                    hdr += s_ints(np, width);
+                    vals += v_elems(np, width);
+                    ++u;
+                } else if (c + 1 < c1) {
+                    ++c;
+                    s = (c - c0) % S;
+                    u = 0;
+                    ok = mbar_wait_bounded(&full[s], (uint32_t)(((c - c0) / S) & 1));
+                    if (ok) {
+                        const int4 inf = info[s];
+                        const unsigned char* base = ring + (size_t)s * D.stage_cap;
+                        nst = inf.x;
+                        hdr = reinterpret_cast<const int32_t*>(base);
+                        vals = reinterpret_cast<const T*>(base + inf.y);
+                        rh = reinterpret_cast<const T*>(base + inf.z);
+                        q0e = inf.w;
+                    }
+                } else {
+                    have = false;
+                }
+            }
+            if (!split_agree(ok)) {
+                if (t2 == 0) atomicOr(flags, kFlagTimeout | kFlagAbort);
+                return;
+            }
+            if (!prep) break;
+        }
+        return;
+    }
+
+    // ---------------- compute warps: solve step k from slot k & 1
+    const int t = threadIdx.x;
+    if (!split_agree(true)) return;
+    for (int k = 0;; ++k) {
+        const int sl = k & 1;
+        const int* m = s_meta + sl * kMetaInts;
+        const int nrows = m[0], q0 = m[1], np = m[2], width = m[3], hoff = m[4], voff = m[5], rel = m[6], last = m[7];
+        if (t < nrows) {
+            const int4 dep = s_dep[sl * kCtaRows + t];
+            T l[4];
+            ld_vec4(l, s_l + 4 * (sl * kCtaRows + t));
+            const T dinv = s_dinv[sl * kCtaRows + t];
+            T acc = s_rhs[sl * kCtaRows + t];
+            T y0, y1, y2, y3;
+            if (kFar) {
+                y0 = dep.x >= 0 ? win[dep.x] : __ldcg(outq + (-dep.x - 2));
+                y1 = dep.y >= 0 ? win[dep.y] : __ldcg(outq + (-dep.y - 2));
+                y2 = dep.z >= 0 ? win[dep.z] : __ldcg(outq + (-dep.z - 2));
+                y3 = dep.w >= 0 ? win[dep.w] : __ldcg(outq + (-dep.w - 2));
+            } else {
+                y0 = win[dep.x];
+                y1 = win[dep.y];
+                y2 = win[dep.z];
+                y3 = win[dep.w];
+            }
+            acc = fma(-l[0], y0, acc);
+            acc = fma(-l[1], y1, acc);
+            acc = fma(-l[2], y2, acc);
+            acc = fma(-l[3], y3, acc);
+            if (width > kRec) {
+                const int32_t* xdep = reinterpret_cast<const int32_t*>(ring + hoff) + kHdrInts + 6 * np;
+                const T* xval = reinterpret_cast<const T*>(ring + voff) + 5 * np;
+                for (int kk = 0; kk < width - kRec; ++kk) {
+                    const int pk = xdep[kk * np + t];
+                    if (kFar && pk <= -2) acc = fma(-xval[kk * np + t], __ldcg(outq + (-pk - 2)), acc);
+                    else acc = fma(-xval[kk * np + t], win[pk], acc);
+                }
+            }
+            const T y = acc * dinv;
+            const int q = q0 + t;
+            win[q & (W - 1)] = y;
+            outq[q] = y;
+            if (kFar) __threadfence_block();
+        }
+        if (!split_agree(true)) return;
+        if (rel >= 0 && lane == 0) mbar_arrive(&empty[rel]);   // chunk solved
+        if (last) break;
+    }
+}
+
 // ------------------------------------------------------------ flag-synchronised variant
 // FP32 only.  The same layout and ring, without the barrier per step: every
 // window slot is one 64-bit word {position, value} written with a single
@@ -1072,6 +1272,17 @@ npcg_status cta_layout_build(Handle* h, Pattern* P, bool upper, CtaLayout* C) {
                                      cudaMemcpyHostToDevice, h->stream));
         NPCG_CUDA(h, cudaStreamSynchronize(h->stream));
     }
+    // split-role kernel: the same chunks in a shallower ring beside the
+    // staging slots (one CTA per SM)
+    for (int f32 = 0; f32 < 2; ++f32) {
+        C->split_stages[f32] = 0;
+        if (!C->window_ok || C->blocked || nunits > h->num_sms || C->nstages[f32] < 2) continue;
+        const size_t used = kBarBytes + win_bytes(*C, f32 != 0) +
+                            (f32 ? split_staging_bytes<float>() : split_staging_bytes<double>());
+        if (used >= kSmemMax) continue;
+        const int st = (int)std::min<size_t>((size_t)C->nstages[f32], (kSmemMax - used) / (size_t)C->stage_cap[f32]);
+        C->split_stages[f32] = st >= 2 ? st : 0;
+    }
     C->nstages[2] = 0;
     C->nchunks[2] = 0;
     if (C->flag_ok) {
@@ -1089,6 +1300,10 @@ npcg_status cta_layout_build(Handle* h, Pattern* P, bool upper, CtaLayout* C) {
     // the launch size never exceeds 220 KB; set once here, outside any capture
     const int mx = 220 * 1024;
     NPCG_CUDA(h, cudaFuncSetAttribute(k_trsv_flag, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    NPCG_CUDA(h, cudaFuncSetAttribute(k_trsv_split<false, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    NPCG_CUDA(h, cudaFuncSetAttribute(k_trsv_split<true, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    NPCG_CUDA(h, cudaFuncSetAttribute(k_trsv_split<false, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    NPCG_CUDA(h, cudaFuncSetAttribute(k_trsv_split<true, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
     NPCG_CUDA(h, cudaFuncSetAttribute(k_trsv_cta<true, false, false, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
     NPCG_CUDA(h, cudaFuncSetAttribute(k_trsv_cta<false, false, false, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
     NPCG_CUDA(h, cudaFuncSetAttribute(k_trsv_cta<true, false, false, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
@@ -1171,6 +1386,28 @@ npcg_status cta_gather(Handle* h, cudaStream_t s, const CtaLayout& C, int64_t n,
 // moves it on.  f32: FP32 factor, arithmetic, right-hand side and outq.
 npcg_status cta_trsv_launch(Handle* h, cudaStream_t s, Pattern* P, const CtaLayout& C, const void* rhs_v,
                             void* outq, const SysState* st, bool f32, int* ticket, double* pub) {
+    if (P->cta_split && C.split_stages[f32] >= 2) {
+        CtaDev d;
+        d.sys_chunk0 = C.sys_chunk0[f32].p;
+        d.chunks = C.chunks[f32].p;
+        d.sbuf = C.sbuf.p;
+        d.vbuf = f32 ? (const void*)C.vbuf32.p : (const void*)C.vbuf.p;
+        d.stages = C.split_stages[f32];
+        d.stage_cap = C.stage_cap[f32];
+        d.win = C.win_slots;
+        const size_t smem = kBarBytes + win_bytes(C, f32) +
+                            (f32 ? split_staging_bytes<float>() : split_staging_bytes<double>()) +
+                            (size_t)C.stage_cap[f32] * C.split_stages[f32];
+        int* flags = P->ctl.p + 1;
+#define NPCG_SPLIT_LAUNCH(F, TT)                                                                              \
+    k_trsv_split<F, TT><<<C.nunits, kSplitThreads, smem, s>>>(d, static_cast<const TT*>(rhs_v),                \
+                                                              static_cast<TT*>(outq), st, flags)
+        if (f32) { if (C.far) NPCG_SPLIT_LAUNCH(true, float); else NPCG_SPLIT_LAUNCH(false, float); }
+        else { if (C.far) NPCG_SPLIT_LAUNCH(true, double); else NPCG_SPLIT_LAUNCH(false, double); }
+#undef NPCG_SPLIT_LAUNCH
+        NPCG_CUDA(h, cudaGetLastError());
+        return NPCG_OK;
+    }
     if (f32 && P->cta_flag && C.flag_ok && C.nstages[2] >= 2) {
         CtaDev d;
         d.sys_chunk0 = C.sys_chunk0[2].p;

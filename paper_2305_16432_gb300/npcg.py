@@ -26,7 +26,7 @@ FP32, BF16 = 0, 1
 LOSS_AB, LOSS_FROB = 0, 1
 PREC_NONE, PREC_JACOBI, PREC_LLT, PREC_LLT32 = 0, 1, 2, 3
 METHOD_GNN, METHOD_IC0, METHOD_JACOBI, METHOD_CG, METHOD_SGS = 0, 1, 2, 3, 4
-TRSV_AUTO, TRSV_SYNCFREE, TRSV_LEVELSYNC, TRSV_LEVELFLAG = 0, 1, 2, 3
+TRSV_AUTO, TRSV_SYNCFREE, TRSV_LEVELSYNC, TRSV_LEVELFLAG, TRSV_LEVELSPLIT = 0, 1, 2, 3, 4
 
 
 class NpcgError(RuntimeError):
@@ -46,7 +46,7 @@ class _Info(C.Structure):
     _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("nnz_L", C.c_int64), ("nsys", C.c_int32),
                 ("nlev_fwd", C.c_int32), ("nlev_bwd", C.c_int32), ("trsv_mode", C.c_int32),
                 ("tuned_ms_syncfree", C.c_float), ("tuned_ms_levelsync", C.c_float),
-                ("tuned_ms_levelflag", C.c_float)]
+                ("tuned_ms_levelflag", C.c_float), ("tuned_ms_levelsplit", C.c_float)]
 
 
 class _Cfg(C.Structure):
@@ -210,12 +210,12 @@ class Pattern:
         self.nsys, self.nlev_fwd, self.nlev_bwd = info.nsys, info.nlev_fwd, info.nlev_bwd
         self.trsv_mode = info.trsv_mode
         self.tuned_ms = {"syncfree": info.tuned_ms_syncfree, "levelsync": info.tuned_ms_levelsync,
-                         "levelflag": info.tuned_ms_levelflag}
+                         "levelflag": info.tuned_ms_levelflag, "levelsplit": info.tuned_ms_levelsplit}
         self.sys_ptr = np.asarray(sys_ptr if sys_ptr is not None else [0, n], dtype=np.int64)
 
     def set_trsv(self, mode):
         """Force a triangular-solve design (TRSV_SYNCFREE / TRSV_LEVELSYNC /
-        TRSV_LEVELFLAG) or restore the tuned one (TRSV_AUTO)."""
+        TRSV_LEVELFLAG / TRSV_LEVELSPLIT) or restore the tuned one (TRSV_AUTO)."""
         self.h.check(lib().npcg_pattern_set_trsv(self.p, int(mode)))
         info = _Info()
         lib().npcg_pattern_get_info(self.p, C.byref(info))

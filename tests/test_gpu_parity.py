@@ -302,13 +302,20 @@ def test_fem256_full_size(N):
     assert np.linalg.norm(_np(xg) - xo) / np.linalg.norm(xo) <= 1e-8
 
 
-@pytest.mark.parametrize("mode", ["syncfree", "levelsync"])
+_MODE = {"syncfree": "TRSV_SYNCFREE", "levelsync": "TRSV_LEVELSYNC", "levelsplit": "TRSV_LEVELSPLIT"}
+
+
+def _set_mode(N, P, mode):
+    P.set_trsv(getattr(N, _MODE[mode]))
+
+
+@pytest.mark.parametrize("mode", ["syncfree", "levelsync", "levelsplit"])
 @pytest.mark.parametrize("name", ["poisson2d_32", "fem34", "fd3d_var"])
 def test_trsv_designs_parity(N, name, mode):
-    # both triangular-solve designs against the oracle, alone and inside PCG
+    # the triangular-solve designs against the oracle, alone and inside PCG
     Ao, (rp, ci, v) = _assemble_both(N, PROBLEMS[name])
     P = N.analyse(rp, ci)
-    P.set_trsv(N.TRSV_SYNCFREE if mode == "syncfree" else N.TRSV_LEVELSYNC)
+    _set_mode(N, P, mode)
     Lo, _ = O.ic0(Ao)
     N.factor_load(P, _gpu(Lo.val))
     r = np.random.default_rng(5).standard_normal(Ao.n)
@@ -321,7 +328,7 @@ def test_trsv_designs_parity(N, name, mode):
     assert np.linalg.norm(_np(xg) - xo) / np.linalg.norm(xo) <= 1e-8
 
 
-@pytest.mark.parametrize("mode", ["syncfree", "levelsync"])
+@pytest.mark.parametrize("mode", ["syncfree", "levelsync", "levelsplit"])
 def test_batched_trsv_designs(N, mode):
     probs = [I.fem2d(26, sigma=1.0, seed=11), I.fd3d(7, 6, 5, sigma=1.0, seed=12), I.fd2d(17, 9, sigma=1.0, seed=13),
              I.fem2d(12, sigma=1.0, seed=14)]
@@ -338,7 +345,7 @@ def test_batched_trsv_designs(N, mode):
     nnz_off = np.cumsum([0] + [a.nnz for a in As])
     rp_cat = np.concatenate([a.row_ptr[:-1] + nnz_off[k] for k, a in enumerate(As)] + [[nnz_off[-1]]])
     P = N.analyse(_gpu(rp_cat, torch.int32), _gpu(np.concatenate(cis), torch.int32), sys_ptr)
-    P.set_trsv(N.TRSV_SYNCFREE if mode == "syncfree" else N.TRSV_LEVELSYNC)
+    _set_mode(N, P, mode)
     v_cat = _gpu(np.concatenate(vs))
     Lg, _ = N.ic0_factor(P, v_cat)
     x, st = N.pcg_solve(P, v_cat, _gpu(np.concatenate(bs)), N.PREC_LLT, Lg, rtol=1e-8)
@@ -350,7 +357,7 @@ def test_batched_trsv_designs(N, mode):
         assert np.linalg.norm(seg - xo) / np.linalg.norm(xo) <= 1e-8
 
 
-@pytest.mark.parametrize("mode", ["syncfree", "levelsync"])
+@pytest.mark.parametrize("mode", ["syncfree", "levelsync", "levelsplit"])
 @pytest.mark.parametrize("name", ["fem34", "fd3d_var"])
 def test_fp32_preconditioner_apply(N, name, mode):
     # P = L' L'^T with L' = fl32(L), solves in FP32: the PCG recurrences stay
@@ -358,7 +365,7 @@ def test_fp32_preconditioner_apply(N, name, mode):
     # stays within 5 % of the FP64-preconditioned oracle
     Ao, (rp, ci, v) = _assemble_both(N, PROBLEMS[name])
     P = N.analyse(rp, ci)
-    P.set_trsv(N.TRSV_SYNCFREE if mode == "syncfree" else N.TRSV_LEVELSYNC)
+    _set_mode(N, P, mode)
     Lo, _ = O.ic0(Ao)
     b = I.rhs(Ao.n, 9)
     xo, ito, _, _ = O.pcg(Ao, b, O.PREC_LLT, Lo, rtol=1e-8)
@@ -528,6 +535,9 @@ def test_flag_trsv_matches_barrier_bit_exact(N, case):
         P.set_trsv(N.TRSV_LEVELFLAG)
         _, yf = N.sptrsv_timed(P, _gpu(r), transpose=tr, reps=1, f32=True)
         assert torch.equal(yb, yf)
+        P.set_trsv(N.TRSV_LEVELSPLIT)
+        _, ys = N.sptrsv_timed(P, _gpu(r), transpose=tr, reps=1, f32=True)
+        assert torch.equal(yb, ys)
         yo = O.trsv_upper(L32, r32) if tr else O.trsv_lower(L32, r32)
         assert _rel(_np(yf), yo) <= 1e-4
 
@@ -641,8 +651,9 @@ def test_time_step_rejects_bad_arcs(N):
         N.assemble_system(I.Problem(I.FEM, 2, 8, 8, 0, 0.0, 0.1, 0, -1.0))
 
 
+@pytest.mark.parametrize("mode", ["levelsync", "levelsplit"])
 @pytest.mark.parametrize("prob", [I.heat2d(130, seed=0), I.heat2d(110, seed=2)])
-def test_hybrid_window_far_dependencies(N, prob):
+def test_hybrid_window_far_dependencies(N, prob, mode):
     # free boundary points of these heat systems have no upper neighbours
     # and sit at backward level 0 while a reader comes thousands of
     # positions later (reach 11,332 and 8,507 > the 8,192-slot window): the
@@ -650,7 +661,7 @@ def test_hybrid_window_far_dependencies(N, prob):
     # from its output; both directions against the oracle, and PCG
     Ao, (rp, ci, v) = _assemble_both(N, prob)
     P = N.analyse(rp, ci)
-    P.set_trsv(N.TRSV_LEVELSYNC)
+    _set_mode(N, P, mode)
     Lo, _ = O.ic0(Ao)
     N.factor_load(P, _gpu(Lo.val))
     r = np.random.default_rng(8).standard_normal(Ao.n)
