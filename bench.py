@@ -326,7 +326,8 @@ def _spmv_roofline(N, P, v, hbm, reps=50):
     ms = e0.elapsed_time(e1) / reps
     byts = 12 * P.nnz + 4 * (P.n + 1) + 16 * P.n
     ach = byts / (ms * 1e-3) / 1e9
-    return {"kernel": "k_spmv_plain (SpMV, FP64)", "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+    kname = "k_spmv_rows" if P.max_row <= 16 else "k_spmv_plain"
+    return {"kernel": kname + " (SpMV, FP64)", "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
             "frac": ach / hbm, "bytes_per_launch": byts, "ms_per_launch": ms}
 
 

@@ -162,6 +162,8 @@ typedef struct {
     float tuned_ms_levelsync;     /* (0 when the design does not apply)         */
     float tuned_ms_levelflag;
     float tuned_ms_levelsplit;
+    int32_t max_row;              /* entries of the longest row of A (rows of at most
+                                     16 take the one-thread-per-row SpMV)          */
 } npcg_pattern_info;
 NPCG_API npcg_status npcg_pattern_get_info(npcg_pattern p, npcg_pattern_info* out);  /* host out */
 /* Overrides the tuned design (NPCG_TRSV_AUTO restores the tuned choice).

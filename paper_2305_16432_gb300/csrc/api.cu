@@ -136,6 +136,7 @@ npcg_status npcg_pattern_get_info(npcg_pattern p, npcg_pattern_info* out) {
     out->tuned_ms_levelsync = p->tune_ms[1];
     out->tuned_ms_levelflag = p->tune_ms[2];
     out->tuned_ms_levelsplit = p->tune_ms[3];
+    out->max_row = p->max_row;
     return NPCG_OK;
 }
 

@@ -18,6 +18,7 @@ constexpr int kWarp = 32;
 constexpr int kSlice = 32;                 // rows per SELL slice = one warp of the solve
 constexpr int kChunk = 512;                // rows per reduction chunk (one block)
 constexpr int kChunkThreads = 256;
+constexpr int kShortRow = 16;    // rows up to this length: one thread per row in the SpMV
 constexpr long long kSpinLimit = 1LL << 22; // polls before a device wait gives up (~1-2 s)
 
 // bits of a canonical-free signalling NaN: "value not yet written"
@@ -164,6 +165,7 @@ struct Pattern {
     Handle* h = nullptr;
     int64_t n = 0, nnz = 0, nnzL = 0;
     int32_t nsys = 1;
+    int32_t max_row = 0;           // longest row of A (entries)
     std::vector<int64_t> sys_ptr_h;
     DevBuf<int64_t> sys_ptr;       // [nsys+1]
     DevBuf<int32_t> row_sys;       // [n] system of each row

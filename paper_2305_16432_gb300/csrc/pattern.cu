@@ -25,7 +25,8 @@ __device__ __forceinline__ int find_sys(const int64_t* sys_ptr, int nsys, int64_
 // present.  Counts tril entries and records the row of every entry.
 __global__ void k_rows(int64_t n, const int32_t* rp, const int32_t* ci, const int64_t* sys_ptr,
                        int nsys, int32_t* row_sys, int32_t* adiag, int32_t* lcount,
-                       int32_t* edge_row, int* flags) {
+                       int32_t* edge_row, int* flags, int* max_row) {
+    int longest = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         int s = find_sys(sys_ptr, nsys, i);
@@ -46,7 +47,11 @@ __global__ void k_rows(int64_t n, const int32_t* rp, const int32_t* ci, const in
         adiag[i] = d;
         lcount[i] = cnt;
         if (bad) atomicOr(flags, kFlagBadPattern);
+        longest = max(longest, b - a);
     }
+    // longest row (selects the SpMV mapping): one atomic per warp
+    longest = __reduce_max_sync(0xffffffffu, longest);
+    if ((threadIdx.x & 31) == 0) atomicMax(max_row, longest);
 }
 
 // mirror[k] = position of (j, i) for k = (i, j); the pattern must be symmetric.
@@ -322,12 +327,15 @@ npcg_status pattern_build(Handle* h, int64_t n, int64_t nnz, const int32_t* rp, 
     NPCG_CUDA(h, P->a2l.alloc(nnz));
     NPCG_CUDA(h, P->ctl.alloc(8));
     NPCG_CUDA(h, cudaMemsetAsync(P->ctl.p, 0, 8 * sizeof(int), h->stream));
-    DevBuf<int32_t> lcount;
+    DevBuf<int32_t> lcount, longest;
     NPCG_CUDA(h, lcount.alloc(n));
+    NPCG_CUDA(h, longest.alloc(1));
+    NPCG_CUDA(h, cudaMemsetAsync(longest.p, 0, sizeof(int32_t), h->stream));
     k_rows<<<grid_for(n, 256, 65535), 256, 0, h->stream>>>(n, P->rp.p, P->ci.p, P->sys_ptr.p, nsys,
                                                            P->row_sys.p, P->adiag.p, lcount.p,
-                                                           P->edge_row.p, P->ctl.p + 1);
+                                                           P->edge_row.p, P->ctl.p + 1, longest.p);
     NPCG_CUDA(h, cudaGetLastError());
+    NPCG_TRY(read_scalar(h, longest.p, &P->max_row));
     int flags = 0;
     NPCG_TRY(read_scalar(h, P->ctl.p + 1, &flags));
     if (flags) return set_error(h, NPCG_EINVAL, "malformed CSR: columns must ascend, stay inside the row's system, and include the diagonal");

@@ -94,6 +94,7 @@ struct PcgArgs {
     const int32_t* cposf;     //   and the forward position of each row
     int rperm_f32;            //   stored as FP32 (NPCG_PREC_LLT32) or FP64
     int precond;
+    int short_rows;           // every row has <= kShortRow entries: one thread per row in the SpMV
 };
 
 __device__ __forceinline__ void store_perm(const PcgArgs& a, int row, double ri) {
@@ -218,24 +219,43 @@ __global__ void k_spmv_p(PcgArgs a, const double* __restrict__ p_old, double* __
     const SysState& s0 = a.st[c.sys];
     if (!s0.active) return;
     const double beta = s0.beta;
-    const int g = threadIdx.x & 7, sub = (threadIdx.x >> 3) & 3, warp = threadIdx.x >> 5;
     double acc[1] = {0.0};
-    for (int base = c.row0 + warp * 4; base < c.row1; base += kChunkThreads / 8) {
-        const int row = base + sub;
-        const bool valid = row < c.row1;
-        double s = 0.0;
-        const int k1 = valid ? a.rp[row + 1] : 0;
-        for (int k = valid ? a.rp[row] + g : 0; k < k1; k += 8) {
-            int j = a.ci[k];
-            s = fma(a.av[k], fma(beta, p_old[j], a.z[j]), s);
-        }
-#pragma unroll
-        for (int o = 4; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, 8);
-        if (g == 0 && valid) {
-            double pi = fma(beta, p_old[row], a.z[row]);
+    if (a.short_rows) {
+        // one thread per row: a warp keeps 32 rows' entries in flight (the
+        // eight-lane mapping below keeps four), which is what a bandwidth-
+        // bound stencil or mesh row of 7-9 entries needs
+        for (int row = c.row0 + threadIdx.x; row < c.row1; row += kChunkThreads) {
+            const int k0 = a.rp[row], k1 = a.rp[row + 1];
+            double s = 0.0;
+#pragma unroll 4
+            for (int k = k0; k < k1; ++k) {
+                const int j = a.ci[k];
+                s = fma(a.av[k], fma(beta, p_old[j], a.z[j]), s);
+            }
+            const double pi = fma(beta, p_old[row], a.z[row]);
             p_new[row] = pi;
             a.w[row] = s;
             acc[0] = fma(pi, s, acc[0]);
+        }
+    } else {
+        const int g = threadIdx.x & 7, sub = (threadIdx.x >> 3) & 3, warp = threadIdx.x >> 5;
+        for (int base = c.row0 + warp * 4; base < c.row1; base += kChunkThreads / 8) {
+            const int row = base + sub;
+            const bool valid = row < c.row1;
+            double s = 0.0;
+            const int k1 = valid ? a.rp[row + 1] : 0;
+            for (int k = valid ? a.rp[row] + g : 0; k < k1; k += 8) {
+                int j = a.ci[k];
+                s = fma(a.av[k], fma(beta, p_old[j], a.z[j]), s);
+            }
+#pragma unroll
+            for (int o = 4; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, 8);
+            if (g == 0 && valid) {
+                double pi = fma(beta, p_old[row], a.z[row]);
+                p_new[row] = pi;
+                a.w[row] = s;
+                acc[0] = fma(pi, s, acc[0]);
+            }
         }
     }
     block_sum<1>(acc, sh);
@@ -430,6 +450,19 @@ __global__ void k_fill_sentinel(int64_t n, double* y) {
         y[i] = sentinel_f64();
 }
 
+// y = A x with one thread per row (rows of at most kShortRow entries)
+__global__ void k_spmv_rows(int64_t n, const int32_t* rp, const int32_t* ci, const double* av,
+                            const double* x, double* y) {
+    for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < n;
+         row += (int64_t)gridDim.x * blockDim.x) {
+        const int k0 = rp[row], k1 = rp[row + 1];
+        double s = 0.0;
+#pragma unroll 4
+        for (int k = k0; k < k1; ++k) s = fma(av[k], x[ci[k]], s);
+        y[row] = s;
+    }
+}
+
 __global__ void k_spmv_plain(int64_t n, const int32_t* rp, const int32_t* ci, const double* av,
                              const double* x, double* y) {
     const int g = threadIdx.x & 7;
@@ -549,6 +582,7 @@ PcgArgs pcg_args(Pattern* P, int precond) {
     a.w = P->w.p;
     a.b = P->b.p;
     a.precond = precond;
+    a.short_rows = P->max_row <= kShortRow;
     const bool cta = P->trsv_mode == kTrsvCta && precond >= NPCG_PREC_LLT;
     a.rperm = cta ? (void*)P->r_cf.p : nullptr;
     a.cposf = cta ? P->cfwd.cpos.p : nullptr;
@@ -768,6 +802,12 @@ void trsv_pick_tuned(Pattern* P) {
 }
 
 npcg_status spmv_run(Handle* h, Pattern* P, const double* A_val, const double* x, double* y) {
+    if (P->max_row <= kShortRow) {
+        const int blocks = std::max(1, std::min(ceil_div(P->n, 256), h->num_sms * 8));
+        k_spmv_rows<<<blocks, 256, 0, h->stream>>>(P->n, P->rp.p, P->ci.p, A_val, x, y);
+        NPCG_CUDA(h, cudaGetLastError());
+        return NPCG_OK;
+    }
     int blocks = std::min(ceil_div(P->n * 8, 256), h->num_sms * 8);
     k_spmv_plain<<<blocks, 256, 0, h->stream>>>(P->n, P->rp.p, P->ci.p, A_val, x, y);
     NPCG_CUDA(h, cudaGetLastError());

@@ -46,7 +46,7 @@ class _Info(C.Structure):
     _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("nnz_L", C.c_int64), ("nsys", C.c_int32),
                 ("nlev_fwd", C.c_int32), ("nlev_bwd", C.c_int32), ("trsv_mode", C.c_int32),
                 ("tuned_ms_syncfree", C.c_float), ("tuned_ms_levelsync", C.c_float),
-                ("tuned_ms_levelflag", C.c_float), ("tuned_ms_levelsplit", C.c_float)]
+                ("tuned_ms_levelflag", C.c_float), ("tuned_ms_levelsplit", C.c_float), ("max_row", C.c_int32)]
 
 
 class _Cfg(C.Structure):
@@ -209,6 +209,7 @@ class Pattern:
         self.n, self.nnz, self.nnz_L = info.n, info.nnz, info.nnz_L
         self.nsys, self.nlev_fwd, self.nlev_bwd = info.nsys, info.nlev_fwd, info.nlev_bwd
         self.trsv_mode = info.trsv_mode
+        self.max_row = info.max_row
         self.tuned_ms = {"syncfree": info.tuned_ms_syncfree, "levelsync": info.tuned_ms_levelsync,
                          "levelflag": info.tuned_ms_levelflag, "levelsplit": info.tuned_ms_levelsplit}
         self.sys_ptr = np.asarray(sys_ptr if sys_ptr is not None else [0, n], dtype=np.int64)

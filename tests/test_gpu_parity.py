@@ -479,7 +479,7 @@ def test_x0_head_parity(N, prec, tol):
     assert np.linalg.norm(b - O.spmv(Ao, _np(x))) / np.linalg.norm(b) <= 2e-8
 
 
-def _wide_spd(n, seed):
+def _wide_spd(n, seed, kmax=7):
     # 2-D 5-point grid plus random symmetric long-range couplings, strictly
     # diagonally dominant: rows with up to ~10 lower neighbours (dependencies
     # beyond the four held in a row's packed record)
@@ -493,7 +493,7 @@ def _wide_spd(n, seed):
             rows.append(i); cols.append(i - 1)
         if y > 0:
             rows.append(i); cols.append(i - m)
-        k = int(g.integers(0, 7))
+        k = int(g.integers(0, kmax))
         for j in (g.integers(max(0, i - 3 * m), i, size=k) if i > 0 else []):
             if j != i - 1 and j != i - m:
                 rows.append(i); cols.append(int(j))
@@ -677,3 +677,22 @@ def test_hybrid_window_far_dependencies(N, prob, mode):
         xg, st = N.pcg_solve(P, _gpu(Ao.val), _gpu(b), pc, _gpu(Lo.val), rtol=1e-8)
         assert st[0]["status"] == 0 and abs(st[0]["iters"] - ito) <= max(1, int(np.ceil(0.05 * ito)))
         assert np.linalg.norm(b - O.spmv(Ao, _np(xg))) / np.linalg.norm(b) <= 2e-8
+
+
+@pytest.mark.parametrize("kmax", [4, 30])
+def test_spmv_and_pcg_row_mappings(N, kmax):
+    # rows of at most 16 entries take the one-thread-per-row SpMV, longer
+    # ones the eight-lanes-per-row mapping: both against the oracle, alone
+    # and inside PCG
+    Ao = _wide_spd(1600, 5, kmax)
+    P = N.analyse(_gpu(Ao.row_ptr, torch.int32), _gpu(Ao.col_idx, torch.int32))
+    longest = int(np.diff(Ao.row_ptr).max())
+    assert P.max_row == longest and (longest <= 16) == (kmax == 4)
+    x = np.random.default_rng(3).standard_normal(Ao.n)
+    assert _rel(_np(N.spmv(P, _gpu(Ao.val), _gpu(x))), O.spmv(Ao, x)) <= 1e-13
+    b = I.rhs(Ao.n, 16)
+    Lo, _ = O.ic0(Ao)
+    xo, ito, _, _ = O.pcg(Ao, b, O.PREC_LLT, Lo, rtol=1e-8)
+    xg, st = N.pcg_solve(P, _gpu(Ao.val), _gpu(b), N.PREC_LLT, _gpu(Lo.val), rtol=1e-8)
+    assert st[0]["status"] == 0 and abs(st[0]["iters"] - ito) <= 1
+    assert np.linalg.norm(_np(xg) - xo) / np.linalg.norm(xo) <= 1e-8
