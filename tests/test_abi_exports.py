@@ -55,3 +55,27 @@ def test_nparams_matches_layout(libpath):
 def test_builds_only_for_sm103a():
     from paper_2305_16432_gb300 import build
     assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    # the ctypes mirrors of the ABI structs have the C layout: size and the
+    # offset of every field, from a host C program compiled against the header
+    from paper_2305_16432_gb300 import npcg as N
+    mirrors = {"npcg_problem": N._Problem, "npcg_pattern_info": N._Info, "npcg_gnn_config": N._Cfg,
+               "npcg_solve_stats": N._Stats}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "npcg.h"', "int main(void) {"]
+    for cname, py in mirrors.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, py in mirrors.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
