@@ -271,7 +271,7 @@ npcg_status npcg_loss_and_grad(npcg_handle h, npcg_pattern p, const double* A_va
                                const double* X, const double* B, const npcg_gnn_config* cfg,
                                const float* weights, double* loss_out, float* grad) {
     NPCG_TRY(check_hp(h, p));
-    if (!A_val || !X || !B || !weights || !loss_out || !grad)
+    if (!A_val || !X || !B || !cfg || !weights || !loss_out || !grad)
         return set_error(H(h), NPCG_EINVAL, "NULL argument");
     if (npairs < 1) return set_error(H(h), NPCG_EINVAL, "npairs must be >= 1");
     return loss_grad_run(H(h), PT(p), A_val, npairs, X, B, cfg, weights, loss_out, grad);
