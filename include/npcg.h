@@ -151,7 +151,11 @@ NPCG_API npcg_status npcg_pattern_free(npcg_pattern p);
  *     compute warps solve step k (one system per SM).
  * npcg_analyse times the designs on the pattern and keeps the fastest. */
 enum { NPCG_TRSV_AUTO = 0, NPCG_TRSV_SYNCFREE = 1, NPCG_TRSV_LEVELSYNC = 2, NPCG_TRSV_LEVELFLAG = 3,
-       NPCG_TRSV_LEVELSPLIT = 4 };
+       NPCG_TRSV_LEVELSPLIT = 4,
+       /* groups of consecutive levels per step (substituted rows, see the
+        * plan in csrc/level_merge.h); reserved: npcg_pattern_set_trsv
+        * returns NPCG_EINVAL until the design has been run on a GPU       */
+       NPCG_TRSV_LEVELMERGE = 5 };
 
 typedef struct {
     int64_t n, nnz, nnz_L;

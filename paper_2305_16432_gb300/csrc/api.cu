@@ -144,6 +144,8 @@ npcg_status npcg_pattern_set_trsv(npcg_pattern p, int32_t mode) {
     if (!p) return NPCG_EINVAL;
     if (mode == NPCG_TRSV_AUTO) {
         trsv_pick_tuned(p);
+    } else if (mode == NPCG_TRSV_LEVELMERGE) {
+        return set_error(p->h, NPCG_EINVAL, "merged-level solves are not enabled yet");
     } else if (mode == NPCG_TRSV_SYNCFREE) {
         p->trsv_mode = kTrsvSyncFree;
         p->cta_flag = false;

@@ -161,6 +161,21 @@ struct FrobLayout {
     DevBuf<double> R;                     // [nS]
 };
 
+// Merged-level solve of one direction (groups of G levels, see
+// level_merge.h): the plan on the device, the level-synchronous layout of
+// the pattern of M (unit diagonal), and the numeric M (+ a trailing 1 for the
+// diagonal) and C of the loaded factor.
+struct MergeDir {
+    bool built = false;
+    int G = 0;
+    int64_t nM = 0, nC = 0;
+    CtaLayout lay;
+    DevBuf<int64_t> mrp, mtp, mtk, mts, crp, ctp, ctk, cts, diag;
+    DevBuf<int32_t> mcol, ccol, ccolpos, prows;
+    std::vector<int64_t> pptr;     // host: rows of pass s are prows[pptr[s] .. pptr[s + 1])
+    DevBuf<double> M, C;
+};
+
 struct Pattern {
     Handle* h = nullptr;
     int64_t n = 0, nnz = 0, nnzL = 0;
@@ -202,6 +217,8 @@ struct Pattern {
     int graph_mode[4] = {0, 0, 0, 0};
     GnnStore gnn;
     FrobLayout frob;
+    MergeDir mfwd, mbwd;           // merged-level solves (built on request)
+    bool cta_merge = false;        // level-ordered solves use the merged-level layouts
     ~Pattern();
 };
 
@@ -274,7 +291,18 @@ npcg_status factor_load(Handle* h, Pattern* P, const double* L_val);
 npcg_status sptrsv_run(Handle* h, Pattern* P, int transpose, const double* r, double* y,
                        const int32_t* sys_active);
 npcg_status spmv_run(Handle* h, Pattern* P, const double* A_val, const double* x, double* y);
-npcg_status cta_layout_build(Handle* h, Pattern* P, bool upper, CtaLayout* C);
+// An arbitrary dependency pattern for cta_layout_build instead of the
+// direction's rows of tril(A): host levels and row pointer, device row
+// pointer and dependency rows; the value of dependency e is entry e of the
+// value array handed to cta_factor_load, the (unit) diagonal entry diag_src.
+struct CtaDeps {
+    const std::vector<int32_t>* lev;
+    const std::vector<int64_t>* drp;
+    const int64_t* drp_dev;
+    const int32_t* drow_dev;
+    int64_t diag_src;
+};
+npcg_status cta_layout_build(Handle* h, Pattern* P, bool upper, CtaLayout* C, const CtaDeps* dep = nullptr);
 npcg_status cta_link(Handle* h, Pattern* P);
 int cta_stages(const CtaLayout& C);
 void trsv_pick_tuned(Pattern* P);
@@ -294,6 +322,9 @@ npcg_status pcg_run(Handle* h, Pattern* P, const double* A_val, const double* b,
                     npcg_solve_stats* stats);
 npcg_status ic0_run(Handle* h, Pattern* P, const double* A_val, double* L_val, double* alpha_out);
 npcg_status sgs_run(Handle* h, Pattern* P, const double* A_val, double* L_val);
+npcg_status merge_build(Handle* h, Pattern* P, int G);
+npcg_status merge_factor_load(Handle* h, Pattern* P, const double* L_val);
+void merge_apply(Handle* h, cudaStream_t s, Pattern* P, bool f32);
 npcg_status gnn_forward_run(Handle* h, Pattern* P, const double* A_val, const double* b,
                             const npcg_gnn_config* cfg, const float* w, double* L_val);
 npcg_status loss_grad_run(Handle* h, Pattern* P, const double* A_val, int npairs,

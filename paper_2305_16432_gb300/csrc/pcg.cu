@@ -592,6 +592,10 @@ PcgArgs pcg_args(Pattern* P, int precond) {
 
 // z = L^-T L^-1 r with the tuned triangular-solve design
 void apply_llt(Handle* h, cudaStream_t s, Pattern* P, bool batched, bool f32) {
+    if (P->trsv_mode == kTrsvCta && P->cta_merge) {
+        merge_apply(h, s, P, f32);
+        return;
+    }
     if (P->trsv_mode == kTrsvCta) {
         if (P->cfwd.blocked) {
             // row blocks publish to y and z (natural order; the update kernel
@@ -625,7 +629,7 @@ void enqueue_iteration(Handle* h, cudaStream_t s, Pattern* P, const PcgArgs& a, 
 
 npcg_status build_graph(Handle* h, Pattern* P, int precond) {
     // the graph is specific to the triangular-solve design
-    const int mode_key = P->trsv_mode | (P->cta_flag ? 16 : 0) | (P->cta_split ? 32 : 0);
+    const int mode_key = P->trsv_mode | (P->cta_flag ? 16 : 0) | (P->cta_split ? 32 : 0) | (P->cta_merge ? 64 : 0);
     if (P->graph[precond] && P->graph_mode[precond] == mode_key) return NPCG_OK;
     if (P->graph[precond]) { cudaGraphExecDestroy(P->graph[precond]); P->graph[precond] = nullptr; }
     PcgArgs a = pcg_args(P, precond);
@@ -671,6 +675,7 @@ npcg_status factor_load(Handle* h, Pattern* P, const double* L_val) {
         NPCG_TRY(cta_factor_load(h, &P->cfwd, L_val));
         NPCG_TRY(cta_factor_load(h, &P->cbwd, L_val));
     }
+    if (P->cta_merge) NPCG_TRY(merge_factor_load(h, P, L_val));
     int blocks = h->num_sms * 4;
     for (TriLayout* T : {&P->fwd, &P->bwd})
         k_load_factor<<<blocks, 256, 0, h->stream>>>(T->slots, T->src.p, L_val, T->val.p, T->val32.p, P->n,
@@ -799,6 +804,7 @@ void trsv_pick_tuned(Pattern* P) {
     P->trsv_mode = m == 0 ? kTrsvSyncFree : kTrsvCta;
     P->cta_flag = m == 2;
     P->cta_split = m == 3;
+    P->cta_merge = false;
 }
 
 npcg_status spmv_run(Handle* h, Pattern* P, const double* A_val, const double* x, double* y) {

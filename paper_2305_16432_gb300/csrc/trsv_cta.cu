@@ -868,6 +868,45 @@ __global__ void k_cta_fill(int64_t n, const int32_t* cperm, const int32_t* step_
     }
 }
 
+// k_cta_fill for an arbitrary dependency pattern (drp / drow, value index =
+// dependency entry) with the diagonal's value at diag_src
+__global__ void k_cta_fill_dep(int64_t n, const int32_t* cperm, const int32_t* step_of_pos, const int4* steps,
+                               const int64_t* soff, const int64_t* voff, const int32_t* cpos, const int64_t* drp,
+                               const int32_t* drow, int64_t diag_src, int32_t* sbuf, int32_t* vsrc) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int row = cperm[q];
+        const int stp = step_of_pos[q];
+        const int4 d = steps[stp];
+        const int np = pad4(d.y);
+        const int t = (int)(q - d.x);
+        int32_t* sb = sbuf + soff[stp];
+        int32_t* vs = vsrc + voff[stp];
+        if (t == 0) { sb[0] = d.x; sb[1] = d.y; sb[2] = d.z; sb[3] = 0; }
+        int32_t* body = sb + kHdrInts;
+        body[4 * np + 2 * t] = row;
+        body[4 * np + 2 * t + 1] = 0;
+        vs[4 * np + t] = (int32_t)diag_src;
+        const int64_t e0 = drp[row];
+        const int cnt = (int)(drp[row + 1] - e0);
+        const int kmax = d.z > kRec ? d.z : kRec;
+        for (int k = 0; k < kmax; ++k) {
+            int dep = -1, src = -1;
+            if (k < cnt) {
+                dep = cpos[drow[e0 + k]];
+                src = (int32_t)(e0 + k);
+            }
+            if (k < kRec) {
+                body[4 * t + k] = dep;
+                vs[4 * t + k] = src;
+            } else {
+                body[6 * np + (k - kRec) * np + t] = dep;
+                vs[5 * np + (k - kRec) * np + t] = src;
+            }
+        }
+    }
+}
+
 __device__ __forceinline__ int32_t* dep_slot(int32_t* body, int np, int t, int k) {
     return k < kRec ? body + 4 * t + k : body + 6 * np + (k - kRec) * np + t;
 }
@@ -1051,11 +1090,12 @@ bool build_chunks(const std::vector<int4>& steps, const std::vector<int64_t>& so
 // Host: builds the per-system level-synchronous layout of one direction.
 // Order: positions sorted by (system, level, row), i.e. the level order of
 // each system, systems one after another.
-npcg_status cta_layout_build(Handle* h, Pattern* P, bool upper, CtaLayout* C) {
+npcg_status cta_layout_build(Handle* h, Pattern* P, bool upper, CtaLayout* C, const CtaDeps* dep) {
     const int64_t n = P->n;
     const TriLayout& T = upper ? P->bwd : P->fwd;
     std::vector<int32_t> lev(n), rp_h(n + 1), Lrp_h(n + 1);
-    NPCG_CUDA(h, cudaMemcpyAsync(lev.data(), T.level.p, n * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+    if (dep) lev = *dep->lev;
+    else NPCG_CUDA(h, cudaMemcpyAsync(lev.data(), T.level.p, n * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
     NPCG_CUDA(h, cudaMemcpyAsync(rp_h.data(), P->rp.p, (n + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
     NPCG_CUDA(h, cudaMemcpyAsync(Lrp_h.data(), P->Lrp.p, (n + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
     NPCG_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -1063,7 +1103,7 @@ npcg_status cta_layout_build(Handle* h, Pattern* P, bool upper, CtaLayout* C) {
     // one per SM, listed in dependency order (the backward solve runs from
     // the last row, so its blocks come last-first)
     std::vector<std::pair<int64_t, int64_t>> units;
-    C->blocked = P->nsys == 1 && n >= kBlockedRows;
+    C->blocked = !dep && P->nsys == 1 && n >= kBlockedRows;
     if (C->blocked) {
         const int64_t B = (n + h->num_sms - 1) / h->num_sms;
         for (int64_t r0 = 0; r0 < n; r0 += B) units.push_back({r0, std::min<int64_t>(n, r0 + B)});
@@ -1077,6 +1117,7 @@ npcg_status cta_layout_build(Handle* h, Pattern* P, bool upper, CtaLayout* C) {
     std::vector<int4> steps;
     std::vector<int2> step_unit;                   // processing-position range of each step's unit
     auto offdiag = [&](int row) {
+        if (dep) return (int)((*dep->drp)[row + 1] - (*dep->drp)[row]);
         int nl = Lrp_h[row + 1] - Lrp_h[row];
         return upper ? (rp_h[row + 1] - rp_h[row]) - nl : nl - 1;
     };
@@ -1151,9 +1192,14 @@ npcg_status cta_layout_build(Handle* h, Pattern* P, bool upper, CtaLayout* C) {
     NPCG_CUDA(h, cudaMemsetAsync(C->sbuf.p, 0, C->sbuf.n * 4, h->stream));
     NPCG_CUDA(h, cudaMemsetAsync(C->vsrc.p, 0xff, C->vsrc.n * 4, h->stream));
     const int blocks = std::max(1, std::min(ceil_div(n, 256), h->num_sms * 8));
-    k_cta_fill<<<blocks, 256, 0, h->stream>>>(n, C->cperm.p, C->step_of_pos.p, C->steps.p, C->soff.p,
-                                              C->voff.p, C->cpos.p, P->Lrp.p, P->Lci.p, P->rp.p, P->ci.p,
-                                              P->mirror.p, P->a2l.p, upper ? 1 : 0, C->sbuf.p, C->vsrc.p);
+    if (dep)
+        k_cta_fill_dep<<<blocks, 256, 0, h->stream>>>(n, C->cperm.p, C->step_of_pos.p, C->steps.p, C->soff.p,
+                                                      C->voff.p, C->cpos.p, dep->drp_dev, dep->drow_dev,
+                                                      dep->diag_src, C->sbuf.p, C->vsrc.p);
+    else
+        k_cta_fill<<<blocks, 256, 0, h->stream>>>(n, C->cperm.p, C->step_of_pos.p, C->steps.p, C->soff.p,
+                                                  C->voff.p, C->cpos.p, P->Lrp.p, P->Lci.p, P->rp.p, P->ci.p,
+                                                  P->mirror.p, P->a2l.p, upper ? 1 : 0, C->sbuf.p, C->vsrc.p);
     k_mark_diag<<<std::max(1, std::min(nsteps, h->num_sms * 8)), 256, 0, h->stream>>>(
         nsteps, C->steps.p, C->voff.p, C->is_diag.p, vo);
     NPCG_CUDA(h, cudaGetLastError());
@@ -1209,7 +1255,7 @@ npcg_status cta_layout_build(Handle* h, Pattern* P, bool upper, CtaLayout* C) {
     size_t fcap = 0;
     int fstages = 0;
     C->flag_ok = false;
-    if (C->window_ok && !C->blocked && !C->far) {
+    if (C->window_ok && !C->blocked && !C->far && !dep) {
         const size_t single = single_bytes(4);
         for (int W = C->win_slots; W <= kWinMax; W *= 2) {
             const size_t wb = (size_t)(W + kWinPad) * sizeof(unsigned long long);
@@ -1276,7 +1322,7 @@ npcg_status cta_layout_build(Handle* h, Pattern* P, bool upper, CtaLayout* C) {
     // staging slots (one CTA per SM)
     for (int f32 = 0; f32 < 2; ++f32) {
         C->split_stages[f32] = 0;
-        if (!C->window_ok || C->blocked || nunits > h->num_sms || C->nstages[f32] < 2) continue;
+        if (!C->window_ok || C->blocked || dep || nunits > h->num_sms || C->nstages[f32] < 2) continue;
         const size_t used = kBarBytes + win_bytes(*C, f32 != 0) +
                             (f32 ? split_staging_bytes<float>() : split_staging_bytes<double>());
         if (used >= kSmemMax) continue;
