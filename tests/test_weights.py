@@ -1,0 +1,36 @@
+"""The committed networks: every weight file matches the parameter count of
+the configuration its training record names, and the benchmark picks each
+workload's own file (CPU only)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import bench
+from paper_2305_16432_gb300 import inputs as I
+
+WDIR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2305_16432_gb300", "weights")
+FILES = sorted(f for f in os.listdir(WDIR) if f.endswith(".npy"))
+
+
+@pytest.mark.parametrize("fname", FILES)
+def test_weights_match_their_config(fname):
+    w = np.load(os.path.join(WDIR, fname))
+    meta = json.load(open(os.path.join(WDIR, fname[:-4] + ".json")))
+    cfg = I.GnnConfig(**meta["config"])
+    assert w.dtype == np.float32 and w.ndim == 1 and len(w) == cfg.nparams
+    assert np.all(np.isfinite(w))
+    w2, kind, meta2 = bench._load_weights(I.GnnConfig(n_mp=6, l=2, l_mp=2, h=64), os.path.join(WDIR, fname))
+    assert kind == "trained" and len(w2) == len(w) and meta2["config"] == meta["config"]
+
+
+def test_bench_picks_each_workloads_network():
+    assert os.path.basename(bench.weights_for("fem2d_256")) == "gnn_6x64_fem2d.npy"
+    assert os.path.basename(bench.weights_for("heat2d_256")) == "gnn_6x64_heat2d.npy"
+    assert os.path.basename(bench.weights_for("batched_256")) == "gnn_6x64.npy"
+    assert os.path.basename(bench.weights_for("fem2d_256", x0=True)) == "gnn_6x64_fem2d_x0.npy"
+    # no dedicated 3-D network is committed: the mixed one serves the 128^3 grid
+    assert os.path.basename(bench.weights_for("fd3d_128")) == "gnn_6x64.npy"
+    meta = json.load(open(os.path.join(WDIR, "gnn_6x64_fem2d_x0.json")))
+    assert meta["config"]["x0_head"] == 1
