@@ -16,7 +16,6 @@
 
 #include <algorithm>
 #include <cstdint>
-#include <map>
 #include <vector>
 
 namespace npcg {
@@ -58,59 +57,76 @@ inline MergePlan build_merge_plan(int64_t n, const std::vector<int64_t>& dep_rp,
     std::vector<int64_t> order(n);
     for (int64_t i = 0; i < n; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int64_t x, int64_t y) { return lev[x] < lev[y]; });
-    // per row: entry maps column -> list of terms (k, src row entry as (row, column))
+    // a term of an entry: L factor k and source entry (row, column), or a direct term (row -1)
     struct Term { int64_t k; int32_t src_row; int32_t src_col; };
-    std::vector<std::map<int32_t, std::vector<Term>>> Mt(n), Ct(n);
+    struct Cand { int32_t col; Term t; };
+    // per row: its entries' columns (ascending) and, per entry, its terms
+    std::vector<std::vector<int32_t>> mcols(n), ccols(n);
+    std::vector<std::vector<int64_t>> mtp_r(n), ctp_r(n);          // term offsets per entry (+ end)
+    std::vector<std::vector<Term>> mterms(n), cterms(n);
+    std::vector<Cand> cm, cc;
+    auto emit = [](std::vector<Cand>& cand, std::vector<int32_t>& cols, std::vector<int64_t>& tp,
+                   std::vector<Term>& terms) {
+        // entries in column order; a column's terms keep their generation order
+        std::stable_sort(cand.begin(), cand.end(), [](const Cand& x, const Cand& y) { return x.col < y.col; });
+        tp.push_back(0);
+        for (size_t a = 0; a < cand.size();) {
+            const int32_t col = cand[a].col;
+            for (; a < cand.size() && cand[a].col == col; ++a) terms.push_back(cand[a].t);
+            cols.push_back(col);
+            tp.push_back((int64_t)terms.size());
+        }
+    };
     for (int64_t oi = 0; oi < n; ++oi) {
         const int64_t i = order[oi];
-        auto& m = Mt[i];
-        auto& c = Ct[i];
-        c[(int32_t)i].push_back({-1, -1, -1});                 // e_i / L_ii
+        cm.clear();
+        cc.clear();
+        cc.push_back({(int32_t)i, {-1, -1, -1}});                       // e_i / L_ii
         for (int64_t e = dep_rp[i]; e < dep_rp[i + 1]; ++e) {
             const int32_t j = dep_row[e];
             const int64_t k = dep_val[e];
             if (p.grp[j] != p.grp[i]) {
-                m[j].push_back({k, -1, -1});                   // + L_ij / L_ii
+                cm.push_back({j, {k, -1, -1}});                         // + L_ij / L_ii
             } else {
-                for (const auto& kv : Mt[j]) m[kv.first].push_back({k, j, kv.first});
-                for (const auto& kv : Ct[j]) c[kv.first].push_back({k, j, kv.first});
+                for (int32_t b : mcols[j]) cm.push_back({b, {k, j, b}});
+                for (int32_t a : ccols[j]) cc.push_back({a, {k, j, a}});
             }
         }
+        emit(cm, mcols[i], mtp_r[i], mterms[i]);
+        emit(cc, ccols[i], ctp_r[i], cterms[i]);
     }
-    // flatten: entries per row ascending, then their terms
+    // flatten: rows ascending, entries ascending, then their terms
     p.mrp.assign(n + 1, 0);
     p.crp.assign(n + 1, 0);
     for (int64_t i = 0; i < n; ++i) {
-        p.mrp[i + 1] = p.mrp[i] + (int64_t)Mt[i].size();
-        p.crp[i + 1] = p.crp[i] + (int64_t)Ct[i].size();
+        p.mrp[i + 1] = p.mrp[i] + (int64_t)mcols[i].size();
+        p.crp[i + 1] = p.crp[i] + (int64_t)ccols[i].size();
+    }
+    p.mcol.reserve(p.mrp[n]);
+    p.ccol.reserve(p.crp[n]);
+    for (int64_t i = 0; i < n; ++i) {
+        p.mcol.insert(p.mcol.end(), mcols[i].begin(), mcols[i].end());
+        p.ccol.insert(p.ccol.end(), ccols[i].begin(), ccols[i].end());
     }
     auto entry = [](const std::vector<int64_t>& rp, const std::vector<int32_t>& col, int32_t row, int32_t c) {
         const auto b = col.begin() + rp[row], e = col.begin() + rp[row + 1];
         return (int64_t)(std::lower_bound(b, e, c) - col.begin());
     };
-    p.mcol.reserve(p.mrp[n]);
-    p.ccol.reserve(p.crp[n]);
-    for (int64_t i = 0; i < n; ++i) {
-        for (const auto& kv : Mt[i]) p.mcol.push_back(kv.first);
-        for (const auto& kv : Ct[i]) p.ccol.push_back(kv.first);
-    }
     p.mtp.assign(1, 0);
     p.ctp.assign(1, 0);
     for (int64_t i = 0; i < n; ++i) {
-        for (const auto& kv : Mt[i]) {
-            for (const Term& t : kv.second) {
-                p.mtk.push_back(t.k);
-                p.mts.push_back(t.src_row < 0 ? -1 : entry(p.mrp, p.mcol, t.src_row, t.src_col));
-            }
-            p.mtp.push_back((int64_t)p.mtk.size());
+        for (const Term& t : mterms[i]) {
+            p.mtk.push_back(t.k);
+            p.mts.push_back(t.src_row < 0 ? -1 : entry(p.mrp, p.mcol, t.src_row, t.src_col));
         }
-        for (const auto& kv : Ct[i]) {
-            for (const Term& t : kv.second) {
-                p.ctk.push_back(t.k);
-                p.cts.push_back(t.src_row < 0 ? -1 : entry(p.crp, p.ccol, t.src_row, t.src_col));
-            }
-            p.ctp.push_back((int64_t)p.ctk.size());
+        for (size_t e = 1; e < mtp_r[i].size(); ++e) p.mtp.push_back(p.mtp[p.mtp.size() - 1] + (mtp_r[i][e] - mtp_r[i][e - 1]));
+        for (const Term& t : cterms[i]) {
+            p.ctk.push_back(t.k);
+            p.cts.push_back(t.src_row < 0 ? -1 : entry(p.crp, p.ccol, t.src_row, t.src_col));
         }
+        for (size_t e = 1; e < ctp_r[i].size(); ++e) p.ctp.push_back(p.ctp[p.ctp.size() - 1] + (ctp_r[i][e] - ctp_r[i][e - 1]));
+        std::vector<Term>().swap(mterms[i]);
+        std::vector<Term>().swap(cterms[i]);
     }
     return p;
 }
