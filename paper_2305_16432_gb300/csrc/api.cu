@@ -131,7 +131,8 @@ npcg_status npcg_pattern_get_info(npcg_pattern p, npcg_pattern_info* out) {
     out->nlev_bwd = p->bwd.nlev;
     out->trsv_mode = p->trsv_mode != kTrsvCta ? NPCG_TRSV_SYNCFREE
                    : p->cta_flag ? NPCG_TRSV_LEVELFLAG
-                   : p->cta_split ? NPCG_TRSV_LEVELSPLIT : NPCG_TRSV_LEVELSYNC;
+                   : p->cta_split ? NPCG_TRSV_LEVELSPLIT
+                   : p->cta_merge ? NPCG_TRSV_LEVELMERGE : NPCG_TRSV_LEVELSYNC;
     out->tuned_ms_syncfree = p->tune_ms[0];
     out->tuned_ms_levelsync = p->tune_ms[1];
     out->tuned_ms_levelflag = p->tune_ms[2];
@@ -145,11 +146,21 @@ npcg_status npcg_pattern_set_trsv(npcg_pattern p, int32_t mode) {
     if (mode == NPCG_TRSV_AUTO) {
         trsv_pick_tuned(p);
     } else if (mode == NPCG_TRSV_LEVELMERGE) {
-        return set_error(p->h, NPCG_EINVAL, "merged-level solves are not enabled yet");
+        if (!kMergeEnabled) return set_error(p->h, NPCG_EINVAL, "merged-level solves are not enabled yet");
+        if (!p->cfwd.built || cta_stages(p->cfwd) < 2 || cta_stages(p->cbwd) < 2)
+            return set_error(p->h, NPCG_EINVAL, "level-synchronous layout does not fit shared memory");
+        NPCG_TRY(merge_build(p->h, p, kMergeLevels));
+        if (cta_stages(p->mfwd.lay) < 2 || cta_stages(p->mbwd.lay) < 2)
+            return set_error(p->h, NPCG_EINVAL, "merged-level layout does not fit shared memory");
+        p->trsv_mode = kTrsvCta;
+        p->cta_flag = false;
+        p->cta_split = false;
+        p->cta_merge = true;
     } else if (mode == NPCG_TRSV_SYNCFREE) {
         p->trsv_mode = kTrsvSyncFree;
         p->cta_flag = false;
         p->cta_split = false;
+        p->cta_merge = false;
     } else if (mode == NPCG_TRSV_LEVELSYNC || mode == NPCG_TRSV_LEVELFLAG || mode == NPCG_TRSV_LEVELSPLIT) {
         if (!p->cfwd.built || cta_stages(p->cfwd) < 2 || cta_stages(p->cbwd) < 2)
             return set_error(p->h, NPCG_EINVAL, "level-synchronous layout does not fit shared memory");
@@ -162,6 +173,7 @@ npcg_status npcg_pattern_set_trsv(npcg_pattern p, int32_t mode) {
         p->trsv_mode = kTrsvCta;
         p->cta_flag = mode == NPCG_TRSV_LEVELFLAG;
         p->cta_split = mode == NPCG_TRSV_LEVELSPLIT;
+        p->cta_merge = false;
     } else {
         return set_error(p->h, NPCG_EINVAL, "unknown triangular-solve mode");
     }

@@ -322,7 +322,12 @@ npcg_status pcg_run(Handle* h, Pattern* P, const double* A_val, const double* b,
                     npcg_solve_stats* stats);
 npcg_status ic0_run(Handle* h, Pattern* P, const double* A_val, double* L_val, double* alpha_out);
 npcg_status sgs_run(Handle* h, Pattern* P, const double* A_val, double* L_val);
+// merged-level solves: offered once they have run on a GPU; G levels per step
+constexpr bool kMergeEnabled = false;
+constexpr int kMergeLevels = 4;
 npcg_status merge_build(Handle* h, Pattern* P, int G);
+npcg_status merge_sptrsv(Handle* h, cudaStream_t s, Pattern* P, int transpose, const double* r, double* y, bool f32,
+                         cudaEvent_t e0, cudaEvent_t e1);
 npcg_status merge_factor_load(Handle* h, Pattern* P, const double* L_val);
 void merge_apply(Handle* h, cudaStream_t s, Pattern* P, bool f32);
 npcg_status gnn_forward_run(Handle* h, Pattern* P, const double* A_val, const double* b,

@@ -687,6 +687,10 @@ npcg_status factor_load(Handle* h, Pattern* P, const double* L_val) {
 npcg_status sptrsv_run(Handle* h, Pattern* P, int transpose, const double* r, double* y,
                        const int32_t*) {
     NPCG_CUDA(h, cudaMemsetAsync(P->ctl.p + 1, 0, 3 * sizeof(int), h->stream));
+    if (P->trsv_mode == kTrsvCta && P->cta_merge) {
+        NPCG_TRY(ensure_pcg_workspace(h, P));
+        return merge_sptrsv(h, h->stream, P, transpose, r, y, false, nullptr, nullptr);
+    }
     if (P->trsv_mode == kTrsvCta) {
         NPCG_TRY(ensure_pcg_workspace(h, P));
         const CtaLayout& C = transpose ? P->cbwd : P->cfwd;
@@ -712,7 +716,9 @@ npcg_status sptrsv_timed_run(Handle* h, Pattern* P, int transpose, const double*
     npcg_status st = NPCG_OK;
     for (int k = 0; k < reps && st == NPCG_OK; ++k) {
         cudaMemsetAsync(P->ctl.p + 1, 0, 3 * sizeof(int), h->stream);
-        if (P->trsv_mode == kTrsvCta) {
+        if (P->trsv_mode == kTrsvCta && P->cta_merge) {
+            st = merge_sptrsv(h, h->stream, P, transpose, r, y, f32, e0, e1);
+        } else if (P->trsv_mode == kTrsvCta) {
             const CtaLayout& C = transpose ? P->cbwd : P->cfwd;
             cta_gather(h, h->stream, C, P->n, r, P->r_cf.p, f32);
             if (C.blocked) k_fill_sentinel<<<h->num_sms * 4, 256, 0, h->stream>>>(P->n, P->y.p);

@@ -212,4 +212,25 @@ void merge_apply(Handle* h, cudaStream_t s, Pattern* P, bool f32) {
     cta_permute(h, s, P, B.lay, P->yq.p, f32, B.lay.cpos.p, P->z.p, false);
 }
 
+// One direction alone (L y = r, or L^T y = r with transpose): natural-order
+// r and y (FP64); the events, when given, bracket the triangular-solve kernel.
+npcg_status merge_sptrsv(Handle* h, cudaStream_t s, Pattern* P, int transpose, const double* r, double* y, bool f32,
+                         cudaEvent_t e0, cudaEvent_t e1) {
+    const MergeDir& D = transpose ? P->mbwd : P->mfwd;
+    if (!D.built) return set_error(h, NPCG_EINVAL, "merged-level layouts are not built");
+    const int64_t n = P->n;
+    const int blocks = std::max(1, std::min(ceil_div(n, 256), h->num_sms * 8));
+    if (f32)
+        k_merge_rhs<double, float><<<blocks, 256, 0, s>>>(n, D.lay.cperm.p, D.crp.p, D.ccol.p, D.C.p, r,
+                                                          reinterpret_cast<float*>(P->r_cf.p));
+    else
+        k_merge_rhs<double, double><<<blocks, 256, 0, s>>>(n, D.lay.cperm.p, D.crp.p, D.ccol.p, D.C.p, r,
+                                                           reinterpret_cast<double*>(P->r_cf.p));
+    NPCG_CUDA(h, cudaGetLastError());
+    if (e0) NPCG_CUDA(h, cudaEventRecord(e0, s));
+    NPCG_TRY(cta_trsv_launch(h, s, P, D.lay, P->r_cf.p, P->yq.p, nullptr, f32));
+    if (e1) NPCG_CUDA(h, cudaEventRecord(e1, s));
+    return cta_permute(h, s, P, D.lay, P->yq.p, f32, D.lay.cpos.p, y, false);
+}
+
 }  // namespace npcg

@@ -26,7 +26,7 @@ FP32, BF16 = 0, 1
 LOSS_AB, LOSS_FROB = 0, 1
 PREC_NONE, PREC_JACOBI, PREC_LLT, PREC_LLT32 = 0, 1, 2, 3
 METHOD_GNN, METHOD_IC0, METHOD_JACOBI, METHOD_CG, METHOD_SGS = 0, 1, 2, 3, 4
-TRSV_AUTO, TRSV_SYNCFREE, TRSV_LEVELSYNC, TRSV_LEVELFLAG, TRSV_LEVELSPLIT = 0, 1, 2, 3, 4
+TRSV_AUTO, TRSV_SYNCFREE, TRSV_LEVELSYNC, TRSV_LEVELFLAG, TRSV_LEVELSPLIT, TRSV_LEVELMERGE = 0, 1, 2, 3, 4, 5
 
 
 class NpcgError(RuntimeError):
@@ -216,7 +216,8 @@ class Pattern:
 
     def set_trsv(self, mode):
         """Force a triangular-solve design (TRSV_SYNCFREE / TRSV_LEVELSYNC /
-        TRSV_LEVELFLAG / TRSV_LEVELSPLIT) or restore the tuned one (TRSV_AUTO)."""
+        TRSV_LEVELFLAG / TRSV_LEVELSPLIT / TRSV_LEVELMERGE) or restore the
+        tuned one (TRSV_AUTO)."""
         self.h.check(lib().npcg_pattern_set_trsv(self.p, int(mode)))
         info = _Info()
         lib().npcg_pattern_get_info(self.p, C.byref(info))

@@ -696,3 +696,63 @@ def test_spmv_and_pcg_row_mappings(N, kmax):
     xg, st = N.pcg_solve(P, _gpu(Ao.val), _gpu(b), N.PREC_LLT, _gpu(Lo.val), rtol=1e-8)
     assert st[0]["status"] == 0 and abs(st[0]["iters"] - ito) <= 1
     assert np.linalg.norm(_np(xg) - xo) / np.linalg.norm(xo) <= 1e-8
+
+
+def _merge_or_skip(N, P):
+    try:
+        P.set_trsv(N.TRSV_LEVELMERGE)
+    except N.NpcgError as e:
+        if "not enabled" in str(e):
+            pytest.skip("merged-level solves are not enabled in this build")
+        raise
+
+
+@pytest.mark.parametrize("name", ["poisson2d_32", "fem34", "fd3d_var"])
+def test_merged_levels_parity(N, name):
+    # groups of levels per step (substituted rows): both directions against
+    # the oracle in FP64 and FP32, and PCG with IC(0) within one iteration
+    Ao, (rp, ci, v) = _assemble_both(N, PROBLEMS[name])
+    P = N.analyse(rp, ci)
+    _merge_or_skip(N, P)
+    assert P.trsv_mode == N.TRSV_LEVELMERGE
+    Lo, _ = O.ic0(Ao)
+    N.factor_load(P, _gpu(Lo.val))
+    r = np.random.default_rng(5).standard_normal(Ao.n)
+    assert _rel(_np(N.sptrsv(P, _gpu(r))), O.trsv_lower(Lo, r)) <= 1e-12
+    assert _rel(_np(N.sptrsv(P, _gpu(r), transpose=True)), O.trsv_upper(Lo, r)) <= 1e-12
+    L32 = O.CSR(Lo.row_ptr, Lo.col_idx, Lo.val.astype(np.float32).astype(np.float64))
+    r32 = r.astype(np.float32).astype(np.float64)
+    _, y32 = N.sptrsv_timed(P, _gpu(r), transpose=False, reps=1, f32=True)
+    assert _rel(_np(y32), O.trsv_lower(L32, r32)) <= 1e-4
+    b = I.rhs(Ao.n, 8)
+    xo, ito, _, _ = O.pcg(Ao, b, O.PREC_LLT, Lo, rtol=1e-8)
+    xg, st = N.pcg_solve(P, v, _gpu(b), N.PREC_LLT, _gpu(Lo.val), rtol=1e-8)
+    assert st[0]["status"] == 0 and abs(st[0]["iters"] - ito) <= 1
+    assert np.linalg.norm(_np(xg) - xo) / np.linalg.norm(xo) <= 1e-8
+
+
+def test_merged_levels_batched_pcg(N):
+    probs = [I.fem2d(30, sigma=1.0, seed=41), I.heat2d(26, seed=42), I.fd3d(8, 7, 6, sigma=1.0, seed=43)]
+    As, cis, vs, bs = [], [], [], []
+    off, sys_ptr = 0, [0]
+    for k, p in enumerate(probs):
+        Ao, (rp, ci, v) = _assemble_both(N, p)
+        As.append(Ao)
+        cis.append(_np(ci) + off)
+        vs.append(_np(v))
+        bs.append(I.rhs(Ao.n, 80 + k))
+        off += Ao.n
+        sys_ptr.append(off)
+    nnz_off = np.cumsum([0] + [a.nnz for a in As])
+    rp_cat = np.concatenate([a.row_ptr[:-1] + nnz_off[k] for k, a in enumerate(As)] + [[nnz_off[-1]]])
+    P = N.analyse(_gpu(rp_cat, torch.int32), _gpu(np.concatenate(cis), torch.int32), sys_ptr)
+    _merge_or_skip(N, P)
+    v_cat = _gpu(np.concatenate(vs))
+    Lg, _ = N.ic0_factor(P, v_cat)
+    x, st = N.pcg_solve(P, v_cat, _gpu(np.concatenate(bs)), N.PREC_LLT32, Lg, rtol=1e-8)
+    xs = _np(x)
+    for k, Ao in enumerate(As):
+        _, ito, _, _ = O.pcg(Ao, bs[k], O.PREC_LLT, O.ic0(Ao)[0], rtol=1e-8)
+        assert st[k]["status"] == 0 and abs(st[k]["iters"] - ito) <= max(1, int(np.ceil(0.05 * ito)))
+        seg = xs[sys_ptr[k]:sys_ptr[k + 1]]
+        assert np.linalg.norm(bs[k] - O.spmv(Ao, seg)) / np.linalg.norm(bs[k]) <= 2e-8
