@@ -441,7 +441,7 @@ def run_solve(args, rank, world, local):
     # PCG: 4 factor loads, init, preconditioner apply, r^T z, per graph trip 2
     # iterations (SpMV, update, r^T z and the apply) + the loop condition, stats;
     # the level-synchronous apply is 2 solves + 2 gathers, the sync-free one 2 solves
-    apply = 4 if P.trsv_mode in (N.TRSV_LEVELSYNC, N.TRSV_LEVELFLAG, N.TRSV_LEVELSPLIT) else 2
+    apply = {N.TRSV_LEVELSYNC: 4, N.TRSV_LEVELFLAG: 4, N.TRSV_LEVELSPLIT: 4, N.TRSV_LEVELMERGE: 5}.get(P.trsv_mode, 2)
     trips = max(1, math.ceil(max(it_l) / 2))
     pcg_launches = 4 + 1 + apply + 1 + (2 * (3 + apply) + 1) * trips + 1
     launches = (gnn_launches + pcg_launches) * args.steps
@@ -491,7 +491,7 @@ def run_solve(args, rank, world, local):
                         "sgs_iters": [x["iters"] for x in st_g] if nsys > 1 else st_g[0]["iters"],
                         "wall_s_timed": wall,
                         "trsv_design": {N.TRSV_LEVELSYNC: "levelsync", N.TRSV_LEVELFLAG: "levelflag",
-                                        N.TRSV_LEVELSPLIT: "levelsplit"}.get(
+                                        N.TRSV_LEVELSPLIT: "levelsplit", N.TRSV_LEVELMERGE: "levelmerge"}.get(
                             P.trsv_mode, "syncfree"),
                         "trsv_tuned_ms_fwd_bwd": P.tuned_ms},
             "roofline": {"kernel": trsv_kernel + " (forward SpTRSV, " + args.apply + ")", "bound": "hbm",

@@ -583,7 +583,9 @@ PcgArgs pcg_args(Pattern* P, int precond) {
     a.b = P->b.p;
     a.precond = precond;
     a.short_rows = P->max_row <= kShortRow;
-    const bool cta = P->trsv_mode == kTrsvCta && precond >= NPCG_PREC_LLT;
+    // the level-synchronous solve reads r in its processing order (the merged
+    // solve gathers r itself)
+    const bool cta = P->trsv_mode == kTrsvCta && !P->cta_merge && precond >= NPCG_PREC_LLT;
     a.rperm = cta ? (void*)P->r_cf.p : nullptr;
     a.cposf = cta ? P->cfwd.cpos.p : nullptr;
     a.rperm_f32 = precond == NPCG_PREC_LLT32;
