@@ -137,6 +137,8 @@ npcg_status npcg_pattern_get_info(npcg_pattern p, npcg_pattern_info* out) {
     out->tuned_ms_levelsync = p->tune_ms[1];
     out->tuned_ms_levelflag = p->tune_ms[2];
     out->tuned_ms_levelsplit = p->tune_ms[3];
+    out->tuned_ms_levelmerge = p->tune_ms[4];
+    out->merge_levels = p->merge_G;
     out->max_row = p->max_row;
     return NPCG_OK;
 }
@@ -149,7 +151,7 @@ npcg_status npcg_pattern_set_trsv(npcg_pattern p, int32_t mode) {
         if (!kMergeEnabled) return set_error(p->h, NPCG_EINVAL, "merged-level solves are not enabled yet");
         if (!p->cfwd.built || cta_stages(p->cfwd) < 2 || cta_stages(p->cbwd) < 2)
             return set_error(p->h, NPCG_EINVAL, "level-synchronous layout does not fit shared memory");
-        NPCG_TRY(merge_build(p->h, p, kMergeLevels));
+        NPCG_TRY(merge_build(p->h, p, p->merge_G ? p->merge_G : kMergeLevels));
         if (cta_stages(p->mfwd.lay) < 2 || cta_stages(p->mbwd.lay) < 2)
             return set_error(p->h, NPCG_EINVAL, "merged-level layout does not fit shared memory");
         p->trsv_mode = kTrsvCta;

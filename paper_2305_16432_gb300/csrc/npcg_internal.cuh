@@ -193,7 +193,9 @@ struct Pattern {
     TriLayout fwd, bwd;            // L y = r and L^T z = y
     CtaLayout cfwd, cbwd;          // level-synchronous layouts
     int trsv_mode = kTrsvSyncFree; // chosen by the autotuner
-    float tune_ms[4] = {0.f, 0.f, 0.f, 0.f}; // measured fwd+bwd time: sync-free, level barrier, level flags, split roles
+    float tune_ms[5] = {0.f, 0.f, 0.f, 0.f, 0.f}; // measured fwd+bwd time: sync-free, level barrier,
+                                                  // level flags, split roles, merged levels
+    int merge_G = 0;               // levels per step of the tuned merged-level layouts (0: none)
     bool cta_flag = false;         // level-ordered solves use the flag-synchronised FP32 kernel
     bool cta_split = false;        // level-ordered solves use the split-role kernel
     DevBuf<double> r_cf, y_cb, yglob;  // rhs in processing order, window backing

@@ -800,6 +800,38 @@ npcg_status trsv_autotune(Handle* h, Pattern* P) {
         }
         P->tune_ms[m] = (float)best;
     }
+    // merged levels: the fastest of 2, 4 and 8 levels per step
+    P->tune_ms[4] = 0.f;
+    P->merge_G = 0;
+    if (kMergeEnabled && !(P->nsys == 1 && P->n >= ((int64_t)1 << 18))) {
+        const int cand[3] = {2, 4, 8};
+        double best_all = 1e30;
+        for (int G : cand) {
+            if (merge_build(h, P, G) != NPCG_OK) continue;
+            if (cta_stages(P->mfwd.lay) < 2 || cta_stages(P->mbwd.lay) < 2) continue;
+            P->trsv_mode = kTrsvCta;
+            P->cta_flag = false;
+            P->cta_split = false;
+            P->cta_merge = true;
+            NPCG_TRY(merge_factor_load(h, P, L.p));
+            double best = 1e30;
+            for (int rep = 0; rep < 3; ++rep) {
+                double f = 0.0, b = 0.0;
+                NPCG_TRY(sptrsv_timed_run(h, P, 0, r.p, y.p, 1, &f, true));
+                NPCG_TRY(sptrsv_timed_run(h, P, 1, r.p, y.p, 1, &b, true));
+                best = std::min(best, f + b);
+            }
+            if (best < best_all) {
+                best_all = best;
+                P->merge_G = G;
+            }
+        }
+        P->cta_merge = false;
+        if (P->merge_G) {
+            P->tune_ms[4] = (float)best_all;
+            NPCG_TRY(merge_build(h, P, P->merge_G));
+        }
+    }
     trsv_pick_tuned(P);
     return NPCG_OK;
 }
@@ -807,12 +839,12 @@ npcg_status trsv_autotune(Handle* h, Pattern* P) {
 // the fastest measured design (a zero time: the design does not apply)
 void trsv_pick_tuned(Pattern* P) {
     int m = 0;
-    for (int k = 1; k < 4; ++k)
+    for (int k = 1; k < 5; ++k)
         if (P->tune_ms[k] > 0.f && P->tune_ms[k] < P->tune_ms[m]) m = k;
     P->trsv_mode = m == 0 ? kTrsvSyncFree : kTrsvCta;
     P->cta_flag = m == 2;
     P->cta_split = m == 3;
-    P->cta_merge = false;
+    P->cta_merge = m == 4 && P->mfwd.built && P->mbwd.built;
 }
 
 npcg_status spmv_run(Handle* h, Pattern* P, const double* A_val, const double* x, double* y) {

@@ -46,7 +46,8 @@ class _Info(C.Structure):
     _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("nnz_L", C.c_int64), ("nsys", C.c_int32),
                 ("nlev_fwd", C.c_int32), ("nlev_bwd", C.c_int32), ("trsv_mode", C.c_int32),
                 ("tuned_ms_syncfree", C.c_float), ("tuned_ms_levelsync", C.c_float),
-                ("tuned_ms_levelflag", C.c_float), ("tuned_ms_levelsplit", C.c_float), ("max_row", C.c_int32)]
+                ("tuned_ms_levelflag", C.c_float), ("tuned_ms_levelsplit", C.c_float), ("max_row", C.c_int32),
+                ("tuned_ms_levelmerge", C.c_float), ("merge_levels", C.c_int32)]
 
 
 class _Cfg(C.Structure):
@@ -211,7 +212,9 @@ class Pattern:
         self.trsv_mode = info.trsv_mode
         self.max_row = info.max_row
         self.tuned_ms = {"syncfree": info.tuned_ms_syncfree, "levelsync": info.tuned_ms_levelsync,
-                         "levelflag": info.tuned_ms_levelflag, "levelsplit": info.tuned_ms_levelsplit}
+                         "levelflag": info.tuned_ms_levelflag, "levelsplit": info.tuned_ms_levelsplit,
+                         "levelmerge": info.tuned_ms_levelmerge}
+        self.merge_levels = info.merge_levels
         self.sys_ptr = np.asarray(sys_ptr if sys_ptr is not None else [0, n], dtype=np.int64)
 
     def set_trsv(self, mode):
