@@ -225,6 +225,7 @@ class Pattern:
         info = _Info()
         lib().npcg_pattern_get_info(self.p, C.byref(info))
         self.trsv_mode = info.trsv_mode
+        self.merge_levels = info.merge_levels
 
     def export(self):
         dev = torch.device("cuda", self.h.device)
