@@ -698,7 +698,7 @@ __global__ void __launch_bounds__(kCtaThreads, 1) k_trsv_flag(CtaDev D, const fl
     int rel = c0;                         // chunks below rel are released by this warp
     StepOps<float> cur, nxt;
     bool have_cur = false;
-    int cur_c = c0, cur_e = 0, nxt_c = c0, nxt_e = 0;
+    int cur_e = 0, nxt_c = c0, nxt_e = 0;
     const int32_t* cur_hdr = whdr;
     const float* cur_vals = wvals;
     const int32_t* nxt_hdr = whdr;
@@ -819,7 +819,6 @@ __global__ void __launch_bounds__(kCtaThreads, 1) k_trsv_flag(CtaDev D, const fl
         if (!have_nxt && wdone) break;
         have_cur = have_nxt;
         cur = nxt;
-        cur_c = nxt_c;
         cur_e = nxt_e;
         cur_hdr = nxt_hdr;
         cur_vals = nxt_vals;
