@@ -803,7 +803,7 @@ npcg_status trsv_autotune(Handle* h, Pattern* P) {
     // merged levels: the fastest of 2, 4 and 8 levels per step
     P->tune_ms[4] = 0.f;
     P->merge_G = 0;
-    if (kMergeEnabled && !(P->nsys == 1 && P->n >= ((int64_t)1 << 18))) {
+    if (kMergeEnabled && !(P->nsys == 1 && P->n >= ((int64_t)1 << 18)) && P->n <= ((int64_t)1 << 22)) {
         const int cand[3] = {2, 4, 8};
         double best_all = 1e30;
         for (int G : cand) {

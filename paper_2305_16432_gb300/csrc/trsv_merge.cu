@@ -152,6 +152,8 @@ npcg_status merge_build(Handle* h, Pattern* P, int G) {
     if (G < 1 || G > 64) return set_error(h, NPCG_EINVAL, "levels per group must be in [1, 64]");
     if (P->nsys == 1 && P->n >= (int64_t)1 << 18)
         return set_error(h, NPCG_EINVAL, "merged levels are built for systems below 2^18 rows");
+    // the plan is built on the host (about a kilobyte per row in flight)
+    if (P->n > (int64_t)1 << 22) return set_error(h, NPCG_EINVAL, "merged levels are built for up to 2^22 rows");
     if (P->mfwd.built && P->mfwd.G == G && P->mbwd.built && P->mbwd.G == G) return NPCG_OK;
     P->mfwd.built = P->mbwd.built = false;
     NPCG_TRY(merge_build_dir(h, P, false, G, &P->mfwd));
