@@ -25,13 +25,16 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle.c with gcc (plain C11, no contraction, no -march)."""
+    """Compile oracle.c with gcc (plain C11, no contraction, no -march), with
+    OpenMP where the compiler has it (used only by set_threads)."""
     os.makedirs(os.path.dirname(_OUT), exist_ok=True)
     if not force and os.path.exists(_OUT) and os.path.getmtime(_OUT) >= os.path.getmtime(_SRC):
         return _OUT
     tmp = _OUT + f".tmp{os.getpid()}"
-    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-                    "-fno-fast-math", "-o", tmp, _SRC, "-lm"], check=True)
+    base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math"]
+    r = subprocess.run(base + ["-fopenmp", "-o", tmp, _SRC, "-lm"], capture_output=True)
+    if r.returncode != 0:
+        subprocess.run(base + ["-o", tmp, _SRC, "-lm"], check=True)
     os.replace(tmp, _OUT)
     return _OUT
 
@@ -56,6 +59,8 @@ def _L():
             lib.or_assemble_fem.restype = C.c_int64
             lib.or_fem_diagonals.argtypes = [C.c_int, i32p, i8p]
             lib.or_spmv.argtypes = [C.c_int32, i32p, i32p, f64p, f64p, f64p]
+            lib.or_set_threads.argtypes = [C.c_int]
+            lib.or_set_threads.restype = C.c_int
             lib.or_tril.argtypes = [C.c_int32, i32p, i32p, vp, vp, vp, vp, vp]
             lib.or_tril.restype = C.c_int64
             lib.or_levels_lower.argtypes = [C.c_int32, i32p, i32p, i32p]
@@ -178,6 +183,13 @@ def fem_diagonals(m, jitter):
     d = np.zeros((m - 1) * (m - 1), np.int8)
     _L().or_fem_diagonals(m, _i32(jitter), d)
     return d
+
+
+def set_threads(k: int) -> int:
+    """Host threads for SpMV and the PCG vector updates (1 = the plain
+    single-threaded oracle); results are identical for every count.  Returns
+    the count in effect (1 when the build has no OpenMP)."""
+    return int(_L().or_set_threads(int(k)))
 
 
 # ------------------------------------------------------------------ sparse

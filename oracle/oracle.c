@@ -1,6 +1,8 @@
 /*
  * oracle.c -- plain, slow, obviously-correct CPU reference of the learned
- * preconditioner hot path, in FP64, single-threaded.
+ * preconditioner hot path, in FP64, single-threaded (an OpenMP build may
+ * spread the independent rows of SpMV and the vector updates of PCG over
+ * host threads, with identical results: or_set_threads).
  *
  * TEST INFRASTRUCTURE ONLY.  Nothing in the product path links, loads or
  * calls this file; only tests/, __graft_entry__.smoke() and bench.py's
@@ -31,6 +33,26 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Host threads for the row-independent loops of the sparse matrix-vector
+ * product and the elementwise vector updates of PCG (OpenMP builds only; the
+ * default is one).  Each row or element is computed by exactly the
+ * arithmetic of the single-threaded loop, and the dot products, triangular
+ * solves and IC(0) stay sequential, so results do not depend on the thread
+ * count.  Returns the count in effect. */
+static int or_threads = 1;
+int or_set_threads(int k) {
+#ifdef _OPENMP
+    or_threads = k < 1 ? 1 : k;
+#else
+    (void)k;
+    or_threads = 1;
+#endif
+    return or_threads;
+}
 
 /* ======================================================================
  * Gaussian random field for log k: random Fourier features of the squared
@@ -306,6 +328,9 @@ int64_t or_assemble_fem(int m, const int32_t* jitter, int M, const double* omega
  * ==================================================================== */
 void or_spmv(int32_t n, const int32_t* rp, const int32_t* ci, const double* v,
              const double* x, double* y) {
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(or_threads) if (or_threads > 1)
+#endif
     for (int32_t i = 0; i < n; ++i) {
         double s = 0.0;
         for (int32_t k = rp[i]; k < rp[i + 1]; ++k) s += v[k] * x[ci[k]];
@@ -502,6 +527,9 @@ int or_pcg(int32_t n, const int32_t* rp, const int32_t* ci, const double* v, con
     double bnorm = sqrt(dot(n, b, b));
     double tol = rtol * bnorm;
     or_spmv(n, rp, ci, v, x, w);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(or_threads) if (or_threads > 1)
+#endif
     for (int32_t i = 0; i < n; ++i) r[i] = b[i] - w[i];
     double rnorm = sqrt(dot(n, r, r));
     int k = 0, status = 0;
@@ -515,6 +543,9 @@ int or_pcg(int32_t n, const int32_t* rp, const int32_t* ci, const double* v, con
         double pw = dot(n, p, w);
         if (!(pw > 0.0) || !isfinite(pw)) { status = 2; break; }
         double alpha = rz / pw;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(or_threads) if (or_threads > 1)
+#endif
         for (int32_t i = 0; i < n; ++i) { x[i] += alpha * p[i]; r[i] -= alpha * w[i]; }
         ++k;
         rnorm = sqrt(dot(n, r, r));
@@ -526,6 +557,9 @@ int or_pcg(int32_t n, const int32_t* rp, const int32_t* ci, const double* v, con
         if (!(rz_new > 0.0) || !isfinite(rz_new)) { status = 2; break; }
         double beta = rz_new / rz;
         rz = rz_new;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(or_threads) if (or_threads > 1)
+#endif
         for (int32_t i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
     }
 done:
@@ -546,6 +580,12 @@ done:
  *   diag_mode 1 (App. A.3, L D L^T with D = diag(A)): L = L' D^{1/2} with a
  *     unit-diagonal L', L'_ij = (s_ij + s_ji)/2, i.e. L_ii = sqrt(A_ii),
  *     L_ij = sqrt(A_jj) (s_ij + s_ji)/2
+ *   diag_mode 2 (the same L D L^T form with D = diag(A), the scaling taken on
+ *     the rows): L = D^{1/2} L~ with a unit-diagonal L~, L~_ij = (s_ij + s_ji)/2,
+ *     i.e. P = D^{1/2} L~ L~^T D^{1/2}, L~ a factor of the Jacobi-scaled
+ *     matrix D^{-1/2} A D^{-1/2}; L_ii = sqrt(A_ii), L_ij = sqrt(A_ii)
+ *     (s_ij + s_ji)/2, and the edge input is that matrix's entry
+ *     A_ij / sqrt(A_ii A_jj) (1 on the diagonal) instead of A_ij / s
  * Flat weights: node encoder, edge encoder, n_mp x (node MLP, edge MLP),
  * decoder; each Linear W[out][in] then b[out].
  * ==================================================================== */
@@ -704,10 +744,17 @@ static void gnn_forward_tape(const or_gnn_cfg* c, int32_t n, const int32_t* rp, 
         double x = b[i] / binf;
         mlp_fwd(w_encv, 1, h, h, l, &x, T->v + (size_t)i * h, T->tev + (size_t)i * Tenc);
     }
-    for (int64_t k = 0; k < nnz; ++k) {
-        double x = av[k] / sA;
-        mlp_fwd(w_ence, 1, h, h, l, &x, T->e + (size_t)k * h, T->tee + (size_t)k * Tenc);
-    }
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t k = rp[i]; k < rp[i + 1]; ++k) {
+            double x;
+            if (c->diag_mode == 2) {
+                const double aii = av[find_entry(rp, ci, i, i)], ajj = av[find_entry(rp, ci, ci[k], ci[k])];
+                x = av[k] / sqrt(aii * ajj);
+            } else {
+                x = av[k] / sA;
+            }
+            mlp_fwd(w_ence, 1, h, h, l, &x, T->e + (size_t)k * h, T->tee + (size_t)k * Tenc);
+        }
     double* in = (double*)malloc(sizeof(double) * 3 * (size_t)h);
     for (int t = 0; t < c->n_mp; ++t) {
         const double* wn = w_mp + t * (pn + pe);
@@ -758,6 +805,14 @@ static void gnn_forward_tape(const or_gnn_cfg* c, int32_t n, const int32_t* rp, 
                 else {
                     int32_t kji = find_entry(rp, ci, j, i);
                     Lv[kk] = sqrt(djj) * 0.5 * (T->s[kij] + T->s[kji]);
+                }
+            } else if (c->diag_mode == 2) {
+                /* L = D^{1/2} L~, unit-diagonal L~_ij = (s_ij + s_ji)/2 */
+                double dii = av[find_entry(rp, ci, i, i)];
+                if (j == i) Lv[kk] = sqrt(dii);
+                else {
+                    int32_t kji = find_entry(rp, ci, j, i);
+                    Lv[kk] = sqrt(dii) * 0.5 * (T->s[kij] + T->s[kji]);
                 }
             } else if (j == i) {
                 Lv[kk] = rs * softplus(T->s[kij]);
@@ -820,11 +875,13 @@ static void gnn_backward(const or_gnn_cfg* c, int32_t n, const int32_t* rp, cons
         for (int32_t kk = Lrp[i]; kk < Lrp[i + 1]; ++kk) {
             int32_t j = Lci[kk];
             int32_t kij = find_entry(rp, ci, i, j);
-            if (c->diag_mode == 1) {
-                /* L_ii = sqrt(A_ii) is fixed; L_ij = sqrt(A_jj) (s_ij + s_ji)/2 */
+            if (c->diag_mode == 1 || c->diag_mode == 2) {
+                /* L_ii = sqrt(A_ii) is fixed; L_ij = sqrt(A_cc) (s_ij + s_ji)/2
+                 * with c = j (mode 1, column scaling) or c = i (mode 2, rows) */
                 if (j != i) {
                     int32_t kji = find_entry(rp, ci, j, i);
-                    double g = sqrt(av[find_entry(rp, ci, j, j)]) * 0.5 * dL[kk];
+                    const int32_t cc = c->diag_mode == 1 ? j : i;
+                    double g = sqrt(av[find_entry(rp, ci, cc, cc)]) * 0.5 * dL[kk];
                     ds[kij] += g;
                     ds[kji] += g;
                 }

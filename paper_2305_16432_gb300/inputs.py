@@ -162,7 +162,7 @@ class GnnConfig:
     l: int = 2
     l_mp: int = 2
     h: int = 16
-    diag_mode: int = 0     # 0: L_ii = softplus(s_ii)
+    diag_mode: int = 0     # 0: L_ii = softplus(s_ii); 1: L = L' D^1/2; 2: L = D^1/2 L~ (D = diag A)
     x0_head: int = 0       # 1: initial-guess head (node MLP of depth l after the decoder)
     loss: int = 0          # training loss: 0 Eq. (loss_Ab), 1 the Frobenius loss Eq. (loss_A)
 

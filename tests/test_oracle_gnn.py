@@ -55,7 +55,13 @@ def _dense_gnn_impl(cfg, D, b, w):
     s = np.max(np.diag(D))
     binf = np.max(np.abs(b)) or 1.0
     V = _mlp(mlps[0], (b / binf)[:, None])
-    E = _mlp(mlps[1], (D / s)[:, :, None]) * mask[:, :, None]
+    if cfg.diag_mode == 2:
+        # edge input: the Jacobi-scaled matrix D^-1/2 A D^-1/2
+        dsq = np.sqrt(np.diag(D))
+        Ein = D / np.outer(dsq, dsq)
+    else:
+        Ein = D / s
+    E = _mlp(mlps[1], Ein[:, :, None]) * mask[:, :, None]
     for t in range(cfg.n_mp):
         agg = np.einsum("ijh,jh->ih", E, V)                 # sum_j e_ij (.) v_j
         V = _mlp(mlps[2 + 2 * t], np.concatenate([V, agg], 1))
@@ -69,6 +75,10 @@ def _dense_gnn_impl(cfg, D, b, w):
         # L' unit lower triangular, P = L' D L'^T with D = diag(A): L = L' D^1/2
         L[np.diag_indices(n)] = 1.0
         return (L @ np.diag(np.sqrt(np.diag(D)))) * np.tril(mask)
+    if cfg.diag_mode == 2:
+        # the rows scaled instead: L = D^1/2 L~, P = D^1/2 L~ L~^T D^1/2
+        L[np.diag_indices(n)] = 1.0
+        return (np.diag(np.sqrt(np.diag(D))) @ L) * np.tril(mask)
     sp = np.maximum(np.diag(S), 0) + np.log1p(np.exp(-np.abs(np.diag(S))))
     L[np.diag_indices(n)] = sp
     return math.sqrt(s) * L * np.tril(mask)
@@ -77,7 +87,8 @@ def _dense_gnn_impl(cfg, D, b, w):
 @pytest.mark.parametrize("cfg", [I.GnnConfig(n_mp=2, l=2, l_mp=2, h=4),
                                  I.GnnConfig(n_mp=3, l=1, l_mp=2, h=5),
                                  I.GnnConfig(n_mp=0, l=2, l_mp=2, h=3),
-                                 I.GnnConfig(n_mp=2, l=2, l_mp=1, h=4, diag_mode=1)])
+                                 I.GnnConfig(n_mp=2, l=2, l_mp=1, h=4, diag_mode=1),
+                                 I.GnnConfig(n_mp=2, l=2, l_mp=2, h=4, diag_mode=2)])
 def test_gnn_matches_dense_formulation(cfg):
     A = O.assemble(I.fem2d(6, sigma=1.0, seed=2))
     b = I.rhs(A.n, 3)
@@ -108,6 +119,47 @@ def test_ldlt_mode_zero_weights_is_jacobi():
     _, it_l, _, _ = O.pcg(A, b, O.PREC_LLT, L, rtol=1e-8)
     _, it_j, _, _ = O.pcg(A, b, O.PREC_JACOBI, rtol=1e-8)
     assert it_l == it_j
+
+
+def test_scaled_mode_zero_weights_is_jacobi():
+    # rows scaled: with zero weights L~ = I, so P = diag(A) again
+    cfg = I.GnnConfig(n_mp=2, l=2, l_mp=2, h=8, diag_mode=2)
+    A = O.assemble(I.fd3d(6, 5, 4, sigma=1.5, seed=4))
+    L = O.gnn_forward(cfg, A, I.rhs(A.n, 1), np.zeros(cfg.nparams))
+    assert np.allclose(L.dense() @ L.dense().T, np.diag(np.diag(A.dense())), rtol=1e-15, atol=0)
+
+
+def _ssor_weights(cfg, omega):
+    # n_mp = 0, l = 1, h = 2: the edge encoder splits its input x into
+    # (relu(x), relu(-x)) and passes them on, the decoder returns
+    # omega (relu(x) - relu(-x)) = omega x, so s_ij = omega * input_ij
+    assert (cfg.n_mp, cfg.l, cfg.h) == (0, 1, 2)
+    parts = []
+    for fi, fo in cfg.linears():
+        parts.append(np.zeros(fi * fo + fo))
+    enc_e1, enc_e2, dec1, dec2 = 2, 3, 4, 5
+    parts[enc_e1][:2] = [1.0, -1.0]                      # W [2][1]
+    parts[enc_e2][:4] = [1.0, 0.0, 0.0, 1.0]             # identity [2][2]
+    parts[dec1][:4] = [1.0, 0.0, 0.0, 1.0]
+    parts[dec2][:2] = [omega, -omega]                    # W [1][2]
+    return np.concatenate(parts)
+
+
+@pytest.mark.parametrize("omega", [1.0, 1.6])
+def test_scaled_mode_represents_ssor(omega):
+    # rows scaled with L~_ij = omega (D^-1/2 A D^-1/2)_ij gives the SSOR
+    # factor L = (D + omega L_A) D^-1/2, and at omega = 1 symmetric
+    # Gauss-Seidel, the oracle's own sgs factor
+    cfg = I.GnnConfig(n_mp=0, l=1, l_mp=1, h=2, diag_mode=2)
+    A = O.assemble(I.fd3d(6, 5, 4, sigma=1.5, seed=7))
+    w = _ssor_weights(cfg, omega)
+    L = O.gnn_forward(cfg, A, I.rhs(A.n, 2), w)
+    D = A.dense()
+    d = np.diag(D)
+    ref = (np.diag(d) + omega * np.tril(D, -1)) @ np.diag(1.0 / np.sqrt(d))
+    assert np.allclose(L.dense(), ref, rtol=1e-14, atol=1e-14 * np.abs(ref).max())
+    if omega == 1.0:
+        assert np.allclose(L.val, O.sgs(A).val, rtol=1e-14, atol=0)
 
 
 def test_gnn_no_message_passing_is_elementwise():
@@ -208,7 +260,8 @@ def test_loss_gradient_wrt_L_by_finite_differences():
 
 @pytest.mark.parametrize("cfg", [I.GnnConfig(n_mp=2, l=2, l_mp=2, h=3),
                                  I.GnnConfig(n_mp=1, l=1, l_mp=1, h=4),
-                                 I.GnnConfig(n_mp=1, l=2, l_mp=1, h=3, diag_mode=1)])
+                                 I.GnnConfig(n_mp=1, l=2, l_mp=1, h=3, diag_mode=1),
+                                 I.GnnConfig(n_mp=1, l=2, l_mp=1, h=3, diag_mode=2)])
 def test_loss_and_grad_central_differences(cfg):
     # central differences, eps = 1e-6, FP64, on every weight
     A = _tiny_system()

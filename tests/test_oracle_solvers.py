@@ -411,3 +411,24 @@ def test_sgs_pcg_between_jacobi_and_ic0_on_poisson():
     _, it_s, _, st = O.pcg(A, b, O.PREC_LLT, O.sgs(A), rtol=1e-8)
     _, it_i, _, _ = O.pcg(A, b, O.PREC_LLT, O.ic0(A)[0], rtol=1e-8)
     assert st == 0 and it_i < it_s < it_j
+
+
+def test_threaded_spmv_and_pcg_identical_to_single_thread():
+    # the all-cores leg of the oracle's timing runs the independent rows of
+    # SpMV and the elementwise PCG updates on several threads; every row and
+    # element keeps the single-threaded arithmetic, so results are identical
+    A = O.assemble(I.fd3d(18, sigma=1.5, corr_len=0.1, seed=2))
+    b = I.rhs(A.n, 3)
+    L, _ = O.ic0(A)
+    x = np.random.default_rng(1).standard_normal(A.n)
+    try:
+        assert O.set_threads(1) == 1
+        y1 = O.spmv(A, x)
+        x1, it1, r1, s1 = O.pcg(A, b, O.PREC_LLT, L, rtol=1e-10)
+        k = O.set_threads(4)
+        y4 = O.spmv(A, x)
+        x4, it4, r4, s4 = O.pcg(A, b, O.PREC_LLT, L, rtol=1e-10)
+    finally:
+        O.set_threads(1)
+    assert k in (1, 4)
+    assert np.array_equal(y1, y4) and np.array_equal(x1, x4) and (it1, r1, s1) == (it4, r4, s4)
