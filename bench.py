@@ -5,18 +5,24 @@ network factor + PCG, the paper's "precompute + solve" total, Sec. 5.1
 "Evaluation Metrics") next to IC(0)-PCG on the same GPU; secondary: SpTRSV
 bandwidth against the HBM roofline.
 
-Workload (one step = one system): 2-D variable-coefficient diffusion,
-P1 FEM on the Delaunay triangulation of a seeded jittered 256 x 256 lattice
-(n = 64,516, nnz = 449,582), log k a GRF (sigma 1, correlation 0.1),
-b ~ N(0,1); 6-layer hidden-64 network; FP64 PCG to 1e-6.  Inputs are
-resident in HBM when the timed region starts (pattern analysed once: a fixed
-mesh, as in the paper's environments); L2 is flushed between steps.
+Default workload (one step = one system): 3-D variable-coefficient
+diffusion, 7-point finite differences on a 128^3 grid (n = 2,097,152,
+nnz = 14,581,760), log k a GRF (sigma 1.5, correlation 0.05), b ~ N(0,1);
+6-layer hidden-64 network on the BF16 tensor cores; FP64 PCG to 1e-6 with
+FP32 triangular solves.  Inputs are resident in HBM when the timed region
+starts (the pattern is analysed once: a fixed mesh, as in the paper's
+environments; the analysis is timed separately as analyse_ms); L2 is flushed
+between steps.  Other workloads: --workload fem2d_256 (2-D FEM, n = 64,516),
+batched_256 (256 uneven systems in one batched solve), heat2d_256 (implicit
+heat step), train_32 (one training step).
 
 --impl reference times the CPU oracle (the method's plain FP64 restatement)
-on the host cores for the same metric; see cpu_baseline below.
-Multi-GPU (torchrun): every rank solves its own systems (independent
-problems, no collective on the data path); value = systems of all ranks per
-unit time, expressed as ms per system.
+on the host cores on a bounded sample of the same workload.
+Multi-GPU (torchrun): a single-system workload runs one replica per rank
+(independent systems seeded by rank, no collective on the data path: weak
+scaling); batched_256 splits its one fixed batch of 256 systems over the
+ranks by a greedy bin-pack on the nonzeros (strong scaling) and gathers the
+per-system statistics to rank 0 in the batch's order.
 """
 from __future__ import annotations
 
@@ -38,6 +44,10 @@ sys.path.insert(0, ROOT)
 WEIGHTS_DIR = os.path.join(ROOT, "paper_2305_16432_gb300", "weights")
 METRIC = "ms to 1e-6 rel. residual per system (learned vs IC(0) PCG); SpTRSV HBM GB/s"
 RTOL = 1e-6
+WORKLOAD_LABEL = {"fem2d_256": "fem2d_256_learned_pcg", "fd3d_128": "fd3d_128_learned_pcg",
+                  "batched_256": "batched_256_learned_pcg", "heat2d_256": "heat2d_256_learned_pcg"}
+SOLVE_WORKLOADS = tuple(WORKLOAD_LABEL)
+L2_FLUSH = "flushed between steps (256 MB write)"
 
 
 def _peaks():
@@ -134,62 +144,66 @@ def _load_weights(cfg, path):
         if meta.get("config"):
             cfg = I.GnnConfig(**meta["config"])
         if len(w) == cfg.nparams:
-            return w, "trained", meta
-    return I.gnn_weights(cfg, 1), "random-init", {}
+            return w, "trained", meta, cfg
+    return I.gnn_weights(cfg, 1), "random-init", {}, cfg
 
 
-def _strip(Ao, frac):
-    """Leading principal block (the first rows of the lexicographic order)."""
-    import oracle as O
-    m = max(2, int(Ao.n * frac))
-    e = int(Ao.row_ptr[m])
-    rows = np.repeat(np.arange(m), np.diff(Ao.row_ptr[:m + 1]))
-    keep = Ao.col_idx[:e] < m
-    rp = np.concatenate([[0], np.cumsum(np.bincount(rows[keep], minlength=m))])
-    return O.CSR(rp, Ao.col_idx[:e][keep], Ao.val[:e][keep])
+# ------------------------------------------------------------------ sharding
+def nnz_estimate(prob) -> int:
+    """Nonzeros of a synthetic system from its shape alone (no assembly):
+    exact for the FD stencils, 7 per unknown for the FEM lattices (six
+    neighbours and the diagonal of an interior lattice node)."""
+    from paper_2305_16432_gb300 import inputs as I
+    if prob.kind == I.FD:
+        nx, ny, nz = prob.nx, prob.ny, (prob.nz if prob.dim == 3 else 1)
+        faces = (nx - 1) * ny * nz + nx * (ny - 1) * nz + (nx * ny * (nz - 1) if prob.dim == 3 else 0)
+        return prob.n + 2 * faces
+    return 7 * prob.n
 
 
-def oracle_estimate(Ao, cfg, w, b, learned_iters, strip_nnz=6000):
-    """Oracle (CPU, FP64, 1 thread) cost of the learned path on one system:
-    network forward timed on a strip of about strip_nnz nonzeros (the
-    leading rows) scaled by nnz, plus PCG: per-iteration oracle cost on the
-    full system (same factor pattern) times the learned path's iteration
-    count.  Returns (ms, sample description)."""
-    import oracle as O
-    S = _strip(Ao, min(1.0, strip_nnz / max(1, Ao.nnz)))
-    t0 = time.perf_counter()
-    O.gnn_forward(cfg, S, b[:S.n], w)
-    t_gnn = (time.perf_counter() - t0) * Ao.nnz / S.nnz
-    L, _ = O.ic0(Ao)
-    k = 10
-    t0 = time.perf_counter()
-    O.pcg(Ao, b, O.PREC_LLT, L, rtol=0.0, max_iter=k)
-    t_it = (time.perf_counter() - t0) / k
-    ms = 1e3 * (t_gnn + t_it * learned_iters)
-    sample = (f"oracle network forward on the first {S.n} of {Ao.n} rows (nnz {S.nnz}) scaled by nnz "
-              f"to the full system, plus oracle PCG cost per iteration over {k} iterations on the full "
-              f"system times {learned_iters} learned-path iterations")
-    return ms, sample
+def partition_by_nnz(weights, world):
+    """Greedy bin-pack of systems onto ranks: the heaviest system first, each
+    into the currently lightest shard (ties to the lower rank).  Returns the
+    sorted system indices of every rank's shard."""
+    order = sorted(range(len(weights)), key=lambda k: (-weights[k], k))
+    load = [0] * world
+    shards = [[] for _ in range(world)]
+    for k in order:
+        r = min(range(world), key=lambda q: (load[q], q))
+        shards[r].append(k)
+        load[r] += weights[k]
+    return [sorted(s) for s in shards]
 
 
-def _host_csr(P_rp, P_ci, v):
-    import oracle as O
-    return O.CSR(P_rp.cpu().numpy(), P_ci.cpu().numpy(), v.cpu().numpy())
+def gather_stats(local, shard, nsys, world):
+    """Per-system statistics of every rank's shard, back in batch order (on
+    every rank; the one collective of the batched path, after the timing)."""
+    if world <= 1:
+        return list(local)
+    import torch.distributed as dist
+    parts = [None] * world
+    dist.all_gather_object(parts, (list(shard), list(local)))
+    out = [None] * nsys
+    for sh, st in parts:
+        for k, s in zip(sh, st):
+            out[k] = s
+    return out
 
 
-SOLVE_WORKLOADS = ("fem2d_256", "fd3d_128", "batched_256", "heat2d_256")
-
-
-def _problems(I, workload, rank):
-    """The systems rank `rank` solves: independent problems, seeded by rank
-    (weak scaling, no data-path collective)."""
+def _problems(I, workload, rank, world):
+    """(systems this rank solves, their indices in the workload's batch).
+    A single-system workload gives every rank its own system seeded by rank
+    (independent replicas); the batch is one fixed set of 256 systems split
+    by partition_by_nnz."""
     if workload == "fem2d_256":
-        return [I.fem2d_256(seed=rank)]
+        return [I.fem2d_256(seed=rank)], [0]
     if workload == "fd3d_128":
-        return [I.fd3d_128(seed=rank)]
+        return [I.fd3d_128(seed=rank)], [0]
     if workload == "heat2d_256":
-        return [I.heat2d(256, seed=rank)]
-    return I.batched_mix(256, seed=rank)
+        return [I.heat2d(256, seed=rank)], [0]
+    batch = I.batched_mix(256, seed=0)
+    shard = partition_by_nnz([nnz_estimate(p) for p in batch], world)[rank] if world > 1 else list(range(len(batch)))
+    return [batch[k] for k in shard], shard
 
 
 def job_ms_per_step(local_ms, world, device=None):
@@ -200,6 +214,11 @@ def job_ms_per_step(local_ms, world, device=None):
     t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
     torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_value(ms_per_step, systems_per_rank, world):
+    """Whole-job metric: ms per system over the systems all ranks solved."""
+    return ms_per_step / (systems_per_rank * world)
 
 
 def host_cpu():
@@ -229,11 +248,144 @@ def grad_allreduce_mean_(g, world):
     return g
 
 
-def job_value(ms_per_step, systems_per_rank, world):
-    """Whole-job metric: ms per system over the systems all ranks solved."""
-    return ms_per_step / (systems_per_rank * world)
+def solve_config(args, cfg, wkind, n, nnz, nnz_L, levels, nsys):
+    """The config block of the JSON line (identical on both arms)."""
+    return {"workload": WORKLOAD_LABEL[args.workload], "systems_per_step": nsys, "n": int(n), "nnz": int(nnz),
+            "nnz_L": int(nnz_L), "levels": int(levels),
+            "gnn": f"n_mp={cfg.n_mp},l={cfg.l},l_mp={cfg.l_mp},h={cfg.h},diag_mode={cfg.diag_mode},"
+                   + args.precision + (",x0_head" if args.x0 else ""),
+            "weights": wkind, "pcg": "fp64 recurrences, " + args.apply + " L L^T solves",
+            "rtol": RTOL, "l2": L2_FLUSH}
 
 
+# ------------------------------------------------------------------ oracle legs
+def _strip(Ao, frac):
+    """Leading principal block (the first rows of the lexicographic order)."""
+    import oracle as O
+    m = max(2, int(Ao.n * frac))
+    e = int(Ao.row_ptr[m])
+    rows = np.repeat(np.arange(m), np.diff(Ao.row_ptr[:m + 1]))
+    keep = Ao.col_idx[:e] < m
+    rp = np.concatenate([[0], np.cumsum(np.bincount(rows[keep], minlength=m))])
+    return O.CSR(rp, Ao.col_idx[:e][keep], Ao.val[:e][keep])
+
+
+def oracle_sample(Ao, cfg, w, b, learned_iters, L_pcg, strip_nnz=6000, k_iter=3, threads=1):
+    """One bounded sample of the oracle's cost for the learned path on one
+    system (CPU, FP64): the network forward timed on a leading strip of
+    about strip_nnz nonzeros and scaled by nnz, plus k_iter PCG iterations on
+    the full system with a factor of the same pattern (L_pcg), scaled to
+    learned_iters.  With threads > 1 the SpMV and vector updates of PCG run
+    on that many host threads (the network forward and the triangular solves
+    stay sequential).  Returns (ms per system, wall ms of the sample,
+    description)."""
+    import oracle as O
+    t_start = time.perf_counter()
+    S = _strip(Ao, min(1.0, strip_nnz / max(1, Ao.nnz)))
+    t0 = time.perf_counter()
+    O.gnn_forward(cfg, S, b[:S.n], w)
+    t_gnn = (time.perf_counter() - t0) * Ao.nnz / S.nnz
+    used = O.set_threads(threads)
+    t0 = time.perf_counter()
+    O.pcg(Ao, b, O.PREC_LLT, L_pcg, rtol=0.0, max_iter=k_iter)
+    t_it = (time.perf_counter() - t0) / k_iter
+    O.set_threads(1)
+    ms = 1e3 * (t_gnn + t_it * learned_iters)
+    wall = 1e3 * (time.perf_counter() - t_start)
+    desc = (f"oracle network forward on the first {S.n} of {Ao.n} rows (nnz {S.nnz}) scaled by nnz to the "
+            f"full system, plus {k_iter} oracle PCG iterations on the full system ({used} thread(s) for SpMV "
+            f"and vector updates) scaled to {learned_iters} iterations")
+    return ms, wall, desc, used
+
+
+def _oracle_system(I, workload):
+    """The workload's first system assembled by the oracle (host), its b,
+    its IC(0) factor (the PCG sample's factor of the same pattern) and its
+    level count."""
+    import oracle as O
+    if workload == "fem2d_256":
+        prob = I.fem2d_256(seed=0)
+    elif workload == "fd3d_128":
+        prob = I.fd3d_128(seed=0)
+    elif workload == "heat2d_256":
+        prob = I.heat2d(256, seed=0)
+    else:
+        raise ValueError(workload)
+    Ao = O.assemble(prob)
+    b = I.rhs(prob.n, 0)
+    Lo, _ = O.ic0(Ao)
+    _, nlev, _, _ = O.levels(Lo)
+    return prob, Ao, b, Lo, nlev
+
+
+def learned_iters_of(meta, workload):
+    """Learned-path PCG iterations of the GPU arm on the workload's system,
+    recorded beside the weights by the benchmark of the committed network."""
+    return int(meta.get("bench_iters", {}).get(workload, 0)) or None
+
+
+def run_reference(args):
+    """The oracle as it stands, timed on the host cores on a bounded sample of
+    the same workload (rank 0 only): every step is one oracle_sample."""
+    rank, world, _ = _dist()
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_2305_16432_gb300 import inputs as I
+    O.build()
+    if args.workload not in ("fem2d_256", "fd3d_128", "heat2d_256"):
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle reference arm covers the single-system "
+                          "workloads (fd3d_128, fem2d_256, heat2d_256)"}))
+        return
+    w, wkind, meta, cfg = _load_weights(I.GnnConfig(n_mp=6, l=2, l_mp=2, h=64), args.weights)
+    prob, Ao, b, Lo, nlev = _oracle_system(I, args.workload)
+    iters = learned_iters_of(meta, args.workload) or 200
+    vals, walls = [], []
+    desc, used = "", 1
+    for s in range(args.warmup + args.steps):
+        ms, wall, desc, used = oracle_sample(Ao, cfg, w, b, iters, Lo)
+        if s >= args.warmup:
+            vals.append(ms)
+            walls.append(wall)
+    v = float(np.mean(vals))
+    config = solve_config(args, cfg, wkind, Ao.n, Ao.nnz, Lo.nnz, nlev, 1)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms/system", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(walls)),
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config,
+            "cpu_baseline": {"value": v, "unit": "ms/system", "cores": used, "kind": "oracle",
+                             "sample": desc + f"; ms_per_step is the wall time of one such sample, value the "
+                                              f"per-system cost it extrapolates to", "host": host_cpu()},
+            "e2e": {"value": v, "unit": "ms/system", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def validate_oracle_estimate(args):
+    """Runs the oracle's full learned path once on the 256^2 FEM system (the
+    network forward over every row, then FP64 PCG with that factor to
+    1e-6) and the sampled estimate beside it, so the extrapolation of
+    oracle_sample is checked against a measurement.  Prints one JSON line."""
+    import oracle as O
+    from paper_2305_16432_gb300 import inputs as I
+    O.build()
+    cfg0 = I.GnnConfig(n_mp=6, l=2, l_mp=2, h=64)
+    w, wkind, meta, cfg = _load_weights(cfg0, weights_for("fem2d_256"))
+    prob, Ao, b, Lo, nlev = _oracle_system(I, "fem2d_256")
+    t0 = time.perf_counter()
+    Lg = O.gnn_forward(cfg, Ao, b, w.astype(np.float64))
+    t_gnn = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    _, it, rel, st = O.pcg(Ao, b, O.PREC_LLT, Lg, rtol=RTOL)
+    t_pcg = time.perf_counter() - t0
+    full_ms = 1e3 * (t_gnn + t_pcg)
+    est, wall, desc, _ = oracle_sample(Ao, cfg, w, b, it, Lo)
+    print(json.dumps({"workload": "fem2d_256", "oracle_full_ms": full_ms, "oracle_gnn_ms": 1e3 * t_gnn,
+                      "oracle_pcg_ms": 1e3 * t_pcg, "oracle_iters": it, "status": st,
+                      "estimate_ms": est, "estimate_over_full": est / full_ms, "sample_wall_ms": wall,
+                      "sample": desc, "host": host_cpu()}), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
 def _assemble(N, I, probs, rank):
     """Assemble every system on the GPU; one concatenated pattern."""
     import torch
@@ -255,44 +407,9 @@ def _assemble(N, I, probs, rank):
     return rp_cat, ci_cat, v_cat, b, sys_ptr
 
 
-def run_reference(args):
-    """The oracle as it stands, timed on the host cores on a bounded sample of
-    the same workload (rank 0 only)."""
-    rank, world, _ = _dist()
-    if rank != 0:
-        return
-    import oracle as O
-    from paper_2305_16432_gb300 import inputs as I
-    O.build()
-    if args.workload not in ("fem2d_256",):
-        print(json.dumps({"impl": "reference", "unavailable": "oracle reference arm is defined for fem2d_256"}))
-        return
-    prob = I.fem2d_256(seed=0)
-    cfg = I.GnnConfig(n_mp=6, l=2, l_mp=2, h=64)
-    w, kind, meta = _load_weights(cfg, weights_for("fem2d_256"))
-    if meta.get("config"):
-        cfg = I.GnnConfig(**meta["config"])
-    Ao = O.assemble(prob)
-    b = I.rhs(prob.n, 0)
-    iters = int(meta.get("learned_iters_fem256", 0)) or 191
-    vals = []
-    sample = ""
-    for s in range(args.warmup + args.steps):
-        ms, sample = oracle_estimate(Ao, cfg, w, b, iters)
-        if s >= args.warmup:
-            vals.append(ms)
-    v = float(np.mean(vals))
-    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms/system", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "fem2d_256_learned_pcg", "n": prob.n, "rtol": RTOL},
-            "cpu_baseline": {"value": v, "unit": "ms/system", "cores": 1, "kind": "oracle", "sample": sample,
-                             "host": host_cpu()},
-            "e2e": {"value": v, "unit": "ms/system", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
-
-
 def _timed(fn, k, stream, flush):
+    """k runs of fn, each between CUDA events on the launching stream, L2
+    flushed before each.  Returns (ms list, last result)."""
     import torch
     ms, last = [], None
     for _ in range(k):
@@ -307,28 +424,23 @@ def _timed(fn, k, stream, flush):
     return ms, last
 
 
-def _spmv_roofline(N, P, v, hbm, reps=50):
-    """SpMV y = A x, back-to-back launches between CUDA events (the kernel is
-    HBM-bound; a secondary roofline beside the triangular solve)."""
+def _spmv_roofline(N, P, v, hbm, flush, reps=20):
+    """SpMV y = A x, one launch between CUDA events after each L2 flush (a
+    cold-cache DRAM number at every size; the kernel is HBM-bound)."""
     import torch
     x = torch.randn(P.n, dtype=torch.float64, device=v.device)
     y = torch.empty_like(x)
     stream = torch.cuda.current_stream()
     for _ in range(3):
         N.spmv(P, v, x, out=y)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(reps):
-        N.spmv(P, v, x, out=y)
-    e1.record(stream)
-    e1.synchronize()
-    ms = e0.elapsed_time(e1) / reps
+    ms, _ = _timed(lambda: N.spmv(P, v, x, out=y), reps, stream, flush)
+    t = float(np.mean(ms))
     byts = 12 * P.nnz + 4 * (P.n + 1) + 16 * P.n
-    ach = byts / (ms * 1e-3) / 1e9
+    ach = byts / (t * 1e-3) / 1e9
     kname = "k_spmv_rows" if P.max_row <= 16 else "k_spmv_plain"
     return {"kernel": kname + " (SpMV, FP64)", "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-            "frac": ach / hbm, "bytes_per_launch": byts, "ms_per_launch": ms}
+            "frac": ach / hbm, "bytes_per_launch": byts, "ms_per_launch": t,
+            "timing": "one launch per event pair, L2 flushed before each"}
 
 
 def run_solve(args, rank, world, local):
@@ -337,15 +449,17 @@ def run_solve(args, rank, world, local):
     from paper_2305_16432_gb300 import npcg as N
 
     prec = N.BF16 if args.precision == "bf16" else N.FP32
-    cfg = I.GnnConfig(n_mp=6, l=2, l_mp=2, h=64)
-    w_np, wkind, wmeta = _load_weights(cfg, args.weights)
-    if wmeta.get("config"):
-        cfg = I.GnnConfig(**wmeta["config"])
+    cfg0 = I.GnnConfig(n_mp=6, l=2, l_mp=2, h=64)
+    w_np, wkind, wmeta, cfg = _load_weights(cfg0, args.weights)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    probs = _problems(I, args.workload, rank)
+    probs, shard = _problems(I, args.workload, rank, world)
     rp, ci, v, b, sys_ptr = _assemble(N, I, probs, rank)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
     P = N.analyse(rp, ci, sys_ptr if len(probs) > 1 else None)
+    torch.cuda.synchronize()
+    analyse_ms = 1e3 * (time.perf_counter() - t0)
     nsys = P.nsys
     w = torch.as_tensor(w_np, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
@@ -356,22 +470,29 @@ def run_solve(args, rank, world, local):
     use_x0 = bool(args.x0)
     if use_x0 and not cfg.x0_head:
         raise SystemExit("--x0 needs weights with an initial-guess head")
+    Lbuf = torch.empty(P.nnz_L, dtype=torch.float64, device=dev)
+
+    def factor():
+        if use_x0:
+            return N.gnn_factor_x0(P, v, b, cfg, w, precision=prec)
+        return N.gnn_factor(P, v, b, cfg, w, precision=prec, out=Lbuf), None
 
     def learned_step():
-        if use_x0:
-            L, x0 = N.gnn_factor_x0(P, v, b, cfg, w, precision=prec)
-        else:
-            L, x0 = N.gnn_factor(P, v, b, cfg, w, precision=prec), None
+        L, x0 = factor()
         x, st = N.pcg_solve(P, v, b, pc, L, rtol=RTOL, x0=x0)
         return st
 
     def ic0_step():
-        L, _ = N.ic0_factor(P, v)
+        L, _ = N.ic0_factor(P, v, out=Lbuf)
         x, st = N.pcg_solve(P, v, b, pc, L, rtol=RTOL)
         return st
 
     def sgs_step():
-        x, st = N.pcg_solve(P, v, b, pc, N.sgs_factor(P, v), rtol=RTOL)
+        x, st = N.pcg_solve(P, v, b, pc, N.sgs_factor(P, v, out=Lbuf), rtol=RTOL)
+        return st
+
+    def jacobi_step():
+        x, st = N.pcg_solve(P, v, b, N.PREC_JACOBI, None, rtol=RTOL)
         return st
 
     for _ in range(args.warmup):
@@ -390,32 +511,48 @@ def run_solve(args, rank, world, local):
     clk = clocks.stop()
     if world > 1:
         torch.distributed.barrier()
+    ms_per_step = job_ms_per_step(float(np.sum(ms_l)) / args.steps, world, dev)
+    total_sys = 256 if args.workload == "batched_256" else nsys * world
+    value = ms_per_step / total_sys
+    st_all = gather_stats(st_l, shard, 256, world) if args.workload == "batched_256" else st_l
+    it_l = [s["iters"] for s in st_l]
+    assert all(s["status"] == 0 for s in st_l), "a system did not converge"
+
+    # the comparison preconditioners on the same systems
     ms_i, st_i = _timed(ic0_step, args.steps, stream, flush)
     sgs_step()
     ms_g, st_g = _timed(sgs_step, args.steps, stream, flush)
-    ms_per_step = job_ms_per_step(float(np.sum(ms_l)) / args.steps, world, dev)
-    value = job_value(ms_per_step, nsys, world)
-    it_l = [s["iters"] for s in st_l]
+    jacobi_step()
+    ms_j, st_j = _timed(jacobi_step, args.steps, stream, flush)
     it_i = [s["iters"] for s in st_i]
-    assert all(s["status"] == 0 for s in st_l + st_i), "a system did not converge"
 
-    # dominant kernel: the level-ordered triangular solve, timed alone
+    # phases of the two totals (precompute and solve), each from CUDA events
+    ms_gnn, _ = _timed(lambda: factor(), args.steps, stream, flush)
+    Lg = factor()[0].clone()
+    x0g = factor()[1]
+    ms_lp, _ = _timed(lambda: N.pcg_solve(P, v, b, pc, Lg, rtol=RTOL, x0=x0g), args.steps, stream, flush)
+    ms_ic, _ = _timed(lambda: N.ic0_factor(P, v, out=Lbuf), args.steps, stream, flush)
+    Li = Lbuf.clone()
+    ms_ip, _ = _timed(lambda: N.pcg_solve(P, v, b, pc, Li, rtol=RTOL), args.steps, stream, flush)
+
+    # dominant kernel: the triangular solve of the tuned design, timed alone
     hbm, bf16, peak_kind = _peaks()
-    Lic, _ = N.ic0_factor(P, v)
-    N.factor_load(P, Lic)
+    N.factor_load(P, Li)
     r = torch.randn(P.n, dtype=torch.float64, device=dev)
     trsv_ms, _ = N.sptrsv_timed(P, r, transpose=False, reps=args.trsv_reps, f32=apply32)
     # SpTRSV bytes per launch: index + value per L entry, row pointer, rhs + solution
     trsv_bytes = (8 if apply32 else 12) * P.nnz_L + 4 * (P.n + 1) + 16 * P.n
     achieved = trsv_bytes / (trsv_ms * 1e-3) / 1e9
-    trsv_kernel = {N.TRSV_LEVELSYNC: "k_trsv_cta", N.TRSV_LEVELSPLIT: "k_trsv_split",
-                   N.TRSV_LEVELFLAG: "k_trsv_flag" if apply32 else "k_trsv_cta"}.get(P.trsv_mode, "k_trsv")
+    design = {N.TRSV_LEVELSYNC: "levelsync", N.TRSV_LEVELFLAG: "levelflag", N.TRSV_LEVELSPLIT: "levelsplit",
+              N.TRSV_LEVELMERGE: "levelmerge"}.get(P.trsv_mode, "syncfree")
+    trsv_kernel = {"levelsync": "k_trsv_cta", "levelsplit": "k_trsv_split", "levelmerge": "k_trsv_cta",
+                   "levelflag": "k_trsv_flag" if apply32 else "k_trsv_cta"}.get(design, "k_trsv")
     # DRAM bytes of one forward launch from an ncu capture of this kernel
     traffic = None
     prof = os.path.join(ROOT, "profiles", "trsv_traffic.json")
     if os.path.exists(prof):
-        traffic = json.load(open(prof)).get(f"{args.workload}_{trsv_kernel}_fwd_bytes")
-    spmv_rl = _spmv_roofline(N, P, v, hbm)
+        traffic = json.load(open(prof)).get(f"{args.workload}_{trsv_kernel}_{design}_fwd_bytes")
+    spmv_rl = _spmv_roofline(N, P, v, hbm, flush)
 
     # end to end through the C ABI with host buffers (pinned)
     a_host = torch.empty(P.nnz, dtype=torch.float64, pin_memory=True)
@@ -431,71 +568,52 @@ def run_solve(args, rank, world, local):
         N.solve_host(P, a_host.numpy(), b_host.numpy(), method=N.METHOD_GNN, cfg=cfg, weights=w,
                      precision=prec, rtol=RTOL, x_host=x_host.numpy(), f32_apply=apply32)
         ts.append(time.perf_counter() - t0)
-    e2e_ms = 1e3 * float(np.mean(ts[args.warmup:])) / (nsys * world)
+    e2e_ms = job_ms_per_step(1e3 * float(np.mean(ts[args.warmup:])), world, dev) / total_sys
     h2d = 8 * (P.nnz + P.n)
     d2h = 8 * P.n
 
     # kernel launches per learned step (counted from the launch structure):
     # network: scales, 2 encoders, 2 per layer, decoder, L assembly
     gnn_launches = 1 + 2 + 2 * cfg.n_mp + 1 + 1
-    # PCG: 4 factor loads, init, preconditioner apply, r^T z, per graph trip 2
-    # iterations (SpMV, update, r^T z and the apply) + the loop condition, stats;
-    # the level-synchronous apply is 2 solves + 2 gathers, the sync-free one 2 solves
-    apply = {N.TRSV_LEVELSYNC: 4, N.TRSV_LEVELFLAG: 4, N.TRSV_LEVELSPLIT: 4, N.TRSV_LEVELMERGE: 5}.get(P.trsv_mode, 2)
+    # PCG: factor loads, init, preconditioner apply, r^T z, per graph trip 2
+    # iterations (SpMV, update, r^T z and the apply) + the loop condition, stats
+    apply = {"levelsync": 4, "levelflag": 4, "levelsplit": 4, "levelmerge": 5}.get(design, 2)
+    loads = 2 + (2 * P.merge_levels if design == "levelmerge" else 0) + 2
     trips = max(1, math.ceil(max(it_l) / 2))
-    pcg_launches = 4 + 1 + apply + 1 + (2 * (3 + apply) + 1) * trips + 1
+    pcg_launches = loads + 1 + apply + 1 + (2 * (3 + apply) + 1) * trips + 1
     launches = (gnn_launches + pcg_launches) * args.steps
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        import oracle as O
-        O.build()
-        bh = b.cpu().numpy()
-        rph, cih, vh = rp.cpu().numpy(), ci.cpu().numpy(), v.cpu().numpy()
-        # a bounded sample: up to three members of the workload, scaled by nnz
-        members = list(range(nsys)) if nsys <= 3 else [0, nsys // 2, nsys - 1]
-        tot_ms, nnz_s, samples = 0.0, 0, []
-        for k in members:
-            r0, r1 = sys_ptr[k], sys_ptr[k + 1]
-            e0, e1 = int(rph[r0]), int(rph[r1])
-            Ao = O.CSR(rph[r0:r1 + 1] - e0, cih[e0:e1] - r0, vh[e0:e1])
-            ms_k, smp = oracle_estimate(Ao, cfg, w_np, bh[r0:r1], it_l[k])
-            tot_ms += ms_k
-            nnz_s += Ao.nnz
-            samples.append(smp)
-        ms_cpu = tot_ms * (P.nnz / nnz_s) / nsys
-        smp = samples[0] if nsys == 1 else (
-            f"{len(members)} of {nsys} members, each: " + samples[0] + "; scaled by nnz to the batch, per system")
-        cpu = {"value": ms_cpu, "unit": "ms/system", "cores": 1, "kind": "oracle", "sample": smp,
-               "host": host_cpu()}
+        cpu = _cpu_baseline(I, cfg, w_np, rp, ci, v, b, sys_ptr, nsys, it_l, P)
 
     if rank == 0:
-        wl = {"fem2d_256": "fem2d_256_learned_pcg", "fd3d_128": "fd3d_128_learned_pcg",
-              "batched_256": "batched_256_learned_pcg", "heat2d_256": "heat2d_256_learned_pcg"}[args.workload]
+        med = lambda a: float(np.median(a)) / nsys   # noqa: E731
         line = {
             "metric": METRIC, "value": value, "unit": "ms/system", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False,
+            "scaling": "strong" if (args.workload == "batched_256" and world > 1) else "weak",
             "vs_baseline": None, "dtype": "f64+" + args.precision, "data": "synthetic",
-            "config": {"workload": wl, "systems_per_step": nsys, "n": P.n, "nnz": P.nnz, "nnz_L": P.nnz_L,
-                       "levels": P.nlev_fwd, "gnn": f"n_mp={cfg.n_mp},l={cfg.l},l_mp={cfg.l_mp},h={cfg.h},"
-                       f"diag_mode={cfg.diag_mode}," + args.precision + (",x0_head" if use_x0 else ""),
-                       "weights": wkind, "pcg": "fp64 recurrences, " + args.apply + " L L^T solves",
-                       "rtol": RTOL, "l2": "flushed between steps (256 MB write)"},
-            "compare": {"learned_iters": it_l if nsys > 1 else it_l[0],
-                        "learned_ms_median": float(np.median(ms_l)),
+            "config": solve_config(args, cfg, wkind, P.n, P.nnz, P.nnz_L, P.nlev_fwd, nsys),
+            "compare": {"learned_iters": [s["iters"] for s in st_all] if len(st_all) > 1 else it_l[0],
+                        "learned_ms_median": med(ms_l),
                         # the paper's statistic: mean of the fastest 5 timed runs
-                        "learned_ms_fastest5_mean": float(np.mean(np.sort(ms_l)[:5])),
+                        "learned_ms_fastest5_mean": float(np.mean(np.sort(ms_l)[:5])) / nsys,
+                        "gnn_ms": med(ms_gnn), "learned_pcg_ms": med(ms_lp),
+                        "ic0_ms_per_system": float(np.mean(ms_i)) / nsys,
                         "ic0_ms_fastest5_mean": float(np.mean(np.sort(ms_i)[:5])) / nsys,
-                        "ic0_ms_per_system": float(np.mean(ms_i)) / nsys, "ic0_iters": it_i if nsys > 1 else it_i[0],
+                        "ic0_factor_ms": med(ms_ic), "ic0_pcg_ms": med(ms_ip),
+                        "ic0_iters": it_i if nsys > 1 else it_i[0],
+                        "jacobi_ms_per_system": float(np.mean(ms_j)) / nsys,
+                        "jacobi_iters": [x["iters"] for x in st_j] if nsys > 1 else st_j[0]["iters"],
                         "sgs_ms_per_system": float(np.mean(ms_g)) / nsys,
                         "sgs_iters": [x["iters"] for x in st_g] if nsys > 1 else st_g[0]["iters"],
-                        "wall_s_timed": wall,
-                        "trsv_design": {N.TRSV_LEVELSYNC: "levelsync", N.TRSV_LEVELFLAG: "levelflag",
-                                        N.TRSV_LEVELSPLIT: "levelsplit", N.TRSV_LEVELMERGE: "levelmerge"}.get(
-                            P.trsv_mode, "syncfree"),
+                        "analyse_ms": analyse_ms,
+                        "wall_s_timed": wall, "trsv_design": design,
+                        "merge_levels": P.merge_levels if design == "levelmerge" else 0,
                         "trsv_tuned_ms_fwd_bwd": P.tuned_ms},
-            "roofline": {"kernel": trsv_kernel + " (forward SpTRSV, " + args.apply + ")", "bound": "hbm",
-                         "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "roofline": {"kernel": trsv_kernel + " (forward SpTRSV, " + args.apply + ", " + design + ")",
+                         "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                          "peak_kind": peak_kind, "traffic": traffic, "bytes_per_launch": trsv_bytes,
                          "ms_per_launch": trsv_ms, "levels": P.nlev_fwd},
             "roofline_spmv": dict(spmv_rl, peak_kind=peak_kind),
@@ -504,7 +622,42 @@ def run_solve(args, rank, world, local):
             "gpu_launches": launches,
             "clocks": clk,
         }
+        if args.workload == "batched_256" and world > 1:
+            line["config"]["parallelism"] = f"{world} shards of one batch of 256 (greedy bin-pack on nnz)"
         print(json.dumps(line), flush=True)
+
+
+def _cpu_baseline(I, cfg, w_np, rp, ci, v, b, sys_ptr, nsys, it_l, P):
+    """The oracle on the host cores, on a bounded sample of the same systems:
+    one core (the oracle as it stands) and all cores (OpenMP SpMV and vector
+    updates).  The PCG sample uses the oracle's own IC(0) factor (the same
+    pattern as the learned one; values do not change the cost)."""
+    import oracle as O
+    O.build()
+    bh = b.cpu().numpy()
+    rph, cih, vh = rp.cpu().numpy(), ci.cpu().numpy(), v.cpu().numpy()
+    members = list(range(nsys)) if nsys <= 3 else [0, nsys // 2, nsys - 1]
+    sysm = {}
+    for k in members:
+        r0, r1 = sys_ptr[k], sys_ptr[k + 1]
+        e0, e1 = int(rph[r0]), int(rph[r1])
+        Ao = O.CSR(rph[r0:r1 + 1] - e0, cih[e0:e1] - r0, vh[e0:e1])
+        sysm[k] = (Ao, O.ic0(Ao)[0], bh[r0:r1])
+    res = {}
+    for threads in (1, os.cpu_count() or 1):
+        tot_ms, nnz_s, desc, used = 0.0, 0, "", 1
+        for k in members:
+            Ao, Lo, bk = sysm[k]
+            ms_k, _, desc, used = oracle_sample(Ao, cfg, w_np, bk, it_l[k], Lo, threads=threads)
+            tot_ms += ms_k
+            nnz_s += Ao.nnz
+        ms_cpu = tot_ms * (P.nnz / nnz_s) / nsys
+        smp = desc if nsys == 1 else (f"{len(members)} of {nsys} members, each: " + desc +
+                                      "; scaled by nnz to the batch, per system")
+        res[threads] = {"value": ms_cpu, "unit": "ms/system", "cores": used, "kind": "oracle", "sample": smp}
+    one = res[1]
+    allc = res[max(res)]
+    return dict(one, host=host_cpu(), all_cores=allc if allc is not one else None)
 
 
 def run_train(args, rank, world, local):
@@ -561,7 +714,7 @@ def run_train(args, rank, world, local):
                            "nnz": P.nnz, "systems": 32, "pairs": pairs,
                            "loss": "Eq. loss_A (Frobenius)" if args.loss == "frob" else "Eq. loss_Ab",
                            "parallelism": f"dp{world} (gradient all-reduce)" if world > 1 else "dp1",
-                           "gnn": "n_mp=6,l=2,l_mp=2,h=64", "l2": "flushed between steps (256 MB write)"},
+                           "gnn": "n_mp=6,l=2,l_mp=2,h=64", "l2": L2_FLUSH},
                 "loss_last": loss, "roofline": None, "cpu_baseline": None, "e2e": None, "clocks": clk}
         print(json.dumps(line), flush=True)
 
@@ -572,8 +725,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="fem2d_256", choices=list(SOLVE_WORKLOADS) + ["train_32"],
-                    help="fem2d_256 (the headline line), fd3d_128, batched_256 or train_32")
+    ap.add_argument("--workload", default="fd3d_128", choices=list(SOLVE_WORKLOADS) + ["train_32"],
+                    help="fd3d_128 (the headline line), fem2d_256, batched_256, heat2d_256 or train_32")
     ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16"],
                     help="network arithmetic: BF16 tensor cores (default) or FP32")
     ap.add_argument("--apply", default="fp32", choices=["fp32", "fp64"],
@@ -584,11 +737,16 @@ def main():
     ap.add_argument("--x0", action="store_true",
                     help="start PCG from the network's initial guess (weights with an initial-guess head)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--validate-oracle-estimate", action="store_true",
+                    help="run the oracle's full learned path on the 256^2 FEM system beside its sampled estimate")
     ap.add_argument("--trsv-reps", type=int, default=50)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.weights is None:
         args.weights = weights_for(args.workload, args.x0)
+    if args.validate_oracle_estimate:
+        validate_oracle_estimate(args)
+        return
     if args.impl == "reference":
         run_reference(args)
         return

@@ -21,8 +21,8 @@ def test_weights_match_their_config(fname):
     cfg = I.GnnConfig(**meta["config"])
     assert w.dtype == np.float32 and w.ndim == 1 and len(w) == cfg.nparams
     assert np.all(np.isfinite(w))
-    w2, kind, meta2 = bench._load_weights(I.GnnConfig(n_mp=6, l=2, l_mp=2, h=64), os.path.join(WDIR, fname))
-    assert kind == "trained" and len(w2) == len(w) and meta2["config"] == meta["config"]
+    w2, kind, meta2, cfg2 = bench._load_weights(I.GnnConfig(n_mp=6, l=2, l_mp=2, h=64), os.path.join(WDIR, fname))
+    assert kind == "trained" and len(w2) == len(w) and meta2["config"] == meta["config"] and cfg2 == cfg
 
 
 def test_bench_picks_each_workloads_network():
