@@ -19,7 +19,7 @@ constexpr int kSlice = 32;                 // rows per SELL slice = one warp of 
 constexpr int kChunk = 512;                // rows per reduction chunk (one block)
 constexpr int kChunkThreads = 256;
 constexpr int kShortRow = 16;    // rows up to this length: one thread per row in the SpMV
-constexpr long long kSpinLimit = 1LL << 22; // polls before a device wait gives up (~1-2 s)
+constexpr long long kSpinLimit = 1LL << 22; // default polls before a device wait gives up (~1-2 s)
 
 // bits of a canonical-free signalling NaN: "value not yet written"
 constexpr unsigned long long kSentinelBits = 0x7FF4DEADBEEFCAFEull;
@@ -217,6 +217,7 @@ struct Pattern {
     // cached iteration graphs (keyed by precond)
     cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};
     int graph_mode[4] = {0, 0, 0, 0};
+    long long graph_spin[4] = {0, 0, 0, 0};   // wait limit the graph's launches were captured with
     GnnStore gnn;
     FrobLayout frob;
     MergeDir mfwd, mbwd;           // merged-level solves (built on request)
@@ -229,6 +230,7 @@ struct Handle {
     cudaStream_t capture_stream = nullptr;   // private, for graph capture
     int device = 0;
     int num_sms = 0;
+    long long spin_limit = kSpinLimit;       // polls before a device wait gives up (npcg_set_wait_limit)
     std::string last_error;
     DevBuf<int> scratch_i;      // small device scratch
     void* host_pinned = nullptr; // small pinned host scratch
@@ -292,6 +294,8 @@ npcg_status pattern_build(Handle* h, int64_t n, int64_t nnz, const int32_t* rp,
 npcg_status factor_load(Handle* h, Pattern* P, const double* L_val);
 npcg_status sptrsv_run(Handle* h, Pattern* P, int transpose, const double* r, double* y,
                        const int32_t* sys_active);
+// the sync-free solve with the first `skip` slices never claimed (failure-path tests)
+npcg_status sptrsv_unclaimed_run(Handle* h, Pattern* P, int transpose, int skip, const double* r, double* y);
 npcg_status spmv_run(Handle* h, Pattern* P, const double* A_val, const double* x, double* y);
 // An arbitrary dependency pattern for cta_layout_build instead of the
 // direction's rows of tril(A): host levels and row pointer, device row
@@ -324,8 +328,9 @@ npcg_status pcg_run(Handle* h, Pattern* P, const double* A_val, const double* b,
                     npcg_solve_stats* stats);
 npcg_status ic0_run(Handle* h, Pattern* P, const double* A_val, double* L_val, double* alpha_out);
 npcg_status sgs_run(Handle* h, Pattern* P, const double* A_val, double* L_val);
-// merged-level solves: offered once they have run on a GPU; G levels per step
-constexpr bool kMergeEnabled = false;
+// merged-level solves (G levels per step): offered to the autotuner and to
+// npcg_pattern_set_trsv
+constexpr bool kMergeEnabled = true;
 constexpr int kMergeLevels = 4;
 npcg_status merge_build(Handle* h, Pattern* P, int G);
 npcg_status merge_sptrsv(Handle* h, cudaStream_t s, Pattern* P, int transpose, const double* r, double* y, bool f32,
