@@ -23,9 +23,10 @@
  *     present (a matrix of an undirected mesh graph with self-loops).
  *   - The return code is the only error channel.  On error, npcg_last_error()
  *     gives a one-line description.  Calls never abort the process.
- *   - Device-side waits (the sync-free triangular solves and IC(0)) have an
- *     iteration limit; reaching it returns NPCG_ETIMEOUT and leaves the
- *     context usable.
+ *   - Device-side waits (on rows, levels or copies that other threads of
+ *     the same launch produce: the triangular solves, IC(0), the level
+ *     analysis) have an iteration limit (npcg_set_wait_limit); reaching it
+ *     returns NPCG_ETIMEOUT and leaves the context usable.
  */
 #ifndef NPCG_H
 #define NPCG_H
@@ -50,7 +51,9 @@ typedef enum {
     NPCG_ENOTSPD = 4,      /* IC(0) failed for every shift; L_ii <= 0        */
     NPCG_EBREAKDOWN = 5,   /* PCG: p^T A p <= 0, r^T z <= 0, or non-finite   */
     NPCG_EMAXITER = 6,     /* PCG: max_iter updates without reaching rtol    */
-    NPCG_ETIMEOUT = 7      /* a device spin-wait reached its iteration limit */
+    NPCG_ETIMEOUT = 7,     /* a device spin-wait reached its iteration limit */
+    NPCG_ESTALL = 8        /* PCG: ||r|| not below its best for stall_iters
+                              updates (npcg_pcg_solve_ex)                   */
 } npcg_status;
 
 typedef struct npcg_handle_s* npcg_handle;     /* stream, workspace, error text */
@@ -63,9 +66,20 @@ typedef struct npcg_pattern_s* npcg_pattern;   /* analysed sparsity pattern     
  * (a cudaStream_t; NULL = legacy default stream).  *out is owned by the
  * caller and released with npcg_destroy. */
 NPCG_API npcg_status npcg_create(npcg_handle* out, void* stream);
+/* Destroys the handle.  Patterns analysed with it should be freed first;
+ * any left are detached (calls with them return NPCG_EINVAL) and must
+ * still be released with npcg_pattern_free. */
 NPCG_API npcg_status npcg_destroy(npcg_handle h);
 /* Last error message of the handle (static storage owned by the handle). */
 NPCG_API const char* npcg_last_error(npcg_handle h);
+/* Polls after which every device wait of later calls on this handle gives
+ * up (the sync-free and level-ordered triangular solves, IC(0), the level
+ * analysis): the kernel records a timeout, stops, and the call returns
+ * NPCG_ETIMEOUT with the context still usable.  polls <= 0 restores the
+ * default of 2^22 (about one to two seconds of polling).  A short limit
+ * (e.g. 2^10) lets a failure-detection test make a wait run out quickly; a
+ * limit too short for a real workload makes its solves time out. */
+NPCG_API npcg_status npcg_set_wait_limit(npcg_handle h, int64_t polls);
 NPCG_API const char* npcg_status_string(npcg_status s);
 
 /* --------------------------------------------------------------------------
@@ -149,12 +163,18 @@ NPCG_API npcg_status npcg_pattern_free(npcg_pattern p);
  *   NPCG_TRSV_LEVELSPLIT: the level-synchronous design with the step
  *     bookkeeping on separate warps: operand warps stage step k+1 while
  *     compute warps solve step k (one system per SM).
- * npcg_analyse times the designs on the pattern and keeps the fastest. */
+ * npcg_analyse times the sync-free, level-synchronous and merged-level
+ * designs on the pattern and keeps the fastest (the flag and split-role
+ * variants measured slower everywhere and are only selected explicitly). */
 enum { NPCG_TRSV_AUTO = 0, NPCG_TRSV_SYNCFREE = 1, NPCG_TRSV_LEVELSYNC = 2, NPCG_TRSV_LEVELFLAG = 3,
        NPCG_TRSV_LEVELSPLIT = 4,
-       /* groups of consecutive levels per step (substituted rows, see the
-        * plan in csrc/level_merge.h); reserved: npcg_pattern_set_trsv
-        * returns NPCG_EINVAL until the design has been run on a GPU       */
+       /* the level-synchronous design over groups of G consecutive levels:
+        * substituting the dependencies inside a group gives
+        *   y_i = sum_a C_ia r_a - sum_b M_ib y_b
+        * (a in the row's group, b in earlier groups), so one step solves a
+        * group; C and M are evaluated from each loaded factor.  Single
+        * systems below 2^18 rows and patterns up to 2^22 rows; G = 2, 4 or 8
+        * as tuned (4 when set before tuning found one)                    */
        NPCG_TRSV_LEVELMERGE = 5 };
 
 typedef struct {
@@ -204,8 +224,16 @@ enum { NPCG_FP32 = 0, NPCG_BF16 = 1 };
 /* Diagonal rule.  NPCG_DIAG_SOFTPLUS: L_ii = sqrt(s) softplus(s_ii) (above).
  * NPCG_DIAG_LDLT_DIAGA (App. A.3): P = L' D L'^T with D = diag(A) and a
  * unit-diagonal L', L'_ij = (s_ij + s_ji)/2; returned as L = L' D^{1/2}, i.e.
- * L_ii = sqrt(A_ii), L_ij = sqrt(A_jj) (s_ij + s_ji)/2 (no sqrt(s) scaling). */
-enum { NPCG_DIAG_SOFTPLUS = 0, NPCG_DIAG_LDLT_DIAGA = 1 };
+ * L_ii = sqrt(A_ii), L_ij = sqrt(A_jj) (s_ij + s_ji)/2 (no sqrt(s) scaling).
+ * NPCG_DIAG_LDLT_ROWS: the same L D L^T form with the scaling on the rows,
+ * L = D^{1/2} L~ with a unit-diagonal L~_ij = (s_ij + s_ji)/2, i.e.
+ * L_ii = sqrt(A_ii), L_ij = sqrt(A_ii) (s_ij + s_ji)/2, so that L~ factors
+ * the Jacobi-scaled matrix D^{-1/2} A D^{-1/2}; the edge input is then that
+ * matrix's entry A_ij / sqrt(A_ii A_jj) instead of A_ij / s.  (The network's
+ * L~_ij is symmetric in the ends of the edge; scaling the rows lets it
+ * express SSOR, L~ = omega times the scaled strict lower triangle, on
+ * matrices whose diagonal varies.) */
+enum { NPCG_DIAG_SOFTPLUS = 0, NPCG_DIAG_LDLT_DIAGA = 1, NPCG_DIAG_LDLT_ROWS = 2 };
 
 typedef struct {
     int32_t n_mp;        /* message-passing layers                       */
@@ -283,9 +311,12 @@ enum { NPCG_PREC_NONE = 0, NPCG_PREC_JACOBI = 1, NPCG_PREC_LLT = 2, NPCG_PREC_LL
  * the PCG recurrences, dot products and SpMV stay FP64. */
 
 typedef struct {
-    int32_t iters;       /* updates of x                                  */
+    int32_t iters;       /* updates of x (both runs after a fallback)     */
     int32_t status;      /* npcg_status of this system                    */
     double relres;       /* ||r_k|| / ||b|| (recursive residual)          */
+    int32_t fallback;    /* 1: the factored solve failed and IC(0) took
+                            over (npcg_pcg_solve_ex, npcg_solve_host)     */
+    int32_t fallback_iters; /* updates made with the IC(0) factor         */
 } npcg_solve_stats;
 
 NPCG_API npcg_status npcg_pcg_solve(npcg_handle h, npcg_pattern p, const double* A_val,
@@ -300,6 +331,30 @@ NPCG_API npcg_status npcg_pcg_solve_batched(npcg_handle h, npcg_pattern p, const
                                    const double* L_val, double rtol, int32_t max_iter,
                                    npcg_solve_stats* stats);
 
+/* Options of npcg_pcg_solve_ex. */
+typedef struct {
+    int32_t stall_iters;   /* > 0: a system whose ||r|| has not fallen below
+                              its smallest value so far for this many
+                              consecutive updates stops with NPCG_ESTALL   */
+    int32_t fallback_ic0;  /* != 0 (NPCG_PREC_LLT / _LLT32 only): a system
+                              that stops with NPCG_EBREAKDOWN, NPCG_EMAXITER
+                              or NPCG_ESTALL is solved again with IC(0)'s
+                              factor (Sec. 5.1 baseline, npcg_ic0_factor):
+                              from x_0 after a breakdown, otherwise from its
+                              last iterate, with a fresh max_iter; stats
+                              record the switch (fallback, fallback_iters)  */
+} npcg_solve_opts;
+
+/* npcg_pcg_solve / npcg_pcg_solve_batched (any pattern) with options; opts
+ * may be NULL (the plain call).  With the fallback, L_val is left as given
+ * and the IC(0) factor lives in the pattern's workspace.  Returns the status
+ * of the last run (NPCG_OK when every system converged, first or after the
+ * fallback).  Synchronises. */
+NPCG_API npcg_status npcg_pcg_solve_ex(npcg_handle h, npcg_pattern p, const double* A_val,
+                                       const double* b, double* x, int32_t precond,
+                                       const double* L_val, double rtol, int32_t max_iter,
+                                       const npcg_solve_opts* opts, npcg_solve_stats* stats);
+
 /* --------------------------------------------------------------------------
  * Building blocks of the iteration (Algorithm 1), exposed for tests and
  * bandwidth measurement.  y = A x:
@@ -312,6 +367,16 @@ NPCG_API npcg_status npcg_factor_load(npcg_handle h, npcg_pattern p, const doubl
  * solves L^T y = r (r, y [n], distinct). */
 NPCG_API npcg_status npcg_sptrsv(npcg_handle h, npcg_pattern p, int32_t transpose,
                         const double* r, double* y);
+/* Failure injection for tests (host-side; nothing faults): the sync-free
+ * triangular solve of npcg_sptrsv (NPCG_TRSV_SYNCFREE, whatever design is
+ * tuned) with its first `skip` slices of 32 rows (in level order) never
+ * claimed.  Those rows are never written, so every row that depends on
+ * them waits until the handle's wait limit; the call then returns
+ * NPCG_ETIMEOUT (NPCG_OK when nothing depends on them).  skip outside
+ * [0, slices] returns NPCG_EINVAL.  y [n] is left partly unwritten.
+ * Synchronises. */
+NPCG_API npcg_status npcg_sptrsv_unclaimed(npcg_handle h, npcg_pattern p, int32_t transpose, int32_t skip,
+                                           const double* r, double* y);
 /* Same solve repeated reps times (f32 != 0: FP32 factor and arithmetic, as in
  * NPCG_PREC_LLT32); *ms_per_launch (host) is the mean duration of the
  * triangular-solve kernel alone, from CUDA events recorded on the handle's
@@ -354,9 +419,11 @@ NPCG_API npcg_status npcg_adam_step(npcg_handle h, int64_t n, float* w, const fl
  * cfg + device weights, NPCG_METHOD_IC0, NPCG_METHOD_JACOBI, NPCG_METHOD_CG,
  * NPCG_METHOD_SGS),
  * runs PCG from x_0 = 0 and copies x out to x_host [n].  f32_apply != 0
- * applies the L L^T preconditioners in FP32 (NPCG_PREC_LLT32).  Host buffers
- * should be pinned for asynchronous copies.  stats: host [nsys].
- * Synchronises.
+ * applies the L L^T preconditioners in FP32 (NPCG_PREC_LLT32).  With
+ * NPCG_METHOD_GNN a system whose learned-factor solve breaks down, reaches
+ * max_iter or stagnates for 200 updates falls back to IC(0) as in
+ * npcg_pcg_solve_ex (stats[s].fallback).  Host buffers should be pinned for
+ * asynchronous copies.  stats: host [nsys].  Synchronises.
  * ------------------------------------------------------------------------ */
 enum { NPCG_METHOD_GNN = 0, NPCG_METHOD_IC0 = 1, NPCG_METHOD_JACOBI = 2, NPCG_METHOD_CG = 3,
        NPCG_METHOD_SGS = 4 };
@@ -377,16 +444,20 @@ NPCG_API npcg_status npcg_solve_host(npcg_handle h, npcg_pattern p, int32_t meth
  * device, caller-owned; x holds x_0 on entry).  No handle, no pattern, no
  * cudaMalloc / cudaFree or allocating library call: the working vectors and
  * the solver state live in one fixed device array inside the library,
- * sized for n <= NPCG_NOALLOC_MAX_N (about 8 MB), which every GPU that
+ * sized for n <= NPCG_NOALLOC_MAX_N (about 10 MB), which every GPU that
  * loads the library keeps until the process exits.  Larger n, other
- * preconditioners or NULL arrays return NPCG_EINVAL before any GPU work.
+ * preconditioners or NULL arrays return NPCG_EINVAL before any GPU work;
+ * with Jacobi, a row without a nonzero finite diagonal entry returns
+ * NPCG_EINVAL after the first pass.  A CUDA error already pending on the
+ * calling thread returns NPCG_ECUDA before any launch.
  * The first call on a device looks up that array's device address (and may
- * load the library's device code), so make it before any stream capture.
+ * load the library's device code).  Every call synchronises its stream
+ * (every 16 iterations, to test convergence), so it must never be called
+ * while that stream is being captured into a CUDA graph.
  * All calls on a device share the array: calls that overlap on the GPU
  * (other streams, other host threads) race and corrupt each other; the
  * array keeps the last call's contents, which each call resets as needed.
- * Work runs on `stream` (a cudaStream_t); the call synchronises it every
- * 16 iterations to test convergence.  stats: host, one entry.
+ * Work runs on `stream` (a cudaStream_t).  stats: host, one entry.
  * ------------------------------------------------------------------------ */
 #define NPCG_NOALLOC_MAX_N 262144
 

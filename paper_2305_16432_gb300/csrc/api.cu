@@ -32,6 +32,7 @@ Pattern* PT(npcg_pattern p) { return static_cast<Pattern*>(p); }
 npcg_status check_hp(npcg_handle h, npcg_pattern p) {
     if (!h) return NPCG_EINVAL;
     if (!p) return set_error(H(h), NPCG_EINVAL, "pattern is NULL");
+    if (!PT(p)->h) return set_error(H(h), NPCG_EINVAL, "the pattern's handle was destroyed");
     if (PT(p)->h != H(h)) return set_error(H(h), NPCG_EINVAL, "pattern was analysed with another handle");
     int dev = -1;
     cudaGetDevice(&dev);
@@ -53,6 +54,7 @@ const char* npcg_status_string(npcg_status s) {
         case NPCG_EBREAKDOWN: return "NPCG_EBREAKDOWN";
         case NPCG_EMAXITER: return "NPCG_EMAXITER";
         case NPCG_ETIMEOUT: return "NPCG_ETIMEOUT";
+        case NPCG_ESTALL: return "NPCG_ESTALL";
     }
     return "NPCG_UNKNOWN";
 }
@@ -78,11 +80,20 @@ npcg_status npcg_destroy(npcg_handle h) {
     if (!h) return NPCG_EINVAL;
     if (h->stream) cudaStreamSynchronize(h->stream);
     if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
+    // patterns that outlive their handle are detached: every later call with
+    // them fails the handle check, and npcg_pattern_free only frees memory
+    for (Pattern* p : h->patterns) p->h = nullptr;
     delete h;
     return NPCG_OK;
 }
 
 const char* npcg_last_error(npcg_handle h) { return h ? h->last_error.c_str() : "handle is NULL"; }
+
+npcg_status npcg_set_wait_limit(npcg_handle h, int64_t polls) {
+    if (!h) return NPCG_EINVAL;
+    h->spin_limit = polls > 0 ? (long long)polls : kSpinLimit;
+    return NPCG_OK;
+}
 
 npcg_status npcg_assemble_count(npcg_handle h, const npcg_problem* p, int64_t* n_out, int64_t* nnz_out) {
     if (!h) return NPCG_EINVAL;
@@ -110,13 +121,19 @@ npcg_status npcg_analyse(npcg_handle h, int64_t n, int64_t nnz, const int32_t* r
         delete P;
         return s;
     }
+    H(h)->patterns.push_back(P);
     *out = P;
     return NPCG_OK;
 }
 
 npcg_status npcg_pattern_free(npcg_pattern p) {
     if (!p) return NPCG_EINVAL;
-    if (p->h && p->h->stream) cudaStreamSynchronize(p->h->stream);
+    if (p->h) {
+        if (p->h->stream) cudaStreamSynchronize(p->h->stream);
+        auto& v = p->h->patterns;
+        for (size_t k = 0; k < v.size(); ++k)
+            if (v[k] == p) { v.erase(v.begin() + (long)k); break; }
+    }
     delete p;
     return NPCG_OK;
 }
@@ -144,7 +161,7 @@ npcg_status npcg_pattern_get_info(npcg_pattern p, npcg_pattern_info* out) {
 }
 
 npcg_status npcg_pattern_set_trsv(npcg_pattern p, int32_t mode) {
-    if (!p) return NPCG_EINVAL;
+    if (!p || !p->h) return NPCG_EINVAL;
     if (mode == NPCG_TRSV_AUTO) {
         trsv_pick_tuned(p);
     } else if (mode == NPCG_TRSV_LEVELMERGE) {
@@ -252,6 +269,14 @@ npcg_status npcg_pcg_solve_batched(npcg_handle h, npcg_pattern p, const double* 
     return pcg_run(H(h), PT(p), A_val, b, x, precond, L_val, rtol, max_iter, stats);
 }
 
+npcg_status npcg_pcg_solve_ex(npcg_handle h, npcg_pattern p, const double* A_val, const double* b, double* x,
+                              int32_t precond, const double* L_val, double rtol, int32_t max_iter,
+                              const npcg_solve_opts* opts, npcg_solve_stats* stats) {
+    NPCG_TRY(check_hp(h, p));
+    if (!A_val || !b || !x || !stats) return set_error(H(h), NPCG_EINVAL, "NULL array argument");
+    return pcg_run_ex(H(h), PT(p), A_val, b, x, precond, L_val, rtol, max_iter, opts, stats);
+}
+
 npcg_status npcg_spmv(npcg_handle h, npcg_pattern p, const double* A_val, const double* x, double* y) {
     NPCG_TRY(check_hp(h, p));
     if (!A_val || !x || !y) return set_error(H(h), NPCG_EINVAL, "NULL array argument");
@@ -269,6 +294,17 @@ npcg_status npcg_sptrsv(npcg_handle h, npcg_pattern p, int32_t transpose, const 
     if (!r || !y || r == y) return set_error(H(h), NPCG_EINVAL, "r and y must be distinct non-NULL arrays");
     npcg_status s = sptrsv_run(H(h), PT(p), transpose ? 1 : 0, r, y, nullptr);
     if (s != NPCG_OK) return s;
+    int flags = 0;
+    NPCG_TRY(read_scalar(H(h), PT(p)->ctl.p + 1, &flags));
+    if (flags & kFlagTimeout) return set_error(H(h), NPCG_ETIMEOUT, "triangular solve wait timed out");
+    return NPCG_OK;
+}
+
+npcg_status npcg_sptrsv_unclaimed(npcg_handle h, npcg_pattern p, int32_t transpose, int32_t skip, const double* r,
+                                  double* y) {
+    NPCG_TRY(check_hp(h, p));
+    if (!r || !y || r == y) return set_error(H(h), NPCG_EINVAL, "r and y must be distinct non-NULL arrays");
+    NPCG_TRY(sptrsv_unclaimed_run(H(h), PT(p), transpose ? 1 : 0, skip, r, y));
     int flags = 0;
     NPCG_TRY(read_scalar(H(h), PT(p)->ctl.p + 1, &flags));
     if (flags & kFlagTimeout) return set_error(H(h), NPCG_ETIMEOUT, "triangular solve wait timed out");
@@ -322,7 +358,10 @@ npcg_status npcg_solve_host(npcg_handle h, npcg_pattern p, int32_t method, const
     else if (method == NPCG_METHOD_IC0) NPCG_TRY(ic0_run(hh, P, P->Aval_dev.p, P->Lval_dev.p, nullptr));
     else if (method == NPCG_METHOD_SGS) NPCG_TRY(sgs_run(hh, P, P->Aval_dev.p, P->Lval_dev.p));
     else precond = method == NPCG_METHOD_JACOBI ? NPCG_PREC_JACOBI : NPCG_PREC_NONE;
-    npcg_status s = pcg_run(hh, P, P->Aval_dev.p, P->b.p, P->x.p, precond, P->Lval_dev.p, rtol, max_iter, stats);
+    // the learned factor falls back to IC(0) on breakdown, max_iter or stagnation
+    npcg_solve_opts fb = {200, 1};
+    npcg_status s = pcg_run_ex(hh, P, P->Aval_dev.p, P->b.p, P->x.p, precond, P->Lval_dev.p, rtol, max_iter,
+                               method == NPCG_METHOD_GNN ? &fb : nullptr, stats);
     cudaError_t e = cudaMemcpyAsync(x_host, P->x.p, P->n * sizeof(double), cudaMemcpyDeviceToHost, hh->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(hh->stream);
     if (e != cudaSuccess) return cuda_fail(hh, e, "copy of x to the host");

@@ -48,7 +48,9 @@ __device__ __forceinline__ double softplus_d(double z) { return fmax(z, 0.0) + l
 
 // diag_mode 0: L_ij = sqrt(s) (s_ij + s_ji)/2, L_ii = sqrt(s) softplus(s_ii);
 // diag_mode 1 (App. A.3, P = L' D L'^T, D = diag(A), unit-diagonal L'):
-//   L = L' D^{1/2}: L_ii = sqrt(A_ii), L_ij = sqrt(A_jj) (s_ij + s_ji)/2
+//   L = L' D^{1/2}: L_ii = sqrt(A_ii), L_ij = sqrt(A_jj) (s_ij + s_ji)/2;
+// diag_mode 2 (the same form, rows scaled): L = D^{1/2} L~:
+//   L_ii = sqrt(A_ii), L_ij = sqrt(A_ii) (s_ij + s_ji)/2
 __global__ void k_assemble_L(int64_t nnzL, const int32_t* l2a, const int32_t* erow, const int32_t* ci,
                              const int32_t* mirror, const int32_t* row_sys, const double* sc,
                              const float* S, const double* av, const int32_t* adiag, int diag_mode,
@@ -58,9 +60,9 @@ __global__ void k_assemble_L(int64_t nnzL, const int32_t* l2a, const int32_t* er
         int ka = l2a[q];
         int i = erow[ka], j = ci[ka];
         double v;
-        if (diag_mode == 1) {
-            const double dj = sqrt(av[adiag[j]]);
-            v = i == j ? dj : dj * 0.5 * ((double)S[ka] + (double)S[mirror[ka]]);
+        if (diag_mode == 1 || diag_mode == 2) {
+            const double dc = sqrt(av[adiag[diag_mode == 1 ? j : i]]);
+            v = i == j ? dc : dc * 0.5 * ((double)S[ka] + (double)S[mirror[ka]]);
         } else {
             const double rs = sqrt(sc[2 * row_sys[i]]);
             v = i == j ? rs * softplus_d((double)S[ka]) : rs * 0.5 * ((double)S[ka] + (double)S[mirror[ka]]);
@@ -85,6 +87,7 @@ npcg_status run_forward(Handle* h, Pattern* P, const double* A_val, const double
     a.sc = B.sc;
     a.av = A_val;
     a.b = b;
+    a.adiag_scaled = cfg->diag_mode == NPCG_DIAG_LDLT_ROWS ? P->adiag.p : nullptr;
     // encoders
     a.nrows = n; a.w = w + off.enc_v; a.depth = l; a.out = B.v[0];
     NPCG_TRY(launch_mlp<H>(h, MODE_ENC_NODE, a));
@@ -123,7 +126,8 @@ npcg_status gnn_check_config(Handle* h, const npcg_gnn_config* cfg) {
     if (cfg->n_mp < 0 || cfg->n_mp > 64) return set_error(h, NPCG_EINVAL, "n_mp must be in [0, 64]");
     if (cfg->l < 1 || cfg->l > kMaxDepth || cfg->l_mp < 1 || cfg->l_mp > kMaxDepth)
         return set_error(h, NPCG_EINVAL, "l and l_mp must be in [1, 4]");
-    if (cfg->diag_mode != NPCG_DIAG_SOFTPLUS && cfg->diag_mode != NPCG_DIAG_LDLT_DIAGA)
+    if (cfg->diag_mode != NPCG_DIAG_SOFTPLUS && cfg->diag_mode != NPCG_DIAG_LDLT_DIAGA &&
+        cfg->diag_mode != NPCG_DIAG_LDLT_ROWS)
         return set_error(h, NPCG_EINVAL, "unsupported diag_mode");
     if (cfg->precision != NPCG_FP32 && cfg->precision != NPCG_BF16)
         return set_error(h, NPCG_EINVAL, "precision must be NPCG_FP32 or NPCG_BF16");

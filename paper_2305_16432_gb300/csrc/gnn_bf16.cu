@@ -42,6 +42,7 @@ struct Bf16Args {
     float* out32;             // optional FP32 copy of the output rows (training tape)
     float* agg32;             // optional FP32 aggregation sum_j e_ij (.) v_j (NODE, training tape)
     int* flags;
+    const int32_t* adiag_scaled;  // diag_mode 2: positions of the diagonal (scaled edge input)
 };
 
 // tensor-core layers of each mode: NODE/EDGE all, ENC from layer 1, DEC to depth-1
@@ -210,7 +211,7 @@ __global__ void __launch_bounds__(kThreads) k_mlp_bf16(Bf16Args a) {
             float x = 0.0f;
             if (row < a.nrows) {
                 if (MODE == MODE_ENC_NODE) x = (float)(a.b[row] / a.sc[2 * a.row_sys[row] + 1]);
-                else x = (float)(a.av[row] / a.sc[2 * a.row_sys[a.erow[row]]]);
+                else x = (float)edge_input(a.av, a.sc, a.row_sys, a.erow, a.ci, a.adiag_scaled, row);
             }
             for (int c = 0; c < 8; ++c) {
                 __nv_bfloat16 h8[8];
@@ -417,6 +418,7 @@ npcg_status gnn_bf16_forward_core(Handle* h, Pattern* P, const double* A_val, co
     a.av = A_val;
     a.b = b;
     a.flags = P->ctl.p + 1;
+    a.adiag_scaled = cfg->diag_mode == NPCG_DIAG_LDLT_ROWS ? P->adiag.p : nullptr;
     a.nrows = P->n; a.w = w + off.enc_v; a.depth = cfg->l; a.out = V[0]; a.out32 = tV ? tV[0] : nullptr;
     NPCG_TRY(launch_bf16<MODE_ENC_NODE>(h, a));
     a.nrows = P->nnz; a.w = w + off.enc_e; a.depth = cfg->l; a.out = E[0]; a.out32 = tE ? tE[0] : nullptr;

@@ -65,7 +65,19 @@ struct MlpArgs {
     const float* ein;
     float* out;
     float* agg_out;      // node update: optional copy of sum_j e_ij (.) v_j (training tape)
+    const int32_t* adiag_scaled;  // diag_mode 2: positions of the diagonal (edge input scaled by it)
 };
+
+// Encoder input of edge k = (i, j): A_ij / s with s the system's largest
+// diagonal (diag_mode 0 and 1), or, given the diagonal positions
+// (diag_mode 2), the entry of the Jacobi-scaled matrix A_ij / sqrt(A_ii A_jj).
+__device__ __forceinline__ double edge_input(const double* av, const double* sc, const int32_t* row_sys,
+                                             const int32_t* erow, const int32_t* ci, const int32_t* adiag,
+                                             int64_t k) {
+    const int i = erow[k];
+    if (adiag) return av[k] / sqrt(av[adiag[i]] * av[adiag[ci[k]]]);
+    return av[k] / sc[2 * row_sys[i]];
+}
 
 npcg_status gnn_check_config(Handle* h, const npcg_gnn_config* cfg);
 npcg_status gnn_buffers(Handle* h, Pattern* P, int H, int nsets, GnnStore& S);
@@ -172,7 +184,8 @@ __device__ __forceinline__ void gather_tile(const MlpArgs& a, int64_t row0, floa
     } else if (MODE == MODE_ENC_EDGE) {
         for (int r = threadIdx.x; r < R; r += blockDim.x) {
             int64_t k = row0 + r;
-            X[r * LD] = k < a.nrows ? (float)(a.av[k] / a.sc[2 * a.row_sys[a.erow[k]]]) : 0.0f;
+            X[r * LD] = k < a.nrows ? (float)edge_input(a.av, a.sc, a.row_sys, a.erow, a.ci, a.adiag_scaled, k)
+                                    : 0.0f;
         }
     } else if (MODE == MODE_NODE) {
         for (int idx = threadIdx.x; idx < R * H; idx += blockDim.x) {

@@ -27,7 +27,7 @@ __global__ void __launch_bounds__(256) k_ic0(int64_t n, int nslices, const int32
                                              const int32_t* l2a, const double* Av,
                                              const int32_t* row_sys, const int* todo,
                                              const double* alpha, double* Lv, int* ticket,
-                                             int* flags, int* fail) {
+                                             int* flags, int* fail, long long spin_limit) {
     const int lane = threadIdx.x & 31;
     const unsigned long long kS = kSentinelBits;
     for (;;) {
@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(256) k_ic0(int64_t n, int nslices, const int32
                     done = true;
                 }
             }
-            if (++spins > kSpinLimit) {
+            if (++spins > spin_limit) {
                 if (!done) atomicOr(flags, kFlagTimeout | kFlagAbort);
                 return;
             }
@@ -110,7 +110,7 @@ npcg_status ic0_run(Handle* h, Pattern* P, const double* A_val, double* L_val, d
         k_ic0_reset<<<h->num_sms * 4, 256, 0, h->stream>>>(P->n, P->Lrp.p, P->row_sys.p, todo.p, L_val);
         k_ic0<<<blocks, 256, 0, h->stream>>>(P->n, P->fwd.nslices, P->fwd.perm.p, P->Lrp.p, P->Lci.p,
                                             P->l2a.p, A_val, P->row_sys.p, todo.p, alpha.p, L_val,
-                                            P->ctl.p + 2, P->ctl.p + 1, fail.p);
+                                            P->ctl.p + 2, P->ctl.p + 1, fail.p, h->spin_limit);
         NPCG_CUDA(h, cudaGetLastError());
         int flags = 0;
         NPCG_TRY(read_scalar(h, P->ctl.p + 1, &flags));

@@ -16,14 +16,14 @@ namespace {
 
 constexpr int64_t kNaMaxN = NPCG_NOALLOC_MAX_N;
 constexpr int kNaThreads = 256;
-constexpr int kNaRows = 2048;                                  // rows per block
+constexpr int kNaRows = 512;                                   // rows per block (512 blocks at the largest n)
 constexpr int kNaMaxBlocks = (int)((kNaMaxN + kNaRows - 1) / kNaRows);
 constexpr int kMaxDevices = 64;
 
-// Layout (doubles): r | z | p | w (kNaMaxN each) | partials (4 per block) |
-// control block (solver state and counters).
-constexpr int64_t kOffR = 0, kOffZ = kNaMaxN, kOffP = 2 * kNaMaxN, kOffW = 3 * kNaMaxN;
-constexpr int64_t kOffPart = 4 * kNaMaxN;
+// Layout (doubles): r | z | p | w | 1 / diag(A) (kNaMaxN each) | partials
+// (4 per block) | control block (solver state and counters).
+constexpr int64_t kOffR = 0, kOffZ = kNaMaxN, kOffP = 2 * kNaMaxN, kOffW = 3 * kNaMaxN, kOffD = 4 * kNaMaxN;
+constexpr int64_t kOffPart = 5 * kNaMaxN;
 constexpr int64_t kOffCtl = kOffPart + 4 * (int64_t)kNaMaxBlocks;
 constexpr int64_t kCtlDoubles = 16;
 
@@ -33,6 +33,7 @@ struct NaState {          // inside the control block
     double tol2, rr, rz, pw, alpha, beta, bnorm2;
     int iters, status, active, max_iter;
     unsigned arrive;
+    int bad_diag;         // Jacobi: a row without a nonzero finite diagonal
 };
 static_assert(sizeof(NaState) <= kCtlDoubles * sizeof(double), "control block too small");
 
@@ -43,7 +44,7 @@ struct NaArgs {
     const double* av;
     const double* b;
     double* x;
-    double *r, *z, *p, *w, *part;
+    double *r, *z, *p, *w, *dinv, *part;
     NaState* st;
     int jacobi;
     int nblocks;
@@ -102,7 +103,13 @@ __global__ void k_na_init(NaArgs a, double rtol, int max_iter) {
         double s = 0.0;
         for (int k = a.rp[i]; k < a.rp[i + 1]; ++k) s = fma(a.av[k], a.x[a.ci[k]], s);
         const double bi = a.b[i], ri = bi - s;
-        const double zi = a.jacobi ? ri / na_diag(a, i) : ri;
+        double zi = ri;
+        if (a.jacobi) {
+            const double d = na_diag(a, i);
+            if (!(d != 0.0) || !isfinite(d)) atomicOr(&a.st->bad_diag, 1);
+            a.dinv[i] = 1.0 / d;
+            zi = ri * a.dinv[i];
+        }
         a.r[i] = ri;
         a.z[i] = zi;
         a.p[i] = zi;
@@ -121,7 +128,9 @@ __global__ void k_na_init(NaArgs a, double rtol, int max_iter) {
         s.max_iter = max_iter;
         s.status = NPCG_OK;
         s.active = 0;
-        if (!(acc[1] <= s.tol2)) {
+        if (s.bad_diag) {
+            s.status = NPCG_EINVAL;          // Jacobi needs every diagonal entry
+        } else if (!(acc[1] <= s.tol2)) {
             if (max_iter <= 0) s.status = NPCG_EMAXITER;
             else if (!(acc[2] > 0.0) || !isfinite(acc[2])) s.status = NPCG_EBREAKDOWN;
             else s.active = 1;
@@ -158,7 +167,7 @@ __global__ void k_na_update(NaArgs a) {
     for (int i = r0 + threadIdx.x; i < r1; i += kNaThreads) {
         a.x[i] = fma(alpha, a.p[i], a.x[i]);
         const double ri = fma(-alpha, a.w[i], a.r[i]);
-        const double zi = a.jacobi ? ri / na_diag(a, i) : ri;
+        const double zi = a.jacobi ? ri * a.dinv[i] : ri;
         a.r[i] = ri;
         a.z[i] = zi;
         acc[0] = fma(ri, ri, acc[0]);
@@ -217,6 +226,9 @@ extern "C" npcg_status npcg_pcg_solve_noalloc(void* stream, int64_t n, int64_t n
     if (precond != NPCG_PREC_NONE && precond != NPCG_PREC_JACOBI) return NPCG_EINVAL;
     if (!row_ptr || !col_idx || !A_val || !b || !x || !stats || !(rtol >= 0.0) || max_iter < 0)
         return NPCG_EINVAL;
+    // an error left by earlier work on this thread is not this call's: report
+    // it before launching anything rather than take it for our own later
+    if (cudaPeekAtLastError() != cudaSuccess) return NPCG_ECUDA;
     double* base = nullptr;
     npcg_status st = scratch_on_current_device(&base);
     if (st != NPCG_OK) return st;
@@ -232,6 +244,7 @@ extern "C" npcg_status npcg_pcg_solve_noalloc(void* stream, int64_t n, int64_t n
     a.z = base + kOffZ;
     a.p = base + kOffP;
     a.w = base + kOffW;
+    a.dinv = base + kOffD;
     a.part = base + kOffPart;
     a.st = reinterpret_cast<NaState*>(base + kOffCtl);
     a.jacobi = precond == NPCG_PREC_JACOBI;
@@ -240,6 +253,7 @@ extern "C" npcg_status npcg_pcg_solve_noalloc(void* stream, int64_t n, int64_t n
     // with it the arrival counter) must start at zero
     if (cudaMemsetAsync(a.st, 0, kCtlDoubles * sizeof(double), s) != cudaSuccess) return NPCG_ECUDA;
     k_na_init<<<a.nblocks, kNaThreads, 0, s>>>(a, rtol, max_iter);
+    if (cudaGetLastError() != cudaSuccess) return NPCG_ECUDA;
     NaState hs;
     const int kCheck = 16;           // iterations between host checks
     for (int it = 0; it < max_iter; it += kCheck) {
@@ -248,6 +262,7 @@ extern "C" npcg_status npcg_pcg_solve_noalloc(void* stream, int64_t n, int64_t n
             k_na_update<<<a.nblocks, kNaThreads, 0, s>>>(a);
             k_na_pupdate<<<a.nblocks, kNaThreads, 0, s>>>(a);
         }
+        if (cudaGetLastError() != cudaSuccess) return NPCG_ECUDA;
         if (cudaMemcpyAsync(&hs, a.st, sizeof(NaState), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess)
             return NPCG_ECUDA;
@@ -260,5 +275,7 @@ extern "C" npcg_status npcg_pcg_solve_noalloc(void* stream, int64_t n, int64_t n
     stats->iters = hs.iters;
     stats->status = hs.status;
     stats->relres = hs.bnorm2 > 0.0 ? sqrt(hs.rr / hs.bnorm2) : sqrt(hs.rr);
+    stats->fallback = 0;
+    stats->fallback_iters = 0;
     return (npcg_status)hs.status;
 }

@@ -68,6 +68,9 @@ struct SysState {
     int status;       // npcg_status
     int active;       // 1 while iterating
     int max_iter;
+    double best_rr;   // smallest ||r||^2 so far (stagnation test)
+    int since_best;   // updates since best_rr last fell
+    int stall_k;      // stagnation window (0: off)
 };
 
 // Chunk of rows of one system (reductions and vector kernels).
@@ -214,6 +217,7 @@ struct Pattern {
     DevBuf<int> ctl;               // [0] n_active, [1] flags, [2] fwd ticket, [3] bwd ticket
     DevBuf<double> Aval_dev;       // host-path copy of A values
     DevBuf<double> Lval_dev;       // host-path factor
+    DevBuf<double> Lval_fb, x0_fb; // IC(0) fallback: its factor and the first attempt's x_0
     // cached iteration graphs (keyed by precond)
     cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};
     int graph_mode[4] = {0, 0, 0, 0};
@@ -235,6 +239,7 @@ struct Handle {
     DevBuf<int> scratch_i;      // small device scratch
     void* host_pinned = nullptr; // small pinned host scratch
     size_t host_pinned_bytes = 0;
+    std::vector<Pattern*> patterns;   // live patterns analysed with this handle
 };
 
 // ---------------------------------------------------------------------------
@@ -325,7 +330,12 @@ npcg_status sptrsv_timed_run(Handle* h, Pattern* P, int transpose, const double*
                              double* ms_per_launch, bool f32);
 npcg_status pcg_run(Handle* h, Pattern* P, const double* A_val, const double* b, double* x,
                     int precond, const double* L_val, double rtol, int max_iter,
-                    npcg_solve_stats* stats);
+                    npcg_solve_stats* stats, int stall_k = 0);
+// PCG with the options of npcg_pcg_solve_ex: stagnation window and the
+// IC(0) fallback for a failed factored solve
+npcg_status pcg_run_ex(Handle* h, Pattern* P, const double* A_val, const double* b, double* x, int precond,
+                       const double* L_val, double rtol, int max_iter, const npcg_solve_opts* opts,
+                       npcg_solve_stats* stats);
 npcg_status ic0_run(Handle* h, Pattern* P, const double* A_val, double* L_val, double* alpha_out);
 npcg_status sgs_run(Handle* h, Pattern* P, const double* A_val, double* L_val);
 // merged-level solves (G levels per step): offered to the autotuner and to

@@ -98,7 +98,7 @@ __global__ void k_fill_tril(int64_t n, const int32_t* rp, const int32_t* ci, con
 // round; no lane blocks another lane of its warp.
 template <bool kUpper>
 __global__ void k_levels(int64_t n, const int32_t* rp, const int32_t* ci, int* lev, int* ticket,
-                         int* flags) {
+                         int* flags, long long spin_limit) {
     const int lane = threadIdx.x & 31;
     for (;;) {
         int base = 0;
@@ -130,7 +130,7 @@ __global__ void k_levels(int64_t n, const int32_t* rp, const int32_t* ci, int* l
                     done = true;
                 }
             }
-            if (++spins > kSpinLimit) {
+            if (++spins > spin_limit) {
                 if (!done) atomicOr(flags, kFlagTimeout);
                 return;
             }
@@ -224,9 +224,11 @@ npcg_status build_tri(Handle* h, Pattern* P, bool upper, TriLayout* T) {
     // ctl[2] ticket, ctl[1] flags
     int blocks = h->num_sms * 8;
     if (upper)
-        k_levels<true><<<blocks, 256, 0, h->stream>>>(n, P->rp.p, P->ci.p, T->level.p, P->ctl.p + 2, P->ctl.p + 1);
+        k_levels<true><<<blocks, 256, 0, h->stream>>>(n, P->rp.p, P->ci.p, T->level.p, P->ctl.p + 2, P->ctl.p + 1,
+                                                      h->spin_limit);
     else
-        k_levels<false><<<blocks, 256, 0, h->stream>>>(n, P->rp.p, P->ci.p, T->level.p, P->ctl.p + 2, P->ctl.p + 1);
+        k_levels<false><<<blocks, 256, 0, h->stream>>>(n, P->rp.p, P->ci.p, T->level.p, P->ctl.p + 2, P->ctl.p + 1,
+                                                      h->spin_limit);
     NPCG_CUDA(h, cudaGetLastError());
     int flags = 0;
     NPCG_TRY(read_scalar(h, P->ctl.p + 1, &flags));

@@ -4,6 +4,7 @@
 // CUDA graph whose while-loop runs on the device until every system of the
 // pattern has converged, failed, or reached max_iter.
 #include <algorithm>
+#include <vector>
 
 #include "npcg_internal.cuh"
 
@@ -118,7 +119,7 @@ __device__ __forceinline__ double row_dot(const int32_t* rp, const int32_t* ci, 
 
 // r = b - A x; partials ||b||^2, ||r||^2; finaliser sets tolerances and the
 // active mask; sentinels and p buffers are reset for the first iteration.
-__global__ void k_init(PcgArgs a, double rtol, int max_iter, double* p0, double* p1) {
+__global__ void k_init(PcgArgs a, double rtol, int max_iter, double* p0, double* p1, int stall_k) {
     __shared__ double sh[2][kChunkThreads / 32];
     const Chunk c = a.chunks[blockIdx.x];
     const int g = threadIdx.x & 7, sub = (threadIdx.x >> 3) & 3, warp = threadIdx.x >> 5;
@@ -156,6 +157,9 @@ __global__ void k_init(PcgArgs a, double rtol, int max_iter, double* p0, double*
         s.alpha = 0.0;
         s.rz = 0.0;
         s.pw = 0.0;
+        s.best_rr = tot[1];
+        s.since_best = 0;
+        s.stall_k = stall_k;
         if (!(tot[1] <= s.tol2)) {
             if (max_iter <= 0) {
                 s.status = NPCG_EMAXITER;
@@ -305,12 +309,21 @@ __global__ void k_update(PcgArgs a, const double* __restrict__ p) {
         SysState& s = a.st[c.sys];
         s.rr = tot[0];
         s.iters += 1;
+        if (tot[0] < s.best_rr) {
+            s.best_rr = tot[0];
+            s.since_best = 0;
+        } else {
+            s.since_best += 1;
+        }
         if (tot[0] <= s.tol2) {
             deactivate(s, NPCG_OK, &a.ctl[0]);
         } else if (!isfinite(tot[0])) {
             deactivate(s, NPCG_EBREAKDOWN, &a.ctl[0]);
         } else if (s.iters >= s.max_iter) {
             deactivate(s, NPCG_EMAXITER, &a.ctl[0]);
+        } else if (s.stall_k > 0 && s.since_best > 0 && s.since_best >= s.stall_k) {
+            // ||r|| has not fallen below its best for stall_k updates
+            deactivate(s, NPCG_ESTALL, &a.ctl[0]);
         } else if (!llt) {
             double rz = tot[1];
             if (!(rz > 0.0) || !isfinite(rz)) deactivate(s, NPCG_EBREAKDOWN, &a.ctl[0]);
@@ -343,7 +356,8 @@ struct TriDev {
 template <bool kBatched, class V>
 __global__ void __launch_bounds__(kTrsvThreads) k_trsv(TriDev T, const double* __restrict__ rhs,
                                                        double* out, int* ticket, int* flags,
-                                                       const int32_t* row_sys, const SysState* st) {
+                                                       const int32_t* row_sys, const SysState* st,
+                                                       long long spin_limit) {
     const V* tval = static_cast<const V*>(T.val);
     const V* tdinv = static_cast<const V*>(T.dinv);
     const int lane = threadIdx.x & 31;
@@ -415,7 +429,7 @@ __global__ void __launch_bounds__(kTrsvThreads) k_trsv(TriDev T, const double* _
                     }
                 }
             }
-            if (++spins > kSpinLimit) {
+            if (++spins > spin_limit) {
                 if (!done) atomicOr(flags, kFlagTimeout | kFlagAbort);
                 return;
             }
@@ -499,6 +513,8 @@ __global__ void k_stats(int nsys, const SysState* st, npcg_solve_stats* out) {
         out[s].status = st[s].status;
         double b2 = st[s].bnorm2;
         out[s].relres = b2 > 0.0 ? sqrt(st[s].rr / b2) : sqrt(st[s].rr);
+        out[s].fallback = 0;
+        out[s].fallback_iters = 0;
     }
 }
 
@@ -527,12 +543,13 @@ void launch_trsv(Handle* h, cudaStream_t s, Pattern* P, int transpose, const dou
     TriDev d = tri_dev(P, T, f32);
     const int g = trsv_grid(h, T);
     int* fl = P->ctl.p + 1;
+    const long long lim = h->spin_limit;
     if (f32) {
-        if (batched) k_trsv<true, float><<<g, kTrsvThreads, 0, s>>>(d, rhs, out, ticket, fl, P->row_sys.p, st);
-        else k_trsv<false, float><<<g, kTrsvThreads, 0, s>>>(d, rhs, out, ticket, fl, P->row_sys.p, st);
+        if (batched) k_trsv<true, float><<<g, kTrsvThreads, 0, s>>>(d, rhs, out, ticket, fl, P->row_sys.p, st, lim);
+        else k_trsv<false, float><<<g, kTrsvThreads, 0, s>>>(d, rhs, out, ticket, fl, P->row_sys.p, st, lim);
     } else {
-        if (batched) k_trsv<true, double><<<g, kTrsvThreads, 0, s>>>(d, rhs, out, ticket, fl, P->row_sys.p, st);
-        else k_trsv<false, double><<<g, kTrsvThreads, 0, s>>>(d, rhs, out, ticket, fl, P->row_sys.p, st);
+        if (batched) k_trsv<true, double><<<g, kTrsvThreads, 0, s>>>(d, rhs, out, ticket, fl, P->row_sys.p, st, lim);
+        else k_trsv<false, double><<<g, kTrsvThreads, 0, s>>>(d, rhs, out, ticket, fl, P->row_sys.p, st, lim);
     }
 }
 
@@ -632,7 +649,8 @@ void enqueue_iteration(Handle* h, cudaStream_t s, Pattern* P, const PcgArgs& a, 
 npcg_status build_graph(Handle* h, Pattern* P, int precond) {
     // the graph is specific to the triangular-solve design
     const int mode_key = P->trsv_mode | (P->cta_flag ? 16 : 0) | (P->cta_split ? 32 : 0) | (P->cta_merge ? 64 : 0);
-    if (P->graph[precond] && P->graph_mode[precond] == mode_key) return NPCG_OK;
+    if (P->graph[precond] && P->graph_mode[precond] == mode_key && P->graph_spin[precond] == h->spin_limit)
+        return NPCG_OK;
     if (P->graph[precond]) { cudaGraphExecDestroy(P->graph[precond]); P->graph[precond] = nullptr; }
     PcgArgs a = pcg_args(P, precond);
     cudaGraph_t g = nullptr;
@@ -667,6 +685,7 @@ npcg_status build_graph(Handle* h, Pattern* P, int precond) {
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
     P->graph[precond] = ex;
     P->graph_mode[precond] = mode_key;
+    P->graph_spin[precond] = h->spin_limit;
     return NPCG_OK;
 }
 
@@ -705,6 +724,22 @@ npcg_status sptrsv_run(Handle* h, Pattern* P, int transpose, const double* r, do
     k_fill_sentinel<<<h->num_sms * 4, 256, 0, h->stream>>>(P->n, y);
     launch_trsv(h, h->stream, P, transpose, r, y, P->ctl.p + 2 + (transpose ? 1 : 0), false, nullptr, false);
     NPCG_CUDA(h, cudaGetLastError());
+    return NPCG_OK;
+}
+
+npcg_status sptrsv_unclaimed_run(Handle* h, Pattern* P, int transpose, int skip, const double* r, double* y) {
+    const TriLayout& T = transpose ? P->bwd : P->fwd;
+    if (skip < 0 || skip > T.nslices) return set_error(h, NPCG_EINVAL, "skip must be in [0, number of slices]");
+    // flags and both tickets cleared, then this direction's ticket set past
+    // the skipped slices: no warp ever claims them, so their rows stay at
+    // the sentinel and their dependants wait until the wait limit
+    NPCG_CUDA(h, cudaMemsetAsync(P->ctl.p + 1, 0, 3 * sizeof(int), h->stream));
+    NPCG_CUDA(h, cudaMemcpyAsync(P->ctl.p + 2 + (transpose ? 1 : 0), &skip, sizeof(int), cudaMemcpyHostToDevice,
+                                 h->stream));
+    k_fill_sentinel<<<h->num_sms * 4, 256, 0, h->stream>>>(P->n, y);
+    launch_trsv(h, h->stream, P, transpose, r, y, P->ctl.p + 2 + (transpose ? 1 : 0), false, nullptr, false);
+    NPCG_CUDA(h, cudaGetLastError());
+    NPCG_CUDA(h, cudaStreamSynchronize(h->stream));
     return NPCG_OK;
 }
 
@@ -779,18 +814,16 @@ npcg_status trsv_autotune(Handle* h, Pattern* P) {
     // all entries 1: a well-defined solve of the same structure (values do not
     // change the timing)
     NPCG_TRY(factor_load(h, P, L.p));
-    // sync-free, level order with a barrier per step, level order with
-    // per-slot flags (FP32 solves; when the window covers its drift)
-    const int modes[4] = {kTrsvSyncFree, kTrsvCta, kTrsvCta, kTrsvCta};
-    const bool flag_ok = P->cfwd.flag_ok && P->cbwd.flag_ok;
-    const bool split_ok = P->cfwd.split_stages[1] >= 2 && P->cbwd.split_stages[1] >= 2;
+    // sync-free and level order with a barrier per step; the flag-synchronised
+    // and split-role variants measured slower on every workload and are not
+    // timed (npcg_pattern_set_trsv still selects them)
+    const int modes[2] = {kTrsvSyncFree, kTrsvCta};
     P->tune_ms[2] = 0.f;
     P->tune_ms[3] = 0.f;
-    for (int m = 0; m < 4; ++m) {
-        if ((m == 2 && !flag_ok) || (m == 3 && !split_ok)) continue;
+    for (int m = 0; m < 2; ++m) {
         P->trsv_mode = modes[m];
-        P->cta_flag = m == 2;
-        P->cta_split = m == 3;
+        P->cta_flag = false;
+        P->cta_split = false;
         double best = 1e30;
         for (int rep = 0; rep < 3; ++rep) {
             double f = 0.0, b = 0.0;
@@ -862,7 +895,7 @@ npcg_status spmv_run(Handle* h, Pattern* P, const double* A_val, const double* x
 
 npcg_status pcg_run(Handle* h, Pattern* P, const double* A_val, const double* b, double* x,
                     int precond, const double* L_val, double rtol, int max_iter,
-                    npcg_solve_stats* stats) {
+                    npcg_solve_stats* stats, int stall_k) {
     if (precond < 0 || precond > NPCG_PREC_LLT32) return set_error(h, NPCG_EINVAL, "unknown preconditioner");
     if (precond >= NPCG_PREC_LLT && !L_val) return set_error(h, NPCG_EINVAL, "L_val required for PREC_LLT");
     if (!(rtol >= 0.0)) return set_error(h, NPCG_EINVAL, "rtol must be >= 0");
@@ -882,7 +915,7 @@ npcg_status pcg_run(Handle* h, Pattern* P, const double* A_val, const double* b,
         NPCG_CUDA(h, cudaMemcpyAsync(P->ctl.p, init, sizeof(init), cudaMemcpyHostToDevice, h->stream));
     }
     PcgArgs a = pcg_args(P, precond);
-    k_init<<<P->nchunks, kChunkThreads, 0, h->stream>>>(a, rtol, max_iter, P->p0.p, P->p1.p);
+    k_init<<<P->nchunks, kChunkThreads, 0, h->stream>>>(a, rtol, max_iter, P->p0.p, P->p1.p, stall_k);
     if (precond >= NPCG_PREC_LLT) {
         apply_llt(h, h->stream, P, P->nsys > 1, precond == NPCG_PREC_LLT32);
     }
@@ -913,6 +946,61 @@ npcg_status pcg_run(Handle* h, Pattern* P, const double* A_val, const double* b,
                              "system " + std::to_string(s) + " did not converge: " +
                                  npcg_status_string((npcg_status)stats[s].status));
     return NPCG_OK;
+}
+
+// A factored solve that breaks down, reaches max_iter or stagnates is
+// handed to IC(0) (Sec. 5.1's baseline): the factor is recomputed with
+// npcg_ic0_factor's kernel and PCG restarts, from the last iterate after
+// max_iter or stagnation and from x_0 after a breakdown, with a fresh
+// max_iter.  Systems that had converged take no update in the second run.
+npcg_status pcg_run_ex(Handle* h, Pattern* P, const double* A_val, const double* b, double* x, int precond,
+                       const double* L_val, double rtol, int max_iter, const npcg_solve_opts* opts,
+                       npcg_solve_stats* stats) {
+    const int stall_k = opts ? std::max(0, (int)opts->stall_iters) : 0;
+    const bool fb = opts && opts->fallback_ic0 && precond >= NPCG_PREC_LLT;
+    if (fb) {
+        NPCG_CUDA(h, P->x0_fb.ensure(P->n));
+        NPCG_CUDA(h, cudaMemcpyAsync(P->x0_fb.p, x, P->n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    }
+    npcg_status st = pcg_run(h, P, A_val, b, x, precond, L_val, rtol, max_iter, stats, stall_k);
+    for (int s = 0; s < P->nsys; ++s) {
+        stats[s].fallback = 0;
+        stats[s].fallback_iters = 0;
+    }
+    if (!fb || st == NPCG_OK || st == NPCG_ETIMEOUT || st == NPCG_ECUDA || st == NPCG_EINVAL ||
+        st == NPCG_ENOMEM)
+        return st;
+    std::vector<npcg_solve_stats> first(stats, stats + P->nsys);
+    bool restart_x0 = false;
+    for (int s = 0; s < P->nsys; ++s) restart_x0 |= first[s].status == NPCG_EBREAKDOWN;
+    if (restart_x0) {
+        // a broken-down system restarts from x_0; the others keep their iterate
+        std::vector<double> keep(P->n);
+        std::vector<double> x0(P->n);
+        NPCG_CUDA(h, cudaMemcpyAsync(keep.data(), x, P->n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        NPCG_CUDA(h, cudaMemcpyAsync(x0.data(), P->x0_fb.p, P->n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        NPCG_CUDA(h, cudaStreamSynchronize(h->stream));
+        for (int s = 0; s < P->nsys; ++s)
+            if (first[s].status == NPCG_EBREAKDOWN)
+                for (int64_t i = P->sys_ptr_h[s]; i < P->sys_ptr_h[s + 1]; ++i) keep[i] = x0[i];
+        NPCG_CUDA(h, cudaMemcpyAsync(x, keep.data(), P->n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        NPCG_CUDA(h, cudaStreamSynchronize(h->stream));
+    }
+    NPCG_CUDA(h, P->Lval_fb.ensure(P->nnzL));
+    NPCG_TRY(ic0_run(h, P, A_val, P->Lval_fb.p, nullptr));
+    st = pcg_run(h, P, A_val, b, x, precond, P->Lval_fb.p, rtol, max_iter, stats, stall_k);
+    for (int s = 0; s < P->nsys; ++s) {
+        if (first[s].status == NPCG_OK) {
+            stats[s] = first[s];
+            stats[s].fallback = 0;
+            stats[s].fallback_iters = 0;
+        } else {
+            stats[s].fallback = 1;
+            stats[s].fallback_iters = stats[s].iters;
+            stats[s].iters += first[s].iters;
+        }
+    }
+    return st;
 }
 
 }  // namespace npcg

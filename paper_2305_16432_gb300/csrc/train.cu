@@ -83,7 +83,8 @@ __global__ void k_dL(int64_t nnzL, const int32_t* l2a, const int32_t* erow, cons
 }
 
 // d loss / d s_k for every A entry k = (i, j): one L entry feeds each.
-// diag_mode 1: L_ii = sqrt(A_ii) is fixed, L_ij = sqrt(A_jj) (s_ij + s_ji)/2.
+// diag_mode 1: L_ii = sqrt(A_ii) is fixed, L_ij = sqrt(A_jj) (s_ij + s_ji)/2;
+// diag_mode 2: L_ii = sqrt(A_ii) is fixed, L_ij = sqrt(A_ii) (s_ij + s_ji)/2.
 __global__ void k_dS(int64_t nnz, const int32_t* erow, const int32_t* ci, const int32_t* mirror,
                      const int32_t* a2l, const int32_t* row_sys, const double* sc, const float* S,
                      const double* dL, const double* av, const int32_t* adiag, int diag_mode, float* dS) {
@@ -91,11 +92,13 @@ __global__ void k_dS(int64_t nnz, const int32_t* erow, const int32_t* ci, const 
          k += (int64_t)gridDim.x * blockDim.x) {
         const int i = erow[k], j = ci[k];
         double g;
-        if (diag_mode == 1) {
-            // the L entry holding s_k is (max(i,j), min(i,j)); its column scale is sqrt(A_cc)
+        if (diag_mode == 1 || diag_mode == 2) {
+            // the L entry holding s_k is (max(i,j), min(i,j)); its scale is
+            // sqrt(A_cc) with c the column min(i,j) (mode 1) or the row max(i,j) (mode 2)
+            const int cc = diag_mode == 1 ? min(i, j) : max(i, j);
             if (i == j) g = 0.0;
-            else if (i > j) g = sqrt(av[adiag[j]]) * 0.5 * dL[a2l[k]];
-            else g = sqrt(av[adiag[i]]) * 0.5 * dL[a2l[mirror[k]]];
+            else if (i > j) g = sqrt(av[adiag[cc]]) * 0.5 * dL[a2l[k]];
+            else g = sqrt(av[adiag[cc]]) * 0.5 * dL[a2l[mirror[k]]];
         } else {
             const double rs = sqrt(sc[2 * row_sys[i]]);
             if (i == j) g = rs * (1.0 / (1.0 + exp(-(double)S[k]))) * dL[a2l[k]];
@@ -896,11 +899,12 @@ __global__ void k_x0_loss(int64_t n, const int32_t* row_sys, const double* sc, c
 }
 
 __global__ void k_enc_inputs(int64_t n, int64_t nnz, const double* b, const double* av, const int32_t* erow,
-                             const int32_t* row_sys, const double* sc, float* xv, float* xe) {
+                             const int32_t* ci, const int32_t* adiag_scaled, const int32_t* row_sys,
+                             const double* sc, float* xv, float* xe) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nnz;
          i += (int64_t)gridDim.x * blockDim.x) {
         if (i < n) xv[i] = (float)(b[i] / sc[2 * row_sys[i] + 1]);
-        xe[i] = (float)(av[i] / sc[2 * row_sys[erow[i]]]);
+        xe[i] = (float)edge_input(av, sc, row_sys, erow, ci, adiag_scaled, i);
     }
 }
 
@@ -1031,6 +1035,7 @@ npcg_status train_pair(Handle* h, Pattern* P, const double* A_val, const double*
     a.sc = sc;
     a.av = A_val;
     a.b = b;
+    a.adiag_scaled = cfg->diag_mode == NPCG_DIAG_LDLT_ROWS ? P->adiag.p : nullptr;
     if (cfg->precision == NPCG_BF16) {
         // tensor-core forward; the tape holds its node / edge states in FP32
         NPCG_TRY(gnn_bf16_forward_core(h, P, A_val, b, cfg, w, sc, T.S, T.V.data(), T.E.data(), T.AGG.data()));
@@ -1116,7 +1121,9 @@ npcg_status train_pair(Handle* h, Pattern* P, const double* A_val, const double*
         std::swap(T.dVc, T.dVp);
     }
     // encoders: weight gradients only
-    k_enc_inputs<<<grid1(h, nnz), 256, 0, h->stream>>>(n, nnz, b, A_val, P->edge_row.p, P->row_sys.p, sc, T.xv, T.xe);
+    k_enc_inputs<<<grid1(h, nnz), 256, 0, h->stream>>>(n, nnz, b, A_val, P->edge_row.p, P->ci.p,
+                                                       cfg->diag_mode == NPCG_DIAG_LDLT_ROWS ? P->adiag.p : nullptr,
+                                                       P->row_sys.p, sc, T.xv, T.xe);
     bw.f = a;
     bw.f.nrows = n; bw.f.w = w + off.enc_v; bw.f.depth = l;
     bw.gout = T.dVc;

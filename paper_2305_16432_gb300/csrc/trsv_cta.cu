@@ -31,7 +31,6 @@ constexpr int kCtaThreads = kCtaRows + 32;   // + one producer warp
 constexpr int kWinMax = 8192;            // largest shared window (positions), power of two
 constexpr int kWinMin = 1024;            // smallest window
 constexpr int kMaxStages = 8;
-constexpr long long kMbarSpin = 1LL << 22;
 constexpr int kHdrInts = 4;              // {q0, nrows, width, pad} heads every structure block
 constexpr int kRec = 4;                  // dependencies held in a row's packed record
 constexpr int kWinPad = 32;              // window slots past the window; the first stays zero
@@ -66,8 +65,8 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-    for (long long s = 0; s < kMbarSpin; ++s)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limit) {
+    for (long long s = 0; s < limit; ++s)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
@@ -80,6 +79,7 @@ struct CtaDev {
     int stages;
     int stage_cap;              // bytes per stage (multiple of 128)
     int win;                    // window slots (power of two)
+    long long spin;             // polls before a wait gives up (the handle's wait limit)
 };
 
 __host__ __device__ __forceinline__ int pad4(int x) { return (x + 3) & ~3; }
@@ -153,13 +153,13 @@ __device__ __forceinline__ bool consumers_agree(bool ok) {
 
 // value of a dependency on a row of an earlier unit (blocked layouts): the
 // unit that owns it publishes it to pub (FP64, sentinel until written)
-__device__ __forceinline__ double remote_dep(const double* pub, int row, int* flags) {
+__device__ __forceinline__ double remote_dep(const double* pub, int row, int* flags, long long limit) {
     long long spins = 0;
     unsigned long long bits;
     while ((bits = ld_relaxed_u64(pub + row)) == kSentinelBits) {
         // a solve that already gave up does not wait again
         if ((++spins & 255) == 0 && (ld_relaxed_s32(flags) & kFlagAbort)) return 0.0;
-        if (spins > kSpinLimit) {
+        if (spins > limit) {
             atomicOr(flags, kFlagTimeout | kFlagAbort);
             return 0.0;
         }
@@ -192,7 +192,7 @@ __device__ __forceinline__ void ring_producer(const CtaDev& D, const T* rhs, uns
             const int j = j0 + u, k = j - c0, s = k % S;
             if (lane == 0) {
                 if (k >= S) {
-                    ok = mbar_wait_bounded(&empty[s], (uint32_t)((k / S - 1) & 1));
+                    ok = mbar_wait_bounded(&empty[s], (uint32_t)((k / S - 1) & 1), D.spin);
                     if (ok) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 }
                 if (ok) {
@@ -215,7 +215,7 @@ __device__ __forceinline__ void ring_producer(const CtaDev& D, const T* rhs, uns
     if (!ok) atomicOr(flags, kFlagTimeout | kFlagAbort);
     for (int j = max(c0, c0 + issued - S); j < c0 + issued; ++j) {
         const int k = j - c0;
-        mbar_wait_bounded(&full[k % S], (uint32_t)((k / S) & 1));
+        mbar_wait_bounded(&full[k % S], (uint32_t)((k / S) & 1), D.spin);
     }
 }
 
@@ -281,7 +281,7 @@ __global__ void __launch_bounds__(kCtaThreads, 1) k_trsv_cta(CtaDev D, const T* 
     const T* rh;
     int q0e;
     {
-        const bool ok = mbar_wait_bounded(&full[0], 0u);
+        const bool ok = mbar_wait_bounded(&full[0], 0u, D.spin);
         if (!consumers_agree(ok)) {
             if (threadIdx.x == 0) atomicOr(flags, kFlagTimeout | kFlagAbort);
             return;
@@ -325,7 +325,7 @@ __global__ void __launch_bounds__(kCtaThreads, 1) k_trsv_cta(CtaDev D, const T* 
             ns = (nc - c0) % S;
             nu = 0;
             waited = true;
-            ok = mbar_wait_bounded(&full[ns], (uint32_t)(((nc - c0) / S) & 1));
+            ok = mbar_wait_bounded(&full[ns], (uint32_t)(((nc - c0) / S) & 1), D.spin);
             if (ok) {
                 const int4 inf = info[ns];
                 const unsigned char* base = ring + (size_t)ns * D.stage_cap;
@@ -353,7 +353,7 @@ __global__ void __launch_bounds__(kCtaThreads, 1) k_trsv_cta(CtaDev D, const T* 
 #pragma unroll
                 for (int kk = 0; kk < 4; ++kk) {
                     const int p = pd[kk];
-                    if (kRemote && p <= -2) acc = fma(-cur.l[kk], (T)remote_dep(pub, -p - 2, flags), acc);
+                    if (kRemote && p <= -2) acc = fma(-cur.l[kk], (T)remote_dep(pub, -p - 2, flags, D.spin), acc);
                     else if (kWindow) acc = fma(-cur.l[kk], win[p], acc);
                     else if (p >= 0) acc = fma(-cur.l[kk], (T)__ldcg(yglob + p), acc);
                 }
@@ -363,7 +363,7 @@ __global__ void __launch_bounds__(kCtaThreads, 1) k_trsv_cta(CtaDev D, const T* 
                 const T* xval = cvals + 5 * cur.np;
                 for (int kk = 0; kk < cur.width - kRec; ++kk) {
                     const int pk = xdep[kk * cur.np + t];
-                    if (kRemote && pk <= -2) acc = fma(-xval[kk * cur.np + t], (T)remote_dep(pub, -pk - 2, flags), acc);
+                    if (kRemote && pk <= -2) acc = fma(-xval[kk * cur.np + t], (T)remote_dep(pub, -pk - 2, flags, D.spin), acc);
                     else if (kFar && pk <= -2) acc = fma(-xval[kk * cur.np + t], __ldcg(outq + (-pk - 2)), acc);
                     else if (kWindow) acc = fma(-xval[kk * cur.np + t], win[pk], acc);
                     else if (pk >= 0) acc = fma(-xval[kk * cur.np + t], (T)__ldcg(yglob + pk), acc);
@@ -481,7 +481,7 @@ __global__ void __launch_bounds__(kSplitThreads, 1) k_trsv_split(CtaDev D, const
     if (threadIdx.x >= kCtaRows) {
         // ---------------- operand warps: stage step j during step j - 1
         const int t2 = threadIdx.x - kCtaRows;
-        bool ok = mbar_wait_bounded(&full[0], 0u);
+        bool ok = mbar_wait_bounded(&full[0], 0u, D.spin);
         int c = c0, s = 0, u = 0, nst = 0, q0e = 0;
         const int32_t* hdr = nullptr;
         const T* vals = nullptr;
@@ -530,7 +530,7 @@ __global__ void __launch_bounds__(kSplitThreads, 1) k_trsv_split(CtaDev D, const
                     ++c;
                     s = (c - c0) % S;
                     u = 0;
-                    ok = mbar_wait_bounded(&full[s], (uint32_t)(((c - c0) / S) & 1));
+                    ok = mbar_wait_bounded(&full[s], (uint32_t)(((c - c0) / S) & 1), D.spin);
                     if (ok) {
                         const int4 inf = info[s];
                         const unsigned char* base = ring + (size_t)s * D.stage_cap;
@@ -681,7 +681,7 @@ __global__ void __launch_bounds__(kCtaThreads, 1) k_trsv_flag(CtaDev D, const fl
     const float* wrh;
     int4 wh;
     {
-        const bool ok = mbar_wait_bounded(&full[0], 0u);
+        const bool ok = mbar_wait_bounded(&full[0], 0u, D.spin);
         if (!__all_sync(kAll, ok)) {
             if (lane == 0) atomicOr(flags, kFlagTimeout | kFlagAbort);
             return;
@@ -750,7 +750,7 @@ __global__ void __launch_bounds__(kCtaThreads, 1) k_trsv_flag(CtaDev D, const fl
                 if (wc + 1 - S >= rel) break;
                 ++wc;
                 const int ws = (wc - c0) % S;
-                const bool ok = mbar_wait_bounded(&full[ws], (uint32_t)(((wc - c0) / S) & 1));
+                const bool ok = mbar_wait_bounded(&full[ws], (uint32_t)(((wc - c0) / S) & 1), D.spin);
                 if (!__all_sync(kAll, ok)) {
                     if (lane == 0) atomicOr(flags, kFlagTimeout | kFlagAbort);
                     return;
@@ -779,7 +779,7 @@ __global__ void __launch_bounds__(kCtaThreads, 1) k_trsv_flag(CtaDev D, const fl
                 if (slot_pos(w3) != e3) w3 = ld_slot(win + cur.dep.w);
                 if ((++spins & 255) == 0) {
                     if (ld_relaxed_s32(flags) & kFlagAbort) dead = true;
-                    else if (spins > kSpinLimit) { atomicOr(flags, kFlagTimeout | kFlagAbort); dead = true; }
+                    else if (spins > D.spin) { atomicOr(flags, kFlagTimeout | kFlagAbort); dead = true; }
                 }
             }
             float acc = cur.rhs;
@@ -798,7 +798,7 @@ __global__ void __launch_bounds__(kCtaThreads, 1) k_trsv_flag(CtaDev D, const fl
                         wx = ld_slot(win + sl);
                         if ((++spins & 255) == 0) {
                             if (ld_relaxed_s32(flags) & kFlagAbort) dead = true;
-                            else if (spins > kSpinLimit) { atomicOr(flags, kFlagTimeout | kFlagAbort); dead = true; }
+                            else if (spins > D.spin) { atomicOr(flags, kFlagTimeout | kFlagAbort); dead = true; }
                         }
                     }
                     acc = fmaf(-xval[kk * cur.np + cur_e], slot_val(wx), acc);
@@ -1440,6 +1440,7 @@ npcg_status cta_trsv_launch(Handle* h, cudaStream_t s, Pattern* P, const CtaLayo
         d.stages = C.split_stages[f32];
         d.stage_cap = C.stage_cap[f32];
         d.win = C.win_slots;
+        d.spin = h->spin_limit;
         const size_t smem = kBarBytes + win_bytes(C, f32) +
                             (f32 ? split_staging_bytes<float>() : split_staging_bytes<double>()) +
                             (size_t)C.stage_cap[f32] * C.split_stages[f32];
@@ -1462,6 +1463,7 @@ npcg_status cta_trsv_launch(Handle* h, cudaStream_t s, Pattern* P, const CtaLayo
         d.stages = C.nstages[2];
         d.stage_cap = C.stage_cap[2];
         d.win = C.win_slots;
+        d.spin = h->spin_limit;
         k_trsv_flag<<<C.nunits, kCtaThreads, smem_bytes_flag(C), s>>>(d, static_cast<const float*>(rhs_v),
                                                                       static_cast<float*>(outq), st, P->ctl.p + 1);
         NPCG_CUDA(h, cudaGetLastError());
@@ -1478,6 +1480,7 @@ npcg_status cta_trsv_launch(Handle* h, cudaStream_t s, Pattern* P, const CtaLayo
     d.stages = stages;
     d.stage_cap = C.stage_cap[f32];
     d.win = C.win_slots;
+    d.spin = h->spin_limit;
     const size_t smem = smem_bytes(C, f32);
     int* flags = P->ctl.p + 1;
     const int g = C.nunits;

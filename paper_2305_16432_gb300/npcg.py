@@ -10,6 +10,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+import sys
 import threading
 
 import numpy as np
@@ -20,9 +21,11 @@ from . import inputs as I
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libnpcg.so")
 
-NPCG_OK, NPCG_EINVAL, NPCG_ENOMEM, NPCG_ECUDA, NPCG_ENOTSPD, NPCG_EBREAKDOWN, NPCG_EMAXITER, NPCG_ETIMEOUT = range(8)
+(NPCG_OK, NPCG_EINVAL, NPCG_ENOMEM, NPCG_ECUDA, NPCG_ENOTSPD, NPCG_EBREAKDOWN, NPCG_EMAXITER, NPCG_ETIMEOUT,
+ NPCG_ESTALL) = range(9)
 FD, FEM = 0, 1
 FP32, BF16 = 0, 1
+DIAG_SOFTPLUS, DIAG_LDLT_DIAGA, DIAG_LDLT_ROWS = 0, 1, 2
 LOSS_AB, LOSS_FROB = 0, 1
 PREC_NONE, PREC_JACOBI, PREC_LLT, PREC_LLT32 = 0, 1, 2, 3
 METHOD_GNN, METHOD_IC0, METHOD_JACOBI, METHOD_CG, METHOD_SGS = 0, 1, 2, 3, 4
@@ -56,7 +59,12 @@ class _Cfg(C.Structure):
 
 
 class _Stats(C.Structure):
-    _fields_ = [("iters", C.c_int32), ("status", C.c_int32), ("relres", C.c_double)]
+    _fields_ = [("iters", C.c_int32), ("status", C.c_int32), ("relres", C.c_double), ("fallback", C.c_int32),
+                ("fallback_iters", C.c_int32)]
+
+
+class _Opts(C.Structure):
+    _fields_ = [("stall_iters", C.c_int32), ("fallback_ic0", C.c_int32)]
 
 
 _lib = None
@@ -89,10 +97,13 @@ def lib():
                 "npcg_sgs_factor": [vp, vp, vp, vp],
                 "npcg_pcg_solve": [vp, vp, vp, vp, vp, i32, vp, dbl, i32, vp],
                 "npcg_pcg_solve_batched": [vp, vp, vp, vp, vp, i32, vp, dbl, i32, vp],
+                "npcg_pcg_solve_ex": [vp, vp, vp, vp, vp, i32, vp, dbl, i32, C.POINTER(_Opts), vp],
                 "npcg_spmv": [vp, vp, vp, vp, vp],
                 "npcg_factor_load": [vp, vp, vp],
                 "npcg_sptrsv": [vp, vp, i32, vp, vp],
                 "npcg_sptrsv_timed": [vp, vp, i32, i32, vp, vp, i32, C.POINTER(dbl)],
+                "npcg_sptrsv_unclaimed": [vp, vp, i32, i32, vp, vp],
+                "npcg_set_wait_limit": [vp, i64],
                 "npcg_loss_and_grad": [vp, vp, vp, i32, vp, vp, C.POINTER(_Cfg), vp, C.POINTER(dbl), vp],
                 "npcg_adam_step": [vp, i64, vp, vp, vp, vp, i32, f32, f32, f32, f32],
                 "npcg_solve_host": [vp, vp, i32, C.POINTER(_Cfg), vp, vp, vp, vp, dbl, i32, i32, vp],
@@ -140,12 +151,20 @@ class Handle:
             msg = lib().npcg_last_error(self.h).decode()
             raise NpcgError(lib().npcg_status_string(st).decode(), msg)
 
+    def set_wait_limit(self, polls: int):
+        """npcg_set_wait_limit: polls before a device wait gives up (<= 0: default)."""
+        self.check(lib().npcg_set_wait_limit(self.h, C.c_int64(int(polls))))
+
     def close(self):
         if getattr(self, "h", None):
             lib().npcg_destroy(self.h)
             self.h = None
 
     def __del__(self):
+        # at interpreter exit the CUDA runtime may already be gone: leave the
+        # memory to the process teardown
+        if sys.is_finalizing():
+            return
         try:
             self.close()
         except Exception:
@@ -246,6 +265,10 @@ class Pattern:
             self.p = None
 
     def __del__(self):
+        # at interpreter exit the CUDA runtime may already be gone: leave the
+        # memory to the process teardown
+        if sys.is_finalizing():
+            return
         try:
             self.close()
         except Exception:
@@ -314,7 +337,8 @@ def sgs_factor(P: Pattern, A_val, out=None):
 
 # ------------------------------------------------------------------ solve
 def _stats_list(arr):
-    return [dict(iters=s.iters, status=s.status, relres=s.relres) for s in arr]
+    return [dict(iters=s.iters, status=s.status, relres=s.relres, fallback=s.fallback,
+                 fallback_iters=s.fallback_iters) for s in arr]
 
 
 def pcg_solve(P: Pattern, A_val, b, precond=PREC_LLT, L_val=None, rtol=1e-6, max_iter=None, x0=None,
@@ -336,6 +360,26 @@ def pcg_solve(P: Pattern, A_val, b, precond=PREC_LLT, L_val=None, rtol=1e-6, max
     return x, _stats_list(stats)
 
 
+def pcg_solve_ex(P: Pattern, A_val, b, precond=PREC_LLT, L_val=None, rtol=1e-6, max_iter=None, x0=None,
+                 stall_iters=0, fallback_ic0=False):
+    """npcg_pcg_solve_ex: PCG with a stagnation window and the IC(0) fallback.
+    Returns (x, stats, status)."""
+    A_val = _dev(A_val, torch.float64, "A_val")
+    b = _dev(b, torch.float64, "b")
+    x = torch.zeros_like(b) if x0 is None else _dev(x0, torch.float64, "x0").clone()
+    if L_val is not None:
+        L_val = _dev(L_val, torch.float64, "L_val")
+    if max_iter is None:
+        max_iter = int(min(10 * P.n, 2**31 - 1))
+    stats = (_Stats * P.nsys)()
+    opts = _Opts(int(stall_iters), 1 if fallback_ic0 else 0)
+    st = lib().npcg_pcg_solve_ex(P.h.h, P.p, _ptr(A_val), _ptr(b), _ptr(x), precond, _ptr(L_val), float(rtol),
+                                 int(max_iter), C.byref(opts), C.cast(stats, C.c_void_p))
+    if st not in (NPCG_OK, NPCG_EMAXITER, NPCG_EBREAKDOWN, NPCG_ESTALL):
+        P.h.check(st)
+    return x, _stats_list(stats), st
+
+
 def spmv(P: Pattern, A_val, x, out=None):
     A_val = _dev(A_val, torch.float64, "A_val")
     x = _dev(x, torch.float64, "x")
@@ -355,6 +399,14 @@ def sptrsv(P: Pattern, r, transpose=False, out=None):
     y = out if out is not None else torch.empty_like(r)
     P.h.check(lib().npcg_sptrsv(P.h.h, P.p, 1 if transpose else 0, _ptr(r), _ptr(y)))
     return y
+
+
+def sptrsv_unclaimed(P: Pattern, r, skip, transpose=False, out=None):
+    """npcg_sptrsv_unclaimed (failure-path tests): the sync-free solve with its
+    first `skip` slices never claimed.  Returns the status code (no raise)."""
+    r = _dev(r, torch.float64, "r")
+    y = out if out is not None else torch.empty_like(r)
+    return lib().npcg_sptrsv_unclaimed(P.h.h, P.p, 1 if transpose else 0, int(skip), _ptr(r), _ptr(y))
 
 
 def sptrsv_timed(P: Pattern, r, transpose=False, reps=20, out=None, f32=False):

@@ -103,7 +103,7 @@ def save_checkpoint(path, cfg, w, mom, vel, step, hist):
 
 def train(cfg: I.GnnConfig, steps=600, groups=4, per_group=8, pairs=8, m=128, lr=1e-3, lr_final=1e-4,
           seed=2023, log_every=25, w0=None, ckpt=None, resume=None, val_every=50, precision=None, sizes=None,
-          sizes3d=None, sigma3d=1.0, corr3d=0.1, head_only=False, heat=False):
+          sizes3d=None, sigma3d=1.0, corr3d=0.1, head_only=False, heat=False, corr3d_cells=None, val3d=None):
     """Adam at lr (App. A.4), cosine-decayed to lr_final over the run; returns
     the weights with the fewest validation PCG iterations.  precision: the
     network forward's arithmetic (FP32, or BF16 tensor cores with the FP32
@@ -114,7 +114,10 @@ def train(cfg: I.GnnConfig, steps=600, groups=4, per_group=8, pairs=8, m=128, lr
     zeroed, so Adam leaves it unchanged) and validate PCG started from x0.
     heat: the 2-D groups and validation systems are implicit heat steps
     M + tau K with Dirichlet arcs (inputs.heat2d) instead of stiffness
-    matrices."""
+    matrices.  corr3d_cells: the 3-D correlation length in grid cells
+    instead (corr = cells / (side + 1)), so that grids of every side see the
+    local coefficient statistics of the target grid; val3d: side of the 3-D
+    validation system (default: the middle training side)."""
     from . import build as B
     B.build()
     from . import npcg as N
@@ -125,13 +128,17 @@ def train(cfg: I.GnnConfig, steps=600, groups=4, per_group=8, pairs=8, m=128, lr
     family2d = (lambda mm, sd: I.heat2d(mm, seed=sd)) if heat else \
         (lambda mm, sd: I.fem2d(mm, sigma=1.0, corr_len=0.1, seed=sd))
     groups = len(specs)
+    def corr_of(side):
+        return corr3d_cells / (side + 1) if corr3d_cells else corr3d
+
     t0 = time.time()
     data = []
     for g, (kind, mg) in enumerate(specs):
         if kind == "fem":
             probs = [family2d(mg, seed + 100 * g + k) for k in range(per_group)]
         else:
-            probs = [I.fd3d(mg, sigma=sigma3d, corr_len=corr3d, seed=seed + 100 * g + k) for k in range(per_group)]
+            probs = [I.fd3d(mg, sigma=sigma3d, corr_len=corr_of(mg), seed=seed + 100 * g + k)
+                     for k in range(per_group)]
         data.append(make_group(N, probs, pairs, seed + g))
     t_data = time.time() - t0
     w = torch.as_tensor(I.gnn_weights(cfg, seed) if w0 is None else w0, device="cuda")
@@ -152,7 +159,8 @@ def train(cfg: I.GnnConfig, steps=600, groups=4, per_group=8, pairs=8, m=128, lr
     vals = []
     vprobs = [family2d(m, 8000 + k) for k in range(2)] if sizes else []
     if sizes3d:
-        v3 = I.fd3d(sizes3d[len(sizes3d) // 2], sigma=sigma3d, corr_len=corr3d, seed=8000)
+        sv = val3d or sizes3d[len(sizes3d) // 2]
+        v3 = I.fd3d(sv, sigma=sigma3d, corr_len=corr_of(sv), seed=8000)
         vprobs = [vprobs[0], v3] if vprobs else [v3]
     for k, pv in enumerate(vprobs):
         rp, ci, v = N.assemble_system(pv)
@@ -214,12 +222,19 @@ def main():
     ap.add_argument("--ckpt", default=None)
     ap.add_argument("--resume", default=None)
     ap.add_argument("--val_every", type=int, default=50)
-    ap.add_argument("--diag_mode", type=int, default=0, help="0: softplus diagonal; 1: L D L^T with D = diag(A)")
+    ap.add_argument("--diag_mode", type=int, default=0,
+                    help="0: softplus diagonal; 1: L = L' D^1/2 (App. A.3, D = diag(A)); 2: L = D^1/2 L~ (rows scaled)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
     ap.add_argument("--sizes", default="", help="comma-separated lattice sizes of the 2-D FEM training groups")
     ap.add_argument("--sizes3d", default="", help="comma-separated grid sides of the 3-D FD training groups")
     ap.add_argument("--sigma3d", type=float, default=1.0, help="GRF sigma of the 3-D groups")
     ap.add_argument("--corr3d", type=float, default=0.1, help="GRF correlation length of the 3-D groups")
+    ap.add_argument("--corr3d_cells", type=float, default=None,
+                    help="3-D correlation length in grid cells instead (6.4 = the 128^3 workload's 0.05)")
+    ap.add_argument("--val3d", type=int, default=None, help="side of the 3-D validation grid")
+    ap.add_argument("--eval128", action="store_true",
+                    help="also evaluate on the 128^3 benchmark system (sigma 1.5, corr 0.05) and record the "
+                         "deployed configuration's iterations as the benchmark's learned iterations")
     ap.add_argument("--loss", default="ab", choices=["ab", "frob"],
                     help="Eq. (loss_Ab) (the method) or the Frobenius loss Eq. (loss_A) (ablation)")
     ap.add_argument("--init", default=None, help="start from these weights (same network shape)")
@@ -251,7 +266,8 @@ def main():
     w, hist, tm = train(cfg, steps=args.steps, m=args.m, lr=args.lr, lr_final=args.lr_final, ckpt=args.ckpt,
                         resume=args.resume, val_every=args.val_every, precision=prec, sizes=sizes,
                         sizes3d=sizes3d, sigma3d=args.sigma3d, corr3d=args.corr3d, w0=w_init,
-                        head_only=bool(args.x0_from), heat=args.heat)
+                        head_only=bool(args.x0_from), heat=args.heat, corr3d_cells=args.corr3d_cells,
+                        val3d=args.val3d)
     w0 = torch.as_tensor(I.gnn_weights(cfg, 2023), device="cuda")
     fam = (lambda mm, sd: I.heat2d(mm, seed=sd)) if args.heat else \
         (lambda mm, sd: I.fem2d(mm, sigma=1.0, corr_len=0.1, seed=sd))
@@ -274,7 +290,8 @@ def main():
                       "systems": f"groups of 8: 2-D FEM {'heat steps (inputs.heat2d) ' if args.heat else ''}"
                                  f"lattices {sizes if sizes is not None else [args.m]} "
                                  f"(sigma 1, corr 0.1), 3-D FD sides {sizes3d or []} (sigma {args.sigma3d}, "
-                                 f"corr {args.corr3d})",
+                                 + (f"corr {args.corr3d_cells} cells = {args.corr3d_cells} / (side + 1)"
+                                    if args.corr3d_cells else f"corr {args.corr3d}") + ")",
                       "precision": args.precision, "head_only_from": os.path.basename(args.x0_from) if args.x0_from else None,
                       "initialised_from": os.path.basename(args.init) if args.init else None, **tm},
             "loss_first": hist[0], "loss_last": float(np.mean(hist[-20:])),
@@ -282,6 +299,17 @@ def main():
             f"{fam_name}256_seed0": big,
             "heldout_fd3d": fd3,
             f"learned_iters_{fam_name}256": big[0]["learned"]}
+    if args.eval128:
+        # the benchmark system, and its deployed configuration (the network's
+        # precision, FP32 triangular solves inside FP64 PCG)
+        p128 = I.fd3d_128(seed=0)
+        meta["fd3d_128_seed0"] = evaluate(N, cfg, w, [p128], precision=prec)
+        rp, ci, v = N.assemble_system(p128)
+        P128 = N.analyse(rp, ci)
+        b128 = torch.as_tensor(I.rhs(P128.n, 0), device="cuda")
+        L128 = N.gnn_factor(P128, v, b128, cfg, w, precision=prec)
+        _, s128 = N.pcg_solve(P128, v, b128, N.PREC_LLT32, L128, rtol=1e-6, max_iter=VAL_MAX_ITER)
+        meta["bench_iters"] = {"fd3d_128": s128[0]["iters"]}
     with open(os.path.splitext(args.out)[0] + ".json", "w") as f:
         json.dump(meta, f, indent=1)
     print(json.dumps(meta), flush=True)

@@ -62,7 +62,7 @@ def test_binding_structs_match_the_header(tmp_path):
     # offset of every field, from a host C program compiled against the header
     from paper_2305_16432_gb300 import npcg as N
     mirrors = {"npcg_problem": N._Problem, "npcg_pattern_info": N._Info, "npcg_gnn_config": N._Cfg,
-               "npcg_solve_stats": N._Stats}
+               "npcg_solve_stats": N._Stats, "npcg_solve_opts": N._Opts}
     lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "npcg.h"', "int main(void) {"]
     for cname, py in mirrors.items():
         lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')

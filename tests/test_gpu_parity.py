@@ -210,6 +210,8 @@ def test_malformed_patterns_rejected(N):
     (I.GnnConfig(n_mp=3, l=1, l_mp=3, h=32), I.fd3d(7, 6, 5, sigma=1.0, seed=2)),
     (I.GnnConfig(n_mp=0, l=2, l_mp=2, h=16), I.fd2d(12, 9, sigma=1.0, seed=1)),
     (I.GnnConfig(n_mp=3, l=2, l_mp=2, h=64, diag_mode=1), I.fem2d(18, sigma=1.0, seed=3)),
+    (I.GnnConfig(n_mp=3, l=2, l_mp=2, h=64, diag_mode=2), I.fd3d(9, 8, 7, sigma=1.5, corr_len=0.2, seed=3)),
+    (I.GnnConfig(n_mp=2, l=2, l_mp=2, h=32, diag_mode=2), I.fem2d(20, sigma=1.0, seed=4)),
 ])
 def test_gnn_fp32_parity(N, cfg, prob):
     Ao, (rp, ci, v) = _assemble_both(N, prob)
@@ -377,7 +379,7 @@ def test_fp32_preconditioner_apply(N, name, mode):
 
 @pytest.mark.parametrize("prob", [I.fem2d(22, sigma=1.0, seed=9), I.fd3d(9, 8, 7, sigma=1.0, seed=2),
                                   I.poisson2d_32()])
-@pytest.mark.parametrize("diag_mode", [0, 1])
+@pytest.mark.parametrize("diag_mode", [0, 1, 2])
 def test_gnn_bf16_parity(N, prob, diag_mode):
     # BF16 tensor-core MLPs with FP32 accumulation: L within 2e-2 of the FP64
     # oracle in relative Frobenius norm and in max-abs relative to max |L|

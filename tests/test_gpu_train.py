@@ -4,7 +4,18 @@ Adam against the oracle's step.
 
 Tolerance: the adjoint runs in FP32 (unit roundoff 6e-8) through chains of
 about ten MLP layers and reductions of up to a few hundred terms, so the
-gradient is compared in relative 2-norm at 1e-4 and the loss at 1e-5.
+loss is compared at 1e-5 relative and the gradient at 1e-4 relative in the
+2-norm of EVERY Linear's weight matrix and, separately, of its bias (a
+whole-vector norm would let a small block be entirely wrong).
+
+BF16 forward (mixed precision): the loss at 4e-2 (quadratic in L, whose bar
+is 2e-2), the whole gradient at 4e-2 in the 2-norm, and every block at 8e-2.
+A block's gradient is a sum over rows of products of two forward states;
+where the inputs carry signs (the node encoder's input b / ||b||_inf with
+b ~ N(0,1)) the sum cancels, |sum| << sum |.|, and the forward's relative
+rounding is amplified by that ratio (5.9 % measured on the node encoder's
+input layer).  A wrong block (a dropped term, a transposed operand, a
+missing bias) is off by O(1) and fails either bar.
 """
 import numpy as np
 import pytest
@@ -28,6 +39,32 @@ def _gpu(a, dtype=torch.float64):
     return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
 
 
+def grad_block_errors(cfg, gg, go):
+    """Relative 2-norm error of the gradient of every Linear's W and b, in
+    the flat layout (per Linear: W[out][in], then b[out])."""
+    errs, k = [], 0
+    for q, (fi, fo) in enumerate(cfg.linears()):
+        for name, size in (("W", fi * fo), ("b", fo)):
+            a, r = gg[k:k + size], go[k:k + size]
+            nr = np.linalg.norm(r)
+            e = np.linalg.norm(a - r) / nr if nr > 0 else np.linalg.norm(a)
+            errs.append((e, f"linear {q} {name} ({fo}x{fi})"))
+            k += size
+    assert k == len(go) == len(gg)
+    return errs
+
+
+def assert_grad_blocks(cfg, gg, go, tol):
+    bad = [(e, name) for e, name in grad_block_errors(cfg, gg, go) if not e <= tol]
+    assert not bad, f"gradient blocks above {tol}: {bad[:6]}"
+
+
+def assert_grad_bf16(cfg, gg, go):
+    # the mixed-precision bars (module docstring)
+    assert np.linalg.norm(gg - go) / np.linalg.norm(go) <= 4e-2
+    assert_grad_blocks(cfg, gg, go, 8e-2)
+
+
 def _pairs(A, k, seed):
     B = I.rhs(A.n, seed, count=k)
     X = np.linalg.solve(A.dense(), B.T).T
@@ -40,6 +77,7 @@ def _pairs(A, k, seed):
     (I.GnnConfig(n_mp=2, l=2, l_mp=2, h=64), I.fem2d(12, sigma=1.0, seed=5)),
     (I.GnnConfig(n_mp=0, l=2, l_mp=2, h=16), I.fd3d(4, 3, 3, sigma=1.0, seed=6)),
     (I.GnnConfig(n_mp=2, l=2, l_mp=2, h=32, diag_mode=1), I.fem2d(9, sigma=1.0, seed=7)),
+    (I.GnnConfig(n_mp=2, l=2, l_mp=2, h=64, diag_mode=2), I.fd3d(5, 4, 4, sigma=1.5, corr_len=0.2, seed=8)),
 ])
 def test_loss_and_grad_parity(N, cfg, prob):
     om, ph = I.grf_features(prob)
@@ -52,7 +90,7 @@ def test_loss_and_grad_parity(N, cfg, prob):
     lg, gg = N.loss_and_grad(P, v, _gpu(X), _gpu(B), cfg, _gpu(w, torch.float32))
     gg = gg.cpu().numpy().astype(np.float64)
     assert abs(lg - lo) <= 1e-5 * abs(lo)
-    assert np.linalg.norm(gg - go) / np.linalg.norm(go) <= 1e-4
+    assert_grad_blocks(cfg, gg, go, 1e-4)
 
 
 def test_loss_and_grad_batched_is_mean_over_systems(N):
@@ -84,7 +122,7 @@ def test_loss_and_grad_batched_is_mean_over_systems(N):
     go = np.mean([r[1] for r in ref], axis=0)
     assert abs(lg - lo) <= 1e-5 * abs(lo)
     gg = gg.cpu().numpy().astype(np.float64)
-    assert np.linalg.norm(gg - go) / np.linalg.norm(go) <= 1e-4
+    assert_grad_blocks(cfg, gg, go, 1e-4)
 
 
 def test_adam_matches_oracle(N):
@@ -120,15 +158,15 @@ def test_autograd_function_matches_oracle_gradient(N):
     (3.0 * loss).backward()
     assert abs(loss.item() - lo) <= 1e-5 * abs(lo)
     gg = wt.grad.cpu().numpy().astype(np.float64)
-    assert np.linalg.norm(gg - 3.0 * go) / np.linalg.norm(3.0 * go) <= 1e-4
+    assert_grad_blocks(cfg, gg, 3.0 * go, 1e-4)
 
 
-@pytest.mark.parametrize("diag_mode", [0, 1])
+@pytest.mark.parametrize("diag_mode", [0, 1, 2])
 def test_loss_and_grad_bf16_forward(N, diag_mode):
     """Mixed precision: BF16 tensor-core forward, FP32 adjoint at its states.
     Bars derived from the BF16 bar on L (2e-2): the loss is quadratic in L
     (2 x 2e-2), and the gradient is bilinear in the residual and the
-    network's states (again 2 x 2e-2, on the 2-norm)."""
+    network's states (again 2 x 2e-2, on every Linear's W and b)."""
     cfg = I.GnnConfig(n_mp=3, l=2, l_mp=2, h=64, diag_mode=diag_mode)
     prob = I.fem2d(14, sigma=1.0, seed=12)
     om, ph = I.grf_features(prob)
@@ -141,7 +179,7 @@ def test_loss_and_grad_bf16_forward(N, diag_mode):
     lg, gg = N.loss_and_grad(P, v, _gpu(X), _gpu(B), cfg, _gpu(w, torch.float32), precision=N.BF16)
     gg = gg.cpu().numpy().astype(np.float64)
     assert abs(lg - lo) <= 4e-2 * abs(lo)
-    assert np.linalg.norm(gg - go) / np.linalg.norm(go) <= 4e-2
+    assert_grad_bf16(cfg, gg, go)
 
 
 @pytest.mark.parametrize("prec,tl,tg", [("fp32", 1e-5, 1e-4), ("bf16", 4e-2, 4e-2)])
@@ -162,7 +200,10 @@ def test_loss_and_grad_x0_head(N, prec, tl, tg):
                              precision=N.FP32 if prec == "fp32" else N.BF16)
     gg = gg.cpu().numpy().astype(np.float64)
     assert abs(lg - lo) <= tl * abs(lo)
-    assert np.linalg.norm(gg - go) / np.linalg.norm(go) <= tg
+    if prec == "bf16":
+        assert_grad_bf16(cfg, gg, go)
+    else:
+        assert_grad_blocks(cfg, gg, go, tg)
 
 
 @pytest.mark.parametrize("cfg,prob", [
@@ -183,7 +224,7 @@ def test_frobenius_loss_and_grad_parity(N, cfg, prob):
     lg, gg = N.loss_and_grad(P, v, _gpu(X), _gpu(B), cfg, _gpu(w, torch.float32))
     gg = gg.cpu().numpy().astype(np.float64)
     assert abs(lg - lo) <= 1e-5 * abs(lo)
-    assert np.linalg.norm(gg - go) / np.linalg.norm(go) <= 1e-4
+    assert_grad_blocks(cfg, gg, go, 1e-4)
 
 
 def test_frobenius_loss_batched_is_mean_over_systems(N):
@@ -214,4 +255,45 @@ def test_frobenius_loss_batched_is_mean_over_systems(N):
         gos.append(g)
     lo, go = np.mean(los), np.mean(gos, axis=0)
     assert abs(lg - lo) <= 1e-5 * abs(lo)
-    assert np.linalg.norm(gg.cpu().numpy() - go) / np.linalg.norm(go) <= 1e-4
+    assert_grad_blocks(cfg, gg.cpu().numpy().astype(np.float64), go, 1e-4)
+
+
+_C4 = {}
+
+
+def _c4_member():
+    """One member of the training workload's size: a 128 x 128 lattice FEM
+    system (n = 15,876, about 110 k edges), the 6 x 64 network, one (x, b)
+    pair; the oracle's FP64 loss and gradient computed once."""
+    if not _C4:
+        cfg = I.GnnConfig(n_mp=6, l=2, l_mp=2, h=64, diag_mode=1)
+        prob = I.fem2d(128, sigma=1.0, corr_len=0.1, seed=1000)
+        om, ph = I.grf_features(prob)
+        Ao = O.assemble(prob, om, ph)
+        B = I.rhs(Ao.n, 91, count=1)
+        L, _ = O.ic0(Ao)
+        x, _, _, st = O.pcg(Ao, B[0], O.PREC_LLT, L, rtol=1e-12)
+        assert st == 0
+        X = x[None, :]
+        w = I.gnn_weights(cfg, 12)
+        lo, go = O.loss_and_grad(cfg, Ao, X, B, w.astype(np.float64))
+        _C4.update(cfg=cfg, prob=prob, om=om, ph=ph, X=X, B=B, w=w, lo=lo, go=go)
+    return _C4
+
+
+@pytest.mark.parametrize("prec,tl,tg", [("fp32", 1e-5, 1e-4), ("bf16", 4e-2, 4e-2)])
+def test_loss_and_grad_training_size_member(N, prec, tl, tg):
+    """A training-sized member against the oracle: many tiles of every
+    kernel, and the many-CTA split of the tensor-core weight gradient with its
+    partial sums, per Linear block at the FP32 and BF16 bars."""
+    c = _c4_member()
+    rp, ci, v = N.assemble_system(c["prob"], c["om"], c["ph"])
+    P = N.analyse(rp, ci)
+    lg, gg = N.loss_and_grad(P, v, _gpu(c["X"]), _gpu(c["B"]), c["cfg"], _gpu(c["w"], torch.float32),
+                             precision=N.FP32 if prec == "fp32" else N.BF16)
+    gg = gg.cpu().numpy().astype(np.float64)
+    assert abs(lg - c["lo"]) <= tl * abs(c["lo"])
+    if prec == "bf16":
+        assert_grad_bf16(c["cfg"], gg, c["go"])
+    else:
+        assert_grad_blocks(c["cfg"], gg, c["go"], tg)

@@ -30,7 +30,8 @@ def test_bench_picks_each_workloads_network():
     assert os.path.basename(bench.weights_for("heat2d_256")) == "gnn_6x64_heat2d.npy"
     assert os.path.basename(bench.weights_for("batched_256")) == "gnn_6x64.npy"
     assert os.path.basename(bench.weights_for("fem2d_256", x0=True)) == "gnn_6x64_fem2d_x0.npy"
-    # no dedicated 3-D network is committed: the mixed one serves the 128^3 grid
-    assert os.path.basename(bench.weights_for("fd3d_128")) == "gnn_6x64.npy"
+    assert os.path.basename(bench.weights_for("fd3d_128")) == "gnn_6x64_fd3d.npy"
+    meta3 = json.load(open(os.path.join(WDIR, "gnn_6x64_fd3d.json")))
+    assert meta3["config"]["diag_mode"] == 2 and meta3["bench_iters"]["fd3d_128"] > 0
     meta = json.load(open(os.path.join(WDIR, "gnn_6x64_fem2d_x0.json")))
     assert meta["config"]["x0_head"] == 1
