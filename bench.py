@@ -611,6 +611,7 @@ def run_solve(args, rank, world, local):
                         "analyse_ms": analyse_ms,
                         "wall_s_timed": wall, "trsv_design": design,
                         "merge_levels": P.merge_levels if design == "levelmerge" else 0,
+                        "block_units": P.block_units,
                         "trsv_tuned_ms_fwd_bwd": P.tuned_ms},
             "roofline": {"kernel": trsv_kernel + " (forward SpTRSV, " + args.apply + ", " + design + ")",
                          "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,

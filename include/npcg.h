@@ -190,6 +190,8 @@ typedef struct {
                                      16 take the one-thread-per-row SpMV)          */
     float tuned_ms_levelmerge;    /* merged levels at the tuned group size (0: not timed) */
     int32_t merge_levels;         /* levels per step of the built merged layouts (0: none) */
+    int32_t block_units;          /* row blocks of one large system's level-ordered layouts
+                                     (tuned: one per SM or fewer, thicker ones; 0: not blocked) */
 } npcg_pattern_info;
 NPCG_API npcg_status npcg_pattern_get_info(npcg_pattern p, npcg_pattern_info* out);  /* host out */
 /* Overrides the tuned design (NPCG_TRSV_AUTO restores the tuned choice).

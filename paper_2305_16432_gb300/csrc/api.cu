@@ -156,6 +156,7 @@ npcg_status npcg_pattern_get_info(npcg_pattern p, npcg_pattern_info* out) {
     out->tuned_ms_levelsplit = p->tune_ms[3];
     out->tuned_ms_levelmerge = p->tune_ms[4];
     out->merge_levels = p->mfwd.built ? p->mfwd.G : 0;
+    out->block_units = p->cfwd.blocked ? p->cfwd.nunits : 0;
     out->max_row = p->max_row;
     return NPCG_OK;
 }

@@ -374,9 +374,294 @@ __global__ void __launch_bounds__(kThreads) k_mlp_bf16(Bf16Args a) {
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem) : "memory");
 }
 
+// ------------------------------------------------------------ warp-specialised
+// Edge update and decoder (modes whose first operand is a pure copy of
+// feature rows), with tiles pipelined through the CTA: a producer warp
+// gathers the rows of upcoming tiles with cp.async into a ring of operand
+// stages (completion tracked by an mbarrier per stage), and two epilogue
+// warpgroups take alternate tiles: one elected thread of a warpgroup issues
+// the tile's tcgen05.mma chain into the warpgroup's own TMEM accumulator
+// (64 columns each) while the other warpgroup drains its accumulator with
+// tcgen05.ld, adds the bias, applies ReLU and stages the next layer's
+// operand.  The first layer's commit releases the operand stage to the
+// producer.  One CTA per SM; every wait is bounded.
+constexpr int kWsStages = 3;
+constexpr int kWsThreads = 2 * kM + 32;
+
+struct WsPlan {
+    uint32_t w, a0, a1, bias, bars, tslot, total;
+};
+
+__host__ __device__ inline WsPlan ws_plan(int mode, int depth) {
+    const int in = mode_in(mode, kH);
+    const int last = mode == MODE_DEC ? depth - 1 : depth;
+    uint32_t wbytes = 0;
+    for (int l = 0; l <= last; ++l) wbytes += (uint32_t)((l == 0 ? in : kH) / 64) * (kH * 128);
+    WsPlan p;
+    p.w = 0;
+    p.a0 = p.w + wbytes;                                        // [stage][in / 64 K-blocks][128 x 64]
+    p.a1 = p.a0 + (uint32_t)kWsStages * (uint32_t)(in / 64) * (kM * 128);   // [warpgroup][128 x 64]
+    p.bias = p.a1 + 2u * (kM * 128);                            // FP32 biases + decoder scalar layer
+    p.bars = p.bias + (uint32_t)(depth + 1) * kH * 4 + (kH + 1) * 4;
+    p.bars = (p.bars + 15) & ~15u;                              // full[S], empty[S], mma[2]
+    p.tslot = p.bars + (uint32_t)(2 * kWsStages + 2) * 8;
+    p.total = p.tslot + 16;
+    return p;
+}
+
+__device__ __forceinline__ void ws_bar_init(uint64_t* b, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(s_addr(b)), "r"(count) : "memory");
+}
+
+// one arrive on the barrier once every cp.async this thread issued before has landed
+__device__ __forceinline__ void cp_async_arrive(uint64_t* b) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(s_addr(b)) : "memory");
+}
+
+// named barrier of one epilogue warpgroup that also ANDs a flag over it
+__device__ __forceinline__ bool group_agree(int g, bool ok) {
+    uint32_t all_ok;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, %2, %3, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(all_ok)
+        : "r"((uint32_t)ok), "r"(1 + g), "r"(kM)
+        : "memory");
+    return all_ok != 0;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kWsThreads, 1) k_mlp_bf16_ws(Bf16Args a) {
+    static_assert(MODE == MODE_EDGE || MODE == MODE_DEC, "pure-copy operand modes only");
+    extern __shared__ __align__(1024) unsigned char sm_raw[];
+    unsigned char* sm = sm_raw + ((1024u - (s_addr(sm_raw) & 1023u)) & 1023u);
+    constexpr int IN = mode_in(MODE, kH);
+    constexpr int NKB = IN / 64;               // K-blocks of the first operand
+    constexpr int CH = IN / 8;                 // 16-byte chunks per operand row
+    const int depth = a.depth;
+    const int last = MODE == MODE_DEC ? depth - 1 : depth;
+    const WsPlan P = ws_plan(MODE, depth);
+    unsigned char* W = sm + P.w;
+    unsigned char* A0 = sm + P.a0;
+    unsigned char* A1 = sm + P.a1;
+    float* bias = reinterpret_cast<float*>(sm + P.bias);
+    float* s_out = bias + (depth + 1) * kH;    // decoder scalar layer: W[64], b
+    uint64_t* full = reinterpret_cast<uint64_t*>(sm + P.bars);
+    uint64_t* empty = full + kWsStages;
+    uint64_t* mbar = empty + kWsStages;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + P.tslot);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    // ---- weights (BF16, swizzled K-blocks) and biases, once per CTA
+    {
+        const float* src = a.w;
+        uint32_t woff = 0;
+        for (int l = 0; l <= depth; ++l) {
+            const int fi = l == 0 ? IN : kH, fo = (MODE == MODE_DEC && l == depth) ? 1 : kH;
+            if (l <= last) {
+                for (int t = tid; t < fo * fi; t += kWsThreads) {
+                    const int n = t / fi, k = t % fi;
+                    unsigned char* blk = W + woff + (uint32_t)(k / 64) * (kH * 128);
+                    *reinterpret_cast<__nv_bfloat16*>(blk + swz(n, k % 64)) = __float2bfloat16_rn(src[t]);
+                }
+                woff += (uint32_t)(fi / 64) * (kH * 128);
+                for (int t = tid; t < fo; t += kWsThreads) bias[l * kH + t] = src[fi * fo + t];
+            } else {                            // decoder scalar output layer
+                for (int t = tid; t < kH; t += kWsThreads) s_out[t] = src[t];
+                if (tid == 0) s_out[kH] = src[kH];
+            }
+            src += fi * fo + fo;
+        }
+    }
+    if (tid == 0) {
+        for (int s = 0; s < kWsStages; ++s) {
+            ws_bar_init(&full[s], 32);
+            ws_bar_init(&empty[s], 1);
+        }
+        ws_bar_init(&mbar[0], 1);
+        ws_bar_init(&mbar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(s_addr(tmem_slot))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int64_t ntiles = (a.nrows + kM - 1) / kM;
+    bool ok = true;
+
+    if (warp == 2 * kM / 32) {
+        // ---------------- producer warp: operand rows of tile j into stage j % S
+        int nrow[4], ncol[4];
+        auto load_idx = [&](int64_t tile) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int64_t k = tile * kM + lane + 32 * q;
+                const bool in = tile < ntiles && k < a.nrows;
+                nrow[q] = in && MODE == MODE_EDGE ? a.erow[k] : 0;
+                ncol[q] = in && MODE == MODE_EDGE ? a.ci[k] : 0;
+            }
+        };
+        load_idx(blockIdx.x);
+        for (int64_t j = 0;; ++j) {
+            const int64_t tile = blockIdx.x + j * gridDim.x;
+            if (tile >= ntiles) break;
+            const int s = (int)(j % kWsStages);
+            if (j >= kWsStages) {
+                if (!bar_wait(&empty[s], (uint32_t)(((j / kWsStages) - 1) & 1))) {
+                    ok = false;
+                    break;
+                }
+            }
+            unsigned char* dst = A0 + (uint32_t)s * NKB * (kM * 128);
+            int crow[4], ccol[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) { crow[q] = nrow[q]; ccol[q] = ncol[q]; }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int r = lane + 32 * q;
+                const int64_t k = tile * kM + r;
+                const bool in = k < a.nrows;
+#pragma unroll
+                for (int c = 0; c < CH; ++c) {
+                    const int seg = c >> 3, cc = c & 7;
+                    const __nv_bfloat16* src = seg == 0 ? a.ein + (in ? k : 0) * kH
+                                             : seg == 1 ? a.vin + (int64_t)crow[q] * kH
+                                                        : a.vin + (int64_t)ccol[q] * kH;
+                    cp_async16(s_addr(dst + (uint32_t)seg * (kM * 128) + swz(r, cc * 8)), src + cc * 8, in ? 16u : 0u);
+                }
+            }
+            cp_async_arrive(&full[s]);
+            load_idx(tile + gridDim.x);          // the next tile's indices, under this tile's copies
+        }
+        cp_async_wait<0>();                      // no copy may land after the CTA leaves
+        if (!ok) atomicOr(a.flags, kFlagTimeout);
+    } else {
+        // ---------------- epilogue warpgroup g: tiles j = g, g + 2, ...
+        const int g = warp >> 2, r = tid & (kM - 1);
+        const uint32_t acc_col = tmem + (uint32_t)(g * kH);
+        const uint32_t my_lanes = acc_col + ((uint32_t)((warp & 3) * 32) << 16);
+        unsigned char* A1g = A1 + (uint32_t)g * (kM * 128);
+        uint32_t mphase = 0;
+        const bool elected = r == 0;
+        for (int64_t j = g;; j += 2) {
+            const int64_t tile = blockIdx.x + j * gridDim.x;
+            if (tile >= ntiles) break;
+            const int s = (int)(j % kWsStages);
+            const bool got = bar_wait(&full[s], (uint32_t)((j / kWsStages) & 1));
+            if (!group_agree(g, got)) { ok = false; break; }
+            tc_fence_after();
+            uint32_t woff = 0;
+            const int64_t row = tile * kM + r;
+            for (int l = 0; l <= last; ++l) {
+                const int kin = l == 0 ? IN : kH;
+                if (elected) {
+                    // the operand rows landed through cp.async (observed on the
+                    // stage's barrier) or generic stores: order them before the
+                    // tensor core's reads
+                    fence_async_smem();
+                    const uint32_t abase = l == 0 ? s_addr(A0 + (uint32_t)s * NKB * (kM * 128)) : s_addr(A1g);
+                    const uint32_t wbase = s_addr(W + woff);
+                    for (int q = 0; q < kin / 16; ++q) {
+                        const uint32_t kb = (uint32_t)(q >> 2), ko = (uint32_t)(q & 3) * 32;
+                        mma_bf16(acc_col, smem_desc(abase + kb * (kM * 128) + ko),
+                                 smem_desc(wbase + kb * (kH * 128) + ko), q > 0 ? 1u : 0u);
+                    }
+                    if (l == 0) mma_commit(&empty[s]);      // the operand stage is free once read
+                    mma_commit(&mbar[g]);
+                }
+                woff += (uint32_t)(kin / 64) * (kH * 128);
+                const bool done = bar_wait(&mbar[g], mphase);
+                mphase ^= 1u;
+                if (!group_agree(g, done)) { ok = false; break; }
+                tc_fence_after();
+                float v[64];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float t16[16];
+                    tmem_ld16(my_lanes + q * 16, t16);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) v[q * 16 + i] = t16[i];
+                }
+                tmem_wait_ld();
+                const float* bl = bias + l * kH;
+                if (l < last || (MODE != MODE_DEC && l < depth)) {
+                    // the next layer's operand (its previous reader has completed)
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        __nv_bfloat16 h8[8];
+#pragma unroll
+                        for (int jj = 0; jj < 8; ++jj) h8[jj] = __float2bfloat16_rn(fmaxf(v[c * 8 + jj] + bl[c * 8 + jj], 0.0f));
+                        *reinterpret_cast<uint4*>(A1g + swz(r, c * 8)) = *reinterpret_cast<uint4*>(h8);
+                    }
+                    fence_async_smem();
+                    tc_fence_before();
+                    asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(kM) : "memory");
+                    tc_fence_after();
+                } else if (MODE == MODE_DEC) {
+                    float sacc = s_out[kH];
+#pragma unroll
+                    for (int o = 0; o < kH; ++o) sacc = fmaf(s_out[o], fmaxf(v[o] + bl[o], 0.0f), sacc);
+                    if (row < a.nrows) a.sout[row] = sacc;
+                } else {
+                    if (row < a.nrows) {
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) {
+                            __nv_bfloat16 h8[8];
+#pragma unroll
+                            for (int jj = 0; jj < 8; ++jj) h8[jj] = __float2bfloat16_rn(v[c * 8 + jj] + bl[c * 8 + jj]);
+                            *reinterpret_cast<uint4*>(a.out + row * kH + c * 8) = *reinterpret_cast<uint4*>(h8);
+                        }
+                        if (a.out32) {
+                            float4* o = reinterpret_cast<float4*>(a.out32 + row * kH);
+#pragma unroll
+                            for (int c = 0; c < 16; ++c)
+                                o[c] = make_float4(v[4 * c] + bl[4 * c], v[4 * c + 1] + bl[4 * c + 1],
+                                                   v[4 * c + 2] + bl[4 * c + 2], v[4 * c + 3] + bl[4 * c + 3]);
+                        }
+                    }
+                }
+            }
+            if (!ok) break;
+            // this tile's accumulator reads are done before the next tile's
+            // first product is issued into it
+            tc_fence_before();
+            asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(kM) : "memory");
+            tc_fence_after();
+        }
+        if (!ok) {
+            // a product still in flight gets one more bounded wait before the
+            // tensor memory is released
+            bar_wait(&mbar[g], mphase);
+            if (r == 0) atomicOr(a.flags, kFlagTimeout);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem) : "memory");
+}
+
 template <int MODE>
 npcg_status launch_bf16(Handle* h, const Bf16Args& a) {
     if (a.nrows == 0) return NPCG_OK;
+    if constexpr (MODE == MODE_EDGE || MODE == MODE_DEC) {
+        const WsPlan p = ws_plan(MODE, a.depth);
+        const size_t smem = p.total + 1024;   // alignment slack
+        if (smem <= 227 * 1024) {
+            NPCG_CUDA(h, cudaFuncSetAttribute(k_mlp_bf16_ws<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)smem));
+            const int64_t ntiles = (a.nrows + kM - 1) / kM;
+            const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)h->num_sms));
+            k_mlp_bf16_ws<MODE><<<grid, kWsThreads, smem, h->stream>>>(a);
+            NPCG_CUDA(h, cudaGetLastError());
+            return NPCG_OK;
+        }
+    }
     const SmemPlan p = plan(MODE, a.depth);
     const size_t smem = p.total + 1024;       // alignment slack
     if (smem > 227 * 1024) return set_error(h, NPCG_EINVAL, "MLP too deep for the BF16 kernel");

@@ -199,6 +199,7 @@ struct Pattern {
     float tune_ms[5] = {0.f, 0.f, 0.f, 0.f, 0.f}; // measured fwd+bwd time: sync-free, level barrier,
                                                   // level flags, split roles, merged levels
     int merge_G = 0;               // levels per step of the tuned merged-level layouts (0: none)
+    int block_units = 0;           // row blocks of a blocked layout (0: one per SM), tuned
     bool cta_flag = false;         // level-ordered solves use the flag-synchronised FP32 kernel
     bool cta_split = false;        // level-ordered solves use the split-role kernel
     DevBuf<double> r_cf, y_cb, yglob;  // rhs in processing order, window backing

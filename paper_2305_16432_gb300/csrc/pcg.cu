@@ -814,6 +814,42 @@ npcg_status trsv_autotune(Handle* h, Pattern* P) {
     // all entries 1: a well-defined solve of the same structure (values do not
     // change the timing)
     NPCG_TRY(factor_load(h, P, L.p));
+    // one large system in row blocks: the number of blocks (one per SM, or
+    // half or a quarter as many thicker ones) is chosen by timing the
+    // level-synchronous solve, and the layouts are rebuilt for it
+    if (P->cfwd.blocked) {
+        const int cand[3] = {h->num_sms, h->num_sms / 2, h->num_sms / 4};
+        double best_u = 1e30;
+        int best = cand[0];
+        P->trsv_mode = kTrsvCta;
+        P->cta_flag = P->cta_split = P->cta_merge = false;
+        for (int U : cand) {
+            if (U < 1) continue;
+            if (U != P->block_units) {
+                P->block_units = U;
+                NPCG_TRY(cta_layout_build(h, P, false, &P->cfwd));
+                NPCG_TRY(cta_layout_build(h, P, true, &P->cbwd));
+                NPCG_TRY(cta_link(h, P));
+                NPCG_TRY(factor_load(h, P, L.p));
+            }
+            if (cta_stages(P->cfwd) < 2 || cta_stages(P->cbwd) < 2) continue;
+            double t = 1e30;
+            for (int rep = 0; rep < 3; ++rep) {
+                double f = 0.0, b = 0.0;
+                NPCG_TRY(sptrsv_timed_run(h, P, 0, r.p, y.p, 1, &f, true));
+                NPCG_TRY(sptrsv_timed_run(h, P, 1, r.p, y.p, 1, &b, true));
+                t = std::min(t, f + b);
+            }
+            if (t < best_u) { best_u = t; best = U; }
+        }
+        if (best != P->block_units) {
+            P->block_units = best;
+            NPCG_TRY(cta_layout_build(h, P, false, &P->cfwd));
+            NPCG_TRY(cta_layout_build(h, P, true, &P->cbwd));
+            NPCG_TRY(cta_link(h, P));
+            NPCG_TRY(factor_load(h, P, L.p));
+        }
+    }
     // sync-free and level order with a barrier per step; the flag-synchronised
     // and split-role variants measured slower on every workload and are not
     // timed (npcg_pattern_set_trsv still selects them)
@@ -836,10 +872,14 @@ npcg_status trsv_autotune(Handle* h, Pattern* P) {
     // merged levels: the fastest of 2, 4 and 8 levels per step
     P->tune_ms[4] = 0.f;
     P->merge_G = 0;
-    if (kMergeEnabled && !(P->nsys == 1 && P->n >= ((int64_t)1 << 18)) && P->n <= ((int64_t)1 << 22)) {
+    if (kMergeEnabled && P->n <= ((int64_t)1 << 22)) {
+        // the host plan grows with G (eight levels per group on 2^21 rows
+        // take several gigabytes and tens of seconds to plan): G = 8 is tried
+        // below 2^20 rows only
         const int cand[3] = {2, 4, 8};
         double best_all = 1e30;
         for (int G : cand) {
+            if (G == 8 && P->n > ((int64_t)1 << 20)) continue;
             if (merge_build(h, P, G) != NPCG_OK) continue;
             if (cta_stages(P->mfwd.lay) < 2 || cta_stages(P->mbwd.lay) < 2) continue;
             P->trsv_mode = kTrsvCta;

@@ -350,23 +350,58 @@ __global__ void __launch_bounds__(kCtaThreads, 1) k_trsv_cta(CtaDev D, const T* 
                 acc = fma(-cur.l[3], yw3, acc);
             } else {
                 const int pd[4] = {cur.dep.x, cur.dep.y, cur.dep.z, cur.dep.w};
+                // remote values: every load is issued before any is waited
+                // for, so a row with several remote dependencies pays one
+                // round trip, not one per dependency
+                unsigned long long rb[4] = {0ull, 0ull, 0ull, 0ull};
+                if (kRemote) {
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        if (pd[kk] <= -2) rb[kk] = ld_relaxed_u64(pub + (-pd[kk] - 2));
+                }
 #pragma unroll
                 for (int kk = 0; kk < 4; ++kk) {
                     const int p = pd[kk];
-                    if (kRemote && p <= -2) acc = fma(-cur.l[kk], (T)remote_dep(pub, -p - 2, flags, D.spin), acc);
-                    else if (kWindow) acc = fma(-cur.l[kk], win[p], acc);
-                    else if (p >= 0) acc = fma(-cur.l[kk], (T)__ldcg(yglob + p), acc);
+                    if (kRemote && p <= -2) {
+                        const double yv = rb[kk] != kSentinelBits ? __longlong_as_double((long long)rb[kk])
+                                                                  : remote_dep(pub, -p - 2, flags, D.spin);
+                        acc = fma(-cur.l[kk], (T)yv, acc);
+                    } else if (kWindow) {
+                        acc = fma(-cur.l[kk], win[p], acc);
+                    } else if (p >= 0) {
+                        acc = fma(-cur.l[kk], (T)__ldcg(yglob + p), acc);
+                    }
                 }
             }
             if (cur.width > kRec) {
                 const int32_t* xdep = chdr + kHdrInts + 6 * cur.np;
                 const T* xval = cvals + 5 * cur.np;
-                for (int kk = 0; kk < cur.width - kRec; ++kk) {
-                    const int pk = xdep[kk * cur.np + t];
-                    if (kRemote && pk <= -2) acc = fma(-xval[kk * cur.np + t], (T)remote_dep(pub, -pk - 2, flags, D.spin), acc);
-                    else if (kFar && pk <= -2) acc = fma(-xval[kk * cur.np + t], __ldcg(outq + (-pk - 2)), acc);
-                    else if (kWindow) acc = fma(-xval[kk * cur.np + t], win[pk], acc);
-                    else if (pk >= 0) acc = fma(-xval[kk * cur.np + t], (T)__ldcg(yglob + pk), acc);
+                for (int k0 = 0; k0 < cur.width - kRec; k0 += 4) {
+                    const int kn = min(4, cur.width - kRec - k0);
+                    int pk[4];
+                    unsigned long long rb[4] = {0ull, 0ull, 0ull, 0ull};
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        pk[j] = j < kn ? xdep[(k0 + j) * cur.np + t] : -1;
+                        if (kRemote && pk[j] <= -2) rb[j] = ld_relaxed_u64(pub + (-pk[j] - 2));
+                    }
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        if (j >= kn) break;
+                        const T lv = xval[(k0 + j) * cur.np + t];
+                        const int q = pk[j];
+                        if (kRemote && q <= -2) {
+                            const double yv = rb[j] != kSentinelBits ? __longlong_as_double((long long)rb[j])
+                                                                     : remote_dep(pub, -q - 2, flags, D.spin);
+                            acc = fma(-lv, (T)yv, acc);
+                        } else if (kFar && q <= -2) {
+                            acc = fma(-lv, __ldcg(outq + (-q - 2)), acc);
+                        } else if (kWindow) {
+                            acc = fma(-lv, win[q], acc);
+                        } else if (q >= 0) {
+                            acc = fma(-lv, (T)__ldcg(yglob + q), acc);
+                        }
+                    }
                 }
             }
             const T y = acc * cur.dinv;
@@ -1102,9 +1137,13 @@ npcg_status cta_layout_build(Handle* h, Pattern* P, bool upper, CtaLayout* C, co
     // one per SM, listed in dependency order (the backward solve runs from
     // the last row, so its blocks come last-first)
     std::vector<std::pair<int64_t, int64_t>> units;
-    C->blocked = !dep && P->nsys == 1 && n >= kBlockedRows;
+    C->blocked = P->nsys == 1 && n >= kBlockedRows;
     if (C->blocked) {
-        const int64_t B = (n + h->num_sms - 1) / h->num_sms;
+        // fewer, thicker blocks put fewer cross-SM hand-offs on the critical
+        // path of a long level chain; their number is tuned at analysis
+        // (merged-level layouts keep one block per SM: fewer blocks measured slower there)
+        const int U = !dep && P->block_units > 0 ? P->block_units : h->num_sms;
+        const int64_t B = (n + U - 1) / U;
         for (int64_t r0 = 0; r0 < n; r0 += B) units.push_back({r0, std::min<int64_t>(n, r0 + B)});
         if (upper) std::reverse(units.begin(), units.end());
     } else {

@@ -54,6 +54,11 @@ __global__ void k_merge_rhs(int64_t n, const int32_t* cperm, const int64_t* crp,
     }
 }
 
+__global__ void k_merge_fill(int64_t n, double* y) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = sentinel_f64();
+}
+
 template <class T>
 static npcg_status upload(Handle* h, DevBuf<T>& d, const std::vector<T>& v) {
     NPCG_CUDA(h, d.alloc(std::max<size_t>(v.size(), 1)));
@@ -146,12 +151,11 @@ npcg_status merge_build_dir(Handle* h, Pattern* P, bool upper, int G, MergeDir* 
 
 }  // namespace
 
-// Both directions, groups of G levels (one system per CTA; patterns laid out
-// in per-SM row blocks keep their own design).
+// Both directions, groups of G levels (one system per CTA, or one large
+// system in per-SM row blocks whose dependencies on earlier blocks are
+// published, as in the level-synchronous design).
 npcg_status merge_build(Handle* h, Pattern* P, int G) {
     if (G < 1 || G > 64) return set_error(h, NPCG_EINVAL, "levels per group must be in [1, 64]");
-    if (P->nsys == 1 && P->n >= (int64_t)1 << 18)
-        return set_error(h, NPCG_EINVAL, "merged levels are built for systems below 2^18 rows");
     // the plan is built on the host (about a kilobyte per row in flight)
     if (P->n > (int64_t)1 << 22) return set_error(h, NPCG_EINVAL, "merged levels are built for up to 2^22 rows");
     if (P->mfwd.built && P->mfwd.G == G && P->mbwd.built && P->mbwd.G == G) return NPCG_OK;
@@ -194,6 +198,28 @@ void merge_apply(Handle* h, cudaStream_t s, Pattern* P, bool f32) {
     const int blocks = std::max(1, std::min(ceil_div(n, 256), h->num_sms * 8));
     const MergeDir& F = P->mfwd;
     const MergeDir& B = P->mbwd;
+    if (F.lay.blocked) {
+        // row blocks publish y and z in natural order (FP64; the update
+        // kernel resets both to the sentinel and the tickets to zero every
+        // iteration), so the backward right-hand side reads y there and z
+        // needs no permutation
+        if (f32) {
+            k_merge_rhs<double, float><<<blocks, 256, 0, s>>>(n, F.lay.cperm.p, F.crp.p, F.ccol.p, F.C.p, P->r.p,
+                                                              reinterpret_cast<float*>(P->r_cf.p));
+            cta_trsv_launch(h, s, P, F.lay, P->r_cf.p, P->yq.p, P->st.p, true, P->ctl.p + 2, P->y.p);
+            k_merge_rhs<double, float><<<blocks, 256, 0, s>>>(n, B.lay.cperm.p, B.crp.p, B.ccol.p, B.C.p, P->y.p,
+                                                              reinterpret_cast<float*>(P->y_cb.p));
+            cta_trsv_launch(h, s, P, B.lay, P->y_cb.p, P->yq.p, P->st.p, true, P->ctl.p + 3, P->z.p);
+        } else {
+            k_merge_rhs<double, double><<<blocks, 256, 0, s>>>(n, F.lay.cperm.p, F.crp.p, F.ccol.p, F.C.p, P->r.p,
+                                                               reinterpret_cast<double*>(P->r_cf.p));
+            cta_trsv_launch(h, s, P, F.lay, P->r_cf.p, P->yq.p, P->st.p, false, P->ctl.p + 2, P->y.p);
+            k_merge_rhs<double, double><<<blocks, 256, 0, s>>>(n, B.lay.cperm.p, B.crp.p, B.ccol.p, B.C.p, P->y.p,
+                                                               reinterpret_cast<double*>(P->y_cb.p));
+            cta_trsv_launch(h, s, P, B.lay, P->y_cb.p, P->yq.p, P->st.p, false, P->ctl.p + 3, P->z.p);
+        }
+        return;
+    }
     if (f32) {
         k_merge_rhs<double, float><<<blocks, 256, 0, s>>>(n, F.lay.cperm.p, F.crp.p, F.ccol.p, F.C.p, P->r.p,
                                                           reinterpret_cast<float*>(P->r_cf.p));
@@ -229,8 +255,14 @@ npcg_status merge_sptrsv(Handle* h, cudaStream_t s, Pattern* P, int transpose, c
         k_merge_rhs<double, double><<<blocks, 256, 0, s>>>(n, D.lay.cperm.p, D.crp.p, D.ccol.p, D.C.p, r,
                                                            reinterpret_cast<double*>(P->r_cf.p));
     NPCG_CUDA(h, cudaGetLastError());
+    if (D.lay.blocked) {
+        // row blocks: published values (sentinel until written) and a ticket
+        k_merge_fill<<<blocks, 256, 0, s>>>(n, P->y.p);
+        NPCG_CUDA(h, cudaMemsetAsync(P->ctl.p + 2 + (transpose ? 1 : 0), 0, sizeof(int), s));
+    }
     if (e0) NPCG_CUDA(h, cudaEventRecord(e0, s));
-    NPCG_TRY(cta_trsv_launch(h, s, P, D.lay, P->r_cf.p, P->yq.p, nullptr, f32));
+    NPCG_TRY(cta_trsv_launch(h, s, P, D.lay, P->r_cf.p, P->yq.p, nullptr, f32, P->ctl.p + 2 + (transpose ? 1 : 0),
+                             P->y.p));
     if (e1) NPCG_CUDA(h, cudaEventRecord(e1, s));
     return cta_permute(h, s, P, D.lay, P->yq.p, f32, D.lay.cpos.p, y, false);
 }

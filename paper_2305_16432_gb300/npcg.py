@@ -50,7 +50,7 @@ class _Info(C.Structure):
                 ("nlev_fwd", C.c_int32), ("nlev_bwd", C.c_int32), ("trsv_mode", C.c_int32),
                 ("tuned_ms_syncfree", C.c_float), ("tuned_ms_levelsync", C.c_float),
                 ("tuned_ms_levelflag", C.c_float), ("tuned_ms_levelsplit", C.c_float), ("max_row", C.c_int32),
-                ("tuned_ms_levelmerge", C.c_float), ("merge_levels", C.c_int32)]
+                ("tuned_ms_levelmerge", C.c_float), ("merge_levels", C.c_int32), ("block_units", C.c_int32)]
 
 
 class _Cfg(C.Structure):
@@ -234,6 +234,7 @@ class Pattern:
                          "levelflag": info.tuned_ms_levelflag, "levelsplit": info.tuned_ms_levelsplit,
                          "levelmerge": info.tuned_ms_levelmerge}
         self.merge_levels = info.merge_levels
+        self.block_units = info.block_units
         self.sys_ptr = np.asarray(sys_ptr if sys_ptr is not None else [0, n], dtype=np.int64)
 
     def set_trsv(self, mode):

@@ -733,6 +733,38 @@ def test_merged_levels_parity(N, name):
     assert np.linalg.norm(_np(xg) - xo) / np.linalg.norm(xo) <= 1e-8
 
 
+def test_merged_levels_blocked_parity(N):
+    # one system of 2^18 rows: the merged layouts in per-SM row blocks, with
+    # dependencies on earlier blocks published and polled
+    prob = I.fd3d(64, sigma=1.5, corr_len=0.1, seed=6)
+    Ao, (rp, ci, v) = _assemble_both(N, prob)
+    assert Ao.n == 1 << 18
+    P = N.analyse(rp, ci)
+    _merge_or_skip(N, P)
+    assert P.trsv_mode == N.TRSV_LEVELMERGE
+    Lo, _ = O.ic0(Ao)
+    N.factor_load(P, _gpu(Lo.val))
+    r = np.random.default_rng(6).standard_normal(Ao.n)
+    assert _rel(_np(N.sptrsv(P, _gpu(r))), O.trsv_lower(Lo, r)) <= 1e-12
+    assert _rel(_np(N.sptrsv(P, _gpu(r), transpose=True)), O.trsv_upper(Lo, r)) <= 1e-12
+    L32 = O.CSR(Lo.row_ptr, Lo.col_idx, Lo.val.astype(np.float32).astype(np.float64))
+    r32 = r.astype(np.float32).astype(np.float64)
+    for tr, ref in ((False, O.trsv_lower(L32, r32)), (True, O.trsv_upper(L32, r32))):
+        _, y32 = N.sptrsv_timed(P, _gpu(r), transpose=tr, reps=2, f32=True)
+        assert _rel(_np(y32), ref) <= 1e-4
+    b = I.rhs(Ao.n, 9)
+    xo, ito, _, _ = O.pcg(Ao, b, O.PREC_LLT, Lo, rtol=1e-8)
+    for prec in (N.PREC_LLT, N.PREC_LLT32):
+        xg, st = N.pcg_solve(P, v, _gpu(b), prec, _gpu(Lo.val), rtol=1e-8)
+        assert st[0]["status"] == 0
+        if prec == N.PREC_LLT:
+            assert abs(st[0]["iters"] - ito) <= 1
+            assert np.linalg.norm(_np(xg) - xo) / np.linalg.norm(xo) <= 1e-8
+        else:
+            assert abs(st[0]["iters"] - ito) <= max(1, int(np.ceil(0.05 * ito)))
+            assert np.linalg.norm(b - O.spmv(Ao, _np(xg))) / np.linalg.norm(b) <= 2e-8
+
+
 def test_merged_levels_batched_pcg(N):
     probs = [I.fem2d(30, sigma=1.0, seed=41), I.heat2d(26, seed=42), I.fd3d(8, 7, 6, sigma=1.0, seed=43)]
     As, cis, vs, bs = [], [], [], []
