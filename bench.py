@@ -706,6 +706,22 @@ def run_train(args, rank, world, local):
     ms, loss = _timed(step, args.steps, stream, flush)
     clk = clocks.stop()
     ms_per_step = job_ms_per_step(float(np.mean(ms)), world, dev)
+    # the step's dense contractions: per pair one network forward (encoders,
+    # n_mp node and edge MLPs, decoder) and its adjoint (input gradients and
+    # weight gradients: twice the forward), i.e. 3x the forward's flops
+    h, n, nnz = cfg.h, P.n, P.nnz
+    fwd = (2 * n * (h + 2 * h * h) + 2 * nnz * (h + 2 * h * h)
+           + cfg.n_mp * (2 * n * (2 * h * h + 2 * h * h) + 2 * nnz * (3 * h * h + 2 * h * h))
+           + 2 * nnz * (2 * h * h + h))
+    flops = 3.0 * fwd * pairs
+    achieved = flops / (ms_per_step * 1e-3) / 1e12
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
+    roofline = {"kernel": "whole training step (tensor-core MLP forward and adjoint, k_mlp_bf16 / "
+                          "k_mlp_bwd_tc / k_wgrad_tc)", "bound": "tensor", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None, "flops_per_step": flops,
+                "peak_kind": "measured sustained" if peaks else "fallback"}
     if rank == 0:
         line = {"metric": "ms per training step (32 systems x 8 pairs, loss + adjoint + Adam)",
                 "value": ms_per_step, "unit": "ms/step", "n_gpus": world, "steps": args.steps,
@@ -716,7 +732,7 @@ def run_train(args, rank, world, local):
                            "loss": "Eq. loss_A (Frobenius)" if args.loss == "frob" else "Eq. loss_Ab",
                            "parallelism": f"dp{world} (gradient all-reduce)" if world > 1 else "dp1",
                            "gnn": "n_mp=6,l=2,l_mp=2,h=64", "l2": L2_FLUSH},
-                "loss_last": loss, "roofline": None, "cpu_baseline": None, "e2e": None, "clocks": clk}
+                "loss_last": loss, "roofline": roofline, "cpu_baseline": None, "e2e": None, "clocks": clk}
         print(json.dumps(line), flush=True)
 
 

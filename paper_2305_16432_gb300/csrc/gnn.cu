@@ -18,13 +18,26 @@ namespace npcg {
 
 namespace {
 
-// per-system input scales: sc[2s] = s (max diagonal), sc[2s+1] = ||b||_inf
-__global__ void k_scales(const int64_t* sys_ptr, const int32_t* adiag, const double* av,
-                         const double* b, double* sc) {
+// Per-system input scales: sc[2s] = s (max diagonal), sc[2s+1] = ||b||_inf.
+// Every reduction chunk (rows of one system) reduces in a block and folds
+// its maxima into the system's running maxima, kept as unsigned keys whose
+// order is the order of the doubles (so atomicMax is exact and the result
+// does not depend on the order of the chunks); a second kernel decodes them
+// and leaves the keys at zero for the next call.
+__device__ __forceinline__ unsigned long long order_key(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double order_key_inv(unsigned long long k) {
+    return __longlong_as_double((long long)((k >> 63) ? (k & 0x7FFFFFFFFFFFFFFFull) : ~k));
+}
+
+__global__ void k_scales_part(const Chunk* chunks, const int32_t* adiag, const double* av, const double* b,
+                              unsigned long long* keys) {
     __shared__ double m0[256], m1[256];
-    const int s = blockIdx.x;
+    const Chunk c = chunks[blockIdx.x];
     double a = 0.0, bb = 0.0;
-    for (int64_t i = sys_ptr[s] + threadIdx.x; i < sys_ptr[s + 1]; i += blockDim.x) {
+    for (int i = c.row0 + threadIdx.x; i < c.row1; i += blockDim.x) {
         a = fmax(a, av[adiag[i]]);
         if (b) bb = fmax(bb, fabs(b[i]));
     }
@@ -39,10 +52,27 @@ __global__ void k_scales(const int64_t* sys_ptr, const int32_t* adiag, const dou
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        sc[2 * s] = m0[0];
-        sc[2 * s + 1] = m1[0] > 0.0 ? m1[0] : 1.0;
+        atomicMax(&keys[2 * c.sys], order_key(m0[0]));
+        atomicMax(&keys[2 * c.sys + 1], order_key(m1[0]));
     }
 }
+
+__global__ void k_scales_fin(int nsys, unsigned long long* keys, double* sc) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < nsys) {
+        const double a = order_key_inv(keys[2 * s]), bb = order_key_inv(keys[2 * s + 1]);
+        sc[2 * s] = a;
+        sc[2 * s + 1] = bb > 0.0 ? bb : 1.0;
+        keys[2 * s] = 0ull;
+        keys[2 * s + 1] = 0ull;
+    }
+}
+
+}  // namespace
+
+npcg_status gnn_scales_run(Handle* h, Pattern* P, const double* A_val, const double* b, double* sc);
+
+namespace {
 
 __device__ __forceinline__ double softplus_d(double z) { return fmax(z, 0.0) + log1p(exp(-fabs(z))); }
 
@@ -76,8 +106,7 @@ npcg_status run_forward(Handle* h, Pattern* P, const double* A_val, const double
                         const npcg_gnn_config* cfg, const float* w, GnnBuffers& B) {
     const int l = cfg->l, lm = cfg->l_mp;
     const int64_t n = P->n, nnz = P->nnz;
-    k_scales<<<P->nsys, 256, 0, h->stream>>>(P->sys_ptr.p, P->adiag.p, A_val, b, B.sc);
-    NPCG_CUDA(h, cudaGetLastError());
+    NPCG_TRY(gnn_scales_run(h, P, A_val, b, B.sc));
     GnnOffsets off = gnn_offsets(H, l, lm, cfg->n_mp);
     MlpArgs a = {};
     a.rp = P->rp.p;
@@ -153,7 +182,13 @@ npcg_status gnn_forward_into(Handle* h, Pattern* P, const double* A_val, const d
 }
 
 npcg_status gnn_scales_run(Handle* h, Pattern* P, const double* A_val, const double* b, double* sc) {
-    k_scales<<<P->nsys, 256, 0, h->stream>>>(P->sys_ptr.p, P->adiag.p, A_val, b, sc);
+    GnnStore& S = P->gnn;
+    if (S.sckey.n < (size_t)2 * P->nsys) {
+        NPCG_CUDA(h, S.sckey.alloc((size_t)2 * P->nsys));
+        NPCG_CUDA(h, cudaMemsetAsync(S.sckey.p, 0, S.sckey.n * sizeof(unsigned long long), h->stream));
+    }
+    k_scales_part<<<P->nchunks, 256, 0, h->stream>>>(P->chunks.p, P->adiag.p, A_val, b, S.sckey.p);
+    k_scales_fin<<<ceil_div(P->nsys, 128), 128, 0, h->stream>>>(P->nsys, S.sckey.p, sc);
     NPCG_CUDA(h, cudaGetLastError());
     return NPCG_OK;
 }

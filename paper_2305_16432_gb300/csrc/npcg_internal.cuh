@@ -144,6 +144,7 @@ enum TrsvMode : int { kTrsvAuto = 0, kTrsvSyncFree = 1, kTrsvCta = 2 };
 struct GnnStore {
     DevBuf<float> v, e, s;         // node / edge features, decoder outputs
     DevBuf<double> sc;             // per-system input scales
+    DevBuf<unsigned long long> sckey;  // their running maxima as ordered keys (zero between calls)
     DevBuf<float> aux;             // adjoint scratch
     DevBuf<double> dL;             // adjoint of L (loss)
     DevBuf<double> Lv;             // L values of the current pair
