@@ -231,15 +231,33 @@ __global__ void __launch_bounds__(kThreads) k_mlp_bf16(Bf16Args a) {
                     if (c < 8) {
                         val = *reinterpret_cast<const uint4*>(a.vin + i * kH + c * 8);
                     } else {
+                        // sum over the row's edges in ascending order; the
+                        // column indices of up to eight edges, then their
+                        // edge and node chunks, are loaded together, so a row
+                        // costs a few round trips instead of two per edge
                         float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-                        for (int k = a.rp[i]; k < a.rp[i + 1]; ++k) {
-                            const uint4 e4 = *reinterpret_cast<const uint4*>(a.ein + (int64_t)k * kH + (c - 8) * 8);
-                            const uint4 v4 = *reinterpret_cast<const uint4*>(a.vin + (int64_t)a.ci[k] * kH + (c - 8) * 8);
-                            const __nv_bfloat16* e8 = reinterpret_cast<const __nv_bfloat16*>(&e4);
-                            const __nv_bfloat16* v8 = reinterpret_cast<const __nv_bfloat16*>(&v4);
+                        const int k1 = a.rp[i + 1];
+                        for (int kb = a.rp[i]; kb < k1; kb += 8) {
+                            int cj[8];
 #pragma unroll
-                            for (int j = 0; j < 8; ++j)
-                                acc[j] = fmaf(__bfloat162float(e8[j]), __bfloat162float(v8[j]), acc[j]);
+                            for (int q = 0; q < 8; ++q) cj[q] = kb + q < k1 ? a.ci[kb + q] : -1;
+                            uint4 e4[8], v4[8];
+#pragma unroll
+                            for (int q = 0; q < 8; ++q) {
+                                if (cj[q] >= 0) {
+                                    e4[q] = *reinterpret_cast<const uint4*>(a.ein + (int64_t)(kb + q) * kH + (c - 8) * 8);
+                                    v4[q] = *reinterpret_cast<const uint4*>(a.vin + (int64_t)cj[q] * kH + (c - 8) * 8);
+                                }
+                            }
+#pragma unroll
+                            for (int q = 0; q < 8; ++q) {
+                                if (cj[q] < 0) break;
+                                const __nv_bfloat16* e8 = reinterpret_cast<const __nv_bfloat16*>(&e4[q]);
+                                const __nv_bfloat16* v8 = reinterpret_cast<const __nv_bfloat16*>(&v4[q]);
+#pragma unroll
+                                for (int j = 0; j < 8; ++j)
+                                    acc[j] = fmaf(__bfloat162float(e8[j]), __bfloat162float(v8[j]), acc[j]);
+                            }
                         }
                         __nv_bfloat16 h8[8];
 #pragma unroll
