@@ -348,7 +348,7 @@ npcg_status merge_build(Handle* h, Pattern* P, int G);
 npcg_status merge_sptrsv(Handle* h, cudaStream_t s, Pattern* P, int transpose, const double* r, double* y, bool f32,
                          cudaEvent_t e0, cudaEvent_t e1);
 npcg_status merge_factor_load(Handle* h, Pattern* P, const double* L_val);
-void merge_apply(Handle* h, cudaStream_t s, Pattern* P, bool f32);
+npcg_status merge_apply(Handle* h, cudaStream_t s, Pattern* P, bool f32);
 npcg_status gnn_forward_run(Handle* h, Pattern* P, const double* A_val, const double* b,
                             const npcg_gnn_config* cfg, const float* w, double* L_val);
 npcg_status loss_grad_run(Handle* h, Pattern* P, const double* A_val, int npairs,

@@ -610,40 +610,39 @@ PcgArgs pcg_args(Pattern* P, int precond) {
 }
 
 // z = L^-T L^-1 r with the tuned triangular-solve design
-void apply_llt(Handle* h, cudaStream_t s, Pattern* P, bool batched, bool f32) {
-    if (P->trsv_mode == kTrsvCta && P->cta_merge) {
-        merge_apply(h, s, P, f32);
-        return;
-    }
+npcg_status apply_llt(Handle* h, cudaStream_t s, Pattern* P, bool batched, bool f32) {
+    if (P->trsv_mode == kTrsvCta && P->cta_merge) return merge_apply(h, s, P, f32);
     if (P->trsv_mode == kTrsvCta) {
         if (P->cfwd.blocked) {
             // row blocks publish to y and z (natural order; the update kernel
             // resets them to the sentinel and the tickets to zero every iteration)
-            cta_trsv_launch(h, s, P, P->cfwd, P->r_cf.p, P->yq.p, P->st.p, f32, P->ctl.p + 2, P->y.p);
-            cta_permute(h, s, P, P->cfwd, P->yq.p, f32, P->cbwd.other.p, P->y_cb.p, f32);
-            cta_trsv_launch(h, s, P, P->cbwd, P->y_cb.p, P->yq.p, P->st.p, f32, P->ctl.p + 3, P->z.p);
-        } else {
-            cta_trsv_launch(h, s, P, P->cfwd, P->r_cf.p, P->yq.p, P->st.p, f32);
-            cta_permute(h, s, P, P->cfwd, P->yq.p, f32, P->cbwd.other.p, P->y_cb.p, f32);
-            cta_trsv_launch(h, s, P, P->cbwd, P->y_cb.p, P->yq.p, P->st.p, f32);
-            cta_permute(h, s, P, P->cbwd, P->yq.p, f32, P->cbwd.cpos.p, P->z.p, false);
+            NPCG_TRY(cta_trsv_launch(h, s, P, P->cfwd, P->r_cf.p, P->yq.p, P->st.p, f32, P->ctl.p + 2, P->y.p));
+            NPCG_TRY(cta_permute(h, s, P, P->cfwd, P->yq.p, f32, P->cbwd.other.p, P->y_cb.p, f32));
+            return cta_trsv_launch(h, s, P, P->cbwd, P->y_cb.p, P->yq.p, P->st.p, f32, P->ctl.p + 3, P->z.p);
         }
-    } else {
-        launch_trsv(h, s, P, 0, P->r.p, P->y.p, P->ctl.p + 2, batched, P->st.p, f32);
-        launch_trsv(h, s, P, 1, P->y.p, P->z.p, P->ctl.p + 3, batched, P->st.p, f32);
+        NPCG_TRY(cta_trsv_launch(h, s, P, P->cfwd, P->r_cf.p, P->yq.p, P->st.p, f32));
+        NPCG_TRY(cta_permute(h, s, P, P->cfwd, P->yq.p, f32, P->cbwd.other.p, P->y_cb.p, f32));
+        NPCG_TRY(cta_trsv_launch(h, s, P, P->cbwd, P->y_cb.p, P->yq.p, P->st.p, f32));
+        return cta_permute(h, s, P, P->cbwd, P->yq.p, f32, P->cbwd.cpos.p, P->z.p, false);
     }
+    launch_trsv(h, s, P, 0, P->r.p, P->y.p, P->ctl.p + 2, batched, P->st.p, f32);
+    launch_trsv(h, s, P, 1, P->y.p, P->z.p, P->ctl.p + 3, batched, P->st.p, f32);
+    NPCG_CUDA(h, cudaGetLastError());
+    return NPCG_OK;
 }
 
 // one PCG iteration (Algorithm 1 loop body) on the stream
-void enqueue_iteration(Handle* h, cudaStream_t s, Pattern* P, const PcgArgs& a, const double* p_old,
-                       double* p_new) {
+npcg_status enqueue_iteration(Handle* h, cudaStream_t s, Pattern* P, const PcgArgs& a, const double* p_old,
+                              double* p_new) {
     const bool batched = P->nsys > 1;
     k_spmv_p<<<P->nchunks, kChunkThreads, 0, s>>>(a, p_old, p_new);
     k_update<<<P->nchunks, kChunkThreads, 0, s>>>(a, p_new);
     if (a.precond >= NPCG_PREC_LLT) {
-        apply_llt(h, s, P, batched, a.precond == NPCG_PREC_LLT32);
+        NPCG_TRY(apply_llt(h, s, P, batched, a.precond == NPCG_PREC_LLT32));
         k_dot_rz<<<P->nchunks, kChunkThreads, 0, s>>>(a, 0);
     }
+    NPCG_CUDA(h, cudaGetLastError());
+    return NPCG_OK;
 }
 
 npcg_status build_graph(Handle* h, Pattern* P, int precond) {
@@ -673,11 +672,17 @@ npcg_status build_graph(Handle* h, Pattern* P, int precond) {
     e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) { cudaGraphDestroy(g); return cuda_fail(h, e, "cudaStreamBeginCaptureToGraph"); }
     // two iterations per trip so the p ping-pong is static
-    enqueue_iteration(h, cs, P, a, P->p0.p, P->p1.p);
-    enqueue_iteration(h, cs, P, a, P->p1.p, P->p0.p);
-    k_set_cond<<<1, 32, 0, cs>>>(hd, P->ctl.p);
+    npcg_status st = enqueue_iteration(h, cs, P, a, P->p0.p, P->p1.p);
+    if (st == NPCG_OK) st = enqueue_iteration(h, cs, P, a, P->p1.p, P->p0.p);
+    if (st == NPCG_OK) k_set_cond<<<1, 32, 0, cs>>>(hd, P->ctl.p);
     cudaGraph_t captured = nullptr;
     e = cudaStreamEndCapture(cs, &captured);
+    if (st != NPCG_OK) {
+        // a refused layout or a failed launch inside the capture: the status
+        // and its message are already recorded on the handle
+        cudaGraphDestroy(g);
+        return st;
+    }
     if (e != cudaSuccess) { cudaGraphDestroy(g); return cuda_fail(h, e, "cudaStreamEndCapture"); }
     cudaGraphExec_t ex = nullptr;
     e = cudaGraphInstantiate(&ex, g, 0);
@@ -956,9 +961,7 @@ npcg_status pcg_run(Handle* h, Pattern* P, const double* A_val, const double* b,
     }
     PcgArgs a = pcg_args(P, precond);
     k_init<<<P->nchunks, kChunkThreads, 0, h->stream>>>(a, rtol, max_iter, P->p0.p, P->p1.p, stall_k);
-    if (precond >= NPCG_PREC_LLT) {
-        apply_llt(h, h->stream, P, P->nsys > 1, precond == NPCG_PREC_LLT32);
-    }
+    if (precond >= NPCG_PREC_LLT) NPCG_TRY(apply_llt(h, h->stream, P, P->nsys > 1, precond == NPCG_PREC_LLT32));
     k_dot_rz<<<P->nchunks, kChunkThreads, 0, h->stream>>>(a, 1);
     NPCG_CUDA(h, cudaGetLastError());
     NPCG_TRY(build_graph(h, P, precond));

@@ -193,7 +193,7 @@ npcg_status merge_factor_load(Handle* h, Pattern* P, const double* L_val) {
 }
 
 // z = L^-T L^-1 r through the merged layouts (r natural order, z natural)
-void merge_apply(Handle* h, cudaStream_t s, Pattern* P, bool f32) {
+npcg_status merge_apply(Handle* h, cudaStream_t s, Pattern* P, bool f32) {
     const int64_t n = P->n;
     const int blocks = std::max(1, std::min(ceil_div(n, 256), h->num_sms * 8));
     const MergeDir& F = P->mfwd;
@@ -206,38 +206,38 @@ void merge_apply(Handle* h, cudaStream_t s, Pattern* P, bool f32) {
         if (f32) {
             k_merge_rhs<double, float><<<blocks, 256, 0, s>>>(n, F.lay.cperm.p, F.crp.p, F.ccol.p, F.C.p, P->r.p,
                                                               reinterpret_cast<float*>(P->r_cf.p));
-            cta_trsv_launch(h, s, P, F.lay, P->r_cf.p, P->yq.p, P->st.p, true, P->ctl.p + 2, P->y.p);
+            NPCG_TRY(cta_trsv_launch(h, s, P, F.lay, P->r_cf.p, P->yq.p, P->st.p, true, P->ctl.p + 2, P->y.p));
             k_merge_rhs<double, float><<<blocks, 256, 0, s>>>(n, B.lay.cperm.p, B.crp.p, B.ccol.p, B.C.p, P->y.p,
                                                               reinterpret_cast<float*>(P->y_cb.p));
-            cta_trsv_launch(h, s, P, B.lay, P->y_cb.p, P->yq.p, P->st.p, true, P->ctl.p + 3, P->z.p);
+            NPCG_TRY(cta_trsv_launch(h, s, P, B.lay, P->y_cb.p, P->yq.p, P->st.p, true, P->ctl.p + 3, P->z.p));
         } else {
             k_merge_rhs<double, double><<<blocks, 256, 0, s>>>(n, F.lay.cperm.p, F.crp.p, F.ccol.p, F.C.p, P->r.p,
                                                                reinterpret_cast<double*>(P->r_cf.p));
-            cta_trsv_launch(h, s, P, F.lay, P->r_cf.p, P->yq.p, P->st.p, false, P->ctl.p + 2, P->y.p);
+            NPCG_TRY(cta_trsv_launch(h, s, P, F.lay, P->r_cf.p, P->yq.p, P->st.p, false, P->ctl.p + 2, P->y.p));
             k_merge_rhs<double, double><<<blocks, 256, 0, s>>>(n, B.lay.cperm.p, B.crp.p, B.ccol.p, B.C.p, P->y.p,
                                                                reinterpret_cast<double*>(P->y_cb.p));
-            cta_trsv_launch(h, s, P, B.lay, P->y_cb.p, P->yq.p, P->st.p, false, P->ctl.p + 3, P->z.p);
+            NPCG_TRY(cta_trsv_launch(h, s, P, B.lay, P->y_cb.p, P->yq.p, P->st.p, false, P->ctl.p + 3, P->z.p));
         }
-        return;
+        return NPCG_OK;
     }
     if (f32) {
         k_merge_rhs<double, float><<<blocks, 256, 0, s>>>(n, F.lay.cperm.p, F.crp.p, F.ccol.p, F.C.p, P->r.p,
                                                           reinterpret_cast<float*>(P->r_cf.p));
-        cta_trsv_launch(h, s, P, F.lay, P->r_cf.p, P->yq.p, P->st.p, true);
+        NPCG_TRY(cta_trsv_launch(h, s, P, F.lay, P->r_cf.p, P->yq.p, P->st.p, true));
         k_merge_rhs<float, float><<<blocks, 256, 0, s>>>(n, B.lay.cperm.p, B.crp.p, B.ccolpos.p, B.C.p,
                                                          reinterpret_cast<const float*>(P->yq.p),
                                                          reinterpret_cast<float*>(P->y_cb.p));
-        cta_trsv_launch(h, s, P, B.lay, P->y_cb.p, P->yq.p, P->st.p, true);
+        NPCG_TRY(cta_trsv_launch(h, s, P, B.lay, P->y_cb.p, P->yq.p, P->st.p, true));
     } else {
         k_merge_rhs<double, double><<<blocks, 256, 0, s>>>(n, F.lay.cperm.p, F.crp.p, F.ccol.p, F.C.p, P->r.p,
                                                            reinterpret_cast<double*>(P->r_cf.p));
-        cta_trsv_launch(h, s, P, F.lay, P->r_cf.p, P->yq.p, P->st.p, false);
+        NPCG_TRY(cta_trsv_launch(h, s, P, F.lay, P->r_cf.p, P->yq.p, P->st.p, false));
         k_merge_rhs<double, double><<<blocks, 256, 0, s>>>(n, B.lay.cperm.p, B.crp.p, B.ccolpos.p, B.C.p,
                                                            reinterpret_cast<const double*>(P->yq.p),
                                                            reinterpret_cast<double*>(P->y_cb.p));
-        cta_trsv_launch(h, s, P, B.lay, P->y_cb.p, P->yq.p, P->st.p, false);
+        NPCG_TRY(cta_trsv_launch(h, s, P, B.lay, P->y_cb.p, P->yq.p, P->st.p, false));
     }
-    cta_permute(h, s, P, B.lay, P->yq.p, f32, B.lay.cpos.p, P->z.p, false);
+    return cta_permute(h, s, P, B.lay, P->yq.p, f32, B.lay.cpos.p, P->z.p, false);
 }
 
 // One direction alone (L y = r, or L^T y = r with transpose): natural-order

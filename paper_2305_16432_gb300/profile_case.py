@@ -11,7 +11,9 @@ of a case that is larger than L2 but holds only a few GB on the device:
 Cases: gnn (BF16 network forward with the 3-D task network: encoders, the
 message-passing node and edge MLPs, the decoder), trsv (forward triangular
 solve of the tuned design, FP32), spmv (y = A x), ic0 (IC(0) factorisation),
-pcg (learned-factor PCG to 1e-6).  Prints the CUDA-event time per repetition.
+pcg (learned-factor PCG to 1e-6).  Prints the CUDA-event time per repetition;
+--profile-range limits a profiler started with --profile-from-start off to
+the timed repetitions.
 """
 from __future__ import annotations
 
@@ -33,6 +35,9 @@ def main():
     ap.add_argument("--grid", type=int, default=64)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=2)
+    ap.add_argument("--profile-range", action="store_true",
+                    help="bracket the timed repetitions with cudaProfilerStart/Stop (for a profiler started "
+                         "with --profile-from-start off)")
     args = ap.parse_args()
     from . import build as B
     B.build()
@@ -67,6 +72,8 @@ def main():
     for _ in range(args.warmup):
         op()
     torch.cuda.synchronize()
+    if args.profile_range:
+        torch.cuda.cudart().cudaProfilerStart()
     times = []
     for _ in range(args.reps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -75,6 +82,8 @@ def main():
         e1.record()
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
+    if args.profile_range:
+        torch.cuda.cudart().cudaProfilerStop()
     print(json.dumps({"case": args.case, "grid": side, "n": P.n, "nnz": P.nnz, "nnz_L": P.nnz_L,
                       "trsv_mode": P.trsv_mode, "block_units": P.block_units, "merge_levels": P.merge_levels,
                       "tuned_ms": P.tuned_ms, "ms": times}))
