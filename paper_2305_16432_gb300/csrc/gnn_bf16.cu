@@ -223,54 +223,59 @@ __global__ void __launch_bounds__(kThreads) k_mlp_bf16(Bf16Args a) {
                 *reinterpret_cast<uint4*>(A0 + swz(tid, c * 8)) = *reinterpret_cast<uint4*>(h8);
             }
         } else if (MODE == MODE_NODE) {
-            for (int idx = tid; idx < kM * 16; idx += kThreads) {
-                const int r = idx >> 4, c = idx & 15;
+            // v_i: eight threads per row, one 16-byte chunk each
+            for (int idx = tid; idx < kM * 8; idx += kThreads) {
+                const int r = idx >> 3, c = idx & 7;
+                const int64_t i = row0 + r;
+                uint4 val = make_uint4(0, 0, 0, 0);
+                if (i < a.nrows) val = *reinterpret_cast<const uint4*>(a.vin + i * kH + c * 8);
+                *reinterpret_cast<uint4*>(A0 + swz(r, c * 8)) = val;
+            }
+            // sum_j e_ij (.) v_j over the row's edges in ascending order,
+            // eight threads per row (one chunk each, so that the edge and node
+            // rows are read as whole lines); the column indices of up to eight
+            // edges, then their edge and node chunks, are loaded together, so
+            // a row costs a few round trips instead of two per edge
+            for (int idx = tid; idx < kM * 8; idx += kThreads) {
+                const int r = idx >> 3, c = idx & 7;
                 const int64_t i = row0 + r;
                 uint4 val = make_uint4(0, 0, 0, 0);
                 if (i < a.nrows) {
-                    if (c < 8) {
-                        val = *reinterpret_cast<const uint4*>(a.vin + i * kH + c * 8);
-                    } else {
-                        // sum over the row's edges in ascending order; the
-                        // column indices of up to eight edges, then their
-                        // edge and node chunks, are loaded together, so a row
-                        // costs a few round trips instead of two per edge
-                        float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-                        const int k1 = a.rp[i + 1];
-                        for (int kb = a.rp[i]; kb < k1; kb += 8) {
-                            int cj[8];
+                    float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                    const int k1 = a.rp[i + 1];
+                    for (int kb = a.rp[i]; kb < k1; kb += 8) {
+                        int cj[8];
 #pragma unroll
-                            for (int q = 0; q < 8; ++q) cj[q] = kb + q < k1 ? a.ci[kb + q] : -1;
-                            uint4 e4[8], v4[8];
+                        for (int q = 0; q < 8; ++q) cj[q] = kb + q < k1 ? a.ci[kb + q] : -1;
+                        uint4 e4[8], v4[8];
 #pragma unroll
-                            for (int q = 0; q < 8; ++q) {
-                                if (cj[q] >= 0) {
-                                    e4[q] = *reinterpret_cast<const uint4*>(a.ein + (int64_t)(kb + q) * kH + (c - 8) * 8);
-                                    v4[q] = *reinterpret_cast<const uint4*>(a.vin + (int64_t)cj[q] * kH + (c - 8) * 8);
-                                }
-                            }
-#pragma unroll
-                            for (int q = 0; q < 8; ++q) {
-                                if (cj[q] < 0) break;
-                                const __nv_bfloat16* e8 = reinterpret_cast<const __nv_bfloat16*>(&e4[q]);
-                                const __nv_bfloat16* v8 = reinterpret_cast<const __nv_bfloat16*>(&v4[q]);
-#pragma unroll
-                                for (int j = 0; j < 8; ++j)
-                                    acc[j] = fmaf(__bfloat162float(e8[j]), __bfloat162float(v8[j]), acc[j]);
+                        for (int q = 0; q < 8; ++q) {
+                            if (cj[q] >= 0) {
+                                e4[q] = *reinterpret_cast<const uint4*>(a.ein + (int64_t)(kb + q) * kH + c * 8);
+                                v4[q] = *reinterpret_cast<const uint4*>(a.vin + (int64_t)cj[q] * kH + c * 8);
                             }
                         }
-                        __nv_bfloat16 h8[8];
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) h8[j] = __float2bfloat16_rn(acc[j]);
-                        val = *reinterpret_cast<uint4*>(h8);
-                        if (a.agg32) {
-                            float4* g = reinterpret_cast<float4*>(a.agg32 + i * kH + (c - 8) * 8);
-                            g[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
-                            g[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+                        for (int q = 0; q < 8; ++q) {
+                            if (cj[q] < 0) break;
+                            const __nv_bfloat16* e8 = reinterpret_cast<const __nv_bfloat16*>(&e4[q]);
+                            const __nv_bfloat16* v8 = reinterpret_cast<const __nv_bfloat16*>(&v4[q]);
+#pragma unroll
+                            for (int j = 0; j < 8; ++j)
+                                acc[j] = fmaf(__bfloat162float(e8[j]), __bfloat162float(v8[j]), acc[j]);
                         }
                     }
+                    __nv_bfloat16 h8[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) h8[j] = __float2bfloat16_rn(acc[j]);
+                    val = *reinterpret_cast<uint4*>(h8);
+                    if (a.agg32) {
+                        float4* g = reinterpret_cast<float4*>(a.agg32 + i * kH + c * 8);
+                        g[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+                        g[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+                    }
                 }
-                *reinterpret_cast<uint4*>(A0 + (uint32_t)(c >> 3) * (kM * 128) + swz(r, (c & 7) * 8)) = val;
+                *reinterpret_cast<uint4*>(A0 + kM * 128 + swz(r, c * 8)) = val;
             }
         } else {      // EDGE: [e | v_row | v_col], DEC: [e]
             constexpr int CH = IN >= 8 ? IN / 8 : 1;     // (encoders never reach here)
@@ -352,15 +357,25 @@ __global__ void __launch_bounds__(kThreads) k_mlp_bf16(Bf16Args a) {
                 for (int o = 0; o < kH; ++o) s = fmaf(s_w0[o], fmaxf(v[o] + bl[o], 0.0f), s);
                 if (row < a.nrows) a.sout[row] = s;
             } else {
-                // last layer: BF16 feature row to global memory
+                // last layer: BF16 feature rows to global memory through A1
+                // (its last reader, this layer's product, has completed), so
+                // that the global stores are whole lines
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    __nv_bfloat16 h8[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) h8[j] = __float2bfloat16_rn(v[c * 8 + j] + bl[c * 8 + j]);
+                    *reinterpret_cast<uint4*>(A1 + swz(tid, c * 8)) = *reinterpret_cast<uint4*>(h8);
+                }
+                __syncthreads();
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int rr = i * 16 + (tid >> 3), cc = tid & 7;
+                    if (row0 + rr < a.nrows)
+                        *reinterpret_cast<uint4*>(a.out + (row0 + rr) * kH + cc * 8) =
+                            *reinterpret_cast<const uint4*>(A1 + swz(rr, cc * 8));
+                }
                 if (row < a.nrows) {
-#pragma unroll
-                    for (int c = 0; c < 8; ++c) {
-                        __nv_bfloat16 h8[8];
-#pragma unroll
-                        for (int j = 0; j < 8; ++j) h8[j] = __float2bfloat16_rn(v[c * 8 + j] + bl[c * 8 + j]);
-                        *reinterpret_cast<uint4*>(a.out + row * kH + c * 8) = *reinterpret_cast<uint4*>(h8);
-                    }
                     if (a.out32) {
                         float4* o = reinterpret_cast<float4*>(a.out32 + row * kH);
 #pragma unroll
@@ -539,17 +554,22 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_mlp_bf16_ws(Bf16Args a) {
             int crow[4], ccol[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) { crow[q] = nrow[q]; ccol[q] = ncol[q]; }
+            // eight lanes per 128-byte row segment, four rows per instruction:
+            // every copy instruction reads whole lines (lane l of the warp
+            // holds the indices of rows l, l + 32, l + 64, l + 96)
+            const int rsub = lane >> 3, cc = lane & 7;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int r = lane + 32 * q;
+            for (int i = 0; i < kM / 4; ++i) {
+                const int r = 4 * i + rsub;
                 const int64_t k = tile * kM + r;
                 const bool in = k < a.nrows;
+                const int jr = __shfl_sync(0xffffffffu, crow[i >> 3], r & 31);
+                const int jc = __shfl_sync(0xffffffffu, ccol[i >> 3], r & 31);
 #pragma unroll
-                for (int c = 0; c < CH; ++c) {
-                    const int seg = c >> 3, cc = c & 7;
+                for (int seg = 0; seg < NKB; ++seg) {
                     const __nv_bfloat16* src = seg == 0 ? a.ein + (in ? k : 0) * kH
-                                             : seg == 1 ? a.vin + (int64_t)crow[q] * kH
-                                                        : a.vin + (int64_t)ccol[q] * kH;
+                                             : seg == 1 ? a.vin + (int64_t)jr * kH
+                                                        : a.vin + (int64_t)jc * kH;
                     cp_async16(s_addr(dst + (uint32_t)seg * (kM * 128) + swz(r, cc * 8)), src + cc * 8, in ? 16u : 0u);
                 }
             }
@@ -626,14 +646,26 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_mlp_bf16_ws(Bf16Args a) {
                     for (int o = 0; o < kH; ++o) sacc = fmaf(s_out[o], fmaxf(v[o] + bl[o], 0.0f), sacc);
                     if (row < a.nrows) a.sout[row] = sacc;
                 } else {
+                    // the output row goes through the warpgroup's operand
+                    // buffer (its last reader, this layer's product, has
+                    // completed), so that the global stores are whole lines
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        __nv_bfloat16 h8[8];
+#pragma unroll
+                        for (int jj = 0; jj < 8; ++jj) h8[jj] = __float2bfloat16_rn(v[c * 8 + jj] + bl[c * 8 + jj]);
+                        *reinterpret_cast<uint4*>(A1g + swz(r, c * 8)) = *reinterpret_cast<uint4*>(h8);
+                    }
+                    asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(kM) : "memory");
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const int rr = i * 16 + (r >> 3), cc = r & 7;
+                        const int64_t orow = tile * kM + rr;
+                        if (orow < a.nrows)
+                            *reinterpret_cast<uint4*>(a.out + orow * kH + cc * 8) =
+                                *reinterpret_cast<const uint4*>(A1g + swz(rr, cc * 8));
+                    }
                     if (row < a.nrows) {
-#pragma unroll
-                        for (int c = 0; c < 8; ++c) {
-                            __nv_bfloat16 h8[8];
-#pragma unroll
-                            for (int jj = 0; jj < 8; ++jj) h8[jj] = __float2bfloat16_rn(v[c * 8 + jj] + bl[c * 8 + jj]);
-                            *reinterpret_cast<uint4*>(a.out + row * kH + c * 8) = *reinterpret_cast<uint4*>(h8);
-                        }
                         if (a.out32) {
                             float4* o = reinterpret_cast<float4*>(a.out32 + row * kH);
 #pragma unroll
