@@ -67,8 +67,12 @@ __host__ __device__ inline SmemPlan plan(int mode, int depth) {
     SmemPlan p;
     p.a0 = 0;                                         // [128 x kin0] operand (kin0 / 64 K-blocks)
     p.a0b = p.a0;                                     // (single operand buffer)
-    p.a1 = p.a0 + a0bytes;                            // [128 x 64] hidden operand
-    p.w = p.a1 + kM * 128;
+    // [128 x 64] hidden operand.  Every layer's product has completed before
+    // its epilogue writes the next operand, so without the async gather (which
+    // refills A0 for the next tile after the first layer) the hidden operand
+    // reuses A0's first K-block: less shared memory, more CTAs per SM
+    p.a1 = async_gather(mode) ? p.a0 + a0bytes : p.a0;
+    p.w = p.a0 + a0bytes + (async_gather(mode) ? kM * 128 : 0);
     p.bias = p.w + wbytes;                            // FP32 biases of every layer + scalar layer weights
     p.idx = p.bias + (uint32_t)(depth + 1) * kH * 4 + 2 * kH * 4 + 64;
     p.idx = (p.idx + 15) & ~15u;                      // async gather: [2 tiles][row, col][128] indices
@@ -391,6 +395,10 @@ __global__ void __launch_bounds__(kThreads) k_mlp_bf16(Bf16Args a) {
             // issued one tile ago; it now receives the tile after next
             sidx[(it & 1) * 2 * kM + tid] = nidx.x;
             sidx[(it & 1) * 2 * kM + kM + tid] = nidx.y;
+            __syncthreads();
+        } else {
+            // the output tile staged in A0 is read out before the next tile's
+            // operand is written there
             __syncthreads();
         }
     }
