@@ -290,7 +290,7 @@ npcg_status launch_bwd(Handle* h, int mode, const MlpBwdArgs& a) {
 // staged once per CTA: B[i][o] = W_l[o][i] (K = o).  The node update reads
 // its aggregation from the forward's tape.
 struct BtPlan {
-    uint32_t a0, ah, g, wf, wb, bias, misc, total;
+    uint32_t a0, ah, g, wf, wb, bias, misc, st, total;
 };
 __host__ __device__ inline BtPlan bt_plan(int in, int depth, bool dec) {
     BtPlan p;
@@ -304,7 +304,10 @@ __host__ __device__ inline BtPlan bt_plan(int in, int depth, bool dec) {
     // backward W_l^T: l = 0 (in/64 blocks), 1..depth-1, depth (unless scalar)
     p.bias = p.wb + (uint32_t)(in / 64) * wblk + (uint32_t)(depth - 1 + (dec ? 0 : 1)) * wblk;
     p.misc = p.bias + (uint32_t)(depth + 1) * kH * 4;
-    p.total = p.misc + 64;
+    // FP32 staging of half a tile (128 rows x 32 columns): rows move between
+    // registers and global memory through it as whole lines
+    p.st = (p.misc + 64 + 127) & ~127u;
+    p.total = p.st + kM * 32 * 4;
     return p;
 }
 
@@ -415,10 +418,50 @@ __global__ void __launch_bounds__(kThreads) k_mlp_bwd_tc(MlpBwdArgs a, const flo
             *reinterpret_cast<uint4*>(Op + swz(tid, c * 8)) = *reinterpret_cast<uint4*>(h2);
         }
     };
-    auto store_row = [&](float* dst, int64_t row, const float (&v)[64]) {
-        float4* o = reinterpret_cast<float4*>(dst + row * kH);
+    // Rows of the tile (row0 + tid) to / from global memory through the
+    // staging buffer, 32 columns at a time: thread tid owns row tid in
+    // registers; in the staging buffer 16-byte chunk c of row r sits at
+    // c ^ (r & 7) (no bank conflicts either way), and the global side moves
+    // four rows' 128-byte halves per warp instruction.  Every thread of the
+    // CTA calls these.
+    float4* stg = reinterpret_cast<float4*>(sm + P.st);
+    auto store_rows = [&](float* dst, int64_t row0, const float (&v)[64]) {
 #pragma unroll
-        for (int c = 0; c < 16; ++c) o[c] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+        for (int h = 0; h < 2; ++h) {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const int o = h * 32 + c * 4;
+                stg[tid * 8 + (c ^ (tid & 7))] = make_float4(v[o], v[o + 1], v[o + 2], v[o + 3]);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int idx = i * kThreads + tid, rr = idx >> 3, cc = idx & 7;
+                if (row0 + rr < a.f.nrows)
+                    reinterpret_cast<float4*>(dst + (row0 + rr) * kH + h * 32)[cc] = stg[rr * 8 + (cc ^ (rr & 7))];
+            }
+            __syncthreads();
+        }
+    };
+    auto load_rows = [&](const float* src, int64_t row0, float (&v)[64]) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int idx = i * kThreads + tid, rr = idx >> 3, cc = idx & 7;
+                stg[rr * 8 + (cc ^ (rr & 7))] =
+                    row0 + rr < a.f.nrows ? reinterpret_cast<const float4*>(src + (row0 + rr) * kH + h * 32)[cc]
+                                          : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const float4 q = stg[tid * 8 + (c ^ (tid & 7))];
+                const int o = h * 32 + c * 4;
+                v[o] = q.x; v[o + 1] = q.y; v[o + 2] = q.z; v[o + 3] = q.w;
+            }
+            __syncthreads();
+        }
     };
 
     const int64_t ntiles = (a.f.nrows + kM - 1) / kM;
@@ -464,7 +507,7 @@ __global__ void __launch_bounds__(kThreads) k_mlp_bwd_tc(MlpBwdArgs a, const flo
             }
             mask[l + 1] = m;
             put_row(Ah + (uint32_t)l * blk, v);
-            if (live) store_row(a.tapeA[l + 1], row, v);
+            store_rows(a.tapeA[l + 1], row0, v);
         }
         if (!ok) break;
         // ---- G_{depth-1}
@@ -475,17 +518,7 @@ __global__ void __launch_bounds__(kThreads) k_mlp_bwd_tc(MlpBwdArgs a, const flo
 #pragma unroll
                 for (int i = 0; i < 64; ++i) v[i] = g * bias[depth * kH + i];
             } else {
-                if (live) {
-                    const float4* gp = reinterpret_cast<const float4*>(a.gout + row * kH);
-#pragma unroll
-                    for (int c = 0; c < 16; ++c) {
-                        const float4 q = gp[c];
-                        v[4 * c] = q.x; v[4 * c + 1] = q.y; v[4 * c + 2] = q.z; v[4 * c + 3] = q.w;
-                    }
-                } else {
-#pragma unroll
-                    for (int i = 0; i < 64; ++i) v[i] = 0.0f;
-                }
+                load_rows(a.gout, row0, v);
                 put_row(Gop, v);
                 const unsigned char* Bop = Wb + (uint32_t)NKB * wblk + (uint32_t)(depth - 1) * wblk;
                 if (!mma_wait(Gop, Bop, 1)) { ok = false; break; }
@@ -495,7 +528,7 @@ __global__ void __launch_bounds__(kThreads) k_mlp_bwd_tc(MlpBwdArgs a, const flo
 #pragma unroll
             for (int i = 0; i < 64; ++i) v[i] = (m >> i) & 1 ? v[i] : 0.0f;
             put_row(Gop, v);
-            if (live) store_row(a.tapeG[depth - 1], row, v);
+            store_rows(a.tapeG[depth - 1], row0, v);
         }
         // ---- G_{l-1} = (G_l W_l) (.) [A_l > 0], l = depth-1 .. 1
         for (int l = depth - 1; l >= 1 && ok; --l) {
@@ -507,7 +540,7 @@ __global__ void __launch_bounds__(kThreads) k_mlp_bwd_tc(MlpBwdArgs a, const flo
 #pragma unroll
             for (int i = 0; i < 64; ++i) v[i] = (m >> i) & 1 ? v[i] : 0.0f;
             put_row(Gop, v);
-            if (live) store_row(a.tapeG[l - 1], row, v);
+            store_rows(a.tapeG[l - 1], row0, v);
         }
         if (!ok) break;
         // ---- input gradient G_0 W_0, one 64-wide segment per product
@@ -515,7 +548,7 @@ __global__ void __launch_bounds__(kThreads) k_mlp_bwd_tc(MlpBwdArgs a, const flo
             if (!mma_wait(Gop, Wb + (uint32_t)s * wblk, 1)) { ok = false; break; }
             float v[64];
             ld64(v);
-            if (live && a.dx[s]) store_row(a.dx[s], row, v);
+            if (a.dx[s]) store_rows(a.dx[s], row0, v);
         }
     }
     if (!ok) {

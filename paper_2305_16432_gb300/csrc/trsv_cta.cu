@@ -299,6 +299,26 @@ __global__ void __launch_bounds__(kCtaThreads, 1) k_trsv_cta(CtaDev D, const T* 
         // overlaps the bookkeeping and the next step's operand loads (the
         // warp issues in order)
         T yw0 = (T)0, yw1 = (T)0, yw2 = (T)0, yw3 = (T)0;
+        // row blocks: the step's remote values (published by earlier blocks)
+        // and local ones (window, or the global solution) are all requested
+        // here, so the L2 round trip of the remote ones overlaps the
+        // bookkeeping below; a remote value not yet published is polled for
+        // when it is used
+        unsigned long long rq[4] = {0ull, 0ull, 0ull, 0ull};
+        T yl[4] = {(T)0, (T)0, (T)0, (T)0};
+        if (kRemote && t < cur.nrows) {
+            const int pd[4] = {cur.dep.x, cur.dep.y, cur.dep.z, cur.dep.w};
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                if (pd[kk] <= -2) {
+                    rq[kk] = ld_relaxed_u64(pub + (-pd[kk] - 2));
+                } else if (kWindow) {
+                    yl[kk] = win[pd[kk]];
+                } else if (pd[kk] >= 0) {
+                    yl[kk] = (T)__ldcg(yglob + pd[kk]);
+                }
+            }
+        }
         if (kWindow && !kRemote && t < cur.nrows) {
             if (kFar) {
                 yw0 = cur.dep.x >= 0 ? win[cur.dep.x] : __ldcg(outq + (-cur.dep.x - 2));
@@ -350,22 +370,15 @@ __global__ void __launch_bounds__(kCtaThreads, 1) k_trsv_cta(CtaDev D, const T* 
                 acc = fma(-cur.l[3], yw3, acc);
             } else {
                 const int pd[4] = {cur.dep.x, cur.dep.y, cur.dep.z, cur.dep.w};
-                // remote values: every load is issued before any is waited
-                // for, so a row with several remote dependencies pays one
-                // round trip, not one per dependency
-                unsigned long long rb[4] = {0ull, 0ull, 0ull, 0ull};
-                if (kRemote) {
-#pragma unroll
-                    for (int kk = 0; kk < 4; ++kk)
-                        if (pd[kk] <= -2) rb[kk] = ld_relaxed_u64(pub + (-pd[kk] - 2));
-                }
 #pragma unroll
                 for (int kk = 0; kk < 4; ++kk) {
                     const int p = pd[kk];
                     if (kRemote && p <= -2) {
-                        const double yv = rb[kk] != kSentinelBits ? __longlong_as_double((long long)rb[kk])
+                        const double yv = rq[kk] != kSentinelBits ? __longlong_as_double((long long)rq[kk])
                                                                   : remote_dep(pub, -p - 2, flags, D.spin);
                         acc = fma(-cur.l[kk], (T)yv, acc);
+                    } else if (kRemote) {
+                        acc = fma(-cur.l[kk], yl[kk], acc);   // zero for a missing dependency
                     } else if (kWindow) {
                         acc = fma(-cur.l[kk], win[p], acc);
                     } else if (p >= 0) {
