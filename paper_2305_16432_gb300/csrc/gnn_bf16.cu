@@ -426,14 +426,16 @@ __global__ void __launch_bounds__(kThreads) k_mlp_bf16(Bf16Args a) {
 // tcgen05.ld, adds the bias, applies ReLU and stages the next layer's
 // operand.  The first layer's commit releases the operand stage to the
 // producer.  One CTA per SM; every wait is bounded.
-constexpr int kWsStages = 3;
-constexpr int kWsThreads = 2 * kM + 32;
+// NG epilogue warpgroups (NG tiles in flight per SM), S operand stages
+__host__ __device__ constexpr int ws_threads(int ng) { return ng * kM + 32; }
+// TMEM columns: 64 per warpgroup, allocated as a power of two
+__host__ __device__ constexpr uint32_t ws_tmem_cols(int ng) { return ng <= 2 ? 128u : 256u; }
 
 struct WsPlan {
-    uint32_t w, a0, a1, bias, bars, tslot, total;
+    uint32_t w, a0, a1, bias, bars, tslot, gen, total;
 };
 
-__host__ __device__ inline WsPlan ws_plan(int mode, int depth) {
+__host__ __device__ inline WsPlan ws_plan(int mode, int depth, int ng, int stages) {
     const int in = mode_in(mode, kH);
     const int last = mode == MODE_DEC ? depth - 1 : depth;
     uint32_t wbytes = 0;
@@ -441,12 +443,13 @@ __host__ __device__ inline WsPlan ws_plan(int mode, int depth) {
     WsPlan p;
     p.w = 0;
     p.a0 = p.w + wbytes;                                        // [stage][in / 64 K-blocks][128 x 64]
-    p.a1 = p.a0 + (uint32_t)kWsStages * (uint32_t)(in / 64) * (kM * 128);   // [warpgroup][128 x 64]
-    p.bias = p.a1 + 2u * (kM * 128);                            // FP32 biases + decoder scalar layer
+    p.a1 = p.a0 + (uint32_t)stages * (uint32_t)(in / 64) * (kM * 128);   // [warpgroup][128 x 64]
+    p.bias = p.a1 + (uint32_t)ng * (kM * 128);                  // FP32 biases + decoder scalar layer
     p.bars = p.bias + (uint32_t)(depth + 1) * kH * 4 + (kH + 1) * 4;
-    p.bars = (p.bars + 15) & ~15u;                              // full[S], empty[S], mma[2]
-    p.tslot = p.bars + (uint32_t)(2 * kWsStages + 2) * 8;
-    p.total = p.tslot + 16;
+    p.bars = (p.bars + 15) & ~15u;                              // full[S], empty[S], mma[NG]
+    p.tslot = p.bars + (uint32_t)(2 * stages + ng) * 8;
+    p.gen = p.tslot + 16;                                       // tile last started in each stage
+    p.total = p.gen + (uint32_t)stages * 4 + 16;
     return p;
 }
 
@@ -470,8 +473,10 @@ __device__ __forceinline__ bool group_agree(int g, bool ok) {
     return all_ok != 0;
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(kWsThreads, 1) k_mlp_bf16_ws(Bf16Args a) {
+template <int MODE, int NG, int S>
+__global__ void __launch_bounds__(ws_threads(NG), 1) k_mlp_bf16_ws(Bf16Args a) {
+    constexpr int kWsStages = S;
+    constexpr int kWsThreads = ws_threads(NG);
     static_assert(MODE == MODE_EDGE || MODE == MODE_DEC, "pure-copy operand modes only");
     extern __shared__ __align__(1024) unsigned char sm_raw[];
     unsigned char* sm = sm_raw + ((1024u - (s_addr(sm_raw) & 1023u)) & 1023u);
@@ -480,7 +485,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_mlp_bf16_ws(Bf16Args a) {
     constexpr int CH = IN / 8;                 // 16-byte chunks per operand row
     const int depth = a.depth;
     const int last = MODE == MODE_DEC ? depth - 1 : depth;
-    const WsPlan P = ws_plan(MODE, depth);
+    const WsPlan P = ws_plan(MODE, depth, NG, S);
     unsigned char* W = sm + P.w;
     unsigned char* A0 = sm + P.a0;
     unsigned char* A1 = sm + P.a1;
@@ -490,6 +495,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_mlp_bf16_ws(Bf16Args a) {
     uint64_t* empty = full + kWsStages;
     uint64_t* mbar = empty + kWsStages;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + P.tslot);
+    int* sgen = reinterpret_cast<int*>(sm + P.gen);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     // ---- weights (BF16, swizzled K-blocks) and biases, once per CTA
@@ -518,12 +524,13 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_mlp_bf16_ws(Bf16Args a) {
             ws_bar_init(&full[s], 32);
             ws_bar_init(&empty[s], 1);
         }
-        ws_bar_init(&mbar[0], 1);
-        ws_bar_init(&mbar[1], 1);
+        for (int g = 0; g < NG; ++g) ws_bar_init(&mbar[g], 1);
+        for (int q = 0; q < S; ++q) sgen[q] = -1;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(s_addr(tmem_slot))
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s_addr(tmem_slot)),
+                     "n"(ws_tmem_cols(NG))
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -535,7 +542,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_mlp_bf16_ws(Bf16Args a) {
     const int64_t ntiles = (a.nrows + kM - 1) / kM;
     bool ok = true;
 
-    if (warp == 2 * kM / 32) {
+    if (warp == NG * kM / 32) {
         // ---------------- producer warp: operand rows of tile j into stage j % S
         int nrow[4], ncol[4];
         auto load_idx = [&](int64_t tile) {
@@ -558,6 +565,8 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_mlp_bf16_ws(Bf16Args a) {
                     break;
                 }
             }
+            // the stage is free for tile j (its previous tile j - S was read)
+            if (lane == 0) *reinterpret_cast<volatile int*>(sgen + s) = (int)j;
             unsigned char* dst = A0 + (uint32_t)s * NKB * (kM * 128);
             int crow[4], ccol[4];
 #pragma unroll
@@ -594,11 +603,22 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_mlp_bf16_ws(Bf16Args a) {
         unsigned char* A1g = A1 + (uint32_t)g * (kM * 128);
         uint32_t mphase = 0;
         const bool elected = r == 0;
-        for (int64_t j = g;; j += 2) {
+        for (int64_t j = g;; j += NG) {
             const int64_t tile = blockIdx.x + j * gridDim.x;
             if (tile >= ntiles) break;
             const int s = (int)(j % kWsStages);
-            const bool got = bar_wait(&full[s], (uint32_t)((j / kWsStages) & 1));
+            // A parity wait tells only the last two phases of a stage apart.
+            // With more warpgroups than stages this warpgroup can ask for tile
+            // j while the stage still waits for tile j - S, whose phase has
+            // the other parity but is not the one wanted; it first waits
+            // (bounded) until the producer has started tile j in the stage.
+            bool got = true;
+            if constexpr (NG > S) {
+                long long spins = 0;
+                while (*reinterpret_cast<volatile int*>(sgen + s) < (int)j)
+                    if (++spins >= kWaitSpin) { got = false; break; }
+            }
+            got = got && bar_wait(&full[s], (uint32_t)((j / kWsStages) & 1));
             if (!group_agree(g, got)) { ok = false; break; }
             tc_fence_after();
             uint32_t woff = 0;
@@ -701,24 +721,38 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_mlp_bf16_ws(Bf16Args a) {
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem) : "memory");
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(ws_tmem_cols(NG))
+                     : "memory");
+}
+
+template <int MODE, int NG, int S>
+bool launch_ws(Handle* h, const Bf16Args& a, npcg_status* st) {
+    const WsPlan p = ws_plan(MODE, a.depth, NG, S);
+    const size_t smem = p.total + 1024;   // alignment slack
+    if (smem > 227 * 1024) return false;
+    *st = NPCG_OK;
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_bf16_ws<MODE, NG, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) { *st = cuda_fail(h, e, "cudaFuncSetAttribute(k_mlp_bf16_ws)"); return true; }
+    const int64_t ntiles = (a.nrows + kM - 1) / kM;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)h->num_sms));
+    k_mlp_bf16_ws<MODE, NG, S><<<grid, ws_threads(NG), smem, h->stream>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) *st = cuda_fail(h, e, "k_mlp_bf16_ws");
+    return true;
 }
 
 template <int MODE>
 npcg_status launch_bf16(Handle* h, const Bf16Args& a) {
     if (a.nrows == 0) return NPCG_OK;
     if constexpr (MODE == MODE_EDGE || MODE == MODE_DEC) {
-        const WsPlan p = ws_plan(MODE, a.depth);
-        const size_t smem = p.total + 1024;   // alignment slack
-        if (smem <= 227 * 1024) {
-            NPCG_CUDA(h, cudaFuncSetAttribute(k_mlp_bf16_ws<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)smem));
-            const int64_t ntiles = (a.nrows + kM - 1) / kM;
-            const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)h->num_sms));
-            k_mlp_bf16_ws<MODE><<<grid, kWsThreads, smem, h->stream>>>(a);
-            NPCG_CUDA(h, cudaGetLastError());
-            return NPCG_OK;
-        }
+        // three tiles in flight per SM where three operand stages fit beside
+        // them, else three tiles over two stages, else two tiles over three
+        npcg_status st = NPCG_OK;
+        if (launch_ws<MODE, 3, 3>(h, a, &st)) return st;
+        if (launch_ws<MODE, 3, 2>(h, a, &st)) return st;
+        if (launch_ws<MODE, 2, 3>(h, a, &st)) return st;
     }
     const SmemPlan p = plan(MODE, a.depth);
     const size_t smem = p.total + 1024;       // alignment slack
