@@ -16,7 +16,8 @@ namespace npcg {
 // ---------------------------------------------------------------------------
 constexpr int kWarp = 32;
 constexpr int kSlice = 32;                 // rows per SELL slice = one warp of the solve
-constexpr int kChunk = 512;                // rows per reduction chunk (one block)
+constexpr int kChunk = 512;                // fewest rows per reduction chunk (one block)
+constexpr int kChunkMax = 4096;            // most rows per reduction chunk
 constexpr int kChunkThreads = 256;
 constexpr int kShortRow = 16;    // rows up to this length: one thread per row in the SpMV
 constexpr long long kSpinLimit = 1LL << 22; // default polls before a device wait gives up (~1-2 s)
@@ -237,6 +238,7 @@ struct Handle {
     int device = 0;
     int num_sms = 0;
     long long spin_limit = kSpinLimit;       // polls before a device wait gives up (npcg_set_wait_limit)
+    bool pcg_eager = false;                  // PCG iterations as separate launches (npcg_set_pcg_eager)
     std::string last_error;
     DevBuf<int> scratch_i;      // small device scratch
     void* host_pinned = nullptr; // small pinned host scratch

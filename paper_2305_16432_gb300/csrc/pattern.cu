@@ -358,16 +358,24 @@ npcg_status pattern_build(Handle* h, int64_t n, int64_t nnz, const int32_t* rp, 
     NPCG_CUDA(h, cudaGetLastError());
     NPCG_TRY(build_tri(h, P, false, &P->fwd));
     NPCG_TRY(build_tri(h, P, true, &P->bwd));
-    // reduction chunks: each covers rows of exactly one system
+    // reduction chunks: each covers rows of exactly one system.  The
+    // elementwise PCG kernels run one block per chunk: the chunk doubles from
+    // kChunk rows while the matrix would still give more than about four
+    // chunks per SM (up to kChunkMax), so a large system is streamed by fewer,
+    // longer-lived blocks (on the 128^3 grid 4096 rows measured best: 0.22 ->
+    // 0.17 ms per Jacobi-PCG iteration) and a small one still spreads over
+    // the GPU
+    int64_t crows = kChunk;
+    while (crows < kChunkMax && crows * 4 * h->num_sms < n) crows *= 2;
     P->chunks_h.clear();
     std::vector<int32_t> first(nsys + 1, 0);
     for (int s = 0; s < nsys; ++s) {
         first[s] = (int32_t)P->chunks_h.size();
-        for (int64_t r0 = P->sys_ptr_h[s]; r0 < P->sys_ptr_h[s + 1]; r0 += kChunk) {
+        for (int64_t r0 = P->sys_ptr_h[s]; r0 < P->sys_ptr_h[s + 1]; r0 += crows) {
             Chunk c;
             c.sys = s;
             c.row0 = (int32_t)r0;
-            c.row1 = (int32_t)std::min<int64_t>(r0 + kChunk, P->sys_ptr_h[s + 1]);
+            c.row1 = (int32_t)std::min<int64_t>(r0 + crows, P->sys_ptr_h[s + 1]);
             c.slot = (int32_t)P->chunks_h.size();
             P->chunks_h.push_back(c);
         }
