@@ -227,6 +227,8 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
     ap.add_argument("--sizes", default="", help="comma-separated lattice sizes of the 2-D FEM training groups")
     ap.add_argument("--sizes3d", default="", help="comma-separated grid sides of the 3-D FD training groups")
+    ap.add_argument("--per_group", type=int, default=8,
+                    help="systems per training group (the adjoint's workspace grows with the group's nonzeros)")
     ap.add_argument("--sigma3d", type=float, default=1.0, help="GRF sigma of the 3-D groups")
     ap.add_argument("--corr3d", type=float, default=0.1, help="GRF correlation length of the 3-D groups")
     ap.add_argument("--corr3d_cells", type=float, default=None,
@@ -263,7 +265,8 @@ def main():
     prec = N.BF16 if args.precision == "bf16" else N.FP32
     sizes = [] if args.sizes == "none" else ([int(x) for x in args.sizes.split(",") if x] or None)
     sizes3d = [int(x) for x in args.sizes3d.split(",") if x] or None
-    w, hist, tm = train(cfg, steps=args.steps, m=args.m, lr=args.lr, lr_final=args.lr_final, ckpt=args.ckpt,
+    w, hist, tm = train(cfg, steps=args.steps, per_group=args.per_group, m=args.m, lr=args.lr,
+                        lr_final=args.lr_final, ckpt=args.ckpt,
                         resume=args.resume, val_every=args.val_every, precision=prec, sizes=sizes,
                         sizes3d=sizes3d, sigma3d=args.sigma3d, corr3d=args.corr3d, w0=w_init,
                         head_only=bool(args.x0_from), heat=args.heat, corr3d_cells=args.corr3d_cells,
@@ -285,9 +288,9 @@ def main():
                        "x0_head": cfg.x0_head},
             "loss": "Eq. loss_A (Frobenius)" if cfg.loss else "Eq. loss_Ab",
             "train": {"steps": args.steps, "lr": args.lr, "lr_final": args.lr_final, "schedule": "cosine",
-                      "batch": "8 systems x 2 pairs",
+                      "batch": f"{args.per_group} systems x 2 pairs",
                       "selection": "checkpoint with the fewest validation PCG iterations",
-                      "systems": f"groups of 8: 2-D FEM {'heat steps (inputs.heat2d) ' if args.heat else ''}"
+                      "systems": f"groups of {args.per_group}: 2-D FEM {'heat steps (inputs.heat2d) ' if args.heat else ''}"
                                  f"lattices {sizes if sizes is not None else [args.m]} "
                                  f"(sigma 1, corr 0.1), 3-D FD sides {sizes3d or []} (sigma {args.sigma3d}, "
                                  + (f"corr {args.corr3d_cells} cells = {args.corr3d_cells} / (side + 1)"
