@@ -254,7 +254,8 @@ def solve_config(args, cfg, wkind, n, nnz, nnz_L, levels, nsys):
             "nnz_L": int(nnz_L), "levels": int(levels),
             "gnn": f"n_mp={cfg.n_mp},l={cfg.l},l_mp={cfg.l_mp},h={cfg.h},diag_mode={cfg.diag_mode},"
                    + args.precision + (",x0_head" if args.x0 else ""),
-            "weights": wkind, "pcg": "fp64 recurrences, " + args.apply + " L L^T solves",
+            "weights": wkind, "pcg": "fp64 recurrences, " + args.apply + " L L^T solves"
+                                     + (", eager launches (profiling)" if getattr(args, "eager_pcg", False) else ""),
             "rtol": RTOL, "l2": L2_FLUSH}
 
 
@@ -757,6 +758,10 @@ def main():
     ap.add_argument("--validate-oracle-estimate", action="store_true",
                     help="run the oracle's full learned path on the 256^2 FEM system beside its sampled estimate")
     ap.add_argument("--trsv-reps", type=int, default=50)
+    ap.add_argument("--eager-pcg", action="store_true",
+                    help="launch each PCG iteration's kernels one by one instead of the device-side loop graph "
+                         "(kernel profilers do not see kernels inside a conditional graph node; results are "
+                         "identical, the timing is not the benchmark's)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.weights is None:
@@ -776,6 +781,9 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2305_16432_gb300 import build as B
     B.build()
+    if args.eager_pcg:
+        from paper_2305_16432_gb300 import npcg as N
+        N.handle().set_pcg_eager(True)
     if args.workload == "train_32":
         run_train(args, rank, world, local)
     else:

@@ -80,6 +80,15 @@ NPCG_API const char* npcg_last_error(npcg_handle h);
  * (e.g. 2^10) lets a failure-detection test make a wait run out quickly; a
  * limit too short for a real workload makes its solves time out. */
 NPCG_API npcg_status npcg_set_wait_limit(npcg_handle h, int64_t polls);
+/* How later PCG calls on this handle launch their iterations (Algorithm 1's
+ * loop).  eager = 0 (default): the loop body is a CUDA graph with a
+ * device-side while node, launched once per solve.  eager != 0: the same
+ * kernels in the same order are enqueued one launch at a time, with the
+ * handle's stream synchronised every 16 iterations to test whether any
+ * system is still iterating.  Results are bit-identical; eager launches
+ * cost more host time.  Kernel profilers do not see the kernels inside a
+ * conditional graph node, so this exists to profile a solve's iterations. */
+NPCG_API npcg_status npcg_set_pcg_eager(npcg_handle h, int32_t eager);
 NPCG_API const char* npcg_status_string(npcg_status s);
 
 /* --------------------------------------------------------------------------

@@ -95,6 +95,12 @@ npcg_status npcg_set_wait_limit(npcg_handle h, int64_t polls) {
     return NPCG_OK;
 }
 
+npcg_status npcg_set_pcg_eager(npcg_handle h, int32_t eager) {
+    if (!h) return NPCG_EINVAL;
+    h->pcg_eager = eager != 0;
+    return NPCG_OK;
+}
+
 npcg_status npcg_assemble_count(npcg_handle h, const npcg_problem* p, int64_t* n_out, int64_t* nnz_out) {
     if (!h) return NPCG_EINVAL;
     if (!n_out || !nnz_out) return set_error(H(h), NPCG_EINVAL, "n_out / nnz_out are NULL");

@@ -964,8 +964,25 @@ npcg_status pcg_run(Handle* h, Pattern* P, const double* A_val, const double* b,
     if (precond >= NPCG_PREC_LLT) NPCG_TRY(apply_llt(h, h->stream, P, P->nsys > 1, precond == NPCG_PREC_LLT32));
     k_dot_rz<<<P->nchunks, kChunkThreads, 0, h->stream>>>(a, 1);
     NPCG_CUDA(h, cudaGetLastError());
-    NPCG_TRY(build_graph(h, P, precond));
-    if (max_iter > 0) NPCG_CUDA(h, cudaGraphLaunch(P->graph[precond], h->stream));
+    if (h->pcg_eager) {
+        // the graph body's kernels enqueued one launch at a time, 16
+        // iterations between tests of the active count (a system that has
+        // stopped makes the kernels of later iterations return at once)
+        constexpr int kEagerPairs = 8;
+        for (int done = 0; done < max_iter; done += 2 * kEagerPairs) {
+            for (int k = 0; k < kEagerPairs; ++k) {
+                NPCG_TRY(enqueue_iteration(h, h->stream, P, a, P->p0.p, P->p1.p));
+                NPCG_TRY(enqueue_iteration(h, h->stream, P, a, P->p1.p, P->p0.p));
+            }
+            int ctl2[2] = {0, 0};
+            NPCG_CUDA(h, cudaMemcpyAsync(ctl2, P->ctl.p, sizeof(ctl2), cudaMemcpyDeviceToHost, h->stream));
+            NPCG_CUDA(h, cudaStreamSynchronize(h->stream));
+            if (ctl2[0] <= 0 || (ctl2[1] & kFlagAbort)) break;
+        }
+    } else {
+        NPCG_TRY(build_graph(h, P, precond));
+        if (max_iter > 0) NPCG_CUDA(h, cudaGraphLaunch(P->graph[precond], h->stream));
+    }
     // stats
     k_stats<<<ceil_div(P->nsys, 128), 128, 0, h->stream>>>(P->nsys, P->st.p, P->stats_dev.p);
     NPCG_CUDA(h, cudaMemcpyAsync(stats, P->stats_dev.p, P->nsys * sizeof(npcg_solve_stats),

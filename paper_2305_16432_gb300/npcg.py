@@ -104,6 +104,7 @@ def lib():
                 "npcg_sptrsv_timed": [vp, vp, i32, i32, vp, vp, i32, C.POINTER(dbl)],
                 "npcg_sptrsv_unclaimed": [vp, vp, i32, i32, vp, vp],
                 "npcg_set_wait_limit": [vp, i64],
+                "npcg_set_pcg_eager": [vp, i32],
                 "npcg_loss_and_grad": [vp, vp, vp, i32, vp, vp, C.POINTER(_Cfg), vp, C.POINTER(dbl), vp],
                 "npcg_adam_step": [vp, i64, vp, vp, vp, vp, i32, f32, f32, f32, f32],
                 "npcg_solve_host": [vp, vp, i32, C.POINTER(_Cfg), vp, vp, vp, vp, dbl, i32, i32, vp],
@@ -154,6 +155,10 @@ class Handle:
     def set_wait_limit(self, polls: int):
         """npcg_set_wait_limit: polls before a device wait gives up (<= 0: default)."""
         self.check(lib().npcg_set_wait_limit(self.h, C.c_int64(int(polls))))
+
+    def set_pcg_eager(self, eager: bool):
+        """npcg_set_pcg_eager: PCG iterations as separate launches (for kernel profilers)."""
+        self.check(lib().npcg_set_pcg_eager(self.h, 1 if eager else 0))
 
     def close(self):
         if getattr(self, "h", None):

@@ -227,3 +227,28 @@ def test_stagnation_window(N):
                                    fallback_ic0=True)
     assert status == N.NPCG_OK and st[0]["fallback"] == 1 and st[0]["iters"] == 2 and st[0]["fallback_iters"] == 1
     assert np.allclose(_np(x), [1.0, 1e-4], rtol=1e-12)
+
+
+# ------------------------------------------------------------ launch modes
+@pytest.mark.parametrize("prec", ["PREC_LLT32", "PREC_JACOBI"])
+def test_eager_iterations_identical_to_graph(N, prec):
+    # the loop graph and one-launch-at-a-time iterations run the same
+    # kernels in the same order: identical statistics and solution bits
+    Ao = O.assemble(I.fem2d(40, sigma=1.0, seed=8))
+    P = _pattern(N, Ao)
+    b = I.rhs(Ao.n, 12)
+    Lo, _ = O.ic0(Ao)
+    L = _gpu(Lo.val) if prec == "PREC_LLT32" else None
+    x1, st1 = N.pcg_solve(P, _gpu(Ao.val), _gpu(b), getattr(N, prec), L, rtol=1e-8)
+    x1 = _np(x1).copy()
+    P.h.set_pcg_eager(True)
+    try:
+        x2, st2 = N.pcg_solve(P, _gpu(Ao.val), _gpu(b), getattr(N, prec), L, rtol=1e-8)
+        x2 = _np(x2)
+        # a maximum below the eager batch of 16 iterations stops on time too
+        _, st3 = N.pcg_solve(P, _gpu(Ao.val), _gpu(b), getattr(N, prec), L, rtol=1e-8, max_iter=5)
+    finally:
+        P.h.set_pcg_eager(False)
+    assert st1[0]["status"] == 0 and st2[0]["status"] == 0
+    assert st1[0]["iters"] == st2[0]["iters"] and np.array_equal(x1, x2)
+    assert st3[0]["status"] == N.NPCG_EMAXITER and st3[0]["iters"] == 5
