@@ -248,14 +248,25 @@ def grad_allreduce_mean_(g, world):
     return g
 
 
+def pcg_launch_mode(args, n, nsys):
+    """How the library launches the PCG iterations here: one launch at a time
+    for a single system of 2^18 rows or more (its triangular solves run in
+    row blocks; the library's default), else the device-side loop graph."""
+    if getattr(args, "eager_pcg", False):
+        return "iterations launched one by one (forced, for profiling)"
+    if nsys == 1 and n >= (1 << 18):
+        return "iterations launched one by one (row-block solves)"
+    return "iterations in a device-side loop graph"
+
+
 def solve_config(args, cfg, wkind, n, nnz, nnz_L, levels, nsys):
     """The config block of the JSON line (identical on both arms)."""
     return {"workload": WORKLOAD_LABEL[args.workload], "systems_per_step": nsys, "n": int(n), "nnz": int(nnz),
             "nnz_L": int(nnz_L), "levels": int(levels),
             "gnn": f"n_mp={cfg.n_mp},l={cfg.l},l_mp={cfg.l_mp},h={cfg.h},diag_mode={cfg.diag_mode},"
                    + args.precision + (",x0_head" if args.x0 else ""),
-            "weights": wkind, "pcg": "fp64 recurrences, " + args.apply + " L L^T solves"
-                                     + (", eager launches (profiling)" if getattr(args, "eager_pcg", False) else ""),
+            "weights": wkind, "pcg": "fp64 recurrences, " + args.apply + " L L^T solves, "
+                                     + pcg_launch_mode(args, n, nsys),
             "rtol": RTOL, "l2": L2_FLUSH}
 
 
@@ -576,12 +587,16 @@ def run_solve(args, rank, world, local):
     # kernel launches per learned step (counted from the launch structure):
     # network: scales, 2 encoders, 2 per layer, decoder, L assembly
     gnn_launches = 1 + 2 + 2 * cfg.n_mp + 1 + 1
-    # PCG: factor loads, init, preconditioner apply, r^T z, per graph trip 2
-    # iterations (SpMV, update, r^T z and the apply) + the loop condition, stats
+    # PCG: factor loads, init, preconditioner apply, r^T z, then per graph
+    # trip 2 iterations (SpMV, update, r^T z and the apply) + the loop
+    # condition, or one by one in batches of 16 iterations, and the stats
     apply = {"levelsync": 4, "levelflag": 4, "levelsplit": 4, "levelmerge": 5}.get(design, 2)
     loads = 2 + (2 * P.merge_levels if design == "levelmerge" else 0) + 2
-    trips = max(1, math.ceil(max(it_l) / 2))
-    pcg_launches = loads + 1 + apply + 1 + (2 * (3 + apply) + 1) * trips + 1
+    if "one by one" in pcg_launch_mode(args, P.n, nsys):
+        loop = (3 + apply) * 16 * max(1, math.ceil(max(it_l) / 16))
+    else:
+        loop = (2 * (3 + apply) + 1) * max(1, math.ceil(max(it_l) / 2))
+    pcg_launches = loads + 1 + apply + 1 + loop + 1
     launches = (gnn_launches + pcg_launches) * args.steps
 
     cpu = None

@@ -81,13 +81,19 @@ NPCG_API const char* npcg_last_error(npcg_handle h);
  * limit too short for a real workload makes its solves time out. */
 NPCG_API npcg_status npcg_set_wait_limit(npcg_handle h, int64_t polls);
 /* How later PCG calls on this handle launch their iterations (Algorithm 1's
- * loop).  eager = 0 (default): the loop body is a CUDA graph with a
- * device-side while node, launched once per solve.  eager != 0: the same
- * kernels in the same order are enqueued one launch at a time, with the
- * handle's stream synchronised every 16 iterations to test whether any
- * system is still iterating.  Results are bit-identical; eager launches
- * cost more host time.  Kernel profilers do not see the kernels inside a
- * conditional graph node, so this exists to profile a solve's iterations. */
+ * loop).  eager = 0: the loop body is a CUDA graph with a device-side while
+ * node, launched once per solve.  eager > 0: the same kernels in the same
+ * order are enqueued one launch at a time, with the handle's stream
+ * synchronised every 16 iterations to test whether any system is still
+ * iterating.  eager < 0 (the default): one launch at a time for the
+ * triangular-solve preconditioners of a single system solved in row blocks
+ * (2^18 rows or more), where it measured faster (on the 128^3 grid, 176
+ * IC(0)-PCG iterations with FP32 solves: 175.6 against 180.2 ms), the graph
+ * otherwise (on a 256^2 FEM system the graph is faster: 39.3 against 41.1
+ * ms for the learned solve).
+ * Results are bit-identical in every mode.  Kernel profilers do not see the
+ * kernels inside a conditional graph node, so eager > 0 also serves to
+ * profile a solve's iterations. */
 NPCG_API npcg_status npcg_set_pcg_eager(npcg_handle h, int32_t eager);
 NPCG_API const char* npcg_status_string(npcg_status s);
 

@@ -97,7 +97,7 @@ npcg_status npcg_set_wait_limit(npcg_handle h, int64_t polls) {
 
 npcg_status npcg_set_pcg_eager(npcg_handle h, int32_t eager) {
     if (!h) return NPCG_EINVAL;
-    h->pcg_eager = eager != 0;
+    h->pcg_eager = eager > 0 ? 1 : eager == 0 ? 0 : -1;
     return NPCG_OK;
 }
 

@@ -238,7 +238,7 @@ struct Handle {
     int device = 0;
     int num_sms = 0;
     long long spin_limit = kSpinLimit;       // polls before a device wait gives up (npcg_set_wait_limit)
-    bool pcg_eager = false;                  // PCG iterations as separate launches (npcg_set_pcg_eager)
+    int pcg_eager = -1;                      // PCG iterations: 1 separate launches, 0 graph, -1 auto (npcg_set_pcg_eager)
     std::string last_error;
     DevBuf<int> scratch_i;      // small device scratch
     void* host_pinned = nullptr; // small pinned host scratch

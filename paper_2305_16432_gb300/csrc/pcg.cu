@@ -964,7 +964,14 @@ npcg_status pcg_run(Handle* h, Pattern* P, const double* A_val, const double* b,
     if (precond >= NPCG_PREC_LLT) NPCG_TRY(apply_llt(h, h->stream, P, P->nsys > 1, precond == NPCG_PREC_LLT32));
     k_dot_rz<<<P->nchunks, kChunkThreads, 0, h->stream>>>(a, 1);
     NPCG_CUDA(h, cudaGetLastError());
-    if (h->pcg_eager) {
+    // the default launches a row-block solve's iterations one by one: with
+    // its triangular solves they measured faster than the same kernels in
+    // the loop graph, while the graph wins for the other designs and for the
+    // elementwise preconditioners
+    const bool eager = h->pcg_eager > 0 ||
+                       (h->pcg_eager < 0 && precond >= NPCG_PREC_LLT && P->trsv_mode == kTrsvCta &&
+                        P->cfwd.built && P->cfwd.blocked);
+    if (eager) {
         // the graph body's kernels enqueued one launch at a time, 16
         // iterations between tests of the active count (a system that has
         // stopped makes the kernels of later iterations return at once)

@@ -156,9 +156,11 @@ class Handle:
         """npcg_set_wait_limit: polls before a device wait gives up (<= 0: default)."""
         self.check(lib().npcg_set_wait_limit(self.h, C.c_int64(int(polls))))
 
-    def set_pcg_eager(self, eager: bool):
-        """npcg_set_pcg_eager: PCG iterations as separate launches (for kernel profilers)."""
-        self.check(lib().npcg_set_pcg_eager(self.h, 1 if eager else 0))
+    def set_pcg_eager(self, eager):
+        """npcg_set_pcg_eager: True launches PCG iterations one by one, False
+        through the loop graph, None restores the default (one by one for a
+        row-block solve's triangular-solve preconditioners, else the graph)."""
+        self.check(lib().npcg_set_pcg_eager(self.h, -1 if eager is None else (1 if eager else 0)))
 
     def close(self):
         if getattr(self, "h", None):

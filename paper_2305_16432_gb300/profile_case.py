@@ -35,6 +35,9 @@ def main():
     ap.add_argument("--grid", type=int, default=64)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=2)
+    ap.add_argument("--trsv", default="auto", choices=["auto", "syncfree", "levelsync", "levelmerge"],
+                    help="triangular-solve design (default: the one the analysis tuned; a profiler's slowdown "
+                         "of the analysis' trial solves can change that choice)")
     ap.add_argument("--profile-range", action="store_true",
                     help="bracket the timed repetitions with cudaProfilerStart/Stop (for a profiler started "
                          "with --profile-from-start off)")
@@ -47,6 +50,8 @@ def main():
     prob = I.fd3d(side, sigma=1.5, corr_len=6.4 / (side + 1), seed=11)
     rp, ci, v = N.assemble_system(prob)
     P = N.analyse(rp, ci)
+    if args.trsv != "auto":
+        P.set_trsv(getattr(N, "TRSV_" + args.trsv.upper()))
     b = torch.as_tensor(I.rhs(P.n, 11), device="cuda")
     meta = json.load(open(os.path.splitext(WEIGHTS)[0] + ".json"))
     cfg = I.GnnConfig(**meta["config"])

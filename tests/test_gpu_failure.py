@@ -239,6 +239,7 @@ def test_eager_iterations_identical_to_graph(N, prec):
     b = I.rhs(Ao.n, 12)
     Lo, _ = O.ic0(Ao)
     L = _gpu(Lo.val) if prec == "PREC_LLT32" else None
+    P.h.set_pcg_eager(False)
     x1, st1 = N.pcg_solve(P, _gpu(Ao.val), _gpu(b), getattr(N, prec), L, rtol=1e-8)
     x1 = _np(x1).copy()
     P.h.set_pcg_eager(True)
@@ -248,7 +249,7 @@ def test_eager_iterations_identical_to_graph(N, prec):
         # a maximum below the eager batch of 16 iterations stops on time too
         _, st3 = N.pcg_solve(P, _gpu(Ao.val), _gpu(b), getattr(N, prec), L, rtol=1e-8, max_iter=5)
     finally:
-        P.h.set_pcg_eager(False)
+        P.h.set_pcg_eager(None)
     assert st1[0]["status"] == 0 and st2[0]["status"] == 0
     assert st1[0]["iters"] == st2[0]["iters"] and np.array_equal(x1, x2)
     assert st3[0]["status"] == N.NPCG_EMAXITER and st3[0]["iters"] == 5
