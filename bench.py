@@ -588,14 +588,14 @@ def run_solve(args, rank, world, local):
     # network: scales, 2 encoders, 2 per layer, decoder, L assembly
     gnn_launches = 1 + 2 + 2 * cfg.n_mp + 1 + 1
     # PCG: factor loads, init, preconditioner apply, r^T z, then per graph
-    # trip 2 iterations (SpMV, update, r^T z and the apply) + the loop
-    # condition, or one by one in batches of 16 iterations, and the stats
+    # trip 2 iterations (p update, SpMV, update, r^T z and the apply) + the
+    # loop condition, or one by one in batches of 16 iterations, and the stats
     apply = {"levelsync": 4, "levelflag": 4, "levelsplit": 4, "levelmerge": 5}.get(design, 2)
     loads = 2 + (2 * P.merge_levels if design == "levelmerge" else 0) + 2
     if "one by one" in pcg_launch_mode(args, P.n, nsys):
-        loop = (3 + apply) * 16 * max(1, math.ceil(max(it_l) / 16))
+        loop = (4 + apply) * 16 * max(1, math.ceil(max(it_l) / 16))
     else:
-        loop = (2 * (3 + apply) + 1) * max(1, math.ceil(max(it_l) / 2))
+        loop = (2 * (4 + apply) + 1) * max(1, math.ceil(max(it_l) / 2))
     pcg_launches = loads + 1 + apply + 1 + loop + 1
     launches = (gnn_launches + pcg_launches) * args.steps
 

@@ -215,14 +215,23 @@ __global__ void k_dot_rz(PcgArgs a, int init) {
     }
 }
 
-// p_new = z + beta p_old (recomputed for every neighbour, written for own
-// rows), w = A p_new, partial p_new^T w; finaliser: alpha = rz / p^T w.
-__global__ void k_spmv_p(PcgArgs a, const double* __restrict__ p_old, double* __restrict__ p_new) {
-    __shared__ double sh[1][kChunkThreads / 32];
+// p_new = z + beta p_old (Algorithm 1), streamed once per iteration so the
+// SpMV below gathers one vector
+__global__ void k_pnew(PcgArgs a, const double* __restrict__ p_old, double* __restrict__ p_new) {
     const Chunk c = a.chunks[blockIdx.x];
     const SysState& s0 = a.st[c.sys];
     if (!s0.active) return;
     const double beta = s0.beta;
+    for (int row = c.row0 + threadIdx.x; row < c.row1; row += kChunkThreads)
+        p_new[row] = fma(beta, p_old[row], a.z[row]);
+}
+
+// w = A p, partial p^T w; finaliser: alpha = rz / p^T w.
+__global__ void k_spmv_p(PcgArgs a, const double* __restrict__ p) {
+    __shared__ double sh[1][kChunkThreads / 32];
+    const Chunk c = a.chunks[blockIdx.x];
+    const SysState& s0 = a.st[c.sys];
+    if (!s0.active) return;
     double acc[1] = {0.0};
     if (a.short_rows) {
         // one thread per row: a warp keeps 32 rows' entries in flight (the
@@ -232,14 +241,9 @@ __global__ void k_spmv_p(PcgArgs a, const double* __restrict__ p_old, double* __
             const int k0 = a.rp[row], k1 = a.rp[row + 1];
             double s = 0.0;
 #pragma unroll 4
-            for (int k = k0; k < k1; ++k) {
-                const int j = a.ci[k];
-                s = fma(a.av[k], fma(beta, p_old[j], a.z[j]), s);
-            }
-            const double pi = fma(beta, p_old[row], a.z[row]);
-            p_new[row] = pi;
+            for (int k = k0; k < k1; ++k) s = fma(a.av[k], p[a.ci[k]], s);
             a.w[row] = s;
-            acc[0] = fma(pi, s, acc[0]);
+            acc[0] = fma(p[row], s, acc[0]);
         }
     } else {
         const int g = threadIdx.x & 7, sub = (threadIdx.x >> 3) & 3, warp = threadIdx.x >> 5;
@@ -248,17 +252,12 @@ __global__ void k_spmv_p(PcgArgs a, const double* __restrict__ p_old, double* __
             const bool valid = row < c.row1;
             double s = 0.0;
             const int k1 = valid ? a.rp[row + 1] : 0;
-            for (int k = valid ? a.rp[row] + g : 0; k < k1; k += 8) {
-                int j = a.ci[k];
-                s = fma(a.av[k], fma(beta, p_old[j], a.z[j]), s);
-            }
+            for (int k = valid ? a.rp[row] + g : 0; k < k1; k += 8) s = fma(a.av[k], p[a.ci[k]], s);
 #pragma unroll
             for (int o = 4; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, 8);
             if (g == 0 && valid) {
-                double pi = fma(beta, p_old[row], a.z[row]);
-                p_new[row] = pi;
                 a.w[row] = s;
-                acc[0] = fma(pi, s, acc[0]);
+                acc[0] = fma(p[row], s, acc[0]);
             }
         }
     }
@@ -635,7 +634,8 @@ npcg_status apply_llt(Handle* h, cudaStream_t s, Pattern* P, bool batched, bool 
 npcg_status enqueue_iteration(Handle* h, cudaStream_t s, Pattern* P, const PcgArgs& a, const double* p_old,
                               double* p_new) {
     const bool batched = P->nsys > 1;
-    k_spmv_p<<<P->nchunks, kChunkThreads, 0, s>>>(a, p_old, p_new);
+    k_pnew<<<P->nchunks, kChunkThreads, 0, s>>>(a, p_old, p_new);
+    k_spmv_p<<<P->nchunks, kChunkThreads, 0, s>>>(a, p_new);
     k_update<<<P->nchunks, kChunkThreads, 0, s>>>(a, p_new);
     if (a.precond >= NPCG_PREC_LLT) {
         NPCG_TRY(apply_llt(h, s, P, batched, a.precond == NPCG_PREC_LLT32));
@@ -879,12 +879,13 @@ npcg_status trsv_autotune(Handle* h, Pattern* P) {
     P->merge_G = 0;
     if (kMergeEnabled && P->n <= ((int64_t)1 << 22)) {
         // the host plan grows with G (eight levels per group on 2^21 rows
-        // take several gigabytes and tens of seconds to plan): G = 8 is tried
-        // below 2^20 rows only
+        // take several gigabytes and tens of seconds to plan, four about 8 s):
+        // above 2^20 rows only G = 2 is tried (on the 128^3 grid G = 4 never
+        // beat it)
         const int cand[3] = {2, 4, 8};
         double best_all = 1e30;
         for (int G : cand) {
-            if (G == 8 && P->n > ((int64_t)1 << 20)) continue;
+            if (G >= 4 && P->n > ((int64_t)1 << 20)) continue;
             if (merge_build(h, P, G) != NPCG_OK) continue;
             if (cta_stages(P->mfwd.lay) < 2 || cta_stages(P->mbwd.lay) < 2) continue;
             P->trsv_mode = kTrsvCta;
