@@ -237,38 +237,73 @@ __global__ void __launch_bounds__(kThreads) k_mlp_bf16(Bf16Args a) {
             }
             // sum_j e_ij (.) v_j over the row's edges in ascending order,
             // eight threads per row (one chunk each, so that the edge and node
-            // rows are read as whole lines); the column indices of up to eight
-            // edges, then their edge and node chunks, are loaded together, so
-            // a row costs a few round trips instead of two per edge
-            for (int idx = tid; idx < kM * 8; idx += kThreads) {
-                const int r = idx >> 3, c = idx & 7;
+            // rows are read as whole lines).  A thread's eight (row, chunk)
+            // items are software-pipelined: every item's edge range is read
+            // first, and the column indices of item k + 1's first eight edges
+            // are requested while item k's edge and node chunks are in
+            // flight, so an item costs about one round trip instead of three
+            // (rows with more than eight edges finish in batches of eight)
+            constexpr int kItems = kM * 8 / kThreads;
+            int rs[kItems], re[kItems];
+#pragma unroll
+            for (int k = 0; k < kItems; ++k) {
+                const int64_t i = row0 + ((tid + k * kThreads) >> 3);
+                rs[k] = i < a.nrows ? a.rp[i] : 0;
+                re[k] = i < a.nrows ? a.rp[i + 1] : 0;
+            }
+            int cj[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) cj[q] = rs[0] + q < re[0] ? a.ci[rs[0] + q] : -1;
+#pragma unroll
+            for (int k = 0; k < kItems; ++k) {
+                const int idx = tid + k * kThreads, r = idx >> 3, c = idx & 7;
                 const int64_t i = row0 + r;
-                uint4 val = make_uint4(0, 0, 0, 0);
-                if (i < a.nrows) {
-                    float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-                    const int k1 = a.rp[i + 1];
-                    for (int kb = a.rp[i]; kb < k1; kb += 8) {
-                        int cj[8];
+                float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                uint4 e4[8], v4[8];
 #pragma unroll
-                        for (int q = 0; q < 8; ++q) cj[q] = kb + q < k1 ? a.ci[kb + q] : -1;
-                        uint4 e4[8], v4[8];
+                for (int q = 0; q < 8; ++q) {
+                    if (cj[q] >= 0) {
+                        e4[q] = *reinterpret_cast<const uint4*>(a.ein + (int64_t)(rs[k] + q) * kH + c * 8);
+                        v4[q] = *reinterpret_cast<const uint4*>(a.vin + (int64_t)cj[q] * kH + c * 8);
+                    }
+                }
+                int cn[8];
+                if (k + 1 < kItems) {
 #pragma unroll
-                        for (int q = 0; q < 8; ++q) {
-                            if (cj[q] >= 0) {
-                                e4[q] = *reinterpret_cast<const uint4*>(a.ein + (int64_t)(kb + q) * kH + c * 8);
-                                v4[q] = *reinterpret_cast<const uint4*>(a.vin + (int64_t)cj[q] * kH + c * 8);
-                            }
-                        }
+                    for (int q = 0; q < 8; ++q) cn[q] = rs[k + 1] + q < re[k + 1] ? a.ci[rs[k + 1] + q] : -1;
+                }
 #pragma unroll
-                        for (int q = 0; q < 8; ++q) {
-                            if (cj[q] < 0) break;
-                            const __nv_bfloat16* e8 = reinterpret_cast<const __nv_bfloat16*>(&e4[q]);
-                            const __nv_bfloat16* v8 = reinterpret_cast<const __nv_bfloat16*>(&v4[q]);
+                for (int q = 0; q < 8; ++q) {
+                    if (cj[q] < 0) break;
+                    const __nv_bfloat16* e8 = reinterpret_cast<const __nv_bfloat16*>(&e4[q]);
+                    const __nv_bfloat16* v8 = reinterpret_cast<const __nv_bfloat16*>(&v4[q]);
 #pragma unroll
-                            for (int j = 0; j < 8; ++j)
-                                acc[j] = fmaf(__bfloat162float(e8[j]), __bfloat162float(v8[j]), acc[j]);
+                    for (int j = 0; j < 8; ++j)
+                        acc[j] = fmaf(__bfloat162float(e8[j]), __bfloat162float(v8[j]), acc[j]);
+                }
+                for (int kb = rs[k] + 8; kb < re[k]; kb += 8) {
+                    int cx[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) cx[q] = kb + q < re[k] ? a.ci[kb + q] : -1;
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        if (cx[q] >= 0) {
+                            e4[q] = *reinterpret_cast<const uint4*>(a.ein + (int64_t)(kb + q) * kH + c * 8);
+                            v4[q] = *reinterpret_cast<const uint4*>(a.vin + (int64_t)cx[q] * kH + c * 8);
                         }
                     }
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        if (cx[q] < 0) break;
+                        const __nv_bfloat16* e8 = reinterpret_cast<const __nv_bfloat16*>(&e4[q]);
+                        const __nv_bfloat16* v8 = reinterpret_cast<const __nv_bfloat16*>(&v4[q]);
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            acc[j] = fmaf(__bfloat162float(e8[j]), __bfloat162float(v8[j]), acc[j]);
+                    }
+                }
+                uint4 val = make_uint4(0, 0, 0, 0);
+                if (i < a.nrows) {
                     __nv_bfloat16 h8[8];
 #pragma unroll
                     for (int j = 0; j < 8; ++j) h8[j] = __float2bfloat16_rn(acc[j]);
@@ -280,6 +315,10 @@ __global__ void __launch_bounds__(kThreads) k_mlp_bf16(Bf16Args a) {
                     }
                 }
                 *reinterpret_cast<uint4*>(A0 + kM * 128 + swz(r, c * 8)) = val;
+                if (k + 1 < kItems) {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) cj[q] = cn[q];
+                }
             }
         } else {      // EDGE: [e | v_row | v_col], DEC: [e]
             constexpr int CH = IN >= 8 ? IN / 8 : 1;     // (encoders never reach here)
