@@ -35,3 +35,17 @@ def test_bench_picks_each_workloads_network():
     assert meta3["config"]["diag_mode"] == 2 and meta3["bench_iters"]["fd3d_128"] > 0
     meta = json.load(open(os.path.join(WDIR, "gnn_6x64_fem2d_x0.json")))
     assert meta["config"]["x0_head"] == 1
+
+
+def test_bench_describes_the_library_launch_mode():
+    # the library launches a single system's PCG iterations one by one from
+    # 2^18 rows (its triangular solves run in row blocks there), and through
+    # the loop graph otherwise; --eager-pcg forces one by one
+    class A:
+        eager_pcg = False
+    assert "one by one" in bench.pcg_launch_mode(A(), 128 ** 3, 1)
+    assert "one by one" in bench.pcg_launch_mode(A(), 1 << 18, 1)
+    assert "graph" in bench.pcg_launch_mode(A(), (1 << 18) - 1, 1)
+    assert "graph" in bench.pcg_launch_mode(A(), 28_800_000, 256)
+    A.eager_pcg = True
+    assert "forced" in bench.pcg_launch_mode(A(), 256 * 256, 1)
