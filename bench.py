@@ -248,13 +248,15 @@ def grad_allreduce_mean_(g, world):
     return g
 
 
-def pcg_launch_mode(args, n, nsys):
-    """How the library launches the PCG iterations here: one launch at a time
-    for a single system of 2^18 rows or more (its triangular solves run in
-    row blocks; the library's default), else the device-side loop graph."""
+def pcg_launch_mode(args, n, nsys, design=None):
+    """How the library launches the PCG iterations of a triangular-solve
+    preconditioner here: one launch at a time for a single system of 2^18
+    rows or more whose tuned solve is level-ordered (it then runs in row
+    blocks; the library's default), else the device-side loop graph.
+    design: the tuned design's name, None when not yet known."""
     if getattr(args, "eager_pcg", False):
         return "iterations launched one by one (forced, for profiling)"
-    if nsys == 1 and n >= (1 << 18):
+    if nsys == 1 and n >= (1 << 18) and design != "syncfree":
         return "iterations launched one by one (row-block solves)"
     return "iterations in a device-side loop graph"
 
@@ -592,7 +594,7 @@ def run_solve(args, rank, world, local):
     # loop condition, or one by one in batches of 16 iterations, and the stats
     apply = {"levelsync": 4, "levelflag": 4, "levelsplit": 4, "levelmerge": 5}.get(design, 2)
     loads = 2 + (2 * P.merge_levels if design == "levelmerge" else 0) + 2
-    if "one by one" in pcg_launch_mode(args, P.n, nsys):
+    if "one by one" in pcg_launch_mode(args, P.n, nsys, design):
         loop = (4 + apply) * 16 * max(1, math.ceil(max(it_l) / 16))
     else:
         loop = (2 * (4 + apply) + 1) * max(1, math.ceil(max(it_l) / 2))

@@ -47,5 +47,7 @@ def test_bench_describes_the_library_launch_mode():
     assert "one by one" in bench.pcg_launch_mode(A(), 1 << 18, 1)
     assert "graph" in bench.pcg_launch_mode(A(), (1 << 18) - 1, 1)
     assert "graph" in bench.pcg_launch_mode(A(), 28_800_000, 256)
+    assert "graph" in bench.pcg_launch_mode(A(), 128 ** 3, 1, "syncfree")
+    assert "one by one" in bench.pcg_launch_mode(A(), 128 ** 3, 1, "levelmerge")
     A.eager_pcg = True
     assert "forced" in bench.pcg_launch_mode(A(), 256 * 256, 1)
